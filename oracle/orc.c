@@ -1,0 +1,449 @@
+/*
+ * orc.c -- plain FP64 CPU oracle of the MITHRA FDTD/PIC time step.
+ *
+ * TEST INFRASTRUCTURE ONLY (see orc.h).  Written from the paper's method
+ * chapter as plain loops in the paper's order and notation: no tiling, no
+ * sorting, no fusion; particles are summed serially in index order.  The grid
+ * loops carry OpenMP pragmas only where every iteration writes its own
+ * vertex, so the thread count never changes a result.
+ *
+ * Readings of the paper that this file takes (the paper is silent, garbled or
+ * self-contradictory at these points):
+ *   - alpha'_6 = alpha'_7 uses (c dt/dy)^2 in its last term (the printed
+ *     second dx is a typo; re-derived from Eq. NSFDtrick).
+ *   - source sign: psi^{n+1} gets +(c dt)^2 * mu0 J for A and
+ *     +(c dt)^2 * rho/eps0 for phi (the physical sign of Eq. HelmholtzA/F).
+ *   - the B_z formula uses A_y in both x-difference terms.
+ *   - the CIC weights are w0 = 1 - delta/D, w1 = delta/D (Eq.
+ *     fieldInterpolation without the absolute value).
+ *   - phi^n belongs to t = (n+1/2) dt and uses rho^{n+1/2} as its source.
+ *   - J^{n+1} is deposited at the mid point of the particle's path over the
+ *     field step with the CIC weights (Eq. currentIntegral).
+ *   - the rest-frame undulator fields follow from the Lorentz transformation
+ *     of the lab field: E_x = -gamma0 beta0 c B'_y, B_y = gamma0 B'_y,
+ *     B_z = B'_z, at lab position z' = gamma0 (z + beta0 c t).
+ *   - the undulator exit (when the length is finite) carries the same taper
+ *     as the entrance, in the distance past the exit.
+ *   - Mur first order at edges and corners: the one-dimensional condition
+ *     along the outward diagonal to the nearest interior vertex, with the
+ *     diagonal length as the spacing.
+ *   - a particle whose cell leaves [1, n-3] in any axis is lost: it deposits
+ *     nothing from that step on.
+ */
+#include "orc.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* CODATA 2018 (exact SI values for c and e). */
+#define ORC_C    299792458.0
+#define ORC_E    1.602176634e-19
+#define ORC_ME   9.1093837015e-31
+#define ORC_EPS0 8.8541878128e-12
+#define ORC_MU0  (1.0 / (ORC_EPS0 * ORC_C * ORC_C))
+#define ORC_PI   3.14159265358979323846
+
+void orc_constants(double out[5]) {
+    out[0] = ORC_C;
+    out[1] = ORC_E;
+    out[2] = ORC_ME;
+    out[3] = ORC_EPS0;
+    out[4] = ORC_MU0;
+}
+
+static inline int64_t ix(const orc_grid* g, int i, int j, int k) {
+    return ((int64_t)k * g->ny + j) * g->nx + i;
+}
+
+static inline int64_t ncell(const orc_grid* g) {
+    return (int64_t)g->nx * g->ny * g->nz;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Coefficients: Sec. "Numerical Dispersion in FDTD", Eq. NSFDCoefficient and
+ * the alpha' table under Eq. updateEquation.  The standard central-difference
+ * scheme is the same table with A = 0. */
+int orc_coefficients(const orc_grid* g, double out[6]) {
+    double cdt = ORC_C * g->dt;
+    double rx2 = (cdt / g->dx) * (cdt / g->dx);
+    double ry2 = (cdt / g->dy) * (cdt / g->dy);
+    double rz2 = (cdt / g->dz) * (cdt / g->dz);
+    double A = 0.0;
+    if (g->stencil == 0) {
+        double qx = g->dz / g->dx, qy = g->dz / g->dy;
+        A = 0.25 * (1.0 + 0.02 / (qx * qx + qy * qy));
+    }
+    out[0] = A;
+    out[1] = 2.0 * (1.0 - (1.0 - 2.0 * A) * rx2 - (1.0 - 2.0 * A) * ry2 - rz2);
+    out[2] = rx2;
+    out[3] = ry2;
+    out[4] = rz2 - 2.0 * A * rx2 - 2.0 * A * ry2;
+    out[5] = cdt * cdt;
+    /* Stability.  Standard scheme: Eq. CFLcondition.  NSFD: the left side of
+     * Eq. NSFDDispersionCD times (c dt)^2 is linear in sin^2(kz dz/2), so its
+     * maximum is max(rx2 + ry2, rz2); a real omega needs that <= 1. */
+    if (g->stencil == 0) {
+        if (rx2 + ry2 >= 1.0) return 1;
+        if (rz2 > 1.0 + 1e-12) return 1;
+        return 0;
+    }
+    return (rx2 + ry2 + rz2 < 1.0) ? 0 : 1;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Potential update, one component: Eq. updateEquation at interior vertices. */
+static void update_interior(const orc_grid* g, const double co[6], const double* pm,
+                            const double* p, const double* s, double scale, double* pn) {
+    const double A = co[0], a1 = co[1], a2 = co[2], a4 = co[3], a6 = co[4], a8 = co[5];
+    const int nx = g->nx, ny = g->ny, nz = g->nz;
+#pragma omp parallel for schedule(static)
+    for (int k = 1; k < nz - 1; ++k) {
+        for (int j = 1; j < ny - 1; ++j) {
+            for (int i = 1; i < nx - 1; ++i) {
+                /* z-weighted neighbour values, Eq. NSFDtrick */
+                double bxp = A * p[ix(g, i + 1, j, k - 1)] + (1.0 - 2.0 * A) * p[ix(g, i + 1, j, k)] + A * p[ix(g, i + 1, j, k + 1)];
+                double bxm = A * p[ix(g, i - 1, j, k - 1)] + (1.0 - 2.0 * A) * p[ix(g, i - 1, j, k)] + A * p[ix(g, i - 1, j, k + 1)];
+                double byp = A * p[ix(g, i, j + 1, k - 1)] + (1.0 - 2.0 * A) * p[ix(g, i, j + 1, k)] + A * p[ix(g, i, j + 1, k + 1)];
+                double bym = A * p[ix(g, i, j - 1, k - 1)] + (1.0 - 2.0 * A) * p[ix(g, i, j - 1, k)] + A * p[ix(g, i, j - 1, k + 1)];
+                int64_t c = ix(g, i, j, k);
+                double v = -pm[c] + a1 * p[c]
+                         + a2 * bxp + a2 * bxm
+                         + a4 * byp + a4 * bym
+                         + a6 * p[ix(g, i, j, k + 1)] + a6 * p[ix(g, i, j, k - 1)];
+                if (s) v += a8 * scale * s[c];
+                pn[c] = v;
+            }
+        }
+    }
+}
+
+static inline int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+/* First-order Mur condition (Sec. "First Order ABCs"): for a boundary vertex b
+ * with nearest interior vertex q at distance d,
+ *   xi_b^{n+1} = beta0 (xi_b^{n-1} + xi_q^{n+1}) + beta1 (xi_b^n + xi_q^n) - xi_q^{n-1}
+ * with beta0 = (c dt - d)/(c dt + d), beta1 = 2 d/(c dt + d). */
+static void mur_boundary(const orc_grid* g, const double* pm, const double* p, double* pn) {
+    const int nx = g->nx, ny = g->ny, nz = g->nz;
+    const double cdt = ORC_C * g->dt;
+    for (int k = 0; k < nz; ++k) {
+        for (int j = 0; j < ny; ++j) {
+            for (int i = 0; i < nx; ++i) {
+                int onb = (i == 0 || i == nx - 1 || j == 0 || j == ny - 1 || k == 0 || k == nz - 1);
+                if (!onb) continue;
+                int qi = clampi(i, 1, nx - 2), qj = clampi(j, 1, ny - 2), qk = clampi(k, 1, nz - 2);
+                double d2 = 0.0;
+                if (qi != i) d2 += g->dx * g->dx;
+                if (qj != j) d2 += g->dy * g->dy;
+                if (qk != k) d2 += g->dz * g->dz;
+                double d = sqrt(d2);
+                double b0 = (cdt - d) / (cdt + d);
+                double b1 = 2.0 * d / (cdt + d);
+                int64_t b = ix(g, i, j, k), q = ix(g, qi, qj, qk);
+                pn[b] = b0 * (pm[b] + pn[q]) + b1 * (p[b] + p[q]) - pm[q];
+            }
+        }
+    }
+}
+
+void orc_potential_step(const orc_grid* g, const double* prev, const double* cur,
+                        const double* src, double* next) {
+    double co[6];
+    orc_coefficients(g, co);
+    const int64_t n = ncell(g);
+    for (int c = 0; c < 4; ++c) {
+        const double* pm = prev + c * n;
+        const double* p = cur + c * n;
+        const double* s = src + c * n;
+        double* pn = next + c * n;
+        if (c == 3 && !g->space_charge) {
+            memset(pn, 0, sizeof(double) * (size_t)n);
+            continue;
+        }
+        /* source term: mu0 J for A, rho/eps0 for phi */
+        double scale = (c < 3) ? ORC_MU0 : 1.0 / ORC_EPS0;
+        update_interior(g, co, pm, p, s, scale, pn);
+        mur_boundary(g, pm, p, pn);
+    }
+}
+
+/* ---------------------------------------------------------------------- */
+/* E and B at the vertices, Sec. "Field Evaluation". */
+void orc_fields(const orc_grid* g, const double* lev_n, const double* lev_np1,
+                double* E, double* B) {
+    const int64_t n = ncell(g);
+    const int nx = g->nx, ny = g->ny, nz = g->nz;
+    const double* Axn = lev_n;
+    const double* Ayn = lev_n + n;
+    const double* Azn = lev_n + 2 * n;
+    const double* phn = lev_n + 3 * n;
+    const double* Ax1 = lev_np1;
+    const double* Ay1 = lev_np1 + n;
+    const double* Az1 = lev_np1 + 2 * n;
+    const double dx = g->dx, dy = g->dy, dz = g->dz, dt = g->dt;
+    memset(E, 0, sizeof(double) * 3 * (size_t)n);
+    memset(B, 0, sizeof(double) * 3 * (size_t)n);
+#pragma omp parallel for schedule(static)
+    for (int k = 1; k < nz - 1; ++k) {
+        for (int j = 1; j < ny - 1; ++j) {
+            for (int i = 1; i < nx - 1; ++i) {
+                int64_t c = ix(g, i, j, k);
+                int64_t xp = ix(g, i + 1, j, k), xm = ix(g, i - 1, j, k);
+                int64_t yp = ix(g, i, j + 1, k), ym = ix(g, i, j - 1, k);
+                int64_t zp = ix(g, i, j, k + 1), zm = ix(g, i, j, k - 1);
+                /* B = curl A, averaged over levels n and n+1 */
+                double bx0 = (Azn[yp] - Azn[ym]) / (2 * dy) - (Ayn[zp] - Ayn[zm]) / (2 * dz);
+                double bx1 = (Az1[yp] - Az1[ym]) / (2 * dy) - (Ay1[zp] - Ay1[zm]) / (2 * dz);
+                double by0 = (Axn[zp] - Axn[zm]) / (2 * dz) - (Azn[xp] - Azn[xm]) / (2 * dx);
+                double by1 = (Ax1[zp] - Ax1[zm]) / (2 * dz) - (Az1[xp] - Az1[xm]) / (2 * dx);
+                double bz0 = (Ayn[xp] - Ayn[xm]) / (2 * dx) - (Axn[yp] - Axn[ym]) / (2 * dy);
+                double bz1 = (Ay1[xp] - Ay1[xm]) / (2 * dx) - (Ax1[yp] - Ax1[ym]) / (2 * dy);
+                B[c] = 0.5 * (bx0 + bx1);
+                B[n + c] = 0.5 * (by0 + by1);
+                B[2 * n + c] = 0.5 * (bz0 + bz1);
+                /* E = -dA/dt - grad phi, phi^n at (n+1/2) dt */
+                E[c] = -(Ax1[c] - Axn[c]) / dt - (phn[xp] - phn[xm]) / (2 * dx);
+                E[n + c] = -(Ay1[c] - Ayn[c]) / dt - (phn[yp] - phn[ym]) / (2 * dy);
+                E[2 * n + c] = -(Az1[c] - Azn[c]) / dt - (phn[zp] - phn[zm]) / (2 * dz);
+            }
+        }
+    }
+}
+
+/* ---------------------------------------------------------------------- */
+/* Undulator, Sec. "Undulator Field": lab field of a planar static undulator,
+ * B'_y = B0 cosh(ku y) sin(ku zeta), B'_z = B0 sinh(ku y) cos(ku zeta), zeta the
+ * lab distance past the entrance; for zeta < 0 the Neumann-shaped fringe
+ * B'_y = B0 cosh(ku y) ku zeta exp(-(ku zeta)^2/2), B'_z = B0 sinh(ku y) exp(..).
+ * B0 from K = e B0 lambda_u / (2 pi m c).  Transformed to the frame moving with
+ * beta0 along +z. */
+void orc_undulator_field(const orc_undulator* u, double y, double z, double t,
+                         double E[3], double B[3]) {
+    const double g0 = u->gamma0;
+    const double b0 = sqrt(1.0 - 1.0 / (g0 * g0));
+    const double ku = 2.0 * ORC_PI / u->lambda_u;
+    const double B0 = 2.0 * ORC_PI * ORC_ME * ORC_C * u->K / (ORC_E * u->lambda_u);
+    /* lab position of the rest-frame event (z, t) */
+    const double zlab = g0 * (z + b0 * ORC_C * t);
+    const double zeta = zlab - u->z_ent_lab;
+    const double ch = cosh(ku * y), sh = sinh(ku * y);
+    double By_l = 0.0, Bz_l = 0.0;
+    if (zeta < 0.0) {
+        if (u->fringe) {
+            double a = ku * zeta;
+            By_l = B0 * ch * a * exp(-0.5 * a * a);
+            Bz_l = B0 * sh * exp(-0.5 * a * a);
+        }
+    } else if (u->length_lab > 0.0 && zeta > u->length_lab) {
+        if (u->fringe) {
+            double a = ku * (zeta - u->length_lab);
+            By_l = B0 * ch * a * exp(-0.5 * a * a);
+            Bz_l = B0 * sh * exp(-0.5 * a * a);
+        }
+    } else {
+        By_l = B0 * ch * sin(ku * zeta);
+        Bz_l = B0 * sh * cos(ku * zeta);
+    }
+    /* E' = 0, B' = (0, By_l, Bz_l); frame velocity +beta0 c z:
+     * E_perp = gamma0 (v x B'), B_perp = gamma0 B'_perp, B_par = B'_par. */
+    E[0] = -g0 * b0 * ORC_C * By_l;
+    E[1] = 0.0;
+    E[2] = 0.0;
+    B[0] = 0.0;
+    B[1] = g0 * By_l;
+    B[2] = Bz_l;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Boris scheme, Eq. BorisScheme, written for a general charge-to-mass ratio
+ * qm (the paper's -e/m for electrons):
+ *   t1 = u + qm dtb E/(2c); alpha = qm dtb / (2 sqrt(1 + t1.t1))
+ *   t2 = t1 + alpha t1 x B; t3 = t1 + t2 x (2 alpha B)/(1 + alpha^2 B.B)
+ *   u' = t3 + qm dtb E/(2c). */
+static void cross(const double a[3], const double b[3], double o[3]) {
+    o[0] = a[1] * b[2] - a[2] * b[1];
+    o[1] = a[2] * b[0] - a[0] * b[2];
+    o[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+void orc_boris(double u[3], const double E[3], const double B[3], double qm, double dtb) {
+    double h = qm * dtb / (2.0 * ORC_C);
+    double t1[3] = {u[0] + h * E[0], u[1] + h * E[1], u[2] + h * E[2]};
+    double alpha = qm * dtb / (2.0 * sqrt(1.0 + t1[0] * t1[0] + t1[1] * t1[1] + t1[2] * t1[2]));
+    double c1[3];
+    cross(t1, B, c1);
+    double t2[3] = {t1[0] + alpha * c1[0], t1[1] + alpha * c1[1], t1[2] + alpha * c1[2]};
+    double bb = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
+    double f = 2.0 * alpha / (1.0 + alpha * alpha * bb);
+    double s[3] = {f * B[0], f * B[1], f * B[2]};
+    double c2[3];
+    cross(t2, s, c2);
+    double t3[3] = {t1[0] + c2[0], t1[1] + c2[1], t1[2] + c2[2]};
+    u[0] = t3[0] + h * E[0];
+    u[1] = t3[1] + h * E[1];
+    u[2] = t3[2] + h * E[2];
+}
+
+/* ---------------------------------------------------------------------- */
+/* Cell index and offset of a position along one axis (the paper's
+ * (i, delta) of Fig. FDTDPICFig1). */
+static inline int cell_of(double r, double r0, double d, double* w1) {
+    double s = (r - r0) / d;
+    double f = floor(s);
+    *w1 = s - f;
+    return (int)f;
+}
+
+static inline int valid_cell(const orc_grid* g, int ci, int cj, int ck) {
+    return ci >= 1 && ci <= g->nx - 3 && cj >= 1 && cj <= g->ny - 3 && ck >= 1 && ck <= g->nz - 3;
+}
+
+static int locate(const orc_grid* g, double x, double y, double z, int c[3], double w1[3]) {
+    c[0] = cell_of(x, g->x0, g->dx, &w1[0]);
+    c[1] = cell_of(y, g->y0, g->dy, &w1[1]);
+    c[2] = cell_of(z, g->z0, g->dz, &w1[2]);
+    return valid_cell(g, c[0], c[1], c[2]);
+}
+
+/* Trilinear weights of Eq. fieldInterpolation: w0 = 1 - delta/D, w1 = delta/D. */
+static inline double wgt(int I, double w1) { return I ? w1 : 1.0 - w1; }
+
+static void gather(const orc_grid* g, const double* F, const int c[3], const double w1[3],
+                   double out[3]) {
+    const int64_t n = ncell(g);
+    out[0] = out[1] = out[2] = 0.0;
+    for (int K = 0; K < 2; ++K)
+        for (int J = 0; J < 2; ++J)
+            for (int I = 0; I < 2; ++I) {
+                double w = wgt(I, w1[0]) * wgt(J, w1[1]) * wgt(K, w1[2]);
+                int64_t v = ix(g, c[0] + I, c[1] + J, c[2] + K);
+                out[0] += w * F[v];
+                out[1] += w * F[n + v];
+                out[2] += w * F[2 * n + v];
+            }
+}
+
+static void scatter(const orc_grid* g, double* F, const int c[3], const double w1[3],
+                    double amount) {
+    for (int K = 0; K < 2; ++K)
+        for (int J = 0; J < 2; ++J)
+            for (int I = 0; I < 2; ++I) {
+                double w = wgt(I, w1[0]) * wgt(J, w1[1]) * wgt(K, w1[2]);
+                F[ix(g, c[0] + I, c[1] + J, c[2] + K)] += w * amount;
+            }
+}
+
+int64_t orc_mark_lost(const orc_grid* g, int64_t np, const double* x, const double* y,
+                      const double* z, int32_t* lost) {
+    int64_t nl = 0;
+    for (int64_t p = 0; p < np; ++p) {
+        int c[3];
+        double w1[3];
+        if (!locate(g, x[p], y[p], z[p], c, w1)) lost[p] = 1;
+        if (lost[p]) ++nl;
+    }
+    return nl;
+}
+
+void orc_deposit_rho(const orc_grid* g, double q_macro, int64_t np, const double* x,
+                     const double* y, const double* z, const int32_t* lost, double* rho_out) {
+    const double V = g->dx * g->dy * g->dz;
+    for (int64_t p = 0; p < np; ++p) {
+        if (lost[p]) continue;
+        int c[3];
+        double w1[3];
+        if (!locate(g, x[p], y[p], z[p], c, w1)) continue;
+        scatter(g, rho_out, c, w1, q_macro / V);
+    }
+}
+
+/* Sec. "Update Algorithm" + "Current Deposition": per particle, n_sub Boris
+ * steps of dt_b = dt/n_sub with the grid E,B held at t_half and the undulator
+ * field at each sub-step time; then J^{n+1} = (q/V) (r_end - r_start)/dt at
+ * the mid point and rho^{n+3/2} = q/V at r_end, both with the CIC weights. */
+int64_t orc_push_deposit(const orc_grid* g, const orc_undulator* und, double q_macro,
+                         double t_half, const double* E, const double* B,
+                         int64_t np, double* x, double* y, double* z,
+                         double* ux, double* uy, double* uz, int32_t* lost,
+                         double* src_out) {
+    const int64_t n = ncell(g);
+    const double qm = -ORC_E / ORC_ME; /* electrons */
+    const double dtb = g->dt / g->n_sub;
+    const double V = g->dx * g->dy * g->dz;
+    int64_t newly_lost = 0;
+    for (int64_t p = 0; p < np; ++p) {
+        if (lost[p]) continue;
+        double r0[3] = {x[p], y[p], z[p]};
+        double r[3] = {x[p], y[p], z[p]};
+        double u[3] = {ux[p], uy[p], uz[p]};
+        int ok = 1;
+        for (int m = 0; m < g->n_sub; ++m) {
+            int c[3];
+            double w1[3];
+            if (!locate(g, r[0], r[1], r[2], c, w1)) { ok = 0; break; }
+            double Eg[3], Bg[3], Eu[3], Bu[3];
+            gather(g, E, c, w1, Eg);
+            gather(g, B, c, w1, Bg);
+            orc_undulator_field(und, r[1], r[2], t_half + m * dtb, Eu, Bu);
+            double Et[3] = {Eg[0] + Eu[0], Eg[1] + Eu[1], Eg[2] + Eu[2]};
+            double Bt[3] = {Bg[0] + Bu[0], Bg[1] + Bu[1], Bg[2] + Bu[2]};
+            orc_boris(u, Et, Bt, qm, dtb);
+            double gam = sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+            r[0] += ORC_C * dtb * u[0] / gam;
+            r[1] += ORC_C * dtb * u[1] / gam;
+            r[2] += ORC_C * dtb * u[2] / gam;
+        }
+        x[p] = r[0]; y[p] = r[1]; z[p] = r[2];
+        ux[p] = u[0]; uy[p] = u[1]; uz[p] = u[2];
+        int c[3];
+        double w1[3];
+        if (ok) ok = locate(g, r[0], r[1], r[2], c, w1);
+        if (!ok) {
+            lost[p] = 1;
+            ++newly_lost;
+            continue;
+        }
+        /* rho^{n+3/2} at the end position */
+        scatter(g, src_out + 3 * n, c, w1, q_macro / V);
+        /* J^{n+1} at the mid point */
+        double rm[3] = {0.5 * (r0[0] + r[0]), 0.5 * (r0[1] + r[1]), 0.5 * (r0[2] + r[2])};
+        int cm[3];
+        double wm[3];
+        locate(g, rm[0], rm[1], rm[2], cm, wm);
+        for (int a = 0; a < 3; ++a) {
+            double J = (q_macro / V) * (r[a] - r0[a]) / g->dt;
+            scatter(g, src_out + a * n, cm, wm, J);
+        }
+    }
+    return newly_lost;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Total power through the vertex plane k_p, in the lab frame: the grid fields
+ * are transformed to the lab (frame velocity beta0 along +z),
+ *   E'_x = g0 (E_x + b0 c B_y), E'_y = g0 (E_y - b0 c B_x),
+ *   B'_x = g0 (B_x - b0 E_y / c), B'_y = g0 (B_y + b0 E_x / c),
+ * and P' = sum over interior (i,j) of (E'_x B'_y - E'_y B'_x)/mu0 dx dy. */
+void orc_radiated_power(const orc_grid* g, double gamma0, const double* E, const double* B,
+                        int32_t k_p, double t, double* p_lab, double* t_lab, double* z_lab) {
+    const int64_t n = ncell(g);
+    const double b0 = sqrt(1.0 - 1.0 / (gamma0 * gamma0));
+    double sum = 0.0;
+    for (int j = 1; j < g->ny - 1; ++j) {
+        for (int i = 1; i < g->nx - 1; ++i) {
+            int64_t c = ix(g, i, j, k_p);
+            double Ex = E[c], Ey = E[n + c];
+            double Bx = B[c], By = B[n + c];
+            double Exl = gamma0 * (Ex + b0 * ORC_C * By);
+            double Eyl = gamma0 * (Ey - b0 * ORC_C * Bx);
+            double Bxl = gamma0 * (Bx - b0 * Ey / ORC_C);
+            double Byl = gamma0 * (By + b0 * Ex / ORC_C);
+            sum += (Exl * Byl - Eyl * Bxl) / ORC_MU0 * g->dx * g->dy;
+        }
+    }
+    double zp = g->z0 + k_p * g->dz;
+    *p_lab = sum;
+    *t_lab = gamma0 * (t + b0 * zp / ORC_C);
+    *z_lab = gamma0 * (zp + b0 * ORC_C * t);
+}

@@ -1,0 +1,103 @@
+/*
+ * orc.h -- plain FP64 CPU oracle of the MITHRA FDTD/PIC time step
+ * (Fallahi, Yahaghi, Kaertner, arXiv 1612.03310).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may load this
+ * library: it is linked or called only by tests/, by __graft_entry__.smoke()
+ * (as the checker) and by bench.py's cpu_baseline / reference legs.  It shares
+ * no code, header, constant or table with the CUDA library; even the physical
+ * constants are written out again here.
+ *
+ * Conventions
+ *   - All quantities SI, in the bunch rest frame unless a name ends in _lab.
+ *   - A scalar field on the grid is an array of nx*ny*nz doubles, vertex
+ *     (i,j,k) at index (k*ny + j)*nx + i (x fastest), vertex position
+ *     (x0 + i*dx, y0 + j*dy, z0 + k*dz).
+ *   - A 4-component potential level is 4 such arrays back to back in the order
+ *     A_x, A_y, A_z, phi.  The source array holds J_x, J_y, J_z [A/m^2] and
+ *     rho [C/m^3] in the same order.  E and B hold 3 arrays each (x, y, z).
+ *   - Particles: absolute positions x,y,z [m] and u = gamma*beta.
+ */
+#ifndef MITHRA_ORACLE_H
+#define MITHRA_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+    int32_t nx, ny, nz;
+    double dx, dy, dz;
+    double x0, y0, z0;      /* position of vertex (0,0,0) */
+    double dt;              /* field time step */
+    int32_t n_sub;          /* Boris sub-steps per field step, dt_b = dt/n_sub */
+    int32_t stencil;        /* 0 = NSFD (Sec. "Numerical Dispersion"), 1 = standard */
+    int32_t space_charge;   /* 0: phi is held at zero */
+} orc_grid;
+
+typedef struct {
+    double gamma0;          /* Lorentz factor of the rest frame */
+    double lambda_u;        /* lab undulator period [m] */
+    double K;               /* undulator parameter */
+    double z_ent_lab;       /* lab z' of the undulator entrance [m] */
+    double length_lab;      /* lab length [m]; <= 0 means no exit */
+    int32_t fringe;         /* 1: Neumann-shaped fringe outside [0, L] */
+} orc_undulator;
+
+/* Coefficients of the update equation (Eq. updateEquation):
+ * out = {A, a1, a2(=a3), a4(=a5), a6(=a7), a8}. Returns 0 when the scheme is
+ * stable for the given grid and dt, 1 otherwise. */
+int orc_coefficients(const orc_grid* g, double out[6]);
+
+/* One potential update: next = level n+1 from prev (n-1), cur (n) and the
+ * sources src (J^n, rho^{n+1/2}).  Interior by Eq. updateEquation, the six
+ * faces (and edges/corners) by the first-order Mur condition. */
+void orc_potential_step(const orc_grid* g, const double* prev, const double* cur,
+                        const double* src, double* next);
+
+/* E and B at t = (n+1/2) dt at the vertices [1, n-2]^3 from A^n, A^{n+1},
+ * phi^n (Sec. "Field Evaluation"); all other vertices are set to zero. */
+void orc_fields(const orc_grid* g, const double* lev_n, const double* lev_np1,
+                double* E, double* B);
+
+/* Static undulator field in the rest frame at (y, z, t) (Eq. undulatorField,
+ * transformed to the moving frame). */
+void orc_undulator_field(const orc_undulator* u, double y, double z, double t,
+                         double E[3], double B[3]);
+
+/* One Boris step (Eq. BorisScheme) for charge-to-mass ratio qm over dtb:
+ * u <- u^{m+1/2} from u^{m-1/2} and the total fields. */
+void orc_boris(double u[3], const double E[3], const double B[3], double qm, double dtb);
+
+/* Advance all particles one field step (n_sub Boris steps), gathering the grid
+ * E,B (Eq. fieldInterpolation) plus the undulator field, and deposit
+ * J^{n+1} (at the mid point of the step) and rho^{n+3/2} into src_out, which
+ * the caller zeroes.  t_half = t at the start positions.  Returns how many
+ * particles were lost in this step. */
+int64_t orc_push_deposit(const orc_grid* g, const orc_undulator* und, double q_macro,
+                         double t_half, const double* E, const double* B,
+                         int64_t np, double* x, double* y, double* z,
+                         double* ux, double* uy, double* uz, int32_t* lost,
+                         double* src_out);
+
+/* rho of the particles at their present positions, added to rho_out. */
+void orc_deposit_rho(const orc_grid* g, double q_macro, int64_t np, const double* x,
+                     const double* y, const double* z, const int32_t* lost, double* rho_out);
+
+/* Marks particles outside the valid region as lost; returns their number. */
+int64_t orc_mark_lost(const orc_grid* g, int64_t np, const double* x, const double* y,
+                      const double* z, int32_t* lost);
+
+/* Radiated power through vertex plane k_p, lab frame, from grid E,B at time t
+ * (rest frame).  Writes P [W], the lab time and the lab position of the plane. */
+void orc_radiated_power(const orc_grid* g, double gamma0, const double* E, const double* B,
+                        int32_t k_p, double t, double* p_lab, double* t_lab, double* z_lab);
+
+/* Physical constants the oracle uses: c, e, m_e, eps0, mu0. */
+void orc_constants(double out[5]);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
