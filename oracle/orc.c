@@ -361,7 +361,10 @@ void orc_deposit_rho(const orc_grid* g, double q_macro, int64_t np, const double
 /* Sec. "Update Algorithm" + "Current Deposition": per particle, n_sub Boris
  * steps of dt_b = dt/n_sub with the grid E,B held at t_half and the undulator
  * field at each sub-step time; then J^{n+1} = (q/V) (r_end - r_start)/dt at
- * the mid point and rho^{n+3/2} = q/V at r_end, both with the CIC weights. */
+ * the mid point and rho^{n+3/2} = q/V at r_end, both with the CIC weights.
+ * r_end - r_start is kept as the sum of the sub-step displacements rather than
+ * formed by subtracting two absolute positions, which would cancel most of
+ * its digits when the displacement is small against the position. */
 int64_t orc_push_deposit(const orc_grid* g, const orc_undulator* und, double q_macro,
                          double t_half, const double* E, const double* B,
                          int64_t np, double* x, double* y, double* z,
@@ -376,6 +379,7 @@ int64_t orc_push_deposit(const orc_grid* g, const orc_undulator* und, double q_m
         if (lost[p]) continue;
         double r0[3] = {x[p], y[p], z[p]};
         double r[3] = {x[p], y[p], z[p]};
+        double dr[3] = {0.0, 0.0, 0.0}; /* r^{n+3/2} - r^{n+1/2}, summed per sub-step */
         double u[3] = {ux[p], uy[p], uz[p]};
         int ok = 1;
         for (int m = 0; m < g->n_sub; ++m) {
@@ -390,9 +394,11 @@ int64_t orc_push_deposit(const orc_grid* g, const orc_undulator* und, double q_m
             double Bt[3] = {Bg[0] + Bu[0], Bg[1] + Bu[1], Bg[2] + Bu[2]};
             orc_boris(u, Et, Bt, qm, dtb);
             double gam = sqrt(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-            r[0] += ORC_C * dtb * u[0] / gam;
-            r[1] += ORC_C * dtb * u[1] / gam;
-            r[2] += ORC_C * dtb * u[2] / gam;
+            for (int a = 0; a < 3; ++a) {
+                double step = ORC_C * dtb * u[a] / gam;
+                r[a] += step;
+                dr[a] += step;
+            }
         }
         x[p] = r[0]; y[p] = r[1]; z[p] = r[2];
         ux[p] = u[0]; uy[p] = u[1]; uz[p] = u[2];
@@ -407,12 +413,12 @@ int64_t orc_push_deposit(const orc_grid* g, const orc_undulator* und, double q_m
         /* rho^{n+3/2} at the end position */
         scatter(g, src_out + 3 * n, c, w1, q_macro / V);
         /* J^{n+1} at the mid point */
-        double rm[3] = {0.5 * (r0[0] + r[0]), 0.5 * (r0[1] + r[1]), 0.5 * (r0[2] + r[2])};
+        double rm[3] = {r0[0] + 0.5 * dr[0], r0[1] + 0.5 * dr[1], r0[2] + 0.5 * dr[2]};
         int cm[3];
         double wm[3];
         locate(g, rm[0], rm[1], rm[2], cm, wm);
         for (int a = 0; a < 3; ++a) {
-            double J = (q_macro / V) * (r[a] - r0[a]) / g->dt;
+            double J = (q_macro / V) * dr[a] / g->dt;
             scatter(g, src_out + a * n, cm, wm, J);
         }
     }
