@@ -1,0 +1,382 @@
+#!/usr/bin/env python3
+"""Throughput of the FDTD/PIC time step on one GB300 (or N replicas).
+
+A step is one pass of the whole hot path over the c2 workload
+(128x128x1024 cells, 2^21 macroparticles, rest-frame IR FEL shaped like the
+paper's Example 1): potential update with Mur faces, E/B from the potentials,
+gather + undulator + Boris push, deposit of J and rho, re-sort of the particles
+into cell tiles, and the radiated-power sample.  Inputs live in HBM for the
+whole run (state 0.8 GB > 129 MB L2, so no L2 flush is needed).
+
+value  = cell-updates/s of the whole step, summed over ranks (weak scaling:
+         every rank runs its own replica; the path has no exchange step);
+e2e    = the same metric through the C ABI from host buffers: create (copy-in
+         of the bunch), K steps, copy-out of the power record and particles.
+--impl reference times the FP64 CPU oracle on the host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("cell-updates/s + particle-pushes/s on 1 GB300 (FP32 vs FP64, % HBM roofline); "
+          "jobs/h, p99")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="mithra", choices=["mithra", "reference"])
+    ap.add_argument("--workload", default="c2")
+    ap.add_argument("--precision", default="p32", choices=["p32", "p64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-p64", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while running."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.uuid = uuid
+        self.rows = []
+        self.p = None
+        self.t = None
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+               "-lms", "200"]
+        if self.uuid:
+            cmd += ["-i", self.uuid]
+        try:
+            self.p = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                      text=True)
+        except OSError:
+            self.p = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.p.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 8:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.p is None:
+            return
+        time.sleep(0.25)
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        if self.t:
+            self.t.join(timeout=5)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            for nm, v in zip(names, r[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(self.rows), "reasons": sorted(reasons)}
+
+
+def algorithmic_bytes(kernel: str, grid: dict, n_particles: int, prec: str) -> float:
+    """Algorithmic bytes per launch (the minimum a kernel must move)."""
+    r = 4 if prec == "p32" else 8
+    interior = (grid["nx"] - 2) * (grid["ny"] - 2) * (grid["nz"] - 2)
+    if kernel == "potential_step":
+        # read psi^n, psi^{n-1}, sources; write psi^{n+1}; zero the sources
+        return interior * 5 * 4 * r
+    if kernel == "push":
+        # read and write cell + 3 fractions + 3 momenta; write key and rank
+        return n_particles * (2 * (4 + 6 * r) + 8)
+    if kernel == "scatter":
+        # read key, rank, offset and the particle; write the particle
+        return n_particles * (12 + 2 * (8 + 6 * r))
+    if kernel == "scan_counts":
+        ntiles = -(-grid["nx"] // 8) * -(-grid["ny"] // 8) * -(-grid["nz"] // 8)
+        return ntiles * 12
+    if kernel == "power":
+        return (grid["nx"] - 2) * (grid["ny"] - 2) * 14 * 4 * r
+    return 0.0
+
+
+def run_gpu(args, rank, world):
+    import torch
+    from paper_1612_03310_gb300 import inputs, mithra
+
+    dev = torch.cuda.current_device()
+    w = inputs.workload(args.workload)
+    g, und = dict(w["grid"], boundary=1), w["undulator"]
+    bunch = inputs.make_bunch(w["bunch_spec"], w["seed"] + rank)
+    n_part = bunch["x"].size
+    ncell = g["nx"] * g["ny"] * g["nz"]
+    prec = mithra.P32 if args.precision == "p32" else mithra.P64
+    kp = g["nz"] - 16
+    stream = torch.cuda.Stream()  # a dedicated stream: events bracket exactly our work
+    torch.cuda.set_stream(stream)
+    K, W = args.steps, args.warmup
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    sim = mithra.Simulation(g, und, bunch, precision=prec, stream=stream.cuda_stream)
+    sim.set_power_sampling(kp, W + K)
+    sim.step(W)
+    sim.sync()
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    sampler = ClockSampler(uuid)
+    sampler.start()
+    time.sleep(0.3)
+    sim.profile(True)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    sim.step(K)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    sampler.stop()
+    ms = e0.elapsed_time(e1)
+    kt = sim.kernel_times()
+    sim.profile(False)
+    power = sim.read_power()
+    parts = sim.copy_particles()
+    sim.close()
+    if world > 1:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    res = dict(ms=ms, kernel_times=kt, clocks=sampler.summary(), n_part=n_part, ncell=ncell,
+               grid=g, n_lost=parts["n_lost"], power_last=float(power[-1, 0]),
+               launches=sum(n for _, n in kt.values()))
+
+    # P64 (plain FP64) on the same workload, shorter
+    if not args.no_p64 and prec == mithra.P32:
+        K64 = max(20, K // 10)
+        sim = mithra.Simulation(g, und, bunch, precision=mithra.P64, stream=stream.cuda_stream)
+        sim.set_power_sampling(kp, W + K64)
+        sim.step(W)
+        sim.profile(True)
+        torch.cuda.synchronize()
+        barrier()
+        e0.record(stream)
+        sim.step(K64)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1)
+        kt64 = sim.kernel_times()
+        sim.close()
+        if world > 1:
+            t = torch.tensor([ms64], device="cuda", dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms64 = float(t.item())
+        res["p64"] = dict(ms=ms64, steps=K64, kernel_times=kt64)
+
+    # end to end through the C ABI from host buffers
+    if not args.no_e2e:
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sim = mithra.Simulation(g, und, bunch, precision=prec, stream=stream.cuda_stream)
+        sim.set_power_sampling(kp, K)
+        sim.step(K)
+        rec = sim.read_power()
+        out = sim.copy_particles()
+        sim.close()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        barrier()
+        e2e_s = t1 - t0
+        if world > 1:
+            t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        res["e2e"] = dict(seconds=e2e_s, h2d=6 * 8 * n_part, d2h=rec.nbytes + 7 * 8 * n_part,
+                          check=float(np.isfinite(out["x"]).all()))
+    return res
+
+
+def cpu_oracle_rate(workload: str, budget_s: float, max_steps: int | None = None):
+    """Times the FP64 oracle on the host cores on the same workload, as many
+    whole steps as fit in budget_s (at least one)."""
+    sys.path.insert(0, os.path.join(ROOT, "oracle"))
+    import oracle
+    from paper_1612_03310_gb300 import inputs
+    oracle.build()
+    w = inputs.workload(workload)
+    bunch = inputs.make_bunch(w["bunch_spec"], w["seed"])
+    o = oracle.OracleSim(w["grid"], w["undulator"], bunch)
+    g = w["grid"]
+    ncell = g["nx"] * g["ny"] * g["nz"]
+    t0 = time.perf_counter()
+    steps = 0
+    while True:
+        o.step(1)
+        steps += 1
+        el = time.perf_counter() - t0
+        if max_steps is not None and steps >= max_steps:
+            break
+        if el + el / steps > budget_s:
+            break
+    el = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return dict(cell_updates_per_s=ncell * steps / el, pushes_per_s=bunch["x"].size * steps / el,
+                steps=steps, seconds=el, cores=cores,
+                sample=f"{steps} whole FP64 oracle steps of {workload} "
+                       f"({g['nx']}x{g['ny']}x{g['nz']} cells, {bunch['x'].size} particles); "
+                       f"the particle loop is serial, the grid loops use OpenMP")
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_1612_03310_gb300 import inputs
+    w = inputs.workload(args.workload)
+    g = w["grid"]
+    cfg = {"workload": inputs.describe(args.workload), "grid": [g["nx"], g["ny"], g["nz"]],
+           "particles": w["bunch_spec"]["n"], "precision": args.precision,
+           "l2": "state 0.8 GB per replica > 129 MB L2 (no flush needed)",
+           "parallelism": f"replicas x{world}"}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        os.environ.setdefault("OMP_NUM_THREADS", str(os.cpu_count() or 1))
+        budget = 120.0
+        r = cpu_oracle_rate(args.workload, budget, max_steps=args.steps + args.warmup)
+        line = {"impl": "reference", "metric": METRIC, "value": r["cell_updates_per_s"],
+                "unit": "cell-updates/s", "n_gpus": 0, "steps": r["steps"],
+                "warmup": 0, "ms_per_step": 1e3 * r["seconds"] / r["steps"],
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64", "data": "synthetic", "config": cfg,
+                "particle_pushes_per_s": r["pushes_per_s"],
+                "cpu_baseline": {"value": r["cell_updates_per_s"], "unit": "cell-updates/s",
+                                 "cores": r["cores"], "kind": "oracle", "sample": r["sample"]},
+                "e2e": {"value": r["cell_updates_per_s"], "unit": "cell-updates/s",
+                        "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import torch
+    if world > 1:
+        torch.cuda.set_device(local)
+        torch.distributed.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    from paper_1612_03310_gb300 import build_lib
+    if rank == 0:
+        build_lib.build()
+    if world > 1:
+        torch.distributed.barrier()
+    res = run_gpu(args, rank, world)
+    if rank != 0:
+        torch.distributed.destroy_process_group()
+        return
+
+    K = args.steps
+    s = res["ms"] / 1e3
+    ncell, npart = res["ncell"], res["n_part"]
+    value = world * ncell * K / s
+    pushes = world * npart * g.get("n_sub", 1) * K / s
+    peak, peak_kind = peaks()
+    kt = res["kernel_times"]
+    dom = max(kt, key=lambda k: kt[k][0])
+    avg_ms = kt[dom][0] / max(kt[dom][1], 1)
+    ab = algorithmic_bytes(dom, res["grid"], npart, args.precision)
+    achieved = ab / (avg_ms / 1e3) / 1e9
+    stencil_ms = kt["potential_step"][0] / max(kt["potential_step"][1], 1)
+    stencil_gbs = algorithmic_bytes("potential_step", res["grid"], npart, args.precision) / (
+        stencil_ms / 1e3) / 1e9
+    total_kernel_ms = sum(v[0] for v in kt.values())
+    line = {
+        "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world,
+        "steps": K, "warmup": args.warmup, "ms_per_step": res["ms"] / K,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if args.precision == "p32" else "f64", "data": "synthetic",
+        "config": cfg,
+        "particle_pushes_per_s": pushes,
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind,
+                     "algorithmic_bytes_per_launch": ab, "avg_launch_ms": avg_ms,
+                     "traffic": None},
+        "stencil": {"kernel": "potential_step", "avg_launch_ms": stencil_ms,
+                    "achieved_gbs": stencil_gbs, "frac": stencil_gbs / peak,
+                    "cell_updates_per_s": ncell / (stencil_ms / 1e3)},
+        "kernel_share": {k: round(v[0] / total_kernel_ms, 4) for k, v in kt.items()},
+        "clocks": res["clocks"],
+        "gpu_launches": res["launches"],
+        "n_lost": res["n_lost"],
+    }
+    if "p64" in res:
+        p = res["p64"]
+        kt64 = p["kernel_times"]
+        st64 = kt64["potential_step"][0] / max(kt64["potential_step"][1], 1)
+        line["p64"] = {"ms_per_step": p["ms"] / p["steps"],
+                       "cell_updates_per_s": world * ncell * p["steps"] / (p["ms"] / 1e3),
+                       "particle_pushes_per_s": world * npart * p["steps"] / (p["ms"] / 1e3),
+                       "stencil_gbs": algorithmic_bytes("potential_step", res["grid"], npart,
+                                                        "p64") / (st64 / 1e3) / 1e9,
+                       "kernel_ms_per_launch": {k: v[0] / max(v[1], 1) for k, v in kt64.items()}}
+    if "e2e" in res:
+        e = res["e2e"]
+        line["e2e"] = {"value": world * ncell * K / e["seconds"], "unit": "cell-updates/s",
+                       "h2d_bytes_per_step": e["h2d"] / K, "d2h_bytes_per_step": e["d2h"] / K,
+                       "seconds": e["seconds"]}
+    if world == 1 and not args.no_cpu_baseline:
+        r = cpu_oracle_rate(args.workload, 20.0)
+        line["cpu_baseline"] = {"value": r["cell_updates_per_s"], "unit": "cell-updates/s",
+                                "cores": r["cores"], "kind": "oracle", "sample": r["sample"],
+                                "particle_pushes_per_s": r["pushes_per_s"]}
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,224 @@
+/*
+ * mithra.h -- C ABI of the GB300 (sm_103a) FDTD/PIC time step of the MITHRA
+ * full-wave free-electron-laser method (Fallahi, Yahaghi, Kaertner,
+ * arXiv 1612.03310).
+ *
+ * One simulation advances, on one GPU and in the Lorentz-boosted bunch rest
+ * frame:
+ *   - the potentials A and phi on a 3-D vertex grid by the NSFD (or standard)
+ *     central-difference update, Sec. "FDTD for Helmholtz Equation",
+ *     Eq. updateEquation, with first-order Mur boundaries, Sec. "First Order
+ *     ABCs";
+ *   - E and B at the vertices from the potentials, Sec. "Field Evaluation";
+ *   - the macroparticles by the Boris scheme (Eq. BorisScheme) in the
+ *     trilinearly gathered grid field (Eq. fieldInterpolation) plus the static
+ *     undulator field transformed into the rest frame (Eq. undulatorField and
+ *     Sec. "Undulator Field");
+ *   - the current and charge densities deposited back to the vertices,
+ *     Sec. "Current Deposition", Eq. currentIntegral.
+ *
+ * Units are SI, rest frame, unless a name ends in _lab (laboratory frame).
+ * Host arrays are double precision; a scalar field on the grid is
+ * nx*ny*nz values with vertex (i,j,k) at index (k*ny + j)*nx + i (x fastest)
+ * and position (x0 + i*dx, y0 + j*dy, z0 + k*dz).
+ *
+ * Every function returns a mithra_status.  Arrays passed in are copied and
+ * never retained; output arrays are caller-allocated host memory.  Work is
+ * ordered on the simulation's CUDA stream; a device-side failure is reported
+ * by the first call that synchronises (mithra_sync and every call that copies
+ * results to the host) and by the next mithra_step.  A failing call leaves a
+ * message for mithra_last_error.  Simulations are independent: an error in
+ * one does not affect another.
+ */
+#ifndef MITHRA_H
+#define MITHRA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mithra_sim mithra_sim; /* opaque, owned by the library */
+
+typedef enum {
+    MITHRA_OK = 0,
+    MITHRA_EINVAL = 1,    /* bad argument, size or layout */
+    MITHRA_EUNSTABLE = 2, /* dt violates the scheme's stability condition */
+    MITHRA_ENOMEM = 3,    /* device or pinned host allocation failed */
+    MITHRA_ECUDA = 4,     /* a CUDA runtime call or kernel failed */
+    MITHRA_ENUMERIC = 5,  /* NaN or Inf seen in a reduction */
+    MITHRA_ELOST = 6,     /* reserved: strict mode for lost particles */
+    MITHRA_EBUSY = 7,     /* reserved: batch slot in use */
+    MITHRA_ENODEV = 8     /* no CUDA device of compute capability 10.3 */
+} mithra_status;
+
+typedef enum {
+    MITHRA_P64 = 0, /* all state and arithmetic in FP64 */
+    MITHRA_P32 = 1  /* FP32 fields and particle phase space; FP64 frame clock,
+                       lab-frame phase of the undulator, particle gamma,
+                       positions' cell bookkeeping and power accumulation */
+} mithra_precision;
+
+/* Field identifiers; the paper's field names (Ex .. Bz, Ax .. Az, Jx .. Jz,
+ * F = phi, Q = rho) in the field-sampling group of its reference card. */
+typedef enum {
+    MITHRA_EX = 0, MITHRA_EY = 1, MITHRA_EZ = 2,
+    MITHRA_BX = 3, MITHRA_BY = 4, MITHRA_BZ = 5,
+    MITHRA_AX = 6, MITHRA_AY = 7, MITHRA_AZ = 8,
+    MITHRA_JX = 9, MITHRA_JY = 10, MITHRA_JZ = 11,
+    MITHRA_PHI = 12, MITHRA_RHO = 13,
+    /* the previous potential level (needed to restart the leapfrog) */
+    MITHRA_AX_PREV = 14, MITHRA_AY_PREV = 15, MITHRA_AZ_PREV = 16, MITHRA_PHI_PREV = 17
+} mithra_field;
+
+/* Grid and time step (Sec. "FDTD for Helmholtz Equation").
+ * nx, ny, nz >= 4 vertices; boundary vertices are updated by the Mur
+ * condition.  Particles live in cells [1, n-3] along each axis (the cell's
+ * eight vertices and their curl/gradient neighbours must exist); a particle
+ * that leaves this region is lost: flagged, counted and never pushed or
+ * deposited again. */
+typedef struct {
+    int32_t nx, ny, nz;
+    double dx, dy, dz;
+    double x0, y0, z0;     /* position of vertex (0,0,0) */
+    double dt;             /* field time step; particle step dt/n_sub */
+    int32_t n_sub;         /* Boris sub-steps per field step, >= 1 */
+    int32_t stencil;       /* 0 = NSFD (Eq. NSFDCoefficient), 1 = standard */
+    int32_t boundary;      /* 1 = first-order Mur (the only value accepted) */
+    int32_t space_charge;  /* 0: phi is held at zero */
+} mithra_grid;
+
+/* Static planar undulator (Eq. undulatorField), given in the laboratory frame:
+ * B'_y = B0 cosh(ku y) sin(ku zeta), B'_z = B0 sinh(ku y) cos(ku zeta) with
+ * zeta the lab distance past the entrance, K = e B0 lambda_u / (2 pi m c).
+ * The rest frame moves with gamma0 along +z; a rest-frame event (z, t) is at
+ * lab position gamma0 (z + beta0 c t).  With fringe = 1 the field outside
+ * [0, length_lab] is the Neumann-shaped taper of Sec. "Undulator Field" (at
+ * the exit in the distance past it).  length_lab <= 0: no exit. */
+typedef struct {
+    double gamma0;
+    double lambda_u;
+    double K;
+    double z_ent_lab;
+    double length_lab;
+    int32_t fringe;
+} mithra_undulator;
+
+/* Macroparticles, host arrays of n doubles in the rest frame at t = t0:
+ * positions r^{1/2} [m] and normalised momenta u^0 = gamma*beta.  Each carries
+ * charge q_macro [C] (negative for electrons) and the electron's
+ * charge-to-mass ratio. */
+typedef struct {
+    int64_t n;
+    double q_macro;
+    const double *x, *y, *z;
+    const double *ux, *uy, *uz;
+} mithra_bunch;
+
+/* Creates a simulation: validates the grid (MITHRA_EUNSTABLE if dt breaks
+ * the stability condition, see mithra_check_grid), allocates device memory
+ * (mithra_footprint bytes), copies the bunch, sorts it into cell tiles and
+ * deposits rho^{1/2}.  Potentials start at zero at levels -1 and 0, J^0 = 0,
+ * the frame clock at t0 = 0.  cuda_stream: a cudaStream_t to order all work
+ * on, or NULL for a stream the library creates and owns (pass
+ * cudaStreamLegacy for the legacy default stream).  On success *out
+ * owns the simulation until mithra_destroy. */
+mithra_status mithra_create(const mithra_grid* grid, const mithra_undulator* und,
+                            const mithra_bunch* bunch, mithra_precision precision,
+                            void* cuda_stream, mithra_sim** out);
+
+/* Enqueues n >= 0 field steps (potential update, E/B, gather, push, deposit,
+ * re-sort, optional power sample) on the stream and returns without waiting.
+ * Returns the status of work that has already finished. */
+mithra_status mithra_step(mithra_sim* sim, int64_t n);
+
+/* Waits for all enqueued work; returns its status. */
+mithra_status mithra_sync(mithra_sim* sim);
+
+/* Number of field steps taken and the rest-frame time t0 + n dt. */
+mithra_status mithra_time(const mithra_sim* sim, int64_t* n_steps, double* t);
+
+/* Copies one whole field (mithra_field id) to host memory out[nx*ny*nz].
+ * E and B are evaluated at t = t0 + (n - 1/2) dt from the two current
+ * potential levels (zero on boundary vertices); A and phi are the newest
+ * level (t0 + n dt, and phi at t0 + (n + 1/2) dt); J is J^n and rho is
+ * rho^{n+1/2}, the sources of the next step. */
+mithra_status mithra_copy_field(mithra_sim* sim, int32_t field, double* out);
+
+/* Overwrites one whole field from host memory (potentials at either level or
+ * a source); E and B cannot be set.  Used to restart a run or to start from a
+ * prepared state. */
+mithra_status mithra_set_field(mithra_sim* sim, int32_t field, const double* in);
+
+/* Samples the fields selected by field_mask (bit f for mithra_field f < 14) at
+ * npts vertices ijk[3*p .. 3*p+2] = (i, j, k).  out[p*m + s] holds the s-th
+ * selected field (ascending id) at point p, m = popcount(field_mask). */
+mithra_status mithra_sample_fields(mithra_sim* sim, uint32_t field_mask, const int32_t* ijk,
+                                   int64_t npts, double* out);
+
+/* Radiated power in +z through the vertex plane k_plane (1 <= k_plane <=
+ * nz-2), in the laboratory frame: the grid E, B at t = t0 + (n - 1/2) dt are
+ * transformed to the lab and the Poynting flux is summed over the interior
+ * (i, j) in FP64.  Also returns the lab time and lab position of the plane at
+ * that instant. */
+mithra_status mithra_radiated_power(mithra_sim* sim, int32_t k_plane, double* p_lab,
+                                    double* t_lab, double* z_lab);
+
+/* Makes every following step also record the radiated power through k_plane
+ * (FP64, on the device) for up to capacity steps; capacity 0 switches the
+ * recording off.  mithra_read_power copies the records: out[3*r] = power [W],
+ * out[3*r+1] = lab time, out[3*r+2] = lab position of the plane; *count
+ * receives the number of records (<= max_records copied). */
+mithra_status mithra_set_power_sampling(mithra_sim* sim, int32_t k_plane, int64_t capacity);
+mithra_status mithra_read_power(mithra_sim* sim, double* out, int64_t max_records,
+                                int64_t* count);
+
+/* Copies the particles back in their original order (the library keeps them
+ * sorted by cell tile on the device): positions [m], momenta, and lost[p] = 1
+ * for lost particles (any of the pointers may be NULL).  *n_lost receives the
+ * number of lost particles. */
+mithra_status mithra_copy_particles(mithra_sim* sim, double* x, double* y, double* z,
+                                    double* ux, double* uy, double* uz, int32_t* lost,
+                                    int64_t* n_lost);
+
+/* Frees everything the simulation owns (waits for its work first). */
+mithra_status mithra_destroy(mithra_sim* sim);
+
+/* Last error message of sim, or of the calling thread when sim is NULL.
+ * The string stays valid until the next call on the same sim / thread. */
+const char* mithra_last_error(const mithra_sim* sim);
+
+/* Per-kernel timing with CUDA events recorded on the simulation's stream:
+ * with enable != 0 every following step records an event pair around each
+ * kernel it launches; enable == 0 stops recording.  mithra_kernel_times waits
+ * for the stream and returns, per kernel id k < *n_kernels, the summed
+ * duration ms[k] (milliseconds) and the number of launches[k] since
+ * profiling was enabled (arrays of max_kernels entries).  mithra_kernel_name
+ * names kernel id k (NULL when out of range). */
+mithra_status mithra_profile(mithra_sim* sim, int32_t enable);
+mithra_status mithra_kernel_times(mithra_sim* sim, double* ms, int64_t* launches,
+                                  int32_t max_kernels, int32_t* n_kernels);
+const char* mithra_kernel_name(int32_t kernel);
+
+/* Host-only checks (no GPU needed). */
+
+/* Validates a grid: sizes, spacings, n_sub, boundary; and the stability
+ * condition of the scheme.  Standard scheme: Eq. CFLcondition.  NSFD: with
+ * r_l = c dt / d_l, the left side of Eq. NSFDDispersionCD times (c dt)^2 is
+ * linear in sin^2(kz dz / 2), so a real omega for every wave vector needs
+ * r_x^2 + r_y^2 < 1 and r_z <= 1. */
+mithra_status mithra_check_grid(const mithra_grid* grid);
+
+/* Device bytes mithra_create will allocate for this grid, particle count and
+ * precision (used for admission by memory footprint). */
+mithra_status mithra_footprint(const mithra_grid* grid, int64_t n_particles,
+                               mithra_precision precision, int64_t* bytes);
+
+/* Library version: major*10000 + minor*100 + patch. */
+int32_t mithra_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MITHRA_H */

@@ -14,6 +14,6 @@ __all__ = ["inputs", "mithra"]
 
 def __getattr__(name):
     if name == "mithra":
-        from . import mithra as _m
-        return _m
+        import importlib
+        return importlib.import_module(__name__ + ".mithra")
     raise AttributeError(name)

@@ -1,0 +1,144 @@
+// common.cuh -- shared device definitions of the GB300 FDTD/PIC step.
+//
+// Storage (both precisions T = float / double):
+//   potentials: two levels, each nx*ny*nz cells of V4<T> {A_x, A_y, A_z, phi},
+//               cell (i,j,k) at (k*ny + j)*nx + i (x fastest);
+//   sources:    one array of V4<T> {J_x, J_y, J_z, rho};
+//   particles:  structure of arrays, double-buffered for the re-sort:
+//               int32 cell (linear cell index, -1 once lost), T fraction of
+//               the cell along x, y, z in [0, 1), T momentum u = gamma*beta,
+//               int32 original index.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mithra {
+
+// CODATA 2018 (c and e exact)
+constexpr double kC = 299792458.0;
+constexpr double kQe = 1.602176634e-19;
+constexpr double kMe = 9.1093837015e-31;
+constexpr double kEps0 = 8.8541878128e-12;
+constexpr double kMu0 = 1.0 / (kEps0 * kC * kC);
+constexpr double kPi = 3.14159265358979323846;
+
+// particles are binned into tiles of kTile^3 cells; a tile is the unit of
+// work of the particle kernel
+constexpr int kTile = 8;
+
+template <typename T>
+struct alignas(4 * sizeof(T)) V4 {
+  T x, y, z, w;
+};
+
+template <typename T>
+__host__ __device__ inline V4<T> v4(T x, T y, T z, T w) {
+  V4<T> r;
+  r.x = x; r.y = y; r.z = z; r.w = w;
+  return r;
+}
+template <typename T>
+__host__ __device__ inline V4<T> operator+(V4<T> a, V4<T> b) {
+  return v4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+}
+template <typename T>
+__host__ __device__ inline V4<T> operator-(V4<T> a, V4<T> b) {
+  return v4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w);
+}
+template <typename T>
+__host__ __device__ inline V4<T> operator*(T s, V4<T> a) {
+  return v4(s * a.x, s * a.y, s * a.z, s * a.w);
+}
+
+template <typename T>
+__device__ inline V4<T> ldg4(const V4<T>* p) {
+  return __ldg(p);
+}
+template <>
+__device__ inline V4<float> ldg4<float>(const V4<float>* p) {
+  float4 v = __ldg(reinterpret_cast<const float4*>(p));
+  return v4(v.x, v.y, v.z, v.w);
+}
+template <>
+__device__ inline V4<double> ldg4<double>(const V4<double>* p) {
+  const double2* q = reinterpret_cast<const double2*>(p);
+  double2 a = __ldg(q), b = __ldg(q + 1);
+  return v4(a.x, a.y, b.x, b.y);
+}
+
+// Device-side simulation clock and status words (one per simulation).
+struct StepState {
+  long long n;          // field steps completed
+  long long n_lost;     // particles lost so far
+  int err;              // bit 0: NaN/Inf in a reduction
+  int pad;
+};
+
+// Stencil coefficients (Eq. updateEquation, NSFD alpha' table) and Mur betas
+// indexed by the mask of axes along which the boundary vertex lies outside
+// the interior (x = 1, y = 2, z = 4).
+template <typename T>
+struct StencilP {
+  int nx, ny, nz;
+  long long nxy;
+  T A, omA2, a1, a2, a4, a6;
+  T sA, sphi;      // (c dt)^2 mu0 and (c dt)^2 / eps0
+  T mb0[8], mb1[8];
+  int space_charge;
+};
+
+// Everything the particle and field-evaluation kernels need.
+template <typename T>
+struct PicP {
+  int nx, ny, nz;
+  long long nxy;
+  double x0, y0, z0, dxd, dyd, dzd;
+  T inv2dx, inv2dy, inv2dz, inv4dx, inv4dy, inv4dz, invdt;
+  // Boris: h = qm dtb / (2c), an = qm dtb / 2
+  T h, an;
+  double cdtb_dx, cdtb_dy, cdtb_dz;  // c dt_b / (dx, dy, dz)
+  int n_sub;
+  double t0, dt, dtb;
+  // undulator (lab field transformed to the rest frame)
+  int und_on, fringe;
+  double g0, b0c, zent, L, lam_u, inv_lam_u, ku_d;
+  T ku, B0, ex_fac, by_fac;  // E_x = ex_fac B'_y, B_y = by_fac B'_y
+  // deposit
+  T qV;                      // q / V
+  double jfx, jfy, jfz;      // (q/V) d_l / dt: J_l per cell of displacement
+  // tiles
+  int ntx, nty, ntz, nkeys;
+};
+
+template <typename T>
+struct Parts {
+  int* cell;
+  T* fx;
+  T* fy;
+  T* fz;
+  T* ux;
+  T* uy;
+  T* uz;
+  int* id;
+};
+
+__host__ __device__ inline long long cidx(int i, int j, int k, int nx, long long nxy) {
+  return (long long)k * nxy + (long long)j * nx + i;
+}
+
+// largest value of T below one: a fraction that rounds up to 1 is clamped so
+// that the cell decided in FP64 stays the particle's cell
+template <typename T>
+__host__ __device__ inline T below_one();
+template <>
+__host__ __device__ inline float below_one<float>() { return 0.99999994f; }
+template <>
+__host__ __device__ inline double below_one<double>() { return 0.99999999999999989; }
+
+template <typename T>
+__device__ inline T to_frac(double f) {
+  T r = (T)f;
+  return r >= (T)1 ? below_one<T>() : r;
+}
+
+}  // namespace mithra

@@ -1,0 +1,755 @@
+// mithra.cu -- host side of the C ABI declared in include/mithra.h:
+// validation, device memory, kernel launch order of one field step, copy-in
+// and copy-out.  The kernels live in field_kernels.cuh and
+// particle_kernels.cuh.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "mithra.h"
+#include "common.cuh"
+#include "field_kernels.cuh"
+#include "particle_kernels.cuh"
+
+using namespace mithra;
+
+namespace {
+thread_local std::string g_thread_err;
+}
+
+struct mithra_sim {
+  mithra_grid g{};
+  mithra_undulator u{};
+  int prec = 1;
+  double q_macro = 0.0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int cur = 0;  // P[cur] holds the newest level
+  int pb = 0;   // particle buffer in use
+  void* P[2] = {nullptr, nullptr};
+  void* S = nullptr;
+  void* pbuf[2] = {nullptr, nullptr};
+  int* key = nullptr;
+  int* rank = nullptr;
+  int* count = nullptr;
+  int* offset = nullptr;
+  StepState* dstate = nullptr;
+  double* d_scalar = nullptr;   // one-off reductions
+  double* d_power_rec = nullptr;
+  int64_t power_cap = 0;
+  int64_t power_first = 0;
+  int32_t power_plane = 0;
+  int64_t np = 0;
+  int ntx = 0, nty = 0, ntz = 0, nkeys = 0;
+  int64_t n_issued = 0;
+  double t0 = 0.0;
+  int* h_err = nullptr;  // pinned mirror of dstate->err
+  std::string err;
+  // per-kernel event timing
+  bool profiling = false;
+  struct Rec { int kernel; cudaEvent_t a, b; };
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> spare;
+  double prof_ms[8] = {0};
+  int64_t prof_n[8] = {0};
+};
+
+namespace {
+
+enum KernelId { K_POTENTIAL = 0, K_POWER, K_PUSH, K_SCAN, K_SCATTER, K_COUNT };
+const char* kKernelNames[K_COUNT] = {"potential_step", "power", "push", "scan_counts", "scatter"};
+
+cudaEvent_t take_event(mithra_sim* s) {
+  if (!s->spare.empty()) {
+    cudaEvent_t e = s->spare.back();
+    s->spare.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Brackets one kernel launch with an event pair when profiling is on.
+struct ProfScope {
+  mithra_sim* s;
+  int k;
+  cudaEvent_t b = nullptr;
+  ProfScope(mithra_sim* sim, int kernel) : s(sim), k(kernel) {
+    if (!s->profiling) return;
+    cudaEvent_t a = take_event(s);
+    b = take_event(s);
+    cudaEventRecord(a, s->stream);
+    s->recs.push_back({k, a, b});
+  }
+  ~ProfScope() {
+    if (b) cudaEventRecord(b, s->stream);
+  }
+};
+
+void flush_profile(mithra_sim* s) {
+  for (auto& r : s->recs) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+      s->prof_ms[r.kernel] += ms;
+      s->prof_n[r.kernel] += 1;
+    }
+    s->spare.push_back(r.a);
+    s->spare.push_back(r.b);
+  }
+  s->recs.clear();
+}
+
+mithra_status fail(mithra_sim* s, mithra_status st, const std::string& msg) {
+  if (s)
+    s->err = msg;
+  else
+    g_thread_err = msg;
+  return st;
+}
+
+mithra_status cuda_fail(mithra_sim* s, cudaError_t e, const char* where) {
+  return fail(s, MITHRA_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define MCHECK(sim, call)                                   \
+  do {                                                      \
+    cudaError_t e_ = (call);                                \
+    if (e_ != cudaSuccess) return cuda_fail(sim, e_, #call); \
+  } while (0)
+
+size_t real_size(int prec) { return prec == MITHRA_P64 ? sizeof(double) : sizeof(float); }
+
+int64_t ncell_of(const mithra_grid* g) { return (int64_t)g->nx * g->ny * g->nz; }
+
+void tiles_of(const mithra_grid* g, int* ntx, int* nty, int* ntz) {
+  *ntx = (g->nx + kTile - 1) / kTile;
+  *nty = (g->ny + kTile - 1) / kTile;
+  *ntz = (g->nz + kTile - 1) / kTile;
+}
+
+// bytes of one particle buffer: cell, 3 fractions, 3 momenta, id
+size_t particle_buffer_bytes(int64_t np, int prec) {
+  return (size_t)np * (2 * sizeof(int) + 6 * real_size(prec)) + 6 * 256;
+}
+
+mithra_status check_grid(const mithra_grid* g, std::string* why) {
+  if (!g) { *why = "grid is NULL"; return MITHRA_EINVAL; }
+  if (g->nx < 4 || g->ny < 4 || g->nz < 4) { *why = "nx, ny, nz must be >= 4"; return MITHRA_EINVAL; }
+  if ((int64_t)g->nx * g->ny * g->nz >= (int64_t)1 << 31) { *why = "grid has >= 2^31 vertices"; return MITHRA_EINVAL; }
+  if (!(g->dx > 0) || !(g->dy > 0) || !(g->dz > 0) || !(g->dt > 0)) { *why = "dx, dy, dz, dt must be > 0"; return MITHRA_EINVAL; }
+  if (g->n_sub < 1) { *why = "n_sub must be >= 1"; return MITHRA_EINVAL; }
+  if (g->stencil != 0 && g->stencil != 1) { *why = "stencil must be 0 (NSFD) or 1 (standard)"; return MITHRA_EINVAL; }
+  if (g->boundary != 1) { *why = "boundary must be 1 (first-order Mur)"; return MITHRA_EINVAL; }
+  const double cdt = kC * g->dt;
+  const double rx2 = (cdt / g->dx) * (cdt / g->dx), ry2 = (cdt / g->dy) * (cdt / g->dy),
+               rz2 = (cdt / g->dz) * (cdt / g->dz);
+  if (g->stencil == 0) {
+    if (rx2 + ry2 >= 1.0 || rz2 > 1.0 + 1e-12) {
+      *why = "NSFD stability needs (c dt/dx)^2 + (c dt/dy)^2 < 1 and c dt <= dz";
+      return MITHRA_EUNSTABLE;
+    }
+  } else if (rx2 + ry2 + rz2 >= 1.0) {
+    *why = "standard scheme stability needs c dt < 1/sqrt(1/dx^2 + 1/dy^2 + 1/dz^2)";
+    return MITHRA_EUNSTABLE;
+  }
+  return MITHRA_OK;
+}
+
+template <typename T>
+StencilP<T> make_stencil(const mithra_grid& g) {
+  StencilP<T> p{};
+  p.nx = g.nx; p.ny = g.ny; p.nz = g.nz;
+  p.nxy = (long long)g.nx * g.ny;
+  const double cdt = kC * g.dt;
+  const double rx2 = (cdt / g.dx) * (cdt / g.dx), ry2 = (cdt / g.dy) * (cdt / g.dy),
+               rz2 = (cdt / g.dz) * (cdt / g.dz);
+  double A = 0.0;
+  if (g.stencil == 0) {
+    const double qx = g.dz / g.dx, qy = g.dz / g.dy;
+    A = 0.25 * (1.0 + 0.02 / (qx * qx + qy * qy));  // Eq. NSFDCoefficient
+  }
+  p.A = (T)A;
+  p.omA2 = (T)(1.0 - 2.0 * A);
+  p.a1 = (T)(2.0 * (1.0 - (1.0 - 2.0 * A) * (rx2 + ry2) - rz2));
+  p.a2 = (T)rx2;
+  p.a4 = (T)ry2;
+  p.a6 = (T)(rz2 - 2.0 * A * (rx2 + ry2));
+  p.sA = (T)(cdt * cdt * kMu0);
+  p.sphi = (T)(cdt * cdt / kEps0);
+  for (int m = 0; m < 8; ++m) {
+    double d2 = 0.0;
+    if (m & 1) d2 += g.dx * g.dx;
+    if (m & 2) d2 += g.dy * g.dy;
+    if (m & 4) d2 += g.dz * g.dz;
+    const double d = std::sqrt(d2);
+    p.mb0[m] = (T)((cdt - d) / (cdt + d));
+    p.mb1[m] = (T)(2.0 * d / (cdt + d));
+  }
+  p.space_charge = g.space_charge ? 1 : 0;
+  return p;
+}
+
+template <typename T>
+PicP<T> make_pic(const mithra_sim* s) {
+  const mithra_grid& g = s->g;
+  const mithra_undulator& u = s->u;
+  PicP<T> p{};
+  p.nx = g.nx; p.ny = g.ny; p.nz = g.nz;
+  p.nxy = (long long)g.nx * g.ny;
+  p.x0 = g.x0; p.y0 = g.y0; p.z0 = g.z0;
+  p.dxd = g.dx; p.dyd = g.dy; p.dzd = g.dz;
+  p.inv2dx = (T)(0.5 / g.dx); p.inv2dy = (T)(0.5 / g.dy); p.inv2dz = (T)(0.5 / g.dz);
+  p.inv4dx = (T)(0.25 / g.dx); p.inv4dy = (T)(0.25 / g.dy); p.inv4dz = (T)(0.25 / g.dz);
+  p.invdt = (T)(1.0 / g.dt);
+  const double qm = -kQe / kMe;  // electrons
+  const double dtb = g.dt / g.n_sub;
+  p.h = (T)(qm * dtb / (2.0 * kC));
+  p.an = (T)(qm * dtb / 2.0);
+  p.cdtb_dx = kC * dtb / g.dx; p.cdtb_dy = kC * dtb / g.dy; p.cdtb_dz = kC * dtb / g.dz;
+  p.n_sub = g.n_sub;
+  p.t0 = s->t0; p.dt = g.dt; p.dtb = dtb;
+  p.und_on = (u.K != 0.0) ? 1 : 0;
+  p.fringe = u.fringe ? 1 : 0;
+  p.g0 = u.gamma0;
+  const double b0 = std::sqrt(1.0 - 1.0 / (u.gamma0 * u.gamma0));
+  p.b0c = b0 * kC;
+  p.zent = u.z_ent_lab;
+  p.L = u.length_lab;
+  p.lam_u = u.lambda_u;
+  p.inv_lam_u = 1.0 / u.lambda_u;
+  p.ku_d = 2.0 * kPi / u.lambda_u;
+  p.ku = (T)p.ku_d;
+  p.B0 = (T)(2.0 * kPi * kMe * kC * u.K / (kQe * u.lambda_u));
+  p.ex_fac = (T)(-u.gamma0 * b0 * kC);
+  p.by_fac = (T)u.gamma0;
+  const double V = g.dx * g.dy * g.dz;
+  p.qV = (T)(s->q_macro / V);
+  p.jfx = s->q_macro / V * g.dx / g.dt;
+  p.jfy = s->q_macro / V * g.dy / g.dt;
+  p.jfz = s->q_macro / V * g.dz / g.dt;
+  p.ntx = s->ntx; p.nty = s->nty; p.ntz = s->ntz; p.nkeys = s->nkeys;
+  return p;
+}
+
+template <typename T>
+Parts<T> parts_of(mithra_sim* s, int b) {
+  Parts<T> P{};
+  char* base = static_cast<char*>(s->pbuf[b]);
+  auto carve = [&](size_t bytes) {
+    char* r = base;
+    base += (bytes + 255) & ~size_t(255);
+    return r;
+  };
+  const size_t n = (size_t)s->np;
+  P.cell = reinterpret_cast<int*>(carve(n * sizeof(int)));
+  P.fx = reinterpret_cast<T*>(carve(n * sizeof(T)));
+  P.fy = reinterpret_cast<T*>(carve(n * sizeof(T)));
+  P.fz = reinterpret_cast<T*>(carve(n * sizeof(T)));
+  P.ux = reinterpret_cast<T*>(carve(n * sizeof(T)));
+  P.uy = reinterpret_cast<T*>(carve(n * sizeof(T)));
+  P.uz = reinterpret_cast<T*>(carve(n * sizeof(T)));
+  P.id = reinterpret_cast<int*>(carve(n * sizeof(int)));
+  return P;
+}
+
+unsigned blocks_for(long long n, int threads) {
+  long long b = (n + threads - 1) / threads;
+  return (unsigned)(b < 1 ? 1 : b);
+}
+
+template <typename T>
+mithra_status launch_step(mithra_sim* s) {
+  const StencilP<T> sp = make_stencil<T>(s->g);
+  const PicP<T> pp = make_pic<T>(s);
+  V4<T>* P0 = static_cast<V4<T>*>(s->P[s->cur]);       // level n
+  V4<T>* P1 = static_cast<V4<T>*>(s->P[1 - s->cur]);   // level n-1 -> n+1
+  V4<T>* S = static_cast<V4<T>*>(s->S);
+  dim3 blk(32, 8, 1);
+  dim3 grd((s->g.nx + 31) / 32, (s->g.ny + 7) / 8, s->g.nz);
+  {
+    ProfScope ps(s, K_POTENTIAL);
+    k_potential_step<T><<<grd, blk, 0, s->stream>>>(sp, P0, P1, S);
+  }
+  if (s->power_cap > 0) {
+    ProfScope ps(s, K_POWER);
+    k_power<T><<<64, 256, 0, s->stream>>>(pp, P0, P1, s->power_plane, s->u.gamma0,
+                                          std::sqrt(1.0 - 1.0 / (s->u.gamma0 * s->u.gamma0)),
+                                          s->d_power_rec - s->power_first, s->dstate,
+                                          s->power_first + s->power_cap, 1, &s->dstate->err);
+  }
+  if (s->np > 0) {
+    Parts<T> A = parts_of<T>(s, s->pb), B = parts_of<T>(s, 1 - s->pb);
+    {
+      ProfScope ps(s, K_PUSH);
+      k_push<T><<<blocks_for(s->np, 256), 256, 0, s->stream>>>(pp, s->dstate, P0, P1, S, A,
+                                                               s->np, s->count, s->key, s->rank,
+                                                               &s->dstate->n_lost);
+    }
+    {
+      ProfScope ps(s, K_SCAN);
+      k_scan_counts<<<1, 1024, 0, s->stream>>>(s->count, s->offset, s->nkeys + 1, s->dstate, 1);
+    }
+    {
+      ProfScope ps(s, K_SCATTER);
+      k_scatter<T><<<blocks_for(s->np, 256), 256, 0, s->stream>>>(A, B, s->np, s->key, s->rank,
+                                                                  s->offset);
+    }
+    s->pb = 1 - s->pb;
+  } else {
+    k_scan_counts<<<1, 32, 0, s->stream>>>(s->count, s->offset, 1, s->dstate, 1);
+  }
+  s->cur = 1 - s->cur;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(s, e, "step launch");
+  return MITHRA_OK;
+}
+
+template <typename T>
+mithra_status init_particles(mithra_sim* s, const mithra_bunch* b) {
+  const PicP<T> pp = make_pic<T>(s);
+  const int64_t n = s->np;
+  double* d = nullptr;
+  MCHECK(s, cudaMalloc(&d, sizeof(double) * 6 * (size_t)n));
+  const double* src[6] = {b->x, b->y, b->z, b->ux, b->uy, b->uz};
+  for (int a = 0; a < 6; ++a)
+    MCHECK(s, cudaMemcpyAsync(d + a * n, src[a], sizeof(double) * n, cudaMemcpyHostToDevice,
+                              s->stream));
+  Parts<T> A = parts_of<T>(s, 0), B = parts_of<T>(s, 1);
+  long long* lost = &s->dstate->n_lost;
+  k_init_particles<T><<<blocks_for(n, 256), 256, 0, s->stream>>>(
+      pp, n, d, d + n, d + 2 * n, d + 3 * n, d + 4 * n, d + 5 * n, A, s->count, s->key, s->rank,
+      lost);
+  k_scan_counts<<<1, 1024, 0, s->stream>>>(s->count, s->offset, s->nkeys + 1, s->dstate, 0);
+  k_scatter<T><<<blocks_for(n, 256), 256, 0, s->stream>>>(A, B, n, s->key, s->rank, s->offset);
+  s->pb = 1;
+  k_deposit_rho<T><<<blocks_for(n, 256), 256, 0, s->stream>>>(pp, B, n,
+                                                              static_cast<V4<T>*>(s->S));
+  MCHECK(s, cudaGetLastError());
+  MCHECK(s, cudaStreamSynchronize(s->stream));
+  MCHECK(s, cudaFree(d));
+  return MITHRA_OK;
+}
+
+mithra_status sync_status(mithra_sim* s) {
+  cudaError_t e = cudaStreamSynchronize(s->stream);
+  if (e != cudaSuccess) return cuda_fail(s, e, "stream synchronize");
+  StepState st;
+  e = cudaMemcpy(&st, s->dstate, sizeof(st), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(s, e, "state copy");
+  if (st.err & 1) return fail(s, MITHRA_ENUMERIC, "NaN or Inf in a power reduction");
+  return MITHRA_OK;
+}
+
+template <typename T>
+mithra_status copy_field_impl(mithra_sim* s, int what, double* out) {
+  const PicP<T> pp = make_pic<T>(s);
+  const int64_t n = ncell_of(&s->g);
+  double* d = nullptr;
+  MCHECK(s, cudaMalloc(&d, sizeof(double) * n));
+  const V4<T>* Pn = static_cast<const V4<T>*>(s->P[s->cur]);
+  const V4<T>* Po = static_cast<const V4<T>*>(s->P[1 - s->cur]);
+  const V4<T>* lev = Pn;
+  int code = 0;
+  if (what <= MITHRA_BZ) code = what;
+  else if (what <= MITHRA_AZ) code = 6 + (what - MITHRA_AX);
+  else if (what <= MITHRA_JZ) code = 10 + (what - MITHRA_JX);
+  else if (what == MITHRA_PHI) code = 9;
+  else if (what == MITHRA_RHO) code = 13;
+  else { lev = Po; code = 6 + (what - MITHRA_AX_PREV); }
+  k_extract<T><<<1024, 256, 0, s->stream>>>(pp, Po, Pn, lev, static_cast<const V4<T>*>(s->S),
+                                            code, d);
+  MCHECK(s, cudaGetLastError());
+  MCHECK(s, cudaMemcpyAsync(out, d, sizeof(double) * n, cudaMemcpyDeviceToHost, s->stream));
+  mithra_status st = sync_status(s);
+  cudaFree(d);
+  return st;
+}
+
+template <typename T>
+mithra_status set_field_impl(mithra_sim* s, int what, const double* in) {
+  const int64_t n = ncell_of(&s->g);
+  V4<T>* dst;
+  int comp;
+  if (what >= MITHRA_AX && what <= MITHRA_AZ) { dst = static_cast<V4<T>*>(s->P[s->cur]); comp = what - MITHRA_AX; }
+  else if (what == MITHRA_PHI) { dst = static_cast<V4<T>*>(s->P[s->cur]); comp = 3; }
+  else if (what >= MITHRA_JX && what <= MITHRA_JZ) { dst = static_cast<V4<T>*>(s->S); comp = what - MITHRA_JX; }
+  else if (what == MITHRA_RHO) { dst = static_cast<V4<T>*>(s->S); comp = 3; }
+  else if (what >= MITHRA_AX_PREV && what <= MITHRA_PHI_PREV) { dst = static_cast<V4<T>*>(s->P[1 - s->cur]); comp = what - MITHRA_AX_PREV; }
+  else return fail(s, MITHRA_EINVAL, "field cannot be set (E and B derive from the potentials)");
+  double* d = nullptr;
+  MCHECK(s, cudaMalloc(&d, sizeof(double) * n));
+  MCHECK(s, cudaMemcpyAsync(d, in, sizeof(double) * n, cudaMemcpyHostToDevice, s->stream));
+  k_insert<T><<<1024, 256, 0, s->stream>>>(n, d, dst, comp);
+  MCHECK(s, cudaGetLastError());
+  mithra_status st = sync_status(s);
+  cudaFree(d);
+  return st;
+}
+
+template <typename T>
+mithra_status sample_impl(mithra_sim* s, uint32_t mask, const int32_t* ijk, int64_t npts,
+                          double* out) {
+  const PicP<T> pp = make_pic<T>(s);
+  const int m = __builtin_popcount(mask);
+  int* dijk = nullptr;
+  double* dout = nullptr;
+  MCHECK(s, cudaMalloc(&dijk, sizeof(int) * 3 * npts));
+  MCHECK(s, cudaMalloc(&dout, sizeof(double) * m * npts));
+  MCHECK(s, cudaMemcpyAsync(dijk, ijk, sizeof(int) * 3 * npts, cudaMemcpyHostToDevice, s->stream));
+  k_sample<T><<<blocks_for(npts, 128), 128, 0, s->stream>>>(
+      pp, static_cast<const V4<T>*>(s->P[1 - s->cur]), static_cast<const V4<T>*>(s->P[s->cur]),
+      static_cast<const V4<T>*>(s->S), dijk, npts, mask, m, dout);
+  MCHECK(s, cudaGetLastError());
+  MCHECK(s, cudaMemcpyAsync(out, dout, sizeof(double) * m * npts, cudaMemcpyDeviceToHost,
+                            s->stream));
+  mithra_status st = sync_status(s);
+  cudaFree(dijk);
+  cudaFree(dout);
+  return st;
+}
+
+template <typename T>
+mithra_status power_impl(mithra_sim* s, int kp, double* p) {
+  const PicP<T> pp = make_pic<T>(s);
+  MCHECK(s, cudaMemsetAsync(s->d_scalar, 0, sizeof(double), s->stream));
+  const double g0 = s->u.gamma0;
+  k_power<T><<<64, 256, 0, s->stream>>>(pp, static_cast<const V4<T>*>(s->P[1 - s->cur]),
+                                        static_cast<const V4<T>*>(s->P[s->cur]), kp, g0,
+                                        std::sqrt(1.0 - 1.0 / (g0 * g0)), s->d_scalar, s->dstate,
+                                        0, 0, &s->dstate->err);
+  MCHECK(s, cudaGetLastError());
+  MCHECK(s, cudaMemcpyAsync(p, s->d_scalar, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  return sync_status(s);
+}
+
+template <typename T>
+mithra_status copy_particles_impl(mithra_sim* s, double* out7) {
+  const PicP<T> pp = make_pic<T>(s);
+  double* d = nullptr;
+  MCHECK(s, cudaMalloc(&d, sizeof(double) * 7 * (size_t)s->np));
+  k_copy_out<T><<<blocks_for(s->np, 256), 256, 0, s->stream>>>(pp, parts_of<T>(s, s->pb),
+                                                               s->np, d);
+  MCHECK(s, cudaGetLastError());
+  MCHECK(s, cudaMemcpyAsync(out7, d, sizeof(double) * 7 * (size_t)s->np, cudaMemcpyDeviceToHost,
+                            s->stream));
+  mithra_status st = sync_status(s);
+  cudaFree(d);
+  return st;
+}
+
+void lab_of(const mithra_sim* s, int32_t kp, double t, double* t_lab, double* z_lab) {
+  const double g0 = s->u.gamma0;
+  const double b0 = std::sqrt(1.0 - 1.0 / (g0 * g0));
+  const double zp = s->g.z0 + kp * s->g.dz;
+  *t_lab = g0 * (t + b0 * zp / kC);
+  *z_lab = g0 * (zp + b0 * kC * t);
+}
+
+void free_all(mithra_sim* s) {
+  if (s->stream) cudaStreamSynchronize(s->stream);
+  void* ptrs[] = {s->P[0], s->P[1], s->S, s->pbuf[0], s->pbuf[1], s->key, s->rank, s->count,
+                  s->offset, s->dstate, s->d_scalar, s->d_power_rec};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (s->h_err) cudaFreeHost(s->h_err);
+  for (auto& r : s->recs) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (cudaEvent_t e : s->spare) cudaEventDestroy(e);
+  if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t mithra_version(void) { return 100; }
+
+const char* mithra_last_error(const mithra_sim* sim) {
+  return sim ? sim->err.c_str() : g_thread_err.c_str();
+}
+
+mithra_status mithra_check_grid(const mithra_grid* grid) {
+  std::string why;
+  mithra_status st = check_grid(grid, &why);
+  if (st != MITHRA_OK) return fail(nullptr, st, why);
+  return MITHRA_OK;
+}
+
+mithra_status mithra_footprint(const mithra_grid* grid, int64_t n_particles,
+                               mithra_precision precision, int64_t* bytes) {
+  std::string why;
+  mithra_status st = check_grid(grid, &why);
+  if (st != MITHRA_OK) return fail(nullptr, st, why);
+  if (!bytes || n_particles < 0) return fail(nullptr, MITHRA_EINVAL, "bad footprint arguments");
+  int ntx, nty, ntz;
+  tiles_of(grid, &ntx, &nty, &ntz);
+  const int64_t nkeys = (int64_t)ntx * nty * ntz;
+  const size_t r = real_size(precision);
+  int64_t b = 3 * ncell_of(grid) * 4 * (int64_t)r;              // 2 levels + sources
+  b += 2 * (int64_t)particle_buffer_bytes(n_particles, precision);
+  b += 2 * n_particles * (int64_t)sizeof(int);                   // key, rank
+  b += 2 * (nkeys + 2) * (int64_t)sizeof(int);                   // count, offset
+  b += (int64_t)sizeof(StepState) + (int64_t)sizeof(double);
+  *bytes = b;
+  return MITHRA_OK;
+}
+
+mithra_status mithra_create(const mithra_grid* grid, const mithra_undulator* und,
+                            const mithra_bunch* bunch, mithra_precision precision,
+                            void* cuda_stream, mithra_sim** out) {
+  if (!out) return fail(nullptr, MITHRA_EINVAL, "out is NULL");
+  *out = nullptr;
+  std::string why;
+  mithra_status st = check_grid(grid, &why);
+  if (st != MITHRA_OK) return fail(nullptr, st, why);
+  if (!und) return fail(nullptr, MITHRA_EINVAL, "undulator is NULL");
+  if (!(und->gamma0 > 1.0) || !(und->lambda_u > 0.0))
+    return fail(nullptr, MITHRA_EINVAL, "undulator needs gamma0 > 1 and lambda_u > 0");
+  if (precision != MITHRA_P32 && precision != MITHRA_P64)
+    return fail(nullptr, MITHRA_EINVAL, "precision must be MITHRA_P32 or MITHRA_P64");
+  const int64_t np = bunch ? bunch->n : 0;
+  if (np < 0 || np >= ((int64_t)1 << 31)) return fail(nullptr, MITHRA_EINVAL, "bad particle count");
+  if (np > 0 && (!bunch->x || !bunch->y || !bunch->z || !bunch->ux || !bunch->uy || !bunch->uz))
+    return fail(nullptr, MITHRA_EINVAL, "bunch arrays must not be NULL");
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1)
+    return fail(nullptr, MITHRA_ENODEV, "no CUDA device");
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess || prop.major != 10 || prop.minor != 3)
+    return fail(nullptr, MITHRA_ENODEV, "this library is built for sm_103a (GB300) only");
+
+  mithra_sim* s = new (std::nothrow) mithra_sim();
+  if (!s) return fail(nullptr, MITHRA_ENOMEM, "host allocation failed");
+  s->g = *grid;
+  s->u = *und;
+  s->prec = precision;
+  s->q_macro = bunch ? bunch->q_macro : 0.0;
+  s->np = np;
+  tiles_of(grid, &s->ntx, &s->nty, &s->ntz);
+  s->nkeys = s->ntx * s->nty * s->ntz;
+  auto bail = [&](mithra_status code, const std::string& msg) {
+    free_all(s);
+    delete s;
+    return fail(nullptr, code, msg);
+  };
+  if (cuda_stream) {
+    s->stream = static_cast<cudaStream_t>(cuda_stream);
+  } else {
+    if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess)
+      return bail(MITHRA_ECUDA, "stream creation failed");
+    s->own_stream = true;
+  }
+  const size_t r = real_size(precision);
+  const size_t field_bytes = (size_t)ncell_of(grid) * 4 * r;
+  auto dalloc = [&](void** p, size_t bytes) { return cudaMalloc(p, bytes < 256 ? 256 : bytes) == cudaSuccess; };
+  bool ok = dalloc(&s->P[0], field_bytes) && dalloc(&s->P[1], field_bytes) &&
+            dalloc(&s->S, field_bytes) &&
+            dalloc(&s->pbuf[0], particle_buffer_bytes(np, precision)) &&
+            dalloc(&s->pbuf[1], particle_buffer_bytes(np, precision)) &&
+            dalloc((void**)&s->key, sizeof(int) * (size_t)(np + 1)) &&
+            dalloc((void**)&s->rank, sizeof(int) * (size_t)(np + 1)) &&
+            dalloc((void**)&s->count, sizeof(int) * (size_t)(s->nkeys + 2)) &&
+            dalloc((void**)&s->offset, sizeof(int) * (size_t)(s->nkeys + 2)) &&
+            dalloc((void**)&s->dstate, sizeof(StepState)) &&
+            dalloc((void**)&s->d_scalar, sizeof(double));
+  if (!ok) return bail(MITHRA_ENOMEM, "device allocation failed");
+  if (cudaMallocHost((void**)&s->h_err, sizeof(int)) != cudaSuccess)
+    return bail(MITHRA_ENOMEM, "pinned allocation failed");
+  *s->h_err = 0;
+  cudaMemsetAsync(s->P[0], 0, field_bytes, s->stream);
+  cudaMemsetAsync(s->P[1], 0, field_bytes, s->stream);
+  cudaMemsetAsync(s->S, 0, field_bytes, s->stream);
+  cudaMemsetAsync(s->count, 0, sizeof(int) * (size_t)(s->nkeys + 2), s->stream);
+  cudaMemsetAsync(s->dstate, 0, sizeof(StepState), s->stream);
+  if (np > 0) {
+    st = (precision == MITHRA_P64) ? init_particles<double>(s, bunch) : init_particles<float>(s, bunch);
+    if (st != MITHRA_OK) {
+      std::string msg = s->err;
+      return bail(st, msg);
+    }
+  }
+  if (cudaStreamSynchronize(s->stream) != cudaSuccess) return bail(MITHRA_ECUDA, "set-up failed");
+  *out = s;
+  return MITHRA_OK;
+}
+
+mithra_status mithra_step(mithra_sim* s, int64_t n) {
+  if (!s) return fail(nullptr, MITHRA_EINVAL, "sim is NULL");
+  if (n < 0) return fail(s, MITHRA_EINVAL, "n must be >= 0");
+  if (*s->h_err & 1) return fail(s, MITHRA_ENUMERIC, "NaN or Inf in a power reduction");
+  for (int64_t t = 0; t < n; ++t) {
+    mithra_status st = (s->prec == MITHRA_P64) ? launch_step<double>(s) : launch_step<float>(s);
+    if (st != MITHRA_OK) return st;
+    s->n_issued += 1;
+  }
+  cudaMemcpyAsync(s->h_err, &s->dstate->err, sizeof(int), cudaMemcpyDeviceToHost, s->stream);
+  return MITHRA_OK;
+}
+
+mithra_status mithra_sync(mithra_sim* s) {
+  if (!s) return fail(nullptr, MITHRA_EINVAL, "sim is NULL");
+  return sync_status(s);
+}
+
+mithra_status mithra_time(const mithra_sim* s, int64_t* n_steps, double* t) {
+  if (!s) return fail(nullptr, MITHRA_EINVAL, "sim is NULL");
+  if (n_steps) *n_steps = s->n_issued;
+  if (t) *t = s->t0 + (double)s->n_issued * s->g.dt;
+  return MITHRA_OK;
+}
+
+mithra_status mithra_copy_field(mithra_sim* s, int32_t field, double* out) {
+  if (!s) return fail(nullptr, MITHRA_EINVAL, "sim is NULL");
+  if (!out || field < 0 || field > MITHRA_PHI_PREV) return fail(s, MITHRA_EINVAL, "bad field id or NULL out");
+  return s->prec == MITHRA_P64 ? copy_field_impl<double>(s, field, out)
+                               : copy_field_impl<float>(s, field, out);
+}
+
+mithra_status mithra_set_field(mithra_sim* s, int32_t field, const double* in) {
+  if (!s) return fail(nullptr, MITHRA_EINVAL, "sim is NULL");
+  if (!in || field < 0 || field > MITHRA_PHI_PREV) return fail(s, MITHRA_EINVAL, "bad field id or NULL in");
+  return s->prec == MITHRA_P64 ? set_field_impl<double>(s, field, in)
+                               : set_field_impl<float>(s, field, in);
+}
+
+mithra_status mithra_sample_fields(mithra_sim* s, uint32_t mask, const int32_t* ijk, int64_t npts,
+                                   double* out) {
+  if (!s) return fail(nullptr, MITHRA_EINVAL, "sim is NULL");
+  if (npts == 0) return MITHRA_OK;
+  if (!ijk || !out || npts < 0 || mask == 0 || (mask >> 14))
+    return fail(s, MITHRA_EINVAL, "bad sampling arguments");
+  for (int64_t p = 0; p < npts; ++p) {
+    const int i = ijk[3 * p], j = ijk[3 * p + 1], k = ijk[3 * p + 2];
+    if (i < 0 || i >= s->g.nx || j < 0 || j >= s->g.ny || k < 0 || k >= s->g.nz)
+      return fail(s, MITHRA_EINVAL, "sample point outside the grid");
+  }
+  return s->prec == MITHRA_P64 ? sample_impl<double>(s, mask, ijk, npts, out)
+                               : sample_impl<float>(s, mask, ijk, npts, out);
+}
+
+mithra_status mithra_radiated_power(mithra_sim* s, int32_t k_plane, double* p_lab, double* t_lab,
+                                    double* z_lab) {
+  if (!s) return fail(nullptr, MITHRA_EINVAL, "sim is NULL");
+  if (k_plane < 1 || k_plane > s->g.nz - 2) return fail(s, MITHRA_EINVAL, "k_plane outside [1, nz-2]");
+  double p = 0.0;
+  mithra_status st = s->prec == MITHRA_P64 ? power_impl<double>(s, k_plane, &p)
+                                           : power_impl<float>(s, k_plane, &p);
+  if (st != MITHRA_OK) return st;
+  const double t = s->t0 + ((double)s->n_issued - 0.5) * s->g.dt;
+  double tl, zl;
+  lab_of(s, k_plane, t, &tl, &zl);
+  if (p_lab) *p_lab = p;
+  if (t_lab) *t_lab = tl;
+  if (z_lab) *z_lab = zl;
+  return MITHRA_OK;
+}
+
+mithra_status mithra_set_power_sampling(mithra_sim* s, int32_t k_plane, int64_t capacity) {
+  if (!s) return fail(nullptr, MITHRA_EINVAL, "sim is NULL");
+  if (capacity < 0) return fail(s, MITHRA_EINVAL, "capacity must be >= 0");
+  if (capacity > 0 && (k_plane < 1 || k_plane > s->g.nz - 2))
+    return fail(s, MITHRA_EINVAL, "k_plane outside [1, nz-2]");
+  MCHECK(s, cudaStreamSynchronize(s->stream));
+  if (s->d_power_rec) {
+    cudaFree(s->d_power_rec);
+    s->d_power_rec = nullptr;
+  }
+  s->power_cap = 0;
+  if (capacity == 0) return MITHRA_OK;
+  if (cudaMalloc((void**)&s->d_power_rec, sizeof(double) * (size_t)capacity) != cudaSuccess)
+    return fail(s, MITHRA_ENOMEM, "power record allocation failed");
+  MCHECK(s, cudaMemset(s->d_power_rec, 0, sizeof(double) * (size_t)capacity));
+  s->power_cap = capacity;
+  s->power_plane = k_plane;
+  s->power_first = s->n_issued;
+  return MITHRA_OK;
+}
+
+mithra_status mithra_read_power(mithra_sim* s, double* out, int64_t max_records, int64_t* count) {
+  if (!s) return fail(nullptr, MITHRA_EINVAL, "sim is NULL");
+  int64_t have = s->n_issued - s->power_first;
+  if (s->power_cap == 0) have = 0;
+  if (have > s->power_cap) have = s->power_cap;
+  if (count) *count = have;
+  const int64_t m = have < max_records ? have : max_records;
+  if (m <= 0 || !out) return sync_status(s);
+  std::vector<double> p((size_t)m);
+  MCHECK(s, cudaMemcpyAsync(p.data(), s->d_power_rec, sizeof(double) * m, cudaMemcpyDeviceToHost,
+                            s->stream));
+  mithra_status st = sync_status(s);
+  if (st != MITHRA_OK) return st;
+  for (int64_t r = 0; r < m; ++r) {
+    const double t = s->t0 + ((double)(s->power_first + r) + 0.5) * s->g.dt;
+    out[3 * r] = p[(size_t)r];
+    lab_of(s, s->power_plane, t, &out[3 * r + 1], &out[3 * r + 2]);
+  }
+  return MITHRA_OK;
+}
+
+mithra_status mithra_copy_particles(mithra_sim* s, double* x, double* y, double* z, double* ux,
+                                    double* uy, double* uz, int32_t* lost, int64_t* n_lost) {
+  if (!s) return fail(nullptr, MITHRA_EINVAL, "sim is NULL");
+  if (s->np > 0 && (x || y || z || ux || uy || uz || lost)) {
+    std::vector<double> buf((size_t)s->np * 7);
+    mithra_status st = s->prec == MITHRA_P64 ? copy_particles_impl<double>(s, buf.data())
+                                             : copy_particles_impl<float>(s, buf.data());
+    if (st != MITHRA_OK) return st;
+    double* dst[6] = {x, y, z, ux, uy, uz};
+    for (int a = 0; a < 6; ++a)
+      if (dst[a]) std::memcpy(dst[a], buf.data() + (size_t)a * s->np, sizeof(double) * s->np);
+    if (lost)
+      for (int64_t q = 0; q < s->np; ++q) lost[q] = buf[(size_t)6 * s->np + q] != 0.0 ? 1 : 0;
+  }
+  if (n_lost) {
+    StepState st;
+    MCHECK(s, cudaStreamSynchronize(s->stream));
+    MCHECK(s, cudaMemcpy(&st, s->dstate, sizeof(st), cudaMemcpyDeviceToHost));
+    *n_lost = st.n_lost;
+  }
+  return MITHRA_OK;
+}
+
+mithra_status mithra_profile(mithra_sim* s, int32_t enable) {
+  if (!s) return fail(nullptr, MITHRA_EINVAL, "sim is NULL");
+  if (enable && !s->profiling) {
+    for (int k = 0; k < K_COUNT; ++k) { s->prof_ms[k] = 0.0; s->prof_n[k] = 0; }
+  }
+  s->profiling = enable != 0;
+  return MITHRA_OK;
+}
+
+mithra_status mithra_kernel_times(mithra_sim* s, double* ms, int64_t* launches,
+                                  int32_t max_kernels, int32_t* n_kernels) {
+  if (!s) return fail(nullptr, MITHRA_EINVAL, "sim is NULL");
+  MCHECK(s, cudaStreamSynchronize(s->stream));
+  flush_profile(s);
+  if (n_kernels) *n_kernels = K_COUNT;
+  for (int k = 0; k < K_COUNT && k < max_kernels; ++k) {
+    if (ms) ms[k] = s->prof_ms[k];
+    if (launches) launches[k] = s->prof_n[k];
+  }
+  return MITHRA_OK;
+}
+
+const char* mithra_kernel_name(int32_t kernel) {
+  return (kernel >= 0 && kernel < K_COUNT) ? kKernelNames[kernel] : nullptr;
+}
+
+mithra_status mithra_destroy(mithra_sim* s) {
+  if (!s) return MITHRA_OK;
+  free_all(s);
+  delete s;
+  return MITHRA_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,281 @@
+"""Thin ctypes binding of the C ABI in include/mithra.h (argument marshalling
+only; every step of the time loop runs in the CUDA library).
+
+The library is loaded from ``_build/libmithra.so`` inside this package; when it
+is missing the binding raises instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_build", "libmithra.so")
+
+OK, EINVAL, EUNSTABLE, ENOMEM, ECUDA, ENUMERIC, ELOST, EBUSY, ENODEV = range(9)
+P64, P32 = 0, 1
+FIELDS = ["Ex", "Ey", "Ez", "Bx", "By", "Bz", "Ax", "Ay", "Az", "Jx", "Jy", "Jz", "phi", "rho",
+          "Ax_prev", "Ay_prev", "Az_prev", "phi_prev"]
+FIELD_ID = {name: i for i, name in enumerate(FIELDS)}
+
+# every symbol include/mithra.h declares
+EXPORTS = ["mithra_create", "mithra_step", "mithra_sync", "mithra_time", "mithra_copy_field",
+           "mithra_set_field", "mithra_sample_fields", "mithra_radiated_power",
+           "mithra_set_power_sampling", "mithra_read_power", "mithra_copy_particles",
+           "mithra_destroy", "mithra_last_error", "mithra_check_grid", "mithra_footprint",
+           "mithra_version", "mithra_profile", "mithra_kernel_times", "mithra_kernel_name"]
+
+
+class MithraError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"mithra status {status}: {msg}")
+        self.status = status
+
+
+class Grid(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
+                ("dx", C.c_double), ("dy", C.c_double), ("dz", C.c_double),
+                ("x0", C.c_double), ("y0", C.c_double), ("z0", C.c_double),
+                ("dt", C.c_double), ("n_sub", C.c_int32), ("stencil", C.c_int32),
+                ("boundary", C.c_int32), ("space_charge", C.c_int32)]
+
+
+class Undulator(C.Structure):
+    _fields_ = [("gamma0", C.c_double), ("lambda_u", C.c_double), ("K", C.c_double),
+                ("z_ent_lab", C.c_double), ("length_lab", C.c_double), ("fringe", C.c_int32)]
+
+
+class Bunch(C.Structure):
+    _fields_ = [("n", C.c_int64), ("q_macro", C.c_double),
+                ("x", C.POINTER(C.c_double)), ("y", C.POINTER(C.c_double)),
+                ("z", C.POINTER(C.c_double)), ("ux", C.POINTER(C.c_double)),
+                ("uy", C.POINTER(C.c_double)), ("uz", C.POINTER(C.c_double))]
+
+
+_lib = None
+
+
+def lib():
+    """Loads libmithra.so; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise MithraError(ENODEV, f"CUDA library missing at {LIB_PATH}: run "
+                                  "__graft_entry__.build() (no CPU fallback exists)")
+    L = C.CDLL(LIB_PATH)
+    dp = C.POINTER(C.c_double)
+    vp = C.c_void_p
+    st = C.c_int
+    L.mithra_create.argtypes = [C.POINTER(Grid), C.POINTER(Undulator), C.POINTER(Bunch), C.c_int,
+                                vp, C.POINTER(vp)]
+    L.mithra_step.argtypes = [vp, C.c_int64]
+    L.mithra_sync.argtypes = [vp]
+    L.mithra_time.argtypes = [vp, C.POINTER(C.c_int64), dp]
+    L.mithra_copy_field.argtypes = [vp, C.c_int32, dp]
+    L.mithra_set_field.argtypes = [vp, C.c_int32, dp]
+    L.mithra_sample_fields.argtypes = [vp, C.c_uint32, C.POINTER(C.c_int32), C.c_int64, dp]
+    L.mithra_radiated_power.argtypes = [vp, C.c_int32, dp, dp, dp]
+    L.mithra_set_power_sampling.argtypes = [vp, C.c_int32, C.c_int64]
+    L.mithra_read_power.argtypes = [vp, dp, C.c_int64, C.POINTER(C.c_int64)]
+    L.mithra_copy_particles.argtypes = [vp, dp, dp, dp, dp, dp, dp, C.POINTER(C.c_int32),
+                                        C.POINTER(C.c_int64)]
+    L.mithra_destroy.argtypes = [vp]
+    L.mithra_last_error.argtypes = [vp]
+    L.mithra_last_error.restype = C.c_char_p
+    L.mithra_check_grid.argtypes = [C.POINTER(Grid)]
+    L.mithra_footprint.argtypes = [C.POINTER(Grid), C.c_int64, C.c_int, C.POINTER(C.c_int64)]
+    L.mithra_version.restype = C.c_int32
+    L.mithra_profile.argtypes = [vp, C.c_int32]
+    L.mithra_kernel_times.argtypes = [vp, dp, C.POINTER(C.c_int64), C.c_int32,
+                                      C.POINTER(C.c_int32)]
+    L.mithra_kernel_name.argtypes = [C.c_int32]
+    L.mithra_kernel_name.restype = C.c_char_p
+    for name in EXPORTS:
+        if name not in ("mithra_last_error", "mithra_version", "mithra_kernel_name"):
+            getattr(L, name).restype = st
+    _lib = L
+    return L
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def make_grid(g: dict) -> Grid:
+    return Grid(int(g["nx"]), int(g["ny"]), int(g["nz"]), g["dx"], g["dy"], g["dz"],
+                g.get("x0", 0.0), g.get("y0", 0.0), g.get("z0", 0.0), g["dt"],
+                int(g.get("n_sub", 1)), int(g.get("stencil", 0)), int(g.get("boundary", 1)),
+                int(g.get("space_charge", 1)))
+
+
+def make_undulator(u: dict | None) -> Undulator:
+    if u is None:
+        return Undulator(1.0e3, 1.0, 0.0, 0.0, 0.0, 0)
+    return Undulator(u["gamma0"], u["lambda_u"], u["K"], u.get("z_ent_lab", 0.0),
+                     u.get("length_lab", 0.0), int(u.get("fringe", 1)))
+
+
+def _check(status: int, handle=None):
+    if status != OK:
+        msg = lib().mithra_last_error(handle)
+        raise MithraError(status, msg.decode() if msg else "")
+
+
+def check_grid(g: dict) -> int:
+    """Status of mithra_check_grid (host only; no GPU needed)."""
+    return lib().mithra_check_grid(C.byref(make_grid(g)))
+
+
+def footprint(g: dict, n_particles: int, precision: int = P32) -> int:
+    out = C.c_int64(0)
+    _check(lib().mithra_footprint(C.byref(make_grid(g)), int(n_particles), int(precision),
+                                  C.byref(out)))
+    return int(out.value)
+
+
+def last_error() -> str:
+    m = lib().mithra_last_error(None)
+    return m.decode() if m else ""
+
+
+CUDA_STREAM_LEGACY = 1  # cudaStreamLegacy
+
+
+def stream_arg(stream):
+    """None: the library creates its own stream.  An int handle is passed
+    through, except 0 (the legacy default stream in CUDA and PyTorch), which
+    the C ABI spells cudaStreamLegacy because NULL means 'library-owned'."""
+    if stream is None:
+        return None
+    return C.c_void_p(int(stream) if int(stream) != 0 else CUDA_STREAM_LEGACY)
+
+
+class Simulation:
+    """One simulation on the current CUDA device (see include/mithra.h)."""
+
+    def __init__(self, grid: dict, undulator: dict | None, bunch: dict | None,
+                 precision: int = P32, stream: int | None = None):
+        L = lib()
+        self.grid = dict(grid)
+        self.precision = precision
+        n = 0 if bunch is None else int(np.asarray(bunch["x"]).size)
+        self.n_particles = n
+        self._keep = []
+        if n:
+            arrs = [np.ascontiguousarray(bunch[k], dtype=np.float64)
+                    for k in ("x", "y", "z", "ux", "uy", "uz")]
+            self._keep = arrs
+            b = Bunch(n, float(bunch.get("q_macro", 0.0)), *[_dp(a) for a in arrs])
+        else:
+            b = Bunch(0, 0.0, None, None, None, None, None, None)
+        h = C.c_void_p()
+        _check(L.mithra_create(C.byref(make_grid(grid)), C.byref(make_undulator(undulator)),
+                               C.byref(b), int(precision),
+                               stream_arg(stream), C.byref(h)))
+        self._keep = []
+        self.h = h
+
+    # -- time loop -------------------------------------------------------
+    def step(self, n: int = 1):
+        _check(lib().mithra_step(self.h, int(n)), self.h)
+
+    def sync(self):
+        _check(lib().mithra_sync(self.h), self.h)
+
+    def time(self):
+        n = C.c_int64()
+        t = C.c_double()
+        _check(lib().mithra_time(self.h, C.byref(n), C.byref(t)), self.h)
+        return int(n.value), float(t.value)
+
+    # -- fields ------------------------------------------------------------
+    def _shape(self):
+        return (self.grid["nz"], self.grid["ny"], self.grid["nx"])
+
+    def copy_field(self, name: str) -> np.ndarray:
+        out = np.empty(self._shape(), dtype=np.float64)
+        _check(lib().mithra_copy_field(self.h, FIELD_ID[name], _dp(out)), self.h)
+        return out
+
+    def set_field(self, name: str, values: np.ndarray):
+        a = np.ascontiguousarray(values, dtype=np.float64).reshape(-1)
+        assert a.size == int(np.prod(self._shape()))
+        _check(lib().mithra_set_field(self.h, FIELD_ID[name], _dp(a)), self.h)
+
+    def sample_fields(self, names, ijk) -> np.ndarray:
+        mask = 0
+        for nm in names:
+            mask |= 1 << FIELD_ID[nm]
+        pts = np.ascontiguousarray(ijk, dtype=np.int32).reshape(-1, 3)
+        m = bin(mask).count("1")
+        out = np.empty((pts.shape[0], m), dtype=np.float64)
+        _check(lib().mithra_sample_fields(self.h, mask, pts.ctypes.data_as(C.POINTER(C.c_int32)),
+                                          pts.shape[0], _dp(out)), self.h)
+        return out
+
+    def radiated_power(self, k_plane: int):
+        p, t, z = C.c_double(), C.c_double(), C.c_double()
+        _check(lib().mithra_radiated_power(self.h, int(k_plane), C.byref(p), C.byref(t),
+                                           C.byref(z)), self.h)
+        return float(p.value), float(t.value), float(z.value)
+
+    def set_power_sampling(self, k_plane: int, capacity: int):
+        _check(lib().mithra_set_power_sampling(self.h, int(k_plane), int(capacity)), self.h)
+
+    def read_power(self, max_records: int | None = None) -> np.ndarray:
+        cnt = C.c_int64()
+        _check(lib().mithra_read_power(self.h, None, 0, C.byref(cnt)), self.h)
+        m = int(cnt.value) if max_records is None else min(int(cnt.value), max_records)
+        out = np.zeros((max(m, 0), 3), dtype=np.float64)
+        if m > 0:
+            _check(lib().mithra_read_power(self.h, _dp(out), m, C.byref(cnt)), self.h)
+        return out
+
+    # -- particles ---------------------------------------------------------
+    def copy_particles(self) -> dict:
+        n = self.n_particles
+        arrs = {k: np.empty(n, dtype=np.float64) for k in ("x", "y", "z", "ux", "uy", "uz")}
+        lost = np.empty(n, dtype=np.int32)
+        nl = C.c_int64()
+        _check(lib().mithra_copy_particles(self.h, *[_dp(arrs[k]) for k in
+                                                     ("x", "y", "z", "ux", "uy", "uz")],
+                                           lost.ctypes.data_as(C.POINTER(C.c_int32)),
+                                           C.byref(nl)), self.h)
+        arrs["lost"] = lost
+        arrs["n_lost"] = int(nl.value)
+        return arrs
+
+    # -- kernel timing ---------------------------------------------------
+    def profile(self, enable: bool = True):
+        _check(lib().mithra_profile(self.h, 1 if enable else 0), self.h)
+
+    def kernel_times(self) -> dict:
+        ms = np.zeros(16)
+        n = np.zeros(16, dtype=np.int64)
+        nk = C.c_int32()
+        _check(lib().mithra_kernel_times(self.h, _dp(ms), n.ctypes.data_as(C.POINTER(C.c_int64)),
+                                         16, C.byref(nk)), self.h)
+        out = {}
+        for k in range(nk.value):
+            out[lib().mithra_kernel_name(k).decode()] = (float(ms[k]), int(n[k]))
+        return out
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().mithra_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

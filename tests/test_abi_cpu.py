@@ -1,0 +1,107 @@
+"""Host-side checks of the C ABI (no GPU): the library loads, exports every
+symbol include/mithra.h declares, and its host-only validation agrees with the
+stability conditions the oracle derives from the paper's dispersion
+relations."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1612_03310_gb300 import build_lib, inputs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def M():
+    build_lib.build()
+    from paper_1612_03310_gb300 import mithra
+    return mithra
+
+
+def declared_symbols():
+    txt = open(os.path.join(ROOT, "include", "mithra.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(mithra_[a-z_]+)\s*\(", txt)))
+
+
+def test_exports_every_declared_symbol(M):
+    names = declared_symbols()
+    assert len(names) >= 15
+    lib = C.CDLL(M.LIB_PATH)
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(M.EXPORTS) == names
+
+
+def test_version(M):
+    assert M.lib().mithra_version() >= 100
+
+
+@pytest.mark.parametrize("stencil", [0, 1])
+@pytest.mark.parametrize("courant", [0.5, 0.9, 0.99, 1.0, 1.01, 1.3])
+def test_stability_check_matches_oracle(M, orc, stencil, courant):
+    g = inputs.random_grid(0, 8, 8, 8, courant=courant, stencil=stencil, dz_over_dx=0.6)
+    _, unstable = orc.coefficients(g)
+    st = M.check_grid(dict(g, boundary=1))
+    assert (st == M.EUNSTABLE) == unstable
+    assert st in (M.OK, M.EUNSTABLE)
+
+
+def test_bad_grids_rejected(M):
+    g = inputs.random_grid(0, 8, 8, 8)
+    for bad in (dict(nx=3), dict(dx=0.0), dict(n_sub=0), dict(stencil=2), dict(boundary=2)):
+        assert M.check_grid({**g, "boundary": 1, **bad}) == M.EINVAL, bad
+        assert M.last_error()
+
+
+def test_footprint_scales(M):
+    g = inputs.workload("c2")["grid"]
+    b32 = M.footprint(g, 2 ** 21, M.P32)
+    b64 = M.footprint(g, 2 ** 21, M.P64)
+    ncell = 128 * 128 * 1024
+    assert b32 > 3 * ncell * 16
+    assert 1.6 < b64 / b32 < 2.0
+
+
+def test_create_without_gpu_fails_loudly(M):
+    pytest.importorskip("torch")
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    g = inputs.random_grid(0, 8, 8, 8)
+    with pytest.raises(M.MithraError) as e:
+        M.Simulation(dict(g, boundary=1), None, None)
+    assert e.value.status == M.ENODEV
+
+
+def test_binding_refuses_missing_library(monkeypatch):
+    from paper_1612_03310_gb300 import mithra
+    monkeypatch.setattr(mithra, "_lib", None)
+    monkeypatch.setattr(mithra, "LIB_PATH", "/nonexistent/libmithra.so")
+    with pytest.raises(mithra.MithraError):
+        mithra.lib()
+
+
+def test_workload_table_pinned():
+    # the rest-frame literals of the workload table against the closed forms
+    # of the Lorentz-boost section (gamma0 = gamma / sqrt(1 + K^2/2), the
+    # boosted mean momentum and spread) and the grid recipe (c dt = rest-frame
+    # period / steps per period, dz = c dt / 0.95)
+    c = 299792458.0
+    for name, gamma, spp in (("c1", 10.0, 32), ("c2", 100.0, 50), ("c3", 100.0, 100)):
+        w = inputs.WORKLOADS[name]
+        u, g, b = w["undulator"], w["grid"], w["bunch"]
+        g0 = gamma / np.sqrt(1 + u["K"] ** 2 / 2)
+        assert u["gamma0"] == pytest.approx(g0, rel=1e-13)
+        b0 = np.sqrt(1 - 1 / g0 ** 2)
+        beta = np.sqrt(1 - 1 / gamma ** 2)
+        gr = gamma * g0 * (1 - beta * b0)
+        assert b["uz_mean"] == pytest.approx(np.sqrt(gr * gr - 1), rel=1e-12)
+        assert b["uz_sigma"] == pytest.approx(gamma * 1e-4 * g0 * (1 - beta * b0), rel=1e-12)
+        cdt = u["lambda_u"] / g0 / spp
+        assert g["dt"] * c == pytest.approx(cdt, rel=1e-13)
+        assert g["dz"] == pytest.approx(cdt / 0.95, rel=1e-13)
+        assert b["kb"] == pytest.approx(g0 * 2 * np.pi / u["lambda_u"] * (1 + b0), rel=1e-12)

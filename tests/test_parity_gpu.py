@@ -1,0 +1,300 @@
+"""GPU parity: the CUDA path, called through the C ABI, against the FP64
+oracle on the same seeded inputs.
+
+Tolerances (relative L2 over a whole field, or per particle):
+  - P64: 1e-10 for one step, 1e-9 over the c1 workload (rounding order only);
+  - P32: the stated bound for FP32 state with FP64 bookkeeping, 1e-4 relative
+    L2 for every field after the configured steps and 1e-3 for the radiated
+    power; single steps are held to 1e-5.
+Index work (the cell of every particle, the lost flags, the per-tile counts)
+is compared exactly, except for particles within 1e-9 (P64) or 1e-5 (P32)
+cells of a cell face, where rounding order may decide either way.
+"""
+import numpy as np
+import pytest
+
+from paper_1612_03310_gb300 import build_lib, inputs
+
+pytestmark = pytest.mark.gpu
+
+FIELDS = ["Ex", "Ey", "Ez", "Bx", "By", "Bz", "Ax", "Ay", "Az", "phi", "Jx", "Jy", "Jz", "rho"]
+
+
+@pytest.fixture(scope="module")
+def M():
+    build_lib.build()
+    from paper_1612_03310_gb300 import mithra
+    try:
+        s = mithra.Simulation(dict(inputs.random_grid(0, 4, 4, 4), boundary=1), None, None)
+        s.close()
+    except mithra.MithraError as e:
+        if e.status == mithra.ENODEV:
+            pytest.skip("no GB300 device")
+        raise
+    return mithra
+
+
+def rel_l2(a, b):
+    nb = np.linalg.norm(b)
+    if nb == 0.0:
+        return float(np.linalg.norm(a))
+    return float(np.linalg.norm(a - b) / nb)
+
+
+def oracle_fields(o):
+    """Fields of an OracleSim in the library's naming and (nz, ny, nx) shape."""
+    g = o.g
+    shp = (g["nz"], g["ny"], g["nx"])
+    n = o.n_cell
+    out = {}
+    for a, nm in enumerate(("Ex", "Ey", "Ez")):
+        out[nm] = o.E[a * n:(a + 1) * n].reshape(shp)
+    for a, nm in enumerate(("Bx", "By", "Bz")):
+        out[nm] = o.B[a * n:(a + 1) * n].reshape(shp)
+    for a, nm in enumerate(("Ax", "Ay", "Az", "phi")):
+        out[nm] = o.cur[a * n:(a + 1) * n].reshape(shp)
+        out[nm + "_prev"] = o.prev[a * n:(a + 1) * n].reshape(shp)
+    for a, nm in enumerate(("Jx", "Jy", "Jz", "rho")):
+        out[nm] = o.src[a * n:(a + 1) * n].reshape(shp)
+    return out
+
+
+def set_state(sim, o, f):
+    """Same potentials and sources on both sides (f from inputs.random_fields)."""
+    n = o.n_cell
+    o.set_potentials(f["prev"], f["cur"])
+    o.set_sources(f["src"])
+    for a, nm in enumerate(("Ax", "Ay", "Az", "phi")):
+        sim.set_field(nm + "_prev", f["prev"][a * n:(a + 1) * n])
+        sim.set_field(nm, f["cur"][a * n:(a + 1) * n])
+    for a, nm in enumerate(("Jx", "Jy", "Jz", "rho")):
+        sim.set_field(nm, f["src"][a * n:(a + 1) * n])
+
+
+def as_f32(f):
+    return {k: v.astype(np.float32).astype(np.float64) for k, v in f.items()}
+
+
+def compare_fields(sim, o, tol, names=FIELDS, report=None):
+    ref = oracle_fields(o)
+    worst = {}
+    for nm in names:
+        got = sim.copy_field(nm)
+        e = rel_l2(got, ref[nm])
+        worst[nm] = e
+    if report is not None:
+        report.update(worst)
+    bad = {k: v for k, v in worst.items() if v > tol}
+    assert not bad, bad
+
+
+def compare_particles(sim, o, tol_cells, face_eps):
+    got = sim.copy_particles()
+    lost_o = o.lost.astype(bool)
+    lost_g = got["lost"].astype(bool)
+    assert np.array_equal(lost_o, lost_g)
+    assert got["n_lost"] == int(lost_o.sum())
+    keep = ~lost_o
+    g = o.g
+    for key, d, r0 in (("x", g["dx"], g["x0"]), ("y", g["dy"], g["y0"]), ("z", g["dz"], g["z0"])):
+        a = (got[key][keep] - r0) / d
+        b = (getattr(o, key)[keep] - r0) / d
+        assert np.abs(a - b).max() <= tol_cells, (key, np.abs(a - b).max())
+        near = np.abs(b - np.round(b)) < face_eps
+        ca, cb = np.floor(a), np.floor(b)
+        assert np.array_equal(ca[~near], cb[~near]), key
+    for key in ("ux", "uy", "uz"):
+        a = got[key][keep]
+        b = getattr(o, key)[keep]
+        scale = max(np.abs(b).max(), 1e-30)
+        assert np.abs(a - b).max() <= tol_cells * 10 * scale + 1e-12, key
+
+
+# ---------------------------------------------------------------------------
+# potential update and Mur boundaries (no particles)
+
+@pytest.mark.parametrize("prec", ["P64", "P32"])
+@pytest.mark.parametrize("shape", [(37, 29, 45), (4, 4, 4), (33, 9, 70), (5, 41, 6)])
+def test_vacuum_update_parity(M, orc, prec, shape):
+    nx, ny, nz = shape
+    g = inputs.random_grid(11, nx, ny, nz)
+    f = inputs.random_fields(12, g)
+    p = getattr(M, prec)
+    if p == M.P32:
+        f = as_f32(f)
+    o = orc.OracleSim(g, None, dict(x=[], y=[], z=[], ux=[], uy=[], uz=[]))
+    with M.Simulation(dict(g, boundary=1), None, None, precision=p) as sim:
+        set_state(sim, o, f)
+        for steps, tol in ((1, 1e-12 if p == M.P64 else 2e-6), (14, 1e-11 if p == M.P64 else 2e-5)):
+            o.step(steps)
+            sim.step(steps)
+            sim.sync()
+            compare_fields(sim, o, tol, names=["Ax", "Ay", "Az", "phi", "Ex", "Ey", "Ez",
+                                               "Bx", "By", "Bz"])
+            ref = oracle_fields(o)
+            for nm in ("Ax_prev", "phi_prev"):
+                assert rel_l2(sim.copy_field(nm), ref[nm]) <= tol
+
+
+# ---------------------------------------------------------------------------
+# one full PIC step from random fields and particles
+
+C1_UND = inputs.WORKLOADS["c1"]["undulator"]
+
+
+@pytest.mark.parametrize("prec", ["P64", "P32"])
+@pytest.mark.parametrize("n_sub", [1, 3])
+def test_pic_step_parity(M, orc, prec, n_sub):
+    g = inputs.random_grid(21, 36, 30, 40, n_sub=n_sub)
+    f = inputs.random_fields(22, g, scale=1e-9)
+    P = inputs.random_particles(23, g, 6000, u_scale=0.3)
+    und = dict(C1_UND, z_ent_lab=0.0)
+    p = getattr(M, prec)
+    if p == M.P32:
+        f = as_f32(f)
+    o = orc.OracleSim(g, und, P)
+    with M.Simulation(dict(g, boundary=1), und, P, precision=p) as sim:
+        # rho^{1/2} from the initial positions agrees before anything else
+        ref = oracle_fields(o)
+        assert rel_l2(sim.copy_field("rho"), ref["rho"]) <= (1e-13 if p == M.P64 else 1e-6)
+        set_state(sim, o, f)
+        tol_f = 1e-10 if p == M.P64 else 1e-5
+        tol_c = 1e-10 if p == M.P64 else 2e-5
+        for steps in (1, 2):
+            o.step(steps)
+            sim.step(steps)
+            sim.sync()
+            compare_fields(sim, o, tol_f)
+            compare_particles(sim, o, tol_c, 1e-9 if p == M.P64 else 1e-5)
+
+
+@pytest.mark.parametrize("prec", ["P64", "P32"])
+def test_lost_particles_flagged(M, orc, prec):
+    g = inputs.random_grid(31, 16, 16, 16)
+    # three particles heading out through x, y and z faces, one staying
+    P = dict(x=np.array([g["x0"] + 12.9 * g["dx"], g["x0"] + 7.5 * g["dx"],
+                         g["x0"] + 7.5 * g["dx"], g["x0"] + 7.5 * g["dx"]]),
+             y=np.array([g["y0"] + 7.5 * g["dy"], g["y0"] + 1.05 * g["dy"],
+                         g["y0"] + 7.5 * g["dy"], g["y0"] + 7.5 * g["dy"]]),
+             z=np.array([g["z0"] + 7.5 * g["dz"], g["z0"] + 7.5 * g["dz"],
+                         g["z0"] + 12.95 * g["dz"], g["z0"] + 7.5 * g["dz"]]),
+             ux=np.array([5.0, 0.0, 0.0, 0.0]), uy=np.array([0.0, -5.0, 0.0, 0.0]),
+             uz=np.array([0.0, 0.0, 5.0, 0.1]), q_macro=-1e-15)
+    o = orc.OracleSim(g, None, P)
+    with M.Simulation(dict(g, boundary=1), None, P, precision=getattr(M, prec)) as sim:
+        for _ in range(3):
+            o.step(1)
+            sim.step(1)
+        got = sim.copy_particles()
+        assert list(got["lost"]) == list(o.lost) == [1, 1, 1, 0]
+        assert got["n_lost"] == 3
+        compare_fields(sim, o, 1e-10 if prec == "P64" else 1e-5, names=["rho", "Jx", "Jz"])
+
+
+@pytest.mark.parametrize("prec", ["P64", "P32"])
+def test_initially_outside_particles_are_lost(M, orc, prec):
+    g = inputs.random_grid(41, 12, 12, 12)
+    P = inputs.random_particles(42, g, 100)
+    P["x"][:10] = g["x0"] + 0.5 * g["dx"]  # cell 0: outside the valid region
+    P["z"][10:20] = g["z0"] + 11.5 * g["dz"]  # beyond the last vertex
+    o = orc.OracleSim(g, None, P)
+    with M.Simulation(dict(g, boundary=1), None, P, precision=getattr(M, prec)) as sim:
+        got = sim.copy_particles()
+        assert got["n_lost"] == o.n_lost == 20
+        assert np.array_equal(got["lost"], o.lost)
+        o.step(2)
+        sim.step(2)
+        compare_particles(sim, o, 1e-10 if prec == "P64" else 2e-5, 1e-5)
+
+
+# ---------------------------------------------------------------------------
+# the c1 workload end to end (200 steps), power recorded every step
+
+@pytest.mark.parametrize("prec", ["P64", "P32"])
+def test_workload_c1(M, orc, prec):
+    w = inputs.workload("c1")
+    P = inputs.make_bunch(w["bunch_spec"], w["seed"])
+    g, und = w["grid"], w["undulator"]
+    kp = g["nz"] - 8
+    p = getattr(M, prec)
+    o = orc.OracleSim(g, und, P)
+    with M.Simulation(dict(g, boundary=1), und, P, precision=p) as sim:
+        sim.set_power_sampling(kp, w["steps"])
+        o.step(w["steps"], power_plane=kp)
+        sim.step(w["steps"])
+        sim.sync()
+        errs = {}
+        compare_fields(sim, o, 1e-9 if p == M.P64 else 1e-4, report=errs)
+        rec = sim.read_power()
+        assert rec.shape == (w["steps"], 3)
+        po = np.array([[s.p_lab, s.t_lab, s.z_lab] for s in o.power])
+        scale = np.abs(po[:, 0]).max()
+        assert scale > 0
+        assert np.abs(rec[:, 0] - po[:, 0]).max() <= (1e-9 if p == M.P64 else 1e-3) * scale
+        np.testing.assert_allclose(rec[:, 1:], po[:, 1:], rtol=1e-13)
+        compare_particles(sim, o, 1e-8 if p == M.P64 else 1e-3, 1e-9 if p == M.P64 else 1e-3)
+        # one-off power at the same plane equals the last record
+        p1, t1, z1 = sim.radiated_power(kp)
+        assert p1 == pytest.approx(rec[-1, 0], rel=1e-12, abs=1e-30)
+        assert t1 == pytest.approx(rec[-1, 1], rel=1e-14)
+
+
+@pytest.mark.parametrize("prec", ["P64", "P32"])
+def test_workload_c2_full_size(M, orc, prec):
+    # c2 at its full size (128x128x1024 cells, 2^21 particles) in the launch
+    # configuration the bench times, two whole steps, every field and particle
+    w = inputs.workload("c2")
+    P = inputs.make_bunch(w["bunch_spec"], w["seed"])
+    g, und = w["grid"], w["undulator"]
+    p = getattr(M, prec)
+    o = orc.OracleSim(g, und, P)
+    with M.Simulation(dict(g, boundary=1), und, P, precision=p) as sim:
+        ref = oracle_fields(o)
+        assert rel_l2(sim.copy_field("rho"), ref["rho"]) <= (1e-13 if p == M.P64 else 1e-6)
+        o.step(2)
+        sim.step(2)
+        sim.sync()
+        compare_fields(sim, o, 1e-10 if p == M.P64 else 1e-5)
+        compare_particles(sim, o, 1e-10 if p == M.P64 else 2e-5, 1e-9 if p == M.P64 else 1e-5)
+
+
+def test_sample_fields_match_copy(M):
+    g = inputs.random_grid(51, 20, 18, 22)
+    f = inputs.random_fields(52, g)
+    with M.Simulation(dict(g, boundary=1), None, None, precision=M.P64) as sim:
+        n = 20 * 18 * 22
+        for a, nm in enumerate(("Ax", "Ay", "Az", "phi")):
+            sim.set_field(nm + "_prev", f["prev"][a * n:(a + 1) * n])
+            sim.set_field(nm, f["cur"][a * n:(a + 1) * n])
+        sim.step(2)
+        rng = np.random.default_rng(0)
+        pts = np.stack([rng.integers(0, 20, 50), rng.integers(0, 18, 50),
+                        rng.integers(0, 22, 50)], axis=1)
+        names = ["Ex", "By", "Az", "rho", "phi"]
+        s = sim.sample_fields(names, pts)
+        for c, nm in enumerate(sorted(names, key=lambda x: M.FIELD_ID[x])):
+            full = sim.copy_field(nm)
+            np.testing.assert_array_equal(s[:, c], full[pts[:, 2], pts[:, 1], pts[:, 0]])
+
+
+def test_empty_bunch_and_time(M, orc):
+    g = inputs.random_grid(61, 10, 10, 10)
+    with M.Simulation(dict(g, boundary=1), C1_UND, None, precision=M.P64) as sim:
+        sim.step(5)
+        n, t = sim.time()
+        assert n == 5 and t == pytest.approx(5 * g["dt"])
+        assert np.abs(sim.copy_field("Ax")).max() == 0.0
+
+
+def test_torch_stream(M):
+    torch = pytest.importorskip("torch")
+    g = inputs.random_grid(71, 12, 12, 12)
+    P = inputs.random_particles(72, g, 500)
+    s = torch.cuda.Stream()
+    with M.Simulation(dict(g, boundary=1), C1_UND, P, precision=M.P32,
+                      stream=s.cuda_stream) as sim, \
+            M.Simulation(dict(g, boundary=1), C1_UND, P, precision=M.P32) as ref:
+        sim.step(3)
+        ref.step(3)
+        s.synchronize()
+        assert rel_l2(sim.copy_field("rho"), ref.copy_field("rho")) < 1e-5
