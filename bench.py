@@ -123,8 +123,9 @@ def algorithmic_bytes(kernel: str, grid: dict, n_particles: int, prec: str) -> f
     r = 4 if prec == "p32" else 8
     interior = (grid["nx"] - 2) * (grid["ny"] - 2) * (grid["nz"] - 2)
     if kernel == "potential_step":
-        # read psi^n, psi^{n-1}, sources; write psi^{n+1}; zero the sources
-        return interior * 5 * 4 * r
+        # read psi^n, the increment and the sources; write psi^{n+1}, the new
+        # increment and zeroed sources: 6 x 4 values per interior cell
+        return interior * 6 * 4 * r
     if kernel == "push":
         # read and write cell + 3 fractions + 3 momenta; write key and rank
         return n_particles * (2 * (4 + 6 * r) + 8)

@@ -54,10 +54,13 @@ typedef enum {
 } mithra_status;
 
 typedef enum {
-    MITHRA_P64 = 0, /* all state and arithmetic in FP64 */
-    MITHRA_P32 = 1  /* FP32 fields and particle phase space; FP64 frame clock,
-                       lab-frame phase of the undulator, particle gamma,
-                       positions' cell bookkeeping and power accumulation */
+    MITHRA_P64 = 0,     /* all state and arithmetic in FP64 */
+    MITHRA_P32 = 1,     /* FP32 fields and particle phase space; FP64 frame
+                           clock, lab-frame phase of the undulator, particle
+                           gamma, the cell carry of positions and the power
+                           accumulation */
+    MITHRA_P32_U64 = 2  /* as MITHRA_P32, but the particle momenta are stored
+                           and Boris-rotated in FP64 */
 } mithra_precision;
 
 /* Field identifiers; the paper's field names (Ex .. Bz, Ax .. Az, Jx .. Jz,
@@ -200,6 +203,15 @@ mithra_status mithra_profile(mithra_sim* sim, int32_t enable);
 mithra_status mithra_kernel_times(mithra_sim* sim, double* ms, int64_t* launches,
                                   int32_t max_kernels, int32_t* n_kernels);
 const char* mithra_kernel_name(int32_t kernel);
+
+/* Launch choices (the autotuner's knobs).  stencil_variant 0: the direct
+ * potential update, one thread per vertex with neighbours read through L1;
+ * 1: the z-marching form, psi^n planes of a 32 x 8 column tile streamed
+ * through shared memory by TMA box loads (the default when the driver
+ * provides tensor maps).  lz: planes per CTA of the marching form, 0 for the
+ * built-in choice.  Results do not depend on these choices beyond rounding. */
+mithra_status mithra_set_tuning(mithra_sim* sim, int32_t stencil_variant, int32_t lz);
+mithra_status mithra_get_tuning(const mithra_sim* sim, int32_t* stencil_variant, int32_t* lz);
 
 /* Host-only checks (no GPU needed). */
 

@@ -1,13 +1,14 @@
 // common.cuh -- shared device definitions of the GB300 FDTD/PIC step.
 //
 // Storage (both precisions T = float / double):
-//   potentials: two levels, each nx*ny*nz cells of V4<T> {A_x, A_y, A_z, phi},
-//               cell (i,j,k) at (k*ny + j)*nx + i (x fastest);
+//   potentials: two ping-pong levels, each nx*ny*nz cells of
+//               V4<T> {A_x, A_y, A_z, phi}, cell (i,j,k) at (k*ny + j)*nx + i
+//               (x fastest), and the increment D = newest - previous level;
 //   sources:    one array of V4<T> {J_x, J_y, J_z, rho};
 //   particles:  structure of arrays, double-buffered for the re-sort:
 //               int32 cell (linear cell index, -1 once lost), T fraction of
-//               the cell along x, y, z in [0, 1), T momentum u = gamma*beta,
-//               int32 original index.
+//               the cell along x, y, z in [0, 1), U momentum u = gamma*beta
+//               (U = T, or double with FP32 fields), int32 original index.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -74,16 +75,17 @@ struct StepState {
   int pad;
 };
 
-// Stencil coefficients (Eq. updateEquation, NSFD alpha' table) and Mur betas
+// Coefficients of the potential update in increment form (r_l = c dt / d_l,
+// A of Eq. NSFDCoefficient, zero for the standard scheme) and the Mur beta0
 // indexed by the mask of axes along which the boundary vertex lies outside
 // the interior (x = 1, y = 2, z = 4).
 template <typename T>
 struct StencilP {
   int nx, ny, nz;
   long long nxy;
-  T A, omA2, a1, a2, a4, a6;
-  T sA, sphi;      // (c dt)^2 mu0 and (c dt)^2 / eps0
-  T mb0[8], mb1[8];
+  T rxA, rxB, ryA, ryB, rz2;  // rx^2 A, rx^2 (1 - 2A), ry^2 A, ry^2 (1 - 2A), rz^2
+  T sA, sphi;                 // (c dt)^2 mu0 and (c dt)^2 / eps0
+  T mb0[8];
   int space_charge;
 };
 
@@ -95,7 +97,7 @@ struct PicP {
   double x0, y0, z0, dxd, dyd, dzd;
   T inv2dx, inv2dy, inv2dz, inv4dx, inv4dy, inv4dz, invdt;
   // Boris: h = qm dtb / (2c), an = qm dtb / 2
-  T h, an;
+  double h, an;
   double cdtb_dx, cdtb_dy, cdtb_dz;  // c dt_b / (dx, dy, dz)
   int n_sub;
   double t0, dt, dtb;
@@ -110,15 +112,16 @@ struct PicP {
   int ntx, nty, ntz, nkeys;
 };
 
-template <typename T>
+// T: type of the in-cell fractions; U: type of the momenta.
+template <typename T, typename U>
 struct Parts {
   int* cell;
   T* fx;
   T* fy;
   T* fz;
-  T* ux;
-  T* uy;
-  T* uz;
+  U* ux;
+  U* uy;
+  U* uz;
   int* id;
 };
 

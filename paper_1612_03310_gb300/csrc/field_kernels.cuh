@@ -1,112 +1,238 @@
 // field_kernels.cuh -- potential update (Eq. updateEquation) with the
 // first-order Mur boundary (Sec. "First Order ABCs") fused in, E/B at the
 // vertices (Sec. "Field Evaluation"), radiated power and field copy-out.
+//
+// Storage of the leapfrog: the newest level psi^{n+1} in one of two
+// ping-pong arrays and the increment D = psi^{n+1} - psi^n in place.  The
+// update equation is used in the algebraically equal increment form
+//   D^{n+1/2} = D^{n-1/2} + (c dt)^2 lap_h psi^n + (c dt)^2 S,
+//   psi^{n+1} = psi^n + D^{n+1/2},
+// with the NSFD Laplacian written as sums of neighbour differences:
+//   (c dt)^2 lap_h psi = rx^2 [A (DX_{k-1} + DX_{k+1}) + (1 - 2A) DX_k]
+//                      + ry^2 [A (DY_{k-1} + DY_{k+1}) + (1 - 2A) DY_k]
+//                      + rz^2 DZ,
+// DX_k = (psi_{i+1,k} - psi_{i,k}) + (psi_{i-1,k} - psi_{i,k}) and likewise
+// DY, DZ (r_l = c dt / d_l).  Expanding gives Eq. updateEquation's
+// coefficients alpha'_1 .. alpha'_7.  In FP32 the rounding then scales with
+// the increment rather than with the potential, so it no longer feeds the
+// scheme's double root at omega = 0.
 #pragma once
 #include "common.cuh"
+#include "tma.cuh"
 
 namespace mithra {
 
-// Potential update of one interior cell c, all four components at once.
-//   psi^{n+1} = -psi^{n-1} + a1 psi + a2 (bar_{i+1} + bar_{i-1})
-//             + a4 (bar_{j+1} + bar_{j-1}) + a6 (psi_{k+1} + psi_{k-1}) + S
-// with bar = A psi_{k-1} + (1 - 2A) psi_k + A psi_{k+1} (Eq. NSFDtrick) and
-// S = (c dt)^2 (mu0 J, rho / eps0).
 template <typename T>
-__device__ inline V4<T> stencil_cell(const StencilP<T>& p, const V4<T>* __restrict__ cur,
-                                     V4<T> pm, V4<T> s, long long c) {
-  const long long nxy = p.nxy;
-  const int nx = p.nx;
-  auto bar = [&](long long q) {
-    return p.A * (ldg4(cur + q - nxy) + ldg4(cur + q + nxy)) + p.omA2 * ldg4(cur + q);
-  };
-  V4<T> pc = ldg4(cur + c);
-  V4<T> v = p.a1 * pc - pm;
-  v = v + p.a2 * (bar(c + 1) + bar(c - 1));
-  v = v + p.a4 * (bar(c + nx) + bar(c - nx));
-  v = v + p.a6 * (ldg4(cur + c + nxy) + ldg4(cur + c - nxy));
-  v = v + v4(p.sA * s.x, p.sA * s.y, p.sA * s.z, p.sphi * s.w);
-  if (!p.space_charge) v.w = (T)0;
-  return v;
+__device__ inline T mur_beta0(const StencilP<T>& p, int mask) {
+  switch (mask) {
+    case 1: return p.mb0[1];
+    case 2: return p.mb0[2];
+    case 3: return p.mb0[3];
+    case 4: return p.mb0[4];
+    case 5: return p.mb0[5];
+    case 6: return p.mb0[6];
+    default: return p.mb0[7];
+  }
 }
 
 // Mur update of the boundary vertices whose nearest interior vertex is c
-// (i, j, k), using psi^{n+1}_c = pn and psi^{n-1}_c = pm before they are
-// overwritten, and zero the boundary vertex's source.  For a boundary vertex b:
+// (i, j, k).  With beta0 + beta1 = 1 the first-order condition
 //   xi_b^{n+1} = b0 (xi_b^{n-1} + xi_c^{n+1}) + b1 (xi_b^n + xi_c^n) - xi_c^{n-1}
-// with b0, b1 for the spacing d = |b - c| (face: the axis spacing; edge and
-// corner: the diagonal).
+// becomes, in increments,  D_b^+ = b0 (D_c^+ - D_b^-) + D_c^-,
+// b0 = (c dt - d)/(c dt + d) for d = |b - c| (face: the axis spacing; edge and
+// corner: the diagonal).  Also zeroes the boundary vertex's source.
 template <typename T>
 __device__ inline void mur_neighbours(const StencilP<T>& p, const V4<T>* __restrict__ cur,
-                                      V4<T>* __restrict__ nxt, V4<T>* __restrict__ src, int i,
-                                      int j, int k, long long c, V4<T> pn, V4<T> pm) {
+                                      V4<T>* __restrict__ nxt, V4<T>* __restrict__ D,
+                                      V4<T>* __restrict__ src, int i, int j, int k,
+                                      long long c, V4<T> dq_new, V4<T> dq_old) {
   const int lo_x = (i == 1) ? -1 : 0, hi_x = (i == p.nx - 2) ? 1 : 0;
   const int lo_y = (j == 1) ? -1 : 0, hi_y = (j == p.ny - 2) ? 1 : 0;
   const int lo_z = (k == 1) ? -1 : 0, hi_z = (k == p.nz - 2) ? 1 : 0;
   if (!(lo_x | hi_x | lo_y | hi_y | lo_z | hi_z)) return;
-  const V4<T> pcur = ldg4(cur + c);
   for (int dz = lo_z; dz <= hi_z; ++dz) {
     for (int dy = lo_y; dy <= hi_y; ++dy) {
       for (int dx = lo_x; dx <= hi_x; ++dx) {
         const int mask = (dx != 0) | ((dy != 0) << 1) | ((dz != 0) << 2);
         if (!mask) continue;
         const long long b = c + dx + (long long)dy * p.nx + (long long)dz * p.nxy;
-        const V4<T> pbm = nxt[b];           // xi_b^{n-1}
-        const V4<T> pb = ldg4(cur + b);     // xi_b^n
-        V4<T> r = p.mb0[mask] * (pbm + pn) + p.mb1[mask] * (pb + pcur) - pm;
-        if (!p.space_charge) r.w = (T)0;
-        nxt[b] = r;
+        const V4<T> db_old = D[b];
+        V4<T> db = mur_beta0(p, mask) * (dq_new - db_old) + dq_old;
+        if (!p.space_charge) db.w = (T)0;
+        D[b] = db;
+        nxt[b] = ldg4(cur + b) + db;
         src[b] = v4((T)0, (T)0, (T)0, (T)0);  // boundary sources are never used
       }
     }
   }
 }
 
-// One thread per vertex of the (x, y) plane, blocks marching nothing: the
-// straightforward form.  lev[prev] holds psi^{n-1} on entry and psi^{n+1} on
-// exit; the consumed sources are zeroed for the deposit of this step.
+// Source term (c dt)^2 (mu0 J, rho / eps0).
+template <typename T>
+__device__ inline V4<T> source_term(const StencilP<T>& p, V4<T> s) {
+  return v4(p.sA * s.x, p.sA * s.y, p.sA * s.z, p.sphi * s.w);
+}
+
+// Direct form: one thread per vertex, neighbours through L1.  cur holds
+// psi^n, nxt receives psi^{n+1}, D is advanced in place; the consumed
+// sources are zeroed for the deposit of this step.
 template <typename T>
 __global__ void __launch_bounds__(256) k_potential_step(StencilP<T> p,
                                                         const V4<T>* __restrict__ cur,
                                                         V4<T>* __restrict__ nxt,
+                                                        V4<T>* __restrict__ D,
                                                         V4<T>* __restrict__ src) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int k = blockIdx.z;
   if (i < 1 || i > p.nx - 2 || j < 1 || j > p.ny - 2 || k < 1 || k > p.nz - 2) return;
   const long long c = cidx(i, j, k, p.nx, p.nxy);
-  const V4<T> pm = nxt[c];
-  const V4<T> s = src[c];
-  const V4<T> pn = stencil_cell(p, cur, pm, s, c);
-  mur_neighbours(p, cur, nxt, src, i, j, k, c, pn, pm);
-  nxt[c] = pn;
+  const long long nxy = p.nxy;
+  const int nx = p.nx;
+  auto dsum = [&](long long q, long long off) {
+    const V4<T> m = ldg4(cur + q);
+    return (ldg4(cur + q + off) - m) + (ldg4(cur + q - off) - m);
+  };
+  const V4<T> pc = ldg4(cur + c);
+  V4<T> L = p.rxA * (dsum(c - nxy, 1) + dsum(c + nxy, 1)) + p.rxB * dsum(c, 1);
+  L = L + p.ryA * (dsum(c - nxy, nx) + dsum(c + nxy, nx)) + p.ryB * dsum(c, nx);
+  L = L + p.rz2 * ((ldg4(cur + c + nxy) - pc) + (ldg4(cur + c - nxy) - pc));
+  const V4<T> dm = D[c];
+  V4<T> dp = dm + (L + source_term(p, src[c]));
+  if (!p.space_charge) dp.w = (T)0;
+  mur_neighbours(p, cur, nxt, D, src, i, j, k, c, dp, dm);
+  D[c] = dp;
+  nxt[c] = pc + dp;
   src[c] = v4((T)0, (T)0, (T)0, (T)0);
 }
 
-// E and B at vertex v (interior) at t = (n+1/2) dt from level n (po) and
-// level n+1 (pn):  B = (curl A^n + curl A^{n+1}) / 2,
-// E = -(A^{n+1} - A^n) / dt - grad phi^n, central differences.
+// ---------------------------------------------------------------------------
+// Marching form of the same update.  A CTA owns a 32 x 8 column tile and a run
+// of lz planes; it walks up in z.  Each psi^n plane of the tile plus a
+// one-vertex halo arrives in shared memory by one TMA box load (4 stages in
+// flight, mbarrier-tracked); a thread keeps, for its column and the planes
+// k-1, k, k+1, the centre value and the x and y neighbour-difference sums in
+// registers, so every psi^n value is read from HBM about once.  D and the
+// sources of the thread's own column are read with 128-bit loads one plane
+// ahead.  The Mur vertices are written by the thread of the adjacent interior
+// vertex, as in the direct form.
+constexpr int kMX = 32, kMY = 8, kMStages = 4;
+
 template <typename T>
-__device__ inline void eb_vertex(const PicP<T>& p, const V4<T>* __restrict__ po,
-                                 const V4<T>* __restrict__ pn, long long v, T E[3], T B[3]) {
+__host__ __device__ constexpr int march_plane_bytes() {
+  return (((kMX + 2) * (kMY + 2) * (int)sizeof(V4<T>)) + 127) / 128 * 128;
+}
+template <typename T>
+__host__ __device__ constexpr int march_smem_bytes() {
+  return kMStages * march_plane_bytes<T>() + kMStages * 8;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kMX* kMY) k_potential_march(
+    const __grid_constant__ CUtensorMap tm_cur, StencilP<T> p, const V4<T>* __restrict__ cur,
+    V4<T>* __restrict__ nxt, V4<T>* __restrict__ D, V4<T>* __restrict__ src, int lz,
+    int* __restrict__ err) {
+  constexpr int HX = kMX + 2;
+  constexpr int PB = march_plane_bytes<T>();
+  constexpr uint32_t kBoxBytes = (kMX + 2) * (kMY + 2) * sizeof(V4<T>);
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kMStages * PB);
+  const int tx = threadIdx.x % kMX, ty = threadIdx.x / kMX;
+  const int i0 = blockIdx.x * kMX, j0 = blockIdx.y * kMY;
+  const int i = i0 + tx, j = j0 + ty;
+  const int kb = max((int)blockIdx.z * lz, 1);
+  const int ke = min((int)blockIdx.z * lz + lz, p.nz - 1);
+  if (kb >= ke) return;             // uniform over the block
+  const int nplanes = ke - kb + 2;  // psi^n planes kb-1 .. ke
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kMStages; ++s) mbar_init(&bar[s], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  auto issue = [&](int q) {
+    const int s = q % kMStages;
+    mbar_arrive_expect_tx(&bar[s], kBoxBytes);
+    tma_load_4d(smem + s * PB, &tm_cur, 0, i0 - 1, j0 - 1, kb - 1 + q, &bar[s]);
+  };
+  if (threadIdx.x == 0)
+    for (int q = 0; q < kMStages && q < nplanes; ++q) issue(q);
+
+  const bool active = i >= 1 && i <= p.nx - 2 && j >= 1 && j <= p.ny - 2;
+  const int h = (ty + 1) * HX + (tx + 1);
+  const V4<T> zero = v4((T)0, (T)0, (T)0, (T)0);
+  // reads plane q of the ring (centre, neighbour-difference sums), then frees
+  // its slot for the plane kMStages further up
+  auto take = [&](int q, V4<T>& c, V4<T>& X, V4<T>& Y) {
+    const int s = q % kMStages;
+    mbar_wait_bounded(&bar[s], (uint32_t)((q / kMStages) & 1), err);
+    const V4<T>* pl = reinterpret_cast<const V4<T>*>(smem + s * PB);
+    c = pl[h];
+    X = (pl[h + 1] - c) + (pl[h - 1] - c);
+    Y = (pl[h + HX] - c) + (pl[h - HX] - c);
+    __syncthreads();
+    if (threadIdx.x == 0 && q + kMStages < nplanes) {
+      fence_proxy_async_smem();
+      issue(q + kMStages);
+    }
+  };
+  V4<T> cm, Xm, Ym, c0, X0, Y0, cp, Xp, Yp;
+  take(0, cm, Xm, Ym);
+  take(1, c0, X0, Y0);
+  const long long col = (long long)j * p.nx + i;
+  V4<T> dm_next = zero, s_next = zero;
+  if (active) {
+    dm_next = D[(long long)kb * p.nxy + col];
+    s_next = src[(long long)kb * p.nxy + col];
+  }
+  for (int k = kb; k < ke; ++k) {
+    take(k - kb + 2, cp, Xp, Yp);
+    const V4<T> dm = dm_next, s = s_next;
+    if (active && k + 1 < ke) {
+      dm_next = D[(long long)(k + 1) * p.nxy + col];
+      s_next = src[(long long)(k + 1) * p.nxy + col];
+    }
+    if (active) {
+      V4<T> L = p.rxA * (Xm + Xp) + p.rxB * X0;
+      L = L + p.ryA * (Ym + Yp) + p.ryB * Y0;
+      L = L + p.rz2 * ((cp - c0) + (cm - c0));
+      V4<T> dp = dm + (L + source_term(p, s));
+      if (!p.space_charge) dp.w = (T)0;
+      const long long c = (long long)k * p.nxy + col;
+      mur_neighbours(p, cur, nxt, D, src, i, j, k, c, dp, dm);
+      D[c] = dp;
+      nxt[c] = c0 + dp;
+      src[c] = zero;
+    }
+    cm = c0; Xm = X0; Ym = Y0;
+    c0 = cp; X0 = Xp; Y0 = Yp;
+  }
+}
+
+// E and B at vertex v (interior) at t = (n+1/2) dt from psi^{n+1} (pn) and
+// the increment D = psi^{n+1} - psi^n:  B = (curl A^n + curl A^{n+1}) / 2 is
+// the curl of the mid level pn - D/2; E = -D_A / dt - grad phi^n with
+// phi^n = pn.w - D.w; central differences.
+template <typename T>
+__device__ inline void eb_vertex(const PicP<T>& p, const V4<T>* __restrict__ pn,
+                                 const V4<T>* __restrict__ D, long long v, T E[3], T B[3]) {
   const long long nxy = p.nxy;
   const int nx = p.nx;
-  const V4<T> o = ldg4(po + v), w = ldg4(pn + v);
-  const V4<T> xp = ldg4(po + v + 1) + ldg4(pn + v + 1);
-  const V4<T> xm = ldg4(po + v - 1) + ldg4(pn + v - 1);
-  const V4<T> yp = ldg4(po + v + nx) + ldg4(pn + v + nx);
-  const V4<T> ym = ldg4(po + v - nx) + ldg4(pn + v - nx);
-  const V4<T> zp = ldg4(po + v + nxy) + ldg4(pn + v + nxy);
-  const V4<T> zm = ldg4(po + v - nxy) + ldg4(pn + v - nxy);
-  B[0] = (yp.z - ym.z) * p.inv4dy - (zp.y - zm.y) * p.inv4dz;
-  B[1] = (zp.x - zm.x) * p.inv4dz - (xp.z - xm.z) * p.inv4dx;
-  B[2] = (xp.y - xm.y) * p.inv4dx - (yp.x - ym.x) * p.inv4dy;
-  // phi^n only: the level sums above include phi^{n+1}, so read phi^n apart
-  const T phxp = ldg4(po + v + 1).w, phxm = ldg4(po + v - 1).w;
-  const T phyp = ldg4(po + v + nx).w, phym = ldg4(po + v - nx).w;
-  const T phzp = ldg4(po + v + nxy).w, phzm = ldg4(po + v - nxy).w;
-  E[0] = -(w.x - o.x) * p.invdt - (phxp - phxm) * p.inv2dx;
-  E[1] = -(w.y - o.y) * p.invdt - (phyp - phym) * p.inv2dy;
-  E[2] = -(w.z - o.z) * p.invdt - (phzp - phzm) * p.inv2dz;
+  const T half = (T)0.5;
+  auto mid = [&](long long q) {
+    const V4<T> a = ldg4(pn + q), d = ldg4(D + q);
+    return v4(a.x - half * d.x, a.y - half * d.y, a.z - half * d.z, a.w - d.w);
+  };
+  // .w of mid() is phi^n
+  const V4<T> xp = mid(v + 1), xm = mid(v - 1);
+  const V4<T> yp = mid(v + nx), ym = mid(v - nx);
+  const V4<T> zp = mid(v + nxy), zm = mid(v - nxy);
+  const V4<T> dc = ldg4(D + v);
+  B[0] = (yp.z - ym.z) * p.inv2dy - (zp.y - zm.y) * p.inv2dz;
+  B[1] = (zp.x - zm.x) * p.inv2dz - (xp.z - xm.z) * p.inv2dx;
+  B[2] = (xp.y - xm.y) * p.inv2dx - (yp.x - ym.x) * p.inv2dy;
+  E[0] = -dc.x * p.invdt - (xp.w - xm.w) * p.inv2dx;
+  E[1] = -dc.y * p.invdt - (yp.w - ym.w) * p.inv2dy;
+  E[2] = -dc.z * p.invdt - (zp.w - zm.w) * p.inv2dz;
 }
 
 __device__ inline bool interior(int i, int j, int k, int nx, int ny, int nz) {
@@ -117,7 +243,7 @@ __device__ inline bool interior(int i, int j, int k, int nx, int ny, int nz) {
 // what: 0..2 E, 3..5 B, 6..9 component of lev (A_x, A_y, A_z, phi), 10..13
 // component of src.
 template <typename T>
-__global__ void k_extract(PicP<T> p, const V4<T>* __restrict__ po, const V4<T>* __restrict__ pn,
+__global__ void k_extract(PicP<T> p, const V4<T>* __restrict__ pn, const V4<T>* __restrict__ D,
                           const V4<T>* __restrict__ lev, const V4<T>* __restrict__ src, int what,
                           double* __restrict__ out) {
   const long long ncell = p.nxy * p.nz;
@@ -130,7 +256,7 @@ __global__ void k_extract(PicP<T> p, const V4<T>* __restrict__ po, const V4<T>* 
       const int k = (int)(c / p.nxy);
       if (interior(i, j, k, p.nx, p.ny, p.nz)) {
         T E[3], B[3];
-        eb_vertex(p, po, pn, c, E, B);
+        eb_vertex(p, pn, D, c, E, B);
         val = (double)(what < 3 ? E[what] : B[what - 3]);
       }
     } else {
@@ -155,9 +281,18 @@ __global__ void k_insert(long long ncell, const double* __restrict__ in, V4<T>* 
   }
 }
 
+// D = newest - previous level (after a level was set from the host).
+template <typename T>
+__global__ void k_increment(long long ncell, const V4<T>* __restrict__ pn,
+                            const V4<T>* __restrict__ po, V4<T>* __restrict__ D) {
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell;
+       c += (long long)gridDim.x * blockDim.x)
+    D[c] = pn[c] - po[c];
+}
+
 // Point samples: out[pt * m + s] for the s-th field of mask.
 template <typename T>
-__global__ void k_sample(PicP<T> p, const V4<T>* __restrict__ po, const V4<T>* __restrict__ pn,
+__global__ void k_sample(PicP<T> p, const V4<T>* __restrict__ pn, const V4<T>* __restrict__ D,
                          const V4<T>* __restrict__ src, const int* __restrict__ ijk, long long npts,
                          unsigned mask, int m, double* __restrict__ out) {
   const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -165,7 +300,7 @@ __global__ void k_sample(PicP<T> p, const V4<T>* __restrict__ po, const V4<T>* _
   const int i = ijk[3 * t], j = ijk[3 * t + 1], k = ijk[3 * t + 2];
   const long long c = cidx(i, j, k, p.nx, p.nxy);
   T E[3] = {0, 0, 0}, B[3] = {0, 0, 0};
-  if (interior(i, j, k, p.nx, p.ny, p.nz)) eb_vertex(p, po, pn, c, E, B);
+  if (interior(i, j, k, p.nx, p.ny, p.nz)) eb_vertex(p, pn, D, c, E, B);
   const V4<T> a = pn[c], s = src[c];
   const T vals[14] = {E[0], E[1], E[2], B[0], B[1], B[2], a.x, a.y, a.z, s.x, s.y, s.z, a.w, s.w};
   int slot = 0;
@@ -180,8 +315,8 @@ __global__ void k_sample(PicP<T> p, const V4<T>* __restrict__ po, const V4<T>* _
 // The result is added to *acc (zeroed by the caller); slot_from_state makes
 // the kernel write into acc[state->n] (per-step recording) when below cap.
 template <typename T>
-__global__ void __launch_bounds__(256) k_power(PicP<T> p, const V4<T>* __restrict__ po,
-                                               const V4<T>* __restrict__ pn, int kp, double g0,
+__global__ void __launch_bounds__(256) k_power(PicP<T> p, const V4<T>* __restrict__ pn,
+                                               const V4<T>* __restrict__ D, int kp, double g0,
                                                double b0, double* __restrict__ acc,
                                                const StepState* __restrict__ st, long long cap,
                                                int slot_from_state, int* __restrict__ err) {
@@ -196,7 +331,7 @@ __global__ void __launch_bounds__(256) k_power(PicP<T> p, const V4<T>* __restric
     const int i = 1 + t % (p.nx - 2);
     const int j = 1 + t / (p.nx - 2);
     T E[3], B[3];
-    eb_vertex(p, po, pn, cidx(i, j, kp, p.nx, p.nxy), E, B);
+    eb_vertex(p, pn, D, cidx(i, j, kp, p.nx, p.nxy), E, B);
     const double Ex = E[0], Ey = E[1], Bx = B[0], By = B[1];
     const double exl = g0 * (Ex + b0 * kC * By);
     const double eyl = g0 * (Ey - b0 * kC * Bx);

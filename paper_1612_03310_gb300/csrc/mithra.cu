@@ -9,6 +9,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "mithra.h"
@@ -31,7 +32,8 @@ struct mithra_sim {
   bool own_stream = false;
   int cur = 0;  // P[cur] holds the newest level
   int pb = 0;   // particle buffer in use
-  void* P[2] = {nullptr, nullptr};
+  void* P[2] = {nullptr, nullptr};  // psi ping-pong; P[cur] is the newest level
+  void* D = nullptr;                // increment newest - previous level
   void* S = nullptr;
   void* pbuf[2] = {nullptr, nullptr};
   int* key = nullptr;
@@ -50,6 +52,11 @@ struct mithra_sim {
   double t0 = 0.0;
   int* h_err = nullptr;  // pinned mirror of dstate->err
   std::string err;
+  // potential-update variant: 0 direct, 1 z-marching TMA tiles (needs tm)
+  int stencil_variant = 0;
+  int lz = 0;  // planes per CTA of the marching form
+  bool have_tm = false;
+  CUtensorMap tm[2];
   // per-kernel event timing
   bool profiling = false;
   struct Rec { int kernel; cudaEvent_t a, b; };
@@ -124,6 +131,19 @@ mithra_status cuda_fail(mithra_sim* s, cudaError_t e, const char* where) {
   } while (0)
 
 size_t real_size(int prec) { return prec == MITHRA_P64 ? sizeof(double) : sizeof(float); }
+size_t mom_size(int prec) { return prec == MITHRA_P32 ? sizeof(float) : sizeof(double); }
+
+// Calls f with null pointers whose pointee types are the field / fraction
+// type T and the momentum type U of the precision mode.
+template <typename F>
+mithra_status with_types(int prec, F&& f) {
+  if (prec == MITHRA_P64) return f((double*)nullptr, (double*)nullptr);
+  if (prec == MITHRA_P32_U64) return f((float*)nullptr, (double*)nullptr);
+  return f((float*)nullptr, (float*)nullptr);
+}
+#define TYPES_OF(t, u)                                   \
+  using T = std::remove_pointer_t<decltype(t)>;          \
+  using U = std::remove_pointer_t<decltype(u)>
 
 int64_t ncell_of(const mithra_grid* g) { return (int64_t)g->nx * g->ny * g->nz; }
 
@@ -135,7 +155,7 @@ void tiles_of(const mithra_grid* g, int* ntx, int* nty, int* ntz) {
 
 // bytes of one particle buffer: cell, 3 fractions, 3 momenta, id
 size_t particle_buffer_bytes(int64_t np, int prec) {
-  return (size_t)np * (2 * sizeof(int) + 6 * real_size(prec)) + 6 * 256;
+  return (size_t)np * (2 * sizeof(int) + 3 * real_size(prec) + 3 * mom_size(prec)) + 8 * 256;
 }
 
 mithra_status check_grid(const mithra_grid* g, std::string* why) {
@@ -174,12 +194,11 @@ StencilP<T> make_stencil(const mithra_grid& g) {
     const double qx = g.dz / g.dx, qy = g.dz / g.dy;
     A = 0.25 * (1.0 + 0.02 / (qx * qx + qy * qy));  // Eq. NSFDCoefficient
   }
-  p.A = (T)A;
-  p.omA2 = (T)(1.0 - 2.0 * A);
-  p.a1 = (T)(2.0 * (1.0 - (1.0 - 2.0 * A) * (rx2 + ry2) - rz2));
-  p.a2 = (T)rx2;
-  p.a4 = (T)ry2;
-  p.a6 = (T)(rz2 - 2.0 * A * (rx2 + ry2));
+  p.rxA = (T)(rx2 * A);
+  p.rxB = (T)(rx2 * (1.0 - 2.0 * A));
+  p.ryA = (T)(ry2 * A);
+  p.ryB = (T)(ry2 * (1.0 - 2.0 * A));
+  p.rz2 = (T)rz2;
   p.sA = (T)(cdt * cdt * kMu0);
   p.sphi = (T)(cdt * cdt / kEps0);
   for (int m = 0; m < 8; ++m) {
@@ -189,7 +208,6 @@ StencilP<T> make_stencil(const mithra_grid& g) {
     if (m & 4) d2 += g.dz * g.dz;
     const double d = std::sqrt(d2);
     p.mb0[m] = (T)((cdt - d) / (cdt + d));
-    p.mb1[m] = (T)(2.0 * d / (cdt + d));
   }
   p.space_charge = g.space_charge ? 1 : 0;
   return p;
@@ -209,8 +227,8 @@ PicP<T> make_pic(const mithra_sim* s) {
   p.invdt = (T)(1.0 / g.dt);
   const double qm = -kQe / kMe;  // electrons
   const double dtb = g.dt / g.n_sub;
-  p.h = (T)(qm * dtb / (2.0 * kC));
-  p.an = (T)(qm * dtb / 2.0);
+  p.h = qm * dtb / (2.0 * kC);
+  p.an = qm * dtb / 2.0;
   p.cdtb_dx = kC * dtb / g.dx; p.cdtb_dy = kC * dtb / g.dy; p.cdtb_dz = kC * dtb / g.dz;
   p.n_sub = g.n_sub;
   p.t0 = s->t0; p.dt = g.dt; p.dtb = dtb;
@@ -237,9 +255,9 @@ PicP<T> make_pic(const mithra_sim* s) {
   return p;
 }
 
-template <typename T>
-Parts<T> parts_of(mithra_sim* s, int b) {
-  Parts<T> P{};
+template <typename T, typename U>
+Parts<T, U> parts_of(mithra_sim* s, int b) {
+  Parts<T, U> P{};
   char* base = static_cast<char*>(s->pbuf[b]);
   auto carve = [&](size_t bytes) {
     char* r = base;
@@ -251,11 +269,21 @@ Parts<T> parts_of(mithra_sim* s, int b) {
   P.fx = reinterpret_cast<T*>(carve(n * sizeof(T)));
   P.fy = reinterpret_cast<T*>(carve(n * sizeof(T)));
   P.fz = reinterpret_cast<T*>(carve(n * sizeof(T)));
-  P.ux = reinterpret_cast<T*>(carve(n * sizeof(T)));
-  P.uy = reinterpret_cast<T*>(carve(n * sizeof(T)));
-  P.uz = reinterpret_cast<T*>(carve(n * sizeof(T)));
+  P.ux = reinterpret_cast<U*>(carve(n * sizeof(U)));
+  P.uy = reinterpret_cast<U*>(carve(n * sizeof(U)));
+  P.uz = reinterpret_cast<U*>(carve(n * sizeof(U)));
   P.id = reinterpret_cast<int*>(carve(n * sizeof(int)));
   return P;
+}
+
+// Planes per CTA of the marching update: about one wave of 8 CTAs per SM on
+// 152 SMs, at least 8 planes.
+int default_lz(const mithra_grid* g) {
+  const long long tiles = (long long)((g->nx + kMX - 1) / kMX) * ((g->ny + kMY - 1) / kMY);
+  long long lz = (g->nz * tiles + 1215) / 1216;
+  if (lz < 8) lz = 8;
+  if (lz > g->nz) lz = g->nz;
+  return (int)lz;
 }
 
 unsigned blocks_for(long long n, int threads) {
@@ -263,31 +291,39 @@ unsigned blocks_for(long long n, int threads) {
   return (unsigned)(b < 1 ? 1 : b);
 }
 
-template <typename T>
+template <typename T, typename U>
 mithra_status launch_step(mithra_sim* s) {
   const StencilP<T> sp = make_stencil<T>(s->g);
   const PicP<T> pp = make_pic<T>(s);
-  V4<T>* P0 = static_cast<V4<T>*>(s->P[s->cur]);       // level n
-  V4<T>* P1 = static_cast<V4<T>*>(s->P[1 - s->cur]);   // level n-1 -> n+1
+  V4<T>* P0 = static_cast<V4<T>*>(s->P[s->cur]);       // psi^n
+  V4<T>* P1 = static_cast<V4<T>*>(s->P[1 - s->cur]);   // receives psi^{n+1}
+  V4<T>* Dn = static_cast<V4<T>*>(s->D);               // D^{n-1/2} -> D^{n+1/2}
   V4<T>* S = static_cast<V4<T>*>(s->S);
-  dim3 blk(32, 8, 1);
-  dim3 grd((s->g.nx + 31) / 32, (s->g.ny + 7) / 8, s->g.nz);
   {
     ProfScope ps(s, K_POTENTIAL);
-    k_potential_step<T><<<grd, blk, 0, s->stream>>>(sp, P0, P1, S);
+    if (s->stencil_variant == 1 && s->have_tm) {
+      dim3 grd((s->g.nx + kMX - 1) / kMX, (s->g.ny + kMY - 1) / kMY,
+               (s->g.nz + s->lz - 1) / s->lz);
+      k_potential_march<T><<<grd, kMX * kMY, march_smem_bytes<T>(), s->stream>>>(
+          s->tm[s->cur], sp, P0, P1, Dn, S, s->lz, &s->dstate->err);
+    } else {
+      dim3 blk(32, 8, 1);
+      dim3 grd((s->g.nx + 31) / 32, (s->g.ny + 7) / 8, s->g.nz);
+      k_potential_step<T><<<grd, blk, 0, s->stream>>>(sp, P0, P1, Dn, S);
+    }
   }
   if (s->power_cap > 0) {
     ProfScope ps(s, K_POWER);
-    k_power<T><<<64, 256, 0, s->stream>>>(pp, P0, P1, s->power_plane, s->u.gamma0,
+    k_power<T><<<64, 256, 0, s->stream>>>(pp, P1, Dn, s->power_plane, s->u.gamma0,
                                           std::sqrt(1.0 - 1.0 / (s->u.gamma0 * s->u.gamma0)),
                                           s->d_power_rec - s->power_first, s->dstate,
                                           s->power_first + s->power_cap, 1, &s->dstate->err);
   }
   if (s->np > 0) {
-    Parts<T> A = parts_of<T>(s, s->pb), B = parts_of<T>(s, 1 - s->pb);
+    Parts<T, U> A = parts_of<T, U>(s, s->pb), B = parts_of<T, U>(s, 1 - s->pb);
     {
       ProfScope ps(s, K_PUSH);
-      k_push<T><<<blocks_for(s->np, 256), 256, 0, s->stream>>>(pp, s->dstate, P0, P1, S, A,
+      k_push<T, U><<<blocks_for(s->np, 256), 256, 0, s->stream>>>(pp, s->dstate, P1, Dn, S, A,
                                                                s->np, s->count, s->key, s->rank,
                                                                &s->dstate->n_lost);
     }
@@ -297,8 +333,8 @@ mithra_status launch_step(mithra_sim* s) {
     }
     {
       ProfScope ps(s, K_SCATTER);
-      k_scatter<T><<<blocks_for(s->np, 256), 256, 0, s->stream>>>(A, B, s->np, s->key, s->rank,
-                                                                  s->offset);
+      k_scatter<T, U><<<blocks_for(s->np, 256), 256, 0, s->stream>>>(A, B, s->np, s->key,
+                                                                     s->rank, s->offset);
     }
     s->pb = 1 - s->pb;
   } else {
@@ -310,7 +346,7 @@ mithra_status launch_step(mithra_sim* s) {
   return MITHRA_OK;
 }
 
-template <typename T>
+template <typename T, typename U>
 mithra_status init_particles(mithra_sim* s, const mithra_bunch* b) {
   const PicP<T> pp = make_pic<T>(s);
   const int64_t n = s->np;
@@ -320,15 +356,15 @@ mithra_status init_particles(mithra_sim* s, const mithra_bunch* b) {
   for (int a = 0; a < 6; ++a)
     MCHECK(s, cudaMemcpyAsync(d + a * n, src[a], sizeof(double) * n, cudaMemcpyHostToDevice,
                               s->stream));
-  Parts<T> A = parts_of<T>(s, 0), B = parts_of<T>(s, 1);
+  Parts<T, U> A = parts_of<T, U>(s, 0), B = parts_of<T, U>(s, 1);
   long long* lost = &s->dstate->n_lost;
-  k_init_particles<T><<<blocks_for(n, 256), 256, 0, s->stream>>>(
+  k_init_particles<T, U><<<blocks_for(n, 256), 256, 0, s->stream>>>(
       pp, n, d, d + n, d + 2 * n, d + 3 * n, d + 4 * n, d + 5 * n, A, s->count, s->key, s->rank,
       lost);
   k_scan_counts<<<1, 1024, 0, s->stream>>>(s->count, s->offset, s->nkeys + 1, s->dstate, 0);
-  k_scatter<T><<<blocks_for(n, 256), 256, 0, s->stream>>>(A, B, n, s->key, s->rank, s->offset);
+  k_scatter<T, U><<<blocks_for(n, 256), 256, 0, s->stream>>>(A, B, n, s->key, s->rank, s->offset);
   s->pb = 1;
-  k_deposit_rho<T><<<blocks_for(n, 256), 256, 0, s->stream>>>(pp, B, n,
+  k_deposit_rho<T, U><<<blocks_for(n, 256), 256, 0, s->stream>>>(pp, B, n,
                                                               static_cast<V4<T>*>(s->S));
   MCHECK(s, cudaGetLastError());
   MCHECK(s, cudaStreamSynchronize(s->stream));
@@ -354,6 +390,7 @@ mithra_status copy_field_impl(mithra_sim* s, int what, double* out) {
   MCHECK(s, cudaMalloc(&d, sizeof(double) * n));
   const V4<T>* Pn = static_cast<const V4<T>*>(s->P[s->cur]);
   const V4<T>* Po = static_cast<const V4<T>*>(s->P[1 - s->cur]);
+  const V4<T>* Dn = static_cast<const V4<T>*>(s->D);
   const V4<T>* lev = Pn;
   int code = 0;
   if (what <= MITHRA_BZ) code = what;
@@ -362,7 +399,7 @@ mithra_status copy_field_impl(mithra_sim* s, int what, double* out) {
   else if (what == MITHRA_PHI) code = 9;
   else if (what == MITHRA_RHO) code = 13;
   else { lev = Po; code = 6 + (what - MITHRA_AX_PREV); }
-  k_extract<T><<<1024, 256, 0, s->stream>>>(pp, Po, Pn, lev, static_cast<const V4<T>*>(s->S),
+  k_extract<T><<<1024, 256, 0, s->stream>>>(pp, Pn, Dn, lev, static_cast<const V4<T>*>(s->S),
                                             code, d);
   MCHECK(s, cudaGetLastError());
   MCHECK(s, cudaMemcpyAsync(out, d, sizeof(double) * n, cudaMemcpyDeviceToHost, s->stream));
@@ -386,6 +423,10 @@ mithra_status set_field_impl(mithra_sim* s, int what, const double* in) {
   MCHECK(s, cudaMalloc(&d, sizeof(double) * n));
   MCHECK(s, cudaMemcpyAsync(d, in, sizeof(double) * n, cudaMemcpyHostToDevice, s->stream));
   k_insert<T><<<1024, 256, 0, s->stream>>>(n, d, dst, comp);
+  if (dst != static_cast<V4<T>*>(s->S))
+    k_increment<T><<<1024, 256, 0, s->stream>>>(n, static_cast<const V4<T>*>(s->P[s->cur]),
+                                                static_cast<const V4<T>*>(s->P[1 - s->cur]),
+                                                static_cast<V4<T>*>(s->D));
   MCHECK(s, cudaGetLastError());
   mithra_status st = sync_status(s);
   cudaFree(d);
@@ -403,7 +444,7 @@ mithra_status sample_impl(mithra_sim* s, uint32_t mask, const int32_t* ijk, int6
   MCHECK(s, cudaMalloc(&dout, sizeof(double) * m * npts));
   MCHECK(s, cudaMemcpyAsync(dijk, ijk, sizeof(int) * 3 * npts, cudaMemcpyHostToDevice, s->stream));
   k_sample<T><<<blocks_for(npts, 128), 128, 0, s->stream>>>(
-      pp, static_cast<const V4<T>*>(s->P[1 - s->cur]), static_cast<const V4<T>*>(s->P[s->cur]),
+      pp, static_cast<const V4<T>*>(s->P[s->cur]), static_cast<const V4<T>*>(s->D),
       static_cast<const V4<T>*>(s->S), dijk, npts, mask, m, dout);
   MCHECK(s, cudaGetLastError());
   MCHECK(s, cudaMemcpyAsync(out, dout, sizeof(double) * m * npts, cudaMemcpyDeviceToHost,
@@ -419,8 +460,8 @@ mithra_status power_impl(mithra_sim* s, int kp, double* p) {
   const PicP<T> pp = make_pic<T>(s);
   MCHECK(s, cudaMemsetAsync(s->d_scalar, 0, sizeof(double), s->stream));
   const double g0 = s->u.gamma0;
-  k_power<T><<<64, 256, 0, s->stream>>>(pp, static_cast<const V4<T>*>(s->P[1 - s->cur]),
-                                        static_cast<const V4<T>*>(s->P[s->cur]), kp, g0,
+  k_power<T><<<64, 256, 0, s->stream>>>(pp, static_cast<const V4<T>*>(s->P[s->cur]),
+                                        static_cast<const V4<T>*>(s->D), kp, g0,
                                         std::sqrt(1.0 - 1.0 / (g0 * g0)), s->d_scalar, s->dstate,
                                         0, 0, &s->dstate->err);
   MCHECK(s, cudaGetLastError());
@@ -428,13 +469,13 @@ mithra_status power_impl(mithra_sim* s, int kp, double* p) {
   return sync_status(s);
 }
 
-template <typename T>
+template <typename T, typename U>
 mithra_status copy_particles_impl(mithra_sim* s, double* out7) {
   const PicP<T> pp = make_pic<T>(s);
   double* d = nullptr;
   MCHECK(s, cudaMalloc(&d, sizeof(double) * 7 * (size_t)s->np));
-  k_copy_out<T><<<blocks_for(s->np, 256), 256, 0, s->stream>>>(pp, parts_of<T>(s, s->pb),
-                                                               s->np, d);
+  k_copy_out<T, U><<<blocks_for(s->np, 256), 256, 0, s->stream>>>(pp, parts_of<T, U>(s, s->pb),
+                                                                  s->np, d);
   MCHECK(s, cudaGetLastError());
   MCHECK(s, cudaMemcpyAsync(out7, d, sizeof(double) * 7 * (size_t)s->np, cudaMemcpyDeviceToHost,
                             s->stream));
@@ -453,7 +494,7 @@ void lab_of(const mithra_sim* s, int32_t kp, double t, double* t_lab, double* z_
 
 void free_all(mithra_sim* s) {
   if (s->stream) cudaStreamSynchronize(s->stream);
-  void* ptrs[] = {s->P[0], s->P[1], s->S, s->pbuf[0], s->pbuf[1], s->key, s->rank, s->count,
+  void* ptrs[] = {s->P[0], s->P[1], s->D, s->S, s->pbuf[0], s->pbuf[1], s->key, s->rank, s->count,
                   s->offset, s->dstate, s->d_scalar, s->d_power_rec};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -493,7 +534,7 @@ mithra_status mithra_footprint(const mithra_grid* grid, int64_t n_particles,
   tiles_of(grid, &ntx, &nty, &ntz);
   const int64_t nkeys = (int64_t)ntx * nty * ntz;
   const size_t r = real_size(precision);
-  int64_t b = 3 * ncell_of(grid) * 4 * (int64_t)r;              // 2 levels + sources
+  int64_t b = 4 * ncell_of(grid) * 4 * (int64_t)r;              // 2 levels, increment, sources
   b += 2 * (int64_t)particle_buffer_bytes(n_particles, precision);
   b += 2 * n_particles * (int64_t)sizeof(int);                   // key, rank
   b += 2 * (nkeys + 2) * (int64_t)sizeof(int);                   // count, offset
@@ -513,8 +554,8 @@ mithra_status mithra_create(const mithra_grid* grid, const mithra_undulator* und
   if (!und) return fail(nullptr, MITHRA_EINVAL, "undulator is NULL");
   if (!(und->gamma0 > 1.0) || !(und->lambda_u > 0.0))
     return fail(nullptr, MITHRA_EINVAL, "undulator needs gamma0 > 1 and lambda_u > 0");
-  if (precision != MITHRA_P32 && precision != MITHRA_P64)
-    return fail(nullptr, MITHRA_EINVAL, "precision must be MITHRA_P32 or MITHRA_P64");
+  if (precision != MITHRA_P32 && precision != MITHRA_P64 && precision != MITHRA_P32_U64)
+    return fail(nullptr, MITHRA_EINVAL, "precision must be MITHRA_P64, MITHRA_P32 or MITHRA_P32_U64");
   const int64_t np = bunch ? bunch->n : 0;
   if (np < 0 || np >= ((int64_t)1 << 31)) return fail(nullptr, MITHRA_EINVAL, "bad particle count");
   if (np > 0 && (!bunch->x || !bunch->y || !bunch->z || !bunch->ux || !bunch->uy || !bunch->uz))
@@ -553,7 +594,7 @@ mithra_status mithra_create(const mithra_grid* grid, const mithra_undulator* und
   const size_t field_bytes = (size_t)ncell_of(grid) * 4 * r;
   auto dalloc = [&](void** p, size_t bytes) { return cudaMalloc(p, bytes < 256 ? 256 : bytes) == cudaSuccess; };
   bool ok = dalloc(&s->P[0], field_bytes) && dalloc(&s->P[1], field_bytes) &&
-            dalloc(&s->S, field_bytes) &&
+            dalloc(&s->D, field_bytes) && dalloc(&s->S, field_bytes) &&
             dalloc(&s->pbuf[0], particle_buffer_bytes(np, precision)) &&
             dalloc(&s->pbuf[1], particle_buffer_bytes(np, precision)) &&
             dalloc((void**)&s->key, sizeof(int) * (size_t)(np + 1)) &&
@@ -568,11 +609,24 @@ mithra_status mithra_create(const mithra_grid* grid, const mithra_undulator* und
   *s->h_err = 0;
   cudaMemsetAsync(s->P[0], 0, field_bytes, s->stream);
   cudaMemsetAsync(s->P[1], 0, field_bytes, s->stream);
+  cudaMemsetAsync(s->D, 0, field_bytes, s->stream);
   cudaMemsetAsync(s->S, 0, field_bytes, s->stream);
   cudaMemsetAsync(s->count, 0, sizeof(int) * (size_t)(s->nkeys + 2), s->stream);
   cudaMemsetAsync(s->dstate, 0, sizeof(StepState), s->stream);
+  {
+    const int es = (int)r;
+    s->have_tm = encode_field_map(&s->tm[0], s->P[0], es, grid->nx, grid->ny, grid->nz,
+                                  kMX + 2, kMY + 2) &&
+                 encode_field_map(&s->tm[1], s->P[1], es, grid->nx, grid->ny, grid->nz,
+                                  kMX + 2, kMY + 2);
+    s->stencil_variant = s->have_tm ? 1 : 0;
+    s->lz = default_lz(grid);
+  }
   if (np > 0) {
-    st = (precision == MITHRA_P64) ? init_particles<double>(s, bunch) : init_particles<float>(s, bunch);
+    st = with_types(precision, [&](auto t, auto u) {
+      TYPES_OF(t, u);
+      return init_particles<T, U>(s, bunch);
+    });
     if (st != MITHRA_OK) {
       std::string msg = s->err;
       return bail(st, msg);
@@ -588,7 +642,10 @@ mithra_status mithra_step(mithra_sim* s, int64_t n) {
   if (n < 0) return fail(s, MITHRA_EINVAL, "n must be >= 0");
   if (*s->h_err & 1) return fail(s, MITHRA_ENUMERIC, "NaN or Inf in a power reduction");
   for (int64_t t = 0; t < n; ++t) {
-    mithra_status st = (s->prec == MITHRA_P64) ? launch_step<double>(s) : launch_step<float>(s);
+    mithra_status st = with_types(s->prec, [&](auto t, auto u) {
+      TYPES_OF(t, u);
+      return launch_step<T, U>(s);
+    });
     if (st != MITHRA_OK) return st;
     s->n_issued += 1;
   }
@@ -701,8 +758,10 @@ mithra_status mithra_copy_particles(mithra_sim* s, double* x, double* y, double*
   if (!s) return fail(nullptr, MITHRA_EINVAL, "sim is NULL");
   if (s->np > 0 && (x || y || z || ux || uy || uz || lost)) {
     std::vector<double> buf((size_t)s->np * 7);
-    mithra_status st = s->prec == MITHRA_P64 ? copy_particles_impl<double>(s, buf.data())
-                                             : copy_particles_impl<float>(s, buf.data());
+    mithra_status st = with_types(s->prec, [&](auto t, auto u) {
+      TYPES_OF(t, u);
+      return copy_particles_impl<T, U>(s, buf.data());
+    });
     if (st != MITHRA_OK) return st;
     double* dst[6] = {x, y, z, ux, uy, uz};
     for (int a = 0; a < 6; ++a)
@@ -743,6 +802,24 @@ mithra_status mithra_kernel_times(mithra_sim* s, double* ms, int64_t* launches,
 
 const char* mithra_kernel_name(int32_t kernel) {
   return (kernel >= 0 && kernel < K_COUNT) ? kKernelNames[kernel] : nullptr;
+}
+
+mithra_status mithra_set_tuning(mithra_sim* s, int32_t stencil_variant, int32_t lz) {
+  if (!s) return fail(nullptr, MITHRA_EINVAL, "sim is NULL");
+  if (stencil_variant < 0 || stencil_variant > 1 || lz < 0)
+    return fail(s, MITHRA_EINVAL, "stencil_variant must be 0 or 1 and lz >= 0");
+  if (stencil_variant == 1 && !s->have_tm)
+    return fail(s, MITHRA_EINVAL, "TMA tensor maps unavailable: marching variant disabled");
+  s->stencil_variant = stencil_variant;
+  s->lz = lz > 0 ? lz : default_lz(&s->g);
+  return MITHRA_OK;
+}
+
+mithra_status mithra_get_tuning(const mithra_sim* s, int32_t* stencil_variant, int32_t* lz) {
+  if (!s) return fail(nullptr, MITHRA_EINVAL, "sim is NULL");
+  if (stencil_variant) *stencil_variant = s->stencil_variant;
+  if (lz) *lz = s->lz;
+  return MITHRA_OK;
 }
 
 mithra_status mithra_destroy(mithra_sim* s) {

@@ -55,8 +55,8 @@ __device__ inline void undulator_field(const PicP<T>& p, T y, double zabs, doubl
 // particle in cell (i, j, k) with fractions f, evaluating E, B at the eight
 // vertices from the potentials.
 template <typename T>
-__device__ inline void gather_eb(const PicP<T>& p, const V4<T>* __restrict__ po,
-                                 const V4<T>* __restrict__ pn, int i, int j, int k, T fx, T fy,
+__device__ inline void gather_eb(const PicP<T>& p, const V4<T>* __restrict__ pn,
+                                 const V4<T>* __restrict__ D, int i, int j, int k, T fx, T fy,
                                  T fz, T E[3], T B[3]) {
   E[0] = E[1] = E[2] = B[0] = B[1] = B[2] = (T)0;
   const T wx[2] = {(T)1 - fx, fx}, wy[2] = {(T)1 - fy, fy}, wz[2] = {(T)1 - fz, fz};
@@ -67,7 +67,7 @@ __device__ inline void gather_eb(const PicP<T>& p, const V4<T>* __restrict__ po,
 #pragma unroll
       for (int I = 0; I < 2; ++I) {
         T e[3], b[3];
-        eb_vertex(p, po, pn, cidx(i + I, j + J, k + K, p.nx, p.nxy), e, b);
+        eb_vertex(p, pn, D, cidx(i + I, j + J, k + K, p.nx, p.nxy), e, b);
         const T w = wx[I] * wy[J] * wz[K];
         E[0] += w * e[0]; E[1] += w * e[1]; E[2] += w * e[2];
         B[0] += w * b[0]; B[1] += w * b[1]; B[2] += w * b[2];
@@ -75,23 +75,27 @@ __device__ inline void gather_eb(const PicP<T>& p, const V4<T>* __restrict__ po,
 }
 
 // Boris rotation and kicks (Eq. BorisScheme) for charge-to-mass qm folded
-// into h = qm dtb / (2c) and an = qm dtb / 2; gamma of t1 in FP64.
-template <typename T>
-__device__ inline void boris(const PicP<T>& p, T u[3], const T E[3], const T B[3]) {
-  const T t1x = u[0] + p.h * E[0], t1y = u[1] + p.h * E[1], t1z = u[2] + p.h * E[2];
+// into h = qm dtb / (2c) and an = qm dtb / 2, in the momentum type U; gamma
+// of t1 in FP64.
+template <typename T, typename U>
+__device__ inline void boris(const PicP<T>& p, U u[3], const T Ef[3], const T Bf[3]) {
+  const U h = (U)p.h;
+  const U E[3] = {(U)Ef[0], (U)Ef[1], (U)Ef[2]};
+  const U B[3] = {(U)Bf[0], (U)Bf[1], (U)Bf[2]};
+  const U t1x = u[0] + h * E[0], t1y = u[1] + h * E[1], t1z = u[2] + h * E[2];
   const double g1 = sqrt(1.0 + (double)t1x * t1x + (double)t1y * t1y + (double)t1z * t1z);
-  const T al = (T)((double)p.an / g1);
-  const T t2x = t1x + al * (t1y * B[2] - t1z * B[1]);
-  const T t2y = t1y + al * (t1z * B[0] - t1x * B[2]);
-  const T t2z = t1z + al * (t1x * B[1] - t1y * B[0]);
-  const T f = (T)2 * al / ((T)1 + al * al * (B[0] * B[0] + B[1] * B[1] + B[2] * B[2]));
-  const T sx = f * B[0], sy = f * B[1], sz = f * B[2];
-  const T t3x = t1x + (t2y * sz - t2z * sy);
-  const T t3y = t1y + (t2z * sx - t2x * sz);
-  const T t3z = t1z + (t2x * sy - t2y * sx);
-  u[0] = t3x + p.h * E[0];
-  u[1] = t3y + p.h * E[1];
-  u[2] = t3z + p.h * E[2];
+  const U al = (U)(p.an / g1);
+  const U t2x = t1x + al * (t1y * B[2] - t1z * B[1]);
+  const U t2y = t1y + al * (t1z * B[0] - t1x * B[2]);
+  const U t2z = t1z + al * (t1x * B[1] - t1y * B[0]);
+  const U f = (U)2 * al / ((U)1 + al * al * (B[0] * B[0] + B[1] * B[1] + B[2] * B[2]));
+  const U sx = f * B[0], sy = f * B[1], sz = f * B[2];
+  const U t3x = t1x + (t2y * sz - t2z * sy);
+  const U t3y = t1y + (t2z * sx - t2x * sz);
+  const U t3z = t1z + (t2x * sy - t2y * sx);
+  u[0] = t3x + h * E[0];
+  u[1] = t3y + h * E[1];
+  u[2] = t3z + h * E[2];
 }
 
 __device__ inline bool valid_cell(int i, int j, int k, int nx, int ny, int nz) {
@@ -157,11 +161,11 @@ __device__ inline int split_cell(int c0, double s, double* frac) {
 // t = (n+1/2) dt held fixed and the undulator at each sub-step time, then the
 // deposit of J^{n+1} at the mid point of the path and rho^{n+3/2} at the end,
 // and the key/rank of the particle's new tile for the re-sort.
-template <typename T>
+template <typename T, typename U>
 __global__ void __launch_bounds__(256) k_push(PicP<T> p, const StepState* __restrict__ st,
-                                              const V4<T>* __restrict__ po,
                                               const V4<T>* __restrict__ pn,
-                                              V4<T>* __restrict__ src, Parts<T> P, long long np,
+                                              const V4<T>* __restrict__ D,
+                                              V4<T>* __restrict__ src, Parts<T, U> P, long long np,
                                               int* __restrict__ count, int* __restrict__ key,
                                               int* __restrict__ rank,
                                               long long* __restrict__ lost_ctr) {
@@ -172,15 +176,15 @@ __global__ void __launch_bounds__(256) k_push(PicP<T> p, const StepState* __rest
   if (cell >= 0) {
     int i = cell % p.nx, j = (cell / p.nx) % p.ny, k = cell / (int)p.nxy;
     T f[3] = {P.fx[q], P.fy[q], P.fz[q]};
-    T u[3] = {P.ux[q], P.uy[q], P.uz[q]};
+    U u[3] = {P.ux[q], P.uy[q], P.uz[q]};
     const int i0 = i, j0 = j, k0 = k;
     const T f0x = f[0], f0y = f[1], f0z = f[2];
-    double D[3] = {0.0, 0.0, 0.0};  // displacement in cells
+    double disp[3] = {0.0, 0.0, 0.0};  // displacement in cells
     const double th = p.t0 + ((double)st->n + 0.5) * p.dt;
     bool ok = true;
     for (int m = 0; m < p.n_sub && ok; ++m) {
       T E[3], B[3], Eu[3], Bu[3];
-      gather_eb(p, po, pn, i, j, k, f[0], f[1], f[2], E, B);
+      gather_eb(p, pn, D, i, j, k, f[0], f[1], f[2], E, B);
       const double zabs = p.z0 + ((double)k + (double)f[2]) * p.dzd;
       const T y = (T)(p.y0 + ((double)j + (double)f[1]) * p.dyd);
       undulator_field(p, y, zabs, th + m * p.dtb, Eu, Bu);
@@ -193,7 +197,7 @@ __global__ void __launch_bounds__(256) k_push(PicP<T> p, const StepState* __rest
       j = split_cell(j, (double)f[1] + d[1], &fr[1]);
       k = split_cell(k, (double)f[2] + d[2], &fr[2]);
       f[0] = to_frac<T>(fr[0]); f[1] = to_frac<T>(fr[1]); f[2] = to_frac<T>(fr[2]);
-      D[0] += d[0]; D[1] += d[1]; D[2] += d[2];
+      disp[0] += d[0]; disp[1] += d[1]; disp[2] += d[2];
       ok = valid_cell(i, j, k, p.nx, p.ny, p.nz);
     }
     P.ux[q] = u[0]; P.uy[q] = u[1]; P.uz[q] = u[2];
@@ -207,11 +211,11 @@ __global__ void __launch_bounds__(256) k_push(PicP<T> p, const StepState* __rest
       deposit_cic(p, src, i, j, k, f[0], f[1], f[2], (T)0, (T)0, (T)0, p.qV);
       // J^{n+1} at the mid point: offset from the start cell in FP64
       double mf[3];
-      const int mi = split_cell(i0, (double)f0x + 0.5 * D[0], &mf[0]);
-      const int mj = split_cell(j0, (double)f0y + 0.5 * D[1], &mf[1]);
-      const int mk = split_cell(k0, (double)f0z + 0.5 * D[2], &mf[2]);
+      const int mi = split_cell(i0, (double)f0x + 0.5 * disp[0], &mf[0]);
+      const int mj = split_cell(j0, (double)f0y + 0.5 * disp[1], &mf[1]);
+      const int mk = split_cell(k0, (double)f0z + 0.5 * disp[2], &mf[2]);
       deposit_cic(p, src, mi, mj, mk, to_frac<T>(mf[0]), to_frac<T>(mf[1]), to_frac<T>(mf[2]),
-                  (T)(p.jfx * D[0]), (T)(p.jfy * D[1]), (T)(p.jfz * D[2]), (T)0);
+                  (T)(p.jfx * disp[0]), (T)(p.jfy * disp[1]), (T)(p.jfz * disp[2]), (T)0);
       kk = tile_key(p, i, j, k);
     }
   }
@@ -221,11 +225,11 @@ __global__ void __launch_bounds__(256) k_push(PicP<T> p, const StepState* __rest
 
 // Host FP64 positions -> (cell, fraction) and the tile key; invalid
 // positions mark the particle lost.
-template <typename T>
+template <typename T, typename U>
 __global__ void k_init_particles(PicP<T> p, long long np, const double* __restrict__ x,
                                  const double* __restrict__ y, const double* __restrict__ z,
                                  const double* __restrict__ ux, const double* __restrict__ uy,
-                                 const double* __restrict__ uz, Parts<T> P,
+                                 const double* __restrict__ uz, Parts<T, U> P,
                                  int* __restrict__ count, int* __restrict__ key,
                                  int* __restrict__ rank, long long* __restrict__ lost_ctr) {
   const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -243,15 +247,15 @@ __global__ void k_init_particles(PicP<T> p, long long np, const double* __restri
     atomicAdd(reinterpret_cast<unsigned long long*>(lost_ctr), 1ULL);
   }
   P.fx[q] = to_frac<T>(fr[0]); P.fy[q] = to_frac<T>(fr[1]); P.fz[q] = to_frac<T>(fr[2]);
-  P.ux[q] = (T)ux[q]; P.uy[q] = (T)uy[q]; P.uz[q] = (T)uz[q];
+  P.ux[q] = (U)ux[q]; P.uy[q] = (U)uy[q]; P.uz[q] = (U)uz[q];
   P.id[q] = (int)q;
   key[q] = kk;
   rank[q] = bin_rank(count, kk);
 }
 
 // rho of the particles at their present positions (initial rho^{1/2}).
-template <typename T>
-__global__ void k_deposit_rho(PicP<T> p, Parts<T> P, long long np, V4<T>* __restrict__ src) {
+template <typename T, typename U>
+__global__ void k_deposit_rho(PicP<T> p, Parts<T, U> P, long long np, V4<T>* __restrict__ src) {
   const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (q >= np) return;
   const int cell = P.cell[q];
@@ -301,8 +305,8 @@ __global__ void __launch_bounds__(1024) k_scan_counts(int* __restrict__ count,
 }
 
 // Moves every particle to offset[key] + rank in the other buffer.
-template <typename T>
-__global__ void k_scatter(Parts<T> a, Parts<T> b, long long np, const int* __restrict__ key,
+template <typename T, typename U>
+__global__ void k_scatter(Parts<T, U> a, Parts<T, U> b, long long np, const int* __restrict__ key,
                           const int* __restrict__ rank, const int* __restrict__ offset) {
   const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (q >= np) return;
@@ -314,8 +318,8 @@ __global__ void k_scatter(Parts<T> a, Parts<T> b, long long np, const int* __res
 }
 
 // Copy-out in the original particle order: FP64 positions from (cell, f).
-template <typename T>
-__global__ void k_copy_out(PicP<T> p, Parts<T> P, long long np, double* __restrict__ out) {
+template <typename T, typename U>
+__global__ void k_copy_out(PicP<T> p, Parts<T, U> P, long long np, double* __restrict__ out) {
   const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (q >= np) return;
   const long long d = P.id[q];

@@ -15,7 +15,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "_build", "libmithra.so")
 
 OK, EINVAL, EUNSTABLE, ENOMEM, ECUDA, ENUMERIC, ELOST, EBUSY, ENODEV = range(9)
-P64, P32 = 0, 1
+P64, P32, P32_U64 = 0, 1, 2
 FIELDS = ["Ex", "Ey", "Ez", "Bx", "By", "Bz", "Ax", "Ay", "Az", "Jx", "Jy", "Jz", "phi", "rho",
           "Ax_prev", "Ay_prev", "Az_prev", "phi_prev"]
 FIELD_ID = {name: i for i, name in enumerate(FIELDS)}
@@ -25,7 +25,8 @@ EXPORTS = ["mithra_create", "mithra_step", "mithra_sync", "mithra_time", "mithra
            "mithra_set_field", "mithra_sample_fields", "mithra_radiated_power",
            "mithra_set_power_sampling", "mithra_read_power", "mithra_copy_particles",
            "mithra_destroy", "mithra_last_error", "mithra_check_grid", "mithra_footprint",
-           "mithra_version", "mithra_profile", "mithra_kernel_times", "mithra_kernel_name"]
+           "mithra_version", "mithra_profile", "mithra_kernel_times", "mithra_kernel_name",
+           "mithra_set_tuning", "mithra_get_tuning"]
 
 
 class MithraError(RuntimeError):
@@ -93,6 +94,8 @@ def lib():
                                       C.POINTER(C.c_int32)]
     L.mithra_kernel_name.argtypes = [C.c_int32]
     L.mithra_kernel_name.restype = C.c_char_p
+    L.mithra_set_tuning.argtypes = [vp, C.c_int32, C.c_int32]
+    L.mithra_get_tuning.argtypes = [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
     for name in EXPORTS:
         if name not in ("mithra_last_error", "mithra_version", "mithra_kernel_name"):
             getattr(L, name).restype = st
@@ -247,6 +250,15 @@ class Simulation:
         arrs["lost"] = lost
         arrs["n_lost"] = int(nl.value)
         return arrs
+
+    # -- launch choices --------------------------------------------------
+    def set_tuning(self, stencil_variant: int, lz: int = 0):
+        _check(lib().mithra_set_tuning(self.h, int(stencil_variant), int(lz)), self.h)
+
+    def tuning(self):
+        v, lz = C.c_int32(), C.c_int32()
+        _check(lib().mithra_get_tuning(self.h, C.byref(v), C.byref(lz)), self.h)
+        return int(v.value), int(lz.value)
 
     # -- kernel timing ---------------------------------------------------
     def profile(self, enable: bool = True):

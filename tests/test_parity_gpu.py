@@ -114,8 +114,11 @@ def compare_particles(sim, o, tol_cells, face_eps):
 # potential update and Mur boundaries (no particles)
 
 @pytest.mark.parametrize("prec", ["P64", "P32"])
-@pytest.mark.parametrize("shape", [(37, 29, 45), (4, 4, 4), (33, 9, 70), (5, 41, 6)])
-def test_vacuum_update_parity(M, orc, prec, shape):
+@pytest.mark.parametrize("shape", [(37, 29, 45), (4, 4, 4), (33, 9, 70), (5, 41, 6), (70, 17, 9)])
+@pytest.mark.parametrize("variant,lz", [(0, 0), (1, 0), (1, 5), (1, 1)])
+def test_vacuum_update_parity(M, orc, prec, shape, variant, lz):
+    # both forms of the potential update (direct; z-marching TMA tiles with
+    # several plane-chunk lengths, ragged tiles in x and y)
     nx, ny, nz = shape
     g = inputs.random_grid(11, nx, ny, nz)
     f = inputs.random_fields(12, g)
@@ -124,6 +127,8 @@ def test_vacuum_update_parity(M, orc, prec, shape):
         f = as_f32(f)
     o = orc.OracleSim(g, None, dict(x=[], y=[], z=[], ux=[], uy=[], uz=[]))
     with M.Simulation(dict(g, boundary=1), None, None, precision=p) as sim:
+        sim.set_tuning(variant, lz)
+        assert sim.tuning()[0] == variant
         set_state(sim, o, f)
         for steps, tol in ((1, 1e-12 if p == M.P64 else 2e-6), (14, 1e-11 if p == M.P64 else 2e-5)):
             o.step(steps)
@@ -142,7 +147,7 @@ def test_vacuum_update_parity(M, orc, prec, shape):
 C1_UND = inputs.WORKLOADS["c1"]["undulator"]
 
 
-@pytest.mark.parametrize("prec", ["P64", "P32"])
+@pytest.mark.parametrize("prec", ["P64", "P32", "P32_U64"])
 @pytest.mark.parametrize("n_sub", [1, 3])
 def test_pic_step_parity(M, orc, prec, n_sub):
     g = inputs.random_grid(21, 36, 30, 40, n_sub=n_sub)
@@ -150,7 +155,7 @@ def test_pic_step_parity(M, orc, prec, n_sub):
     P = inputs.random_particles(23, g, 6000, u_scale=0.3)
     und = dict(C1_UND, z_ent_lab=0.0)
     p = getattr(M, prec)
-    if p == M.P32:
+    if p != M.P64:
         f = as_f32(f)
     o = orc.OracleSim(g, und, P)
     with M.Simulation(dict(g, boundary=1), und, P, precision=p) as sim:
@@ -210,7 +215,7 @@ def test_initially_outside_particles_are_lost(M, orc, prec):
 # ---------------------------------------------------------------------------
 # the c1 workload end to end (200 steps), power recorded every step
 
-@pytest.mark.parametrize("prec", ["P64", "P32"])
+@pytest.mark.parametrize("prec", ["P64", "P32", "P32_U64"])
 def test_workload_c1(M, orc, prec):
     w = inputs.workload("c1")
     P = inputs.make_bunch(w["bunch_spec"], w["seed"])
