@@ -160,7 +160,10 @@ def run_gpu(args, rank, world):
         if world > 1:
             torch.distributed.barrier()
 
+    from paper_1612_03310_gb300 import autotune
+    tuning = autotune.tune(g, und, bunch, prec, stream=stream.cuda_stream)  # untimed
     sim = mithra.Simulation(g, und, bunch, precision=prec, stream=stream.cuda_stream)
+    sim.set_tuning(**tuning)
     sim.set_power_sampling(kp, W + K)
     sim.step(W)
     sim.sync()
@@ -194,6 +197,7 @@ def run_gpu(args, rank, world):
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms = float(t.item())
     res = dict(ms=ms, kernel_times=kt, clocks=sampler.summary(), n_part=n_part, ncell=ncell,
+               tuning=tuning,
                grid=g, n_lost=parts["n_lost"], power_last=float(power[-1, 0]),
                launches=sum(n for _, n in kt.values()))
 
@@ -201,6 +205,7 @@ def run_gpu(args, rank, world):
     if not args.no_p64 and prec == mithra.P32:
         K64 = max(20, K // 10)
         sim = mithra.Simulation(g, und, bunch, precision=mithra.P64, stream=stream.cuda_stream)
+        sim.set_tuning(**autotune.tune(g, und, bunch, mithra.P64, stream=stream.cuda_stream))
         sim.set_power_sampling(kp, W + K64)
         sim.step(W)
         sim.profile(True)
@@ -225,6 +230,7 @@ def run_gpu(args, rank, world):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         sim = mithra.Simulation(g, und, bunch, precision=prec, stream=stream.cuda_stream)
+        sim.set_tuning(**tuning)
         sim.set_power_sampling(kp, K)
         sim.step(K)
         rec = sim.read_power()
@@ -354,6 +360,7 @@ def main():
         "kernel_share": {k: round(v[0] / total_kernel_ms, 4) for k, v in kt.items()},
         "clocks": res["clocks"],
         "gpu_launches": res["launches"],
+        "tuning": res["tuning"],
         "n_lost": res["n_lost"],
     }
     if "p64" in res:

@@ -204,14 +204,28 @@ mithra_status mithra_kernel_times(mithra_sim* sim, double* ms, int64_t* launches
                                   int32_t max_kernels, int32_t* n_kernels);
 const char* mithra_kernel_name(int32_t kernel);
 
-/* Launch choices (the autotuner's knobs).  stencil_variant 0: the direct
- * potential update, one thread per vertex with neighbours read through L1;
- * 1: the z-marching form, psi^n planes of a 32 x 8 column tile streamed
- * through shared memory by TMA box loads (the default when the driver
- * provides tensor maps).  lz: planes per CTA of the marching form, 0 for the
- * built-in choice.  Results do not depend on these choices beyond rounding. */
-mithra_status mithra_set_tuning(mithra_sim* sim, int32_t stencil_variant, int32_t lz);
-mithra_status mithra_get_tuning(const mithra_sim* sim, int32_t* stencil_variant, int32_t* lz);
+/* Launch choices (the autotuner's knobs).  Results do not depend on them
+ * beyond floating-point rounding.
+ *   stencil_variant 0: the direct potential update, one thread per vertex with
+ *     neighbours read through L1; 1: the z-marching form, psi^n, D and source
+ *     planes of a 32 x 8 column tile streamed through a shared-memory ring by
+ *     TMA box loads.
+ *   lz: planes per CTA of the marching form (0: about two waves of CTAs).
+ *   push_variant 0: one thread per particle, E and B evaluated at the eight
+ *     vertices from global memory; 1: persistent CTAs over 8^3-cell particle
+ *     tiles with the potentials, E/B and the deposit block in shared memory.
+ *   push_ctas_per_sm: persistent CTAs per SM of push variant 1 (0: as many as
+ *     fit).
+ * Variant 1 of both is the default when the driver provides TMA tensor maps. */
+typedef struct {
+    int32_t stencil_variant;
+    int32_t lz;
+    int32_t push_variant;
+    int32_t push_ctas_per_sm;
+} mithra_tuning;
+
+mithra_status mithra_set_tuning(mithra_sim* sim, const mithra_tuning* tuning);
+mithra_status mithra_get_tuning(const mithra_sim* sim, mithra_tuning* tuning);
 
 /* Host-only checks (no GPU needed). */
 

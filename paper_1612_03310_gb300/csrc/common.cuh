@@ -71,7 +71,9 @@ __device__ inline V4<double> ldg4<double>(const V4<double>* p) {
 struct StepState {
   long long n;          // field steps completed
   long long n_lost;     // particles lost so far
-  int err;              // bit 0: NaN/Inf in a reduction
+  int err;              // bit 0: NaN/Inf in a reduction; bit 1: a bounded wait gave up
+  int n_tiles;          // non-empty particle tiles listed by the last scan
+  int work;             // next entry of the tile list to hand out
   int pad;
 };
 
@@ -98,16 +100,18 @@ struct PicP {
   T inv2dx, inv2dy, inv2dz, inv4dx, inv4dy, inv4dz, invdt;
   // Boris: h = qm dtb / (2c), an = qm dtb / 2
   double h, an;
-  double cdtb_dx, cdtb_dy, cdtb_dz;  // c dt_b / (dx, dy, dz)
+  T cx, cy, cz;  // c dt_b / (dx, dy, dz): cells moved per unit beta in a sub-step
   int n_sub;
   double t0, dt, dtb;
   // undulator (lab field transformed to the rest frame)
   int und_on, fringe;
   double g0, b0c, zent, L, lam_u, inv_lam_u, ku_d;
   T ku, B0, ex_fac, by_fac;  // E_x = ex_fac B'_y, B_y = by_fac B'_y
+  T g0dz;                    // gamma0 dz: lab length of one cell along z
+  T y0f, dyf;                // y0 and dy in T
   // deposit
   T qV;                      // q / V
-  double jfx, jfy, jfz;      // (q/V) d_l / dt: J_l per cell of displacement
+  T jx, jy, jz;              // (q/V) d_l / dt: J_l per cell of displacement
   // tiles
   int ntx, nty, ntz, nkeys;
 };

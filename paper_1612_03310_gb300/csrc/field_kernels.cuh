@@ -108,35 +108,45 @@ __global__ void __launch_bounds__(256) k_potential_step(StencilP<T> p,
 
 // ---------------------------------------------------------------------------
 // Marching form of the same update.  A CTA owns a 32 x 8 column tile and a run
-// of lz planes; it walks up in z.  Each psi^n plane of the tile plus a
-// one-vertex halo arrives in shared memory by one TMA box load (4 stages in
-// flight, mbarrier-tracked); a thread keeps, for its column and the planes
-// k-1, k, k+1, the centre value and the x and y neighbour-difference sums in
-// registers, so every psi^n value is read from HBM about once.  D and the
-// sources of the thread's own column are read with 128-bit loads one plane
-// ahead.  The Mur vertices are written by the thread of the adjacent interior
-// vertex, as in the direct form.
-constexpr int kMX = 32, kMY = 8, kMStages = 4;
+// of lz planes; it walks up in z.  For every plane three TMA box loads land in
+// one stage of a shared-memory ring (kMStages stages in flight, one mbarrier
+// each): psi^n of the tile plus a one-vertex halo, and the tile's D and
+// sources.  A thread keeps, for its column and the planes k-1, k, k+1, the
+// centre value and the x and y neighbour-difference sums in registers, so
+// every input value is read from HBM about once and no thread waits on its
+// own loads.  The Mur vertices are written by the thread of the adjacent
+// interior vertex, as in the direct form.
+constexpr int kMX = 32, kMY = 8, kMStages = 3;
 
 template <typename T>
-__host__ __device__ constexpr int march_plane_bytes() {
-  return (((kMX + 2) * (kMY + 2) * (int)sizeof(V4<T>)) + 127) / 128 * 128;
+__host__ __device__ constexpr int march_psi_bytes() {
+  return (kMX + 2) * (kMY + 2) * (int)sizeof(V4<T>);
+}
+template <typename T>
+__host__ __device__ constexpr int march_col_bytes() {
+  return kMX * kMY * (int)sizeof(V4<T>);
+}
+template <typename T>
+__host__ __device__ constexpr int march_stage_bytes() {
+  return ((march_psi_bytes<T>() + 127) / 128 * 128) + 2 * march_col_bytes<T>();
 }
 template <typename T>
 __host__ __device__ constexpr int march_smem_bytes() {
-  return kMStages * march_plane_bytes<T>() + kMStages * 8;
+  return kMStages * march_stage_bytes<T>() + kMStages * 8;
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kMX* kMY) k_potential_march(
-    const __grid_constant__ CUtensorMap tm_cur, StencilP<T> p, const V4<T>* __restrict__ cur,
+__global__ void __launch_bounds__(kMX* kMY, (sizeof(T) == 4 ? 4 : 1)) k_potential_march(
+    const __grid_constant__ CUtensorMap tm_cur, const __grid_constant__ CUtensorMap tm_d,
+    const __grid_constant__ CUtensorMap tm_s, StencilP<T> p, const V4<T>* __restrict__ cur,
     V4<T>* __restrict__ nxt, V4<T>* __restrict__ D, V4<T>* __restrict__ src, int lz,
     int* __restrict__ err) {
   constexpr int HX = kMX + 2;
-  constexpr int PB = march_plane_bytes<T>();
-  constexpr uint32_t kBoxBytes = (kMX + 2) * (kMY + 2) * sizeof(V4<T>);
+  constexpr int SB = march_stage_bytes<T>();
+  constexpr int OFF_D = (march_psi_bytes<T>() + 127) / 128 * 128;
+  constexpr int OFF_S = OFF_D + march_col_bytes<T>();
   extern __shared__ __align__(128) unsigned char smem[];
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kMStages * PB);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kMStages * SB);
   const int tx = threadIdx.x % kMX, ty = threadIdx.x / kMX;
   const int i0 = blockIdx.x * kMX, j0 = blockIdx.y * kMY;
   const int i = i0 + tx, j = j0 + ty;
@@ -149,10 +159,19 @@ __global__ void __launch_bounds__(kMX* kMY) k_potential_march(
     mbar_fence_init();
   }
   __syncthreads();
+  // stage q holds psi^n of plane kb-1+q and, for interior planes, D and the
+  // sources of plane kb-2+q (the plane updated when stage q arrives)
   auto issue = [&](int q) {
     const int s = q % kMStages;
-    mbar_arrive_expect_tx(&bar[s], kBoxBytes);
-    tma_load_4d(smem + s * PB, &tm_cur, 0, i0 - 1, j0 - 1, kb - 1 + q, &bar[s]);
+    unsigned char* base = smem + s * SB;
+    const int kd = kb - 2 + q;
+    const bool cols = kd >= kb && kd < ke;
+    mbar_arrive_expect_tx(&bar[s], march_psi_bytes<T>() + (cols ? 2 * march_col_bytes<T>() : 0));
+    tma_load_4d(base, &tm_cur, 0, i0 - 1, j0 - 1, kb - 1 + q, &bar[s]);
+    if (cols) {
+      tma_load_4d(base + OFF_D, &tm_d, 0, i0, j0, kd, &bar[s]);
+      tma_load_4d(base + OFF_S, &tm_s, 0, i0, j0, kd, &bar[s]);
+    }
   };
   if (threadIdx.x == 0)
     for (int q = 0; q < kMStages && q < nplanes; ++q) issue(q);
@@ -160,42 +179,37 @@ __global__ void __launch_bounds__(kMX* kMY) k_potential_march(
   const bool active = i >= 1 && i <= p.nx - 2 && j >= 1 && j <= p.ny - 2;
   const int h = (ty + 1) * HX + (tx + 1);
   const V4<T> zero = v4((T)0, (T)0, (T)0, (T)0);
-  // reads plane q of the ring (centre, neighbour-difference sums), then frees
-  // its slot for the plane kMStages further up
-  auto take = [&](int q, V4<T>& c, V4<T>& X, V4<T>& Y) {
+  // reads stage q (centre, neighbour-difference sums, and D and the source of
+  // the thread's own vertex), then frees the slot for the stage kMStages up
+  auto take = [&](int q, V4<T>& c, V4<T>& X, V4<T>& Y, V4<T>& dm, V4<T>& sv) {
     const int s = q % kMStages;
     mbar_wait_bounded(&bar[s], (uint32_t)((q / kMStages) & 1), err);
-    const V4<T>* pl = reinterpret_cast<const V4<T>*>(smem + s * PB);
+    const unsigned char* base = smem + s * SB;
+    const V4<T>* pl = reinterpret_cast<const V4<T>*>(base);
     c = pl[h];
     X = (pl[h + 1] - c) + (pl[h - 1] - c);
     Y = (pl[h + HX] - c) + (pl[h - HX] - c);
+    if (q >= 2) {
+      dm = reinterpret_cast<const V4<T>*>(base + OFF_D)[threadIdx.x];
+      sv = reinterpret_cast<const V4<T>*>(base + OFF_S)[threadIdx.x];
+    }
     __syncthreads();
     if (threadIdx.x == 0 && q + kMStages < nplanes) {
       fence_proxy_async_smem();
       issue(q + kMStages);
     }
   };
-  V4<T> cm, Xm, Ym, c0, X0, Y0, cp, Xp, Yp;
-  take(0, cm, Xm, Ym);
-  take(1, c0, X0, Y0);
+  V4<T> cm, Xm, Ym, c0, X0, Y0, cp, Xp, Yp, dm = zero, sv = zero;
+  take(0, cm, Xm, Ym, dm, sv);
+  take(1, c0, X0, Y0, dm, sv);
   const long long col = (long long)j * p.nx + i;
-  V4<T> dm_next = zero, s_next = zero;
-  if (active) {
-    dm_next = D[(long long)kb * p.nxy + col];
-    s_next = src[(long long)kb * p.nxy + col];
-  }
   for (int k = kb; k < ke; ++k) {
-    take(k - kb + 2, cp, Xp, Yp);
-    const V4<T> dm = dm_next, s = s_next;
-    if (active && k + 1 < ke) {
-      dm_next = D[(long long)(k + 1) * p.nxy + col];
-      s_next = src[(long long)(k + 1) * p.nxy + col];
-    }
+    take(k - kb + 2, cp, Xp, Yp, dm, sv);
     if (active) {
       V4<T> L = p.rxA * (Xm + Xp) + p.rxB * X0;
       L = L + p.ryA * (Ym + Yp) + p.ryB * Y0;
       L = L + p.rz2 * ((cp - c0) + (cm - c0));
-      V4<T> dp = dm + (L + source_term(p, s));
+      V4<T> dp = dm + (L + source_term(p, sv));
       if (!p.space_charge) dp.w = (T)0;
       const long long c = (long long)k * p.nxy + col;
       mur_neighbours(p, cur, nxt, D, src, i, j, k, c, dp, dm);

@@ -16,6 +16,7 @@
 #include "common.cuh"
 #include "field_kernels.cuh"
 #include "particle_kernels.cuh"
+#include "tile_push.cuh"
 
 using namespace mithra;
 
@@ -40,6 +41,7 @@ struct mithra_sim {
   int* rank = nullptr;
   int* count = nullptr;
   int* offset = nullptr;
+  int* tiles = nullptr;  // non-empty tile list written by the scan
   StepState* dstate = nullptr;
   double* d_scalar = nullptr;   // one-off reductions
   double* d_power_rec = nullptr;
@@ -55,8 +57,18 @@ struct mithra_sim {
   // potential-update variant: 0 direct, 1 z-marching TMA tiles (needs tm)
   int stencil_variant = 0;
   int lz = 0;  // planes per CTA of the marching form
+  int march_resident = 608;  // marching CTAs resident on the device at once
   bool have_tm = false;
-  CUtensorMap tm[2];
+  CUtensorMap tm[2];      // psi buffers, plane boxes of the marching update
+  CUtensorMap tm_box[2];  // psi buffers, 11^3 boxes of the tiled particle step
+  CUtensorMap tm_box_d;   // increment, 11^3 boxes
+  CUtensorMap tm_col_d;   // increment, 32 x 8 column boxes of the marching update
+  CUtensorMap tm_col_s;   // sources, 32 x 8 column boxes
+  int push_variant = 0;   // 0 per-particle, 1 tiled (needs the box maps)
+  int push_grid = 0;      // persistent CTAs of the tiled particle step
+  int push_max_per_sm = 1;
+  int push_ctas_per_sm = 0;
+  int n_sm = 152;
   // per-kernel event timing
   bool profiling = false;
   struct Rec { int kernel; cudaEvent_t a, b; };
@@ -229,7 +241,7 @@ PicP<T> make_pic(const mithra_sim* s) {
   const double dtb = g.dt / g.n_sub;
   p.h = qm * dtb / (2.0 * kC);
   p.an = qm * dtb / 2.0;
-  p.cdtb_dx = kC * dtb / g.dx; p.cdtb_dy = kC * dtb / g.dy; p.cdtb_dz = kC * dtb / g.dz;
+  p.cx = (T)(kC * dtb / g.dx); p.cy = (T)(kC * dtb / g.dy); p.cz = (T)(kC * dtb / g.dz);
   p.n_sub = g.n_sub;
   p.t0 = s->t0; p.dt = g.dt; p.dtb = dtb;
   p.und_on = (u.K != 0.0) ? 1 : 0;
@@ -246,11 +258,14 @@ PicP<T> make_pic(const mithra_sim* s) {
   p.B0 = (T)(2.0 * kPi * kMe * kC * u.K / (kQe * u.lambda_u));
   p.ex_fac = (T)(-u.gamma0 * b0 * kC);
   p.by_fac = (T)u.gamma0;
+  p.g0dz = (T)(u.gamma0 * g.dz);
+  p.y0f = (T)g.y0;
+  p.dyf = (T)g.dy;
   const double V = g.dx * g.dy * g.dz;
   p.qV = (T)(s->q_macro / V);
-  p.jfx = s->q_macro / V * g.dx / g.dt;
-  p.jfy = s->q_macro / V * g.dy / g.dt;
-  p.jfz = s->q_macro / V * g.dz / g.dt;
+  p.jx = (T)(s->q_macro / V * g.dx / g.dt);
+  p.jy = (T)(s->q_macro / V * g.dy / g.dt);
+  p.jz = (T)(s->q_macro / V * g.dz / g.dt);
   p.ntx = s->ntx; p.nty = s->nty; p.ntz = s->ntz; p.nkeys = s->nkeys;
   return p;
 }
@@ -276,14 +291,47 @@ Parts<T, U> parts_of(mithra_sim* s, int b) {
   return P;
 }
 
-// Planes per CTA of the marching update: about one wave of 8 CTAs per SM on
-// 152 SMs, at least 8 planes.
-int default_lz(const mithra_grid* g) {
+// Persistent grid of the tiled particle step: as many CTAs as fit on the
+// device at once.
+template <typename T, typename U>
+mithra_status setup_push_grid(mithra_sim* s) {
+  const int smem = tile_smem_bytes<T>();
+  MCHECK(s, cudaFuncSetAttribute(k_push_tiled<T, U>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 smem));
+  int dev = 0, nsm = 0, per_sm = 0;
+  MCHECK(s, cudaGetDevice(&dev));
+  MCHECK(s, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  MCHECK(s, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_push_tiled<T, U>, 256, smem));
+  s->n_sm = nsm;
+  s->push_max_per_sm = per_sm > 0 ? per_sm : 1;
+  s->push_grid = nsm * s->push_max_per_sm;
+  return MITHRA_OK;
+}
+
+// Planes per CTA of the marching update: the column tiles times the plane
+// runs fill two waves of the CTAs the device holds at once (resident), with
+// at least 8 planes per run.
+int default_lz(const mithra_grid* g, int resident) {
   const long long tiles = (long long)((g->nx + kMX - 1) / kMX) * ((g->ny + kMY - 1) / kMY);
-  long long lz = (g->nz * tiles + 1215) / 1216;
+  long long runs = 2 * resident / tiles;
+  if (runs < 1) runs = 1;
+  long long lz = (g->nz + runs - 1) / runs;
   if (lz < 8) lz = 8;
   if (lz > g->nz) lz = g->nz;
   return (int)lz;
+}
+
+template <typename T>
+mithra_status setup_march(mithra_sim* s) {
+  MCHECK(s, cudaFuncSetAttribute(k_potential_march<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 march_smem_bytes<T>()));
+  int dev = 0, nsm = 0, per_sm = 0;
+  MCHECK(s, cudaGetDevice(&dev));
+  MCHECK(s, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  MCHECK(s, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_potential_march<T>,
+                                                          kMX * kMY, march_smem_bytes<T>()));
+  s->march_resident = nsm * (per_sm > 0 ? per_sm : 1);
+  return MITHRA_OK;
 }
 
 unsigned blocks_for(long long n, int threads) {
@@ -305,7 +353,7 @@ mithra_status launch_step(mithra_sim* s) {
       dim3 grd((s->g.nx + kMX - 1) / kMX, (s->g.ny + kMY - 1) / kMY,
                (s->g.nz + s->lz - 1) / s->lz);
       k_potential_march<T><<<grd, kMX * kMY, march_smem_bytes<T>(), s->stream>>>(
-          s->tm[s->cur], sp, P0, P1, Dn, S, s->lz, &s->dstate->err);
+          s->tm[s->cur], s->tm_col_d, s->tm_col_s, sp, P0, P1, Dn, S, s->lz, &s->dstate->err);
     } else {
       dim3 blk(32, 8, 1);
       dim3 grd((s->g.nx + 31) / 32, (s->g.ny + 7) / 8, s->g.nz);
@@ -323,13 +371,20 @@ mithra_status launch_step(mithra_sim* s) {
     Parts<T, U> A = parts_of<T, U>(s, s->pb), B = parts_of<T, U>(s, 1 - s->pb);
     {
       ProfScope ps(s, K_PUSH);
-      k_push<T, U><<<blocks_for(s->np, 256), 256, 0, s->stream>>>(pp, s->dstate, P1, Dn, S, A,
-                                                               s->np, s->count, s->key, s->rank,
-                                                               &s->dstate->n_lost);
+      if (s->push_variant == 1 && s->have_tm) {
+        k_push_tiled<T, U><<<s->push_grid, 256, tile_smem_bytes<T>(), s->stream>>>(
+            s->tm_box[1 - s->cur], s->tm_box_d, pp, s->dstate, P1, Dn, S, A, s->offset, s->tiles,
+            s->count, s->key, s->rank, &s->dstate->n_lost, s->np);
+      } else {
+        k_push<T, U><<<blocks_for(s->np, 256), 256, 0, s->stream>>>(pp, s->dstate, P1, Dn, S, A,
+                                                                 s->np, s->count, s->key,
+                                                                 s->rank, &s->dstate->n_lost);
+      }
     }
     {
       ProfScope ps(s, K_SCAN);
-      k_scan_counts<<<1, 1024, 0, s->stream>>>(s->count, s->offset, s->nkeys + 1, s->dstate, 1);
+      k_scan_counts<<<1, 1024, 0, s->stream>>>(s->count, s->offset, s->tiles, s->nkeys,
+                                               s->dstate, 1);
     }
     {
       ProfScope ps(s, K_SCATTER);
@@ -338,7 +393,7 @@ mithra_status launch_step(mithra_sim* s) {
     }
     s->pb = 1 - s->pb;
   } else {
-    k_scan_counts<<<1, 32, 0, s->stream>>>(s->count, s->offset, 1, s->dstate, 1);
+    k_scan_counts<<<1, 32, 0, s->stream>>>(s->count, s->offset, s->tiles, 0, s->dstate, 1);
   }
   s->cur = 1 - s->cur;
   cudaError_t e = cudaGetLastError();
@@ -361,7 +416,8 @@ mithra_status init_particles(mithra_sim* s, const mithra_bunch* b) {
   k_init_particles<T, U><<<blocks_for(n, 256), 256, 0, s->stream>>>(
       pp, n, d, d + n, d + 2 * n, d + 3 * n, d + 4 * n, d + 5 * n, A, s->count, s->key, s->rank,
       lost);
-  k_scan_counts<<<1, 1024, 0, s->stream>>>(s->count, s->offset, s->nkeys + 1, s->dstate, 0);
+  k_scan_counts<<<1, 1024, 0, s->stream>>>(s->count, s->offset, s->tiles, s->nkeys, s->dstate,
+                                           0);
   k_scatter<T, U><<<blocks_for(n, 256), 256, 0, s->stream>>>(A, B, n, s->key, s->rank, s->offset);
   s->pb = 1;
   k_deposit_rho<T, U><<<blocks_for(n, 256), 256, 0, s->stream>>>(pp, B, n,
@@ -495,7 +551,7 @@ void lab_of(const mithra_sim* s, int32_t kp, double t, double* t_lab, double* z_
 void free_all(mithra_sim* s) {
   if (s->stream) cudaStreamSynchronize(s->stream);
   void* ptrs[] = {s->P[0], s->P[1], s->D, s->S, s->pbuf[0], s->pbuf[1], s->key, s->rank, s->count,
-                  s->offset, s->dstate, s->d_scalar, s->d_power_rec};
+                  s->offset, s->tiles, s->dstate, s->d_scalar, s->d_power_rec};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (s->h_err) cudaFreeHost(s->h_err);
@@ -537,7 +593,7 @@ mithra_status mithra_footprint(const mithra_grid* grid, int64_t n_particles,
   int64_t b = 4 * ncell_of(grid) * 4 * (int64_t)r;              // 2 levels, increment, sources
   b += 2 * (int64_t)particle_buffer_bytes(n_particles, precision);
   b += 2 * n_particles * (int64_t)sizeof(int);                   // key, rank
-  b += 2 * (nkeys + 2) * (int64_t)sizeof(int);                   // count, offset
+  b += 3 * (nkeys + 2) * (int64_t)sizeof(int);                   // count, offset, tiles
   b += (int64_t)sizeof(StepState) + (int64_t)sizeof(double);
   *bytes = b;
   return MITHRA_OK;
@@ -601,6 +657,7 @@ mithra_status mithra_create(const mithra_grid* grid, const mithra_undulator* und
             dalloc((void**)&s->rank, sizeof(int) * (size_t)(np + 1)) &&
             dalloc((void**)&s->count, sizeof(int) * (size_t)(s->nkeys + 2)) &&
             dalloc((void**)&s->offset, sizeof(int) * (size_t)(s->nkeys + 2)) &&
+            dalloc((void**)&s->tiles, sizeof(int) * (size_t)(s->nkeys + 1)) &&
             dalloc((void**)&s->dstate, sizeof(StepState)) &&
             dalloc((void**)&s->d_scalar, sizeof(double));
   if (!ok) return bail(MITHRA_ENOMEM, "device allocation failed");
@@ -619,8 +676,27 @@ mithra_status mithra_create(const mithra_grid* grid, const mithra_undulator* und
                                   kMX + 2, kMY + 2) &&
                  encode_field_map(&s->tm[1], s->P[1], es, grid->nx, grid->ny, grid->nz,
                                   kMX + 2, kMY + 2);
+    s->have_tm = s->have_tm &&
+                 encode_field_map(&s->tm_box[0], s->P[0], es, grid->nx, grid->ny, grid->nz, kTP,
+                                  kTP, kTP) &&
+                 encode_field_map(&s->tm_box[1], s->P[1], es, grid->nx, grid->ny, grid->nz, kTP,
+                                  kTP, kTP) &&
+                 encode_field_map(&s->tm_box_d, s->D, es, grid->nx, grid->ny, grid->nz, kTP, kTP,
+                                  kTP) &&
+                 encode_field_map(&s->tm_col_d, s->D, es, grid->nx, grid->ny, grid->nz, kMX, kMY) &&
+                 encode_field_map(&s->tm_col_s, s->S, es, grid->nx, grid->ny, grid->nz, kMX, kMY);
     s->stencil_variant = s->have_tm ? 1 : 0;
-    s->lz = default_lz(grid);
+    s->push_variant = s->have_tm ? 1 : 0;
+    st = with_types(precision, [&](auto t, auto u) {
+      TYPES_OF(t, u);
+      mithra_status r = setup_push_grid<T, U>(s);
+      return r == MITHRA_OK ? setup_march<T>(s) : r;
+    });
+    s->lz = default_lz(grid, s->march_resident);
+    if (st != MITHRA_OK) {
+      std::string msg = s->err;
+      return bail(st, msg);
+    }
   }
   if (np > 0) {
     st = with_types(precision, [&](auto t, auto u) {
@@ -804,21 +880,31 @@ const char* mithra_kernel_name(int32_t kernel) {
   return (kernel >= 0 && kernel < K_COUNT) ? kKernelNames[kernel] : nullptr;
 }
 
-mithra_status mithra_set_tuning(mithra_sim* s, int32_t stencil_variant, int32_t lz) {
+mithra_status mithra_set_tuning(mithra_sim* s, const mithra_tuning* t) {
   if (!s) return fail(nullptr, MITHRA_EINVAL, "sim is NULL");
-  if (stencil_variant < 0 || stencil_variant > 1 || lz < 0)
-    return fail(s, MITHRA_EINVAL, "stencil_variant must be 0 or 1 and lz >= 0");
-  if (stencil_variant == 1 && !s->have_tm)
-    return fail(s, MITHRA_EINVAL, "TMA tensor maps unavailable: marching variant disabled");
-  s->stencil_variant = stencil_variant;
-  s->lz = lz > 0 ? lz : default_lz(&s->g);
+  if (!t || t->stencil_variant < 0 || t->stencil_variant > 1 || t->lz < 0 ||
+      t->push_variant < 0 || t->push_variant > 1 || t->push_ctas_per_sm < 0)
+    return fail(s, MITHRA_EINVAL, "bad tuning: variants 0 or 1, lz >= 0, ctas >= 0");
+  if ((t->stencil_variant == 1 || t->push_variant == 1) && !s->have_tm)
+    return fail(s, MITHRA_EINVAL, "TMA tensor maps unavailable: variant 1 disabled");
+  s->stencil_variant = t->stencil_variant;
+  s->lz = t->lz > 0 ? t->lz : default_lz(&s->g, s->march_resident);
+  s->push_variant = t->push_variant;
+  s->push_ctas_per_sm = t->push_ctas_per_sm;
+  const int per_sm = (t->push_ctas_per_sm > 0 && t->push_ctas_per_sm < s->push_max_per_sm)
+                         ? t->push_ctas_per_sm
+                         : s->push_max_per_sm;
+  s->push_grid = s->n_sm * per_sm;
   return MITHRA_OK;
 }
 
-mithra_status mithra_get_tuning(const mithra_sim* s, int32_t* stencil_variant, int32_t* lz) {
+mithra_status mithra_get_tuning(const mithra_sim* s, mithra_tuning* t) {
   if (!s) return fail(nullptr, MITHRA_EINVAL, "sim is NULL");
-  if (stencil_variant) *stencil_variant = s->stencil_variant;
-  if (lz) *lz = s->lz;
+  if (!t) return fail(nullptr, MITHRA_EINVAL, "tuning is NULL");
+  t->stencil_variant = s->stencil_variant;
+  t->lz = s->lz;
+  t->push_variant = s->push_variant;
+  t->push_ctas_per_sm = s->push_ctas_per_sm;
   return MITHRA_OK;
 }
 

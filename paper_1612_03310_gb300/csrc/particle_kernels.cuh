@@ -18,33 +18,59 @@ __device__ inline double sinh_t(double a) { return sinh(a); }
 __device__ inline float exp_t(float a) { return expf(a); }
 __device__ inline double exp_t(double a) { return exp(a); }
 
-// Rest-frame undulator field at (y, z_abs, t).  The lab distance past the
-// entrance, zeta = gamma0 (z + beta0 c t) - z'_ent, and its reduction modulo
-// lambda_u are FP64; the trigonometric and hyperbolic factors are in T.
+// Rest-frame undulator field.  The lab position of a rest-frame event (z, t)
+// is z' = gamma0 (z + beta0 c t); zeta = z' - z'_ent is the distance past the
+// entrance.  The large, moving-window part of zeta is kept in FP64 once per
+// reference plane kref and time (UndFrame): its phase reduced modulo lambda_u,
+// the entrance and exit thresholds and the fringe arguments there.  A
+// particle adds its offset from the reference plane, gamma0 dz ((k - kref) +
+// f_z), in its own precision T.
 template <typename T>
-__device__ inline void undulator_field(const PicP<T>& p, T y, double zabs, double t, T E[3],
-                                       T B[3]) {
+struct UndFrame {
+  T ph0;      // ku zeta_ref reduced to (-pi, pi]
+  T thr_lo;   // offsets below this are before the entrance
+  T thr_hi;   // offsets above this are past the exit
+  T a_lo0;    // ku zeta_ref (fringe argument before the entrance)
+  T a_hi0;    // ku (zeta_ref - L) (fringe argument past the exit)
+};
+
+template <typename T>
+__device__ inline UndFrame<T> und_frame(const PicP<T>& p, int kref, double t) {
+  const double zeta = p.g0 * (p.z0 + (double)kref * p.dzd + p.b0c * t) - p.zent;
+  UndFrame<T> fr;
+  fr.ph0 = (T)(p.ku_d * (zeta - p.lam_u * rint(zeta * p.inv_lam_u)));
+  fr.thr_lo = (T)(-zeta);
+  fr.thr_hi = p.L > 0.0 ? (T)(p.L - zeta) : (T)3.0e38;
+  fr.a_lo0 = (T)(p.ku_d * zeta);
+  fr.a_hi0 = (T)(p.ku_d * (zeta - p.L));
+  return fr;
+}
+
+// Field at transverse position y and offset zl = (k - kref) + f_z cells from
+// the frame's reference plane.
+template <typename T>
+__device__ inline void undulator_field(const PicP<T>& p, const UndFrame<T>& fr, T y, T zl,
+                                       T E[3], T B[3]) {
   E[0] = E[1] = E[2] = (T)0;
   B[0] = B[1] = B[2] = (T)0;
   if (!p.und_on) return;
-  const double zeta = p.g0 * (zabs + p.b0c * t) - p.zent;
+  const T zr = p.g0dz * zl;  // lab distance from the reference plane
   const T ky = p.ku * y;
   const T ch = cosh_t(ky), sh = sinh_t(ky);
   T by, bz;
-  const bool before = zeta < 0.0;
-  const bool after = p.L > 0.0 && zeta > p.L;
+  const bool before = zr < fr.thr_lo;
+  const bool after = zr > fr.thr_hi;
   if (before || after) {
     if (!p.fringe) return;
-    const T a = (T)(p.ku_d * (before ? zeta : zeta - p.L));
+    const T a = (before ? fr.a_lo0 : fr.a_hi0) + p.ku * zr;
     const T e = exp_t((T)(-0.5) * a * a);
     by = p.B0 * ch * a * e;
     bz = p.B0 * sh * e;
   } else {
-    const double zr = zeta - p.lam_u * rint(zeta * p.inv_lam_u);
-    T s, c;
-    sincos_t((T)(p.ku_d * zr), &s, &c);
-    by = p.B0 * ch * s;
-    bz = p.B0 * sh * c;
+    T sn, cs;
+    sincos_t(fr.ph0 + p.ku * zr, &sn, &cs);
+    by = p.B0 * ch * sn;
+    bz = p.B0 * sh * cs;
   }
   E[0] = p.ex_fac * by;
   B[1] = p.by_fac * by;
@@ -74,6 +100,19 @@ __device__ inline void gather_eb(const PicP<T>& p, const V4<T>* __restrict__ pn,
       }
 }
 
+// 1/sqrt(x) for x >= 1 in FP64 by the Newton-Raphson iteration for the
+// reciprocal square root, y <- y (3 - x y^2) / 2, from an FP32 seed (rsqrtf):
+// the error squares each step, one step reaches ~1e-13 (enough next to FP32
+// momenta), two reach FP64 rounding (used when T is double).  Gives
+// 1/gamma = 1/sqrt(1 + u.u) without an FP64 square root or division.
+template <typename T>
+__device__ inline double rsqrt_nr(double x) {
+  double y = (double)rsqrtf((float)x);
+  y = y * (1.5 - 0.5 * x * y * y);  // relative error ~1e-13 after one step
+  if (sizeof(T) == 8) y = y * (1.5 - 0.5 * x * y * y);  // FP64 rounding
+  return y;
+}
+
 // Boris rotation and kicks (Eq. BorisScheme) for charge-to-mass qm folded
 // into h = qm dtb / (2c) and an = qm dtb / 2, in the momentum type U; gamma
 // of t1 in FP64.
@@ -83,8 +122,9 @@ __device__ inline void boris(const PicP<T>& p, U u[3], const T Ef[3], const T Bf
   const U E[3] = {(U)Ef[0], (U)Ef[1], (U)Ef[2]};
   const U B[3] = {(U)Bf[0], (U)Bf[1], (U)Bf[2]};
   const U t1x = u[0] + h * E[0], t1y = u[1] + h * E[1], t1z = u[2] + h * E[2];
-  const double g1 = sqrt(1.0 + (double)t1x * t1x + (double)t1y * t1y + (double)t1z * t1z);
-  const U al = (U)(p.an / g1);
+  const double ig1 =
+      rsqrt_nr<U>(1.0 + (double)t1x * t1x + (double)t1y * t1y + (double)t1z * t1z);
+  const U al = (U)(p.an * ig1);
   const U t2x = t1x + al * (t1y * B[2] - t1z * B[1]);
   const U t2y = t1y + al * (t1z * B[0] - t1x * B[2]);
   const U t2z = t1z + al * (t1x * B[1] - t1y * B[0]);
@@ -157,6 +197,48 @@ __device__ inline int split_cell(int c0, double s, double* frac) {
   return c0 + (int)fl;
 }
 
+// Splits an offset in cells (relative to cell index c0) into the cell index
+// and the fraction in [0, 1), in the fraction type T.
+template <typename T>
+__device__ inline int split_cell_t(int c0, T s, T* frac) {
+  const T fl = floor(s);
+  T r = s - fl;
+  if (r >= (T)1) r = below_one<T>();
+  *frac = r;
+  return c0 + (int)fl;
+}
+
+// n_sub Boris steps of one particle (Eq. BorisScheme) with the grid E, B from
+// gather(i, j, k, f, E, B) and the undulator at each sub-step time, through
+// the frame frame(m, k, &kref) of sub-step m; 1/gamma in FP64, the position
+// advanced in cells (fraction type T, carry into the cell index).  disp
+// receives the displacement in cells over the field step.  Returns false when
+// the particle leaves the valid cells.
+template <typename T, typename U, typename Gather, typename Frame>
+__device__ inline bool push_particle(const PicP<T>& p, int& i, int& j, int& k, T f[3], U u[3],
+                                     T disp[3], Gather&& gather, Frame&& frame) {
+  disp[0] = disp[1] = disp[2] = (T)0;
+  for (int m = 0; m < p.n_sub; ++m) {
+    T E[3], B[3], Eu[3], Bu[3];
+    gather(i, j, k, f, E, B);
+    int kref;
+    const UndFrame<T> fr = frame(m, k, &kref);
+    const T y = p.y0f + ((T)j + f[1]) * p.dyf;
+    undulator_field(p, fr, y, (T)(k - kref) + f[2], Eu, Bu);
+    for (int e = 0; e < 3; ++e) { E[e] += Eu[e]; B[e] += Bu[e]; }
+    boris(p, u, E, B);
+    const T ig = (T)rsqrt_nr<T>(1.0 + (double)u[0] * u[0] + (double)u[1] * u[1] +
+                                (double)u[2] * u[2]);
+    const T d[3] = {p.cx * ig * (T)u[0], p.cy * ig * (T)u[1], p.cz * ig * (T)u[2]};
+    i = split_cell_t(i, f[0] + d[0], &f[0]);
+    j = split_cell_t(j, f[1] + d[1], &f[1]);
+    k = split_cell_t(k, f[2] + d[2], &f[2]);
+    disp[0] += d[0]; disp[1] += d[1]; disp[2] += d[2];
+    if (!valid_cell(i, j, k, p.nx, p.ny, p.nz)) return false;
+  }
+  return true;
+}
+
 // One field step of every particle: n_sub Boris steps with the grid E, B at
 // t = (n+1/2) dt held fixed and the undulator at each sub-step time, then the
 // deposit of J^{n+1} at the mid point of the path and rho^{n+3/2} at the end,
@@ -171,35 +253,25 @@ __global__ void __launch_bounds__(256) k_push(PicP<T> p, const StepState* __rest
                                               long long* __restrict__ lost_ctr) {
   const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (q >= np) return;
-  int cell = P.cell[q];
+  const int cell = P.cell[q];
   int kk = p.nkeys;  // bucket of lost particles
   if (cell >= 0) {
     int i = cell % p.nx, j = (cell / p.nx) % p.ny, k = cell / (int)p.nxy;
     T f[3] = {P.fx[q], P.fy[q], P.fz[q]};
     U u[3] = {P.ux[q], P.uy[q], P.uz[q]};
     const int i0 = i, j0 = j, k0 = k;
-    const T f0x = f[0], f0y = f[1], f0z = f[2];
-    double disp[3] = {0.0, 0.0, 0.0};  // displacement in cells
+    const T f0[3] = {f[0], f[1], f[2]};
+    T disp[3];
     const double th = p.t0 + ((double)st->n + 0.5) * p.dt;
-    bool ok = true;
-    for (int m = 0; m < p.n_sub && ok; ++m) {
-      T E[3], B[3], Eu[3], Bu[3];
-      gather_eb(p, pn, D, i, j, k, f[0], f[1], f[2], E, B);
-      const double zabs = p.z0 + ((double)k + (double)f[2]) * p.dzd;
-      const T y = (T)(p.y0 + ((double)j + (double)f[1]) * p.dyd);
-      undulator_field(p, y, zabs, th + m * p.dtb, Eu, Bu);
-      for (int a = 0; a < 3; ++a) { E[a] += Eu[a]; B[a] += Bu[a]; }
-      boris(p, u, E, B);
-      const double g = sqrt(1.0 + (double)u[0] * u[0] + (double)u[1] * u[1] + (double)u[2] * u[2]);
-      const double d[3] = {p.cdtb_dx * u[0] / g, p.cdtb_dy * u[1] / g, p.cdtb_dz * u[2] / g};
-      double fr[3];
-      i = split_cell(i, (double)f[0] + d[0], &fr[0]);
-      j = split_cell(j, (double)f[1] + d[1], &fr[1]);
-      k = split_cell(k, (double)f[2] + d[2], &fr[2]);
-      f[0] = to_frac<T>(fr[0]); f[1] = to_frac<T>(fr[1]); f[2] = to_frac<T>(fr[2]);
-      disp[0] += d[0]; disp[1] += d[1]; disp[2] += d[2];
-      ok = valid_cell(i, j, k, p.nx, p.ny, p.nz);
-    }
+    const bool ok = push_particle(
+        p, i, j, k, f, u, disp,
+        [&](int a, int b, int c, const T* ff, T* E, T* B) {
+          gather_eb(p, pn, D, a, b, c, ff[0], ff[1], ff[2], E, B);
+        },
+        [&](int m, int kc, int* kref) {
+          *kref = kc;
+          return und_frame(p, kc, th + m * p.dtb);
+        });
     P.ux[q] = u[0]; P.uy[q] = u[1]; P.uz[q] = u[2];
     if (!ok) {
       P.cell[q] = -1;
@@ -209,13 +281,13 @@ __global__ void __launch_bounds__(256) k_push(PicP<T> p, const StepState* __rest
       P.fx[q] = f[0]; P.fy[q] = f[1]; P.fz[q] = f[2];
       // rho^{n+3/2} at the end position
       deposit_cic(p, src, i, j, k, f[0], f[1], f[2], (T)0, (T)0, (T)0, p.qV);
-      // J^{n+1} at the mid point: offset from the start cell in FP64
-      double mf[3];
-      const int mi = split_cell(i0, (double)f0x + 0.5 * disp[0], &mf[0]);
-      const int mj = split_cell(j0, (double)f0y + 0.5 * disp[1], &mf[1]);
-      const int mk = split_cell(k0, (double)f0z + 0.5 * disp[2], &mf[2]);
-      deposit_cic(p, src, mi, mj, mk, to_frac<T>(mf[0]), to_frac<T>(mf[1]), to_frac<T>(mf[2]),
-                  (T)(p.jfx * disp[0]), (T)(p.jfy * disp[1]), (T)(p.jfz * disp[2]), (T)0);
+      // J^{n+1} at the mid point of the path
+      T mf[3];
+      const int mi = split_cell_t(i0, f0[0] + (T)0.5 * disp[0], &mf[0]);
+      const int mj = split_cell_t(j0, f0[1] + (T)0.5 * disp[1], &mf[1]);
+      const int mk = split_cell_t(k0, f0[2] + (T)0.5 * disp[2], &mf[2]);
+      deposit_cic(p, src, mi, mj, mk, mf[0], mf[1], mf[2], p.jx * disp[0], p.jy * disp[1],
+                  p.jz * disp[2], (T)0);
       kk = tile_key(p, i, j, k);
     }
   }
@@ -264,44 +336,66 @@ __global__ void k_deposit_rho(PicP<T> p, Parts<T, U> P, long long np, V4<T>* __r
   deposit_cic(p, src, i, j, k, P.fx[q], P.fy[q], P.fz[q], (T)0, (T)0, (T)0, p.qV);
 }
 
-// Exclusive scan of the per-tile counts (one block), resetting the counts for
-// the next step.  offset[nkeys + 1] receives the total.  With advance != 0 the
-// block also advances the step counter: it runs last in every step.
-__global__ void __launch_bounds__(1024) k_scan_counts(int* __restrict__ count,
-                                                      int* __restrict__ offset, int n,
-                                                      StepState* __restrict__ st, int advance) {
-  __shared__ int warp_sums[32];
-  const int per = (n + blockDim.x - 1) / blockDim.x;
-  const int beg = min(n, (int)threadIdx.x * per), end = min(n, beg + per);
-  int s = 0;
-  for (int t = beg; t < end; ++t) s += count[t];
-  // block-wide exclusive scan of s
+// Block-wide exclusive scan of one int per thread (blockDim a multiple of 32,
+// at most 1024); *total receives the block sum.  Uses ws[32] shared ints.
+__device__ inline int block_exclusive_scan(int v, int* ws, int* total) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  int incl = s;
+  int incl = v;
   for (int o = 1; o < 32; o <<= 1) {
-    const int v = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += v;
+    const int t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
   }
-  if (lane == 31) warp_sums[wid] = incl;
+  __syncthreads();
+  if (lane == 31) ws[wid] = incl;
   __syncthreads();
   if (wid == 0) {
-    int w = (lane < (int)(blockDim.x >> 5)) ? warp_sums[lane] : 0;
+    int w = (lane < (int)(blockDim.x >> 5)) ? ws[lane] : 0;
     for (int o = 1; o < 32; o <<= 1) {
-      const int v = __shfl_up_sync(0xffffffffu, w, o);
-      if (lane >= o) w += v;
+      const int t = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += t;
     }
-    warp_sums[lane] = w;  // inclusive over warps
+    ws[lane] = w;  // inclusive over warps
   }
   __syncthreads();
-  int run = incl - s + (wid > 0 ? warp_sums[wid - 1] : 0);
+  *total = ws[31];
+  return incl - v + (wid > 0 ? ws[wid - 1] : 0);
+}
+
+// Exclusive scan of the per-tile counts (one block), resetting the counts for
+// the next step; offset[nkeys + 1] receives the total.  Also lists the
+// non-empty tiles (key < nkeys; key nkeys holds the lost particles) for the
+// tiled particle kernel and resets its work counter.  With advance != 0 the
+// block also advances the step counter: it runs last in every step.
+__global__ void __launch_bounds__(1024) k_scan_counts(int* __restrict__ count,
+                                                      int* __restrict__ offset,
+                                                      int* __restrict__ tiles, int nkeys,
+                                                      StepState* __restrict__ st, int advance) {
+  __shared__ int ws[32];
+  const int n = nkeys + 1;
+  const int per = (n + blockDim.x - 1) / blockDim.x;
+  const int beg = min(n, (int)threadIdx.x * per), end = min(n, beg + per);
+  int s = 0, ne = 0;
+  for (int t = beg; t < end; ++t) {
+    const int c = count[t];
+    s += c;
+    ne += (c > 0 && t < nkeys) ? 1 : 0;
+  }
+  int total, ntiles;
+  int run = block_exclusive_scan(s, ws, &total);
+  int slot = block_exclusive_scan(ne, ws, &ntiles);
   for (int t = beg; t < end; ++t) {
     const int c = count[t];
     offset[t] = run;
     run += c;
+    if (c > 0 && t < nkeys) tiles[slot++] = t;
     count[t] = 0;
   }
-  if (threadIdx.x == blockDim.x - 1) offset[n] = run;
-  if (advance && threadIdx.x == 0) st->n += 1;
+  if (threadIdx.x == 0) {
+    offset[n] = total;
+    st->n_tiles = ntiles;
+    st->work = 0;
+    if (advance) st->n += 1;
+  }
 }
 
 // Moves every particle to offset[key] + rank in the other buffer.

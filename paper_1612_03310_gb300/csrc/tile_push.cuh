@@ -1,0 +1,246 @@
+// tile_push.cuh -- particle step by cell tiles.
+//
+// A persistent CTA takes non-empty 8^3-cell tiles from the list the last
+// re-sort produced.  For each tile it
+//   1. loads psi^{n+1} and the increment D over the vertices
+//      [t0 - 1, t0 + 9]^3 (11^3, two TMA box loads, one mbarrier);
+//   2. evaluates E and B at t = (n+1/2) dt at the tile's 9^3 vertices
+//      (Sec. "Field Evaluation") into shared memory;
+//   3. pushes the tile's particles: trilinear gather from shared memory
+//      (Eq. fieldInterpolation), rest-frame undulator field, Boris
+//      (Eq. BorisScheme), FP64 cell carry;
+//   4. deposits J^{n+1} (mid point) and rho^{n+3/2} (end point) into a
+//      shared-memory copy of the 11^3 vertices with shared atomics, and adds
+//      it to the global sources with one 128-bit vector atomic per touched
+//      vertex.
+// A particle whose sub-step leaves the tile (n_sub > 1) gathers from global
+// memory, and one whose deposit leaves the 11^3 block deposits with global
+// atomics: the same arithmetic on another path.  Particles lost in earlier
+// steps only get their re-sort bucket.
+#pragma once
+#include "common.cuh"
+#include "field_kernels.cuh"
+#include "particle_kernels.cuh"
+#include "tma.cuh"
+
+namespace mithra {
+
+constexpr int kTP = kTile + 3;             // potential / deposit vertices per axis
+constexpr int kTE = kTile + 1;             // E/B vertices per axis
+constexpr int kTPC = kTP * kTP * kTP;      // 1331
+constexpr int kTEC = kTE * kTE * kTE;      // 729
+
+template <typename T>
+__host__ __device__ constexpr int tile_box_bytes() {
+  return kTPC * (int)sizeof(V4<T>);
+}
+template <typename T>
+__host__ __device__ constexpr int tile_box_stride() {
+  return (tile_box_bytes<T>() + 127) / 128 * 128;
+}
+template <typename T>
+__host__ __device__ constexpr int tile_eb_offset() {
+  return 2 * tile_box_stride<T>();
+}
+template <typename T>
+__host__ __device__ constexpr int tile_smem_bytes() {
+  return tile_eb_offset<T>() + kTEC * 2 * (int)sizeof(V4<T>) + 16;
+}
+
+// E, B at local vertex (a, b, c) of the potential box (strides 1, 11, 121),
+// same arithmetic as eb_vertex.
+template <typename T>
+__device__ inline void eb_local(const PicP<T>& p, const V4<T>* __restrict__ sP,
+                                const V4<T>* __restrict__ sD, int l, V4<T>& E, V4<T>& B) {
+  constexpr int SX = 1, SY = kTP, SZ = kTP * kTP;
+  const T half = (T)0.5;
+  auto mid = [&](int q) {
+    const V4<T> a = sP[q], d = sD[q];
+    return v4(a.x - half * d.x, a.y - half * d.y, a.z - half * d.z, a.w - d.w);
+  };
+  const V4<T> xp = mid(l + SX), xm = mid(l - SX);
+  const V4<T> yp = mid(l + SY), ym = mid(l - SY);
+  const V4<T> zp = mid(l + SZ), zm = mid(l - SZ);
+  const V4<T> dc = sD[l];
+  B.x = (yp.z - ym.z) * p.inv2dy - (zp.y - zm.y) * p.inv2dz;
+  B.y = (zp.x - zm.x) * p.inv2dz - (xp.z - xm.z) * p.inv2dx;
+  B.z = (xp.y - xm.y) * p.inv2dx - (yp.x - ym.x) * p.inv2dy;
+  B.w = (T)0;
+  E.x = -dc.x * p.invdt - (xp.w - xm.w) * p.inv2dx;
+  E.y = -dc.y * p.invdt - (yp.w - ym.w) * p.inv2dy;
+  E.z = -dc.z * p.invdt - (zp.w - zm.w) * p.inv2dz;
+  E.w = (T)0;
+}
+
+template <typename T>
+__device__ inline void sdep(V4<T>* a, T x, T y, T z, T w) {
+  if (x != (T)0) atomicAdd(&a->x, x);
+  if (y != (T)0) atomicAdd(&a->y, y);
+  if (z != (T)0) atomicAdd(&a->z, z);
+  if (w != (T)0) atomicAdd(&a->w, w);
+}
+
+// CIC deposit into the shared 11^3 block whose vertex (0,0,0) is global
+// (i0-1, j0-1, k0-1); falls back to global atomics outside it.
+template <typename T>
+__device__ inline void deposit_tile(const PicP<T>& p, V4<T>* __restrict__ sJ,
+                                    V4<T>* __restrict__ src, int i0, int j0, int k0, int i, int j,
+                                    int k, T fx, T fy, T fz, T jx, T jy, T jz, T rho) {
+  const int li = i - (i0 - 1), lj = j - (j0 - 1), lk = k - (k0 - 1);
+  if (li < 0 || li > kTP - 2 || lj < 0 || lj > kTP - 2 || lk < 0 || lk > kTP - 2) {
+    deposit_cic(p, src, i, j, k, fx, fy, fz, jx, jy, jz, rho);
+    return;
+  }
+  const T wx[2] = {(T)1 - fx, fx}, wy[2] = {(T)1 - fy, fy}, wz[2] = {(T)1 - fz, fz};
+#pragma unroll
+  for (int K = 0; K < 2; ++K)
+#pragma unroll
+    for (int J = 0; J < 2; ++J)
+#pragma unroll
+      for (int I = 0; I < 2; ++I) {
+        const T w = wx[I] * wy[J] * wz[K];
+        sdep(sJ + ((lk + K) * kTP + (lj + J)) * kTP + (li + I), w * jx, w * jy, w * jz, w * rho);
+      }
+}
+
+template <typename T, typename U>
+__global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 3 : 1)) k_push_tiled(
+    const __grid_constant__ CUtensorMap tm_pn, const __grid_constant__ CUtensorMap tm_d,
+    PicP<T> p, StepState* __restrict__ st, const V4<T>* __restrict__ pn,
+    const V4<T>* __restrict__ D, V4<T>* __restrict__ src, Parts<T, U> P,
+    const int* __restrict__ offset, const int* __restrict__ tiles, int* __restrict__ count,
+    int* __restrict__ key, int* __restrict__ rank, long long* __restrict__ lost_ctr,
+    long long np) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  V4<T>* sP = reinterpret_cast<V4<T>*>(smem);
+  V4<T>* sD = reinterpret_cast<V4<T>*>(smem + tile_box_stride<T>());
+  V4<T>* sEB = reinterpret_cast<V4<T>*>(smem + tile_eb_offset<T>());  // E, B per vertex
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + tile_eb_offset<T>() +
+                                              kTEC * 2 * (int)sizeof(V4<T>));
+  V4<T>* sJ = sP;  // deposit block, reuses the psi box once E, B are built
+  __shared__ int s_tile;
+  constexpr int kMaxFrames = 16;
+  __shared__ UndFrame<T> s_frame[kMaxFrames];  // undulator frames of the tile
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  const int ntiles = st->n_tiles;
+  const double th = p.t0 + ((double)st->n + 0.5) * p.dt;
+  uint32_t phase = 0;
+  for (;;) {
+    if (tid == 0) s_tile = atomicAdd(&st->work, 1);
+    __syncthreads();
+    const int t = s_tile;
+    if (t >= ntiles) break;
+    const int tile = tiles[t];
+    const int i0 = (tile % p.ntx) * kTile;
+    const int j0 = ((tile / p.ntx) % p.nty) * kTile;
+    const int k0 = (tile / (p.ntx * p.nty)) * kTile;
+    if (tid == 0) {
+      fence_proxy_async_smem();
+      mbar_arrive_expect_tx(bar, 2u * tile_box_bytes<T>());
+      tma_load_4d(sP, &tm_pn, 0, i0 - 1, j0 - 1, k0 - 1, bar);
+      tma_load_4d(sD, &tm_d, 0, i0 - 1, j0 - 1, k0 - 1, bar);
+    }
+    // FP64 moving-window bookkeeping once per tile and sub-step
+    for (int m = tid; m < p.n_sub && m < kMaxFrames; m += blockDim.x)
+      s_frame[m] = und_frame(p, k0, th + m * p.dtb);
+    mbar_wait_bounded(bar, phase, &st->err);
+    phase ^= 1u;
+    // E and B at the tile's vertices
+    for (int v = tid; v < kTEC; v += blockDim.x) {
+      const int a = v % kTE, b = (v / kTE) % kTE, c = v / (kTE * kTE);
+      V4<T> E = v4((T)0, (T)0, (T)0, (T)0), B = E;
+      if (interior(i0 + a, j0 + b, k0 + c, p.nx, p.ny, p.nz))
+        eb_local(p, sP, sD, ((c + 1) * kTP + (b + 1)) * kTP + (a + 1), E, B);
+      sEB[2 * v] = E;
+      sEB[2 * v + 1] = B;
+    }
+    __syncthreads();
+    for (int c = tid; c < kTPC; c += blockDim.x) sJ[c] = v4((T)0, (T)0, (T)0, (T)0);
+    __syncthreads();
+
+    const int beg = offset[tile], end = offset[tile + 1];
+    for (int q = beg + tid; q < end; q += blockDim.x) {
+      const int cell = P.cell[q];
+      int kk = p.nkeys;
+      if (cell >= 0) {
+        int i = cell % p.nx, j = (cell / p.nx) % p.ny, k = cell / (int)p.nxy;
+        T f[3] = {P.fx[q], P.fy[q], P.fz[q]};
+        U u[3] = {P.ux[q], P.uy[q], P.uz[q]};
+        const int ia = i, ja = j, ka = k;
+        const T f0[3] = {f[0], f[1], f[2]};
+        T disp[3];
+        const bool ok = push_particle(
+            p, i, j, k, f, u, disp, [&](int ci, int cj, int ck, const T* ff, T* E, T* B) {
+              const int a = ci - i0, b = cj - j0, c = ck - k0;
+              if (a >= 0 && a < kTile && b >= 0 && b < kTile && c >= 0 && c < kTile) {
+                const T wx[2] = {(T)1 - ff[0], ff[0]}, wy[2] = {(T)1 - ff[1], ff[1]},
+                        wz[2] = {(T)1 - ff[2], ff[2]};
+                E[0] = E[1] = E[2] = B[0] = B[1] = B[2] = (T)0;
+#pragma unroll
+                for (int K = 0; K < 2; ++K)
+#pragma unroll
+                  for (int J = 0; J < 2; ++J)
+#pragma unroll
+                    for (int I = 0; I < 2; ++I) {
+                      const int v = ((c + K) * kTE + (b + J)) * kTE + (a + I);
+                      const V4<T> e = sEB[2 * v], bb = sEB[2 * v + 1];
+                      const T w = wx[I] * wy[J] * wz[K];
+                      E[0] += w * e.x; E[1] += w * e.y; E[2] += w * e.z;
+                      B[0] += w * bb.x; B[1] += w * bb.y; B[2] += w * bb.z;
+                    }
+              } else {
+                gather_eb(p, pn, D, ci, cj, ck, ff[0], ff[1], ff[2], E, B);
+              }
+            },
+            [&](int m, int kc, int* kref) {
+              *kref = k0;
+              return m < kMaxFrames ? s_frame[m] : und_frame(p, k0, th + m * p.dtb);
+            });
+        P.ux[q] = u[0]; P.uy[q] = u[1]; P.uz[q] = u[2];
+        if (!ok) {
+          P.cell[q] = -1;
+          atomicAdd(reinterpret_cast<unsigned long long*>(lost_ctr), 1ULL);
+        } else {
+          P.cell[q] = (int)cidx(i, j, k, p.nx, p.nxy);
+          P.fx[q] = f[0]; P.fy[q] = f[1]; P.fz[q] = f[2];
+          deposit_tile(p, sJ, src, i0, j0, k0, i, j, k, f[0], f[1], f[2], (T)0, (T)0, (T)0,
+                       p.qV);
+          T mf[3];
+          const int mi = split_cell_t(ia, f0[0] + (T)0.5 * disp[0], &mf[0]);
+          const int mj = split_cell_t(ja, f0[1] + (T)0.5 * disp[1], &mf[1]);
+          const int mk = split_cell_t(ka, f0[2] + (T)0.5 * disp[2], &mf[2]);
+          deposit_tile(p, sJ, src, i0, j0, k0, mi, mj, mk, mf[0], mf[1], mf[2], p.jx * disp[0],
+                       p.jy * disp[1], p.jz * disp[2], (T)0);
+          kk = tile_key(p, i, j, k);
+        }
+      }
+      key[q] = kk;
+      rank[q] = bin_rank(count, kk);
+    }
+    __syncthreads();
+    // add the block to the global sources (touched vertices only)
+    for (int c = tid; c < kTPC; c += blockDim.x) {
+      const V4<T> v = sJ[c];
+      if (v.x != (T)0 || v.y != (T)0 || v.z != (T)0 || v.w != (T)0) {
+        const int a = c % kTP, b = (c / kTP) % kTP, cc = c / (kTP * kTP);
+        dep_add(src + cidx(i0 - 1 + a, j0 - 1 + b, k0 - 1 + cc, p.nx, p.nxy), v.x, v.y, v.z,
+                v.w);
+      }
+    }
+    __syncthreads();
+  }
+  // particles lost before this step sit at the tail of the sorted order (the
+  // bucket after the last tile); they keep that bucket in the re-sort
+  for (long long q = offset[p.nkeys] + (long long)blockIdx.x * blockDim.x + tid; q < np;
+       q += (long long)gridDim.x * blockDim.x) {
+    key[q] = p.nkeys;
+    rank[q] = bin_rank(count, p.nkeys);
+  }
+}
+
+}  // namespace mithra

@@ -91,15 +91,15 @@ inline TensorMapEncodeTiled tensor_map_encoder() {
 }
 
 // Tensor map of a 4-component field array (nx*ny*nz cells of 4 values of
-// elem_bytes each, x fastest) with a box of 4 x bx x by x 1 values.
+// elem_bytes each, x fastest) with a box of 4 x bx x by x bz values.
 inline bool encode_field_map(CUtensorMap* tm, void* base, int elem_bytes, int nx, int ny, int nz,
-                             int bx, int by) {
+                             int bx, int by, int bz = 1) {
   TensorMapEncodeTiled enc = tensor_map_encoder();
   if (!enc) return false;
   const cuuint64_t cell = 4ull * elem_bytes;
   const cuuint64_t dims[4] = {4, (cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
   const cuuint64_t strides[3] = {cell, cell * nx, cell * nx * ny};
-  const cuuint32_t box[4] = {4, (cuuint32_t)bx, (cuuint32_t)by, 1};
+  const cuuint32_t box[4] = {4, (cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz};
   const cuuint32_t estr[4] = {1, 1, 1, 1};
   CUresult r = enc(tm, elem_bytes == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                        : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,

@@ -48,6 +48,11 @@ class Undulator(C.Structure):
                 ("z_ent_lab", C.c_double), ("length_lab", C.c_double), ("fringe", C.c_int32)]
 
 
+class Tuning(C.Structure):
+    _fields_ = [("stencil_variant", C.c_int32), ("lz", C.c_int32), ("push_variant", C.c_int32),
+                ("push_ctas_per_sm", C.c_int32)]
+
+
 class Bunch(C.Structure):
     _fields_ = [("n", C.c_int64), ("q_macro", C.c_double),
                 ("x", C.POINTER(C.c_double)), ("y", C.POINTER(C.c_double)),
@@ -94,8 +99,8 @@ def lib():
                                       C.POINTER(C.c_int32)]
     L.mithra_kernel_name.argtypes = [C.c_int32]
     L.mithra_kernel_name.restype = C.c_char_p
-    L.mithra_set_tuning.argtypes = [vp, C.c_int32, C.c_int32]
-    L.mithra_get_tuning.argtypes = [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
+    L.mithra_set_tuning.argtypes = [vp, C.POINTER(Tuning)]
+    L.mithra_get_tuning.argtypes = [vp, C.POINTER(Tuning)]
     for name in EXPORTS:
         if name not in ("mithra_last_error", "mithra_version", "mithra_kernel_name"):
             getattr(L, name).restype = st
@@ -252,13 +257,19 @@ class Simulation:
         return arrs
 
     # -- launch choices --------------------------------------------------
-    def set_tuning(self, stencil_variant: int, lz: int = 0):
-        _check(lib().mithra_set_tuning(self.h, int(stencil_variant), int(lz)), self.h)
+    def set_tuning(self, stencil_variant: int | None = None, lz: int | None = None,
+                   push_variant: int | None = None, push_ctas_per_sm: int | None = None):
+        t = self.tuning()
+        for k, v in (("stencil_variant", stencil_variant), ("lz", lz),
+                     ("push_variant", push_variant), ("push_ctas_per_sm", push_ctas_per_sm)):
+            if v is not None:
+                t[k] = int(v)
+        _check(lib().mithra_set_tuning(self.h, C.byref(Tuning(**t))), self.h)
 
-    def tuning(self):
-        v, lz = C.c_int32(), C.c_int32()
-        _check(lib().mithra_get_tuning(self.h, C.byref(v), C.byref(lz)), self.h)
-        return int(v.value), int(lz.value)
+    def tuning(self) -> dict:
+        t = Tuning()
+        _check(lib().mithra_get_tuning(self.h, C.byref(t)), self.h)
+        return {k: int(getattr(t, k)) for k, _ in Tuning._fields_}
 
     # -- kernel timing ---------------------------------------------------
     def profile(self, enable: bool = True):

@@ -127,8 +127,8 @@ def test_vacuum_update_parity(M, orc, prec, shape, variant, lz):
         f = as_f32(f)
     o = orc.OracleSim(g, None, dict(x=[], y=[], z=[], ux=[], uy=[], uz=[]))
     with M.Simulation(dict(g, boundary=1), None, None, precision=p) as sim:
-        sim.set_tuning(variant, lz)
-        assert sim.tuning()[0] == variant
+        sim.set_tuning(stencil_variant=variant, lz=lz)
+        assert sim.tuning()["stencil_variant"] == variant
         set_state(sim, o, f)
         for steps, tol in ((1, 1e-12 if p == M.P64 else 2e-6), (14, 1e-11 if p == M.P64 else 2e-5)):
             o.step(steps)
@@ -149,7 +149,11 @@ C1_UND = inputs.WORKLOADS["c1"]["undulator"]
 
 @pytest.mark.parametrize("prec", ["P64", "P32", "P32_U64"])
 @pytest.mark.parametrize("n_sub", [1, 3])
-def test_pic_step_parity(M, orc, prec, n_sub):
+@pytest.mark.parametrize("push_variant", [0, 1])
+def test_pic_step_parity(M, orc, prec, n_sub, push_variant):
+    # per-particle and tiled particle kernels; n_sub = 3 lets sub-steps leave
+    # the tile (gather from global memory); the 36 x 30 x 40 grid has ragged
+    # tiles in every axis
     g = inputs.random_grid(21, 36, 30, 40, n_sub=n_sub)
     f = inputs.random_fields(22, g, scale=1e-9)
     P = inputs.random_particles(23, g, 6000, u_scale=0.3)
@@ -159,6 +163,7 @@ def test_pic_step_parity(M, orc, prec, n_sub):
         f = as_f32(f)
     o = orc.OracleSim(g, und, P)
     with M.Simulation(dict(g, boundary=1), und, P, precision=p) as sim:
+        sim.set_tuning(push_variant=push_variant)
         # rho^{1/2} from the initial positions agrees before anything else
         ref = oracle_fields(o)
         assert rel_l2(sim.copy_field("rho"), ref["rho"]) <= (1e-13 if p == M.P64 else 1e-6)
@@ -215,8 +220,9 @@ def test_initially_outside_particles_are_lost(M, orc, prec):
 # ---------------------------------------------------------------------------
 # the c1 workload end to end (200 steps), power recorded every step
 
-@pytest.mark.parametrize("prec", ["P64", "P32", "P32_U64"])
-def test_workload_c1(M, orc, prec):
+@pytest.mark.parametrize("prec,push_variant", [("P64", 1), ("P32", 1), ("P32_U64", 1),
+                                               ("P64", 0), ("P32", 0)])
+def test_workload_c1(M, orc, prec, push_variant):
     w = inputs.workload("c1")
     P = inputs.make_bunch(w["bunch_spec"], w["seed"])
     g, und = w["grid"], w["undulator"]
@@ -224,6 +230,7 @@ def test_workload_c1(M, orc, prec):
     p = getattr(M, prec)
     o = orc.OracleSim(g, und, P)
     with M.Simulation(dict(g, boundary=1), und, P, precision=p) as sim:
+        sim.set_tuning(push_variant=push_variant)
         sim.set_power_sampling(kp, w["steps"])
         o.step(w["steps"], power_plane=kp)
         sim.step(w["steps"])
