@@ -196,8 +196,10 @@ def run_gpu(args, rank, world):
         t = torch.tensor([ms], device="cuda", dtype=torch.float64)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms = float(t.item())
+    rec = autotune.record(g, n_part, prec) or {}
     res = dict(ms=ms, kernel_times=kt, clocks=sampler.summary(), n_part=n_part, ncell=ncell,
-               tuning=tuning,
+               tuning=tuning, trials=[{k: (round(v, 4) if k == "ms" else v) for k, v in t.items()}
+                                      for t in rec.get("trials", [])],
                grid=g, n_lost=parts["n_lost"], power_last=float(power[-1, 0]),
                launches=sum(n for _, n in kt.values()))
 
@@ -361,6 +363,7 @@ def main():
         "clocks": res["clocks"],
         "gpu_launches": res["launches"],
         "tuning": res["tuning"],
+        "tuning_trials": res.get("trials"),
         "n_lost": res["n_lost"],
     }
     if "p64" in res:

@@ -132,6 +132,11 @@ def tune(grid: dict, undulator: dict | None, bunch: dict | None, precision: int,
     return best
 
 
+def record(grid: dict, n_particles: int, precision: int) -> dict | None:
+    """The cached entry (choice, best times, all trials) of a shape."""
+    return _load().get(key_of(grid, n_particles, precision))
+
+
 def apply(sim, grid: dict, undulator: dict | None, bunch: dict | None, precision: int,
           **kw) -> dict:
     """Tunes (or looks up) this shape and applies the choice to sim."""

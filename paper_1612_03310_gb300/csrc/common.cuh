@@ -67,6 +67,24 @@ __device__ inline V4<double> ldg4<double>(const V4<double>* p) {
   return v4(a.x, a.y, b.x, b.y);
 }
 
+// Division of non-negative 32-bit integers by an invariant divisor d >= 2 by
+// multiplication (Granlund and Montgomery, "Division by Invariant Integers
+// using Multiplication", 1994): with m = floor(2^64 / d) + 1 (exactly 2^64 / d
+// for powers of two), n / d = floor(n m / 2^64) for all n < 2^32.
+struct FastDiv {
+  unsigned long long m;
+  int d;
+};
+inline FastDiv make_fastdiv(int d) {
+  FastDiv f;
+  f.d = d;
+  f.m = ~0ull / (unsigned long long)d + 1ull;
+  return f;
+}
+__device__ inline int fdiv(int n, const FastDiv& f) {
+  return (int)__umul64hi((unsigned long long)(unsigned)n, f.m);
+}
+
 // Device-side simulation clock and status words (one per simulation).
 struct StepState {
   long long n;          // field steps completed
@@ -114,6 +132,7 @@ struct PicP {
   T jx, jy, jz;              // (q/V) d_l / dt: J_l per cell of displacement
   // tiles
   int ntx, nty, ntz, nkeys;
+  FastDiv fd_nx, fd_nxy;  // cell index -> (i, j, k)
 };
 
 // T: type of the in-cell fractions; U: type of the momenta.
@@ -131,6 +150,15 @@ struct Parts {
 
 __host__ __device__ inline long long cidx(int i, int j, int k, int nx, long long nxy) {
   return (long long)k * nxy + (long long)j * nx + i;
+}
+
+// (i, j, k) of a linear cell index (k * ny + j) * nx + i.
+template <typename P>
+__device__ inline void decode_cell(const P& p, int cell, int* i, int* j, int* k) {
+  *k = fdiv(cell, p.fd_nxy);
+  const int r = cell - *k * (int)p.nxy;
+  *j = fdiv(r, p.fd_nx);
+  *i = r - *j * p.nx;
 }
 
 // largest value of T below one: a fraction that rounds up to 1 is clamped so

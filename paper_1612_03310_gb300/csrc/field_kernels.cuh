@@ -114,8 +114,10 @@ __global__ void __launch_bounds__(256) k_potential_step(StencilP<T> p,
 // sources.  A thread keeps, for its column and the planes k-1, k, k+1, the
 // centre value and the x and y neighbour-difference sums in registers, so
 // every input value is read from HBM about once and no thread waits on its
-// own loads.  The Mur vertices are written by the thread of the adjacent
-// interior vertex, as in the direct form.
+// own loads.  Stages are recycled through per-stage "empty" barriers that
+// every warp arrives on, so warps do not wait for each other plane by plane.
+// The Mur vertices are written by the thread of the adjacent interior vertex,
+// as in the direct form.
 constexpr int kMX = 32, kMY = 8, kMStages = 3;
 
 template <typename T>
@@ -132,7 +134,7 @@ __host__ __device__ constexpr int march_stage_bytes() {
 }
 template <typename T>
 __host__ __device__ constexpr int march_smem_bytes() {
-  return kMStages * march_stage_bytes<T>() + kMStages * 8;
+  return kMStages * march_stage_bytes<T>() + 2 * kMStages * 8;
 }
 
 template <typename T>
@@ -145,8 +147,10 @@ __global__ void __launch_bounds__(kMX* kMY, (sizeof(T) == 4 ? 4 : 1)) k_potentia
   constexpr int SB = march_stage_bytes<T>();
   constexpr int OFF_D = (march_psi_bytes<T>() + 127) / 128 * 128;
   constexpr int OFF_S = OFF_D + march_col_bytes<T>();
+  constexpr int kWarps = kMX * kMY / 32;
   extern __shared__ __align__(128) unsigned char smem[];
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + kMStages * SB);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + kMStages * SB);
+  uint64_t* empty = full + kMStages;
   const int tx = threadIdx.x % kMX, ty = threadIdx.x / kMX;
   const int i0 = blockIdx.x * kMX, j0 = blockIdx.y * kMY;
   const int i = i0 + tx, j = j0 + ty;
@@ -155,7 +159,10 @@ __global__ void __launch_bounds__(kMX* kMY, (sizeof(T) == 4 ? 4 : 1)) k_potentia
   if (kb >= ke) return;             // uniform over the block
   const int nplanes = ke - kb + 2;  // psi^n planes kb-1 .. ke
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kMStages; ++s) mbar_init(&bar[s], 1);
+    for (int s = 0; s < kMStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], kWarps);
+    }
     mbar_fence_init();
   }
   __syncthreads();
@@ -166,11 +173,11 @@ __global__ void __launch_bounds__(kMX* kMY, (sizeof(T) == 4 ? 4 : 1)) k_potentia
     unsigned char* base = smem + s * SB;
     const int kd = kb - 2 + q;
     const bool cols = kd >= kb && kd < ke;
-    mbar_arrive_expect_tx(&bar[s], march_psi_bytes<T>() + (cols ? 2 * march_col_bytes<T>() : 0));
-    tma_load_4d(base, &tm_cur, 0, i0 - 1, j0 - 1, kb - 1 + q, &bar[s]);
+    mbar_arrive_expect_tx(&full[s], march_psi_bytes<T>() + (cols ? 2 * march_col_bytes<T>() : 0));
+    tma_load_4d(base, &tm_cur, 0, i0 - 1, j0 - 1, kb - 1 + q, &full[s]);
     if (cols) {
-      tma_load_4d(base + OFF_D, &tm_d, 0, i0, j0, kd, &bar[s]);
-      tma_load_4d(base + OFF_S, &tm_s, 0, i0, j0, kd, &bar[s]);
+      tma_load_4d(base + OFF_D, &tm_d, 0, i0, j0, kd, &full[s]);
+      tma_load_4d(base + OFF_S, &tm_s, 0, i0, j0, kd, &full[s]);
     }
   };
   if (threadIdx.x == 0)
@@ -179,11 +186,14 @@ __global__ void __launch_bounds__(kMX* kMY, (sizeof(T) == 4 ? 4 : 1)) k_potentia
   const bool active = i >= 1 && i <= p.nx - 2 && j >= 1 && j <= p.ny - 2;
   const int h = (ty + 1) * HX + (tx + 1);
   const V4<T> zero = v4((T)0, (T)0, (T)0, (T)0);
-  // reads stage q (centre, neighbour-difference sums, and D and the source of
-  // the thread's own vertex), then frees the slot for the stage kMStages up
+  // Reads stage q (centre, neighbour-difference sums, and D and the source of
+  // the thread's own vertex); each warp then marks the stage consumed on its
+  // empty barrier, and the issuing thread refills the slot with stage
+  // q + kMStages once every warp has consumed it (no block-wide barrier).
   auto take = [&](int q, V4<T>& c, V4<T>& X, V4<T>& Y, V4<T>& dm, V4<T>& sv) {
     const int s = q % kMStages;
-    mbar_wait_bounded(&bar[s], (uint32_t)((q / kMStages) & 1), err);
+    const uint32_t par = (uint32_t)((q / kMStages) & 1);
+    mbar_wait_bounded(&full[s], par, err);
     const unsigned char* base = smem + s * SB;
     const V4<T>* pl = reinterpret_cast<const V4<T>*>(base);
     c = pl[h];
@@ -193,8 +203,10 @@ __global__ void __launch_bounds__(kMX* kMY, (sizeof(T) == 4 ? 4 : 1)) k_potentia
       dm = reinterpret_cast<const V4<T>*>(base + OFF_D)[threadIdx.x];
       sv = reinterpret_cast<const V4<T>*>(base + OFF_S)[threadIdx.x];
     }
-    __syncthreads();
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) mbar_arrive(&empty[s]);
     if (threadIdx.x == 0 && q + kMStages < nplanes) {
+      mbar_wait_bounded(&empty[s], par, err);
       fence_proxy_async_smem();
       issue(q + kMStages);
     }

@@ -42,6 +42,7 @@ struct mithra_sim {
   int* count = nullptr;
   int* offset = nullptr;
   int* tiles = nullptr;  // non-empty tile list written by the scan
+  int2* scan_part = nullptr;  // block sums of the two-pass scan
   StepState* dstate = nullptr;
   double* d_scalar = nullptr;   // one-off reductions
   double* d_power_rec = nullptr;
@@ -174,6 +175,11 @@ mithra_status check_grid(const mithra_grid* g, std::string* why) {
   if (!g) { *why = "grid is NULL"; return MITHRA_EINVAL; }
   if (g->nx < 4 || g->ny < 4 || g->nz < 4) { *why = "nx, ny, nz must be >= 4"; return MITHRA_EINVAL; }
   if ((int64_t)g->nx * g->ny * g->nz >= (int64_t)1 << 31) { *why = "grid has >= 2^31 vertices"; return MITHRA_EINVAL; }
+  {
+    const int64_t tiles = (int64_t)((g->nx + kTile - 1) / kTile) * ((g->ny + kTile - 1) / kTile) *
+                          ((g->nz + kTile - 1) / kTile);
+    if (tiles + 1 > (int64_t)kScanBlock * kScanBlock) { *why = "grid has too many 8^3 tiles (> 2^20)"; return MITHRA_EINVAL; }
+  }
   if (!(g->dx > 0) || !(g->dy > 0) || !(g->dz > 0) || !(g->dt > 0)) { *why = "dx, dy, dz, dt must be > 0"; return MITHRA_EINVAL; }
   if (g->n_sub < 1) { *why = "n_sub must be >= 1"; return MITHRA_EINVAL; }
   if (g->stencil != 0 && g->stencil != 1) { *why = "stencil must be 0 (NSFD) or 1 (standard)"; return MITHRA_EINVAL; }
@@ -267,6 +273,8 @@ PicP<T> make_pic(const mithra_sim* s) {
   p.jy = (T)(s->q_macro / V * g.dy / g.dt);
   p.jz = (T)(s->q_macro / V * g.dz / g.dt);
   p.ntx = s->ntx; p.nty = s->nty; p.ntz = s->ntz; p.nkeys = s->nkeys;
+  p.fd_nx = make_fastdiv(g.nx);
+  p.fd_nxy = make_fastdiv(g.nx * g.ny);
   return p;
 }
 
@@ -289,6 +297,14 @@ Parts<T, U> parts_of(mithra_sim* s, int b) {
   P.uz = reinterpret_cast<U*>(carve(n * sizeof(U)));
   P.id = reinterpret_cast<int*>(carve(n * sizeof(int)));
   return P;
+}
+
+// Two-pass scan of the per-tile counts (see k_scan_final).
+void launch_scan(mithra_sim* s, int advance) {
+  const int nb = (s->nkeys + 1 + kScanBlock - 1) / kScanBlock;
+  k_scan_partials<<<nb, kScanBlock, 0, s->stream>>>(s->count, s->nkeys, s->scan_part);
+  k_scan_final<<<nb, kScanBlock, 0, s->stream>>>(s->count, s->offset, s->tiles, s->nkeys,
+                                                 s->scan_part, nb, s->dstate, advance);
 }
 
 // Persistent grid of the tiled particle step: as many CTAs as fit on the
@@ -383,8 +399,7 @@ mithra_status launch_step(mithra_sim* s) {
     }
     {
       ProfScope ps(s, K_SCAN);
-      k_scan_counts<<<1, 1024, 0, s->stream>>>(s->count, s->offset, s->tiles, s->nkeys,
-                                               s->dstate, 1);
+      launch_scan(s, 1);
     }
     {
       ProfScope ps(s, K_SCATTER);
@@ -393,7 +408,7 @@ mithra_status launch_step(mithra_sim* s) {
     }
     s->pb = 1 - s->pb;
   } else {
-    k_scan_counts<<<1, 32, 0, s->stream>>>(s->count, s->offset, s->tiles, 0, s->dstate, 1);
+    launch_scan(s, 1);
   }
   s->cur = 1 - s->cur;
   cudaError_t e = cudaGetLastError();
@@ -416,8 +431,7 @@ mithra_status init_particles(mithra_sim* s, const mithra_bunch* b) {
   k_init_particles<T, U><<<blocks_for(n, 256), 256, 0, s->stream>>>(
       pp, n, d, d + n, d + 2 * n, d + 3 * n, d + 4 * n, d + 5 * n, A, s->count, s->key, s->rank,
       lost);
-  k_scan_counts<<<1, 1024, 0, s->stream>>>(s->count, s->offset, s->tiles, s->nkeys, s->dstate,
-                                           0);
+  launch_scan(s, 0);
   k_scatter<T, U><<<blocks_for(n, 256), 256, 0, s->stream>>>(A, B, n, s->key, s->rank, s->offset);
   s->pb = 1;
   k_deposit_rho<T, U><<<blocks_for(n, 256), 256, 0, s->stream>>>(pp, B, n,
@@ -551,7 +565,7 @@ void lab_of(const mithra_sim* s, int32_t kp, double t, double* t_lab, double* z_
 void free_all(mithra_sim* s) {
   if (s->stream) cudaStreamSynchronize(s->stream);
   void* ptrs[] = {s->P[0], s->P[1], s->D, s->S, s->pbuf[0], s->pbuf[1], s->key, s->rank, s->count,
-                  s->offset, s->tiles, s->dstate, s->d_scalar, s->d_power_rec};
+                  s->offset, s->tiles, s->scan_part, s->dstate, s->d_scalar, s->d_power_rec};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (s->h_err) cudaFreeHost(s->h_err);
@@ -658,6 +672,7 @@ mithra_status mithra_create(const mithra_grid* grid, const mithra_undulator* und
             dalloc((void**)&s->count, sizeof(int) * (size_t)(s->nkeys + 2)) &&
             dalloc((void**)&s->offset, sizeof(int) * (size_t)(s->nkeys + 2)) &&
             dalloc((void**)&s->tiles, sizeof(int) * (size_t)(s->nkeys + 1)) &&
+            dalloc((void**)&s->scan_part, sizeof(int2) * (size_t)(s->nkeys / kScanBlock + 2)) &&
             dalloc((void**)&s->dstate, sizeof(StepState)) &&
             dalloc((void**)&s->d_scalar, sizeof(double));
   if (!ok) return bail(MITHRA_ENOMEM, "device allocation failed");

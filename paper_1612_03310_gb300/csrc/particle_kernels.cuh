@@ -11,10 +11,19 @@ namespace mithra {
 // --- math in the particle's precision ------------------------------------
 __device__ inline void sincos_t(float a, float* s, float* c) { sincosf(a, s, c); }
 __device__ inline void sincos_t(double a, double* s, double* c) { sincos(a, s, c); }
-__device__ inline float cosh_t(float a) { return coshf(a); }
-__device__ inline double cosh_t(double a) { return cosh(a); }
-__device__ inline float sinh_t(float a) { return sinhf(a); }
-__device__ inline double sinh_t(double a) { return sinh(a); }
+// cosh and sinh of the same argument from one expm1: with m = e^a - 1,
+// sinh a = m (1 + e^{-a}) / 2 (no cancellation for small a) and
+// cosh a = (e^a + e^{-a}) / 2.
+__device__ inline void coshsinh_t(float a, float* ch, float* sh) {
+  const float m = expm1f(a);
+  const float inv = 1.0f / (1.0f + m);
+  *ch = 0.5f * ((1.0f + m) + inv);
+  *sh = 0.5f * m * (1.0f + inv);
+}
+__device__ inline void coshsinh_t(double a, double* ch, double* sh) {
+  *ch = cosh(a);
+  *sh = sinh(a);
+}
 __device__ inline float exp_t(float a) { return expf(a); }
 __device__ inline double exp_t(double a) { return exp(a); }
 
@@ -55,8 +64,8 @@ __device__ inline void undulator_field(const PicP<T>& p, const UndFrame<T>& fr, 
   B[0] = B[1] = B[2] = (T)0;
   if (!p.und_on) return;
   const T zr = p.g0dz * zl;  // lab distance from the reference plane
-  const T ky = p.ku * y;
-  const T ch = cosh_t(ky), sh = sinh_t(ky);
+  T ch, sh;
+  coshsinh_t(p.ku * y, &ch, &sh);
   T by, bz;
   const bool before = zr < fr.thr_lo;
   const bool after = zr > fr.thr_hi;
@@ -256,7 +265,8 @@ __global__ void __launch_bounds__(256) k_push(PicP<T> p, const StepState* __rest
   const int cell = P.cell[q];
   int kk = p.nkeys;  // bucket of lost particles
   if (cell >= 0) {
-    int i = cell % p.nx, j = (cell / p.nx) % p.ny, k = cell / (int)p.nxy;
+    int i, j, k;
+    decode_cell(p, cell, &i, &j, &k);
     T f[3] = {P.fx[q], P.fy[q], P.fz[q]};
     U u[3] = {P.ux[q], P.uy[q], P.uz[q]};
     const int i0 = i, j0 = j, k0 = k;
@@ -332,7 +342,8 @@ __global__ void k_deposit_rho(PicP<T> p, Parts<T, U> P, long long np, V4<T>* __r
   if (q >= np) return;
   const int cell = P.cell[q];
   if (cell < 0) return;
-  const int i = cell % p.nx, j = (cell / p.nx) % p.ny, k = cell / (int)p.nxy;
+  int i, j, k;
+  decode_cell(p, cell, &i, &j, &k);
   deposit_cic(p, src, i, j, k, P.fx[q], P.fy[q], P.fz[q], (T)0, (T)0, (T)0, p.qV);
 }
 
@@ -361,38 +372,56 @@ __device__ inline int block_exclusive_scan(int v, int* ws, int* total) {
   return incl - v + (wid > 0 ? ws[wid - 1] : 0);
 }
 
-// Exclusive scan of the per-tile counts (one block), resetting the counts for
-// the next step; offset[nkeys + 1] receives the total.  Also lists the
-// non-empty tiles (key < nkeys; key nkeys holds the lost particles) for the
-// tiled particle kernel and resets its work counter.  With advance != 0 the
-// block also advances the step counter: it runs last in every step.
-__global__ void __launch_bounds__(1024) k_scan_counts(int* __restrict__ count,
-                                                      int* __restrict__ offset,
-                                                      int* __restrict__ tiles, int nkeys,
-                                                      StepState* __restrict__ st, int advance) {
+// Exclusive scan of the per-tile counts in two coalesced passes over blocks of
+// kScanBlock entries.  Pass 1 writes each block's sums (particles, non-empty
+// tiles).  Pass 2 scans those sums, then its block: offset[t] (offset[nkeys+1]
+// = total), the list of non-empty tiles (key < nkeys; key nkeys holds the
+// lost particles) for the tiled particle kernel, the reset counts, and, in
+// block 0, the tile count, the reset work counter and (advance != 0: the last
+// kernel of a step) the step counter.
+constexpr int kScanBlock = 1024;
+
+__global__ void __launch_bounds__(kScanBlock) k_scan_partials(const int* __restrict__ count,
+                                                              int nkeys, int2* __restrict__ part) {
   __shared__ int ws[32];
-  const int n = nkeys + 1;
-  const int per = (n + blockDim.x - 1) / blockDim.x;
-  const int beg = min(n, (int)threadIdx.x * per), end = min(n, beg + per);
-  int s = 0, ne = 0;
-  for (int t = beg; t < end; ++t) {
-    const int c = count[t];
-    s += c;
-    ne += (c > 0 && t < nkeys) ? 1 : 0;
-  }
-  int total, ntiles;
-  int run = block_exclusive_scan(s, ws, &total);
-  int slot = block_exclusive_scan(ne, ws, &ntiles);
-  for (int t = beg; t < end; ++t) {
-    const int c = count[t];
-    offset[t] = run;
-    run += c;
-    if (c > 0 && t < nkeys) tiles[slot++] = t;
+  const int t = blockIdx.x * kScanBlock + threadIdx.x;
+  const int c = (t <= nkeys) ? count[t] : 0;
+  int tot, ne;
+  block_exclusive_scan(c, ws, &tot);
+  block_exclusive_scan((c > 0 && t < nkeys) ? 1 : 0, ws, &ne);
+  if (threadIdx.x == 0) part[blockIdx.x] = make_int2(tot, ne);
+}
+
+__global__ void __launch_bounds__(kScanBlock) k_scan_final(int* __restrict__ count,
+                                                           int* __restrict__ offset,
+                                                           int* __restrict__ tiles, int nkeys,
+                                                           const int2* __restrict__ part,
+                                                           int nblocks, StepState* __restrict__ st,
+                                                           int advance) {
+  __shared__ int ws[32];
+  __shared__ int base[2], total[2];
+  // bases of this block from the block sums (nblocks <= kScanBlock)
+  const int2 pv = (threadIdx.x < nblocks) ? part[threadIdx.x] : make_int2(0, 0);
+  int all_c, all_n;
+  const int bc = block_exclusive_scan(pv.x, ws, &all_c);
+  const int bn = block_exclusive_scan(pv.y, ws, &all_n);
+  if (threadIdx.x == blockIdx.x) { base[0] = bc; base[1] = bn; }
+  if (threadIdx.x == 0) { total[0] = all_c; total[1] = all_n; }
+  __syncthreads();
+  const int t = blockIdx.x * kScanBlock + threadIdx.x;
+  const int c = (t <= nkeys) ? count[t] : 0;
+  const bool nonempty = c > 0 && t < nkeys;
+  int dummy;
+  const int off = base[0] + block_exclusive_scan(c, ws, &dummy);
+  const int slot = base[1] + block_exclusive_scan(nonempty ? 1 : 0, ws, &dummy);
+  if (t <= nkeys) {
+    offset[t] = off;
     count[t] = 0;
+    if (nonempty) tiles[slot] = t;
   }
-  if (threadIdx.x == 0) {
-    offset[n] = total;
-    st->n_tiles = ntiles;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    offset[nkeys + 1] = total[0];
+    st->n_tiles = total[1];
     st->work = 0;
     if (advance) st->n += 1;
   }
@@ -420,7 +449,8 @@ __global__ void k_copy_out(PicP<T> p, Parts<T, U> P, long long np, double* __res
   const int cell = P.cell[q];
   double x = 0, y = 0, z = 0, lost = 1.0;
   if (cell >= 0) {
-    const int i = cell % p.nx, j = (cell / p.nx) % p.ny, k = cell / (int)p.nxy;
+    int i, j, k;
+  decode_cell(p, cell, &i, &j, &k);
     x = p.x0 + ((double)i + (double)P.fx[q]) * p.dxd;
     y = p.y0 + ((double)j + (double)P.fy[q]) * p.dyd;
     z = p.z0 + ((double)k + (double)P.fz[q]) * p.dzd;

@@ -72,18 +72,12 @@ __device__ inline void eb_local(const PicP<T>& p, const V4<T>* __restrict__ sP,
   E.w = (T)0;
 }
 
-template <typename T>
-__device__ inline void sdep(V4<T>* a, T x, T y, T z, T w) {
-  if (x != (T)0) atomicAdd(&a->x, x);
-  if (y != (T)0) atomicAdd(&a->y, y);
-  if (z != (T)0) atomicAdd(&a->z, z);
-  if (w != (T)0) atomicAdd(&a->w, w);
-}
-
 // CIC deposit into the shared 11^3 block whose vertex (0,0,0) is global
-// (i0-1, j0-1, k0-1); falls back to global atomics outside it.
-template <typename T>
-__device__ inline void deposit_tile(const PicP<T>& p, V4<T>* __restrict__ sJ,
+// (i0-1, j0-1, k0-1), one array per component (stride kTPC: J_x, J_y, J_z,
+// rho); kRho selects the charge (one component) or the current (three).
+// Falls back to global atomics outside the block.
+template <bool kRho, typename T>
+__device__ inline void deposit_tile(const PicP<T>& p, T* __restrict__ sJ,
                                     V4<T>* __restrict__ src, int i0, int j0, int k0, int i, int j,
                                     int k, T fx, T fy, T fz, T jx, T jy, T jz, T rho) {
   const int li = i - (i0 - 1), lj = j - (j0 - 1), lk = k - (k0 - 1);
@@ -99,7 +93,14 @@ __device__ inline void deposit_tile(const PicP<T>& p, V4<T>* __restrict__ sJ,
 #pragma unroll
       for (int I = 0; I < 2; ++I) {
         const T w = wx[I] * wy[J] * wz[K];
-        sdep(sJ + ((lk + K) * kTP + (lj + J)) * kTP + (li + I), w * jx, w * jy, w * jz, w * rho);
+        T* a = sJ + ((lk + K) * kTP + (lj + J)) * kTP + (li + I);
+        if (kRho) {
+          atomicAdd(a + 3 * kTPC, w * rho);
+        } else {
+          atomicAdd(a, w * jx);
+          atomicAdd(a + kTPC, w * jy);
+          atomicAdd(a + 2 * kTPC, w * jz);
+        }
       }
 }
 
@@ -114,10 +115,14 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 3 : 1)) k_push_tiled(
   extern __shared__ __align__(128) unsigned char smem[];
   V4<T>* sP = reinterpret_cast<V4<T>*>(smem);
   V4<T>* sD = reinterpret_cast<V4<T>*>(smem + tile_box_stride<T>());
-  V4<T>* sEB = reinterpret_cast<V4<T>*>(smem + tile_eb_offset<T>());  // E, B per vertex
+  V4<T>* sE = reinterpret_cast<V4<T>*>(smem + tile_eb_offset<T>());  // E per vertex
+  V4<T>* sB = sE + kTEC;                                                 // B per vertex
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + tile_eb_offset<T>() +
                                               kTEC * 2 * (int)sizeof(V4<T>));
-  V4<T>* sJ = sP;  // deposit block, reuses the psi box once E, B are built
+  // deposit block, reuses the psi box once E, B are built: one array per
+  // component (J_x, J_y, J_z, rho), so that atomics of a component from
+  // different vertices spread over all banks
+  T* sJ = reinterpret_cast<T*>(sP);
   __shared__ int s_tile;
   constexpr int kMaxFrames = 16;
   __shared__ UndFrame<T> s_frame[kMaxFrames];  // undulator frames of the tile
@@ -156,11 +161,11 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 3 : 1)) k_push_tiled(
       V4<T> E = v4((T)0, (T)0, (T)0, (T)0), B = E;
       if (interior(i0 + a, j0 + b, k0 + c, p.nx, p.ny, p.nz))
         eb_local(p, sP, sD, ((c + 1) * kTP + (b + 1)) * kTP + (a + 1), E, B);
-      sEB[2 * v] = E;
-      sEB[2 * v + 1] = B;
+      sE[v] = E;
+      sB[v] = B;
     }
     __syncthreads();
-    for (int c = tid; c < kTPC; c += blockDim.x) sJ[c] = v4((T)0, (T)0, (T)0, (T)0);
+    for (int c = tid; c < 4 * kTPC; c += blockDim.x) sJ[c] = (T)0;
     __syncthreads();
 
     const int beg = offset[tile], end = offset[tile + 1];
@@ -168,7 +173,8 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 3 : 1)) k_push_tiled(
       const int cell = P.cell[q];
       int kk = p.nkeys;
       if (cell >= 0) {
-        int i = cell % p.nx, j = (cell / p.nx) % p.ny, k = cell / (int)p.nxy;
+        int i, j, k;
+    decode_cell(p, cell, &i, &j, &k);
         T f[3] = {P.fx[q], P.fy[q], P.fz[q]};
         U u[3] = {P.ux[q], P.uy[q], P.uz[q]};
         const int ia = i, ja = j, ka = k;
@@ -188,7 +194,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 3 : 1)) k_push_tiled(
 #pragma unroll
                     for (int I = 0; I < 2; ++I) {
                       const int v = ((c + K) * kTE + (b + J)) * kTE + (a + I);
-                      const V4<T> e = sEB[2 * v], bb = sEB[2 * v + 1];
+                      const V4<T> e = sE[v], bb = sB[v];
                       const T w = wx[I] * wy[J] * wz[K];
                       E[0] += w * e.x; E[1] += w * e.y; E[2] += w * e.z;
                       B[0] += w * bb.x; B[1] += w * bb.y; B[2] += w * bb.z;
@@ -208,14 +214,14 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 3 : 1)) k_push_tiled(
         } else {
           P.cell[q] = (int)cidx(i, j, k, p.nx, p.nxy);
           P.fx[q] = f[0]; P.fy[q] = f[1]; P.fz[q] = f[2];
-          deposit_tile(p, sJ, src, i0, j0, k0, i, j, k, f[0], f[1], f[2], (T)0, (T)0, (T)0,
-                       p.qV);
+          deposit_tile<true>(p, sJ, src, i0, j0, k0, i, j, k, f[0], f[1], f[2], (T)0, (T)0,
+                             (T)0, p.qV);
           T mf[3];
           const int mi = split_cell_t(ia, f0[0] + (T)0.5 * disp[0], &mf[0]);
           const int mj = split_cell_t(ja, f0[1] + (T)0.5 * disp[1], &mf[1]);
           const int mk = split_cell_t(ka, f0[2] + (T)0.5 * disp[2], &mf[2]);
-          deposit_tile(p, sJ, src, i0, j0, k0, mi, mj, mk, mf[0], mf[1], mf[2], p.jx * disp[0],
-                       p.jy * disp[1], p.jz * disp[2], (T)0);
+          deposit_tile<false>(p, sJ, src, i0, j0, k0, mi, mj, mk, mf[0], mf[1], mf[2],
+                              p.jx * disp[0], p.jy * disp[1], p.jz * disp[2], (T)0);
           kk = tile_key(p, i, j, k);
         }
       }
@@ -225,7 +231,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 3 : 1)) k_push_tiled(
     __syncthreads();
     // add the block to the global sources (touched vertices only)
     for (int c = tid; c < kTPC; c += blockDim.x) {
-      const V4<T> v = sJ[c];
+      const V4<T> v = v4(sJ[c], sJ[kTPC + c], sJ[2 * kTPC + c], sJ[3 * kTPC + c]);
       if (v.x != (T)0 || v.y != (T)0 || v.z != (T)0 || v.w != (T)0) {
         const int a = c % kTP, b = (c / kTP) % kTP, cc = c / (kTP * kTP);
         dep_add(src + cidx(i0 - 1 + a, j0 - 1 + b, k0 - 1 + cc, p.nx, p.nxy), v.x, v.y, v.z,

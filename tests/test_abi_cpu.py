@@ -105,3 +105,19 @@ def test_workload_table_pinned():
         assert g["dt"] * c == pytest.approx(cdt, rel=1e-13)
         assert g["dz"] == pytest.approx(cdt / 0.95, rel=1e-13)
         assert b["kb"] == pytest.approx(g0 * 2 * np.pi / u["lambda_u"] * (1 + b0), rel=1e-12)
+
+
+def test_division_by_invariant_multiplication():
+    # the cell-index decode divides by nx and nx*ny as floor(n m / 2^64) with
+    # m = floor((2^64 - 1) / d) + 1 (Granlund and Montgomery); check the
+    # identity on grid-sized divisors and the extreme dividends
+    import random
+    rng = random.Random(0)
+    divs = [4, 5, 7, 8, 31, 32, 33, 127, 128, 129, 160, 256, 1000, 4096, 25600, 65536, 65537,
+            131071, 2 ** 20 - 3]
+    for d in divs:
+        m = ((1 << 64) - 1) // d + 1
+        ns = [0, 1, d - 1, d, d + 1, 2 ** 31 - 1, 2 ** 31 - 2] + [rng.randrange(2 ** 31)
+                                                                   for _ in range(2000)]
+        for n in ns:
+            assert (n * m) >> 64 == n // d, (n, d)

@@ -310,3 +310,21 @@ def test_torch_stream(M):
         ref.step(3)
         s.synchronize()
         assert rel_l2(sim.copy_field("rho"), ref.copy_field("rho")) < 1e-5
+
+
+def test_autotuned_choice_matches_default(M, tmp_path, monkeypatch):
+    from paper_1612_03310_gb300 import autotune
+    monkeypatch.setattr(autotune, "CACHE_DIR", str(tmp_path))
+    g = dict(inputs.random_grid(81, 40, 36, 48), boundary=1)
+    P = inputs.random_particles(82, g, 3000)
+    best = autotune.tune(g, C1_UND, P, M.P32, steps=2, warmup=1)
+    st = {(c["stencil_variant"], c["lz"]) for c in autotune.stencil_candidates(g)}
+    assert (best["stencil_variant"], best["lz"]) in st
+    assert best["push_variant"] in (0, 1)
+    with M.Simulation(g, C1_UND, P, precision=M.P32) as a, \
+            M.Simulation(g, C1_UND, P, precision=M.P32) as b:
+        b.set_tuning(**best)
+        a.step(6)
+        b.step(6)
+        for nm in ("Ax", "Ez", "rho", "Jx"):
+            assert rel_l2(b.copy_field(nm), a.copy_field(nm)) < 1e-5, nm
