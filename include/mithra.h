@@ -227,6 +227,35 @@ typedef struct {
 mithra_status mithra_set_tuning(mithra_sim* sim, const mithra_tuning* tuning);
 mithra_status mithra_get_tuning(const mithra_sim* sim, mithra_tuning* tuning);
 
+/* Radiated power through vertex plane k_plane (1 <= k_plane <= nz-2), as
+ * mithra_radiated_power computes it, from caller-owned device arrays, and
+ * without allocating any memory.  The paper has no counterpart: this entry
+ * point exists for callers that cannot call cudaMalloc, such as code running
+ * while a stream is captured into a CUDA graph, an operator inside another
+ * framework whose allocator owns the device memory, or a real-time loop that
+ * must not wait on the allocator.
+ *   psi_newest: device array of nx*ny*nz cells of 4 values {A_x, A_y, A_z,
+ *     phi} of the newest potential level (float for MITHRA_P32 and
+ *     MITHRA_P32_U64, double for MITHRA_P64), cell (i,j,k) at
+ *     (k*ny + j)*nx + i; increment: the same layout, newest minus previous
+ *     level.  E and B are taken at the time between the two levels.
+ *   gamma0: Lorentz factor of the rest frame; *p_lab (host) receives the
+ *     lab-frame power [W]; cuda_stream: stream to run on (NULL: the legacy
+ *     default stream); the call waits for its own work.
+ * Scratch memory is one fixed file-scope device array of 8192 + 1 doubles
+ * (64 KiB per device that loads the library, held until exit): grids with
+ * ny > 8192 are rejected with MITHRA_EINVAL.  The first call on a device
+ * looks up that array's device address (cudaGetSymbolAddress) with the
+ * device current; make that first call before any stream capture.  All calls
+ * on a device share the array and it keeps the last call's partial sums;
+ * every call writes the entries it reads, so none needs clearing, but calls
+ * whose GPU work overlaps (unordered streams) race on it: order them.
+ * Errors are reported by mithra_last_error(NULL). */
+mithra_status mithra_plane_power_noalloc(const mithra_grid* grid, double gamma0,
+                                         mithra_precision precision, const void* psi_newest,
+                                         const void* increment, int32_t k_plane, double* p_lab,
+                                         void* cuda_stream);
+
 /* Host-only checks (no GPU needed). */
 
 /* Validates a grid: sizes, spacings, n_sub, boundary; and the stability

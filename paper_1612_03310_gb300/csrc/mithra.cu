@@ -24,6 +24,10 @@ namespace {
 thread_local std::string g_thread_err;
 }
 
+namespace mithra {
+void set_thread_error(const std::string& msg) { g_thread_err = msg; }
+}
+
 struct mithra_sim {
   mithra_grid g{};
   mithra_undulator u{};

@@ -26,7 +26,7 @@ EXPORTS = ["mithra_create", "mithra_step", "mithra_sync", "mithra_time", "mithra
            "mithra_set_power_sampling", "mithra_read_power", "mithra_copy_particles",
            "mithra_destroy", "mithra_last_error", "mithra_check_grid", "mithra_footprint",
            "mithra_version", "mithra_profile", "mithra_kernel_times", "mithra_kernel_name",
-           "mithra_set_tuning", "mithra_get_tuning"]
+           "mithra_set_tuning", "mithra_get_tuning", "mithra_plane_power_noalloc"]
 
 
 class MithraError(RuntimeError):
@@ -99,6 +99,8 @@ def lib():
                                       C.POINTER(C.c_int32)]
     L.mithra_kernel_name.argtypes = [C.c_int32]
     L.mithra_kernel_name.restype = C.c_char_p
+    L.mithra_plane_power_noalloc.argtypes = [C.POINTER(Grid), C.c_double, C.c_int, vp, vp,
+                                             C.c_int32, dp, vp]
     L.mithra_set_tuning.argtypes = [vp, C.POINTER(Tuning)]
     L.mithra_get_tuning.argtypes = [vp, C.POINTER(Tuning)]
     for name in EXPORTS:
@@ -142,6 +144,18 @@ def footprint(g: dict, n_particles: int, precision: int = P32) -> int:
     _check(lib().mithra_footprint(C.byref(make_grid(g)), int(n_particles), int(precision),
                                   C.byref(out)))
     return int(out.value)
+
+
+def plane_power_noalloc(grid: dict, gamma0: float, precision: int, psi_newest_ptr: int,
+                        increment_ptr: int, k_plane: int, stream: int | None = None) -> float:
+    """Lab-frame power through vertex plane k_plane from device arrays the
+    caller owns (device pointers as integers), with no allocation inside the
+    library; see mithra_plane_power_noalloc in include/mithra.h."""
+    out = C.c_double()
+    _check(lib().mithra_plane_power_noalloc(C.byref(make_grid(grid)), float(gamma0), int(precision),
+                                            C.c_void_p(psi_newest_ptr), C.c_void_p(increment_ptr),
+                                            int(k_plane), C.byref(out), stream_arg(stream)))
+    return float(out.value)
 
 
 def last_error() -> str:
