@@ -256,6 +256,31 @@ mithra_status mithra_plane_power_noalloc(const mithra_grid* grid, double gamma0,
                                          const void* increment, int32_t k_plane, double* p_lab,
                                          void* cuda_stream);
 
+/* Batched stepping (the served and batched forms): a batch advances all its
+ * member simulations together.  Each member keeps its own stream, buffers and
+ * launch choices; the batch captures one CUDA graph that forks from the
+ * batch's stream to every member stream, runs two steps of every member and
+ * joins back, and replays it for every pair of steps (two steps return each
+ * member's ping-pong buffers to their state at capture).  The graph is
+ * captured again after the membership changes or after an odd step count.
+ * A member must have been created with its own stream (cuda_stream NULL, or
+ * a non-default stream other than the batch's); while in a batch it is
+ * stepped only by mithra_batch_step (mithra_step returns MITHRA_EBUSY), and
+ * all other calls on it stay valid.  mithra_batch_remove orders the sim's
+ * later work after the batch's; destroying a member removes it first. */
+typedef struct mithra_batch mithra_batch;
+
+mithra_status mithra_batch_create(void* cuda_stream, mithra_batch** out);
+mithra_status mithra_batch_add(mithra_batch* batch, mithra_sim* sim);
+mithra_status mithra_batch_remove(mithra_batch* batch, mithra_sim* sim);
+/* Enqueues n steps of every member and returns without waiting. */
+mithra_status mithra_batch_step(mithra_batch* batch, int64_t n);
+/* Waits for the batch and returns the first failing member's status. */
+mithra_status mithra_batch_sync(mithra_batch* batch);
+int32_t mithra_batch_size(const mithra_batch* batch);
+const char* mithra_batch_last_error(const mithra_batch* batch);
+mithra_status mithra_batch_destroy(mithra_batch* batch);
+
 /* Host-only checks (no GPU needed). */
 
 /* Validates a grid: sizes, spacings, n_sub, boundary; and the stability

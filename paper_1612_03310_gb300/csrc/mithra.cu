@@ -74,6 +74,7 @@ struct mithra_sim {
   int push_max_per_sm = 1;
   int push_ctas_per_sm = 0;
   int n_sm = 152;
+  mithra_batch* in_batch = nullptr;  // the batch that steps this sim, if any
   // per-kernel event timing
   bool profiling = false;
   struct Rec { int kernel; cudaEvent_t a, b; };
@@ -732,17 +733,25 @@ mithra_status mithra_create(const mithra_grid* grid, const mithra_undulator* und
   return MITHRA_OK;
 }
 
+namespace {
+mithra_status launch_one_step(mithra_sim* s) {
+  mithra_status st = with_types(s->prec, [&](auto t, auto u) {
+    TYPES_OF(t, u);
+    return launch_step<T, U>(s);
+  });
+  if (st == MITHRA_OK) s->n_issued += 1;
+  return st;
+}
+}  // namespace
+
 mithra_status mithra_step(mithra_sim* s, int64_t n) {
   if (!s) return fail(nullptr, MITHRA_EINVAL, "sim is NULL");
   if (n < 0) return fail(s, MITHRA_EINVAL, "n must be >= 0");
   if (*s->h_err & 1) return fail(s, MITHRA_ENUMERIC, "NaN or Inf in a power reduction");
+  if (s->in_batch) return fail(s, MITHRA_EBUSY, "sim belongs to a batch: step it with mithra_batch_step");
   for (int64_t t = 0; t < n; ++t) {
-    mithra_status st = with_types(s->prec, [&](auto t, auto u) {
-      TYPES_OF(t, u);
-      return launch_step<T, U>(s);
-    });
+    mithra_status st = launch_one_step(s);
     if (st != MITHRA_OK) return st;
-    s->n_issued += 1;
   }
   cudaMemcpyAsync(s->h_err, &s->dstate->err, sizeof(int), cudaMemcpyDeviceToHost, s->stream);
   return MITHRA_OK;
@@ -929,8 +938,231 @@ mithra_status mithra_get_tuning(const mithra_sim* s, mithra_tuning* t) {
 
 mithra_status mithra_destroy(mithra_sim* s) {
   if (!s) return MITHRA_OK;
+  if (s->in_batch) mithra_batch_remove(s->in_batch, s);
   free_all(s);
   delete s;
+  return MITHRA_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batched stepping: one CUDA graph advances every member by two steps.  Each
+// member's kernels stay on its own stream; the graph forks from the batch's
+// stream to every member stream and joins back, so independent members run
+// concurrently.  Two steps bring each member's ping-pong buffers back to the
+// state they had at capture, so the same graph serves every later pair of
+// steps; it is captured again only when the membership changes.
+
+struct mithra_batch {
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::vector<mithra_sim*> sims;
+  cudaGraphExec_t exec = nullptr;
+  bool dirty = true;
+  cudaEvent_t fork = nullptr;
+  cudaEvent_t done = nullptr;
+  std::vector<cudaEvent_t> joins;
+  std::string err;
+};
+
+namespace {
+
+mithra_status bfail(mithra_batch* b, mithra_status st, const std::string& msg) {
+  if (b) b->err = msg; else g_thread_err = msg;
+  return st;
+}
+
+void drop_graph(mithra_batch* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  b->exec = nullptr;
+  b->dirty = true;
+}
+
+mithra_status capture(mithra_batch* b) {
+  drop_graph(b);
+  while (b->joins.size() < b->sims.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+      return bfail(b, MITHRA_ECUDA, "event creation failed");
+    b->joins.push_back(e);
+  }
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return bfail(b, MITHRA_ECUDA, std::string("begin capture: ") + cudaGetErrorString(e));
+  mithra_status st = MITHRA_OK;
+  cudaEventRecord(b->fork, b->stream);
+  for (size_t k = 0; k < b->sims.size() && st == MITHRA_OK; ++k) {
+    mithra_sim* s = b->sims[k];
+    cudaStreamWaitEvent(s->stream, b->fork, 0);
+    const bool prof = s->profiling;
+    s->profiling = false;
+    for (int t = 0; t < 2 && st == MITHRA_OK; ++t) {
+      st = with_types(s->prec, [&](auto tt, auto uu) {
+        TYPES_OF(tt, uu);
+        return launch_step<T, U>(s);
+      });
+    }
+    s->profiling = prof;
+    cudaEventRecord(b->joins[k], s->stream);
+    cudaStreamWaitEvent(b->stream, b->joins[k], 0);
+  }
+  e = cudaStreamEndCapture(b->stream, &graph);
+  if (st != MITHRA_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return bfail(b, st, "capture of a member's step failed");
+  }
+  if (e != cudaSuccess) return bfail(b, MITHRA_ECUDA, std::string("end capture: ") + cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&b->exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return bfail(b, MITHRA_ECUDA, std::string("instantiate: ") + cudaGetErrorString(e));
+  b->dirty = false;
+  return MITHRA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mithra_status mithra_batch_create(void* cuda_stream, mithra_batch** out) {
+  if (!out) return bfail(nullptr, MITHRA_EINVAL, "out is NULL");
+  *out = nullptr;
+  mithra_batch* b = new (std::nothrow) mithra_batch();
+  if (!b) return bfail(nullptr, MITHRA_ENOMEM, "host allocation failed");
+  if (cuda_stream) {
+    b->stream = static_cast<cudaStream_t>(cuda_stream);
+  } else {
+    if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      delete b;
+      return bfail(nullptr, MITHRA_ECUDA, "stream creation failed");
+    }
+    b->own_stream = true;
+  }
+  if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming) != cudaSuccess) {
+    if (b->own_stream) cudaStreamDestroy(b->stream);
+    delete b;
+    return bfail(nullptr, MITHRA_ECUDA, "event creation failed");
+  }
+  *out = b;
+  return MITHRA_OK;
+}
+
+mithra_status mithra_batch_add(mithra_batch* b, mithra_sim* s) {
+  if (!b || !s) return bfail(b, MITHRA_EINVAL, "batch or sim is NULL");
+  if (s->in_batch) return bfail(b, MITHRA_EBUSY, "sim already belongs to a batch");
+  if (s->stream == b->stream || s->stream == nullptr ||
+      s->stream == reinterpret_cast<cudaStream_t>(1) || s->stream == reinterpret_cast<cudaStream_t>(2))
+    return bfail(b, MITHRA_EINVAL, "a batched sim needs its own non-default stream");
+  // work already queued on the sim's stream comes before the batch's work
+  cudaEvent_t e;
+  if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+    return bfail(b, MITHRA_ECUDA, "event creation failed");
+  cudaEventRecord(e, s->stream);
+  cudaStreamWaitEvent(b->stream, e, 0);
+  cudaEventDestroy(e);
+  b->sims.push_back(s);
+  s->in_batch = b;
+  drop_graph(b);
+  return MITHRA_OK;
+}
+
+mithra_status mithra_batch_remove(mithra_batch* b, mithra_sim* s) {
+  if (!b || !s) return bfail(b, MITHRA_EINVAL, "batch or sim is NULL");
+  for (size_t k = 0; k < b->sims.size(); ++k) {
+    if (b->sims[k] == s) {
+      // later work on the sim's own stream waits for the batch
+      cudaEvent_t e;
+      if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess) {
+        cudaEventRecord(e, b->stream);
+        cudaStreamWaitEvent(s->stream, e, 0);
+        cudaEventDestroy(e);
+      }
+      b->sims.erase(b->sims.begin() + (long)k);
+      s->in_batch = nullptr;
+      drop_graph(b);
+      return MITHRA_OK;
+    }
+  }
+  return bfail(b, MITHRA_EINVAL, "sim is not in this batch");
+}
+
+mithra_status mithra_batch_step(mithra_batch* b, int64_t n) {
+  if (!b) return bfail(nullptr, MITHRA_EINVAL, "batch is NULL");
+  if (n < 0) return bfail(b, MITHRA_EINVAL, "n must be >= 0");
+  if (b->sims.empty() || n == 0) return MITHRA_OK;
+  if (n >= 2 && (b->dirty || !b->exec)) {
+    mithra_status st = capture(b);
+    if (st != MITHRA_OK) return st;
+  }
+  while (b->joins.size() < b->sims.size()) {
+    cudaEvent_t e;
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+      return bfail(b, MITHRA_ECUDA, "event creation failed");
+    b->joins.push_back(e);
+  }
+  // work queued on a member's own stream comes before the batch's
+  for (size_t k = 0; k < b->sims.size(); ++k) {
+    cudaEventRecord(b->joins[k], b->sims[k]->stream);
+    cudaStreamWaitEvent(b->stream, b->joins[k], 0);
+  }
+  for (int64_t t = 0; t + 1 < n; t += 2) {
+    cudaError_t e = cudaGraphLaunch(b->exec, b->stream);
+    if (e != cudaSuccess) return bfail(b, MITHRA_ECUDA, std::string("graph launch: ") + cudaGetErrorString(e));
+    for (mithra_sim* s : b->sims) s->n_issued += 2;
+  }
+  if (n % 2) {
+    // one more step for every member, outside the graph
+    cudaEventRecord(b->fork, b->stream);
+    for (size_t k = 0; k < b->sims.size(); ++k) {
+      mithra_sim* s = b->sims[k];
+      cudaStreamWaitEvent(s->stream, b->fork, 0);
+      mithra_status st = launch_one_step(s);
+      if (st != MITHRA_OK) return bfail(b, st, s->err);
+      if (b->joins.size() <= k) {
+        cudaEvent_t e;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+          return bfail(b, MITHRA_ECUDA, "event creation failed");
+        b->joins.push_back(e);
+      }
+      cudaEventRecord(b->joins[k], s->stream);
+      cudaStreamWaitEvent(b->stream, b->joins[k], 0);
+    }
+    drop_graph(b);  // members' parities changed
+  }
+  // later work on a member's own stream waits for the batch
+  cudaEventRecord(b->done, b->stream);
+  for (mithra_sim* s : b->sims) cudaStreamWaitEvent(s->stream, b->done, 0);
+  return MITHRA_OK;
+}
+
+mithra_status mithra_batch_sync(mithra_batch* b) {
+  if (!b) return bfail(nullptr, MITHRA_EINVAL, "batch is NULL");
+  cudaError_t e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) return bfail(b, MITHRA_ECUDA, std::string("synchronize: ") + cudaGetErrorString(e));
+  for (mithra_sim* s : b->sims) {
+    mithra_status st = sync_status(s);
+    if (st != MITHRA_OK) return bfail(b, st, s->err);
+  }
+  return MITHRA_OK;
+}
+
+int32_t mithra_batch_size(const mithra_batch* b) { return b ? (int32_t)b->sims.size() : 0; }
+
+const char* mithra_batch_last_error(const mithra_batch* b) {
+  return b ? b->err.c_str() : g_thread_err.c_str();
+}
+
+mithra_status mithra_batch_destroy(mithra_batch* b) {
+  if (!b) return MITHRA_OK;
+  cudaStreamSynchronize(b->stream);
+  for (mithra_sim* s : b->sims) s->in_batch = nullptr;
+  drop_graph(b);
+  for (cudaEvent_t e : b->joins) cudaEventDestroy(e);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->done) cudaEventDestroy(b->done);
+  if (b->own_stream) cudaStreamDestroy(b->stream);
+  delete b;
   return MITHRA_OK;
 }
 

@@ -26,7 +26,10 @@ EXPORTS = ["mithra_create", "mithra_step", "mithra_sync", "mithra_time", "mithra
            "mithra_set_power_sampling", "mithra_read_power", "mithra_copy_particles",
            "mithra_destroy", "mithra_last_error", "mithra_check_grid", "mithra_footprint",
            "mithra_version", "mithra_profile", "mithra_kernel_times", "mithra_kernel_name",
-           "mithra_set_tuning", "mithra_get_tuning", "mithra_plane_power_noalloc"]
+           "mithra_set_tuning", "mithra_get_tuning", "mithra_plane_power_noalloc",
+           "mithra_batch_create", "mithra_batch_add", "mithra_batch_remove", "mithra_batch_step",
+           "mithra_batch_sync", "mithra_batch_size", "mithra_batch_last_error",
+           "mithra_batch_destroy"]
 
 
 class MithraError(RuntimeError):
@@ -101,10 +104,21 @@ def lib():
     L.mithra_kernel_name.restype = C.c_char_p
     L.mithra_plane_power_noalloc.argtypes = [C.POINTER(Grid), C.c_double, C.c_int, vp, vp,
                                              C.c_int32, dp, vp]
+    L.mithra_batch_create.argtypes = [vp, C.POINTER(vp)]
+    L.mithra_batch_add.argtypes = [vp, vp]
+    L.mithra_batch_remove.argtypes = [vp, vp]
+    L.mithra_batch_step.argtypes = [vp, C.c_int64]
+    L.mithra_batch_sync.argtypes = [vp]
+    L.mithra_batch_size.argtypes = [vp]
+    L.mithra_batch_size.restype = C.c_int32
+    L.mithra_batch_last_error.argtypes = [vp]
+    L.mithra_batch_last_error.restype = C.c_char_p
+    L.mithra_batch_destroy.argtypes = [vp]
     L.mithra_set_tuning.argtypes = [vp, C.POINTER(Tuning)]
     L.mithra_get_tuning.argtypes = [vp, C.POINTER(Tuning)]
     for name in EXPORTS:
-        if name not in ("mithra_last_error", "mithra_version", "mithra_kernel_name"):
+        if name not in ("mithra_last_error", "mithra_version", "mithra_kernel_name",
+                        "mithra_batch_size", "mithra_batch_last_error"):
             getattr(L, name).restype = st
     _lib = L
     return L
@@ -304,6 +318,57 @@ class Simulation:
         if getattr(self, "h", None):
             lib().mithra_destroy(self.h)
             self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class Batch:
+    """Steps several simulations together through one captured CUDA graph
+    (see mithra_batch_* in include/mithra.h)."""
+
+    def __init__(self, stream: int | None = None):
+        h = C.c_void_p()
+        _check(lib().mithra_batch_create(stream_arg(stream), C.byref(h)))
+        self.h = h
+        self.members: list[Simulation] = []
+
+    def _check(self, st):
+        if st != OK:
+            m = lib().mithra_batch_last_error(self.h)
+            raise MithraError(st, m.decode() if m else "")
+
+    def add(self, sim: Simulation):
+        self._check(lib().mithra_batch_add(self.h, sim.h))
+        self.members.append(sim)
+
+    def remove(self, sim: Simulation):
+        self._check(lib().mithra_batch_remove(self.h, sim.h))
+        self.members.remove(sim)
+
+    def step(self, n: int = 1):
+        self._check(lib().mithra_batch_step(self.h, int(n)))
+
+    def sync(self):
+        self._check(lib().mithra_batch_sync(self.h))
+
+    def __len__(self):
+        return int(lib().mithra_batch_size(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().mithra_batch_destroy(self.h)
+            self.h = None
+            self.members = []
 
     def __del__(self):
         try:
