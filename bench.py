@@ -45,6 +45,15 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-p64", action="store_true")
+    ap.add_argument("--mode", default="step", choices=["step", "batch", "serve"],
+                    help="step: one simulation (c2); batch: 64 uneven simulations (c4); "
+                         "serve: continuous batching of Poisson arrivals (c5)")
+    ap.add_argument("--job-steps", type=int, default=100,
+                    help="batch mode: steps timed per job (jobs of 1000 steps are scaled)")
+    ap.add_argument("--plain-jobs", type=int, default=8,
+                    help="batch mode: jobs run one by one in plain FP64")
+    ap.add_argument("--duration", type=float, default=60.0, help="serve mode: seconds per run")
+    ap.add_argument("--rate", type=float, default=20.0, help="serve mode: arrivals per second")
     return ap.parse_args()
 
 
@@ -282,8 +291,120 @@ def cpu_oracle_rate(workload: str, budget_s: float, max_steps: int | None = None
                        f"the particle loop is serial, the grid loops use OpenMP")
 
 
+def run_batch(args) -> dict:
+    """c4: 64 simulations of uneven size advanced together (P32, one captured
+    graph per two steps) against the plain form (P64, one simulation after
+    another, one launch sequence per step).  Jobs are 1000 steps; the timed
+    runs take --job-steps steps and jobs/h is scaled to 1000-step jobs."""
+    import torch
+    from paper_1612_03310_gb300 import autotune, inputs, mithra
+    jobs = inputs.batch_jobs(64, steps=1000)
+    K = args.job_steps
+    scale = 1000.0 / K
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    sims = []
+    for j in jobs:
+        g = dict(j["grid"], boundary=1)
+        sim = mithra.Simulation(g, j["undulator"], inputs.make_bunch(j["bunch_spec"], j["seed"]),
+                                precision=mithra.P32)
+        sim.set_tuning(stencil_variant=0, push_variant=1, push_ctas_per_sm=0)
+        sim.set_power_sampling(g["nz"] - 8, K + 4)
+        sims.append(sim)
+    b = mithra.Batch(stream=stream.cuda_stream)
+    for sim in sims:
+        b.add(sim)
+    b.step(4)  # warm-up (and graph capture)
+    b.sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    b.step(K)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_batch = e0.elapsed_time(e1)
+    p32 = [sim.read_power()[:, 0] for sim in sims[:args.plain_jobs]]
+    b.close()
+    for sim in sims:
+        sim.close()
+    # plain FP64, one job at a time
+    t_plain = 0.0
+    errs = []
+    for k, j in enumerate(jobs[:args.plain_jobs]):
+        g = dict(j["grid"], boundary=1)
+        sim = mithra.Simulation(g, j["undulator"], inputs.make_bunch(j["bunch_spec"], j["seed"]),
+                                precision=mithra.P64, stream=stream.cuda_stream)
+        sim.set_power_sampling(g["nz"] - 8, K + 4)
+        sim.step(4)
+        sim.sync()
+        e0.record(stream)
+        sim.step(K)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_plain += e0.elapsed_time(e1)
+        p64 = sim.read_power()[:, 0]
+        sim.close()
+        errs.append(float(np.abs(p32[k] - p64).max() / max(np.abs(p64).max(), 1e-300)))
+    per_job_plain = t_plain / args.plain_jobs * scale / 1e3
+    jobs_h_batch = 3600.0 * len(jobs) / (ms_batch * scale / 1e3)
+    jobs_h_plain = 3600.0 / per_job_plain
+    cells = sum(j["grid"]["nx"] * j["grid"]["ny"] * j["grid"]["nz"] for j in jobs)
+    parts = sum(j["bunch_spec"]["n"] for j in jobs)
+    return {"metric": "jobs/h, 64 uneven simulations of 1000 steps (c4)", "impl": "mithra",
+            "mode": "batch", "value": jobs_h_batch, "unit": "jobs/h", "higher_is_better": True,
+            "n_gpus": 1, "steps": K, "ms_per_step": ms_batch / K,
+            "plain_p64_jobs_per_h": jobs_h_plain, "speedup_vs_plain": jobs_h_batch / jobs_h_plain,
+            "cell_updates_per_s": cells * K / (ms_batch / 1e3),
+            "particle_pushes_per_s": parts * K / (ms_batch / 1e3),
+            "power_rel_err_p32_vs_p64": {"max": max(errs), "jobs": len(errs)},
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"c4: 64 grids 48^2x192..128^2x768, {cells} cells, "
+                                   f"{parts} particles, 64-512 particles per cell column",
+                       "timed": f"{K} steps per job, jobs/h scaled to 1000 steps",
+                       "plain": f"P64, {args.plain_jobs} jobs one after another"}}
+
+
+def run_serve(args) -> dict:
+    """c5: Poisson arrivals of design-sweep jobs served by continuous
+    batching, at the configured rate and at half of the measured capacity."""
+    import torch
+    from paper_1612_03310_gb300 import serve, inputs
+    free, _ = torch.cuda.mem_get_info()
+    budget = int(0.85 * free)
+    out = {}
+    runs = [("rate", args.rate)]
+    for name, rate in runs:
+        jobs = inputs.serve_jobs(int(rate * args.duration) + 1, rate)
+        srv = serve.Server(budget, max_slots=64, tick_steps=64)
+        st = srv.run(jobs, time_limit=args.duration)
+        st.pop("done")
+        out[name] = dict(st, offered_rate=rate)
+    cap = out["rate"]["completed"] / out["rate"]["wall_s"]
+    half = max(0.05, 0.5 * cap)
+    jobs = inputs.serve_jobs(int(half * args.duration) + 1, half, seed=6)
+    srv = serve.Server(budget, max_slots=64, tick_steps=64)
+    st = srv.run(jobs, time_limit=args.duration + 120.0)
+    st.pop("done")
+    out["half_capacity"] = dict(st, offered_rate=half)
+    r = out["rate"]
+    return {"metric": "jobs/h and p50/p99 latency, continuous batching (c5)", "impl": "mithra",
+            "mode": "serve", "value": r["jobs_per_hour"], "unit": "jobs/h",
+            "higher_is_better": True, "n_gpus": 1, "p50_s": r["p50_s"], "p99_s": r["p99_s"],
+            "dtype": "f32", "data": "synthetic", "runs": out,
+            "config": {"workload": "c5: Poisson arrivals, grids 32^2x128..160^2x1024, "
+                                   "1e3-4e6 particles, 500-5000 steps",
+                       "duration_s": args.duration, "hbm_budget": budget}}
+
+
 def main():
     args = parse()
+    if args.mode in ("batch", "serve") and args.impl == "mithra":
+        import torch
+        torch.cuda.set_device(0)
+        from paper_1612_03310_gb300 import build_lib
+        build_lib.build()
+        print(json.dumps(run_batch(args) if args.mode == "batch" else run_serve(args)))
+        return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))

@@ -142,6 +142,66 @@ def random_particles(seed: int, grid: dict, n: int, u_scale: float = 0.3,
                 q_macro=-1.0e-15)
 
 
+# ---------------------------------------------------------------------------
+# Design-sweep jobs for the batched (c4) and served (c5) forms, drawn directly
+# in rest-frame terms: frame Lorentz factor gamma0, undulator K, lambda_u =
+# 3 cm, 50 steps per rest-frame undulator period (c dt = lambda_u / gamma0 /
+# 50), dz = c dt / 0.95, dx = dy = 3 dz; the undulator fills the lab from
+# z' = 0 on (no entrance inside the run); transverse Gaussian bunch of
+# sigma = nx dx / 12 (cut at 3 sigma), uniform z over the central half,
+# rest-frame drift u_z in [0.2, 0.4].
+
+def _job(rng: np.random.Generator, nx: int, nz: int, n_particles: int, steps: int,
+         jid: int) -> dict:
+    c = 299792458.0
+    lam_u = 0.03
+    gamma0 = float(rng.uniform(15.0, 160.0))
+    K = float(rng.uniform(0.5, 2.0))
+    cdt = lam_u / gamma0 / 50.0
+    dz = cdt / 0.95
+    dx = 3.0 * dz
+    grid = centred_grid(dict(nx=nx, ny=nx, nz=nz, dx=dx, dy=dx, dz=dz, dt=cdt / c, n_sub=1,
+                             stencil=0, space_charge=1))
+    und = dict(gamma0=gamma0, lambda_u=lam_u, K=K, z_ent_lab=0.0, length_lab=0.0, fringe=1)
+    bunch = dict(n=int(n_particles), charge=10.0e-12, sigma_r=nx * dx / 12.0, trunc=3.0,
+                 z_lo=0.25 * nz * dz, z_hi=0.75 * nz * dz,
+                 uz_mean=float(rng.uniform(0.2, 0.4)), uz_sigma=1.0e-4, ut_sigma=0.0,
+                 bf=1.0e-3, kb=4.0 * np.pi * gamma0 / lam_u)
+    return dict(jid=jid, grid=grid, undulator=und, bunch_spec=bunch, steps=int(steps),
+                seed=int(rng.integers(1 << 30)))
+
+
+def batch_jobs(n_jobs: int = 64, steps: int = 1000, seed: int = 4) -> list[dict]:
+    """c4: grids nx = ny in {48, 64, 80, 96, 112, 128}, nz = 4 nx, with 64-512
+    particles per cell column (log-uniform)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    jobs = []
+    for k in range(n_jobs):
+        nx = int(rng.choice([48, 64, 80, 96, 112, 128]))
+        ppc = float(np.exp(rng.uniform(np.log(64.0), np.log(512.0))))
+        jobs.append(_job(rng, nx, 4 * nx, int(ppc * nx * nx), steps, k))
+    return jobs
+
+
+def serve_jobs(n_jobs: int, rate: float, seed: int = 5) -> list[dict]:
+    """c5: Poisson arrivals at `rate` jobs/s; nx = ny in [32, 160], nz in
+    [128, 1024] (multiples of 64), 1e3-4e6 particles (log-uniform), 500-5000
+    steps.  Each job carries its arrival time in seconds."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    t = 0.0
+    jobs = []
+    for k in range(n_jobs):
+        t += float(rng.exponential(1.0 / rate))
+        nx = int(rng.integers(32, 161))
+        nz = 64 * int(rng.integers(2, 17))
+        npart = int(np.exp(rng.uniform(np.log(1.0e3), np.log(4.0e6))))
+        steps = int(rng.integers(500, 5001))
+        j = _job(rng, nx, nz, npart, steps, k)
+        j["arrival"] = t
+        jobs.append(j)
+    return jobs
+
+
 def describe(name: str) -> str:
     w = WORKLOADS[name]
     g = w["grid"]
@@ -150,4 +210,4 @@ def describe(name: str) -> str:
 
 
 __all__ = ["WORKLOADS", "workload", "make_bunch", "random_grid", "random_fields",
-           "random_particles", "centred_grid", "describe"]
+           "random_particles", "centred_grid", "describe", "batch_jobs", "serve_jobs"]

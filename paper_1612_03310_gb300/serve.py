@@ -1,0 +1,164 @@
+"""Continuous-batching job server for FEL design sweeps.
+
+Jobs (grid, undulator, bunch, step count, arrival time) arrive over time.
+The server keeps every admitted job's fields and particles resident on the
+device and advances all of them together through one mithra batch (one
+captured CUDA graph per pair of steps).  Admission is first come, first
+served while the job's device footprint (mithra_footprint) fits the HBM
+budget and a slot is free; a job that does not fit waits, later smaller jobs
+may go ahead of it (first fit).  Each tick advances the batch by the steps
+until the next member finishes (at most tick_steps), so jobs retire exactly
+at their step count; a finished job's power record is read back, its memory
+freed, and its latency (arrival to completion) recorded.
+
+Time is the wall clock (clock="wall", arrivals in seconds) or the server's
+own step counter (clock="steps", arrivals in steps), the latter for
+reproducible schedules in tests.
+"""
+from __future__ import annotations
+
+import time
+from collections import deque
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import inputs, mithra
+
+
+@dataclass
+class JobState:
+    spec: dict
+    arrival: float
+    footprint: int = 0
+    sim: object = None
+    remaining: int = 0
+    t_admit: float | None = None
+    t_done: float | None = None
+    power: np.ndarray | None = None
+    fields: dict = field(default_factory=dict)
+
+
+class Server:
+    def __init__(self, hbm_budget: int, max_slots: int = 64, tick_steps: int = 64,
+                 precision: int = mithra.P32, tuning: dict | None = None,
+                 keep_fields: tuple = (), power_plane_from_top: int = 8,
+                 clock: str = "wall", sim_factory=None, batch_factory=None,
+                 footprint_fn=None):
+        self.budget = int(hbm_budget)
+        self.max_slots = int(max_slots)
+        self.tick_steps = int(tick_steps)
+        self.precision = precision
+        self.tuning = dict(stencil_variant=0, lz=0, push_variant=1, push_ctas_per_sm=0) \
+            if tuning is None else dict(tuning)
+        self.keep_fields = tuple(keep_fields)
+        self.kp_top = int(power_plane_from_top)
+        self.clock = clock
+        self._sim = sim_factory or mithra.Simulation
+        self._batch = batch_factory or mithra.Batch
+        self._fp = footprint_fn or mithra.footprint
+        self.used = 0
+        self.steps_done = 0
+        self.queue_depth: list[tuple[float, int]] = []
+
+    # -- helpers --------------------------------------------------------
+    def _now(self, t0: float) -> float:
+        return (time.perf_counter() - t0) if self.clock == "wall" else float(self.steps_done)
+
+    def _admit(self, js: JobState, batch, now: float):
+        spec = js.spec
+        g = dict(spec["grid"], boundary=1)
+        bunch = inputs.make_bunch(spec["bunch_spec"], spec["seed"])
+        sim = self._sim(g, spec["undulator"], bunch, precision=self.precision)
+        if self.tuning:
+            sim.set_tuning(**self.tuning)
+        sim.set_power_sampling(g["nz"] - self.kp_top, spec["steps"])
+        batch.add(sim)
+        js.sim = sim
+        js.remaining = spec["steps"]
+        js.t_admit = now
+        self.used += js.footprint
+
+    def _retire(self, js: JobState, batch, now: float):
+        js.power = js.sim.read_power()
+        for nm in self.keep_fields:
+            js.fields[nm] = js.sim.copy_field(nm)
+        batch.remove(js.sim)
+        js.sim.close()
+        js.sim = None
+        js.t_done = now
+        self.used -= js.footprint
+
+    # -- main loop ---------------------------------------------------------
+    def run(self, jobs: list[dict], time_limit: float | None = None) -> dict:
+        pending = deque(sorted((JobState(j, float(j.get("arrival", 0.0))) for j in jobs),
+                               key=lambda s: s.arrival))
+        for js in pending:
+            js.footprint = int(self._fp(dict(js.spec["grid"], boundary=1),
+                                        js.spec["bunch_spec"]["n"], self.precision))
+            if js.footprint > self.budget:
+                raise ValueError(f"job {js.spec.get('jid')} needs {js.footprint} B > budget")
+        queue: list[JobState] = []
+        active: list[JobState] = []
+        done: list[JobState] = []
+        batch = self._batch()
+        t0 = time.perf_counter()
+        try:
+            while pending or queue or active:
+                now = self._now(t0)
+                if time_limit is not None and now > time_limit:
+                    break
+                while pending and pending[0].arrival <= now:
+                    queue.append(pending.popleft())
+                for js in list(queue):  # first fit in arrival order
+                    if len(active) >= self.max_slots:
+                        break
+                    if self.used + js.footprint <= self.budget:
+                        queue.remove(js)
+                        self._admit(js, batch, now)
+                        active.append(js)
+                self.queue_depth.append((now, len(queue)))
+                if not active:
+                    if self.clock == "steps":
+                        self.steps_done = int(np.ceil(pending[0].arrival)) if pending else \
+                            self.steps_done
+                    elif pending:
+                        time.sleep(max(0.0, min(0.01, pending[0].arrival - now)))
+                    continue
+                tick = min([self.tick_steps] + [js.remaining for js in active])
+                if self.clock == "steps" and pending:
+                    # stop at the next arrival so that it is admitted on time
+                    tick = max(1, min(tick, int(np.ceil(pending[0].arrival)) - self.steps_done))
+                batch.step(tick)
+                batch.sync()
+                self.steps_done += tick
+                now = self._now(t0)
+                for js in active:
+                    js.remaining -= tick
+                for js in [a for a in active if a.remaining == 0]:
+                    self._retire(js, batch, now)
+                    active.remove(js)
+                    done.append(js)
+        finally:
+            for js in active:
+                try:
+                    batch.remove(js.sim)
+                    js.sim.close()
+                except Exception:
+                    pass
+            batch.close()
+        wall = time.perf_counter() - t0
+        return self.stats(done, queue + active + list(pending), wall)
+
+    def stats(self, done: list[JobState], left: list[JobState], wall: float) -> dict:
+        lat = np.array([js.t_done - js.arrival for js in done]) if done else np.array([])
+        cells = sum(js.spec["grid"]["nx"] * js.spec["grid"]["ny"] * js.spec["grid"]["nz"] *
+                    js.spec["steps"] for js in done)
+        return dict(
+            completed=len(done), unfinished=len(left), wall_s=wall,
+            jobs_per_hour=3600.0 * len(done) / wall if wall > 0 else 0.0,
+            p50_s=float(np.percentile(lat, 50)) if lat.size else None,
+            p99_s=float(np.percentile(lat, 99)) if lat.size else None,
+            cell_updates_per_s=cells / wall if wall > 0 else 0.0,
+            max_queue=max((q for _, q in self.queue_depth), default=0),
+            done=done)

@@ -1,0 +1,106 @@
+"""Host logic of the continuous-batching server (no GPU): admission by
+footprint and slots, first fit in arrival order, ticks that stop at the next
+completion, exact step counts per job, latency bookkeeping; with fake
+simulations and batch."""
+import numpy as np
+import pytest
+
+from paper_1612_03310_gb300 import inputs, serve
+
+
+class FakeSim:
+    log = []
+
+    def __init__(self, grid, und, bunch, precision=1):
+        self.grid = grid
+        self.steps = 0
+        self.closed = False
+
+    def set_tuning(self, **kw):
+        pass
+
+    def set_power_sampling(self, kp, cap):
+        self.cap = cap
+
+    def read_power(self):
+        return np.zeros((self.steps, 3))
+
+    def copy_field(self, nm):
+        return np.zeros(1)
+
+    def close(self):
+        self.closed = True
+
+
+class FakeBatch:
+    def __init__(self):
+        self.members = []
+        self.ticks = []
+
+    def add(self, s):
+        assert len(self.members) < 64
+        self.members.append(s)
+
+    def remove(self, s):
+        self.members.remove(s)
+
+    def step(self, n):
+        self.ticks.append((n, len(self.members)))
+        for s in self.members:
+            s.steps += n
+
+    def sync(self):
+        pass
+
+    def close(self):
+        pass
+
+
+def make_jobs(arrivals, steps, sizes):
+    rng = np.random.default_rng(0)
+    jobs = []
+    for k, (a, st, nx) in enumerate(zip(arrivals, steps, sizes)):
+        j = inputs._job(rng, nx, 64, 1000, st, k)
+        j["arrival"] = a
+        jobs.append(j)
+    return jobs
+
+
+def run(jobs, budget, slots=8, tick=16):
+    b = FakeBatch()
+    srv = serve.Server(budget, max_slots=slots, tick_steps=tick, clock="steps",
+                       sim_factory=FakeSim, batch_factory=lambda: b,
+                       footprint_fn=lambda g, n, p: g["nx"] * 1000)
+    return srv.run(jobs), b
+
+
+def test_exact_steps_and_latency():
+    jobs = make_jobs([0, 0, 10, 40], [50, 30, 20, 5], [32, 32, 32, 32])
+    st, b = run(jobs, budget=10 ** 9)
+    assert st["completed"] == 4 and st["unfinished"] == 0
+    for js in st["done"]:
+        assert js.power.shape[0] == js.spec["steps"]  # retired exactly at its count
+        assert js.t_done - js.t_admit == js.spec["steps"]  # no queueing: never waited
+    assert all(n <= 16 for n, _ in b.ticks)
+
+
+def test_admission_by_footprint_first_fit():
+    # budget fits one 64-job or two 32-jobs at a time
+    jobs = make_jobs([0, 0, 0], [20, 20, 20], [64, 32, 32])
+    st, b = run(jobs, budget=64 * 1000)
+    done = {js.spec["jid"]: js for js in st["done"]}
+    assert done[0].t_admit == 0
+    assert done[1].t_admit >= done[0].t_done and done[2].t_admit >= done[0].t_done
+    assert max(m for _, m in b.ticks) <= 2
+
+
+def test_slot_limit():
+    jobs = make_jobs([0] * 5, [10] * 5, [32] * 5)
+    st, b = run(jobs, budget=10 ** 9, slots=2)
+    assert max(m for _, m in b.ticks) == 2 and st["completed"] == 5
+
+
+def test_oversized_job_rejected():
+    jobs = make_jobs([0], [10], [128])
+    with pytest.raises(ValueError):
+        run(jobs, budget=1000)
