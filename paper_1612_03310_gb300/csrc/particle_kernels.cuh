@@ -122,18 +122,27 @@ __device__ inline double rsqrt_nr(double x) {
   return y;
 }
 
+// 1/sqrt(x) in the momentum type: FP64 as above; FP32 from the rsqrtf seed
+// with one FP32 Newton-Raphson step.
+__device__ inline float rsqrt_u(float x) {
+  const float y = rsqrtf(x);
+  return y * (1.5f - 0.5f * x * y * y);
+}
+__device__ inline double rsqrt_u(double x) { return rsqrt_nr<double>(x); }
+
 // Boris rotation and kicks (Eq. BorisScheme) for charge-to-mass qm folded
-// into h = qm dtb / (2c) and an = qm dtb / 2, in the momentum type U; gamma
-// of t1 in FP64.
+// into h = qm dtb / (2c) and an = qm dtb / 2, in the momentum type U.  The
+// gamma of the half-kicked momentum t1, which only sets the rotation angle,
+// is taken in U as well; the gamma that moves the particle is recomputed in
+// FP64 by the caller.
 template <typename T, typename U>
 __device__ inline void boris(const PicP<T>& p, U u[3], const T Ef[3], const T Bf[3]) {
   const U h = (U)p.h;
   const U E[3] = {(U)Ef[0], (U)Ef[1], (U)Ef[2]};
   const U B[3] = {(U)Bf[0], (U)Bf[1], (U)Bf[2]};
   const U t1x = u[0] + h * E[0], t1y = u[1] + h * E[1], t1z = u[2] + h * E[2];
-  const double ig1 =
-      rsqrt_nr<U>(1.0 + (double)t1x * t1x + (double)t1y * t1y + (double)t1z * t1z);
-  const U al = (U)(p.an * ig1);
+  const U ig1 = rsqrt_u((U)1 + t1x * t1x + t1y * t1y + t1z * t1z);
+  const U al = (U)p.an * ig1;
   const U t2x = t1x + al * (t1y * B[2] - t1z * B[1]);
   const U t2y = t1y + al * (t1z * B[0] - t1x * B[2]);
   const U t2z = t1z + al * (t1x * B[1] - t1y * B[0]);
