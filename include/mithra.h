@@ -88,7 +88,10 @@ typedef struct {
     double dt;             /* field time step; particle step dt/n_sub */
     int32_t n_sub;         /* Boris sub-steps per field step, >= 1 */
     int32_t stencil;       /* 0 = NSFD (Eq. NSFDCoefficient), 1 = standard */
-    int32_t boundary;      /* 1 = first-order Mur (the only value accepted) */
+    int32_t boundary;      /* 1 = first-order Mur on every boundary vertex (Sec.
+                              "First Order ABCs"); 2 = second-order Mur (Sec.
+                              "Second Order ABCs") on face vertices, first order
+                              on edge and corner vertices */
     int32_t space_charge;  /* 0: phi is held at zero */
 } mithra_grid;
 
@@ -204,6 +207,36 @@ mithra_status mithra_kernel_times(mithra_sim* sim, double* ms, int64_t* launches
                                   int32_t max_kernels, int32_t* n_kernels);
 const char* mithra_kernel_name(int32_t kernel);
 
+/* Bunch sampling (the input group "bunch-sampling": mean position, mean
+ * momentum, position spread and momentum spread along x, y, z) and the
+ * bunching factor |<exp(i k_b z)>| over the particles not lost, at the
+ * current state (positions r^{n+1/2}, momenta u^n).  out (host, 14 doubles):
+ * out[0..2] mean x, y, z [m]; out[3..5] mean u_x, u_y, u_z; out[6..8] rms
+ * spread of x, y, z; out[9..11] rms spread of u_x, u_y, u_z; out[12] the
+ * bunching factor at k_b [1/m] (rest frame); out[13] the number of particles
+ * counted.  FP64 sums in a fixed order; waits for the stream. */
+mithra_status mithra_bunch_stats(mithra_sim* sim, double k_b, double* out);
+
+/* Frequency-resolved radiated power (FEL-OUTPUT radiation-power with
+ * wavelengths).  mithra_set_spectrum starts running Fourier sums of the lab
+ * fields E'_x, E'_y, B'_x, B'_y (the transformation of mithra_radiated_power)
+ * at the interior vertices of vertex plane k_plane, one set per lab
+ * wavelength lambda_lab[m] (host array, metres, n_wavelengths <= 64; 0 stops
+ * and frees them): every following step adds the sample at lab time
+ * t' = gamma0 (t + beta0 z_p / c), t = (n + 1/2) dt, weighted by
+ * exp(-i w_m t') gamma0 dt, where w_m = 2 pi c (1 - beta0) / lambda_lab[m] is
+ * the angular frequency at which a forward lab wave of that wavelength
+ * passes the plane (which moves with the rest frame).  Device memory:
+ * 64 B x (nx-2)(ny-2) per wavelength.  MITHRA_EBUSY while the sim is in a
+ * batch.  mithra_read_spectrum writes, per wavelength, the energy through
+ * the plane per unit of that angular frequency so far [J s],
+ *   dW/dw = (1/pi) sum Re(E'~x B'~y* - E'~y B'~x*) dx dy / mu0,
+ * (dW_domega: host, n_wavelengths doubles; may be NULL) and the number of
+ * samples taken; it waits for the stream. */
+mithra_status mithra_set_spectrum(mithra_sim* sim, int32_t k_plane, int32_t n_wavelengths,
+                                  const double* lambda_lab);
+mithra_status mithra_read_spectrum(mithra_sim* sim, double* dW_domega, int64_t* n_samples);
+
 /* Launch choices (the autotuner's knobs).  Results do not depend on them
  * beyond floating-point rounding.
  *   stencil_variant 0: the direct potential update, one thread per vertex with
@@ -216,12 +249,18 @@ const char* mithra_kernel_name(int32_t kernel);
  *     tiles with the potentials, E/B and the deposit block in shared memory.
  *   push_ctas_per_sm: persistent CTAs per SM of push variant 1 (0: as many as
  *     fit).
+ *   push_sparse_below: push variant 1 only; a tile holding fewer particles
+ *     than this skips the shared-memory staging: one warp pushes its
+ *     particles with E and B from global memory and deposits with global
+ *     atomics, after the CTAs have taken every denser tile (0: every tile is
+ *     staged).  Takes effect from the tile list of the next re-sort.
  * Variant 1 of both is the default when the driver provides TMA tensor maps. */
 typedef struct {
     int32_t stencil_variant;
     int32_t lz;
     int32_t push_variant;
     int32_t push_ctas_per_sm;
+    int32_t push_sparse_below;
 } mithra_tuning;
 
 mithra_status mithra_set_tuning(mithra_sim* sim, const mithra_tuning* tuning);

@@ -50,7 +50,7 @@ class _Grid(C.Structure):
                 ("dx", C.c_double), ("dy", C.c_double), ("dz", C.c_double),
                 ("x0", C.c_double), ("y0", C.c_double), ("z0", C.c_double),
                 ("dt", C.c_double), ("n_sub", C.c_int32), ("stencil", C.c_int32),
-                ("space_charge", C.c_int32)]
+                ("space_charge", C.c_int32), ("boundary", C.c_int32)]
 
 
 class _Und(C.Structure):
@@ -86,6 +86,11 @@ def lib():
         _lib.orc_radiated_power.argtypes = [C.POINTER(_Grid), C.c_double, dp, dp, C.c_int32,
                                             C.c_double, dp, dp, dp]
         _lib.orc_constants.argtypes = [dp]
+        _lib.orc_bunch_stats.argtypes = [C.c_int64, dp, dp, dp, dp, dp, dp, ip, C.c_double, dp]
+        _lib.orc_spectrum_accumulate.argtypes = [C.POINTER(_Grid), C.c_double, dp, dp,
+                                                 C.c_int32, C.c_double, C.c_double, C.c_int32,
+                                                 dp, dp]
+        _lib.orc_spectrum_density.argtypes = [C.POINTER(_Grid), C.c_int32, dp, dp]
     return _lib
 
 
@@ -108,7 +113,7 @@ def make_grid(g: dict) -> _Grid:
     return _Grid(int(g["nx"]), int(g["ny"]), int(g["nz"]), g["dx"], g["dy"], g["dz"],
                  g.get("x0", 0.0), g.get("y0", 0.0), g.get("z0", 0.0), g["dt"],
                  int(g.get("n_sub", 1)), int(g.get("stencil", 0)),
-                 int(g.get("space_charge", 1)))
+                 int(g.get("space_charge", 1)), int(g.get("boundary", 1)))
 
 
 def make_und(u: dict | None) -> _Und:
@@ -161,6 +166,36 @@ def radiated_power(g: dict, gamma0: float, E, B, k_p: int, t: float):
     return float(p[0]), float(tl[0]), float(zl[0])
 
 
+def bunch_stats(x, y, z, ux, uy, uz, lost, k_b: float) -> np.ndarray:
+    """Means, rms spreads and bunching factor (orc_bunch_stats)."""
+    a = [np.ascontiguousarray(v, dtype=np.float64) for v in (x, y, z, ux, uy, uz)]
+    lo = np.ascontiguousarray(lost, dtype=np.int32)
+    out = np.zeros(14)
+    lib().orc_bunch_stats(a[0].size, *[_p(v) for v in a], _p(lo), float(k_b), _p(out))
+    return out
+
+
+def spectrum_accumulate(g: dict, gamma0: float, E, B, k_p: int, t_lab: float, dt_lab: float,
+                        omega, acc: np.ndarray):
+    om = np.ascontiguousarray(omega, dtype=np.float64)
+    lib().orc_spectrum_accumulate(C.byref(make_grid(g)), gamma0, _p(E), _p(B), int(k_p), t_lab,
+                                  dt_lab, om.size, _p(om), _p(acc))
+
+
+def spectrum_density(g: dict, n_freq: int, acc: np.ndarray) -> np.ndarray:
+    out = np.zeros(n_freq)
+    lib().orc_spectrum_density(C.byref(make_grid(g)), int(n_freq), _p(acc), _p(out))
+    return out
+
+
+def observed_omega(lambda_lab, gamma0: float) -> np.ndarray:
+    """Angular frequency at which a forward lab wave of wavelength lambda_lab
+    passes a plane moving with the rest frame: 2 pi c (1 - beta0) / lambda."""
+    b0 = np.sqrt(1.0 - 1.0 / (gamma0 * gamma0))
+    c = constants()["c"]
+    return 2.0 * np.pi * c * (1.0 - b0) / np.asarray(lambda_lab, dtype=np.float64)
+
+
 @dataclass
 class PowerSample:
     step: int
@@ -210,6 +245,30 @@ class OracleSim:
         self.t0 = float(t0)
         self.n = 0
         self.power: list[PowerSample] = []
+        self.spec_plane = None
+        self.spec_omega = None
+        self.spec_acc = None
+        self.spec_samples = 0
+
+    def set_spectrum(self, k_plane: int, lambda_lab):
+        """Running Fourier sums of the lab fields at plane k_plane, one set
+        per lab wavelength, from the next step on (orc_spectrum_accumulate)."""
+        g0 = self.u["gamma0"] if self.u else 1.0e3
+        self.spec_plane = int(k_plane)
+        self.spec_omega = observed_omega(lambda_lab, g0)
+        nv = (self.g["nx"] - 2) * (self.g["ny"] - 2)
+        self.spec_acc = np.zeros(self.spec_omega.size * nv * 8)
+        self.spec_samples = 0
+
+    def spectrum(self) -> np.ndarray:
+        """Energy per unit observed angular frequency so far [J s]."""
+        out = np.zeros(self.spec_omega.size)
+        lib().orc_spectrum_density(C.byref(self._G), self.spec_omega.size, _p(self.spec_acc),
+                                   _p(out))
+        return out
+
+    def bunch_stats(self, k_b: float) -> np.ndarray:
+        return bunch_stats(self.x, self.y, self.z, self.ux, self.uy, self.uz, self.lost, k_b)
 
     def set_potentials(self, prev: np.ndarray, cur: np.ndarray):
         self.prev[:] = prev
@@ -234,10 +293,19 @@ class OracleSim:
                 C.byref(self._G), C.byref(self._U), self.q_macro, th, _p(self.E), _p(self.B),
                 self.np, _p(self.x), _p(self.y), _p(self.z), _p(self.ux), _p(self.uy),
                 _p(self.uz), _p(self.lost), _p(self.src_next)))
+            g0 = self.u["gamma0"] if self.u else 1.0e3
             if power_plane is not None:
-                p, tl, zl = radiated_power(self.g, self.u["gamma0"] if self.u else 1.0e3,
-                                           self.E, self.B, power_plane, th)
+                p, tl, zl = radiated_power(self.g, g0, self.E, self.B, power_plane, th)
                 self.power.append(PowerSample(self.n, p, tl, zl))
+            if self.spec_plane is not None:
+                b0 = np.sqrt(1.0 - 1.0 / (g0 * g0))
+                zp = self.g.get("z0", 0.0) + self.spec_plane * self.g["dz"]
+                t_lab = g0 * (th + b0 * zp / constants()["c"])
+                L.orc_spectrum_accumulate(C.byref(self._G), g0, _p(self.E), _p(self.B),
+                                          self.spec_plane, t_lab, g0 * self.g["dt"],
+                                          self.spec_omega.size, _p(self.spec_omega),
+                                          _p(self.spec_acc))
+                self.spec_samples += 1
             # rotate: (n-1, n, n+1) -> (n, n+1, scratch)
             self.prev, self.cur, self.nxt = self.cur, self.nxt, self.prev
             self.src, self.src_next = self.src_next, self.src

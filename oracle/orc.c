@@ -121,9 +121,46 @@ static void update_interior(const orc_grid* g, const double co[6], const double*
 static inline int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
 
 /* First-order Mur condition (Sec. "First Order ABCs"): for a boundary vertex b
+ * (every boundary vertex, or with boundary == 2 the edge and corner vertices)
  * with nearest interior vertex q at distance d,
  *   xi_b^{n+1} = beta0 (xi_b^{n-1} + xi_q^{n+1}) + beta1 (xi_b^n + xi_q^n) - xi_q^{n-1}
  * with beta0 = (c dt - d)/(c dt + d), beta1 = 2 d/(c dt + d). */
+/* Second-order Mur condition (Sec. "Second Order ABCs") at a face vertex b
+ * (exactly one axis on the boundary), written for the face normal to axis a
+ * as the paper writes it for z: with q the interior neighbour along a, dn
+ * the spacing along a, and t1, t2 the two tangential axes (r_t = c dt / d_t),
+ *   xi_b^{n+1} = g0 xi_b^{n-1} + g1 xi_b^n - xi_q^{n-1} + g1 xi_q^n + g0 xi_q^{n+1}
+ *              + g5 (xi_q,t1+ + xi_q,t1- + xi_b,t1+ + xi_b,t1-)^n
+ *              + g7 (xi_q,t2+ + xi_q,t2- + xi_b,t2+ + xi_b,t2-)^n,
+ *   g0 = (c dt - dn)/(c dt + dn),  g1 = dn (2 - r_t1^2 - r_t2^2)/(c dt + dn),
+ *   g5 = r_t1^2 dn / (2 (c dt + dn)),  g7 = r_t2^2 dn / (2 (c dt + dn)).
+ * These coefficients are those of the Engquist-Majda form with +c/2 in front
+ * of the tangential second derivatives (the printed PDE's -c/2 is a sign
+ * slip; the printed coefficients follow from +c/2). */
+static double mur2_face(const orc_grid* g, const double* pm, const double* p, const double* pn,
+                        int i, int j, int k, int qi, int qj, int qk) {
+    const double cdt = ORC_C * g->dt;
+    const double d[3] = {g->dx, g->dy, g->dz};
+    const int a = (qi != i) ? 0 : (qj != j) ? 1 : 2;  /* normal axis */
+    const int t1 = (a == 0) ? 1 : 0, t2 = (a == 2) ? 1 : 2;
+    const double dn = d[a];
+    const double r1 = cdt / d[t1], r2 = cdt / d[t2];
+    const double g0 = (cdt - dn) / (cdt + dn);
+    const double g1 = dn * (2.0 - r1 * r1 - r2 * r2) / (cdt + dn);
+    const double g5 = r1 * r1 * dn / (2.0 * (cdt + dn));
+    const double g7 = r2 * r2 * dn / (2.0 * (cdt + dn));
+    const int64_t b = ix(g, i, j, k), q = ix(g, qi, qj, qk);
+    int e1[3] = {0, 0, 0}, e2[3] = {0, 0, 0};
+    e1[t1] = 1;
+    e2[t2] = 1;
+    double v = g0 * pm[b] + g1 * p[b] - pm[q] + g1 * p[q] + g0 * pn[q];
+    v += g5 * (p[ix(g, qi + e1[0], qj + e1[1], qk + e1[2])] + p[ix(g, qi - e1[0], qj - e1[1], qk - e1[2])]
+             + p[ix(g, i + e1[0], j + e1[1], k + e1[2])] + p[ix(g, i - e1[0], j - e1[1], k - e1[2])]);
+    v += g7 * (p[ix(g, qi + e2[0], qj + e2[1], qk + e2[2])] + p[ix(g, qi - e2[0], qj - e2[1], qk - e2[2])]
+             + p[ix(g, i + e2[0], j + e2[1], k + e2[2])] + p[ix(g, i - e2[0], j - e2[1], k - e2[2])]);
+    return v;
+}
+
 static void mur_boundary(const orc_grid* g, const double* pm, const double* p, double* pn) {
     const int nx = g->nx, ny = g->ny, nz = g->nz;
     const double cdt = ORC_C * g->dt;
@@ -133,6 +170,11 @@ static void mur_boundary(const orc_grid* g, const double* pm, const double* p, d
                 int onb = (i == 0 || i == nx - 1 || j == 0 || j == ny - 1 || k == 0 || k == nz - 1);
                 if (!onb) continue;
                 int qi = clampi(i, 1, nx - 2), qj = clampi(j, 1, ny - 2), qk = clampi(k, 1, nz - 2);
+                int naxes = (qi != i) + (qj != j) + (qk != k);
+                if (g->boundary == 2 && naxes == 1) {
+                    pn[ix(g, i, j, k)] = mur2_face(g, pm, p, pn, i, j, k, qi, qj, qk);
+                    continue;
+                }
                 double d2 = 0.0;
                 if (qi != i) d2 += g->dx * g->dx;
                 if (qj != j) d2 += g->dy * g->dy;
@@ -452,4 +494,75 @@ void orc_radiated_power(const orc_grid* g, double gamma0, const double* E, const
     *p_lab = sum;
     *t_lab = gamma0 * (t + b0 * zp / ORC_C);
     *z_lab = gamma0 * (zp + b0 * ORC_C * t);
+}
+
+/* ---------------------------------------------------------------------- */
+/* Bunch sampling and bunching factor. */
+void orc_bunch_stats(int64_t np, const double* x, const double* y, const double* z,
+                     const double* ux, const double* uy, const double* uz,
+                     const int32_t* lost, double k_b, double out[14]) {
+    const double* v[6] = {x, y, z, ux, uy, uz};
+    double s1[6] = {0, 0, 0, 0, 0, 0}, s2[6] = {0, 0, 0, 0, 0, 0};
+    double re = 0.0, im = 0.0, n = 0.0;
+    for (int64_t p = 0; p < np; ++p) {
+        if (lost[p]) continue;
+        n += 1.0;
+        for (int a = 0; a < 6; ++a) {
+            s1[a] += v[a][p];
+            s2[a] += v[a][p] * v[a][p];
+        }
+        re += cos(k_b * z[p]);
+        im += sin(k_b * z[p]);
+    }
+    for (int a = 0; a < 6; ++a) {
+        double m = n > 0 ? s1[a] / n : 0.0;
+        double var = n > 0 ? s2[a] / n - m * m : 0.0;
+        out[a] = m;
+        out[6 + a] = var > 0 ? sqrt(var) : 0.0;
+    }
+    out[12] = n > 0 ? sqrt(re * re + im * im) / n : 0.0;
+    out[13] = n;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Running Fourier sums of the lab fields at a plane. */
+void orc_spectrum_accumulate(const orc_grid* g, double gamma0, const double* E,
+                             const double* B, int32_t k_p, double t_lab, double dt_lab,
+                             int32_t n_freq, const double* omega, double* acc) {
+    const int64_t n = ncell(g);
+    const int64_t nv = (int64_t)(g->nx - 2) * (g->ny - 2);
+    const double b0 = sqrt(1.0 - 1.0 / (gamma0 * gamma0));
+    for (int m = 0; m < n_freq; ++m) {
+        const double c = cos(omega[m] * t_lab) * dt_lab, s = -sin(omega[m] * t_lab) * dt_lab;
+        for (int j = 1; j < g->ny - 1; ++j) {
+            for (int i = 1; i < g->nx - 1; ++i) {
+                int64_t q = ix(g, i, j, k_p);
+                double Ex = E[q], Ey = E[n + q];
+                double Bx = B[q], By = B[n + q];
+                double F[4];
+                F[0] = gamma0 * (Ex + b0 * ORC_C * By);
+                F[1] = gamma0 * (Ey - b0 * ORC_C * Bx);
+                F[2] = gamma0 * (Bx - b0 * Ey / ORC_C);
+                F[3] = gamma0 * (By + b0 * Ex / ORC_C);
+                double* a = acc + ((int64_t)m * nv + (int64_t)(j - 1) * (g->nx - 2) + (i - 1)) * 8;
+                for (int f = 0; f < 4; ++f) {
+                    a[2 * f] += F[f] * c;
+                    a[2 * f + 1] += F[f] * s;
+                }
+            }
+        }
+    }
+}
+
+void orc_spectrum_density(const orc_grid* g, int32_t n_freq, const double* acc, double* out) {
+    const int64_t nv = (int64_t)(g->nx - 2) * (g->ny - 2);
+    for (int m = 0; m < n_freq; ++m) {
+        double sum = 0.0;
+        for (int64_t v = 0; v < nv; ++v) {
+            const double* a = acc + ((int64_t)m * nv + v) * 8;
+            /* Re(Ex By*) - Re(Ey Bx*) */
+            sum += (a[0] * a[6] + a[1] * a[7]) - (a[2] * a[4] + a[3] * a[5]);
+        }
+        out[m] = sum * g->dx * g->dy / (ORC_MU0 * ORC_PI);
+    }
 }

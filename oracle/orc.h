@@ -34,6 +34,8 @@ typedef struct {
     int32_t n_sub;          /* Boris sub-steps per field step, dt_b = dt/n_sub */
     int32_t stencil;        /* 0 = NSFD (Sec. "Numerical Dispersion"), 1 = standard */
     int32_t space_charge;   /* 0: phi is held at zero */
+    int32_t boundary;       /* 1: first-order Mur everywhere; 2: second-order Mur on
+                               face vertices, first order on edges and corners */
 } orc_grid;
 
 typedef struct {
@@ -52,7 +54,8 @@ int orc_coefficients(const orc_grid* g, double out[6]);
 
 /* One potential update: next = level n+1 from prev (n-1), cur (n) and the
  * sources src (J^n, rho^{n+1/2}).  Interior by Eq. updateEquation, the six
- * faces (and edges/corners) by the first-order Mur condition. */
+ * faces by the Mur condition of order g->boundary (Sec. "First Order ABCs",
+ * Sec. "Second Order ABCs"), edges and corners by the first-order one. */
 void orc_potential_step(const orc_grid* g, const double* prev, const double* cur,
                         const double* src, double* next);
 
@@ -93,6 +96,31 @@ int64_t orc_mark_lost(const orc_grid* g, int64_t np, const double* x, const doub
  * (rest frame).  Writes P [W], the lab time and the lab position of the plane. */
 void orc_radiated_power(const orc_grid* g, double gamma0, const double* E, const double* B,
                         int32_t k_p, double t, double* p_lab, double* t_lab, double* z_lab);
+
+/* Bunch sampling (Sec. "bunch-sampling" of the input groups: mean position,
+ * mean momentum, position spread and momentum spread along x, y, z) and the
+ * bunching factor |<exp(i k_b z)>| over the particles not lost.
+ * out[0..2] mean x, y, z; out[3..5] mean ux, uy, uz; out[6..8] rms spread of
+ * x, y, z; out[9..11] rms spread of ux, uy, uz; out[12] bunching factor;
+ * out[13] number of particles counted.  Sums run serially in index order. */
+void orc_bunch_stats(int64_t np, const double* x, const double* y, const double* z,
+                     const double* ux, const double* uy, const double* uz,
+                     const int32_t* lost, double k_b, double out[14]);
+
+/* Frequency-resolved radiated power (FEL-OUTPUT radiation-power with
+ * wavelengths).  The lab fields at interior vertices of plane k_p (the
+ * transformation of orc_radiated_power) sampled at lab time t_lab are added
+ * to running Fourier sums at the observed angular frequencies omega[m]:
+ *   acc[((m * nv) + v) * 8 + 2f + {0,1}] += F_f (cos, -sin)(omega[m] t_lab) dt_lab,
+ * F = (E'_x, E'_y, B'_x, B'_y), v = (j-1)(nx-2) + (i-1). */
+void orc_spectrum_accumulate(const orc_grid* g, double gamma0, const double* E,
+                             const double* B, int32_t k_p, double t_lab, double dt_lab,
+                             int32_t n_freq, const double* omega, double* acc);
+
+/* Energy through the plane per unit observed angular frequency from the
+ * running sums (Parseval for real signals):
+ *   out[m] = (1/pi) sum_v Re(E~x B~y* - E~y B~x*) dx dy / mu0   [J s]. */
+void orc_spectrum_density(const orc_grid* g, int32_t n_freq, const double* acc, double* out);
 
 /* Physical constants the oracle uses: c, e, m_e, eps0, mu0. */
 void orc_constants(double out[5]);

@@ -9,7 +9,10 @@ in a JSON file so that later runs of the same shape skip the search.
 
 The candidates: the direct stencil and the marching stencil with a range of
 plane runs per CTA; the per-particle push and the tiled push with 1 .. max
-persistent CTAs per SM.
+persistent CTAs per SM, then, for the tiled push with the best CTA count, a
+range of sparse-tile thresholds (tiles below it skip the shared-memory
+staging).  A threshold only acts from the next re-sort, so every push
+candidate gets one untimed step before it is timed.
 """
 from __future__ import annotations
 
@@ -58,7 +61,7 @@ def device_name() -> str:
 def key_of(grid: dict, n_particles: int, precision: int) -> str:
     # particle counts are bucketed by powers of two
     nb = max(int(n_particles), 1).bit_length()
-    return (f"{device_name()}|p{precision}|{grid['nx']}x{grid['ny']}x{grid['nz']}|"
+    return (f"v2|{device_name()}|p{precision}|{grid['nx']}x{grid['ny']}x{grid['nz']}|"
             f"n2^{nb}|sub{grid.get('n_sub', 1)}")
 
 
@@ -79,10 +82,20 @@ def stencil_candidates(grid: dict) -> list[dict]:
 
 
 def push_candidates(max_per_sm: int = 3) -> list[dict]:
-    out = [dict(push_variant=0, push_ctas_per_sm=0)]
+    out = [dict(push_variant=0, push_ctas_per_sm=0, push_sparse_below=0)]
     for c in range(1, max_per_sm + 1):
-        out.append(dict(push_variant=1, push_ctas_per_sm=c))
+        out.append(dict(push_variant=1, push_ctas_per_sm=c, push_sparse_below=0))
     return out
+
+
+SPARSE_THRESHOLDS = (16, 32, 64, 128)
+
+
+def sparse_candidates(best: dict) -> list[dict]:
+    """Sparse-tile thresholds on top of the best tiled-push choice."""
+    if best.get("push_variant") != 1:
+        return []
+    return [dict(best, push_sparse_below=s) for s in SPARSE_THRESHOLDS]
 
 
 def tune(grid: dict, undulator: dict | None, bunch: dict | None, precision: int,
@@ -110,17 +123,24 @@ def tune(grid: dict, undulator: dict | None, bunch: dict | None, precision: int,
             trials.append(dict(c, ms=ms))
             if ms < best_st_ms:
                 best_st, best_st_ms = c, ms
-        best_pu, best_pu_ms = dict(push_variant=0, push_ctas_per_sm=0), float("inf")
+        best_pu = dict(push_variant=0, push_ctas_per_sm=0, push_sparse_below=0)
+        best_pu_ms = float("inf")
         if n > 0:
-            for c in push_candidates():
+            def trial(c):
+                nonlocal best_pu, best_pu_ms
                 try:
                     sim.set_tuning(**c)
                 except mithra.MithraError:
-                    continue
+                    return
+                sim.step(1)  # the re-sort applies the candidate's tile lists
                 ms = _kernel_ms(sim, steps)["push"]
                 trials.append(dict(c, ms=ms))
                 if ms < best_pu_ms:
                     best_pu, best_pu_ms = c, ms
+            for c in push_candidates():
+                trial(c)
+            for c in sparse_candidates(best_pu):
+                trial(c)
     finally:
         sim.close()
     best = dict(best_st or dict(stencil_variant=0, lz=0))

@@ -90,9 +90,11 @@ struct StepState {
   long long n;          // field steps completed
   long long n_lost;     // particles lost so far
   int err;              // bit 0: NaN/Inf in a reduction; bit 1: a bounded wait gave up
-  int n_tiles;          // non-empty particle tiles listed by the last scan
-  int work;             // next entry of the tile list to hand out
-  int pad;
+  int n_tiles;          // dense tiles listed by the last scan (entries 0 .. n_tiles-1)
+  int work;             // next dense entry of the tile list to hand out
+  int n_sparse;         // sparse tiles, listed after the dense ones
+  int work_sparse;      // next sparse entry to hand out
+  int pad[2];
 };
 
 // Coefficients of the potential update in increment form (r_l = c dt / d_l,
@@ -106,6 +108,11 @@ struct StencilP {
   T rxA, rxB, ryA, ryB, rz2;  // rx^2 A, rx^2 (1 - 2A), ry^2 A, ry^2 (1 - 2A), rz^2
   T sA, sphi;                 // (c dt)^2 mu0 and (c dt)^2 / eps0
   T mb0[8];
+  // second-order Mur on face vertices (mur2 != 0): m2[a][0], m2[a][1] =
+  // (c dt / d_t)^2 d_a / (2 (c dt + d_a)) for the face normal to axis a and
+  // its tangential axes t in the order (y, z), (x, z), (x, y)
+  T m2[3][2];
+  int mur2;
   int space_charge;
 };
 

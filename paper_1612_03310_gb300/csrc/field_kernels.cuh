@@ -1,5 +1,5 @@
-// field_kernels.cuh -- potential update (Eq. updateEquation) with the
-// first-order Mur boundary (Sec. "First Order ABCs") fused in, E/B at the
+// field_kernels.cuh -- potential update (Eq. updateEquation) with the Mur
+// boundary (Sec. "First Order ABCs", "Second Order ABCs") fused in, E/B at the
 // vertices (Sec. "Field Evaluation"), radiated power and field copy-out.
 //
 // Storage of the leapfrog: the newest level psi^{n+1} in one of two
@@ -35,36 +35,33 @@ __device__ inline T mur_beta0(const StencilP<T>& p, int mask) {
   }
 }
 
-// Mur update of the boundary vertices whose nearest interior vertex is c
-// (i, j, k).  With beta0 + beta1 = 1 the first-order condition
-//   xi_b^{n+1} = b0 (xi_b^{n-1} + xi_c^{n+1}) + b1 (xi_b^n + xi_c^n) - xi_c^{n-1}
-// becomes, in increments,  D_b^+ = b0 (D_c^+ - D_b^-) + D_c^-,
-// b0 = (c dt - d)/(c dt + d) for d = |b - c| (face: the axis spacing; edge and
-// corner: the diagonal).  Also zeroes the boundary vertex's source.
+// Second-order Mur (Sec. "Second Order ABCs") at the face vertex b next to
+// interior vertex c, face normal to the single axis of mask: the printed
+// update equals the first-order one (beta1 = 1 - beta0 on xi^n) plus
+//   sum_t g_t [(d^2_t xi^n)_b + (d^2_t xi^n)_c],  d^2_t f = f_{t+} - 2 f + f_{t-},
+// over the two tangential axes t, g_t = (c dt/d_t)^2 d_a / (2 (c dt + d_a)),
+// which is the increment to add to the first-order D_b.
 template <typename T>
-__device__ inline void mur_neighbours(const StencilP<T>& p, const V4<T>* __restrict__ cur,
-                                      V4<T>* __restrict__ nxt, V4<T>* __restrict__ D,
-                                      V4<T>* __restrict__ src, int i, int j, int k,
-                                      long long c, V4<T> dq_new, V4<T> dq_old) {
-  const int lo_x = (i == 1) ? -1 : 0, hi_x = (i == p.nx - 2) ? 1 : 0;
-  const int lo_y = (j == 1) ? -1 : 0, hi_y = (j == p.ny - 2) ? 1 : 0;
-  const int lo_z = (k == 1) ? -1 : 0, hi_z = (k == p.nz - 2) ? 1 : 0;
-  if (!(lo_x | hi_x | lo_y | hi_y | lo_z | hi_z)) return;
-  for (int dz = lo_z; dz <= hi_z; ++dz) {
-    for (int dy = lo_y; dy <= hi_y; ++dy) {
-      for (int dx = lo_x; dx <= hi_x; ++dx) {
-        const int mask = (dx != 0) | ((dy != 0) << 1) | ((dz != 0) << 2);
-        if (!mask) continue;
-        const long long b = c + dx + (long long)dy * p.nx + (long long)dz * p.nxy;
-        const V4<T> db_old = D[b];
-        V4<T> db = mur_beta0(p, mask) * (dq_new - db_old) + dq_old;
-        if (!p.space_charge) db.w = (T)0;
-        D[b] = db;
-        nxt[b] = ldg4(cur + b) + db;
-        src[b] = v4((T)0, (T)0, (T)0, (T)0);  // boundary sources are never used
-      }
-    }
-  }
+__device__ inline V4<T> mur2_terms(const StencilP<T>& p, const V4<T>* __restrict__ cur, int mask,
+                                   long long b, long long c) {
+  const int a = mask == 1 ? 0 : (mask == 2 ? 1 : 2);
+  const long long o1 = (a == 0) ? (long long)p.nx : 1;
+  const long long o2 = (a == 2) ? (long long)p.nx : p.nxy;
+  auto d2 = [&](long long v, long long o) {
+    const V4<T> m = ldg4(cur + v);
+    return (ldg4(cur + v + o) - m) + (ldg4(cur + v - o) - m);
+  };
+  // coefficients picked without a run-time index into the parameter block
+  const T g1 = a == 0 ? p.m2[0][0] : (a == 1 ? p.m2[1][0] : p.m2[2][0]);
+  const T g2 = a == 0 ? p.m2[0][1] : (a == 1 ? p.m2[1][1] : p.m2[2][1]);
+  return g1 * (d2(b, o1) + d2(c, o1)) + g2 * (d2(b, o2) + d2(c, o2));
+}
+
+// A source vertex needs its zeroing store only when the last deposit touched
+// it (the bunch covers a small part of the grid; NaN counts as touched).
+template <typename T>
+__device__ inline bool nonzero(V4<T> s) {
+  return !(s.x == (T)0 && s.y == (T)0 && s.z == (T)0 && s.w == (T)0);
 }
 
 // Source term (c dt)^2 (mu0 J, rho / eps0).
@@ -73,20 +70,14 @@ __device__ inline V4<T> source_term(const StencilP<T>& p, V4<T> s) {
   return v4(p.sA * s.x, p.sA * s.y, p.sA * s.z, p.sphi * s.w);
 }
 
-// Direct form: one thread per vertex, neighbours through L1.  cur holds
-// psi^n, nxt receives psi^{n+1}, D is advanced in place; the consumed
-// sources are zeroed for the deposit of this step.
+// Increment D^{n+1/2} of interior vertex c = (i, j, k) (the update equation
+// in increment form), neighbours of psi^n read through L1; *dm receives
+// D^{n-1/2} and *sv the source read.
 template <typename T>
-__global__ void __launch_bounds__(256) k_potential_step(StencilP<T> p,
-                                                        const V4<T>* __restrict__ cur,
-                                                        V4<T>* __restrict__ nxt,
-                                                        V4<T>* __restrict__ D,
-                                                        V4<T>* __restrict__ src) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  const int k = blockIdx.z;
-  if (i < 1 || i > p.nx - 2 || j < 1 || j > p.ny - 2 || k < 1 || k > p.nz - 2) return;
-  const long long c = cidx(i, j, k, p.nx, p.nxy);
+__device__ inline V4<T> interior_increment(const StencilP<T>& p, const V4<T>* __restrict__ cur,
+                                           const V4<T>* __restrict__ D,
+                                           const V4<T>* __restrict__ src, long long c,
+                                           V4<T>* pc_out, V4<T>* dm_out, V4<T>* sv_out) {
   const long long nxy = p.nxy;
   const int nx = p.nx;
   auto dsum = [&](long long q, long long off) {
@@ -98,12 +89,96 @@ __global__ void __launch_bounds__(256) k_potential_step(StencilP<T> p,
   L = L + p.ryA * (dsum(c - nxy, nx) + dsum(c + nxy, nx)) + p.ryB * dsum(c, nx);
   L = L + p.rz2 * ((ldg4(cur + c + nxy) - pc) + (ldg4(cur + c - nxy) - pc));
   const V4<T> dm = D[c];
-  V4<T> dp = dm + (L + source_term(p, src[c]));
+  const V4<T> sv = src[c];
+  V4<T> dp = dm + (L + source_term(p, sv));
   if (!p.space_charge) dp.w = (T)0;
-  mur_neighbours(p, cur, nxt, D, src, i, j, k, c, dp, dm);
+  *pc_out = pc;
+  *dm_out = dm;
+  *sv_out = sv;
+  return dp;
+}
+
+// Boundary vertex b of the launch shape below: grid (x, y, 6) of 32 x 8
+// blocks, blockIdx.z picks the face (z-, z+: all (i, j); y-, y+: all i, k in
+// [1, nz-2]; x-, x+: j, k in [1, ny-2] x [1, nz-2]), the block's 2-D thread
+// index the vertex on it.  Returns false for threads past the face.
+__device__ inline bool boundary_vertex(int nx, int ny, int nz, int* i, int* j, int* k) {
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  const int v = blockIdx.y * blockDim.y + threadIdx.y;
+  const int f = blockIdx.z;
+  if (f < 2) {
+    if (u >= nx || v >= ny) return false;
+    *i = u; *j = v; *k = f == 0 ? 0 : nz - 1;
+  } else if (f < 4) {
+    if (u >= nx || v >= nz - 2) return false;
+    *i = u; *k = v + 1; *j = f == 2 ? 0 : ny - 1;
+  } else {
+    if (u >= ny - 2 || v >= nz - 2) return false;
+    *j = u + 1; *k = v + 1; *i = f == 4 ? 0 : nx - 1;
+  }
+  return true;
+}
+
+// Mur update of every boundary vertex b, launched before the interior
+// update (which then carries no boundary code).  With beta0 + beta1 = 1 the
+// first-order condition
+//   xi_b^{n+1} = b0 (xi_b^{n-1} + xi_q^{n+1}) + b1 (xi_b^n + xi_q^n) - xi_q^{n-1}
+// becomes, in increments,  D_b^+ = b0 (D_q^+ - D_b^-) + D_q^-,
+// for q the nearest interior vertex and b0 = (c dt - d)/(c dt + d), d = |b - q|
+// (face: the axis spacing; edge and corner: the diagonal).  D_q^+ is
+// evaluated here from the same inputs as the interior update (whose D_q^- is
+// still in place).  Face vertices of a second-order grid add mur2_terms.  The
+// boundary sources are zeroed (no deposit reads them).
+template <typename T>
+__global__ void __launch_bounds__(256) k_mur_boundary(StencilP<T> p,
+                                                      const V4<T>* __restrict__ cur,
+                                                      V4<T>* __restrict__ nxt,
+                                                      V4<T>* __restrict__ D,
+                                                      V4<T>* __restrict__ src) {
+  int i, j, k;
+  if (!boundary_vertex(p.nx, p.ny, p.nz, &i, &j, &k)) return;
+  const int qi = min(max(i, 1), p.nx - 2), qj = min(max(j, 1), p.ny - 2),
+            qk = min(max(k, 1), p.nz - 2);
+  const int mask = (qi != i) | ((qj != j) << 1) | ((qk != k) << 2);
+  const long long b = cidx(i, j, k, p.nx, p.nxy), q = cidx(qi, qj, qk, p.nx, p.nxy);
+  V4<T> pq, dq_old, sq;
+  const V4<T> dq_new = interior_increment(p, cur, D, src, q, &pq, &dq_old, &sq);
+  const V4<T> db_old = D[b];
+  V4<T> db = mur_beta0(p, mask) * (dq_new - db_old) + dq_old;
+  if (p.mur2 && (mask & (mask - 1)) == 0) db = db + mur2_terms(p, cur, mask, b, q);
+  if (!p.space_charge) db.w = (T)0;
+  D[b] = db;
+  nxt[b] = ldg4(cur + b) + db;
+  src[b] = v4((T)0, (T)0, (T)0, (T)0);
+}
+
+// Launch shape of k_mur_boundary.
+__host__ inline dim3 mur_grid(int nx, int ny, int nz) {
+  const int d0 = nx > ny ? nx : ny;
+  const int d1 = ny > nz ? ny : nz;
+  return dim3((d0 + 31) / 32, (d1 + 7) / 8, 6);
+}
+
+// Direct form of the interior update: one thread per vertex, neighbours
+// through L1.  cur holds psi^n, nxt receives psi^{n+1}, D is advanced in
+// place; the consumed sources are zeroed for the deposit of this step
+// (stored only where non-zero).
+template <typename T>
+__global__ void __launch_bounds__(256) k_potential_step(StencilP<T> p,
+                                                        const V4<T>* __restrict__ cur,
+                                                        V4<T>* __restrict__ nxt,
+                                                        V4<T>* __restrict__ D,
+                                                        V4<T>* __restrict__ src) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = blockIdx.z;
+  if (i < 1 || i > p.nx - 2 || j < 1 || j > p.ny - 2 || k < 1 || k > p.nz - 2) return;
+  const long long c = cidx(i, j, k, p.nx, p.nxy);
+  V4<T> pc, dm, sv;
+  const V4<T> dp = interior_increment(p, cur, D, src, c, &pc, &dm, &sv);
+  if (nonzero(sv)) src[c] = v4((T)0, (T)0, (T)0, (T)0);
   D[c] = dp;
   nxt[c] = pc + dp;
-  src[c] = v4((T)0, (T)0, (T)0, (T)0);
 }
 
 // ---------------------------------------------------------------------------
@@ -116,8 +191,7 @@ __global__ void __launch_bounds__(256) k_potential_step(StencilP<T> p,
 // every input value is read from HBM about once and no thread waits on its
 // own loads.  Stages are recycled through per-stage "empty" barriers that
 // every warp arrives on, so warps do not wait for each other plane by plane.
-// The Mur vertices are written by the thread of the adjacent interior vertex,
-// as in the direct form.
+// The Mur vertices are written by k_mur_boundary before this kernel.
 constexpr int kMX = 32, kMY = 8, kMStages = 3;
 
 template <typename T>
@@ -222,12 +296,11 @@ __global__ void __launch_bounds__(kMX* kMY, (sizeof(T) == 4 ? 4 : 1)) k_potentia
       L = L + p.ryA * (Ym + Yp) + p.ryB * Y0;
       L = L + p.rz2 * ((cp - c0) + (cm - c0));
       V4<T> dp = dm + (L + source_term(p, sv));
-      if (!p.space_charge) dp.w = (T)0;
       const long long c = (long long)k * p.nxy + col;
-      mur_neighbours(p, cur, nxt, D, src, i, j, k, c, dp, dm);
+      if (nonzero(sv)) src[c] = zero;
+      if (!p.space_charge) dp.w = (T)0;
       D[c] = dp;
       nxt[c] = c0 + dp;
-      src[c] = zero;
     }
     cm = c0; Xm = X0; Ym = Y0;
     c0 = cp; X0 = Xp; Y0 = Yp;

@@ -17,6 +17,7 @@
 #include "field_kernels.cuh"
 #include "particle_kernels.cuh"
 #include "tile_push.cuh"
+#include "diag.cuh"
 
 using namespace mithra;
 
@@ -46,13 +47,20 @@ struct mithra_sim {
   int* count = nullptr;
   int* offset = nullptr;
   int* tiles = nullptr;  // non-empty tile list written by the scan
-  int2* scan_part = nullptr;  // block sums of the two-pass scan
+  int4* scan_part = nullptr;  // block sums of the two-pass scan
   StepState* dstate = nullptr;
   double* d_scalar = nullptr;   // one-off reductions
   double* d_power_rec = nullptr;
   int64_t power_cap = 0;
   int64_t power_first = 0;
   int32_t power_plane = 0;
+  // frequency-resolved power: running Fourier sums at one plane
+  int32_t spec_plane = 0;
+  int32_t spec_nf = 0;
+  double* d_spec_omega = nullptr;
+  double* d_spec_acc = nullptr;
+  double* d_spec_out = nullptr;
+  long long* d_spec_samples = nullptr;
   int64_t np = 0;
   int ntx = 0, nty = 0, ntz = 0, nkeys = 0;
   int64_t n_issued = 0;
@@ -73,6 +81,7 @@ struct mithra_sim {
   int push_grid = 0;      // persistent CTAs of the tiled particle step
   int push_max_per_sm = 1;
   int push_ctas_per_sm = 0;
+  int push_sparse_below = 0;  // tiles with fewer particles take the per-warp path
   int n_sm = 152;
   mithra_batch* in_batch = nullptr;  // the batch that steps this sim, if any
   // per-kernel event timing
@@ -86,8 +95,9 @@ struct mithra_sim {
 
 namespace {
 
-enum KernelId { K_POTENTIAL = 0, K_POWER, K_PUSH, K_SCAN, K_SCATTER, K_COUNT };
-const char* kKernelNames[K_COUNT] = {"potential_step", "power", "push", "scan_counts", "scatter"};
+enum KernelId { K_POTENTIAL = 0, K_POWER, K_PUSH, K_SCAN, K_SCATTER, K_SPECTRUM, K_COUNT };
+const char* kKernelNames[K_COUNT] = {"potential_step", "power", "push", "scan_counts", "scatter",
+                                     "spectrum"};
 
 cudaEvent_t take_event(mithra_sim* s) {
   if (!s->spare.empty()) {
@@ -188,7 +198,10 @@ mithra_status check_grid(const mithra_grid* g, std::string* why) {
   if (!(g->dx > 0) || !(g->dy > 0) || !(g->dz > 0) || !(g->dt > 0)) { *why = "dx, dy, dz, dt must be > 0"; return MITHRA_EINVAL; }
   if (g->n_sub < 1) { *why = "n_sub must be >= 1"; return MITHRA_EINVAL; }
   if (g->stencil != 0 && g->stencil != 1) { *why = "stencil must be 0 (NSFD) or 1 (standard)"; return MITHRA_EINVAL; }
-  if (g->boundary != 1) { *why = "boundary must be 1 (first-order Mur)"; return MITHRA_EINVAL; }
+  if (g->boundary != 1 && g->boundary != 2) {
+    *why = "boundary must be 1 (first-order Mur) or 2 (second-order Mur)";
+    return MITHRA_EINVAL;
+  }
   const double cdt = kC * g->dt;
   const double rx2 = (cdt / g->dx) * (cdt / g->dx), ry2 = (cdt / g->dy) * (cdt / g->dy),
                rz2 = (cdt / g->dz) * (cdt / g->dz);
@@ -232,6 +245,14 @@ StencilP<T> make_stencil(const mithra_grid& g) {
     const double d = std::sqrt(d2);
     p.mb0[m] = (T)((cdt - d) / (cdt + d));
   }
+  const double dd[3] = {g.dx, g.dy, g.dz};
+  const int tang[3][2] = {{1, 2}, {0, 2}, {0, 1}};
+  for (int a = 0; a < 3; ++a)
+    for (int t = 0; t < 2; ++t) {
+      const double r = cdt / dd[tang[a][t]];
+      p.m2[a][t] = (T)(r * r * dd[a] / (2.0 * (cdt + dd[a])));
+    }
+  p.mur2 = g.boundary == 2 ? 1 : 0;
   p.space_charge = g.space_charge ? 1 : 0;
   return p;
 }
@@ -307,9 +328,12 @@ Parts<T, U> parts_of(mithra_sim* s, int b) {
 // Two-pass scan of the per-tile counts (see k_scan_final).
 void launch_scan(mithra_sim* s, int advance) {
   const int nb = (s->nkeys + 1 + kScanBlock - 1) / kScanBlock;
-  k_scan_partials<<<nb, kScanBlock, 0, s->stream>>>(s->count, s->nkeys, s->scan_part);
+  const int sparse_below = s->push_variant == 1 ? s->push_sparse_below : 0;
+  k_scan_partials<<<nb, kScanBlock, 0, s->stream>>>(s->count, s->nkeys, sparse_below,
+                                                    s->scan_part);
   k_scan_final<<<nb, kScanBlock, 0, s->stream>>>(s->count, s->offset, s->tiles, s->nkeys,
-                                                 s->scan_part, nb, s->dstate, advance);
+                                                 sparse_below, s->scan_part, nb, s->dstate,
+                                                 advance);
 }
 
 // Persistent grid of the tiled particle step: as many CTAs as fit on the
@@ -370,6 +394,8 @@ mithra_status launch_step(mithra_sim* s) {
   V4<T>* S = static_cast<V4<T>*>(s->S);
   {
     ProfScope ps(s, K_POTENTIAL);
+    k_mur_boundary<T><<<mur_grid(s->g.nx, s->g.ny, s->g.nz), dim3(32, 8), 0, s->stream>>>(
+        sp, P0, P1, Dn, S);
     if (s->stencil_variant == 1 && s->have_tm) {
       dim3 grd((s->g.nx + kMX - 1) / kMX, (s->g.ny + kMY - 1) / kMY,
                (s->g.nz + s->lz - 1) / s->lz);
@@ -387,6 +413,15 @@ mithra_status launch_step(mithra_sim* s) {
                                           std::sqrt(1.0 - 1.0 / (s->u.gamma0 * s->u.gamma0)),
                                           s->d_power_rec - s->power_first, s->dstate,
                                           s->power_first + s->power_cap, 1, &s->dstate->err);
+  }
+  if (s->spec_nf > 0) {
+    ProfScope ps(s, K_SPECTRUM);
+    const double g0 = s->u.gamma0;
+    const long long nv = (long long)(s->g.nx - 2) * (s->g.ny - 2);
+    k_spectrum_accumulate<T><<<blocks_for(nv, 256), 256, 0, s->stream>>>(
+        pp, P1, Dn, s->spec_plane, g0, std::sqrt(1.0 - 1.0 / (g0 * g0)),
+        s->g.z0 + s->spec_plane * s->g.dz, s->dstate, s->spec_nf, s->d_spec_omega,
+        s->d_spec_acc, s->d_spec_samples);
   }
   if (s->np > 0) {
     Parts<T, U> A = parts_of<T, U>(s, s->pb), B = parts_of<T, U>(s, 1 - s->pb);
@@ -559,6 +594,32 @@ mithra_status copy_particles_impl(mithra_sim* s, double* out7) {
   return st;
 }
 
+template <typename T, typename U>
+mithra_status bunch_stats_impl(mithra_sim* s, double kb, double* out14) {
+  const PicP<T> pp = make_pic<T>(s);
+  const int nb = (int)std::min<long long>(blocks_for(s->np, 256), 1024);
+  double* d = nullptr;
+  MCHECK(s, cudaMalloc(&d, sizeof(double) * ((size_t)nb * kBunchSums + 14)));
+  k_bunch_partial<T, U><<<nb, 256, 0, s->stream>>>(pp, parts_of<T, U>(s, s->pb), s->np, kb, d);
+  k_bunch_final<<<1, 32, 0, s->stream>>>(d, nb, d + (size_t)nb * kBunchSums);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(out14, d + (size_t)nb * kBunchSums, sizeof(double) * 14,
+                        cudaMemcpyDeviceToHost, s->stream);
+  mithra_status st = e == cudaSuccess ? sync_status(s) : cuda_fail(s, e, "bunch statistics");
+  cudaFree(d);
+  return st;
+}
+
+void free_spectrum(mithra_sim* s) {
+  for (void* p : {(void*)s->d_spec_omega, (void*)s->d_spec_acc, (void*)s->d_spec_out,
+                  (void*)s->d_spec_samples})
+    if (p) cudaFree(p);
+  s->d_spec_omega = s->d_spec_acc = s->d_spec_out = nullptr;
+  s->d_spec_samples = nullptr;
+  s->spec_nf = 0;
+}
+
 void lab_of(const mithra_sim* s, int32_t kp, double t, double* t_lab, double* z_lab) {
   const double g0 = s->u.gamma0;
   const double b0 = std::sqrt(1.0 - 1.0 / (g0 * g0));
@@ -570,7 +631,8 @@ void lab_of(const mithra_sim* s, int32_t kp, double t, double* t_lab, double* z_
 void free_all(mithra_sim* s) {
   if (s->stream) cudaStreamSynchronize(s->stream);
   void* ptrs[] = {s->P[0], s->P[1], s->D, s->S, s->pbuf[0], s->pbuf[1], s->key, s->rank, s->count,
-                  s->offset, s->tiles, s->scan_part, s->dstate, s->d_scalar, s->d_power_rec};
+                  s->offset, s->tiles, s->scan_part, s->dstate, s->d_scalar, s->d_power_rec,
+                  s->d_spec_omega, s->d_spec_acc, s->d_spec_out, s->d_spec_samples};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (s->h_err) cudaFreeHost(s->h_err);
@@ -613,6 +675,7 @@ mithra_status mithra_footprint(const mithra_grid* grid, int64_t n_particles,
   b += 2 * (int64_t)particle_buffer_bytes(n_particles, precision);
   b += 2 * n_particles * (int64_t)sizeof(int);                   // key, rank
   b += 3 * (nkeys + 2) * (int64_t)sizeof(int);                   // count, offset, tiles
+  b += (nkeys / kScanBlock + 2) * (int64_t)sizeof(int4);         // scan block sums
   b += (int64_t)sizeof(StepState) + (int64_t)sizeof(double);
   *bytes = b;
   return MITHRA_OK;
@@ -677,7 +740,7 @@ mithra_status mithra_create(const mithra_grid* grid, const mithra_undulator* und
             dalloc((void**)&s->count, sizeof(int) * (size_t)(s->nkeys + 2)) &&
             dalloc((void**)&s->offset, sizeof(int) * (size_t)(s->nkeys + 2)) &&
             dalloc((void**)&s->tiles, sizeof(int) * (size_t)(s->nkeys + 1)) &&
-            dalloc((void**)&s->scan_part, sizeof(int2) * (size_t)(s->nkeys / kScanBlock + 2)) &&
+            dalloc((void**)&s->scan_part, sizeof(int4) * (size_t)(s->nkeys / kScanBlock + 2)) &&
             dalloc((void**)&s->dstate, sizeof(StepState)) &&
             dalloc((void**)&s->d_scalar, sizeof(double));
   if (!ok) return bail(MITHRA_ENOMEM, "device allocation failed");
@@ -857,6 +920,82 @@ mithra_status mithra_read_power(mithra_sim* s, double* out, int64_t max_records,
   return MITHRA_OK;
 }
 
+mithra_status mithra_bunch_stats(mithra_sim* s, double k_b, double* out) {
+  if (!s) return fail(nullptr, MITHRA_EINVAL, "sim is NULL");
+  if (!out || !std::isfinite(k_b)) return fail(s, MITHRA_EINVAL, "out is NULL or k_b not finite");
+  if (s->np == 0) {
+    for (int a = 0; a < 14; ++a) out[a] = 0.0;
+    return sync_status(s);
+  }
+  return with_types(s->prec, [&](auto t, auto u) {
+    TYPES_OF(t, u);
+    return bunch_stats_impl<T, U>(s, k_b, out);
+  });
+}
+
+mithra_status mithra_set_spectrum(mithra_sim* s, int32_t k_plane, int32_t n_wavelengths,
+                                  const double* lambda_lab) {
+  if (!s) return fail(nullptr, MITHRA_EINVAL, "sim is NULL");
+  if (s->in_batch) return fail(s, MITHRA_EBUSY, "sim is stepped by a batch");
+  if (n_wavelengths < 0 || n_wavelengths > kMaxSpectrum)
+    return fail(s, MITHRA_EINVAL, "n_wavelengths outside [0, 64]");
+  if (n_wavelengths > 0) {
+    if (k_plane < 1 || k_plane > s->g.nz - 2)
+      return fail(s, MITHRA_EINVAL, "k_plane outside [1, nz-2]");
+    if (!lambda_lab) return fail(s, MITHRA_EINVAL, "lambda_lab is NULL");
+    for (int m = 0; m < n_wavelengths; ++m)
+      if (!(lambda_lab[m] > 0.0) || !std::isfinite(lambda_lab[m]))
+        return fail(s, MITHRA_EINVAL, "wavelengths must be finite and > 0");
+  }
+  MCHECK(s, cudaStreamSynchronize(s->stream));
+  free_spectrum(s);
+  if (n_wavelengths == 0) return MITHRA_OK;
+  const long long nv = (long long)(s->g.nx - 2) * (s->g.ny - 2);
+  const size_t acc_bytes = sizeof(double) * 8 * (size_t)nv * (size_t)n_wavelengths;
+  if (cudaMalloc((void**)&s->d_spec_omega, sizeof(double) * n_wavelengths) != cudaSuccess ||
+      cudaMalloc((void**)&s->d_spec_acc, acc_bytes) != cudaSuccess ||
+      cudaMalloc((void**)&s->d_spec_out, sizeof(double) * n_wavelengths) != cudaSuccess ||
+      cudaMalloc((void**)&s->d_spec_samples, sizeof(long long)) != cudaSuccess) {
+    free_spectrum(s);
+    return fail(s, MITHRA_ENOMEM, "spectrum allocation failed");
+  }
+  // a forward lab wave of wavelength lambda passes the plane, which moves
+  // with the rest frame at beta0 c, at angular frequency 2 pi c (1 - beta0) / lambda
+  const double g0 = s->u.gamma0;
+  const double b0 = std::sqrt(1.0 - 1.0 / (g0 * g0));
+  std::vector<double> om((size_t)n_wavelengths);
+  for (int m = 0; m < n_wavelengths; ++m) om[m] = 2.0 * kPi * kC * (1.0 - b0) / lambda_lab[m];
+  MCHECK(s, cudaMemcpy(s->d_spec_omega, om.data(), sizeof(double) * n_wavelengths,
+                       cudaMemcpyHostToDevice));
+  MCHECK(s, cudaMemset(s->d_spec_acc, 0, acc_bytes));
+  MCHECK(s, cudaMemset(s->d_spec_samples, 0, sizeof(long long)));
+  s->spec_plane = k_plane;
+  s->spec_nf = n_wavelengths;
+  return MITHRA_OK;
+}
+
+mithra_status mithra_read_spectrum(mithra_sim* s, double* dW_domega, int64_t* n_samples) {
+  if (!s) return fail(nullptr, MITHRA_EINVAL, "sim is NULL");
+  if (s->spec_nf == 0) {
+    if (n_samples) *n_samples = 0;
+    return sync_status(s);
+  }
+  const long long nv = (long long)(s->g.nx - 2) * (s->g.ny - 2);
+  k_spectrum_density<<<s->spec_nf, 256, 0, s->stream>>>(s->d_spec_acc, nv,
+                                                        s->g.dx * s->g.dy / (kPi * kMu0),
+                                                        s->d_spec_out);
+  MCHECK(s, cudaGetLastError());
+  long long ns = 0;
+  if (dW_domega)
+    MCHECK(s, cudaMemcpyAsync(dW_domega, s->d_spec_out, sizeof(double) * s->spec_nf,
+                              cudaMemcpyDeviceToHost, s->stream));
+  MCHECK(s, cudaMemcpyAsync(&ns, s->d_spec_samples, sizeof(long long), cudaMemcpyDeviceToHost,
+                            s->stream));
+  mithra_status st = sync_status(s);
+  if (n_samples) *n_samples = ns;
+  return st;
+}
+
 mithra_status mithra_copy_particles(mithra_sim* s, double* x, double* y, double* z, double* ux,
                                     double* uy, double* uz, int32_t* lost, int64_t* n_lost) {
   if (!s) return fail(nullptr, MITHRA_EINVAL, "sim is NULL");
@@ -911,14 +1050,17 @@ const char* mithra_kernel_name(int32_t kernel) {
 mithra_status mithra_set_tuning(mithra_sim* s, const mithra_tuning* t) {
   if (!s) return fail(nullptr, MITHRA_EINVAL, "sim is NULL");
   if (!t || t->stencil_variant < 0 || t->stencil_variant > 1 || t->lz < 0 ||
-      t->push_variant < 0 || t->push_variant > 1 || t->push_ctas_per_sm < 0)
-    return fail(s, MITHRA_EINVAL, "bad tuning: variants 0 or 1, lz >= 0, ctas >= 0");
+      t->push_variant < 0 || t->push_variant > 1 || t->push_ctas_per_sm < 0 ||
+      t->push_sparse_below < 0)
+    return fail(s, MITHRA_EINVAL,
+                "bad tuning: variants 0 or 1, lz >= 0, ctas >= 0, sparse_below >= 0");
   if ((t->stencil_variant == 1 || t->push_variant == 1) && !s->have_tm)
     return fail(s, MITHRA_EINVAL, "TMA tensor maps unavailable: variant 1 disabled");
   s->stencil_variant = t->stencil_variant;
   s->lz = t->lz > 0 ? t->lz : default_lz(&s->g, s->march_resident);
   s->push_variant = t->push_variant;
   s->push_ctas_per_sm = t->push_ctas_per_sm;
+  s->push_sparse_below = t->push_sparse_below;
   const int per_sm = (t->push_ctas_per_sm > 0 && t->push_ctas_per_sm < s->push_max_per_sm)
                          ? t->push_ctas_per_sm
                          : s->push_max_per_sm;
@@ -933,6 +1075,7 @@ mithra_status mithra_get_tuning(const mithra_sim* s, mithra_tuning* t) {
   t->lz = s->lz;
   t->push_variant = s->push_variant;
   t->push_ctas_per_sm = s->push_ctas_per_sm;
+  t->push_sparse_below = s->push_sparse_below;
   return MITHRA_OK;
 }
 

@@ -382,56 +382,76 @@ __device__ inline int block_exclusive_scan(int v, int* ws, int* total) {
 }
 
 // Exclusive scan of the per-tile counts in two coalesced passes over blocks of
-// kScanBlock entries.  Pass 1 writes each block's sums (particles, non-empty
-// tiles).  Pass 2 scans those sums, then its block: offset[t] (offset[nkeys+1]
-// = total), the list of non-empty tiles (key < nkeys; key nkeys holds the
-// lost particles) for the tiled particle kernel, the reset counts, and, in
-// block 0, the tile count, the reset work counter and (advance != 0: the last
-// kernel of a step) the step counter.
+// kScanBlock entries.  Pass 1 writes each block's sums (particles, dense
+// tiles, sparse tiles).  Pass 2 scans those sums, then its block: offset[t]
+// (offset[nkeys+1] = total), the list of non-empty tiles (key < nkeys; key
+// nkeys holds the lost particles) for the tiled particle kernel -- tiles with
+// at least sparse_below particles first (dense), then the others (sparse),
+// each group in key order -- the reset counts, and, in block 0, the two tile
+// counts, the reset work counters and (advance != 0: the last kernel of a
+// step) the step counter.  sparse_below = 0 lists every tile as dense.
 constexpr int kScanBlock = 1024;
 
+__device__ inline void tile_class(int c, int t, int nkeys, int sparse_below, int* dense,
+                                  int* sparse) {
+  const bool nonempty = c > 0 && t < nkeys;
+  *dense = (nonempty && c >= sparse_below) ? 1 : 0;
+  *sparse = (nonempty && c < sparse_below) ? 1 : 0;
+}
+
 __global__ void __launch_bounds__(kScanBlock) k_scan_partials(const int* __restrict__ count,
-                                                              int nkeys, int2* __restrict__ part) {
+                                                              int nkeys, int sparse_below,
+                                                              int4* __restrict__ part) {
   __shared__ int ws[32];
   const int t = blockIdx.x * kScanBlock + threadIdx.x;
   const int c = (t <= nkeys) ? count[t] : 0;
-  int tot, ne;
+  int dn, sp;
+  tile_class(c, t, nkeys, sparse_below, &dn, &sp);
+  int tot, nd, ns;
   block_exclusive_scan(c, ws, &tot);
-  block_exclusive_scan((c > 0 && t < nkeys) ? 1 : 0, ws, &ne);
-  if (threadIdx.x == 0) part[blockIdx.x] = make_int2(tot, ne);
+  block_exclusive_scan(dn, ws, &nd);
+  block_exclusive_scan(sp, ws, &ns);
+  if (threadIdx.x == 0) part[blockIdx.x] = make_int4(tot, nd, ns, 0);
 }
 
 __global__ void __launch_bounds__(kScanBlock) k_scan_final(int* __restrict__ count,
                                                            int* __restrict__ offset,
                                                            int* __restrict__ tiles, int nkeys,
-                                                           const int2* __restrict__ part,
+                                                           int sparse_below,
+                                                           const int4* __restrict__ part,
                                                            int nblocks, StepState* __restrict__ st,
                                                            int advance) {
   __shared__ int ws[32];
-  __shared__ int base[2], total[2];
+  __shared__ int base[3], total[3];
   // bases of this block from the block sums (nblocks <= kScanBlock)
-  const int2 pv = (threadIdx.x < nblocks) ? part[threadIdx.x] : make_int2(0, 0);
-  int all_c, all_n;
+  const int4 pv = (threadIdx.x < nblocks) ? part[threadIdx.x] : make_int4(0, 0, 0, 0);
+  int all_c, all_d, all_s;
   const int bc = block_exclusive_scan(pv.x, ws, &all_c);
-  const int bn = block_exclusive_scan(pv.y, ws, &all_n);
-  if (threadIdx.x == blockIdx.x) { base[0] = bc; base[1] = bn; }
-  if (threadIdx.x == 0) { total[0] = all_c; total[1] = all_n; }
+  const int bd = block_exclusive_scan(pv.y, ws, &all_d);
+  const int bs = block_exclusive_scan(pv.z, ws, &all_s);
+  if (threadIdx.x == blockIdx.x) { base[0] = bc; base[1] = bd; base[2] = bs; }
+  if (threadIdx.x == 0) { total[0] = all_c; total[1] = all_d; total[2] = all_s; }
   __syncthreads();
   const int t = blockIdx.x * kScanBlock + threadIdx.x;
   const int c = (t <= nkeys) ? count[t] : 0;
-  const bool nonempty = c > 0 && t < nkeys;
+  int dn, sp;
+  tile_class(c, t, nkeys, sparse_below, &dn, &sp);
   int dummy;
   const int off = base[0] + block_exclusive_scan(c, ws, &dummy);
-  const int slot = base[1] + block_exclusive_scan(nonempty ? 1 : 0, ws, &dummy);
+  const int sd = base[1] + block_exclusive_scan(dn, ws, &dummy);
+  const int ss = total[1] + base[2] + block_exclusive_scan(sp, ws, &dummy);
   if (t <= nkeys) {
     offset[t] = off;
     count[t] = 0;
-    if (nonempty) tiles[slot] = t;
+    if (dn) tiles[sd] = t;
+    if (sp) tiles[ss] = t;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     offset[nkeys + 1] = total[0];
     st->n_tiles = total[1];
+    st->n_sparse = total[2];
     st->work = 0;
+    st->work_sparse = 0;
     if (advance) st->n += 1;
   }
 }

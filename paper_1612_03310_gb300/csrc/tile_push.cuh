@@ -1,7 +1,7 @@
 // tile_push.cuh -- particle step by cell tiles.
 //
-// A persistent CTA takes non-empty 8^3-cell tiles from the list the last
-// re-sort produced.  For each tile it
+// A persistent CTA takes dense 8^3-cell tiles from the list the last re-sort
+// produced.  For each tile it
 //   1. loads psi^{n+1} and the increment D over the vertices
 //      [t0 - 1, t0 + 9]^3 (11^3, two TMA box loads, one mbarrier);
 //   2. evaluates E and B at t = (n+1/2) dt at the tile's 9^3 vertices
@@ -15,8 +15,10 @@
 //      vertex.
 // A particle whose sub-step leaves the tile (n_sub > 1) gathers from global
 // memory, and one whose deposit leaves the 11^3 block deposits with global
-// atomics: the same arithmetic on another path.  Particles lost in earlier
-// steps only get their re-sort bucket.
+// atomics: the same arithmetic on another path.  Sparse tiles (fewer
+// particles than the staging pays for) are then taken one per warp on that
+// global path.  Particles lost in earlier steps only get their re-sort
+// bucket.
 #pragma once
 #include "common.cuh"
 #include "field_kernels.cuh"
@@ -104,6 +106,52 @@ __device__ inline void deposit_tile(const PicP<T>& p, T* __restrict__ sJ,
       }
 }
 
+// One particle's field step (shared by the staged and the per-warp path):
+// push, then the deposits of rho at the end point and J at the mid point
+// through dep(kRho, i, j, k, f, jx, jy, jz, rho), and the re-sort bucket.
+template <typename T, typename U, typename Gather, typename Frame, typename Dep>
+__device__ inline void tile_particle(const PicP<T>& p, Parts<T, U>& P, long long q,
+                                     int* __restrict__ count, int* __restrict__ key,
+                                     int* __restrict__ rank, long long* __restrict__ lost_ctr,
+                                     Gather&& gather, Frame&& frame, Dep&& dep) {
+  const int cell = P.cell[q];
+  int kk = p.nkeys;
+  if (cell >= 0) {
+    int i, j, k;
+    decode_cell(p, cell, &i, &j, &k);
+    T f[3] = {P.fx[q], P.fy[q], P.fz[q]};
+    U u[3] = {P.ux[q], P.uy[q], P.uz[q]};
+    const int ia = i, ja = j, ka = k;
+    const T f0[3] = {f[0], f[1], f[2]};
+    T disp[3];
+    const bool ok = push_particle(p, i, j, k, f, u, disp, gather, frame);
+    P.ux[q] = u[0]; P.uy[q] = u[1]; P.uz[q] = u[2];
+    if (!ok) {
+      P.cell[q] = -1;
+      atomicAdd(reinterpret_cast<unsigned long long*>(lost_ctr), 1ULL);
+    } else {
+      P.cell[q] = (int)cidx(i, j, k, p.nx, p.nxy);
+      P.fx[q] = f[0]; P.fy[q] = f[1]; P.fz[q] = f[2];
+      dep(true, i, j, k, f, (T)0, (T)0, (T)0, p.qV);
+      T mf[3];
+      const int mi = split_cell_t(ia, f0[0] + (T)0.5 * disp[0], &mf[0]);
+      const int mj = split_cell_t(ja, f0[1] + (T)0.5 * disp[1], &mf[1]);
+      const int mk = split_cell_t(ka, f0[2] + (T)0.5 * disp[2], &mf[2]);
+      dep(false, mi, mj, mk, mf, p.jx * disp[0], p.jy * disp[1], p.jz * disp[2], (T)0);
+      kk = tile_key(p, i, j, k);
+    }
+  }
+  key[q] = kk;
+  rank[q] = bin_rank(count, kk);
+}
+
+template <typename T>
+__device__ inline void tile_origin(const PicP<T>& p, int tile, int* i0, int* j0, int* k0) {
+  *i0 = (tile % p.ntx) * kTile;
+  *j0 = ((tile / p.ntx) % p.nty) * kTile;
+  *k0 = (tile / (p.ntx * p.nty)) * kTile;
+}
+
 template <typename T, typename U>
 __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 3 : 1)) k_push_tiled(
     const __grid_constant__ CUtensorMap tm_pn, const __grid_constant__ CUtensorMap tm_d,
@@ -141,9 +189,8 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 3 : 1)) k_push_tiled(
     const int t = s_tile;
     if (t >= ntiles) break;
     const int tile = tiles[t];
-    const int i0 = (tile % p.ntx) * kTile;
-    const int j0 = ((tile / p.ntx) % p.nty) * kTile;
-    const int k0 = (tile / (p.ntx * p.nty)) * kTile;
+    int i0, j0, k0;
+    tile_origin(p, tile, &i0, &j0, &k0);
     if (tid == 0) {
       fence_proxy_async_smem();
       mbar_arrive_expect_tx(bar, 2u * tile_box_bytes<T>());
@@ -170,63 +217,42 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 3 : 1)) k_push_tiled(
 
     const int beg = offset[tile], end = offset[tile + 1];
     for (int q = beg + tid; q < end; q += blockDim.x) {
-      const int cell = P.cell[q];
-      int kk = p.nkeys;
-      if (cell >= 0) {
-        int i, j, k;
-    decode_cell(p, cell, &i, &j, &k);
-        T f[3] = {P.fx[q], P.fy[q], P.fz[q]};
-        U u[3] = {P.ux[q], P.uy[q], P.uz[q]};
-        const int ia = i, ja = j, ka = k;
-        const T f0[3] = {f[0], f[1], f[2]};
-        T disp[3];
-        const bool ok = push_particle(
-            p, i, j, k, f, u, disp, [&](int ci, int cj, int ck, const T* ff, T* E, T* B) {
-              const int a = ci - i0, b = cj - j0, c = ck - k0;
-              if (a >= 0 && a < kTile && b >= 0 && b < kTile && c >= 0 && c < kTile) {
-                const T wx[2] = {(T)1 - ff[0], ff[0]}, wy[2] = {(T)1 - ff[1], ff[1]},
-                        wz[2] = {(T)1 - ff[2], ff[2]};
-                E[0] = E[1] = E[2] = B[0] = B[1] = B[2] = (T)0;
+      tile_particle(
+          p, P, q, count, key, rank, lost_ctr,
+          [&](int ci, int cj, int ck, const T* ff, T* E, T* B) {
+            const int a = ci - i0, b = cj - j0, c = ck - k0;
+            if (a >= 0 && a < kTile && b >= 0 && b < kTile && c >= 0 && c < kTile) {
+              const T wx[2] = {(T)1 - ff[0], ff[0]}, wy[2] = {(T)1 - ff[1], ff[1]},
+                      wz[2] = {(T)1 - ff[2], ff[2]};
+              E[0] = E[1] = E[2] = B[0] = B[1] = B[2] = (T)0;
 #pragma unroll
-                for (int K = 0; K < 2; ++K)
+              for (int K = 0; K < 2; ++K)
 #pragma unroll
-                  for (int J = 0; J < 2; ++J)
+                for (int J = 0; J < 2; ++J)
 #pragma unroll
-                    for (int I = 0; I < 2; ++I) {
-                      const int v = ((c + K) * kTE + (b + J)) * kTE + (a + I);
-                      const V4<T> e = sE[v], bb = sB[v];
-                      const T w = wx[I] * wy[J] * wz[K];
-                      E[0] += w * e.x; E[1] += w * e.y; E[2] += w * e.z;
-                      B[0] += w * bb.x; B[1] += w * bb.y; B[2] += w * bb.z;
-                    }
-              } else {
-                gather_eb(p, pn, D, ci, cj, ck, ff[0], ff[1], ff[2], E, B);
-              }
-            },
-            [&](int m, int kc, int* kref) {
-              *kref = k0;
-              return m < kMaxFrames ? s_frame[m] : und_frame(p, k0, th + m * p.dtb);
-            });
-        P.ux[q] = u[0]; P.uy[q] = u[1]; P.uz[q] = u[2];
-        if (!ok) {
-          P.cell[q] = -1;
-          atomicAdd(reinterpret_cast<unsigned long long*>(lost_ctr), 1ULL);
-        } else {
-          P.cell[q] = (int)cidx(i, j, k, p.nx, p.nxy);
-          P.fx[q] = f[0]; P.fy[q] = f[1]; P.fz[q] = f[2];
-          deposit_tile<true>(p, sJ, src, i0, j0, k0, i, j, k, f[0], f[1], f[2], (T)0, (T)0,
-                             (T)0, p.qV);
-          T mf[3];
-          const int mi = split_cell_t(ia, f0[0] + (T)0.5 * disp[0], &mf[0]);
-          const int mj = split_cell_t(ja, f0[1] + (T)0.5 * disp[1], &mf[1]);
-          const int mk = split_cell_t(ka, f0[2] + (T)0.5 * disp[2], &mf[2]);
-          deposit_tile<false>(p, sJ, src, i0, j0, k0, mi, mj, mk, mf[0], mf[1], mf[2],
-                              p.jx * disp[0], p.jy * disp[1], p.jz * disp[2], (T)0);
-          kk = tile_key(p, i, j, k);
-        }
-      }
-      key[q] = kk;
-      rank[q] = bin_rank(count, kk);
+                  for (int I = 0; I < 2; ++I) {
+                    const int v = ((c + K) * kTE + (b + J)) * kTE + (a + I);
+                    const V4<T> e = sE[v], bb = sB[v];
+                    const T w = wx[I] * wy[J] * wz[K];
+                    E[0] += w * e.x; E[1] += w * e.y; E[2] += w * e.z;
+                    B[0] += w * bb.x; B[1] += w * bb.y; B[2] += w * bb.z;
+                  }
+            } else {
+              gather_eb(p, pn, D, ci, cj, ck, ff[0], ff[1], ff[2], E, B);
+            }
+          },
+          [&](int m, int kc, int* kref) {
+            *kref = k0;
+            return m < kMaxFrames ? s_frame[m] : und_frame(p, k0, th + m * p.dtb);
+          },
+          [&](bool rho, int i, int j, int k, const T* f, T jx, T jy, T jz, T q) {
+            if (rho)
+              deposit_tile<true>(p, sJ, src, i0, j0, k0, i, j, k, f[0], f[1], f[2], jx, jy, jz,
+                                 q);
+            else
+              deposit_tile<false>(p, sJ, src, i0, j0, k0, i, j, k, f[0], f[1], f[2], jx, jy, jz,
+                                  q);
+          });
     }
     __syncthreads();
     // add the block to the global sources (touched vertices only)
@@ -239,6 +265,43 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 3 : 1)) k_push_tiled(
       }
     }
     __syncthreads();
+  }
+  // Sparse tiles: one warp per tile, no staging -- E and B evaluated at the
+  // vertices from global memory and the deposits added with global atomics.
+  // The whole CTA has left the loop above, so the E/B area is free for the
+  // warps' undulator frames.
+  const int nsparse = st->n_sparse;
+  if (nsparse > 0) {
+    const int lane = tid & 31;
+    UndFrame<T>* wf = reinterpret_cast<UndFrame<T>*>(sE) + (tid >> 5) * kMaxFrames;
+    for (;;) {
+      int w = 0;
+      if (lane == 0) w = atomicAdd(&st->work_sparse, 1);
+      w = __shfl_sync(0xffffffffu, w, 0);
+      if (w >= nsparse) break;
+      const int tile = tiles[ntiles + w];
+      int i0, j0, k0;
+      tile_origin(p, tile, &i0, &j0, &k0);
+      __syncwarp();
+      for (int m = lane; m < p.n_sub && m < kMaxFrames; m += 32)
+        wf[m] = und_frame(p, k0, th + m * p.dtb);
+      __syncwarp();
+      const int beg = offset[tile], end = offset[tile + 1];
+      for (int q = beg + lane; q < end; q += 32) {
+        tile_particle(
+            p, P, q, count, key, rank, lost_ctr,
+            [&](int ci, int cj, int ck, const T* ff, T* E, T* B) {
+              gather_eb(p, pn, D, ci, cj, ck, ff[0], ff[1], ff[2], E, B);
+            },
+            [&](int m, int kc, int* kref) {
+              *kref = k0;
+              return m < kMaxFrames ? wf[m] : und_frame(p, k0, th + m * p.dtb);
+            },
+            [&](bool rho, int i, int j, int k, const T* f, T jx, T jy, T jz, T q) {
+              deposit_cic(p, src, i, j, k, f[0], f[1], f[2], jx, jy, jz, q);
+            });
+      }
+    }
   }
   // particles lost before this step sit at the tail of the sorted order (the
   // bucket after the last tile); they keep that bucket in the re-sort

@@ -29,7 +29,8 @@ EXPORTS = ["mithra_create", "mithra_step", "mithra_sync", "mithra_time", "mithra
            "mithra_set_tuning", "mithra_get_tuning", "mithra_plane_power_noalloc",
            "mithra_batch_create", "mithra_batch_add", "mithra_batch_remove", "mithra_batch_step",
            "mithra_batch_sync", "mithra_batch_size", "mithra_batch_last_error",
-           "mithra_batch_destroy"]
+           "mithra_batch_destroy", "mithra_bunch_stats", "mithra_set_spectrum",
+           "mithra_read_spectrum"]
 
 
 class MithraError(RuntimeError):
@@ -53,7 +54,7 @@ class Undulator(C.Structure):
 
 class Tuning(C.Structure):
     _fields_ = [("stencil_variant", C.c_int32), ("lz", C.c_int32), ("push_variant", C.c_int32),
-                ("push_ctas_per_sm", C.c_int32)]
+                ("push_ctas_per_sm", C.c_int32), ("push_sparse_below", C.c_int32)]
 
 
 class Bunch(C.Structure):
@@ -270,6 +271,30 @@ class Simulation:
             _check(lib().mithra_read_power(self.h, _dp(out), m, C.byref(cnt)), self.h)
         return out
 
+    # -- diagnostics -------------------------------------------------------
+    BUNCH_STATS = ("mean_x", "mean_y", "mean_z", "mean_ux", "mean_uy", "mean_uz",
+                   "rms_x", "rms_y", "rms_z", "rms_ux", "rms_uy", "rms_uz", "bunching", "n")
+
+    def bunch_stats(self, k_b: float) -> np.ndarray:
+        """mithra_bunch_stats: 14 values (names in BUNCH_STATS)."""
+        out = np.zeros(14)
+        _check(lib().mithra_bunch_stats(self.h, C.c_double(k_b), _dp(out)), self.h)
+        return out
+
+    def set_spectrum(self, k_plane: int, lambda_lab) -> None:
+        lam = np.ascontiguousarray(lambda_lab, dtype=np.float64)
+        self._spec_n = int(lam.size)
+        _check(lib().mithra_set_spectrum(self.h, int(k_plane), self._spec_n,
+                                         _dp(lam) if lam.size else None), self.h)
+
+    def read_spectrum(self):
+        """(dW/domega per wavelength [J s], number of samples)."""
+        n = getattr(self, "_spec_n", 0)
+        out = np.zeros(n)
+        ns = C.c_int64()
+        _check(lib().mithra_read_spectrum(self.h, _dp(out) if n else None, C.byref(ns)), self.h)
+        return out, int(ns.value)
+
     # -- particles ---------------------------------------------------------
     def copy_particles(self) -> dict:
         n = self.n_particles
@@ -286,10 +311,12 @@ class Simulation:
 
     # -- launch choices --------------------------------------------------
     def set_tuning(self, stencil_variant: int | None = None, lz: int | None = None,
-                   push_variant: int | None = None, push_ctas_per_sm: int | None = None):
+                   push_variant: int | None = None, push_ctas_per_sm: int | None = None,
+                   push_sparse_below: int | None = None):
         t = self.tuning()
         for k, v in (("stencil_variant", stencil_variant), ("lz", lz),
-                     ("push_variant", push_variant), ("push_ctas_per_sm", push_ctas_per_sm)):
+                     ("push_variant", push_variant), ("push_ctas_per_sm", push_ctas_per_sm),
+                     ("push_sparse_below", push_sparse_below)):
             if v is not None:
                 t[k] = int(v)
         _check(lib().mithra_set_tuning(self.h, C.byref(Tuning(**t))), self.h)

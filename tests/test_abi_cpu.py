@@ -52,7 +52,9 @@ def test_stability_check_matches_oracle(M, orc, stencil, courant):
 
 def test_bad_grids_rejected(M):
     g = inputs.random_grid(0, 8, 8, 8)
-    for bad in (dict(nx=3), dict(dx=0.0), dict(n_sub=0), dict(stencil=2), dict(boundary=2)):
+    assert M.check_grid(dict(g, boundary=2)) == M.check_grid(dict(g, boundary=1)) == M.OK
+    for bad in (dict(nx=3), dict(dx=0.0), dict(n_sub=0), dict(stencil=2), dict(boundary=0),
+                dict(boundary=3)):
         assert M.check_grid({**g, "boundary": 1, **bad}) == M.EINVAL, bad
         assert M.last_error()
 

@@ -11,7 +11,8 @@ class FakeSim:
 
     def __init__(self, grid, und, bunch, precision=1, stream=None):
         FakeSim.made += 1
-        self.t = dict(stencil_variant=1, lz=0, push_variant=1, push_ctas_per_sm=0)
+        self.t = dict(stencil_variant=1, lz=0, push_variant=1, push_ctas_per_sm=0,
+                      push_sparse_below=0)
         self.closed = False
 
     def step(self, n):
@@ -26,8 +27,11 @@ class FakeSim:
     def kernel_times(self):
         t = self.t
         # stencil: marching with lz = 32 fastest; push: tiled with 2 CTAs/SM
+        # and sparse tiles below 64
         st = 1.0 if t["stencil_variant"] == 0 else 0.5 + abs(t["lz"] - 32) / 100.0
         pu = 2.0 if t["push_variant"] == 0 else 0.4 + abs(t["push_ctas_per_sm"] - 2) / 10.0
+        if t["push_variant"] == 1 and t["push_sparse_below"]:
+            pu -= 0.1 - abs(t["push_sparse_below"] - 64) / 1000.0
         return {"potential_step": (st * 4, 4), "push": (pu * 4, 4)}
 
     def close(self):
@@ -50,15 +54,20 @@ def test_candidates_cover_both_forms():
     assert all(c["lz"] <= g["nz"] for c in st)
     assert any(c["stencil_variant"] == 1 for c in st)
     pu = autotune.push_candidates(3)
-    assert dict(push_variant=0, push_ctas_per_sm=0) in pu
+    assert dict(push_variant=0, push_ctas_per_sm=0, push_sparse_below=0) in pu
     assert [c["push_ctas_per_sm"] for c in pu if c["push_variant"] == 1] == [1, 2, 3]
+    assert autotune.sparse_candidates(pu[0]) == []
+    sp = autotune.sparse_candidates(pu[2])
+    assert [c["push_sparse_below"] for c in sp] == list(autotune.SPARSE_THRESHOLDS)
+    assert all(c["push_ctas_per_sm"] == pu[2]["push_ctas_per_sm"] for c in sp)
 
 
 def test_picks_fastest_and_caches(fake):
     g = inputs.random_grid(0, 64, 64, 256)
     b = inputs.random_particles(1, g, 1000)
     best = autotune.tune(g, None, b, 1)
-    assert best == dict(stencil_variant=1, lz=32, push_variant=1, push_ctas_per_sm=2)
+    assert best == dict(stencil_variant=1, lz=32, push_variant=1, push_ctas_per_sm=2,
+                        push_sparse_below=64)
     assert fake.made == 1
     again = autotune.tune(g, None, b, 1)
     assert again == best and fake.made == 1  # served from the cache

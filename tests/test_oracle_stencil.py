@@ -12,7 +12,9 @@ mathematics fix, independent of the oracle's own code:
   - one update equals the operator assembled by Kronecker products of 1-D
     difference matrices (brute force on an 8^3 grid);
   - Mur boundaries act the same on opposite faces (mirror symmetry) and absorb
-    an outgoing pulse far better than a reflecting wall.
+    an outgoing pulse far better than a reflecting wall;
+  - at oblique incidence the first- and second-order Mur conditions reflect
+    as the continuous Engquist-Majda operators predict.
 """
 import numpy as np
 import pytest
@@ -88,11 +90,14 @@ def test_wrong_omega_is_detected(orc):
     assert abs(w_nsfd - w_std) / w_nsfd > 1e-3
 
 
-def test_nsfd_exact_along_z_and_mur_absorbs(orc):
+@pytest.mark.parametrize("boundary", [1, 2])
+def test_nsfd_exact_along_z_and_mur_absorbs(orc, boundary):
     # c dt = dz: NSFD keeps the vacuum speed of light along z; a pulse moving
     # towards -z shifts one cell per step and leaves through k = 0 without
-    # reflection (beta0 = 0 in the first-order Mur condition).
-    g = inputs.random_grid(0, 40, 40, 32, courant=1.0, stencil=0, dz_over_dx=0.5)
+    # reflection (beta0 = 0 in the first-order Mur condition; the second-order
+    # terms vanish for a field uniform along the face).
+    g = dict(inputs.random_grid(0, 40, 40, 32, courant=1.0, stencil=0, dz_over_dx=0.5),
+             boundary=boundary)
     i, j, k = _coords(g)
     prof = lambda kk: np.exp(-0.5 * ((kk - 12.0) / 2.0) ** 2)  # noqa: E731
     # psi(k, n) = f(k + n): moving to -z
@@ -190,8 +195,9 @@ def test_brute_force_operator_8cubed(orc, stencil):
 
 
 @pytest.mark.parametrize("axis", [0, 1, 2])
-def test_mur_mirror_symmetry(orc, axis):
-    g = inputs.random_grid(0, 9, 10, 11)
+@pytest.mark.parametrize("boundary", [1, 2])
+def test_mur_mirror_symmetry(orc, axis, boundary):
+    g = dict(inputs.random_grid(0, 9, 10, 11), boundary=boundary)
     f = inputs.random_fields(7, g)
     shp = (4, g["nz"], g["ny"], g["nx"])
     ax = 3 - axis  # numpy axis of x/y/z in (comp, k, j, i)
@@ -229,3 +235,56 @@ def test_mur_absorbs_outgoing_pulse(orc):
     line = cur.reshape(4, g["nz"], g["ny"], g["nx"])[:, 25, 25, 20:39]
     left = np.abs(line).max()
     assert left < 0.05, left
+
+
+def _oblique_reflection(orc, boundary, theta_deg, below):
+    """A Gaussian wave packet (carrier 8 cells, envelope 8 cells along and 12
+    across its direction) runs at theta to the normal of the k = 0 face.
+    Returns the field over the original domain after the packet has met the
+    face, on a grid that extends `below` planes beyond it, and the incident
+    norm."""
+    nx, ny, nz = 80, 40, 48
+    h = 1.0e-4
+    g = dict(nx=nx, ny=ny, nz=nz + below, dx=h, dy=h, dz=h, x0=0.0, y0=0.0, z0=0.0,
+             dt=0.5 * h / C0, n_sub=1, stencil=1, space_charge=1, boundary=boundary)
+    th = np.radians(theta_deg)
+    k, j, i = np.meshgrid(np.arange(g["nz"]) - below, np.arange(ny), np.arange(nx),
+                          indexing="ij")
+    x, y, z = i - 20.0, j - (ny - 1) / 2.0, k - 30.0
+
+    def packet(t):  # t: c t in cells
+        s = np.sin(th) * x - np.cos(th) * z - t
+        u = np.cos(th) * x + np.sin(th) * z
+        return (np.exp(-(s / 8.0) ** 2 - (u / 12.0) ** 2 - (y / 12.0) ** 2)
+                * np.cos(2 * np.pi * s / 8.0))
+
+    n = g["nx"] * g["ny"] * g["nz"]
+    zero = np.zeros(3 * n)
+    prev = np.concatenate([packet(-0.5).ravel(), zero])
+    cur = np.concatenate([packet(0.0).ravel(), zero])
+    inc = np.linalg.norm(packet(0.0)[below:])
+    src = np.zeros(4 * n)
+    for _ in range(150):
+        nxt = orc.potential_step(g, prev, cur, src)
+        prev, cur = cur, nxt
+    return cur[:n].reshape(g["nz"], ny, nx)[below:], inc
+
+
+def test_mur_oblique_reflection_first_and_second_order(orc):
+    # Reflection of a plane wave at incidence theta from the continuous
+    # boundary operators (Engquist-Majda): first order
+    # R1 = (1 - cos)/(1 + cos), second order R2 = R1^2 (0.172 and 0.029 at
+    # 45 degrees).  The reflected field is the difference between runs on the
+    # domain and on one extended 48 planes beyond the face (same boundary
+    # order, so the other faces act alike in both).  A wrong sign of the
+    # second-order tangential terms reflects more than the first order.
+    c = np.cos(np.radians(45.0))
+    r1_theory = (1 - c) / (1 + c)
+    r = {}
+    for b in (1, 2):
+        ext, inc = _oblique_reflection(orc, b, 45.0, 48)
+        dom, _ = _oblique_reflection(orc, b, 45.0, 0)
+        r[b] = np.linalg.norm(dom - ext) / inc
+    assert abs(r[1] - r1_theory) < 0.2 * r1_theory, r
+    assert 0.5 * r1_theory ** 2 < r[2] < 1.5 * r1_theory ** 2, r
+    assert r[2] < 0.3 * r[1], r

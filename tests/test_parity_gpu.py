@@ -116,17 +116,19 @@ def compare_particles(sim, o, tol_cells, face_eps):
 @pytest.mark.parametrize("prec", ["P64", "P32"])
 @pytest.mark.parametrize("shape", [(37, 29, 45), (4, 4, 4), (33, 9, 70), (5, 41, 6), (70, 17, 9)])
 @pytest.mark.parametrize("variant,lz", [(0, 0), (1, 0), (1, 5), (1, 1)])
-def test_vacuum_update_parity(M, orc, prec, shape, variant, lz):
+@pytest.mark.parametrize("boundary", [1, 2])
+def test_vacuum_update_parity(M, orc, prec, shape, variant, lz, boundary):
     # both forms of the potential update (direct; z-marching TMA tiles with
-    # several plane-chunk lengths, ragged tiles in x and y)
+    # several plane-chunk lengths, ragged tiles in x and y); first- and
+    # second-order Mur with random values on every boundary vertex
     nx, ny, nz = shape
-    g = inputs.random_grid(11, nx, ny, nz)
+    g = dict(inputs.random_grid(11, nx, ny, nz), boundary=boundary)
     f = inputs.random_fields(12, g)
     p = getattr(M, prec)
     if p == M.P32:
         f = as_f32(f)
     o = orc.OracleSim(g, None, dict(x=[], y=[], z=[], ux=[], uy=[], uz=[]))
-    with M.Simulation(dict(g, boundary=1), None, None, precision=p) as sim:
+    with M.Simulation(g, None, None, precision=p) as sim:
         sim.set_tuning(stencil_variant=variant, lz=lz)
         assert sim.tuning()["stencil_variant"] == variant
         set_state(sim, o, f)
@@ -149,11 +151,13 @@ C1_UND = inputs.WORKLOADS["c1"]["undulator"]
 
 @pytest.mark.parametrize("prec", ["P64", "P32", "P32_U64"])
 @pytest.mark.parametrize("n_sub", [1, 3])
-@pytest.mark.parametrize("push_variant", [0, 1])
-def test_pic_step_parity(M, orc, prec, n_sub, push_variant):
+@pytest.mark.parametrize("push_variant,sparse_below", [(0, 0), (1, 0), (1, 60), (1, 1 << 30)])
+def test_pic_step_parity(M, orc, prec, n_sub, push_variant, sparse_below):
     # per-particle and tiled particle kernels; n_sub = 3 lets sub-steps leave
     # the tile (gather from global memory); the 36 x 30 x 40 grid has ragged
-    # tiles in every axis
+    # tiles in every axis.  About 60 particles per tile: sparse_below = 60
+    # sends part of the tiles to the per-warp path from the second step on,
+    # 2^30 all of them.
     g = inputs.random_grid(21, 36, 30, 40, n_sub=n_sub)
     f = inputs.random_fields(22, g, scale=1e-9)
     P = inputs.random_particles(23, g, 6000, u_scale=0.3)
@@ -163,7 +167,7 @@ def test_pic_step_parity(M, orc, prec, n_sub, push_variant):
         f = as_f32(f)
     o = orc.OracleSim(g, und, P)
     with M.Simulation(dict(g, boundary=1), und, P, precision=p) as sim:
-        sim.set_tuning(push_variant=push_variant)
+        sim.set_tuning(push_variant=push_variant, push_sparse_below=sparse_below)
         # rho^{1/2} from the initial positions agrees before anything else
         ref = oracle_fields(o)
         assert rel_l2(sim.copy_field("rho"), ref["rho"]) <= (1e-13 if p == M.P64 else 1e-6)
@@ -220,17 +224,18 @@ def test_initially_outside_particles_are_lost(M, orc, prec):
 # ---------------------------------------------------------------------------
 # the c1 workload end to end (200 steps), power recorded every step
 
-@pytest.mark.parametrize("prec,push_variant", [("P64", 1), ("P32", 1), ("P32_U64", 1),
-                                               ("P64", 0), ("P32", 0)])
-def test_workload_c1(M, orc, prec, push_variant):
+@pytest.mark.parametrize("prec,push_variant,sparse_below,boundary", [
+    ("P64", 1, 0, 1), ("P32", 1, 0, 1), ("P32_U64", 1, 0, 1), ("P64", 0, 0, 1), ("P32", 0, 0, 1),
+    ("P32", 1, 256, 1), ("P64", 1, 256, 1), ("P64", 1, 0, 2), ("P32", 1, 0, 2)])
+def test_workload_c1(M, orc, prec, push_variant, sparse_below, boundary):
     w = inputs.workload("c1")
     P = inputs.make_bunch(w["bunch_spec"], w["seed"])
-    g, und = w["grid"], w["undulator"]
+    g, und = dict(w["grid"], boundary=boundary), w["undulator"]
     kp = g["nz"] - 8
     p = getattr(M, prec)
     o = orc.OracleSim(g, und, P)
-    with M.Simulation(dict(g, boundary=1), und, P, precision=p) as sim:
-        sim.set_tuning(push_variant=push_variant)
+    with M.Simulation(g, und, P, precision=p) as sim:
+        sim.set_tuning(push_variant=push_variant, push_sparse_below=sparse_below)
         sim.set_power_sampling(kp, w["steps"])
         o.step(w["steps"], power_plane=kp)
         sim.step(w["steps"])
