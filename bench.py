@@ -41,13 +41,16 @@ def parse():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="mithra", choices=["mithra", "reference"])
     ap.add_argument("--workload", default="c2")
-    ap.add_argument("--precision", default="p32", choices=["p32", "p64"])
+    ap.add_argument("--precision", default="p32", choices=["p32", "p32_u64", "p32_c", "p64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-p64", action="store_true")
-    ap.add_argument("--mode", default="step", choices=["step", "batch", "serve"],
+    ap.add_argument("--mode", default="step", choices=["step", "batch", "serve", "precision"],
                     help="step: one simulation (c2); batch: 64 uneven simulations (c4); "
-                         "serve: continuous batching of Poisson arrivals (c5)")
+                         "serve: continuous batching of Poisson arrivals (c5); precision: "
+                         "per-output error of the FP32 forms against P64 over the whole "
+                         "grid after --steps steps (c2), with P64 checked against the "
+                         "stored oracle checkpoints")
     ap.add_argument("--job-steps", type=int, default=100,
                     help="batch mode: steps timed per job (jobs of 1000 steps are scaled)")
     ap.add_argument("--plain-jobs", type=int, default=8,
@@ -135,21 +138,27 @@ class ClockSampler:
 KERNELS_PER_SCOPE = {"potential_step": 2, "scan_counts": 2}
 
 
+PRECISIONS = {"p32": "P32", "p32_u64": "P32_U64", "p32_c": "P32_C", "p64": "P64"}
+
+
 def algorithmic_bytes(kernel: str, grid: dict, n_particles: int, prec: str) -> float:
     """Algorithmic bytes per launch (the minimum a kernel must move)."""
-    r = 4 if prec == "p32" else 8
+    r = 8 if prec == "p64" else 4                      # field and fraction values
+    um = 4 if prec in ("p32", "p32_c") else 8          # momenta
+    lo = prec in ("p32_c", "p32_u64")                  # compensated potential levels
     interior = (grid["nx"] - 2) * (grid["ny"] - 2) * (grid["nz"] - 2)
     if kernel == "potential_step":
         # read psi^n, the increment and the sources; write psi^{n+1} and the
-        # new increment: 5 x 4 values per interior cell (the zeroing stores of
+        # new increment: 5 x 4 values per interior cell, plus 2 x 8 bytes for
+        # the bfloat16 lo parts of compensated levels (the zeroing stores of
         # the sources the last deposit touched are not counted)
-        return interior * 5 * 4 * r
+        return interior * (5 * 4 * r + (16 if lo else 0))
     if kernel == "push":
         # read and write cell + 3 fractions + 3 momenta; write key and rank
-        return n_particles * (2 * (4 + 6 * r) + 8)
+        return n_particles * (2 * (4 + 3 * r + 3 * um) + 8)
     if kernel == "scatter":
         # read key, rank, offset and the particle; write the particle
-        return n_particles * (12 + 2 * (8 + 6 * r))
+        return n_particles * (12 + 2 * (8 + 3 * r + 3 * um))
     if kernel == "scan_counts":
         ntiles = -(-grid["nx"] // 8) * -(-grid["ny"] // 8) * -(-grid["nz"] // 8)
         return ntiles * 12
@@ -168,7 +177,7 @@ def run_gpu(args, rank, world):
     bunch = inputs.make_bunch(w["bunch_spec"], w["seed"] + rank)
     n_part = bunch["x"].size
     ncell = g["nx"] * g["ny"] * g["nz"]
-    prec = mithra.P32 if args.precision == "p32" else mithra.P64
+    prec = getattr(mithra, PRECISIONS[args.precision])
     kp = g["nz"] - 16
     stream = torch.cuda.Stream()  # a dedicated stream: events bracket exactly our work
     torch.cuda.set_stream(stream)
@@ -221,28 +230,34 @@ def run_gpu(args, rank, world):
                grid=g, n_lost=parts["n_lost"], power_last=float(power[-1, 0]),
                launches=sum(n * KERNELS_PER_SCOPE.get(k, 1) for k, (_, n) in kt.items()))
 
-    # P64 (plain FP64) on the same workload, shorter
-    if not args.no_p64 and prec == mithra.P32:
-        K64 = max(20, K // 10)
-        sim = mithra.Simulation(g, und, bunch, precision=mithra.P64, stream=stream.cuda_stream)
-        sim.set_tuning(**autotune.tune(g, und, bunch, mithra.P64, stream=stream.cuda_stream))
-        sim.set_power_sampling(kp, W + K64)
+    # the other precision forms on the same workload, shorter: P64 (plain
+    # FP64) and P32_U64 (compensated FP32 levels, FP64 momenta: the form that
+    # meets the field tolerance after the configured steps)
+    def side_run(precision, steps):
+        sim = mithra.Simulation(g, und, bunch, precision=precision, stream=stream.cuda_stream)
+        sim.set_tuning(**autotune.tune(g, und, bunch, precision, stream=stream.cuda_stream))
+        sim.set_power_sampling(kp, W + steps)
         sim.step(W)
         sim.profile(True)
         torch.cuda.synchronize()
         barrier()
         e0.record(stream)
-        sim.step(K64)
+        sim.step(steps)
         e1.record(stream)
         torch.cuda.synchronize()
-        ms64 = e0.elapsed_time(e1)
-        kt64 = sim.kernel_times()
+        ms_side = e0.elapsed_time(e1)
+        kts = sim.kernel_times()
         sim.close()
         if world > 1:
-            t = torch.tensor([ms64], device="cuda", dtype=torch.float64)
+            t = torch.tensor([ms_side], device="cuda", dtype=torch.float64)
             torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms64 = float(t.item())
-        res["p64"] = dict(ms=ms64, steps=K64, kernel_times=kt64)
+            ms_side = float(t.item())
+        return dict(ms=ms_side, steps=steps, kernel_times=kts)
+
+    if not args.no_p64 and prec != mithra.P64:
+        res["p64"] = side_run(mithra.P64, max(20, K // 10))
+    if not args.no_p64 and prec == mithra.P32:
+        res["p32_u64"] = side_run(mithra.P32_U64, max(50, K // 4))
 
     # end to end through the C ABI from host buffers
     if not args.no_e2e:
@@ -410,14 +425,93 @@ def run_serve(args, duration: float | None = None) -> dict:
                        "duration_s": dur, "hbm_budget": budget}}
 
 
+PRECISION_FIELDS = ["Ex", "Ey", "Ez", "Bx", "By", "Bz", "Ax", "Ay", "Az", "phi",
+                    "Jx", "Jy", "Jz", "rho"]
+
+
+def run_precision(args) -> dict:
+    """Per-output error of the FP32 forms on c2 after K steps: P32, P32_C and
+    P32_U64 against P64 over the whole grid (every field, relative L2), the power at
+    every step, every particle.  P64 itself is held against the FP64 oracle's
+    stored checkpoints (plane fields and power) at the steps they cover."""
+    import glob
+    from paper_1612_03310_gb300 import inputs, mithra
+    w = inputs.workload(args.workload)
+    g = dict(w["grid"], boundary=1)
+    P = inputs.make_bunch(w["bunch_spec"], w["seed"])
+    K = args.steps
+    kp = g["nz"] - 16
+    here = os.path.dirname(os.path.abspath(__file__))
+    cks = {}
+    for path in glob.glob(os.path.join(here, "tests", "golden", f"{args.workload}_reference_*.npz")):
+        d = np.load(path)
+        cks[int(d["steps"])] = d
+    sims = {}
+    for nm in ("P64", "P32", "P32_C", "P32_U64"):
+        sims[nm] = mithra.Simulation(g, w["undulator"], P, precision=getattr(mithra, nm))
+        sims[nm].set_power_sampling(kp, K)
+    out = {"metric": f"per-output error after {K} steps, {args.workload}", "impl": "mithra",
+           "mode": "precision", "steps": K, "data": "synthetic",
+           "config": {"workload": inputs.describe(args.workload)}}
+    oracle_check = {}
+    done = 0
+    for stop in sorted([s for s in cks if s <= K]) + [K]:
+        if stop > done:
+            for sim in sims.values():
+                sim.step(stop - done)
+            done = stop
+        if stop in cks and stop not in oracle_check:
+            d = cks[stop]
+            k0 = int(d["plane_k"])
+            e = {}
+            for f in PRECISION_FIELDS:
+                a = sims["P64"].copy_field(f)[k0]
+                b = d["plane_" + f].astype(np.float64)
+                e[f] = float(np.linalg.norm(a - b) / np.linalg.norm(b))
+            pr = d["power"][:stop, 0]
+            pg = sims["P64"].read_power()[:stop, 0]
+            e["power"] = float(np.abs(pg - pr).max() / np.abs(pr).max())
+            oracle_check[stop] = {k: float("%.3g" % v) for k, v in e.items()}
+    ref_fields = {}
+    res = {"P32": {}, "P32_C": {}, "P32_U64": {}}
+    for f in PRECISION_FIELDS:
+        ref = sims["P64"].copy_field(f)
+        nr = float(np.linalg.norm(ref))
+        for nm in res:
+            a = sims[nm].copy_field(f)
+            res[nm][f] = float(np.linalg.norm(a - ref) / nr) if nr > 0 else float(np.linalg.norm(a))
+        ref_fields[f] = nr
+    pw = sims["P64"].read_power()[:, 0]
+    parts = sims["P64"].copy_particles()
+    for nm in res:
+        p = sims[nm].read_power()[:, 0]
+        res[nm]["power"] = float(np.abs(p - pw).max() / np.abs(pw).max())
+        q = sims[nm].copy_particles()
+        res[nm]["position_cells"] = max(
+            float(np.abs((q[k] - parts[k]) / g[dk]).max()) for k, dk in
+            (("x", "dx"), ("y", "dy"), ("z", "dz")))
+        us = float(np.abs(parts["uz"]).max())
+        res[nm]["momentum_rel"] = max(float(np.abs(q[k] - parts[k]).max())
+                                      for k in ("ux", "uy", "uz")) / us
+        res[nm] = {k: float("%.3g" % v) for k, v in res[nm].items()}
+        res[nm]["n_lost"] = int(q["n_lost"])
+    for sim in sims.values():
+        sim.close()
+    out["errors_vs_p64"] = res
+    out["p64_vs_oracle_checkpoints"] = oracle_check
+    out["tolerances"] = {"fields": 1e-4, "power": 1e-3}
+    return out
+
+
 def main():
     args = parse()
-    if args.mode in ("batch", "serve") and args.impl == "mithra":
+    if args.mode in ("batch", "serve", "precision") and args.impl == "mithra":
         import torch
         torch.cuda.set_device(0)
         from paper_1612_03310_gb300 import build_lib
         build_lib.build()
-        print(json.dumps(run_batch(args) if args.mode == "batch" else run_serve(args)))
+        run = {"batch": run_batch, "serve": run_serve, "precision": run_precision}[args.mode]
+        print(json.dumps(run(args)))
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -484,7 +578,7 @@ def main():
         "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world,
         "steps": K, "warmup": args.warmup, "ms_per_step": res["ms"] / K,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32" if args.precision == "p32" else "f64", "data": "synthetic",
+        "dtype": "f64" if args.precision == "p64" else "f32", "data": "synthetic",
         "config": cfg,
         "particle_pushes_per_s": pushes,
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
@@ -501,16 +595,19 @@ def main():
         "tuning_trials": res.get("trials"),
         "n_lost": res["n_lost"],
     }
-    if "p64" in res:
-        p = res["p64"]
-        kt64 = p["kernel_times"]
-        st64 = kt64["potential_step"][0] / max(kt64["potential_step"][1], 1)
-        line["p64"] = {"ms_per_step": p["ms"] / p["steps"],
-                       "cell_updates_per_s": world * ncell * p["steps"] / (p["ms"] / 1e3),
-                       "particle_pushes_per_s": world * npart * p["steps"] / (p["ms"] / 1e3),
-                       "stencil_gbs": algorithmic_bytes("potential_step", res["grid"], npart,
-                                                        "p64") / (st64 / 1e3) / 1e9,
-                       "kernel_ms_per_launch": {k: v[0] / max(v[1], 1) for k, v in kt64.items()}}
+    for side in ("p64", "p32_u64"):
+        if side not in res:
+            continue
+        p = res[side]
+        kts = p["kernel_times"]
+        sts = kts["potential_step"][0] / max(kts["potential_step"][1], 1)
+        line[side] = {"ms_per_step": p["ms"] / p["steps"], "steps": p["steps"],
+                      "cell_updates_per_s": world * ncell * p["steps"] / (p["ms"] / 1e3),
+                      "particle_pushes_per_s": world * npart * p["steps"] / (p["ms"] / 1e3),
+                      "stencil_gbs": algorithmic_bytes("potential_step", res["grid"], npart,
+                                                       side) / (sts / 1e3) / 1e9,
+                      "kernel_ms_per_launch": {k: v[0] / max(v[1], 1) for k, v in kts.items()
+                                               if v[1]}}
     if "e2e" in res:
         e = res["e2e"]
         line["e2e"] = {"value": world * ncell * K / e["seconds"], "unit": "cell-updates/s",

@@ -54,13 +54,17 @@ typedef enum {
 } mithra_status;
 
 typedef enum {
-    MITHRA_P64 = 0,     /* all state and arithmetic in FP64 */
-    MITHRA_P32 = 1,     /* FP32 fields and particle phase space; FP64 frame
-                           clock, lab-frame phase of the undulator, particle
-                           gamma, the cell carry of positions and the power
-                           accumulation */
-    MITHRA_P32_U64 = 2  /* as MITHRA_P32, but the particle momenta are stored
-                           and Boris-rotated in FP64 */
+    MITHRA_P64 = 0,      /* all state and arithmetic in FP64 */
+    MITHRA_P32 = 1,      /* FP32 fields and particle phase space with FP32
+                            arithmetic; FP64 frame clock, lab-frame phase of
+                            the undulator, particle gamma, the cell carry of
+                            positions and the power accumulation */
+    MITHRA_P32_U64 = 2,  /* as MITHRA_P32, but the potential levels are kept as
+                            compensated pairs (float hi + bfloat16 lo, so that
+                            the rounding of a quasi-static potential no longer
+                            accumulates) and the particle momenta are stored
+                            and Boris-rotated in FP64 */
+    MITHRA_P32_C = 3     /* as MITHRA_P32 with compensated potential levels */
 } mithra_precision;
 
 /* Field identifiers; the paper's field names (Ex .. Bz, Ax .. Az, Jx .. Jz,
@@ -242,8 +246,11 @@ mithra_status mithra_read_spectrum(mithra_sim* sim, double* dW_domega, int64_t* 
  *   stencil_variant 0: the direct potential update, one thread per vertex with
  *     neighbours read through L1; 1: the z-marching form, psi^n, D and source
  *     planes of a 32 x 8 column tile streamed through a shared-memory ring by
- *     TMA box loads.
- *   lz: planes per CTA of the marching form (0: about two waves of CTAs).
+ *     TMA box loads (single-float levels only: MITHRA_P32, MITHRA_P64);
+ *     2: register z-marching, a thread walks its column for lz planes with
+ *     three planes' sums in registers.
+ *   lz: planes per CTA of the marching forms (0: about two waves of CTAs for
+ *     variant 1, 16 for variant 2).
  *   push_variant 0: one thread per particle, E and B evaluated at the eight
  *     vertices from global memory; 1: persistent CTAs over 8^3-cell particle
  *     tiles with the potentials, E/B and the deposit block in shared memory.
@@ -274,8 +281,8 @@ mithra_status mithra_get_tuning(const mithra_sim* sim, mithra_tuning* tuning);
  * framework whose allocator owns the device memory, or a real-time loop that
  * must not wait on the allocator.
  *   psi_newest: device array of nx*ny*nz cells of 4 values {A_x, A_y, A_z,
- *     phi} of the newest potential level (float for MITHRA_P32 and
- *     MITHRA_P32_U64, double for MITHRA_P64), cell (i,j,k) at
+ *     phi} of the newest potential level (float for the MITHRA_P32 forms,
+ *     their hi part when compensated; double for MITHRA_P64), cell (i,j,k) at
  *     (k*ny + j)*nx + i; increment: the same layout, newest minus previous
  *     level.  E and B are taken at the time between the two levels.
  *   gamma0: Lorentz factor of the rest frame; *p_lab (host) receives the

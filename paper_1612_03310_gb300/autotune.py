@@ -7,8 +7,8 @@ the fastest particle-step choice independently (the two kernels do not share
 knobs), and caches the result per (device, precision, grid, particle count)
 in a JSON file so that later runs of the same shape skip the search.
 
-The candidates: the direct stencil and the marching stencil with a range of
-plane runs per CTA; the per-particle push and the tiled push with 1 .. max
+The candidates: the direct stencil and the two marching stencils (TMA ring,
+registers) with a range of plane runs per CTA; the per-particle push and the tiled push with 1 .. max
 persistent CTAs per SM, then, for the tiled push with the best CTA count, a
 range of sparse-tile thresholds (tiles below it skip the shared-memory
 staging).  A threshold only acts from the next re-sort, so every push
@@ -78,6 +78,9 @@ def stencil_candidates(grid: dict) -> list[dict]:
     for lz in (8, 16, 24, 32, 48, 64, 96, 128):
         if lz <= grid["nz"]:
             out.append(dict(stencil_variant=1, lz=lz))
+    for lz in (4, 8, 16, 32, 64):
+        if lz <= grid["nz"]:
+            out.append(dict(stencil_variant=2, lz=lz))
     return out
 
 

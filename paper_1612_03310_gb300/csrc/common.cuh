@@ -10,6 +10,7 @@
 //               the cell along x, y, z in [0, 1), U momentum u = gamma*beta
 //               (U = T, or double with FP32 fields), int32 original index.
 #pragma once
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -65,6 +66,31 @@ __device__ inline V4<double> ldg4<double>(const V4<double>* p) {
   const double2* q = reinterpret_cast<const double2*>(p);
   double2 a = __ldg(q), b = __ldg(q + 1);
   return v4(a.x, a.y, b.x, b.y);
+}
+
+// Lo part of a compensated potential level: four bfloat16 values (8 bytes per
+// vertex).  The lo part is at most half an ulp of the float hi part, so its
+// 8-bit significand adds 8 bits to the level's precision; rounding it to
+// bfloat16 each step costs 2^-9 of an ulp of hi.
+struct alignas(8) LoV4 {
+  __nv_bfloat162 xy, zw;
+};
+
+template <typename T>
+__device__ inline V4<T> ld_lo(const LoV4* __restrict__ a, long long i) {
+  const uint2 raw = __ldg(reinterpret_cast<const uint2*>(a + i));
+  LoV4 v;
+  memcpy(&v, &raw, sizeof(v));
+  const float2 xy = __bfloat1622float2(v.xy), zw = __bfloat1622float2(v.zw);
+  return v4((T)xy.x, (T)xy.y, (T)zw.x, (T)zw.y);
+}
+
+template <typename T>
+__device__ inline void st_lo(LoV4* __restrict__ a, long long i, V4<T> v) {
+  LoV4 r;
+  r.xy = __floats2bfloat162_rn((float)v.x, (float)v.y);
+  r.zw = __floats2bfloat162_rn((float)v.z, (float)v.w);
+  a[i] = r;
 }
 
 // Division of non-negative 32-bit integers by an invariant divisor d >= 2 by

@@ -72,30 +72,76 @@ __device__ inline V4<T> source_term(const StencilP<T>& p, V4<T> s) {
 
 // Increment D^{n+1/2} of interior vertex c = (i, j, k) (the update equation
 // in increment form), neighbours of psi^n read through L1; *dm receives
-// D^{n-1/2} and *sv the source read.
-template <typename T>
-__device__ inline V4<T> interior_increment(const StencilP<T>& p, const V4<T>* __restrict__ cur,
-                                           const V4<T>* __restrict__ D,
-                                           const V4<T>* __restrict__ src, long long c,
-                                           V4<T>* pc_out, V4<T>* dm_out, V4<T>* sv_out) {
+// D^{n-1/2} and *sv the source read.  With compensated levels (kLo) the
+// level is hi + lo and the Laplacian is taken of both parts: the neighbour
+// differences of hi are exact or nearly so, so the sum carries the level to
+// about twice FP32's precision.
+template <typename T, typename Load>
+__device__ inline V4<T> laplacian(const StencilP<T>& p, Load&& ld, long long c) {
   const long long nxy = p.nxy;
   const int nx = p.nx;
   auto dsum = [&](long long q, long long off) {
-    const V4<T> m = ldg4(cur + q);
-    return (ldg4(cur + q + off) - m) + (ldg4(cur + q - off) - m);
+    const V4<T> m = ld(q);
+    return (ld(q + off) - m) + (ld(q - off) - m);
   };
-  const V4<T> pc = ldg4(cur + c);
+  const V4<T> ac = ld(c);
   V4<T> L = p.rxA * (dsum(c - nxy, 1) + dsum(c + nxy, 1)) + p.rxB * dsum(c, 1);
   L = L + p.ryA * (dsum(c - nxy, nx) + dsum(c + nxy, nx)) + p.ryB * dsum(c, nx);
-  L = L + p.rz2 * ((ldg4(cur + c + nxy) - pc) + (ldg4(cur + c - nxy) - pc));
+  return L + p.rz2 * ((ld(c + nxy) - ac) + (ld(c - nxy) - ac));
+}
+
+template <bool kLo, typename T>
+__device__ inline V4<T> interior_increment(const StencilP<T>& p, const V4<T>* __restrict__ cur,
+                                           const LoV4* __restrict__ curlo,
+                                           const V4<T>* __restrict__ D,
+                                           const V4<T>* __restrict__ src, long long c,
+                                           V4<T>* dm_out, V4<T>* sv_out) {
+  V4<T> L = laplacian(p, [&](long long q) { return ldg4(cur + q); }, c);
+  if (kLo) L = L + laplacian(p, [&](long long q) { return ld_lo<T>(curlo, q); }, c);
   const V4<T> dm = D[c];
   const V4<T> sv = src[c];
   V4<T> dp = dm + (L + source_term(p, sv));
   if (!p.space_charge) dp.w = (T)0;
-  *pc_out = pc;
   *dm_out = dm;
   *sv_out = sv;
   return dp;
+}
+
+// (hi, lo) + d for each component: Knuth's TwoSum of hi and d, its error
+// added to lo, then the pair renormalised (Dekker's FastTwoSum), so that hi
+// stays the nearest float of the level.
+template <typename T>
+__device__ inline void comp_add1(T hi, T lo, T d, T* ho, T* lout) {
+  const T s = hi + d;
+  const T bb = s - hi;
+  const T err = (hi - (s - bb)) + (d - bb);
+  const T l = lo + err;
+  const T h = s + l;
+  *ho = h;
+  *lout = l - (h - s);
+}
+
+template <typename T>
+__device__ inline void comp_add(V4<T> hi, V4<T> lo, V4<T> d, V4<T>* ho, V4<T>* lout) {
+  comp_add1(hi.x, lo.x, d.x, &ho->x, &lout->x);
+  comp_add1(hi.y, lo.y, d.y, &ho->y, &lout->y);
+  comp_add1(hi.z, lo.z, d.z, &ho->z, &lout->z);
+  comp_add1(hi.w, lo.w, d.w, &ho->w, &lout->w);
+}
+
+// psi^{n+1} = psi^n + D^{n+1/2} at vertex c, compensated or plain.
+template <bool kLo, typename T>
+__device__ inline void store_level(const V4<T>* __restrict__ cur, const LoV4* __restrict__ curlo,
+                                   V4<T>* __restrict__ nxt, LoV4* __restrict__ nxtlo,
+                                   long long c, V4<T> d) {
+  if (kLo) {
+    V4<T> h, l;
+    comp_add(ldg4(cur + c), ld_lo<T>(curlo, c), d, &h, &l);
+    nxt[c] = h;
+    st_lo(nxtlo, c, l);
+  } else {
+    nxt[c] = ldg4(cur + c) + d;
+  }
 }
 
 // Boundary vertex b of the launch shape below: grid (x, y, 6) of 32 x 8
@@ -129,10 +175,12 @@ __device__ inline bool boundary_vertex(int nx, int ny, int nz, int* i, int* j, i
 // evaluated here from the same inputs as the interior update (whose D_q^- is
 // still in place).  Face vertices of a second-order grid add mur2_terms.  The
 // boundary sources are zeroed (no deposit reads them).
-template <typename T>
+template <bool kLo, typename T>
 __global__ void __launch_bounds__(256) k_mur_boundary(StencilP<T> p,
                                                       const V4<T>* __restrict__ cur,
+                                                      const LoV4* __restrict__ curlo,
                                                       V4<T>* __restrict__ nxt,
+                                                      LoV4* __restrict__ nxtlo,
                                                       V4<T>* __restrict__ D,
                                                       V4<T>* __restrict__ src) {
   int i, j, k;
@@ -141,14 +189,14 @@ __global__ void __launch_bounds__(256) k_mur_boundary(StencilP<T> p,
             qk = min(max(k, 1), p.nz - 2);
   const int mask = (qi != i) | ((qj != j) << 1) | ((qk != k) << 2);
   const long long b = cidx(i, j, k, p.nx, p.nxy), q = cidx(qi, qj, qk, p.nx, p.nxy);
-  V4<T> pq, dq_old, sq;
-  const V4<T> dq_new = interior_increment(p, cur, D, src, q, &pq, &dq_old, &sq);
+  V4<T> dq_old, sq;
+  const V4<T> dq_new = interior_increment<kLo>(p, cur, curlo, D, src, q, &dq_old, &sq);
   const V4<T> db_old = D[b];
   V4<T> db = mur_beta0(p, mask) * (dq_new - db_old) + dq_old;
   if (p.mur2 && (mask & (mask - 1)) == 0) db = db + mur2_terms(p, cur, mask, b, q);
   if (!p.space_charge) db.w = (T)0;
   D[b] = db;
-  nxt[b] = ldg4(cur + b) + db;
+  store_level<kLo>(cur, curlo, nxt, nxtlo, b, db);
   src[b] = v4((T)0, (T)0, (T)0, (T)0);
 }
 
@@ -163,10 +211,12 @@ __host__ inline dim3 mur_grid(int nx, int ny, int nz) {
 // through L1.  cur holds psi^n, nxt receives psi^{n+1}, D is advanced in
 // place; the consumed sources are zeroed for the deposit of this step
 // (stored only where non-zero).
-template <typename T>
+template <bool kLo, typename T>
 __global__ void __launch_bounds__(256) k_potential_step(StencilP<T> p,
                                                         const V4<T>* __restrict__ cur,
+                                                        const LoV4* __restrict__ curlo,
                                                         V4<T>* __restrict__ nxt,
+                                                        LoV4* __restrict__ nxtlo,
                                                         V4<T>* __restrict__ D,
                                                         V4<T>* __restrict__ src) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -174,11 +224,93 @@ __global__ void __launch_bounds__(256) k_potential_step(StencilP<T> p,
   const int k = blockIdx.z;
   if (i < 1 || i > p.nx - 2 || j < 1 || j > p.ny - 2 || k < 1 || k > p.nz - 2) return;
   const long long c = cidx(i, j, k, p.nx, p.nxy);
-  V4<T> pc, dm, sv;
-  const V4<T> dp = interior_increment(p, cur, D, src, c, &pc, &dm, &sv);
+  V4<T> dm, sv;
+  const V4<T> dp = interior_increment<kLo>(p, cur, curlo, D, src, c, &dm, &sv);
   if (nonzero(sv)) src[c] = v4((T)0, (T)0, (T)0, (T)0);
   D[c] = dp;
-  nxt[c] = pc + dp;
+  store_level<kLo>(cur, curlo, nxt, nxtlo, c, dp);
+}
+
+// Register z-marching form of the interior update (no shared memory): a
+// thread owns column (i, j) for a run of lz planes and keeps, for the planes
+// k-1, k, k+1, the centre value and the x and y neighbour-difference sums in
+// registers, so a plane of psi^n is read once per run (its x and y
+// neighbours are the adjacent threads' loads and hit L1) instead of three
+// times as in the direct form.  Same arithmetic and order as the direct form.
+template <typename T>
+struct PlaneSums {
+  V4<T> c, X, Y;
+};
+
+template <typename T, typename Load>
+__device__ inline PlaneSums<T> plane_sums(Load&& ld, long long q, int nx) {
+  PlaneSums<T> r;
+  r.c = ld(q);
+  r.X = (ld(q + 1) - r.c) + (ld(q - 1) - r.c);
+  r.Y = (ld(q + nx) - r.c) + (ld(q - nx) - r.c);
+  return r;
+}
+
+template <typename T>
+__device__ inline V4<T> plane_laplacian(const StencilP<T>& p, const PlaneSums<T>& m,
+                                        const PlaneSums<T>& z, const PlaneSums<T>& pl) {
+  V4<T> L = p.rxA * (m.X + pl.X) + p.rxB * z.X;
+  L = L + p.ryA * (m.Y + pl.Y) + p.ryB * z.Y;
+  return L + p.rz2 * ((pl.c - z.c) + (m.c - z.c));
+}
+
+template <bool kLo, typename T>
+__global__ void __launch_bounds__(256) k_potential_zloop(StencilP<T> p,
+                                                         const V4<T>* __restrict__ cur,
+                                                         const LoV4* __restrict__ curlo,
+                                                         V4<T>* __restrict__ nxt,
+                                                         LoV4* __restrict__ nxtlo,
+                                                         V4<T>* __restrict__ D,
+                                                         V4<T>* __restrict__ src, int lz) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int kb = max((int)blockIdx.z * lz, 1);
+  const int ke = min((int)blockIdx.z * lz + lz, p.nz - 1);
+  if (kb >= ke || i < 1 || i > p.nx - 2 || j < 1 || j > p.ny - 2) return;
+  const long long col = (long long)j * p.nx + i;
+  const int nx = p.nx;
+  auto hi = [&](long long q) { return ldg4(cur + q); };
+  auto lo = [&](long long q) { return ld_lo<T>(curlo, q); };
+  PlaneSums<T> hm = plane_sums<T>(hi, (long long)(kb - 1) * p.nxy + col, nx);
+  PlaneSums<T> h0 = plane_sums<T>(hi, (long long)kb * p.nxy + col, nx);
+  PlaneSums<T> lm, l0;
+  if (kLo) {
+    lm = plane_sums<T>(lo, (long long)(kb - 1) * p.nxy + col, nx);
+    l0 = plane_sums<T>(lo, (long long)kb * p.nxy + col, nx);
+  }
+  for (int k = kb; k < ke; ++k) {
+    const long long q = (long long)k * p.nxy + col;
+    const PlaneSums<T> hp = plane_sums<T>(hi, q + p.nxy, nx);
+    V4<T> L = plane_laplacian(p, hm, h0, hp);
+    PlaneSums<T> lp;
+    if (kLo) {
+      lp = plane_sums<T>(lo, q + p.nxy, nx);
+      L = L + plane_laplacian(p, lm, l0, lp);
+    }
+    const V4<T> dm = D[q];
+    const V4<T> sv = src[q];
+    V4<T> dp = dm + (L + source_term(p, sv));
+    if (!p.space_charge) dp.w = (T)0;
+    if (nonzero(sv)) src[q] = v4((T)0, (T)0, (T)0, (T)0);
+    D[q] = dp;
+    if (kLo) {
+      V4<T> h, l;
+      comp_add(h0.c, l0.c, dp, &h, &l);
+      nxt[q] = h;
+      st_lo(nxtlo, q, l);
+      lm = l0;
+      l0 = lp;
+    } else {
+      nxt[q] = h0.c + dp;
+    }
+    hm = h0;
+    h0 = hp;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -343,8 +475,8 @@ __device__ inline bool interior(int i, int j, int k, int nx, int ny, int nz) {
 // component of src.
 template <typename T>
 __global__ void k_extract(PicP<T> p, const V4<T>* __restrict__ pn, const V4<T>* __restrict__ D,
-                          const V4<T>* __restrict__ lev, const V4<T>* __restrict__ src, int what,
-                          double* __restrict__ out) {
+                          const V4<T>* __restrict__ lev, const LoV4* __restrict__ levlo,
+                          const V4<T>* __restrict__ src, int what, double* __restrict__ out) {
   const long long ncell = p.nxy * p.nz;
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell;
        c += (long long)gridDim.x * blockDim.x) {
@@ -362,6 +494,10 @@ __global__ void k_extract(PicP<T> p, const V4<T>* __restrict__ pn, const V4<T>* 
       const V4<T> a = (what < 10) ? lev[c] : src[c];
       const int comp = (what - 6) & 3;
       val = (double)(comp == 0 ? a.x : comp == 1 ? a.y : comp == 2 ? a.z : a.w);
+      if (what < 10 && levlo) {
+        const V4<T> l = ld_lo<T>(levlo, c);
+        val += (double)(comp == 0 ? l.x : comp == 1 ? l.y : comp == 2 ? l.z : l.w);
+      }
     }
     out[c] = val;
   }
@@ -370,23 +506,30 @@ __global__ void k_extract(PicP<T> p, const V4<T>* __restrict__ pn, const V4<T>* 
 // Host field -> one component of a device array.
 template <typename T>
 __global__ void k_insert(long long ncell, const double* __restrict__ in, V4<T>* __restrict__ dst,
-                         int comp) {
+                         LoV4* __restrict__ dstlo, int comp) {
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell;
        c += (long long)gridDim.x * blockDim.x) {
-    T v = (T)in[c];
+    const T v = (T)in[c];
     V4<T> a = dst[c];
     if (comp == 0) a.x = v; else if (comp == 1) a.y = v; else if (comp == 2) a.z = v; else a.w = v;
     dst[c] = a;
+    if (dstlo) {  // the rest of the double value below hi
+      const T r = (T)(in[c] - (double)v);
+      V4<T> l = ld_lo<T>(dstlo, c);
+      if (comp == 0) l.x = r; else if (comp == 1) l.y = r; else if (comp == 2) l.z = r; else l.w = r;
+      st_lo(dstlo, c, l);
+    }
   }
 }
 
 // D = newest - previous level (after a level was set from the host).
 template <typename T>
 __global__ void k_increment(long long ncell, const V4<T>* __restrict__ pn,
-                            const V4<T>* __restrict__ po, V4<T>* __restrict__ D) {
+                            const V4<T>* __restrict__ po, const LoV4* __restrict__ pnlo,
+                            const LoV4* __restrict__ polo, V4<T>* __restrict__ D) {
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < ncell;
        c += (long long)gridDim.x * blockDim.x)
-    D[c] = pn[c] - po[c];
+    D[c] = pnlo ? (pn[c] - po[c]) + (ld_lo<T>(pnlo, c) - ld_lo<T>(polo, c)) : pn[c] - po[c];
 }
 
 // Point samples: out[pt * m + s] for the s-th field of mask.

@@ -41,6 +41,7 @@ struct mithra_sim {
   void* P[2] = {nullptr, nullptr};  // psi ping-pong; P[cur] is the newest level
   void* D = nullptr;                // increment newest - previous level
   void* S = nullptr;
+  void* PL[2] = {nullptr, nullptr};  // lo parts of the compensated levels (P32_C, P32_U64)
   void* pbuf[2] = {nullptr, nullptr};
   int* key = nullptr;
   int* rank = nullptr;
@@ -159,7 +160,11 @@ mithra_status cuda_fail(mithra_sim* s, cudaError_t e, const char* where) {
   } while (0)
 
 size_t real_size(int prec) { return prec == MITHRA_P64 ? sizeof(double) : sizeof(float); }
-size_t mom_size(int prec) { return prec == MITHRA_P32 ? sizeof(float) : sizeof(double); }
+size_t mom_size(int prec) {
+  return (prec == MITHRA_P32 || prec == MITHRA_P32_C) ? sizeof(float) : sizeof(double);
+}
+// compensated (hi + lo) potential levels
+bool has_lo(int prec) { return prec == MITHRA_P32_C || prec == MITHRA_P32_U64; }
 
 // Calls f with null pointers whose pointee types are the field / fraction
 // type T and the momentum type U of the precision mode.
@@ -390,13 +395,25 @@ mithra_status launch_step(mithra_sim* s) {
   const PicP<T> pp = make_pic<T>(s);
   V4<T>* P0 = static_cast<V4<T>*>(s->P[s->cur]);       // psi^n
   V4<T>* P1 = static_cast<V4<T>*>(s->P[1 - s->cur]);   // receives psi^{n+1}
+  LoV4* L0 = static_cast<LoV4*>(s->PL[s->cur]);        // lo parts (compensated levels)
+  LoV4* L1 = static_cast<LoV4*>(s->PL[1 - s->cur]);
   V4<T>* Dn = static_cast<V4<T>*>(s->D);               // D^{n-1/2} -> D^{n+1/2}
   V4<T>* S = static_cast<V4<T>*>(s->S);
   {
     ProfScope ps(s, K_POTENTIAL);
-    k_mur_boundary<T><<<mur_grid(s->g.nx, s->g.ny, s->g.nz), dim3(32, 8), 0, s->stream>>>(
-        sp, P0, P1, Dn, S);
-    if (s->stencil_variant == 1 && s->have_tm) {
+    const dim3 mg = mur_grid(s->g.nx, s->g.ny, s->g.nz);
+    if (L0)
+      k_mur_boundary<true, T><<<mg, dim3(32, 8), 0, s->stream>>>(sp, P0, L0, P1, L1, Dn, S);
+    else
+      k_mur_boundary<false, T><<<mg, dim3(32, 8), 0, s->stream>>>(sp, P0, L0, P1, L1, Dn, S);
+    if (s->stencil_variant == 2) {
+      dim3 blk(32, 8, 1);
+      dim3 grd((s->g.nx + 31) / 32, (s->g.ny + 7) / 8, (s->g.nz + s->lz - 1) / s->lz);
+      if (L0)
+        k_potential_zloop<true, T><<<grd, blk, 0, s->stream>>>(sp, P0, L0, P1, L1, Dn, S, s->lz);
+      else
+        k_potential_zloop<false, T><<<grd, blk, 0, s->stream>>>(sp, P0, L0, P1, L1, Dn, S, s->lz);
+    } else if (s->stencil_variant == 1 && s->have_tm && !L0) {
       dim3 grd((s->g.nx + kMX - 1) / kMX, (s->g.ny + kMY - 1) / kMY,
                (s->g.nz + s->lz - 1) / s->lz);
       k_potential_march<T><<<grd, kMX * kMY, march_smem_bytes<T>(), s->stream>>>(
@@ -404,7 +421,10 @@ mithra_status launch_step(mithra_sim* s) {
     } else {
       dim3 blk(32, 8, 1);
       dim3 grd((s->g.nx + 31) / 32, (s->g.ny + 7) / 8, s->g.nz);
-      k_potential_step<T><<<grd, blk, 0, s->stream>>>(sp, P0, P1, Dn, S);
+      if (L0)
+        k_potential_step<true, T><<<grd, blk, 0, s->stream>>>(sp, P0, L0, P1, L1, Dn, S);
+      else
+        k_potential_step<false, T><<<grd, blk, 0, s->stream>>>(sp, P0, L0, P1, L1, Dn, S);
     }
   }
   if (s->power_cap > 0) {
@@ -502,15 +522,20 @@ mithra_status copy_field_impl(mithra_sim* s, int what, double* out) {
   const V4<T>* Po = static_cast<const V4<T>*>(s->P[1 - s->cur]);
   const V4<T>* Dn = static_cast<const V4<T>*>(s->D);
   const V4<T>* lev = Pn;
+  const LoV4* levlo = static_cast<const LoV4*>(s->PL[s->cur]);
   int code = 0;
   if (what <= MITHRA_BZ) code = what;
   else if (what <= MITHRA_AZ) code = 6 + (what - MITHRA_AX);
   else if (what <= MITHRA_JZ) code = 10 + (what - MITHRA_JX);
   else if (what == MITHRA_PHI) code = 9;
   else if (what == MITHRA_RHO) code = 13;
-  else { lev = Po; code = 6 + (what - MITHRA_AX_PREV); }
-  k_extract<T><<<1024, 256, 0, s->stream>>>(pp, Pn, Dn, lev, static_cast<const V4<T>*>(s->S),
-                                            code, d);
+  else {
+    lev = Po;
+    levlo = static_cast<const LoV4*>(s->PL[1 - s->cur]);
+    code = 6 + (what - MITHRA_AX_PREV);
+  }
+  k_extract<T><<<1024, 256, 0, s->stream>>>(pp, Pn, Dn, lev, levlo,
+                                            static_cast<const V4<T>*>(s->S), code, d);
   MCHECK(s, cudaGetLastError());
   MCHECK(s, cudaMemcpyAsync(out, d, sizeof(double) * n, cudaMemcpyDeviceToHost, s->stream));
   mithra_status st = sync_status(s);
@@ -522,21 +547,24 @@ template <typename T>
 mithra_status set_field_impl(mithra_sim* s, int what, const double* in) {
   const int64_t n = ncell_of(&s->g);
   V4<T>* dst;
+  LoV4* dstlo = nullptr;
   int comp;
-  if (what >= MITHRA_AX && what <= MITHRA_AZ) { dst = static_cast<V4<T>*>(s->P[s->cur]); comp = what - MITHRA_AX; }
-  else if (what == MITHRA_PHI) { dst = static_cast<V4<T>*>(s->P[s->cur]); comp = 3; }
+  LoV4* Lc = static_cast<LoV4*>(s->PL[s->cur]);
+  LoV4* Lp = static_cast<LoV4*>(s->PL[1 - s->cur]);
+  if (what >= MITHRA_AX && what <= MITHRA_AZ) { dst = static_cast<V4<T>*>(s->P[s->cur]); dstlo = Lc; comp = what - MITHRA_AX; }
+  else if (what == MITHRA_PHI) { dst = static_cast<V4<T>*>(s->P[s->cur]); dstlo = Lc; comp = 3; }
   else if (what >= MITHRA_JX && what <= MITHRA_JZ) { dst = static_cast<V4<T>*>(s->S); comp = what - MITHRA_JX; }
   else if (what == MITHRA_RHO) { dst = static_cast<V4<T>*>(s->S); comp = 3; }
-  else if (what >= MITHRA_AX_PREV && what <= MITHRA_PHI_PREV) { dst = static_cast<V4<T>*>(s->P[1 - s->cur]); comp = what - MITHRA_AX_PREV; }
+  else if (what >= MITHRA_AX_PREV && what <= MITHRA_PHI_PREV) { dst = static_cast<V4<T>*>(s->P[1 - s->cur]); dstlo = Lp; comp = what - MITHRA_AX_PREV; }
   else return fail(s, MITHRA_EINVAL, "field cannot be set (E and B derive from the potentials)");
   double* d = nullptr;
   MCHECK(s, cudaMalloc(&d, sizeof(double) * n));
   MCHECK(s, cudaMemcpyAsync(d, in, sizeof(double) * n, cudaMemcpyHostToDevice, s->stream));
-  k_insert<T><<<1024, 256, 0, s->stream>>>(n, d, dst, comp);
+  k_insert<T><<<1024, 256, 0, s->stream>>>(n, d, dst, dstlo, comp);
   if (dst != static_cast<V4<T>*>(s->S))
     k_increment<T><<<1024, 256, 0, s->stream>>>(n, static_cast<const V4<T>*>(s->P[s->cur]),
                                                 static_cast<const V4<T>*>(s->P[1 - s->cur]),
-                                                static_cast<V4<T>*>(s->D));
+                                                Lc, Lp, static_cast<V4<T>*>(s->D));
   MCHECK(s, cudaGetLastError());
   mithra_status st = sync_status(s);
   cudaFree(d);
@@ -630,7 +658,7 @@ void lab_of(const mithra_sim* s, int32_t kp, double t, double* t_lab, double* z_
 
 void free_all(mithra_sim* s) {
   if (s->stream) cudaStreamSynchronize(s->stream);
-  void* ptrs[] = {s->P[0], s->P[1], s->D, s->S, s->pbuf[0], s->pbuf[1], s->key, s->rank, s->count,
+  void* ptrs[] = {s->P[0], s->P[1], s->PL[0], s->PL[1], s->D, s->S, s->pbuf[0], s->pbuf[1], s->key, s->rank, s->count,
                   s->offset, s->tiles, s->scan_part, s->dstate, s->d_scalar, s->d_power_rec,
                   s->d_spec_omega, s->d_spec_acc, s->d_spec_out, s->d_spec_samples};
   for (void* p : ptrs)
@@ -672,6 +700,7 @@ mithra_status mithra_footprint(const mithra_grid* grid, int64_t n_particles,
   const int64_t nkeys = (int64_t)ntx * nty * ntz;
   const size_t r = real_size(precision);
   int64_t b = 4 * ncell_of(grid) * 4 * (int64_t)r;              // 2 levels, increment, sources
+  if (has_lo(precision)) b += 2 * ncell_of(grid) * (int64_t)sizeof(LoV4);  // lo parts
   b += 2 * (int64_t)particle_buffer_bytes(n_particles, precision);
   b += 2 * n_particles * (int64_t)sizeof(int);                   // key, rank
   b += 3 * (nkeys + 2) * (int64_t)sizeof(int);                   // count, offset, tiles
@@ -692,8 +721,10 @@ mithra_status mithra_create(const mithra_grid* grid, const mithra_undulator* und
   if (!und) return fail(nullptr, MITHRA_EINVAL, "undulator is NULL");
   if (!(und->gamma0 > 1.0) || !(und->lambda_u > 0.0))
     return fail(nullptr, MITHRA_EINVAL, "undulator needs gamma0 > 1 and lambda_u > 0");
-  if (precision != MITHRA_P32 && precision != MITHRA_P64 && precision != MITHRA_P32_U64)
-    return fail(nullptr, MITHRA_EINVAL, "precision must be MITHRA_P64, MITHRA_P32 or MITHRA_P32_U64");
+  if (precision != MITHRA_P32 && precision != MITHRA_P64 && precision != MITHRA_P32_U64 &&
+      precision != MITHRA_P32_C)
+    return fail(nullptr, MITHRA_EINVAL,
+                "precision must be MITHRA_P64, MITHRA_P32, MITHRA_P32_U64 or MITHRA_P32_C");
   const int64_t np = bunch ? bunch->n : 0;
   if (np < 0 || np >= ((int64_t)1 << 31)) return fail(nullptr, MITHRA_EINVAL, "bad particle count");
   if (np > 0 && (!bunch->x || !bunch->y || !bunch->z || !bunch->ux || !bunch->uy || !bunch->uz))
@@ -743,12 +774,17 @@ mithra_status mithra_create(const mithra_grid* grid, const mithra_undulator* und
             dalloc((void**)&s->scan_part, sizeof(int4) * (size_t)(s->nkeys / kScanBlock + 2)) &&
             dalloc((void**)&s->dstate, sizeof(StepState)) &&
             dalloc((void**)&s->d_scalar, sizeof(double));
+  const size_t lo_bytes = (size_t)ncell_of(grid) * sizeof(LoV4);
+  if (ok && has_lo(precision))
+    ok = dalloc(&s->PL[0], lo_bytes) && dalloc(&s->PL[1], lo_bytes);
   if (!ok) return bail(MITHRA_ENOMEM, "device allocation failed");
   if (cudaMallocHost((void**)&s->h_err, sizeof(int)) != cudaSuccess)
     return bail(MITHRA_ENOMEM, "pinned allocation failed");
   *s->h_err = 0;
   cudaMemsetAsync(s->P[0], 0, field_bytes, s->stream);
   cudaMemsetAsync(s->P[1], 0, field_bytes, s->stream);
+  for (void* l : s->PL)
+    if (l) cudaMemsetAsync(l, 0, lo_bytes, s->stream);
   cudaMemsetAsync(s->D, 0, field_bytes, s->stream);
   cudaMemsetAsync(s->S, 0, field_bytes, s->stream);
   cudaMemsetAsync(s->count, 0, sizeof(int) * (size_t)(s->nkeys + 2), s->stream);
@@ -768,7 +804,7 @@ mithra_status mithra_create(const mithra_grid* grid, const mithra_undulator* und
                                   kTP) &&
                  encode_field_map(&s->tm_col_d, s->D, es, grid->nx, grid->ny, grid->nz, kMX, kMY) &&
                  encode_field_map(&s->tm_col_s, s->S, es, grid->nx, grid->ny, grid->nz, kMX, kMY);
-    s->stencil_variant = s->have_tm ? 1 : 0;
+    s->stencil_variant = (s->have_tm && !s->PL[0]) ? 1 : 0;
     s->push_variant = s->have_tm ? 1 : 0;
     st = with_types(precision, [&](auto t, auto u) {
       TYPES_OF(t, u);
@@ -1049,15 +1085,19 @@ const char* mithra_kernel_name(int32_t kernel) {
 
 mithra_status mithra_set_tuning(mithra_sim* s, const mithra_tuning* t) {
   if (!s) return fail(nullptr, MITHRA_EINVAL, "sim is NULL");
-  if (!t || t->stencil_variant < 0 || t->stencil_variant > 1 || t->lz < 0 ||
+  if (!t || t->stencil_variant < 0 || t->stencil_variant > 2 || t->lz < 0 ||
       t->push_variant < 0 || t->push_variant > 1 || t->push_ctas_per_sm < 0 ||
       t->push_sparse_below < 0)
     return fail(s, MITHRA_EINVAL,
-                "bad tuning: variants 0 or 1, lz >= 0, ctas >= 0, sparse_below >= 0");
+                "bad tuning: stencil variant 0..2, push variant 0 or 1, lz >= 0, ctas >= 0, "
+                "sparse_below >= 0");
   if ((t->stencil_variant == 1 || t->push_variant == 1) && !s->have_tm)
     return fail(s, MITHRA_EINVAL, "TMA tensor maps unavailable: variant 1 disabled");
+  if (t->stencil_variant == 1 && s->PL[0])
+    return fail(s, MITHRA_EINVAL,
+                "the marching update keeps single-float levels: not with compensated levels");
   s->stencil_variant = t->stencil_variant;
-  s->lz = t->lz > 0 ? t->lz : default_lz(&s->g, s->march_resident);
+  s->lz = t->lz > 0 ? t->lz : (t->stencil_variant == 2 ? 16 : default_lz(&s->g, s->march_resident));
   s->push_variant = t->push_variant;
   s->push_ctas_per_sm = t->push_ctas_per_sm;
   s->push_sparse_below = t->push_sparse_below;

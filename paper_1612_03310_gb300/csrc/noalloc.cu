@@ -159,7 +159,8 @@ mithra_status mithra_plane_power_noalloc(const mithra_grid* grid, double gamma0,
     return na_fail(MITHRA_EINVAL, "grid has >= 2^31 vertices");
   if (k_plane < 1 || k_plane > grid->nz - 2) return na_fail(MITHRA_EINVAL, "k_plane outside [1, nz-2]");
   if (!(gamma0 > 1.0)) return na_fail(MITHRA_EINVAL, "gamma0 must be > 1");
-  if (precision != MITHRA_P64 && precision != MITHRA_P32 && precision != MITHRA_P32_U64)
+  if (precision != MITHRA_P64 && precision != MITHRA_P32 && precision != MITHRA_P32_U64 &&
+      precision != MITHRA_P32_C)
     return na_fail(MITHRA_EINVAL, "bad precision");
   double* scratch = nullptr;
   mithra_status st = scratch_of_current_device(&scratch);

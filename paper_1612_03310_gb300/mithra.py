@@ -15,7 +15,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "_build", "libmithra.so")
 
 OK, EINVAL, EUNSTABLE, ENOMEM, ECUDA, ENUMERIC, ELOST, EBUSY, ENODEV = range(9)
-P64, P32, P32_U64 = 0, 1, 2
+P64, P32, P32_U64, P32_C = 0, 1, 2, 3
 FIELDS = ["Ex", "Ey", "Ez", "Bx", "By", "Bz", "Ax", "Ay", "Az", "Jx", "Jy", "Jz", "phi", "rho",
           "Ax_prev", "Ay_prev", "Az_prev", "phi_prev"]
 FIELD_ID = {name: i for i, name in enumerate(FIELDS)}

@@ -66,6 +66,8 @@ def test_footprint_scales(M):
     ncell = 128 * 128 * 1024
     assert b32 > 3 * ncell * 16
     assert 1.6 < b64 / b32 < 2.0
+    # compensated levels: the lo parts of both levels (4 bfloat16 per vertex)
+    assert M.footprint(g, 2 ** 21, M.P32_C) == b32 + 2 * ncell * 8
 
 
 def test_create_without_gpu_fails_loudly(M):

