@@ -140,6 +140,11 @@ KERNELS_PER_SCOPE = {"potential_step": 2, "scan_counts": 2}
 
 PRECISIONS = {"p32": "P32", "p32_u64": "P32_U64", "p32_c": "P32_C", "p64": "P64"}
 
+# DRAM bytes (read + write) per launch from one ncu capture of the kernels as
+# they are now (profiles/top_kernels_c2_p32.md), by (kernel, precision,
+# workload); a kernel changed since its capture must leave this table
+NCU_TRAFFIC = {("push", "p32", "c2"): 179166464 + 61266944}
+
 
 def algorithmic_bytes(kernel: str, grid: dict, n_particles: int, prec: str) -> float:
     """Algorithmic bytes per launch (the minimum a kernel must move)."""
@@ -584,7 +589,7 @@ def main():
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "peak_kind": peak_kind,
                      "algorithmic_bytes_per_launch": ab, "avg_launch_ms": avg_ms,
-                     "traffic": None},
+                     "traffic": NCU_TRAFFIC.get((dom, args.precision, args.workload))},
         "stencil": {"kernel": "potential_step", "avg_launch_ms": stencil_ms,
                     "achieved_gbs": stencil_gbs, "frac": stencil_gbs / peak,
                     "cell_updates_per_s": ncell / (stencil_ms / 1e3)},

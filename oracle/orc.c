@@ -260,8 +260,77 @@ void orc_fields(const orc_grid* g, const double* lev_n, const double* lev_np1,
  * B'_y = B0 cosh(ku y) ku zeta exp(-(ku zeta)^2/2), B'_z = B0 sinh(ku y) exp(..).
  * B0 from K = e B0 lambda_u / (2 pi m c).  Transformed to the frame moving with
  * beta0 along +z. */
+/* Optical undulator (input group UNDULATOR with undulator-type optical and
+ * beam-type plane-wave; the signal types of the FIELD section): in the lab the
+ * vector potential is A' = p A0 s(tau) with tau = t' - d (z' - z0)/c, so
+ *   E' = -dA'/dt' = -p A0 s'(tau),   B' = curl A' = -(d/c) z x p A0 s'(tau).
+ * s is the signal of the paper's list with x = tau - t0, w = 2 pi c / lambda0,
+ * carrier C = cos(w x + cep), envelope width tau_v (variance / c):
+ *   Gaussian  s = C exp(-2 ln2 x^2/tau_v^2)
+ *   sech      s = C / cosh(x/tau_v)
+ *   flat-top  s = C exp(-2 ln2 x^2/tau_v^2) for x <= 0, s = C for x > 0
+ *   Neumann   s = -4 ln2 (x/tau_v) C exp(-2 ln2 x^2/tau_v^2)
+ * (the Neumann signal is written with x/tau_v where the paper prints
+ * x/tau^2, so that A0 keeps its meaning as the amplitude).  s' is the exact
+ * derivative.  The rest frame moves at +beta0 c along z:
+ *   E_perp = gamma0 (E' + v x B'),  B_perp = gamma0 (B' - v x E'/c^2). */
+static double signal_derivative(const orc_undulator* u, double x) {
+    const double w = 2.0 * ORC_PI * ORC_C / u->lambda_l;
+    const double tv = u->variance / ORC_C;
+    const double ph = w * x + u->cep;
+    const double C = cos(ph), dC = -w * sin(ph);
+    const double a = 2.0 * log(2.0) / (tv * tv);
+    switch (u->signal) {
+        case 0: {
+            const double G = exp(-a * x * x);
+            const double k = -4.0 * log(2.0) / tv;
+            /* d/dx [k x C G] */
+            return k * (C * G + x * dC * G + x * C * (-2.0 * a * x) * G);
+        }
+        case 1: {
+            const double G = exp(-a * x * x);
+            return dC * G + C * (-2.0 * a * x) * G;
+        }
+        case 2: {
+            const double ch = cosh(x / tv);
+            return dC / ch - C * tanh(x / tv) / (tv * ch);
+        }
+        default: {
+            if (x > 0.0) return dC;
+            const double G = exp(-a * x * x);
+            return dC * G + C * (-2.0 * a * x) * G;
+        }
+    }
+}
+
+static void optical_field(const orc_undulator* u, double z, double t, double E[3], double B[3]) {
+    const double g0 = u->gamma0;
+    const double b0 = sqrt(1.0 - 1.0 / (g0 * g0));
+    const double d = (double)u->direction;
+    const double zl = g0 * (z + b0 * ORC_C * t);
+    const double tl = g0 * (t + b0 * z / ORC_C);
+    const double tau = tl - d * (zl - u->z0_lab) / ORC_C;
+    const double A0 = u->a0 * ORC_ME * ORC_C / ORC_E;
+    const double sp = signal_derivative(u, tau - u->offset / ORC_C);
+    /* lab fields: E' = -p A0 s', B' = -(d/c) z x p A0 s' with z x p = (-p_y, p_x, 0) */
+    const double Ex = -u->pol_x * A0 * sp, Ey = -u->pol_y * A0 * sp;
+    const double Bx = -(d / ORC_C) * (-u->pol_y) * A0 * sp;
+    const double By = -(d / ORC_C) * (u->pol_x) * A0 * sp;
+    /* v x F = b0 c z x F = b0 c (-F_y, F_x, 0) */
+    E[0] = g0 * (Ex - b0 * ORC_C * By);
+    E[1] = g0 * (Ey + b0 * ORC_C * Bx);
+    E[2] = 0.0;
+    B[0] = g0 * (Bx + b0 * Ey / ORC_C);
+    B[1] = g0 * (By - b0 * Ex / ORC_C);
+    B[2] = 0.0;
+}
+
 void orc_undulator_field(const orc_undulator* u, double y, double z, double t,
                          double E[3], double B[3]) {
+    if (u->type == 1) {
+        optical_field(u, z, t, E, B);
+        return;
+    }
     const double g0 = u->gamma0;
     const double b0 = sqrt(1.0 - 1.0 / (g0 * g0));
     const double ku = 2.0 * ORC_PI / u->lambda_u;

@@ -45,6 +45,22 @@ typedef struct {
     double z_ent_lab;       /* lab z' of the undulator entrance [m] */
     double length_lab;      /* lab length [m]; <= 0 means no exit */
     int32_t fringe;         /* 1: Neumann-shaped fringe outside [0, L] */
+    int32_t type;           /* 0: static undulator; 1: optical undulator, a plane
+                               wave along z (input group UNDULATOR, beam-type
+                               plane-wave) */
+    /* optical undulator, lab frame: vector potential A' = p A0 s(tau),
+     * tau = t' - d (z' - z0)/c, a0 = e A0 / (m_e c) */
+    double a0;              /* strength parameter */
+    double lambda_l;        /* carrier wavelength lambda0 [m] */
+    double pol_x, pol_y;    /* unit transverse polarization p */
+    double z0_lab;          /* reference position of the wave [m] */
+    double offset;          /* c t0 [m] */
+    double variance;        /* c tau [m] */
+    double cep;             /* carrier envelope phase [rad] */
+    int32_t direction;      /* d = -1: the wave travels towards -z; +1: towards +z */
+    int32_t signal;         /* 0 modulated Neumann, 1 modulated Gaussian,
+                               2 modulated hyperbolic secant, 3 sinusoidal pulse
+                               (flat-top) */
 } orc_undulator;
 
 /* Coefficients of the update equation (Eq. updateEquation):
@@ -64,8 +80,9 @@ void orc_potential_step(const orc_grid* g, const double* prev, const double* cur
 void orc_fields(const orc_grid* g, const double* lev_n, const double* lev_np1,
                 double* E, double* B);
 
-/* Static undulator field in the rest frame at (y, z, t) (Eq. undulatorField,
- * transformed to the moving frame). */
+/* Undulator field in the rest frame at (y, z, t): the static undulator
+ * (Eq. undulatorField) or the optical plane wave, transformed to the moving
+ * frame. */
 void orc_undulator_field(const orc_undulator* u, double y, double z, double t,
                          double E[3], double B[3]);
 
