@@ -99,13 +99,28 @@ typedef struct {
     int32_t space_charge;  /* 0: phi is held at zero */
 } mithra_grid;
 
-/* Static planar undulator (Eq. undulatorField), given in the laboratory frame:
+/* Undulator, given in the laboratory frame.  The rest frame moves with gamma0
+ * along +z; a rest-frame event (z, t) is at lab position gamma0 (z + beta0 c t)
+ * and lab time gamma0 (t + beta0 z / c).
+ * type 0, static planar undulator (Eq. undulatorField):
  * B'_y = B0 cosh(ku y) sin(ku zeta), B'_z = B0 sinh(ku y) cos(ku zeta) with
  * zeta the lab distance past the entrance, K = e B0 lambda_u / (2 pi m c).
- * The rest frame moves with gamma0 along +z; a rest-frame event (z, t) is at
- * lab position gamma0 (z + beta0 c t).  With fringe = 1 the field outside
- * [0, length_lab] is the Neumann-shaped taper of Sec. "Undulator Field" (at
- * the exit in the distance past it).  length_lab <= 0: no exit. */
+ * With fringe = 1 the field outside [0, length_lab] is the Neumann-shaped
+ * taper of Sec. "Undulator Field" (at the exit in the distance past it).
+ * length_lab <= 0: no exit.  K = 0 switches the undulator off.
+ * type 1, optical undulator (input group UNDULATOR, undulator-type optical,
+ * beam-type plane-wave): a plane wave along z with vector potential
+ * A' = p A0 s(tau), tau = t' - direction (z' - z0_lab)/c, a0 = e A0/(m c),
+ * p = (pol_x, pol_y) the unit transverse polarization (normalised by the
+ * library), s the signal of the FIELD section's list with x = tau - offset/c,
+ * w0 = 2 pi c / lambda_l, tau_v = variance / c, C = cos(w0 x + cep):
+ *   signal 0 modulated Neumann   -4 ln2 (x/tau_v) C exp(-2 ln2 x^2/tau_v^2)
+ *   signal 1 modulated Gaussian   C exp(-2 ln2 x^2/tau_v^2)
+ *   signal 2 hyperbolic secant    C / cosh(x/tau_v)
+ *   signal 3 sinusoidal pulse     the Gaussian for x <= 0, C for x > 0
+ *                                 (flat-top)
+ * E' = -dA'/dt', B' = curl A'; direction -1 travels towards -z (the
+ * counter-propagating laser of the paper's examples), +1 towards +z. */
 typedef struct {
     double gamma0;
     double lambda_u;
@@ -113,6 +128,16 @@ typedef struct {
     double z_ent_lab;
     double length_lab;
     int32_t fringe;
+    int32_t type;         /* 0 static, 1 optical plane wave */
+    double a0;            /* optical: strength parameter */
+    double lambda_l;      /* optical: carrier wavelength [m] */
+    double pol_x, pol_y;  /* optical: transverse polarization */
+    double z0_lab;        /* optical: reference position of the wave [m] */
+    double offset;        /* optical: c t0 [m] */
+    double variance;      /* optical: c tau_v [m] */
+    double cep;           /* optical: carrier envelope phase [rad] */
+    int32_t direction;    /* optical: -1 or +1 */
+    int32_t signal;       /* optical: 0..3 */
 } mithra_undulator;
 
 /* Macroparticles, host arrays of n doubles in the rest frame at t = t0:

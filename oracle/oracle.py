@@ -98,6 +98,8 @@ def lib():
                                                  C.c_int32, C.c_double, C.c_double, C.c_int32,
                                                  dp, dp]
         _lib.orc_spectrum_density.argtypes = [C.POINTER(_Grid), C.c_int32, dp, dp]
+        _lib.orc_seed_correction.argtypes = [C.POINTER(_Grid), C.POINTER(_Und), C.c_double, dp]
+        _lib.orc_incident_potential.argtypes = [C.POINTER(_Und), C.c_double, C.c_double, dp]
     return _lib
 
 
@@ -203,6 +205,12 @@ def spectrum_density(g: dict, n_freq: int, acc: np.ndarray) -> np.ndarray:
     return out
 
 
+def incident_potential(u: dict, z: float, t: float) -> np.ndarray:
+    out = np.zeros(2)
+    lib().orc_incident_potential(C.byref(make_und(dict(u, type="optical"))), z, t, _p(out))
+    return out
+
+
 def observed_omega(lambda_lab, gamma0: float) -> np.ndarray:
     """Angular frequency at which a forward lab wave of wavelength lambda_lab
     passes a plane moving with the rest frame: 2 pi c (1 - beta0) / lambda."""
@@ -260,6 +268,7 @@ class OracleSim:
         self.t0 = float(t0)
         self.n = 0
         self.power: list[PowerSample] = []
+        self.seed = None
         self.spec_plane = None
         self.spec_omega = None
         self.spec_acc = None
@@ -282,6 +291,11 @@ class OracleSim:
                                    _p(out))
         return out
 
+    def set_seed(self, seed: dict | None):
+        """Plane-wave seed injected through the TF/SF planes (orc_seed_correction);
+        the same keys as an optical undulator; None switches it off."""
+        self.seed = None if seed is None else make_und(dict(seed, type="optical"))
+
     def bunch_stats(self, k_b: float) -> np.ndarray:
         return bunch_stats(self.x, self.y, self.z, self.ux, self.uy, self.uz, self.lost, k_b)
 
@@ -301,6 +315,9 @@ class OracleSim:
         for _ in range(nsteps):
             L.orc_potential_step(C.byref(self._G), _p(self.prev), _p(self.cur), _p(self.src),
                                  _p(self.nxt))
+            if self.seed is not None:
+                L.orc_seed_correction(C.byref(self._G), C.byref(self.seed),
+                                      self.t0 + self.n * self.g["dt"], _p(self.nxt))
             L.orc_fields(C.byref(self._G), _p(self.cur), _p(self.nxt), _p(self.E), _p(self.B))
             self.src_next[:] = 0.0
             th = self.t_half()

@@ -303,6 +303,60 @@ static double signal_derivative(const orc_undulator* u, double x) {
     }
 }
 
+static double signal_value(const orc_undulator* u, double x) {
+    const double w = 2.0 * ORC_PI * ORC_C / u->lambda_l;
+    const double tv = u->variance / ORC_C;
+    const double C = cos(w * x + u->cep);
+    const double a = 2.0 * log(2.0) / (tv * tv);
+    switch (u->signal) {
+        case 0: return -4.0 * log(2.0) * (x / tv) * C * exp(-a * x * x);
+        case 1: return C * exp(-a * x * x);
+        case 2: return C / cosh(x / tv);
+        default: return x > 0.0 ? C : C * exp(-a * x * x);
+    }
+}
+
+static double wave_tau(const orc_undulator* u, double z, double t) {
+    const double g0 = u->gamma0;
+    const double b0 = sqrt(1.0 - 1.0 / (g0 * g0));
+    const double zl = g0 * (z + b0 * ORC_C * t);
+    const double tl = g0 * (t + b0 * z / ORC_C);
+    return tl - (double)u->direction * (zl - u->z0_lab) / ORC_C;
+}
+
+void orc_incident_potential(const orc_undulator* u, double z, double t, double out[2]) {
+    const double A0 = u->a0 * ORC_ME * ORC_C / ORC_E;
+    const double s = signal_value(u, wave_tau(u, z, t) - u->offset / ORC_C);
+    out[0] = u->pol_x * A0 * s;
+    out[1] = u->pol_y * A0 * s;
+}
+
+void orc_seed_correction(const orc_grid* g, const orc_undulator* seed, double t_n,
+                         double* next) {
+    double co[6];
+    orc_coefficients(g, co);
+    const double A = co[0], a2 = co[2], a4 = co[3], a6 = co[4];
+    const int64_t n = ncell(g);
+    const int ks = 2, kt = 3;
+    double fs[2], ft[2];
+    /* the incident potential on the two planes (uniform in x and y) */
+    orc_incident_potential(seed, g->z0 + ks * g->dz, t_n, fs);
+    orc_incident_potential(seed, g->z0 + kt * g->dz, t_n, ft);
+    for (int c = 0; c < 2; ++c) {
+        double* pn = next + c * n;
+        for (int j = 1; j < g->ny - 1; ++j) {
+            for (int i = 1; i < g->nx - 1; ++i) {
+                /* scattered-field plane: its k+1 neighbours hold the total field */
+                pn[ix(g, i, j, ks)] -= A * (a2 * ft[c] + a2 * ft[c] + a4 * ft[c] + a4 * ft[c])
+                                     + a6 * ft[c];
+                /* total-field plane: its k-1 neighbours hold the scattered field */
+                pn[ix(g, i, j, kt)] += A * (a2 * fs[c] + a2 * fs[c] + a4 * fs[c] + a4 * fs[c])
+                                     + a6 * fs[c];
+            }
+        }
+    }
+}
+
 static void optical_field(const orc_undulator* u, double z, double t, double E[3], double B[3]) {
     const double g0 = u->gamma0;
     const double b0 = sqrt(1.0 - 1.0 / (g0 * g0));

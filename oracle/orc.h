@@ -75,6 +75,25 @@ int orc_coefficients(const orc_grid* g, double out[6]);
 void orc_potential_step(const orc_grid* g, const double* prev, const double* cur,
                         const double* src, double* next);
 
+/* Seed field (Sec. "Seed Field"): a plane wave along z given in the lab
+ * frame like the optical undulator (the same parameters, orc_undulator with
+ * type 1), injected by the total-field/scattered-field technique: the
+ * vertex plane k = 2 is the last of the scattered-field region (next to the
+ * z = z_min boundary), k = 3 the first of the total-field region.  After the
+ * update of level n+1 the stencil's coupling across the two planes is
+ * corrected with the incident vector potential f^n (A components only; the
+ * seed's phi is zero):
+ *   k = 2:  psi' = psi - [A (a2 f_{i+1,k+1} + a2 f_{i-1,k+1} + a4 f_{j+1,k+1}
+ *                           + a4 f_{j-1,k+1}) + a6 f_{k+1}]
+ *   k = 3:  psi' = psi + [A (a2 f_{i+1,k-1} + ...) + a6 f_{k-1}],
+ * over interior (i, j), with f^n = p A0 s(tau) at the vertex and t_n. */
+void orc_seed_correction(const orc_grid* g, const orc_undulator* seed, double t_n,
+                         double* next);
+
+/* The incident vector potential of a plane-wave seed or optical undulator at
+ * rest-frame (z, t): out = A0 s(tau) times the polarization (x, y). */
+void orc_incident_potential(const orc_undulator* u, double z, double t, double out[2]);
+
 /* E and B at t = (n+1/2) dt at the vertices [1, n-2]^3 from A^n, A^{n+1},
  * phi^n (Sec. "Field Evaluation"); all other vertices are set to zero. */
 void orc_fields(const orc_grid* g, const double* lev_n, const double* lev_np1,

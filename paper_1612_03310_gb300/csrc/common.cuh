@@ -156,8 +156,15 @@ struct PicP {
   double t0, dt, dtb;
   // undulator (lab field transformed to the rest frame)
   int und_on, fringe;
+  int und_type;              // 0 static, 1 optical plane wave
   double g0, b0c, zent, L, lam_u, inv_lam_u, ku_d;
   T ku, B0, ex_fac, by_fac;  // E_x = ex_fac B'_y, B_y = by_fac B'_y
+  // optical: tau = gamma0 (1 - d beta0) t + gamma0 (beta0 - d) z / c + d z0'/c;
+  // rest-frame E = (oex, oey) s'(tau), B = (obx, oby) s'(tau)
+  int osig;
+  double w0_d, cep, t0o, tau_t, tau_z, tau_c;
+  T w0, env_a, inv_tv, oex, oey, obx, oby;
+  T dtau_cell;               // gamma0 (beta0 - d) dz / c: tau per cell along z
   T g0dz;                    // gamma0 dz: lab length of one cell along z
   T y0f, dyf;                // y0 and dy in T
   // deposit

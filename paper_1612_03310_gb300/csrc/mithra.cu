@@ -281,10 +281,36 @@ PicP<T> make_pic(const mithra_sim* s) {
   p.cx = (T)(kC * dtb / g.dx); p.cy = (T)(kC * dtb / g.dy); p.cz = (T)(kC * dtb / g.dz);
   p.n_sub = g.n_sub;
   p.t0 = s->t0; p.dt = g.dt; p.dtb = dtb;
-  p.und_on = (u.K != 0.0) ? 1 : 0;
+  p.und_type = u.type == 1 ? 1 : 0;
+  p.und_on = (u.type == 1) ? (u.a0 != 0.0) : (u.K != 0.0);
   p.fringe = u.fringe ? 1 : 0;
   p.g0 = u.gamma0;
   const double b0 = std::sqrt(1.0 - 1.0 / (u.gamma0 * u.gamma0));
+  if (p.und_type == 1) {
+    // optical plane wave: tau of a rest-frame event, the signal constants,
+    // and the rest-frame field per unit s' (E_perp = gamma0 (E' + v x B'),
+    // B_perp = gamma0 (B' - v x E'/c^2) of E' = -p A0 s', B' = -(d/c) z x p A0 s')
+    const double d = u.direction < 0 ? -1.0 : 1.0;
+    const double pn = std::sqrt(u.pol_x * u.pol_x + u.pol_y * u.pol_y);
+    const double px = u.pol_x / pn, py = u.pol_y / pn;
+    const double A0 = u.a0 * kMe * kC / kQe;
+    const double tv = u.variance / kC;
+    p.osig = u.signal;
+    p.w0_d = 2.0 * kPi * kC / u.lambda_l;
+    p.cep = u.cep;
+    p.t0o = u.offset / kC;
+    p.tau_t = u.gamma0 * (1.0 - d * b0);
+    p.tau_z = u.gamma0 * (b0 - d) / kC;
+    p.tau_c = d * u.z0_lab / kC;
+    p.w0 = (T)p.w0_d;
+    p.env_a = (T)(2.0 * std::log(2.0) / (tv * tv));
+    p.inv_tv = (T)(1.0 / tv);
+    p.oex = (T)(-u.gamma0 * (1.0 - d * b0) * A0 * px);
+    p.oey = (T)(-u.gamma0 * (1.0 - d * b0) * A0 * py);
+    p.obx = (T)(u.gamma0 * (d - b0) * A0 * py / kC);
+    p.oby = (T)(-u.gamma0 * (d - b0) * A0 * px / kC);
+    p.dtau_cell = (T)(p.tau_z * g.dz);
+  }
   p.b0c = b0 * kC;
   p.zent = u.z_ent_lab;
   p.L = u.length_lab;
@@ -346,12 +372,15 @@ void launch_scan(mithra_sim* s, int advance) {
 template <typename T, typename U>
 mithra_status setup_push_grid(mithra_sim* s) {
   const int smem = tile_smem_bytes<T>();
-  MCHECK(s, cudaFuncSetAttribute(k_push_tiled<T, U>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 smem));
+  MCHECK(s, cudaFuncSetAttribute(k_push_tiled<false, T, U>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  MCHECK(s, cudaFuncSetAttribute(k_push_tiled<true, T, U>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
   int dev = 0, nsm = 0, per_sm = 0;
   MCHECK(s, cudaGetDevice(&dev));
   MCHECK(s, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  MCHECK(s, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_push_tiled<T, U>, 256, smem));
+  MCHECK(s, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_push_tiled<false, T, U>,
+                                                          256, smem));
   s->n_sm = nsm;
   s->push_max_per_sm = per_sm > 0 ? per_sm : 1;
   s->push_grid = nsm * s->push_max_per_sm;
@@ -447,14 +476,17 @@ mithra_status launch_step(mithra_sim* s) {
     Parts<T, U> A = parts_of<T, U>(s, s->pb), B = parts_of<T, U>(s, 1 - s->pb);
     {
       ProfScope ps(s, K_PUSH);
+      const bool opt = pp.und_type == 1;
       if (s->push_variant == 1 && s->have_tm) {
-        k_push_tiled<T, U><<<s->push_grid, 256, tile_smem_bytes<T>(), s->stream>>>(
+        auto kern = opt ? k_push_tiled<true, T, U> : k_push_tiled<false, T, U>;
+        kern<<<s->push_grid, 256, tile_smem_bytes<T>(), s->stream>>>(
             s->tm_box[1 - s->cur], s->tm_box_d, pp, s->dstate, P1, Dn, S, A, s->offset, s->tiles,
             s->count, s->key, s->rank, &s->dstate->n_lost, s->np);
       } else {
-        k_push<T, U><<<blocks_for(s->np, 256), 256, 0, s->stream>>>(pp, s->dstate, P1, Dn, S, A,
-                                                                 s->np, s->count, s->key,
-                                                                 s->rank, &s->dstate->n_lost);
+        auto kern = opt ? k_push<true, T, U> : k_push<false, T, U>;
+        kern<<<blocks_for(s->np, 256), 256, 0, s->stream>>>(pp, s->dstate, P1, Dn, S, A, s->np,
+                                                             s->count, s->key, s->rank,
+                                                             &s->dstate->n_lost);
       }
     }
     {
@@ -719,8 +751,18 @@ mithra_status mithra_create(const mithra_grid* grid, const mithra_undulator* und
   mithra_status st = check_grid(grid, &why);
   if (st != MITHRA_OK) return fail(nullptr, st, why);
   if (!und) return fail(nullptr, MITHRA_EINVAL, "undulator is NULL");
-  if (!(und->gamma0 > 1.0) || !(und->lambda_u > 0.0))
-    return fail(nullptr, MITHRA_EINVAL, "undulator needs gamma0 > 1 and lambda_u > 0");
+  if (!(und->gamma0 > 1.0)) return fail(nullptr, MITHRA_EINVAL, "undulator needs gamma0 > 1");
+  if (und->type == 1) {
+    if (!(und->lambda_l > 0.0) || !(und->variance > 0.0) || !std::isfinite(und->a0) ||
+        !(und->pol_x * und->pol_x + und->pol_y * und->pol_y > 0.0) ||
+        (und->direction != 1 && und->direction != -1) || und->signal < 0 || und->signal > 3 ||
+        !std::isfinite(und->offset) || !std::isfinite(und->z0_lab) || !std::isfinite(und->cep))
+      return fail(nullptr, MITHRA_EINVAL,
+                  "optical undulator needs lambda_l > 0, variance > 0, a polarization, "
+                  "direction +-1 and signal 0..3");
+  } else if (und->type != 0 || !(und->lambda_u > 0.0)) {
+    return fail(nullptr, MITHRA_EINVAL, "undulator type must be 0 (static, lambda_u > 0) or 1");
+  }
   if (precision != MITHRA_P32 && precision != MITHRA_P64 && precision != MITHRA_P32_U64 &&
       precision != MITHRA_P32_C)
     return fail(nullptr, MITHRA_EINVAL,

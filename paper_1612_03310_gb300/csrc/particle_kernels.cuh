@@ -36,8 +36,8 @@ __device__ inline double exp_t(double a) { return exp(a); }
 // f_z), in its own precision T.
 template <typename T>
 struct UndFrame {
-  T ph0;      // ku zeta_ref reduced to (-pi, pi]
-  T thr_lo;   // offsets below this are before the entrance
+  T ph0;      // ku zeta_ref reduced to (-pi, pi]; optical: carrier phase w0 x_ref + cep
+  T thr_lo;   // offsets below this are before the entrance; optical: x_ref = tau_ref - t0
   T thr_hi;   // offsets above this are past the exit
   T a_lo0;    // ku zeta_ref (fringe argument before the entrance)
   T a_hi0;    // ku (zeta_ref - L) (fringe argument past the exit)
@@ -45,8 +45,18 @@ struct UndFrame {
 
 template <typename T>
 __device__ inline UndFrame<T> und_frame(const PicP<T>& p, int kref, double t) {
-  const double zeta = p.g0 * (p.z0 + (double)kref * p.dzd + p.b0c * t) - p.zent;
   UndFrame<T> fr;
+  if (p.und_type == 1) {
+    // optical: signal argument x = tau - t0 at the reference plane, and the
+    // carrier phase there reduced to (-pi, pi], in FP64
+    const double x = p.tau_t * t + p.tau_z * (p.z0 + (double)kref * p.dzd) + p.tau_c - p.t0o;
+    const double ph = p.w0_d * x + p.cep;
+    fr.ph0 = (T)(ph - 2.0 * kPi * rint(ph * (0.5 / kPi)));
+    fr.thr_lo = (T)x;
+    fr.thr_hi = fr.a_lo0 = fr.a_hi0 = (T)0;
+    return fr;
+  }
+  const double zeta = p.g0 * (p.z0 + (double)kref * p.dzd + p.b0c * t) - p.zent;
   fr.ph0 = (T)(p.ku_d * (zeta - p.lam_u * rint(zeta * p.inv_lam_u)));
   fr.thr_lo = (T)(-zeta);
   fr.thr_hi = p.L > 0.0 ? (T)(p.L - zeta) : (T)3.0e38;
@@ -57,12 +67,56 @@ __device__ inline UndFrame<T> und_frame(const PicP<T>& p, int kref, double t) {
 
 // Field at transverse position y and offset zl = (k - kref) + f_z cells from
 // the frame's reference plane.
+// Derivative s'(x) of the optical undulator's signal (the FIELD section's
+// list; see mithra_undulator) at x = x_ref + dx with the carrier phase
+// ph = ph_ref + w0 dx.
 template <typename T>
+__device__ inline T signal_derivative(const PicP<T>& p, T x, T ph) {
+  T sn, cs;
+  sincos_t(ph, &sn, &cs);
+  const T dC = -p.w0 * sn;
+  switch (p.osig) {
+    case 0: {
+      const T G = exp_t(-p.env_a * x * x);
+      const T k = (T)(-4.0 * 0.69314718055994531) * p.inv_tv;
+      return k * G * (cs + x * dC - (T)2 * p.env_a * x * x * cs);
+    }
+    case 1: {
+      const T G = exp_t(-p.env_a * x * x);
+      return G * (dC - (T)2 * p.env_a * x * cs);
+    }
+    case 2: {
+      const T u = x * p.inv_tv;
+      T ch, sh;
+      coshsinh_t(u, &ch, &sh);
+      return (dC - cs * p.inv_tv * (sh / ch)) / ch;
+    }
+    default: {
+      if (x > (T)0) return dC;
+      const T G = exp_t(-p.env_a * x * x);
+      return G * (dC - (T)2 * p.env_a * x * cs);
+    }
+  }
+}
+
+// kOpt selects the optical undulator at compile time (a separate
+// instantiation of the particle kernels), so that the static kernels carry
+// none of its registers.
+template <bool kOpt, typename T>
 __device__ inline void undulator_field(const PicP<T>& p, const UndFrame<T>& fr, T y, T zl,
                                        T E[3], T B[3]) {
   E[0] = E[1] = E[2] = (T)0;
   B[0] = B[1] = B[2] = (T)0;
   if (!p.und_on) return;
+  if (kOpt) {
+    const T dx = p.dtau_cell * zl;
+    const T sp = signal_derivative(p, fr.thr_lo + dx, fr.ph0 + p.w0 * dx);
+    E[0] = p.oex * sp;
+    E[1] = p.oey * sp;
+    B[0] = p.obx * sp;
+    B[1] = p.oby * sp;
+    return;
+  }
   const T zr = p.g0dz * zl;  // lab distance from the reference plane
   T ch, sh;
   coshsinh_t(p.ku * y, &ch, &sh);
@@ -232,7 +286,7 @@ __device__ inline int split_cell_t(int c0, T s, T* frac) {
 // advanced in cells (fraction type T, carry into the cell index).  disp
 // receives the displacement in cells over the field step.  Returns false when
 // the particle leaves the valid cells.
-template <typename T, typename U, typename Gather, typename Frame>
+template <bool kOpt, typename T, typename U, typename Gather, typename Frame>
 __device__ inline bool push_particle(const PicP<T>& p, int& i, int& j, int& k, T f[3], U u[3],
                                      T disp[3], Gather&& gather, Frame&& frame) {
   disp[0] = disp[1] = disp[2] = (T)0;
@@ -242,7 +296,7 @@ __device__ inline bool push_particle(const PicP<T>& p, int& i, int& j, int& k, T
     int kref;
     const UndFrame<T> fr = frame(m, k, &kref);
     const T y = p.y0f + ((T)j + f[1]) * p.dyf;
-    undulator_field(p, fr, y, (T)(k - kref) + f[2], Eu, Bu);
+    undulator_field<kOpt>(p, fr, y, (T)(k - kref) + f[2], Eu, Bu);
     for (int e = 0; e < 3; ++e) { E[e] += Eu[e]; B[e] += Bu[e]; }
     boris(p, u, E, B);
     const T ig = (T)rsqrt_nr<T>(1.0 + (double)u[0] * u[0] + (double)u[1] * u[1] +
@@ -261,7 +315,7 @@ __device__ inline bool push_particle(const PicP<T>& p, int& i, int& j, int& k, T
 // t = (n+1/2) dt held fixed and the undulator at each sub-step time, then the
 // deposit of J^{n+1} at the mid point of the path and rho^{n+3/2} at the end,
 // and the key/rank of the particle's new tile for the re-sort.
-template <typename T, typename U>
+template <bool kOpt, typename T, typename U>
 __global__ void __launch_bounds__(256) k_push(PicP<T> p, const StepState* __restrict__ st,
                                               const V4<T>* __restrict__ pn,
                                               const V4<T>* __restrict__ D,
@@ -282,7 +336,7 @@ __global__ void __launch_bounds__(256) k_push(PicP<T> p, const StepState* __rest
     const T f0[3] = {f[0], f[1], f[2]};
     T disp[3];
     const double th = p.t0 + ((double)st->n + 0.5) * p.dt;
-    const bool ok = push_particle(
+    const bool ok = push_particle<kOpt>(
         p, i, j, k, f, u, disp,
         [&](int a, int b, int c, const T* ff, T* E, T* B) {
           gather_eb(p, pn, D, a, b, c, ff[0], ff[1], ff[2], E, B);

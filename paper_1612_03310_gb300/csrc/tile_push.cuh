@@ -109,7 +109,7 @@ __device__ inline void deposit_tile(const PicP<T>& p, T* __restrict__ sJ,
 // One particle's field step (shared by the staged and the per-warp path):
 // push, then the deposits of rho at the end point and J at the mid point
 // through dep(kRho, i, j, k, f, jx, jy, jz, rho), and the re-sort bucket.
-template <typename T, typename U, typename Gather, typename Frame, typename Dep>
+template <bool kOpt, typename T, typename U, typename Gather, typename Frame, typename Dep>
 __device__ inline void tile_particle(const PicP<T>& p, Parts<T, U>& P, long long q,
                                      int* __restrict__ count, int* __restrict__ key,
                                      int* __restrict__ rank, long long* __restrict__ lost_ctr,
@@ -124,7 +124,7 @@ __device__ inline void tile_particle(const PicP<T>& p, Parts<T, U>& P, long long
     const int ia = i, ja = j, ka = k;
     const T f0[3] = {f[0], f[1], f[2]};
     T disp[3];
-    const bool ok = push_particle(p, i, j, k, f, u, disp, gather, frame);
+    const bool ok = push_particle<kOpt>(p, i, j, k, f, u, disp, gather, frame);
     P.ux[q] = u[0]; P.uy[q] = u[1]; P.uz[q] = u[2];
     if (!ok) {
       P.cell[q] = -1;
@@ -152,7 +152,7 @@ __device__ inline void tile_origin(const PicP<T>& p, int tile, int* i0, int* j0,
   *k0 = (tile / (p.ntx * p.nty)) * kTile;
 }
 
-template <typename T, typename U>
+template <bool kOpt, typename T, typename U>
 __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 3 : 1)) k_push_tiled(
     const __grid_constant__ CUtensorMap tm_pn, const __grid_constant__ CUtensorMap tm_d,
     PicP<T> p, StepState* __restrict__ st, const V4<T>* __restrict__ pn,
@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 3 : 1)) k_push_tiled(
 
     const int beg = offset[tile], end = offset[tile + 1];
     for (int q = beg + tid; q < end; q += blockDim.x) {
-      tile_particle(
+      tile_particle<kOpt>(
           p, P, q, count, key, rank, lost_ctr,
           [&](int ci, int cj, int ck, const T* ff, T* E, T* B) {
             const int a = ci - i0, b = cj - j0, c = ck - k0;
@@ -288,7 +288,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 3 : 1)) k_push_tiled(
       __syncwarp();
       const int beg = offset[tile], end = offset[tile + 1];
       for (int q = beg + lane; q < end; q += 32) {
-        tile_particle(
+        tile_particle<kOpt>(
             p, P, q, count, key, rank, lost_ctr,
             [&](int ci, int cj, int ck, const T* ff, T* E, T* B) {
               gather_eb(p, pn, D, ci, cj, ck, ff[0], ff[1], ff[2], E, B);

@@ -49,7 +49,14 @@ class Grid(C.Structure):
 
 class Undulator(C.Structure):
     _fields_ = [("gamma0", C.c_double), ("lambda_u", C.c_double), ("K", C.c_double),
-                ("z_ent_lab", C.c_double), ("length_lab", C.c_double), ("fringe", C.c_int32)]
+                ("z_ent_lab", C.c_double), ("length_lab", C.c_double), ("fringe", C.c_int32),
+                ("type", C.c_int32), ("a0", C.c_double), ("lambda_l", C.c_double),
+                ("pol_x", C.c_double), ("pol_y", C.c_double), ("z0_lab", C.c_double),
+                ("offset", C.c_double), ("variance", C.c_double), ("cep", C.c_double),
+                ("direction", C.c_int32), ("signal", C.c_int32)]
+
+
+SIGNALS = {"neumann": 0, "gaussian": 1, "secant-hyperbolic": 2, "flat-top": 3}
 
 
 class Tuning(C.Structure):
@@ -137,8 +144,16 @@ def make_grid(g: dict) -> Grid:
 
 
 def make_undulator(u: dict | None) -> Undulator:
+    """Static: gamma0, lambda_u, K, z_ent_lab, length_lab, fringe.  Optical
+    (type "optical"): gamma0, a0, lambda_l, polarization (px, py), z0_lab,
+    offset, variance, cep, direction (-1 or +1), signal (a SIGNALS name)."""
     if u is None:
         return Undulator(1.0e3, 1.0, 0.0, 0.0, 0.0, 0)
+    if u.get("type", "static") == "optical":
+        px, py = u.get("polarization", (0.0, 1.0))
+        return Undulator(u["gamma0"], 1.0, 0.0, 0.0, 0.0, 0, 1, u["a0"], u["lambda_l"], px, py,
+                         u.get("z0_lab", 0.0), u["offset"], u["variance"], u.get("cep", 0.0),
+                         int(u.get("direction", -1)), SIGNALS[u.get("signal", "flat-top")])
     return Undulator(u["gamma0"], u["lambda_u"], u["K"], u.get("z_ent_lab", 0.0),
                      u.get("length_lab", 0.0), int(u.get("fringe", 1)))
 

@@ -337,3 +337,66 @@ def test_autotuned_choice_matches_default(M, tmp_path, monkeypatch):
         b.step(6)
         for nm in ("Ax", "Ez", "rho", "Jx"):
             assert rel_l2(b.copy_field(nm), a.copy_field(nm)) < 1e-5, nm
+
+
+# ---------------------------------------------------------------------------
+# optical undulator (plane wave along z)
+
+def optical_c1(signal="flat-top", direction=-1, pol=(0.0, 1.0)):
+    """c1's frame with the paper's equivalent optical undulator: a0 = K,
+    lambda0 = 2 lambda_u, its rise two wavelengths ahead of the bunch."""
+    u = inputs.WORKLOADS["c1"]["undulator"]
+    lam = 2 * u["lambda_u"]
+    return dict(type="optical", gamma0=u["gamma0"], a0=u["K"], lambda_l=lam, polarization=pol,
+                z0_lab=0.0, offset=0.0325 + 2 * lam, variance=lam, cep=0.3,
+                direction=direction, signal=signal)
+
+
+@pytest.mark.parametrize("prec", ["P64", "P32"])
+@pytest.mark.parametrize("signal", ["neumann", "gaussian", "secant-hyperbolic", "flat-top"])
+@pytest.mark.parametrize("push_variant", [0, 1])
+def test_optical_pic_step_parity(M, orc, prec, signal, push_variant):
+    g = inputs.random_grid(51, 36, 30, 40, n_sub=2)
+    f = inputs.random_fields(52, g, scale=1e-9)
+    P = inputs.random_particles(53, g, 3000, u_scale=0.3)
+    und = dict(optical_c1(signal, pol=(0.6, 0.8)), offset=0.0)
+    p = getattr(M, prec)
+    if p != M.P64:
+        f = as_f32(f)
+    o = orc.OracleSim(g, und, P)
+    with M.Simulation(dict(g, boundary=1), und, P, precision=p) as sim:
+        sim.set_tuning(push_variant=push_variant)
+        set_state(sim, o, f)
+        for steps in (1, 2):
+            o.step(steps)
+            sim.step(steps)
+            sim.sync()
+            compare_fields(sim, o, 1e-10 if p == M.P64 else 1e-5)
+            compare_particles(sim, o, 1e-10 if p == M.P64 else 2e-5, 1e-9 if p == M.P64 else 1e-5)
+
+
+@pytest.mark.parametrize("prec,direction", [("P64", -1), ("P32", -1), ("P64", 1)])
+def test_workload_c1_optical(M, orc, prec, direction):
+    w = inputs.workload("c1")
+    P = inputs.make_bunch(w["bunch_spec"], w["seed"])
+    g, und = dict(w["grid"], boundary=1), optical_c1(direction=direction)
+    kp = g["nz"] - 8
+    p = getattr(M, prec)
+    o = orc.OracleSim(g, und, P)
+    with M.Simulation(g, und, P, precision=p) as sim:
+        sim.set_power_sampling(kp, w["steps"])
+        o.step(w["steps"], power_plane=kp)
+        sim.step(w["steps"])
+        sim.sync()
+        compare_fields(sim, o, 1e-9 if p == M.P64 else 1e-4)
+        rec = sim.read_power()
+        po = np.array([s.p_lab for s in o.power])
+        scale = np.abs(po).max()
+        assert scale > 0
+        assert np.abs(rec[:, 0] - po).max() <= (1e-9 if p == M.P64 else 1e-3) * scale
+        compare_particles(sim, o, 1e-8 if p == M.P64 else 1e-3, 1e-9 if p == M.P64 else 1e-3)
+        if direction < 0:
+            # the counter-propagating laser drives the bunch: transverse
+            # momenta of order a0
+            got = sim.copy_particles()
+            assert np.abs(got["uy"]).max() > 0.3 * und["a0"]
