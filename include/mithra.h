@@ -236,6 +236,17 @@ mithra_status mithra_kernel_times(mithra_sim* sim, double* ms, int64_t* launches
                                   int32_t max_kernels, int32_t* n_kernels);
 const char* mithra_kernel_name(int32_t kernel);
 
+/* Seed field (Sec. "Seed Field"), injected by the total-field/scattered-
+ * field technique: wave describes a plane wave along z in the lab frame with
+ * the parameters of an optical undulator (type must be 1; its gamma0 is not
+ * used, the simulation's frame is).  Vertex plane k = 2 is the last of the
+ * scattered-field region next to the z = z_min boundary, k = 3 the first of
+ * the total-field region; after each update of the potentials the coupling
+ * across the two planes is corrected with the incident vector potential of
+ * level n, so that the seed enters the total-field region.  NULL switches
+ * the seed off.  Needs nz >= 8; MITHRA_EBUSY while the sim is in a batch. */
+mithra_status mithra_set_seed(mithra_sim* sim, const mithra_undulator* wave);
+
 /* Bunch sampling (the input group "bunch-sampling": mean position, mean
  * momentum, position spread and momentum spread along x, y, z) and the
  * bunching factor |<exp(i k_b z)>| over the particles not lost, at the

@@ -313,6 +313,66 @@ __global__ void __launch_bounds__(256) k_potential_zloop(StencilP<T> p,
   }
 }
 
+// Seed field (Sec. "Seed Field"): a plane wave along z given in the lab like
+// the optical undulator, injected by the total-field/scattered-field planes
+// k = 2 (last scattered-field plane, next to the z = z_min boundary) and
+// k = 3 (first total-field plane).  The update of level n+1 took, across the
+// two planes, neighbours of the other region; with the incident vector
+// potential f^n uniform in x and y, the coupling of a plane to its z
+// neighbour is (c dt/dz)^2 f (the NSFD cross terms of a uniform field sum to
+// the same), so the increment and level n+1 get
+//   k = 2:  -(c dt/dz)^2 f^n(z_3),    k = 3:  +(c dt/dz)^2 f^n(z_2)
+// in the A_x, A_y components (the seed has no phi and no A_z).
+struct SeedP {
+  int on, signal;
+  double ax, ay;                  // A0 times the unit polarization
+  double w0, cep, t0o, inv_tv, env_a;
+  double tau_t, tau_z, tau_c;     // tau = tau_t t + tau_z z + tau_c
+  double z2, z3;                  // rest-frame z of the planes k = 2 and 3
+  double t0, dt;
+};
+
+// Signal s(x) of the FIELD section's list (see mithra_undulator), FP64.
+__device__ inline double seed_signal(const SeedP& q, double x) {
+  const double C = cos(q.w0 * x + q.cep);
+  switch (q.signal) {
+    case 0: return -4.0 * 0.69314718055994531 * (x * q.inv_tv) * C * exp(-q.env_a * x * x);
+    case 1: return C * exp(-q.env_a * x * x);
+    case 2: return C / cosh(x * q.inv_tv);
+    default: return x > 0.0 ? C : C * exp(-q.env_a * x * x);
+  }
+}
+
+template <bool kLo, typename T>
+__global__ void __launch_bounds__(256) k_seed_tfsf(StencilP<T> p, SeedP q,
+                                                   const StepState* __restrict__ st,
+                                                   V4<T>* __restrict__ nxt,
+                                                   LoV4* __restrict__ nxtlo,
+                                                   V4<T>* __restrict__ D) {
+  const int i = 1 + blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = 1 + blockIdx.y * blockDim.y + threadIdx.y;
+  const int k = 2 + blockIdx.z;  // 2: scattered-field plane, 3: total-field plane
+  if (i > p.nx - 2 || j > p.ny - 2) return;
+  const double tn = q.t0 + (double)st->n * q.dt;  // time of level n
+  // the incident potential on the other plane of the pair
+  const double zo = (k == 2) ? q.z3 : q.z2;
+  const double s = seed_signal(q, q.tau_t * tn + q.tau_z * zo + q.tau_c - q.t0o);
+  const double sign = (k == 2) ? -1.0 : 1.0;
+  const T cx = (T)(sign * (double)p.rz2 * q.ax * s);
+  const T cy = (T)(sign * (double)p.rz2 * q.ay * s);
+  const V4<T> corr = v4(cx, cy, (T)0, (T)0);
+  const long long c = cidx(i, j, k, p.nx, p.nxy);
+  D[c] = D[c] + corr;
+  if (kLo) {
+    V4<T> h, l;
+    comp_add(nxt[c], ld_lo<T>(nxtlo, c), corr, &h, &l);
+    nxt[c] = h;
+    st_lo(nxtlo, c, l);
+  } else {
+    nxt[c] = nxt[c] + corr;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Marching form of the same update.  A CTA owns a 32 x 8 column tile and a run
 // of lz planes; it walks up in z.  For every plane three TMA box loads land in

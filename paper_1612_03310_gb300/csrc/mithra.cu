@@ -55,6 +55,7 @@ struct mithra_sim {
   int64_t power_cap = 0;
   int64_t power_first = 0;
   int32_t power_plane = 0;
+  SeedP seed{};                     // TF/SF seed (seed.on = 0: none)
   // frequency-resolved power: running Fourier sums at one plane
   int32_t spec_plane = 0;
   int32_t spec_nf = 0;
@@ -454,6 +455,14 @@ mithra_status launch_step(mithra_sim* s) {
         k_potential_step<true, T><<<grd, blk, 0, s->stream>>>(sp, P0, L0, P1, L1, Dn, S);
       else
         k_potential_step<false, T><<<grd, blk, 0, s->stream>>>(sp, P0, L0, P1, L1, Dn, S);
+    }
+    if (s->seed.on) {
+      dim3 blk(32, 8, 1);
+      dim3 grd((s->g.nx - 2 + 31) / 32, (s->g.ny - 2 + 7) / 8, 2);
+      if (L0)
+        k_seed_tfsf<true, T><<<grd, blk, 0, s->stream>>>(sp, s->seed, s->dstate, P1, L1, Dn);
+      else
+        k_seed_tfsf<false, T><<<grd, blk, 0, s->stream>>>(sp, s->seed, s->dstate, P1, L1, Dn);
     }
   }
   if (s->power_cap > 0) {
@@ -995,6 +1004,50 @@ mithra_status mithra_read_power(mithra_sim* s, double* out, int64_t max_records,
     out[3 * r] = p[(size_t)r];
     lab_of(s, s->power_plane, t, &out[3 * r + 1], &out[3 * r + 2]);
   }
+  return MITHRA_OK;
+}
+
+mithra_status mithra_set_seed(mithra_sim* s, const mithra_undulator* w) {
+  if (!s) return fail(nullptr, MITHRA_EINVAL, "sim is NULL");
+  if (s->in_batch) return fail(s, MITHRA_EBUSY, "sim is stepped by a batch");
+  if (!w) {
+    s->seed = SeedP{};
+    return MITHRA_OK;
+  }
+  if (w->type != 1 || !(w->lambda_l > 0.0) || !(w->variance > 0.0) || !std::isfinite(w->a0) ||
+      !(w->pol_x * w->pol_x + w->pol_y * w->pol_y > 0.0) ||
+      (w->direction != 1 && w->direction != -1) || w->signal < 0 || w->signal > 3 ||
+      !std::isfinite(w->offset) || !std::isfinite(w->z0_lab) || !std::isfinite(w->cep))
+    return fail(s, MITHRA_EINVAL,
+                "seed needs type 1, lambda_l > 0, variance > 0, a polarization, direction +-1 "
+                "and signal 0..3");
+  if (s->g.nz < 8 || s->g.nx < 4 || s->g.ny < 4)
+    return fail(s, MITHRA_EINVAL, "seeding needs nz >= 8 (planes 2 and 3 inside)");
+  const double g0 = s->u.gamma0;  // the simulation's frame
+  const double b0 = std::sqrt(1.0 - 1.0 / (g0 * g0));
+  const double d = w->direction;
+  const double pn = std::sqrt(w->pol_x * w->pol_x + w->pol_y * w->pol_y);
+  const double A0 = w->a0 * kMe * kC / kQe;
+  const double tv = w->variance / kC;
+  SeedP q{};
+  q.on = 1;
+  q.signal = w->signal;
+  q.ax = A0 * w->pol_x / pn;
+  q.ay = A0 * w->pol_y / pn;
+  q.w0 = 2.0 * kPi * kC / w->lambda_l;
+  q.cep = w->cep;
+  q.t0o = w->offset / kC;
+  q.inv_tv = 1.0 / tv;
+  q.env_a = 2.0 * std::log(2.0) / (tv * tv);
+  q.tau_t = g0 * (1.0 - d * b0);
+  q.tau_z = g0 * (b0 - d) / kC;
+  q.tau_c = d * w->z0_lab / kC;
+  q.z2 = s->g.z0 + 2.0 * s->g.dz;
+  q.z3 = s->g.z0 + 3.0 * s->g.dz;
+  q.t0 = s->t0;
+  q.dt = s->g.dt;
+  MCHECK(s, cudaStreamSynchronize(s->stream));
+  s->seed = q;
   return MITHRA_OK;
 }
 

@@ -30,7 +30,7 @@ EXPORTS = ["mithra_create", "mithra_step", "mithra_sync", "mithra_time", "mithra
            "mithra_batch_create", "mithra_batch_add", "mithra_batch_remove", "mithra_batch_step",
            "mithra_batch_sync", "mithra_batch_size", "mithra_batch_last_error",
            "mithra_batch_destroy", "mithra_bunch_stats", "mithra_set_spectrum",
-           "mithra_read_spectrum"]
+           "mithra_read_spectrum", "mithra_set_seed"]
 
 
 class MithraError(RuntimeError):
@@ -285,6 +285,15 @@ class Simulation:
         if m > 0:
             _check(lib().mithra_read_power(self.h, _dp(out), m, C.byref(cnt)), self.h)
         return out
+
+    def set_seed(self, seed: dict | None) -> None:
+        """mithra_set_seed: a plane-wave seed with an optical undulator's keys
+        (type is implied), or None to switch it off."""
+        if seed is None:
+            _check(lib().mithra_set_seed(self.h, None), self.h)
+            return
+        w = make_undulator(dict(seed, type="optical", gamma0=seed.get("gamma0", 2.0)))
+        _check(lib().mithra_set_seed(self.h, C.byref(w)), self.h)
 
     # -- diagnostics -------------------------------------------------------
     BUNCH_STATS = ("mean_x", "mean_y", "mean_z", "mean_ux", "mean_uy", "mean_uz",
