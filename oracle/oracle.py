@@ -160,6 +160,19 @@ def fields(g: dict, lev_n, lev_np1):
     return E, B
 
 
+def deposit_rho(g: dict, q_macro: float, x, y, z) -> np.ndarray:
+    """rho of particles at (x, y, z) (those outside the valid region are
+    skipped), shape (nz, ny, nx)."""
+    G = make_grid(g)
+    xs, ys, zs = (np.ascontiguousarray(a, dtype=np.float64) for a in (x, y, z))
+    lost = np.zeros(xs.size, dtype=np.int32)
+    lib().orc_mark_lost(C.byref(G), xs.size, _p(xs), _p(ys), _p(zs), _p(lost))
+    rho = np.zeros(int(g["nx"]) * int(g["ny"]) * int(g["nz"]))
+    lib().orc_deposit_rho(C.byref(G), float(q_macro), xs.size, _p(xs), _p(ys), _p(zs), _p(lost),
+                          _p(rho))
+    return rho.reshape(g["nz"], g["ny"], g["nx"])
+
+
 def undulator_field(u: dict, y: float, z: float, t: float):
     E = np.zeros(3)
     B = np.zeros(3)

@@ -17,6 +17,7 @@ from paper_1612_03310_gb300 import build_lib, inputs
 
 pytestmark = pytest.mark.gpu
 
+C0 = 299792458.0
 FIELDS = ["Ex", "Ey", "Ez", "Bx", "By", "Bz", "Ax", "Ay", "Az", "phi", "Jx", "Jy", "Jz", "rho"]
 
 
@@ -400,3 +401,51 @@ def test_workload_c1_optical(M, orc, prec, direction):
             # momenta of order a0
             got = sim.copy_particles()
             assert np.abs(got["uy"]).max() > 0.3 * und["a0"]
+
+
+def test_workload_c3_first_step_sampled(M, orc):
+    # c3 at its full size (256x256x2048 cells, 2^24 particles) in the launch
+    # configuration the bench tunes, P32: outputs the oracle computes one by
+    # one.  Before the first step rho^{1/2} is the deposit of the bunch; after
+    # it, with zero potential levels -1 and 0 and J^0 = 0, phi^1 =
+    # (c dt)^2 rho^{1/2} / eps0 and A^1 = 0 at interior vertices, the grid E, B
+    # at t = dt/2 vanish, and every particle has made one Boris step in the
+    # undulator field alone.
+    from paper_1612_03310_gb300 import autotune
+    w = inputs.workload("c3")
+    P = inputs.make_bunch(w["bunch_spec"], w["seed"])
+    g, und = dict(w["grid"], boundary=1), w["undulator"]
+    nz, ny, nx = g["nz"], g["ny"], g["nx"]
+    rng = np.random.default_rng(9)
+    pts = np.stack([rng.integers(1, nz - 1, 2000), rng.integers(1, ny - 1, 2000),
+                    rng.integers(1, nx - 1, 2000)], axis=1)
+    o_rho = orc.deposit_rho(g, P["q_macro"], P["x"], P["y"], P["z"])   # (nz, ny, nx)
+    eps0 = 8.8541878128e-12
+    cdt2 = (C0 * g["dt"]) ** 2
+    with M.Simulation(g, und, P, precision=M.P32) as sim:
+        autotune.apply(sim, g, und, P, M.P32)
+        rho = sim.copy_field("rho")
+        assert rel_l2(rho, o_rho) <= 1e-6
+        sim.step(1)
+        phi = sim.copy_field("phi")
+        got = phi[pts[:, 0], pts[:, 1], pts[:, 2]]
+        want = cdt2 * o_rho[pts[:, 0], pts[:, 1], pts[:, 2]] / eps0
+        scale = np.abs(cdt2 * o_rho / eps0).max()
+        assert np.abs(got - want).max() <= 1e-6 * scale
+        del phi, rho
+        for nm in ("Ax", "Ay", "Az"):
+            assert np.abs(sim.copy_field(nm)[1:-1, 1:-1, 1:-1]).max() == 0.0
+        parts = sim.copy_particles()
+    # one Boris step per sampled particle in the undulator field at t = dt/2
+    qm = -1.602176634e-19 / 9.1093837015e-31
+    sel = np.arange(0, P["x"].size, 4096)
+    for q in sel:
+        u = np.array([P["ux"][q], P["uy"][q], P["uz"][q]])
+        E, B = orc.undulator_field(und, P["y"][q], P["z"][q], 0.5 * g["dt"])
+        u1 = orc.boris(u, E, B, qm, g["dt"])
+        v = C0 * u1 / np.sqrt(1 + u1 @ u1)
+        for a, key in enumerate(("ux", "uy", "uz")):
+            assert parts[key][q] == pytest.approx(u1[a], rel=2e-6, abs=2e-6 * max(abs(u1[2]), 1e-30))
+        for a, (key, d) in enumerate((("x", "dx"), ("y", "dy"), ("z", "dz"))):
+            r1 = P[key][q] + v[a] * g["dt"]
+            assert abs(parts[key][q] - r1) <= 2e-5 * g[d]
