@@ -172,6 +172,31 @@ def algorithmic_bytes(kernel: str, grid: dict, n_particles: int, prec: str) -> f
     return 0.0
 
 
+def max_over_ranks(x: float, world: int) -> float:
+    """The largest value over the ranks (the slowest replica's time); the
+    reduction runs on the process group's own device (CUDA for NCCL)."""
+    if world <= 1:
+        return x
+    import torch
+    dev = "cuda" if torch.distributed.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], device=dev, dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_bunch(workload: dict, rank: int) -> dict:
+    """Each rank runs its own replica of the workload with its own seed."""
+    from paper_1612_03310_gb300 import inputs
+    return inputs.make_bunch(workload["bunch_spec"], workload["seed"] + rank)
+
+
+def replica_totals(world: int, ncell: int, npart: int, n_sub: int, steps: int,
+                   seconds: float) -> tuple:
+    """Whole-job cell-updates/s and particle-pushes/s: every rank advanced its
+    own replica by `steps` steps; `seconds` is the slowest rank's time."""
+    return world * ncell * steps / seconds, world * npart * n_sub * steps / seconds
+
+
 def run_gpu(args, rank, world):
     import torch
     from paper_1612_03310_gb300 import inputs, mithra
@@ -179,7 +204,7 @@ def run_gpu(args, rank, world):
     dev = torch.cuda.current_device()
     w = inputs.workload(args.workload)
     g, und = dict(w["grid"], boundary=1), w["undulator"]
-    bunch = inputs.make_bunch(w["bunch_spec"], w["seed"] + rank)
+    bunch = replica_bunch(w, rank)
     n_part = bunch["x"].size
     ncell = g["nx"] * g["ny"] * g["nz"]
     prec = getattr(mithra, PRECISIONS[args.precision])
@@ -224,10 +249,7 @@ def run_gpu(args, rank, world):
     power = sim.read_power()
     parts = sim.copy_particles()
     sim.close()
-    if world > 1:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world)
     rec = autotune.record(g, n_part, prec) or {}
     res = dict(ms=ms, kernel_times=kt, clocks=sampler.summary(), n_part=n_part, ncell=ncell,
                tuning=tuning, trials=[{k: (round(v, 4) if k == "ms" else v) for k, v in t.items()}
@@ -253,10 +275,7 @@ def run_gpu(args, rank, world):
         ms_side = e0.elapsed_time(e1)
         kts = sim.kernel_times()
         sim.close()
-        if world > 1:
-            t = torch.tensor([ms_side], device="cuda", dtype=torch.float64)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms_side = float(t.item())
+        ms_side = max_over_ranks(ms_side, world)
         return dict(ms=ms_side, steps=steps, kernel_times=kts)
 
     if not args.no_p64 and prec != mithra.P64:
@@ -279,11 +298,7 @@ def run_gpu(args, rank, world):
         torch.cuda.synchronize()
         t1 = time.perf_counter()
         barrier()
-        e2e_s = t1 - t0
-        if world > 1:
-            t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        e2e_s = max_over_ranks(t1 - t0, world)
         res["e2e"] = dict(seconds=e2e_s, h2d=6 * 8 * n_part, d2h=rec.nbytes + 7 * 8 * n_part,
                           check=float(np.isfinite(out["x"]).all()))
     return res
@@ -567,8 +582,7 @@ def main():
     K = args.steps
     s = res["ms"] / 1e3
     ncell, npart = res["ncell"], res["n_part"]
-    value = world * ncell * K / s
-    pushes = world * npart * g.get("n_sub", 1) * K / s
+    value, pushes = replica_totals(world, ncell, npart, g.get("n_sub", 1), K, s)
     peak, peak_kind = peaks()
     kt = res["kernel_times"]
     dom = max(kt, key=lambda k: kt[k][0])

@@ -1,0 +1,61 @@
+"""The multi-GPU form is replicas only (the path has no exchange step): the
+host logic of bench.py's N > 1 run -- each rank its own seed, the slowest
+rank's time by a MAX all-reduce, whole-job totals -- checked with two gloo
+ranks on the CPU."""
+import importlib.util
+import os
+import socket
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _bench():
+    spec = importlib.util.spec_from_file_location("bench", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def _rank(rank, world, port, out):
+    import sys
+    sys.path.insert(0, ROOT)
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    torch.distributed.init_process_group("gloo", rank=rank, world_size=world)
+    b = _bench()
+    t = b.max_over_ranks(1.5 + rank, world)          # the slowest rank: 2.5
+    from paper_1612_03310_gb300 import inputs
+    w = inputs.workload("c1")
+    bunch = b.replica_bunch(w, rank)
+    torch.distributed.barrier()
+    torch.distributed.destroy_process_group()
+    np.save(os.path.join(out, f"r{rank}.npy"), np.array([t, bunch["x"][0], bunch["z"][7]]))
+
+
+def test_two_gloo_replicas(tmp_path):
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    torch.multiprocessing.start_processes(_rank, args=(2, port, str(tmp_path)), nprocs=2,
+                                          join=True, start_method="spawn")
+    r0 = np.load(tmp_path / "r0.npy")
+    r1 = np.load(tmp_path / "r1.npy")
+    assert r0[0] == r1[0] == 2.5
+    # rank 0 runs the workload's own bunch, rank 1 another seed
+    from paper_1612_03310_gb300 import inputs
+    w = inputs.workload("c1")
+    P = inputs.make_bunch(w["bunch_spec"], w["seed"])
+    assert r0[1] == P["x"][0] and r0[2] == P["z"][7]
+    assert r1[1] != r0[1]
+
+
+def test_replica_totals():
+    b = _bench()
+    v, p = b.replica_totals(4, 1000, 50, 2, 10, 0.5)
+    assert v == 4 * 1000 * 10 / 0.5
+    assert p == 4 * 50 * 2 * 10 / 0.5
+    assert b.max_over_ranks(3.0, 1) == 3.0
