@@ -257,6 +257,19 @@ mithra_status mithra_set_seed(mithra_sim* sim, const mithra_undulator* wave);
  * counted.  FP64 sums in a fixed order; waits for the stream. */
 mithra_status mithra_bunch_stats(mithra_sim* sim, double k_b, double* out);
 
+/* Bunch sampling with time (the group's rhythm): after every `every`-th step
+ * from now on, the statistics of mithra_bunch_stats at k_b are recorded on
+ * the device, up to `capacity` records (every = 0 or capacity = 0 stops and
+ * frees them; MITHRA_EBUSY while the sim is in a batch).  mithra_read_bunch
+ * copies up to max_records records of 15 doubles each into out (host):
+ * out[15 r] = the number of steps the simulation had completed at the
+ * sample, out[15 r + 1 .. 15 r + 14] = the statistics; *count receives the
+ * number recorded so far.  Both wait for the stream. */
+mithra_status mithra_set_bunch_sampling(mithra_sim* sim, double k_b, int32_t every,
+                                        int64_t capacity);
+mithra_status mithra_read_bunch(mithra_sim* sim, double* out, int64_t max_records,
+                                int64_t* count);
+
 /* Frequency-resolved radiated power (FEL-OUTPUT radiation-power with
  * wavelengths).  mithra_set_spectrum starts running Fourier sums of the lab
  * fields E'_x, E'_y, B'_x, B'_y (the transformation of mithra_radiated_power)

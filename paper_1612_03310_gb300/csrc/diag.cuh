@@ -23,11 +23,21 @@ __device__ inline double block_sum256(double v, double* red) {
   return s;
 }
 
+// A recording sample is due after the step whose device counter n has
+// (n - first) % every == every - 1.
+__device__ inline bool bunch_due(const StepState* __restrict__ st, long long first, int every) {
+  return every <= 0 || (st->n - first) % every == every - 1;
+}
+
 // Pass 1: per-block sums over the particles not lost, positions in FP64 from
-// (cell, fraction).
+// (cell, fraction).  With st, only when a recording sample is due.
+
 template <typename T, typename U>
 __global__ void __launch_bounds__(256) k_bunch_partial(PicP<T> p, Parts<T, U> P, long long np,
-                                                       double kb, double* __restrict__ part) {
+                                                       double kb, double* __restrict__ part,
+                                                       const StepState* __restrict__ st = nullptr,
+                                                       long long first = 0, int every = 0) {
+  if (st && !bunch_due(st, first, every)) return;
   __shared__ double red[8];
   double acc[kBunchSums];
   for (int m = 0; m < kBunchSums; ++m) acc[m] = 0.0;
@@ -60,8 +70,20 @@ __global__ void __launch_bounds__(256) k_bunch_partial(PicP<T> p, Parts<T, U> P,
 
 // Pass 2: the block sums in block order, then means, rms spreads and the
 // bunching factor into out[14] (layout of mithra_bunch_stats).
+// With st: the sample goes to record (n - first) / every of out (15 values:
+// the step count after the sampled step, then the 14 statistics) when due
+// and within cap records.
 __global__ void k_bunch_final(const double* __restrict__ part, int nblocks,
-                              double* __restrict__ out) {
+                              double* __restrict__ out,
+                              const StepState* __restrict__ st = nullptr, long long first = 0,
+                              int every = 0, long long cap = 0) {
+  if (st) {
+    if (!bunch_due(st, first, every)) return;
+    const long long r = (st->n - first) / every;
+    if (r >= cap) return;
+    if (threadIdx.x == 0) out[r * 15] = (double)(st->n + 1);
+    out += r * 15 + 1;
+  }
   __shared__ double tot[kBunchSums];
   const int m = threadIdx.x;
   if (m < kBunchSums) {

@@ -56,6 +56,12 @@ struct mithra_sim {
   int64_t power_first = 0;
   int32_t power_plane = 0;
   SeedP seed{};                     // TF/SF seed (seed.on = 0: none)
+  // bunch sampling every bunch_every steps into d_bunch_rec (15 doubles each)
+  int32_t bunch_every = 0;
+  double bunch_kb = 0.0;
+  int64_t bunch_first = 0, bunch_cap = 0;
+  double* d_bunch_rec = nullptr;
+  double* d_bunch_part = nullptr;
   // frequency-resolved power: running Fourier sums at one plane
   int32_t spec_plane = 0;
   int32_t spec_nf = 0;
@@ -498,6 +504,14 @@ mithra_status launch_step(mithra_sim* s) {
                                                              &s->dstate->n_lost);
       }
     }
+    if (s->bunch_every > 0) {
+      ProfScope ps(s, K_SPECTRUM);
+      const int nb = (int)std::min<long long>(blocks_for(s->np, 256), 1024);
+      k_bunch_partial<T, U><<<nb, 256, 0, s->stream>>>(pp, A, s->np, s->bunch_kb, s->d_bunch_part,
+                                                        s->dstate, s->bunch_first, s->bunch_every);
+      k_bunch_final<<<1, 32, 0, s->stream>>>(s->d_bunch_part, nb, s->d_bunch_rec, s->dstate,
+                                             s->bunch_first, s->bunch_every, s->bunch_cap);
+    }
     {
       ProfScope ps(s, K_SCAN);
       launch_scan(s, 1);
@@ -701,7 +715,8 @@ void free_all(mithra_sim* s) {
   if (s->stream) cudaStreamSynchronize(s->stream);
   void* ptrs[] = {s->P[0], s->P[1], s->PL[0], s->PL[1], s->D, s->S, s->pbuf[0], s->pbuf[1], s->key, s->rank, s->count,
                   s->offset, s->tiles, s->scan_part, s->dstate, s->d_scalar, s->d_power_rec,
-                  s->d_spec_omega, s->d_spec_acc, s->d_spec_out, s->d_spec_samples};
+                  s->d_spec_omega, s->d_spec_acc, s->d_spec_out, s->d_spec_samples,
+                  s->d_bunch_rec, s->d_bunch_part};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (s->h_err) cudaFreeHost(s->h_err);
@@ -1062,6 +1077,42 @@ mithra_status mithra_bunch_stats(mithra_sim* s, double k_b, double* out) {
     TYPES_OF(t, u);
     return bunch_stats_impl<T, U>(s, k_b, out);
   });
+}
+
+mithra_status mithra_set_bunch_sampling(mithra_sim* s, double k_b, int32_t every,
+                                        int64_t capacity) {
+  if (!s) return fail(nullptr, MITHRA_EINVAL, "sim is NULL");
+  if (s->in_batch) return fail(s, MITHRA_EBUSY, "sim is stepped by a batch");
+  if (every < 0 || capacity < 0 || !std::isfinite(k_b))
+    return fail(s, MITHRA_EINVAL, "every and capacity must be >= 0, k_b finite");
+  MCHECK(s, cudaStreamSynchronize(s->stream));
+  if (s->d_bunch_rec) cudaFree(s->d_bunch_rec);
+  if (s->d_bunch_part) cudaFree(s->d_bunch_part);
+  s->d_bunch_rec = s->d_bunch_part = nullptr;
+  s->bunch_every = 0;
+  s->bunch_cap = 0;
+  if (every == 0 || capacity == 0 || s->np == 0) return MITHRA_OK;
+  if (cudaMalloc((void**)&s->d_bunch_rec, sizeof(double) * 15 * (size_t)capacity) != cudaSuccess ||
+      cudaMalloc((void**)&s->d_bunch_part, sizeof(double) * 1024 * kBunchSums) != cudaSuccess)
+    return fail(s, MITHRA_ENOMEM, "bunch record allocation failed");
+  MCHECK(s, cudaMemset(s->d_bunch_rec, 0, sizeof(double) * 15 * (size_t)capacity));
+  s->bunch_every = every;
+  s->bunch_kb = k_b;
+  s->bunch_first = s->n_issued;
+  s->bunch_cap = capacity;
+  return MITHRA_OK;
+}
+
+mithra_status mithra_read_bunch(mithra_sim* s, double* out, int64_t max_records, int64_t* count) {
+  if (!s) return fail(nullptr, MITHRA_EINVAL, "sim is NULL");
+  int64_t have = s->bunch_every > 0 ? (s->n_issued - s->bunch_first) / s->bunch_every : 0;
+  if (have > s->bunch_cap) have = s->bunch_cap;
+  if (count) *count = have;
+  const int64_t m = have < max_records ? have : max_records;
+  if (m <= 0 || !out) return sync_status(s);
+  MCHECK(s, cudaMemcpyAsync(out, s->d_bunch_rec, sizeof(double) * 15 * (size_t)m,
+                            cudaMemcpyDeviceToHost, s->stream));
+  return sync_status(s);
 }
 
 mithra_status mithra_set_spectrum(mithra_sim* s, int32_t k_plane, int32_t n_wavelengths,

@@ -30,7 +30,8 @@ EXPORTS = ["mithra_create", "mithra_step", "mithra_sync", "mithra_time", "mithra
            "mithra_batch_create", "mithra_batch_add", "mithra_batch_remove", "mithra_batch_step",
            "mithra_batch_sync", "mithra_batch_size", "mithra_batch_last_error",
            "mithra_batch_destroy", "mithra_bunch_stats", "mithra_set_spectrum",
-           "mithra_read_spectrum", "mithra_set_seed"]
+           "mithra_read_spectrum", "mithra_set_seed", "mithra_set_bunch_sampling",
+           "mithra_read_bunch"]
 
 
 class MithraError(RuntimeError):
@@ -141,6 +142,14 @@ def make_grid(g: dict) -> Grid:
                 g.get("x0", 0.0), g.get("y0", 0.0), g.get("z0", 0.0), g["dt"],
                 int(g.get("n_sub", 1)), int(g.get("stencil", 0)), int(g.get("boundary", 1)),
                 int(g.get("space_charge", 1)))
+
+
+def normalized_wavelengths(lambda_r: float, f_min: float, f_max: float, df: float) -> np.ndarray:
+    """Lab wavelengths for a sweep over frequencies normalised to the
+    radiation wavelength lambda_r (FEL-OUTPUT minimum-/maximum-normalized-
+    frequency and normalized-frequency-resolution): lambda_r / f."""
+    f = np.arange(f_min, f_max + 0.5 * df, df)
+    return lambda_r / f
 
 
 def make_undulator(u: dict | None) -> Undulator:
@@ -303,6 +312,20 @@ class Simulation:
         """mithra_bunch_stats: 14 values (names in BUNCH_STATS)."""
         out = np.zeros(14)
         _check(lib().mithra_bunch_stats(self.h, C.c_double(k_b), _dp(out)), self.h)
+        return out
+
+    def set_bunch_sampling(self, k_b: float, every: int, capacity: int) -> None:
+        _check(lib().mithra_set_bunch_sampling(self.h, C.c_double(k_b), int(every),
+                                               int(capacity)), self.h)
+
+    def read_bunch(self) -> np.ndarray:
+        """Records (n, 15): steps completed, then the BUNCH_STATS values."""
+        cnt = C.c_int64()
+        _check(lib().mithra_read_bunch(self.h, None, 0, C.byref(cnt)), self.h)
+        out = np.zeros((int(cnt.value), 15))
+        if cnt.value:
+            _check(lib().mithra_read_bunch(self.h, _dp(out), int(cnt.value), C.byref(cnt)),
+                   self.h)
         return out
 
     def set_spectrum(self, k_plane: int, lambda_lab) -> None:

@@ -125,3 +125,12 @@ def test_division_by_invariant_multiplication():
                                                                    for _ in range(2000)]
         for n in ns:
             assert (n * m) >> 64 == n // d, (n, d)
+
+
+def test_normalized_wavelengths():
+    """Frequencies normalised to the radiation wavelength map to lab
+    wavelengths lambda_r / f, both ends included."""
+    from paper_1612_03310_gb300 import mithra
+    lam = mithra.normalized_wavelengths(2.0e-6, 0.9, 1.1, 0.05)
+    assert lam.size == 5
+    assert np.allclose(2.0e-6 / lam, [0.9, 0.95, 1.0, 1.05, 1.1])

@@ -54,6 +54,47 @@ def test_bunch_stats_match_oracle(M, orc, prec):
             assert abs(got[12] - ref[12]) <= (1e-12 if p == M.P64 else 1e-5)
 
 
+@pytest.mark.parametrize("prec", ["P64", "P32"])
+def test_bunch_sampling_records_match_oracle(M, orc, prec):
+    """Samples every 7 steps into 5 records: the steps they were taken at
+    exactly, the statistics as mithra_bunch_stats within its tolerance."""
+    w, P = _c1()
+    g, und = dict(w["grid"], boundary=1), w["undulator"]
+    kb = w["bunch_spec"]["kb"]
+    p = getattr(M, prec)
+    rtol = 1e-11 if p == M.P64 else 2e-6
+    o = orc.OracleSim(g, und, P)
+    with M.Simulation(g, und, P, precision=p) as sim:
+        sim.step(3)
+        o.step(3)
+        sim.set_bunch_sampling(kb, 7, 5)
+        assert sim.read_bunch().shape == (0, 15)
+        sim.step(47)                     # samples due at 10, 17, ..., 45, 52
+        rec = sim.read_bunch()
+        assert rec.shape == (5, 15)
+        assert list(rec[:, 0]) == [10, 17, 24, 31, 38]
+        now = 3
+        for r in rec:
+            o.step(int(r[0]) - now)
+            now = int(r[0])
+            ref = o.bunch_stats(kb)
+            got = r[1:]
+            assert got[13] == ref[13]
+            for a in range(3):
+                scale = ref[6 + a] + abs(ref[a])
+                assert abs(got[a] - ref[a]) <= rtol * scale, (a, got[a], ref[a])
+            assert abs(got[12] - ref[12]) <= (1e-12 if p == M.P64 else 1e-5)
+        # a fresh request restarts the records; every = 0 stops them
+        sim.set_bunch_sampling(kb, 1, 4)
+        sim.step(2)
+        assert list(sim.read_bunch()[:, 0]) == [51, 52]
+        sim.set_bunch_sampling(kb, 0, 0)
+        sim.step(1)
+        assert sim.read_bunch().shape == (0, 15)
+        with pytest.raises(M.MithraError):
+            sim.set_bunch_sampling(kb, -1, 4)
+
+
 def test_bunch_stats_empty_and_errors(M):
     g = dict(inputs.random_grid(0, 8, 8, 8), boundary=1)
     with M.Simulation(g, None, None) as sim:
