@@ -175,7 +175,10 @@ __device__ inline bool boundary_vertex(int nx, int ny, int nz, int* i, int* j, i
 // evaluated here from the same inputs as the interior update (whose D_q^- is
 // still in place).  Face vertices of a second-order grid add mur2_terms.  The
 // boundary sources are zeroed (no deposit reads them).
-template <bool kLo, typename T>
+// With kRest, the vertices that k_potential_zloop_mur1 updates (an x or y
+// face vertex whose interior neighbour q lies on a plane 2 .. nz-3 and next
+// to no other face) are skipped.
+template <bool kLo, typename T, bool kRest = false>
 __global__ void __launch_bounds__(256) k_mur_boundary(StencilP<T> p,
                                                       const V4<T>* __restrict__ cur,
                                                       const LoV4* __restrict__ curlo,
@@ -188,6 +191,10 @@ __global__ void __launch_bounds__(256) k_mur_boundary(StencilP<T> p,
   const int qi = min(max(i, 1), p.nx - 2), qj = min(max(j, 1), p.ny - 2),
             qk = min(max(k, 1), p.nz - 2);
   const int mask = (qi != i) | ((qj != j) << 1) | ((qk != k) << 2);
+  if (kRest && qk != 1 && qk != p.nz - 2) {
+    const bool qx = qi == 1 || qi == p.nx - 2, qy = qj == 1 || qj == p.ny - 2;
+    if ((mask == 1 && !qy && p.nx > 3) || (mask == 2 && !qx && p.ny > 3)) return;
+  }
   const long long b = cidx(i, j, k, p.nx, p.nxy), q = cidx(qi, qj, qk, p.nx, p.nxy);
   V4<T> dq_old, sq;
   const V4<T> dq_new = interior_increment<kLo>(p, cur, curlo, D, src, q, &dq_old, &sq);
@@ -259,14 +266,16 @@ __device__ inline V4<T> plane_laplacian(const StencilP<T>& p, const PlaneSums<T>
   return L + p.rz2 * ((pl.c - z.c) + (m.c - z.c));
 }
 
-template <bool kLo, typename T>
-__global__ void __launch_bounds__(256) k_potential_zloop(StencilP<T> p,
-                                                         const V4<T>* __restrict__ cur,
-                                                         const LoV4* __restrict__ curlo,
-                                                         V4<T>* __restrict__ nxt,
-                                                         LoV4* __restrict__ nxtlo,
-                                                         V4<T>* __restrict__ D,
-                                                         V4<T>* __restrict__ src, int lz) {
+// kMur: a column next to exactly one x or y face also applies first-order
+// Mur (the condition of k_mur_boundary, from this thread's own D_q^- and
+// D_q^+) to its boundary vertex on the planes 2 .. nz-3; every other
+// boundary vertex is left to k_mur_boundary<.., kRest = true>.
+template <bool kLo, typename T, bool kMur>
+__device__ __forceinline__ void zloop_body(const StencilP<T>& p, const V4<T>* __restrict__ cur,
+                                           const LoV4* __restrict__ curlo,
+                                           V4<T>* __restrict__ nxt, LoV4* __restrict__ nxtlo,
+                                           V4<T>* __restrict__ D, V4<T>* __restrict__ src,
+                                           int lz) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int kb = max((int)blockIdx.z * lz, 1);
@@ -283,8 +292,26 @@ __global__ void __launch_bounds__(256) k_potential_zloop(StencilP<T> p,
     lm = plane_sums<T>(lo, (long long)(kb - 1) * p.nxy + col, nx);
     l0 = plane_sums<T>(lo, (long long)kb * p.nxy + col, nx);
   }
+  // kMur: a column next to exactly one x or y face has one boundary vertex
+  // at the fixed offset bo (|bo| = 1: an x face; nx >= 3, so |bo| = nx is a
+  // y face)
+  int bo = 0;
+  if (kMur) {
+    const int fx = (i == 1) | ((i == nx - 2) << 1), fy = (j == 1) | ((j == p.ny - 2) << 1);
+    if ((fx != 0) + (fy != 0) == 1 && fx != 3 && fy != 3)
+      bo = fx == 1 ? -1 : fx == 2 ? 1 : fy == 1 ? -nx : nx;
+  }
   for (int k = kb; k < ke; ++k) {
     const long long q = (long long)k * p.nxy + col;
+    const bool zface = kMur && (k == 1 || k == p.nz - 2);
+    const bool fast = kMur && bo != 0 && !zface;
+    // the compensated form has the registers to issue the boundary loads early
+    V4<T> dbm, cb, cbl;
+    if (kLo && fast) {
+      dbm = D[q + bo];
+      cb = ldg4(cur + q + bo);
+      cbl = ld_lo<T>(curlo, q + bo);
+    }
     const PlaneSums<T> hp = plane_sums<T>(hi, q + p.nxy, nx);
     V4<T> L = plane_laplacian(p, hm, h0, hp);
     PlaneSums<T> lp;
@@ -308,9 +335,49 @@ __global__ void __launch_bounds__(256) k_potential_zloop(StencilP<T> p,
     } else {
       nxt[q] = h0.c + dp;
     }
+    if (fast) {
+      if (!kLo) {
+        dbm = D[q + bo];
+        cb = ldg4(cur + q + bo);
+      }
+      V4<T> db = mur_beta0(p, (bo == 1 || bo == -1) ? 1 : 2) * (dp - dbm) + dm;
+      if (!p.space_charge) db.w = (T)0;
+      D[q + bo] = db;
+      if (kLo) {
+        V4<T> h, l;
+        comp_add(cb, cbl, db, &h, &l);
+        nxt[q + bo] = h;
+        st_lo(nxtlo, q + bo, l);
+      } else {
+        nxt[q + bo] = cb + db;
+      }
+      src[q + bo] = v4((T)0, (T)0, (T)0, (T)0);
+    }
     hm = h0;
     h0 = hp;
   }
+}
+
+template <bool kLo, typename T>
+__global__ void __launch_bounds__(256) k_potential_zloop(StencilP<T> p,
+                                                         const V4<T>* __restrict__ cur,
+                                                         const LoV4* __restrict__ curlo,
+                                                         V4<T>* __restrict__ nxt,
+                                                         LoV4* __restrict__ nxtlo,
+                                                         V4<T>* __restrict__ D,
+                                                         V4<T>* __restrict__ src, int lz) {
+  zloop_body<kLo, T, false>(p, cur, curlo, nxt, nxtlo, D, src, lz);
+}
+
+// The same with first-order Mur fused; the register caps keep the
+// occupancy of the plain form.
+template <bool kLo, typename T>
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? (kLo ? 2 : 4) : (kLo ? 1 : 2))
+    k_potential_zloop_mur1(StencilP<T> p, const V4<T>* __restrict__ cur,
+                           const LoV4* __restrict__ curlo, V4<T>* __restrict__ nxt,
+                           LoV4* __restrict__ nxtlo, V4<T>* __restrict__ D,
+                           V4<T>* __restrict__ src, int lz) {
+  zloop_body<kLo, T, true>(p, cur, curlo, nxt, nxtlo, D, src, lz);
 }
 
 // Seed field (Sec. "Seed Field"): a plane wave along z given in the lab like

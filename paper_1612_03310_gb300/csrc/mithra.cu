@@ -437,16 +437,28 @@ mithra_status launch_step(mithra_sim* s) {
   V4<T>* S = static_cast<V4<T>*>(s->S);
   {
     ProfScope ps(s, K_POTENTIAL);
+    // first-order Mur at the x and y faces is fused into the z-marching
+    // form (the rest first, by the boundary kernel); the other forms and
+    // second-order Mur take the boundary kernel for every boundary vertex
+    const bool fused = s->stencil_variant == 2 && s->g.boundary == 1;
     const dim3 mg = mur_grid(s->g.nx, s->g.ny, s->g.nz);
-    if (L0)
+    if (fused && L0)
+      k_mur_boundary<true, T, true><<<mg, dim3(32, 8), 0, s->stream>>>(sp, P0, L0, P1, L1, Dn, S);
+    else if (fused)
+      k_mur_boundary<false, T, true><<<mg, dim3(32, 8), 0, s->stream>>>(sp, P0, L0, P1, L1, Dn, S);
+    else if (L0)
       k_mur_boundary<true, T><<<mg, dim3(32, 8), 0, s->stream>>>(sp, P0, L0, P1, L1, Dn, S);
     else
       k_mur_boundary<false, T><<<mg, dim3(32, 8), 0, s->stream>>>(sp, P0, L0, P1, L1, Dn, S);
     if (s->stencil_variant == 2) {
       dim3 blk(32, 8, 1);
       dim3 grd((s->g.nx + 31) / 32, (s->g.ny + 7) / 8, (s->g.nz + s->lz - 1) / s->lz);
-      if (L0)
+      if (L0 && fused)
+        k_potential_zloop_mur1<true, T><<<grd, blk, 0, s->stream>>>(sp, P0, L0, P1, L1, Dn, S, s->lz);
+      else if (L0)
         k_potential_zloop<true, T><<<grd, blk, 0, s->stream>>>(sp, P0, L0, P1, L1, Dn, S, s->lz);
+      else if (fused)
+        k_potential_zloop_mur1<false, T><<<grd, blk, 0, s->stream>>>(sp, P0, L0, P1, L1, Dn, S, s->lz);
       else
         k_potential_zloop<false, T><<<grd, blk, 0, s->stream>>>(sp, P0, L0, P1, L1, Dn, S, s->lz);
     } else if (s->stencil_variant == 1 && s->have_tm && !L0) {

@@ -184,6 +184,18 @@ __device__ inline float rsqrt_u(float x) {
 }
 __device__ inline double rsqrt_u(double x) { return rsqrt_nr<double>(x); }
 
+// 1/gamma = 1/sqrt(1 + u.u) that moves the particle: FP32 momenta take it in
+// FP32 (rsqrtf seed, one Newton-Raphson step: a few ulp, below the rounding
+// of the momenta themselves); FP64 momenta by rsqrt_nr in FP64.
+template <typename T>
+__device__ inline T inv_gamma(const float u[3]) {
+  return (T)rsqrt_u(1.0f + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+}
+template <typename T>
+__device__ inline T inv_gamma(const double u[3]) {
+  return (T)rsqrt_nr<T>(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+}
+
 // Boris rotation and kicks (Eq. BorisScheme) for charge-to-mass qm folded
 // into h = qm dtb / (2c) and an = qm dtb / 2, in the momentum type U.  The
 // gamma of the half-kicked momentum t1, which only sets the rotation angle,
@@ -299,8 +311,7 @@ __device__ inline bool push_particle(const PicP<T>& p, int& i, int& j, int& k, T
     undulator_field<kOpt>(p, fr, y, (T)(k - kref) + f[2], Eu, Bu);
     for (int e = 0; e < 3; ++e) { E[e] += Eu[e]; B[e] += Bu[e]; }
     boris(p, u, E, B);
-    const T ig = (T)rsqrt_nr<T>(1.0 + (double)u[0] * u[0] + (double)u[1] * u[1] +
-                                (double)u[2] * u[2]);
+    const T ig = inv_gamma<T>(u);
     const T d[3] = {p.cx * ig * (T)u[0], p.cy * ig * (T)u[1], p.cz * ig * (T)u[2]};
     i = split_cell_t(i, f[0] + d[0], &f[0]);
     j = split_cell_t(j, f[1] + d[1], &f[1]);
