@@ -149,6 +149,9 @@ struct PicP {
   long long nxy;
   double x0, y0, z0, dxd, dyd, dzd;
   T inv2dx, inv2dy, inv2dz, inv4dx, inv4dy, inv4dz, invdt;
+  // lo parts of the level that E and B are evaluated from (compensated
+  // forms), nullptr otherwise; set at each launch beside that level
+  const LoV4* plo;
   // Boris: h = qm dtb / (2c), an = qm dtb / 2
   double h, an;
   T cx, cy, cz;  // c dt_b / (dx, dy, dz): cells moved per unit beta in a sub-step

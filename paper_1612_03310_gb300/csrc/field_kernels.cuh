@@ -372,7 +372,7 @@ __global__ void __launch_bounds__(256) k_potential_zloop(StencilP<T> p,
 // The same with first-order Mur fused; the register caps keep the
 // occupancy of the plain form.
 template <bool kLo, typename T>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? (kLo ? 2 : 4) : (kLo ? 1 : 2))
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? (kLo ? 2 : 3) : (kLo ? 1 : 2))
     k_potential_zloop_mur1(StencilP<T> p, const V4<T>* __restrict__ cur,
                            const LoV4* __restrict__ curlo, V4<T>* __restrict__ nxt,
                            LoV4* __restrict__ nxtlo, V4<T>* __restrict__ D,
@@ -570,27 +570,54 @@ __global__ void __launch_bounds__(kMX* kMY, (sizeof(T) == 4 ? 4 : 1)) k_potentia
 // the increment D = psi^{n+1} - psi^n:  B = (curl A^n + curl A^{n+1}) / 2 is
 // the curl of the mid level pn - D/2; E = -D_A / dt - grad phi^n with
 // phi^n = pn.w - D.w; central differences.
+// Central differences of the level psi^{n+1} + lo and of D between the
+// neighbours a+ and a- of a vertex, A at the mid level (psi^{n+1} - D/2)
+// and phi at level n (psi^{n+1} - D): the parts are differenced apart
+// (neighbouring hi values subtract exactly), so that the lo parts of the
+// compensated forms reach E and B.
+template <typename T>
+__device__ inline V4<T> level_diff(V4<T> hp, V4<T> hm, V4<T> dp, V4<T> dm) {
+  const T half = (T)0.5;
+  return v4((hp.x - hm.x) - half * (dp.x - dm.x), (hp.y - hm.y) - half * (dp.y - dm.y),
+            (hp.z - hm.z) - half * (dp.z - dm.z), (hp.w - hm.w) - (dp.w - dm.w));
+}
+
+// E and B at t = (n+1/2) dt (Sec. "Field Evaluation") from the differences
+// along x, y, z (level_diff) and the increment dc at the vertex.
+template <typename T>
+__device__ inline void eb_from_diffs(const PicP<T>& p, V4<T> gx, V4<T> gy, V4<T> gz, V4<T> dc,
+                                     T E[3], T B[3]) {
+  B[0] = gy.z * p.inv2dy - gz.y * p.inv2dz;
+  B[1] = gz.x * p.inv2dz - gx.z * p.inv2dx;
+  B[2] = gx.y * p.inv2dx - gy.x * p.inv2dy;
+  E[0] = -dc.x * p.invdt - gx.w * p.inv2dx;
+  E[1] = -dc.y * p.invdt - gy.w * p.inv2dy;
+  E[2] = -dc.z * p.invdt - gz.w * p.inv2dz;
+}
+
+// Adds the lo-part differences around global vertex v (p.plo set).
+template <typename T>
+__device__ inline void add_lo_diffs(const PicP<T>& p, long long v, V4<T>& gx, V4<T>& gy,
+                                    V4<T>& gz) {
+  const LoV4* lo = p.plo;
+  gx = gx + (ld_lo<T>(lo, v + 1) - ld_lo<T>(lo, v - 1));
+  gy = gy + (ld_lo<T>(lo, v + p.nx) - ld_lo<T>(lo, v - p.nx));
+  gz = gz + (ld_lo<T>(lo, v + p.nxy) - ld_lo<T>(lo, v - p.nxy));
+}
+
+// E and B at interior vertex v from the level pn = psi^{n+1} (lo parts in
+// p.plo) and the increment D = psi^{n+1} - psi^n.
 template <typename T>
 __device__ inline void eb_vertex(const PicP<T>& p, const V4<T>* __restrict__ pn,
                                  const V4<T>* __restrict__ D, long long v, T E[3], T B[3]) {
   const long long nxy = p.nxy;
   const int nx = p.nx;
-  const T half = (T)0.5;
-  auto mid = [&](long long q) {
-    const V4<T> a = ldg4(pn + q), d = ldg4(D + q);
-    return v4(a.x - half * d.x, a.y - half * d.y, a.z - half * d.z, a.w - d.w);
-  };
-  // .w of mid() is phi^n
-  const V4<T> xp = mid(v + 1), xm = mid(v - 1);
-  const V4<T> yp = mid(v + nx), ym = mid(v - nx);
-  const V4<T> zp = mid(v + nxy), zm = mid(v - nxy);
-  const V4<T> dc = ldg4(D + v);
-  B[0] = (yp.z - ym.z) * p.inv2dy - (zp.y - zm.y) * p.inv2dz;
-  B[1] = (zp.x - zm.x) * p.inv2dz - (xp.z - xm.z) * p.inv2dx;
-  B[2] = (xp.y - xm.y) * p.inv2dx - (yp.x - ym.x) * p.inv2dy;
-  E[0] = -dc.x * p.invdt - (xp.w - xm.w) * p.inv2dx;
-  E[1] = -dc.y * p.invdt - (yp.w - ym.w) * p.inv2dy;
-  E[2] = -dc.z * p.invdt - (zp.w - zm.w) * p.inv2dz;
+  V4<T> gx = level_diff(ldg4(pn + v + 1), ldg4(pn + v - 1), ldg4(D + v + 1), ldg4(D + v - 1));
+  V4<T> gy = level_diff(ldg4(pn + v + nx), ldg4(pn + v - nx), ldg4(D + v + nx), ldg4(D + v - nx));
+  V4<T> gz =
+      level_diff(ldg4(pn + v + nxy), ldg4(pn + v - nxy), ldg4(D + v + nxy), ldg4(D + v - nxy));
+  if (p.plo) add_lo_diffs(p, v, gx, gy, gz);
+  eb_from_diffs(p, gx, gy, gz, ldg4(D + v), E, B);
 }
 
 __device__ inline bool interior(int i, int j, int k, int nx, int ny, int nz) {

@@ -428,11 +428,12 @@ unsigned blocks_for(long long n, int threads) {
 template <typename T, typename U>
 mithra_status launch_step(mithra_sim* s) {
   const StencilP<T> sp = make_stencil<T>(s->g);
-  const PicP<T> pp = make_pic<T>(s);
+  PicP<T> pp = make_pic<T>(s);
   V4<T>* P0 = static_cast<V4<T>*>(s->P[s->cur]);       // psi^n
   V4<T>* P1 = static_cast<V4<T>*>(s->P[1 - s->cur]);   // receives psi^{n+1}
   LoV4* L0 = static_cast<LoV4*>(s->PL[s->cur]);        // lo parts (compensated levels)
   LoV4* L1 = static_cast<LoV4*>(s->PL[1 - s->cur]);
+  pp.plo = L1;  // E and B of this step come from psi^{n+1}
   V4<T>* Dn = static_cast<V4<T>*>(s->D);               // D^{n-1/2} -> D^{n+1/2}
   V4<T>* S = static_cast<V4<T>*>(s->S);
   {
@@ -581,7 +582,8 @@ mithra_status sync_status(mithra_sim* s) {
 
 template <typename T>
 mithra_status copy_field_impl(mithra_sim* s, int what, double* out) {
-  const PicP<T> pp = make_pic<T>(s);
+  PicP<T> pp = make_pic<T>(s);
+  pp.plo = static_cast<const LoV4*>(s->PL[s->cur]);
   const int64_t n = ncell_of(&s->g);
   double* d = nullptr;
   MCHECK(s, cudaMalloc(&d, sizeof(double) * n));
@@ -641,7 +643,8 @@ mithra_status set_field_impl(mithra_sim* s, int what, const double* in) {
 template <typename T>
 mithra_status sample_impl(mithra_sim* s, uint32_t mask, const int32_t* ijk, int64_t npts,
                           double* out) {
-  const PicP<T> pp = make_pic<T>(s);
+  PicP<T> pp = make_pic<T>(s);
+  pp.plo = static_cast<const LoV4*>(s->PL[s->cur]);
   const int m = __builtin_popcount(mask);
   int* dijk = nullptr;
   double* dout = nullptr;
@@ -662,7 +665,8 @@ mithra_status sample_impl(mithra_sim* s, uint32_t mask, const int32_t* ijk, int6
 
 template <typename T>
 mithra_status power_impl(mithra_sim* s, int kp, double* p) {
-  const PicP<T> pp = make_pic<T>(s);
+  PicP<T> pp = make_pic<T>(s);
+  pp.plo = static_cast<const LoV4*>(s->PL[s->cur]);
   MCHECK(s, cudaMemsetAsync(s->d_scalar, 0, sizeof(double), s->stream));
   const double g0 = s->u.gamma0;
   k_power<T><<<64, 256, 0, s->stream>>>(pp, static_cast<const V4<T>*>(s->P[s->cur]),

@@ -184,16 +184,12 @@ __device__ inline float rsqrt_u(float x) {
 }
 __device__ inline double rsqrt_u(double x) { return rsqrt_nr<double>(x); }
 
-// 1/gamma = 1/sqrt(1 + u.u) that moves the particle: FP32 momenta take it in
-// FP32 (rsqrtf seed, one Newton-Raphson step: a few ulp, below the rounding
-// of the momenta themselves); FP64 momenta by rsqrt_nr in FP64.
-template <typename T>
-__device__ inline T inv_gamma(const float u[3]) {
-  return (T)rsqrt_u(1.0f + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-}
-template <typename T>
-__device__ inline T inv_gamma(const double u[3]) {
-  return (T)rsqrt_nr<T>(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+// 1/gamma = 1/sqrt(1 + u.u) that moves the particle, recomputed from the
+// momentum in FP64 whatever the momentum type (rsqrt_nr).
+template <typename T, typename U>
+__device__ inline T inv_gamma(const U u[3]) {
+  return (T)rsqrt_nr<T>(1.0 + (double)u[0] * u[0] + (double)u[1] * u[1] +
+                        (double)u[2] * u[2]);
 }
 
 // Boris rotation and kicks (Eq. BorisScheme) for charge-to-mass qm folded

@@ -49,29 +49,21 @@ __host__ __device__ constexpr int tile_smem_bytes() {
   return tile_eb_offset<T>() + kTEC * 2 * (int)sizeof(V4<T>) + 16;
 }
 
-// E, B at local vertex (a, b, c) of the potential box (strides 1, 11, 121),
-// same arithmetic as eb_vertex.
+// E, B at local vertex l of the potential box (strides 1, 11, 121), global
+// index g (for the lo parts), same arithmetic as eb_vertex.
 template <typename T>
 __device__ inline void eb_local(const PicP<T>& p, const V4<T>* __restrict__ sP,
-                                const V4<T>* __restrict__ sD, int l, V4<T>& E, V4<T>& B) {
+                                const V4<T>* __restrict__ sD, int l, long long g, V4<T>& E,
+                                V4<T>& B) {
   constexpr int SX = 1, SY = kTP, SZ = kTP * kTP;
-  const T half = (T)0.5;
-  auto mid = [&](int q) {
-    const V4<T> a = sP[q], d = sD[q];
-    return v4(a.x - half * d.x, a.y - half * d.y, a.z - half * d.z, a.w - d.w);
-  };
-  const V4<T> xp = mid(l + SX), xm = mid(l - SX);
-  const V4<T> yp = mid(l + SY), ym = mid(l - SY);
-  const V4<T> zp = mid(l + SZ), zm = mid(l - SZ);
-  const V4<T> dc = sD[l];
-  B.x = (yp.z - ym.z) * p.inv2dy - (zp.y - zm.y) * p.inv2dz;
-  B.y = (zp.x - zm.x) * p.inv2dz - (xp.z - xm.z) * p.inv2dx;
-  B.z = (xp.y - xm.y) * p.inv2dx - (yp.x - ym.x) * p.inv2dy;
-  B.w = (T)0;
-  E.x = -dc.x * p.invdt - (xp.w - xm.w) * p.inv2dx;
-  E.y = -dc.y * p.invdt - (yp.w - ym.w) * p.inv2dy;
-  E.z = -dc.z * p.invdt - (zp.w - zm.w) * p.inv2dz;
-  E.w = (T)0;
+  V4<T> gx = level_diff(sP[l + SX], sP[l - SX], sD[l + SX], sD[l - SX]);
+  V4<T> gy = level_diff(sP[l + SY], sP[l - SY], sD[l + SY], sD[l - SY]);
+  V4<T> gz = level_diff(sP[l + SZ], sP[l - SZ], sD[l + SZ], sD[l - SZ]);
+  if (p.plo) add_lo_diffs(p, g, gx, gy, gz);
+  T e[3], b[3];
+  eb_from_diffs(p, gx, gy, gz, sD[l], e, b);
+  E = v4(e[0], e[1], e[2], (T)0);
+  B = v4(b[0], b[1], b[2], (T)0);
 }
 
 // CIC deposit into the shared 11^3 block whose vertex (0,0,0) is global
@@ -104,6 +96,48 @@ __device__ inline void deposit_tile(const PicP<T>& p, T* __restrict__ sJ,
           atomicAdd(a + 2 * kTPC, w * jz);
         }
       }
+}
+
+// Charge deposit of the FP32 forms into the 11^3 block.  Every rho
+// contribution is w q/V with a CIC weight w in [0, 1], so the block sums the
+// integers hi = rint(w 2^b) and lo = rint((w 2^b - hi) 2^b) with int32
+// shared atomics (native, unlike FP32 shared atomics), b = min(21, 30 -
+// ceil(log2 n_t)) for the tile's n_t particles: neither sum can overflow
+// (n_t 2^b <= 2^30), one contribution is resolved to 2^-2b q/V, and the sums
+// do not depend on the order of the atomics.  Rounding to an integer by
+// adding 1.5 2^23, exact for |x| < 2^22 (w 2^b <= 2^21; the products by
+// powers of two are exact).
+__device__ inline void rho_fixed_add(int* __restrict__ hi, int* __restrict__ lo, int v, float w,
+                                     float sb) {
+  const float M = 12582912.0f;
+  const float X = w * sb;
+  const float t = X + M;
+  const float Y = (X - (t - M)) * sb;
+  atomicAdd(hi + v, __float_as_int(t) - __float_as_int(M));
+  atomicAdd(lo + v, __float_as_int(Y + M) - __float_as_int(M));
+}
+
+template <typename T>
+__device__ inline void deposit_rho_fixed(const PicP<T>& p, int* __restrict__ hi,
+                                         int* __restrict__ lo, V4<T>* __restrict__ src, int i0,
+                                         int j0, int k0, int i, int j, int k, T fx, T fy, T fz,
+                                         float sb) {
+  const int li = i - (i0 - 1), lj = j - (j0 - 1), lk = k - (k0 - 1);
+  if (sb == 0.0f || li < 0 || li > kTP - 2 || lj < 0 || lj > kTP - 2 || lk < 0 ||
+      lk > kTP - 2) {
+    deposit_cic(p, src, i, j, k, fx, fy, fz, (T)0, (T)0, (T)0, p.qV);
+    return;
+  }
+  const float wx[2] = {1.0f - (float)fx, (float)fx}, wy[2] = {1.0f - (float)fy, (float)fy},
+              wz[2] = {1.0f - (float)fz, (float)fz};
+#pragma unroll
+  for (int K = 0; K < 2; ++K)
+#pragma unroll
+    for (int J = 0; J < 2; ++J)
+#pragma unroll
+      for (int I = 0; I < 2; ++I)
+        rho_fixed_add(hi, lo, ((lk + K) * kTP + (lj + J)) * kTP + (li + I),
+                      wx[I] * wy[J] * wz[K], sb);
 }
 
 // One particle's field step (shared by the staged and the per-warp path):
@@ -167,10 +201,15 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 3 : 1)) k_push_tiled(
   V4<T>* sB = sE + kTEC;                                                 // B per vertex
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem + tile_eb_offset<T>() +
                                               kTEC * 2 * (int)sizeof(V4<T>));
-  // deposit block, reuses the psi box once E, B are built: one array per
-  // component (J_x, J_y, J_z, rho), so that atomics of a component from
-  // different vertices spread over all banks
+  // deposit block, reuses the psi box once E, B are built.  FP64: one array
+  // per component (J_x, J_y, J_z, rho), so that atomics of a component from
+  // different vertices spread over all banks.  FP32: the fixed-point rho
+  // sums (hi, lo), the current going to global memory directly (vector
+  // atomics in L2, measured faster than FP32 shared-memory atomics).
+  constexpr bool kF32 = sizeof(T) == 4;
   T* sJ = reinterpret_cast<T*>(sP);
+  int* sRh = reinterpret_cast<int*>(sP);
+  int* sRl = sRh + kTPC;
   __shared__ int s_tile;
   constexpr int kMaxFrames = 16;
   __shared__ UndFrame<T> s_frame[kMaxFrames];  // undulator frames of the tile
@@ -207,15 +246,27 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 3 : 1)) k_push_tiled(
       const int a = v % kTE, b = (v / kTE) % kTE, c = v / (kTE * kTE);
       V4<T> E = v4((T)0, (T)0, (T)0, (T)0), B = E;
       if (interior(i0 + a, j0 + b, k0 + c, p.nx, p.ny, p.nz))
-        eb_local(p, sP, sD, ((c + 1) * kTP + (b + 1)) * kTP + (a + 1), E, B);
+        eb_local(p, sP, sD, ((c + 1) * kTP + (b + 1)) * kTP + (a + 1),
+                 cidx(i0 + a, j0 + b, k0 + c, p.nx, p.nxy), E, B);
       sE[v] = E;
       sB[v] = B;
     }
     __syncthreads();
-    for (int c = tid; c < 4 * kTPC; c += blockDim.x) sJ[c] = (T)0;
+    const int beg = offset[tile], end = offset[tile + 1];
+    // fixed-point scale 2^b of the FP32 charge block (0: tiles of more
+    // than 2^16 particles deposit rho in global memory)
+    float sb = 0.0f;
+    int bsh = 0;
+    if (kF32) {
+      const int nt = end - beg;
+      bsh = min(21, 30 - (nt > 1 ? 32 - __clz(nt - 1) : 0));
+      if (nt <= 65536) sb = __int_as_float((127 + bsh) << 23);
+      for (int c = tid; c < 2 * kTPC; c += blockDim.x) sRh[c] = 0;
+    } else {
+      for (int c = tid; c < 4 * kTPC; c += blockDim.x) sJ[c] = (T)0;
+    }
     __syncthreads();
 
-    const int beg = offset[tile], end = offset[tile + 1];
     for (int q = beg + tid; q < end; q += blockDim.x) {
       tile_particle<kOpt>(
           p, P, q, count, key, rank, lost_ctr,
@@ -246,22 +297,41 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 3 : 1)) k_push_tiled(
             return m < kMaxFrames ? s_frame[m] : und_frame(p, k0, th + m * p.dtb);
           },
           [&](bool rho, int i, int j, int k, const T* f, T jx, T jy, T jz, T q) {
-            if (rho)
+            if (kF32) {
+              if (rho)
+                deposit_rho_fixed(p, sRh, sRl, src, i0, j0, k0, i, j, k, f[0], f[1], f[2], sb);
+              else
+                deposit_cic(p, src, i, j, k, f[0], f[1], f[2], jx, jy, jz, (T)0);
+            } else if (rho) {
               deposit_tile<true>(p, sJ, src, i0, j0, k0, i, j, k, f[0], f[1], f[2], jx, jy, jz,
                                  q);
-            else
+            } else {
               deposit_tile<false>(p, sJ, src, i0, j0, k0, i, j, k, f[0], f[1], f[2], jx, jy, jz,
                                   q);
+            }
           });
     }
     __syncthreads();
     // add the block to the global sources (touched vertices only)
-    for (int c = tid; c < kTPC; c += blockDim.x) {
-      const V4<T> v = v4(sJ[c], sJ[kTPC + c], sJ[2 * kTPC + c], sJ[3 * kTPC + c]);
-      if (v.x != (T)0 || v.y != (T)0 || v.z != (T)0 || v.w != (T)0) {
-        const int a = c % kTP, b = (c / kTP) % kTP, cc = c / (kTP * kTP);
-        dep_add(src + cidx(i0 - 1 + a, j0 - 1 + b, k0 - 1 + cc, p.nx, p.nxy), v.x, v.y, v.z,
-                v.w);
+    if (kF32) {
+      const float s1 = (float)p.qV * __int_as_float((127 - bsh) << 23);
+      const float s2 = s1 * __int_as_float((127 - bsh) << 23);
+      for (int c = tid; c < kTPC; c += blockDim.x) {
+        const int h = sRh[c], l = sRl[c];
+        if (h != 0 || l != 0) {
+          const int a = c % kTP, b = (c / kTP) % kTP, cc = c / (kTP * kTP);
+          atomicAdd(&src[cidx(i0 - 1 + a, j0 - 1 + b, k0 - 1 + cc, p.nx, p.nxy)].w,
+                    (T)((float)h * s1 + (float)l * s2));
+        }
+      }
+    } else {
+      for (int c = tid; c < kTPC; c += blockDim.x) {
+        const V4<T> v = v4(sJ[c], sJ[kTPC + c], sJ[2 * kTPC + c], sJ[3 * kTPC + c]);
+        if (v.x != (T)0 || v.y != (T)0 || v.z != (T)0 || v.w != (T)0) {
+          const int a = c % kTP, b = (c / kTP) % kTP, cc = c / (kTP * kTP);
+          dep_add(src + cidx(i0 - 1 + a, j0 - 1 + b, k0 - 1 + cc, p.nx, p.nxy), v.x, v.y, v.z,
+                  v.w);
+        }
       }
     }
     __syncthreads();

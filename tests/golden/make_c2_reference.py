@@ -7,7 +7,10 @@ The GPU parity test for the long run compares against these samples:
     tolerance is 1e-4, far above float32 rounding);
   - the lab-frame radiated power through plane nz - 16 at every step;
   - positions and momenta of particles 0, 512, 1024, ... (4096 of them);
-  - the full FP64 L2 norm of every field.
+  - the full FP64 L2 norm of every field;
+  - at the last checkpoint, E and B on every 4th vertex along each axis
+    (offset 2), float32: a uniform sample of the whole grid for the
+    field L2 error.
 Checkpoints at steps 1000, 2000 and 5000 are written as they are reached
 (c2_reference_<step>.npz).
 
@@ -60,6 +63,10 @@ def main(out_dir):
         done = ck
         f = fields_of(o)
         sel = slice(0, None, 512)
+        sub = {}
+        if ck == CHECKPOINTS[-1]:
+            sub = {f"sub_{nm}": f[nm][2::4, 2::4, 2::4].astype(np.float32)
+                   for nm in FIELDS[:6]}
         np.savez_compressed(
             os.path.join(out_dir, f"c2_reference_{ck}.npz"),
             steps=ck, plane_k=PLANE_K, power_k=POWER_K,
@@ -68,7 +75,7 @@ def main(out_dir):
             power=np.array([[s.p_lab, s.t_lab, s.z_lab] for s in o.power]),
             particle_index=np.arange(o.np)[sel],
             x=o.x[sel], y=o.y[sel], z=o.z[sel], ux=o.ux[sel], uy=o.uy[sel], uz=o.uz[sel],
-            lost=o.lost[sel], n_lost=o.n_lost)
+            lost=o.lost[sel], n_lost=o.n_lost, **sub)
         print(f"step {ck}: {time.time() - t0:.0f} s", flush=True)
 
 
