@@ -143,7 +143,7 @@ PRECISIONS = {"p32": "P32", "p32_u64": "P32_U64", "p32_c": "P32_C", "p64": "P64"
 # DRAM bytes (read + write) per launch from one ncu capture of the kernels as
 # they are now (profiles/top_kernels_c2_p32.md), by (kernel, precision,
 # workload); a kernel changed since its capture must leave this table
-NCU_TRAFFIC = {("push", "p32", "c2"): 179166464 + 61266944}
+NCU_TRAFFIC: dict = {}
 
 
 def algorithmic_bytes(kernel: str, grid: dict, n_particles: int, prec: str) -> float:

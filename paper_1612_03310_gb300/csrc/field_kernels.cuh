@@ -606,8 +606,9 @@ __device__ inline void add_lo_diffs(const PicP<T>& p, long long v, V4<T>& gx, V4
 }
 
 // E and B at interior vertex v from the level pn = psi^{n+1} (lo parts in
-// p.plo) and the increment D = psi^{n+1} - psi^n.
-template <typename T>
+// p.plo; kLo = false: the caller knows there are none) and the increment
+// D = psi^{n+1} - psi^n.
+template <bool kLo = true, typename T>
 __device__ inline void eb_vertex(const PicP<T>& p, const V4<T>* __restrict__ pn,
                                  const V4<T>* __restrict__ D, long long v, T E[3], T B[3]) {
   const long long nxy = p.nxy;
@@ -616,7 +617,7 @@ __device__ inline void eb_vertex(const PicP<T>& p, const V4<T>* __restrict__ pn,
   V4<T> gy = level_diff(ldg4(pn + v + nx), ldg4(pn + v - nx), ldg4(D + v + nx), ldg4(D + v - nx));
   V4<T> gz =
       level_diff(ldg4(pn + v + nxy), ldg4(pn + v - nxy), ldg4(D + v + nxy), ldg4(D + v - nxy));
-  if (p.plo) add_lo_diffs(p, v, gx, gy, gz);
+  if (kLo && p.plo) add_lo_diffs(p, v, gx, gy, gz);
   eb_from_diffs(p, gx, gy, gz, ldg4(D + v), E, B);
 }
 

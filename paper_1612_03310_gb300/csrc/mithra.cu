@@ -374,20 +374,39 @@ void launch_scan(mithra_sim* s, int advance) {
                                                  advance);
 }
 
+// Instantiated forms of the particle step: without lo parts (P32, P64) and
+// with them (P32_C, P32_U64).
+template <typename T, typename U>
+constexpr bool push_form_plain() { return sizeof(U) == sizeof(T); }
+template <typename T, typename U>
+constexpr bool push_form_lo() { return sizeof(T) == 4; }
+
 // Persistent grid of the tiled particle step: as many CTAs as fit on the
 // device at once.
 template <typename T, typename U>
 mithra_status setup_push_grid(mithra_sim* s) {
   const int smem = tile_smem_bytes<T>();
-  MCHECK(s, cudaFuncSetAttribute(k_push_tiled<false, T, U>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-  MCHECK(s, cudaFuncSetAttribute(k_push_tiled<true, T, U>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  if constexpr (push_form_plain<T, U>()) {
+    MCHECK(s, cudaFuncSetAttribute(k_push_tiled<false, T, U>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    MCHECK(s, cudaFuncSetAttribute(k_push_tiled<true, T, U>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  }
+  if constexpr (push_form_lo<T, U>()) {
+    MCHECK(s, cudaFuncSetAttribute(k_push_tiled<false, T, U, true>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    MCHECK(s, cudaFuncSetAttribute(k_push_tiled<true, T, U, true>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  }
   int dev = 0, nsm = 0, per_sm = 0;
   MCHECK(s, cudaGetDevice(&dev));
   MCHECK(s, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  MCHECK(s, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_push_tiled<false, T, U>,
-                                                          256, smem));
+  if constexpr (push_form_plain<T, U>())
+    MCHECK(s, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_push_tiled<false, T, U>,
+                                                            256, smem));
+  else
+    MCHECK(s, cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                  &per_sm, k_push_tiled<false, T, U, true>, 256, smem));
   s->n_sm = nsm;
   s->push_max_per_sm = per_sm > 0 ? per_sm : 1;
   s->push_grid = nsm * s->push_max_per_sm;
@@ -505,13 +524,25 @@ mithra_status launch_step(mithra_sim* s) {
     {
       ProfScope ps(s, K_PUSH);
       const bool opt = pp.und_type == 1;
+      const bool lo = L1 != nullptr;
+      constexpr bool kAnyLo = !push_form_plain<T, U>();  // a form that exists, for the type
       if (s->push_variant == 1 && s->have_tm) {
-        auto kern = opt ? k_push_tiled<true, T, U> : k_push_tiled<false, T, U>;
+        decltype(&k_push_tiled<false, T, U, kAnyLo>) kern = nullptr;
+        if constexpr (push_form_plain<T, U>())
+          if (!lo) kern = opt ? k_push_tiled<true, T, U> : k_push_tiled<false, T, U>;
+        if constexpr (push_form_lo<T, U>())
+          if (lo) kern = opt ? k_push_tiled<true, T, U, true> : k_push_tiled<false, T, U, true>;
+        if (!kern) return fail(s, MITHRA_EINVAL, "no particle-step form for this precision");
         kern<<<s->push_grid, 256, tile_smem_bytes<T>(), s->stream>>>(
             s->tm_box[1 - s->cur], s->tm_box_d, pp, s->dstate, P1, Dn, S, A, s->offset, s->tiles,
             s->count, s->key, s->rank, &s->dstate->n_lost, s->np);
       } else {
-        auto kern = opt ? k_push<true, T, U> : k_push<false, T, U>;
+        decltype(&k_push<false, T, U, kAnyLo>) kern = nullptr;
+        if constexpr (push_form_plain<T, U>())
+          if (!lo) kern = opt ? k_push<true, T, U> : k_push<false, T, U>;
+        if constexpr (push_form_lo<T, U>())
+          if (lo) kern = opt ? k_push<true, T, U, true> : k_push<false, T, U, true>;
+        if (!kern) return fail(s, MITHRA_EINVAL, "no particle-step form for this precision");
         kern<<<blocks_for(s->np, 256), 256, 0, s->stream>>>(pp, s->dstate, P1, Dn, S, A, s->np,
                                                              s->count, s->key, s->rank,
                                                              &s->dstate->n_lost);

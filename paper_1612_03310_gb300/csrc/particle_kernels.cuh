@@ -143,7 +143,7 @@ __device__ inline void undulator_field(const PicP<T>& p, const UndFrame<T>& fr, 
 // Trilinear gather of E, B (Eq. fieldInterpolation, w0 = 1 - f, w1 = f) at a
 // particle in cell (i, j, k) with fractions f, evaluating E, B at the eight
 // vertices from the potentials.
-template <typename T>
+template <bool kLo = true, typename T>
 __device__ inline void gather_eb(const PicP<T>& p, const V4<T>* __restrict__ pn,
                                  const V4<T>* __restrict__ D, int i, int j, int k, T fx, T fy,
                                  T fz, T E[3], T B[3]) {
@@ -156,7 +156,7 @@ __device__ inline void gather_eb(const PicP<T>& p, const V4<T>* __restrict__ pn,
 #pragma unroll
       for (int I = 0; I < 2; ++I) {
         T e[3], b[3];
-        eb_vertex(p, pn, D, cidx(i + I, j + J, k + K, p.nx, p.nxy), e, b);
+        eb_vertex<kLo>(p, pn, D, cidx(i + I, j + J, k + K, p.nx, p.nxy), e, b);
         const T w = wx[I] * wy[J] * wz[K];
         E[0] += w * e[0]; E[1] += w * e[1]; E[2] += w * e[2];
         B[0] += w * b[0]; B[1] += w * b[1]; B[2] += w * b[2];
@@ -322,7 +322,7 @@ __device__ inline bool push_particle(const PicP<T>& p, int& i, int& j, int& k, T
 // t = (n+1/2) dt held fixed and the undulator at each sub-step time, then the
 // deposit of J^{n+1} at the mid point of the path and rho^{n+3/2} at the end,
 // and the key/rank of the particle's new tile for the re-sort.
-template <bool kOpt, typename T, typename U>
+template <bool kOpt, typename T, typename U, bool kLo = false>
 __global__ void __launch_bounds__(256) k_push(PicP<T> p, const StepState* __restrict__ st,
                                               const V4<T>* __restrict__ pn,
                                               const V4<T>* __restrict__ D,
@@ -346,7 +346,7 @@ __global__ void __launch_bounds__(256) k_push(PicP<T> p, const StepState* __rest
     const bool ok = push_particle<kOpt>(
         p, i, j, k, f, u, disp,
         [&](int a, int b, int c, const T* ff, T* E, T* B) {
-          gather_eb(p, pn, D, a, b, c, ff[0], ff[1], ff[2], E, B);
+          gather_eb<kLo>(p, pn, D, a, b, c, ff[0], ff[1], ff[2], E, B);
         },
         [&](int m, int kc, int* kref) {
           *kref = kc;

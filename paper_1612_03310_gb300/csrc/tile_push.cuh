@@ -51,7 +51,7 @@ __host__ __device__ constexpr int tile_smem_bytes() {
 
 // E, B at local vertex l of the potential box (strides 1, 11, 121), global
 // index g (for the lo parts), same arithmetic as eb_vertex.
-template <typename T>
+template <bool kLo, typename T>
 __device__ inline void eb_local(const PicP<T>& p, const V4<T>* __restrict__ sP,
                                 const V4<T>* __restrict__ sD, int l, long long g, V4<T>& E,
                                 V4<T>& B) {
@@ -59,7 +59,7 @@ __device__ inline void eb_local(const PicP<T>& p, const V4<T>* __restrict__ sP,
   V4<T> gx = level_diff(sP[l + SX], sP[l - SX], sD[l + SX], sD[l - SX]);
   V4<T> gy = level_diff(sP[l + SY], sP[l - SY], sD[l + SY], sD[l - SY]);
   V4<T> gz = level_diff(sP[l + SZ], sP[l - SZ], sD[l + SZ], sD[l - SZ]);
-  if (p.plo) add_lo_diffs(p, g, gx, gy, gz);
+  if (kLo && p.plo) add_lo_diffs(p, g, gx, gy, gz);
   T e[3], b[3];
   eb_from_diffs(p, gx, gy, gz, sD[l], e, b);
   E = v4(e[0], e[1], e[2], (T)0);
@@ -186,7 +186,7 @@ __device__ inline void tile_origin(const PicP<T>& p, int tile, int* i0, int* j0,
   *k0 = (tile / (p.ntx * p.nty)) * kTile;
 }
 
-template <bool kOpt, typename T, typename U>
+template <bool kOpt, typename T, typename U, bool kLo = false>
 __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 3 : 1)) k_push_tiled(
     const __grid_constant__ CUtensorMap tm_pn, const __grid_constant__ CUtensorMap tm_d,
     PicP<T> p, StepState* __restrict__ st, const V4<T>* __restrict__ pn,
@@ -246,7 +246,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 3 : 1)) k_push_tiled(
       const int a = v % kTE, b = (v / kTE) % kTE, c = v / (kTE * kTE);
       V4<T> E = v4((T)0, (T)0, (T)0, (T)0), B = E;
       if (interior(i0 + a, j0 + b, k0 + c, p.nx, p.ny, p.nz))
-        eb_local(p, sP, sD, ((c + 1) * kTP + (b + 1)) * kTP + (a + 1),
+        eb_local<kLo>(p, sP, sD, ((c + 1) * kTP + (b + 1)) * kTP + (a + 1),
                  cidx(i0 + a, j0 + b, k0 + c, p.nx, p.nxy), E, B);
       sE[v] = E;
       sB[v] = B;
@@ -289,7 +289,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 3 : 1)) k_push_tiled(
                     B[0] += w * bb.x; B[1] += w * bb.y; B[2] += w * bb.z;
                   }
             } else {
-              gather_eb(p, pn, D, ci, cj, ck, ff[0], ff[1], ff[2], E, B);
+              gather_eb<kLo>(p, pn, D, ci, cj, ck, ff[0], ff[1], ff[2], E, B);
             }
           },
           [&](int m, int kc, int* kref) {
@@ -361,7 +361,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 3 : 1)) k_push_tiled(
         tile_particle<kOpt>(
             p, P, q, count, key, rank, lost_ctr,
             [&](int ci, int cj, int ck, const T* ff, T* E, T* B) {
-              gather_eb(p, pn, D, ci, cj, ck, ff[0], ff[1], ff[2], E, B);
+              gather_eb<kLo>(p, pn, D, ci, cj, ck, ff[0], ff[1], ff[2], E, B);
             },
             [&](int m, int kc, int* kref) {
               *kref = k0;
