@@ -140,10 +140,15 @@ KERNELS_PER_SCOPE = {"potential_step": 2, "scan_counts": 2}
 
 PRECISIONS = {"p32": "P32", "p32_u64": "P32_U64", "p32_c": "P32_C", "p64": "P64"}
 
-# DRAM bytes (read + write) per launch from one ncu capture of the kernels as
-# they are now (profiles/top_kernels_c2_p32.md), by (kernel, precision,
-# workload); a kernel changed since its capture must leave this table
-NCU_TRAFFIC: dict = {}
+# DRAM bytes (read + write) per launch from one ncu capture (--set full, the
+# c2 step in the bench's launch configuration) of the kernels as they are
+# now, by (timed scope, precision, workload); a kernel changed since its
+# capture must leave this table
+NCU_TRAFFIC = {
+    # k_mur_boundary<0, float, 1> + k_potential_zloop_mur1<0, float>
+    ("potential_step", "p32", "c2"): 6278912 + 815240448 + 528015104,
+    ("push", "p32", "c2"): 179204096 + 62242304,
+}
 
 
 def algorithmic_bytes(kernel: str, grid: dict, n_particles: int, prec: str) -> float:
