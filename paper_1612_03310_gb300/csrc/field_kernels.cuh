@@ -175,9 +175,55 @@ __device__ inline bool boundary_vertex(int nx, int ny, int nz, int* i, int* j, i
 // evaluated here from the same inputs as the interior update (whose D_q^- is
 // still in place).  Face vertices of a second-order grid add mur2_terms.  The
 // boundary sources are zeroed (no deposit reads them).
-// With kRest, the vertices that k_potential_zloop_mur1 updates (an x or y
-// face vertex whose interior neighbour q lies on a plane 2 .. nz-3 and next
-// to no other face) are skipped.
+// The boundary vertices that k_potential_zloop_mur1 leaves (every vertex but
+// the x and y face vertices whose interior neighbour q lies on a plane
+// 2 .. nz-3 next to no other face), enumerated one per thread of a 1-D grid
+// of rest_count threads: the z faces; on each x face the rows k = 1, nz-2
+// and the columns j = 1, ny-2; on each y face the rows k = 1, nz-2 and the
+// columns i = 0, 1, nx-2, nx-1.  nx, ny, nz >= 4, so no vertex is listed
+// twice.
+__host__ __device__ inline long long rest_count(int nx, int ny, int nz) {
+  return 2LL * nx * ny + 4LL * (ny - 2) + 4LL * (nz - 4) + 4LL * nx + 8LL * (nz - 4);
+}
+__device__ inline bool rest_vertex(int nx, int ny, int nz, int* i, int* j, int* k) {
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long nxy = (long long)nx * ny;
+  if (t < 2 * nxy) {  // z faces
+    const long long r = t % nxy;
+    *i = (int)(r % nx); *j = (int)(r / nx); *k = t < nxy ? 0 : nz - 1;
+    return true;
+  }
+  t -= 2 * nxy;
+  const int ry = ny - 2, cz = nz - 4;
+  if (t < 4LL * ry) {  // x faces, rows k = 1, nz-2
+    const int face = (int)(t / (2 * ry)), rr = (int)(t % (2 * ry));
+    *i = face ? nx - 1 : 0; *j = 1 + rr % ry; *k = rr / ry ? nz - 2 : 1;
+    return true;
+  }
+  t -= 4LL * ry;
+  if (t < 4LL * cz) {  // x faces, columns j = 1, ny-2, planes 2 .. nz-3
+    const int face = (int)(t / (2 * cz)), rr = (int)(t % (2 * cz));
+    *i = face ? nx - 1 : 0; *j = rr / cz ? ny - 2 : 1; *k = 2 + rr % cz;
+    return true;
+  }
+  t -= 4LL * cz;
+  if (t < 4LL * nx) {  // y faces, rows k = 1, nz-2
+    const int face = (int)(t / (2 * nx)), rr = (int)(t % (2 * nx));
+    *j = face ? ny - 1 : 0; *i = rr % nx; *k = rr / nx ? nz - 2 : 1;
+    return true;
+  }
+  t -= 4LL * nx;
+  if (t < 8LL * cz) {  // y faces, columns i = 0, 1, nx-2, nx-1, planes 2 .. nz-3
+    const int face = (int)(t / (4 * cz)), rr = (int)(t % (4 * cz));
+    const int c = rr / cz;
+    *j = face ? ny - 1 : 0; *i = c < 2 ? c : nx - 4 + c; *k = 2 + rr % cz;
+    return true;
+  }
+  return false;
+}
+
+// With kRest, only the vertices of rest_vertex (1-D launch of rest_count
+// threads).
 template <bool kLo, typename T, bool kRest = false>
 __global__ void __launch_bounds__(256) k_mur_boundary(StencilP<T> p,
                                                       const V4<T>* __restrict__ cur,
@@ -187,14 +233,12 @@ __global__ void __launch_bounds__(256) k_mur_boundary(StencilP<T> p,
                                                       V4<T>* __restrict__ D,
                                                       V4<T>* __restrict__ src) {
   int i, j, k;
-  if (!boundary_vertex(p.nx, p.ny, p.nz, &i, &j, &k)) return;
+  if (kRest ? !rest_vertex(p.nx, p.ny, p.nz, &i, &j, &k)
+            : !boundary_vertex(p.nx, p.ny, p.nz, &i, &j, &k))
+    return;
   const int qi = min(max(i, 1), p.nx - 2), qj = min(max(j, 1), p.ny - 2),
             qk = min(max(k, 1), p.nz - 2);
   const int mask = (qi != i) | ((qj != j) << 1) | ((qk != k) << 2);
-  if (kRest && qk != 1 && qk != p.nz - 2) {
-    const bool qx = qi == 1 || qi == p.nx - 2, qy = qj == 1 || qj == p.ny - 2;
-    if ((mask == 1 && !qy && p.nx > 3) || (mask == 2 && !qx && p.ny > 3)) return;
-  }
   const long long b = cidx(i, j, k, p.nx, p.nxy), q = cidx(qi, qj, qk, p.nx, p.nxy);
   V4<T> dq_old, sq;
   const V4<T> dq_new = interior_increment<kLo>(p, cur, curlo, D, src, q, &dq_old, &sq);

@@ -72,6 +72,10 @@ struct mithra_sim {
   int64_t np = 0;
   int ntx = 0, nty = 0, ntz = 0, nkeys = 0;
   int64_t n_issued = 0;
+  // two steps captured as a CUDA graph, one per parity of the level
+  // ping-pong at its start (index cur); dropped when a launch parameter
+  // changes
+  cudaGraphExec_t step_exec[2] = {nullptr, nullptr};
   double t0 = 0.0;
   int* h_err = nullptr;  // pinned mirror of dstate->err
   std::string err;
@@ -462,10 +466,11 @@ mithra_status launch_step(mithra_sim* s) {
     // second-order Mur take the boundary kernel for every boundary vertex
     const bool fused = s->stencil_variant == 2 && s->g.boundary == 1;
     const dim3 mg = mur_grid(s->g.nx, s->g.ny, s->g.nz);
+    const unsigned rg = blocks_for(rest_count(s->g.nx, s->g.ny, s->g.nz), 256);
     if (fused && L0)
-      k_mur_boundary<true, T, true><<<mg, dim3(32, 8), 0, s->stream>>>(sp, P0, L0, P1, L1, Dn, S);
+      k_mur_boundary<true, T, true><<<rg, 256, 0, s->stream>>>(sp, P0, L0, P1, L1, Dn, S);
     else if (fused)
-      k_mur_boundary<false, T, true><<<mg, dim3(32, 8), 0, s->stream>>>(sp, P0, L0, P1, L1, Dn, S);
+      k_mur_boundary<false, T, true><<<rg, 256, 0, s->stream>>>(sp, P0, L0, P1, L1, Dn, S);
     else if (L0)
       k_mur_boundary<true, T><<<mg, dim3(32, 8), 0, s->stream>>>(sp, P0, L0, P1, L1, Dn, S);
     else
@@ -772,6 +777,8 @@ void free_all(mithra_sim* s) {
     cudaEventDestroy(r.b);
   }
   for (cudaEvent_t e : s->spare) cudaEventDestroy(e);
+  for (cudaGraphExec_t e : s->step_exec)
+    if (e) cudaGraphExecDestroy(e);
   if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
 }
 
@@ -946,6 +953,39 @@ mithra_status mithra_create(const mithra_grid* grid, const mithra_undulator* und
 }
 
 namespace {
+void drop_step_graphs(mithra_sim* s) {
+  for (auto& e : s->step_exec) {
+    if (e) cudaGraphExecDestroy(e);
+    e = nullptr;
+  }
+}
+
+// Captures two steps from the current state (they bring the level and
+// particle buffers back to it) into s->step_exec[s->cur].
+mithra_status capture_step_pair(mithra_sim* s) {
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return cuda_fail(s, e, "begin capture of the step");
+  mithra_status st = MITHRA_OK;
+  for (int k = 0; k < 2 && st == MITHRA_OK; ++k)
+    st = with_types(s->prec, [&](auto t, auto u) {
+      TYPES_OF(t, u);
+      return launch_step<T, U>(s);
+    });
+  e = cudaStreamEndCapture(s->stream, &graph);
+  if (st != MITHRA_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return st;
+  }
+  if (e != cudaSuccess) return cuda_fail(s, e, "end capture of the step");
+  cudaGraphExec_t ex = nullptr;
+  e = cudaGraphInstantiate(&ex, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return cuda_fail(s, e, "instantiate the step graph");
+  s->step_exec[s->cur] = ex;
+  return MITHRA_OK;
+}
+
 mithra_status launch_one_step(mithra_sim* s) {
   mithra_status st = with_types(s->prec, [&](auto t, auto u) {
     TYPES_OF(t, u);
@@ -961,7 +1001,24 @@ mithra_status mithra_step(mithra_sim* s, int64_t n) {
   if (n < 0) return fail(s, MITHRA_EINVAL, "n must be >= 0");
   if (*s->h_err & 1) return fail(s, MITHRA_ENUMERIC, "NaN or Inf in a power reduction");
   if (s->in_batch) return fail(s, MITHRA_EBUSY, "sim belongs to a batch: step it with mithra_batch_step");
-  for (int64_t t = 0; t < n; ++t) {
+  int64_t t = 0;
+  // runs of steps replay a captured pair (no profiling events inside; the
+  // legacy and per-thread default streams cannot be captured)
+  const bool graph = n >= 3 && !s->profiling && s->stream != nullptr &&
+                     s->stream != reinterpret_cast<cudaStream_t>(1) &&
+                     s->stream != reinterpret_cast<cudaStream_t>(2);
+  if (graph) {
+    if (!s->step_exec[s->cur]) {
+      mithra_status st = capture_step_pair(s);
+      if (st != MITHRA_OK) return st;
+    }
+    for (; t + 1 < n; t += 2) {
+      cudaError_t e = cudaGraphLaunch(s->step_exec[s->cur], s->stream);
+      if (e != cudaSuccess) return cuda_fail(s, e, "step graph launch");
+      s->n_issued += 2;
+    }
+  }
+  for (; t < n; ++t) {
     mithra_status st = launch_one_step(s);
     if (st != MITHRA_OK) return st;
   }
@@ -990,6 +1047,7 @@ mithra_status mithra_copy_field(mithra_sim* s, int32_t field, double* out) {
 
 mithra_status mithra_set_field(mithra_sim* s, int32_t field, const double* in) {
   if (!s) return fail(nullptr, MITHRA_EINVAL, "sim is NULL");
+  drop_step_graphs(s);
   if (!in || field < 0 || field > MITHRA_PHI_PREV) return fail(s, MITHRA_EINVAL, "bad field id or NULL in");
   return s->prec == MITHRA_P64 ? set_field_impl<double>(s, field, in)
                                : set_field_impl<float>(s, field, in);
@@ -1029,6 +1087,7 @@ mithra_status mithra_radiated_power(mithra_sim* s, int32_t k_plane, double* p_la
 
 mithra_status mithra_set_power_sampling(mithra_sim* s, int32_t k_plane, int64_t capacity) {
   if (!s) return fail(nullptr, MITHRA_EINVAL, "sim is NULL");
+  drop_step_graphs(s);
   if (capacity < 0) return fail(s, MITHRA_EINVAL, "capacity must be >= 0");
   if (capacity > 0 && (k_plane < 1 || k_plane > s->g.nz - 2))
     return fail(s, MITHRA_EINVAL, "k_plane outside [1, nz-2]");
@@ -1071,6 +1130,7 @@ mithra_status mithra_read_power(mithra_sim* s, double* out, int64_t max_records,
 
 mithra_status mithra_set_seed(mithra_sim* s, const mithra_undulator* w) {
   if (!s) return fail(nullptr, MITHRA_EINVAL, "sim is NULL");
+  drop_step_graphs(s);
   if (s->in_batch) return fail(s, MITHRA_EBUSY, "sim is stepped by a batch");
   if (!w) {
     s->seed = SeedP{};
@@ -1129,6 +1189,7 @@ mithra_status mithra_bunch_stats(mithra_sim* s, double k_b, double* out) {
 mithra_status mithra_set_bunch_sampling(mithra_sim* s, double k_b, int32_t every,
                                         int64_t capacity) {
   if (!s) return fail(nullptr, MITHRA_EINVAL, "sim is NULL");
+  drop_step_graphs(s);
   if (s->in_batch) return fail(s, MITHRA_EBUSY, "sim is stepped by a batch");
   if (every < 0 || capacity < 0 || !std::isfinite(k_b))
     return fail(s, MITHRA_EINVAL, "every and capacity must be >= 0, k_b finite");
@@ -1165,6 +1226,7 @@ mithra_status mithra_read_bunch(mithra_sim* s, double* out, int64_t max_records,
 mithra_status mithra_set_spectrum(mithra_sim* s, int32_t k_plane, int32_t n_wavelengths,
                                   const double* lambda_lab) {
   if (!s) return fail(nullptr, MITHRA_EINVAL, "sim is NULL");
+  drop_step_graphs(s);
   if (s->in_batch) return fail(s, MITHRA_EBUSY, "sim is stepped by a batch");
   if (n_wavelengths < 0 || n_wavelengths > kMaxSpectrum)
     return fail(s, MITHRA_EINVAL, "n_wavelengths outside [0, 64]");
@@ -1278,6 +1340,7 @@ const char* mithra_kernel_name(int32_t kernel) {
 
 mithra_status mithra_set_tuning(mithra_sim* s, const mithra_tuning* t) {
   if (!s) return fail(nullptr, MITHRA_EINVAL, "sim is NULL");
+  drop_step_graphs(s);
   if (!t || t->stencil_variant < 0 || t->stencil_variant > 2 || t->lz < 0 ||
       t->push_variant < 0 || t->push_variant > 1 || t->push_ctas_per_sm < 0 ||
       t->push_sparse_below < 0)
@@ -1439,6 +1502,7 @@ mithra_status mithra_batch_add(mithra_batch* b, mithra_sim* s) {
   cudaEventDestroy(e);
   b->sims.push_back(s);
   s->in_batch = b;
+  drop_step_graphs(s);
   drop_graph(b);
   return MITHRA_OK;
 }

@@ -185,11 +185,35 @@ __device__ inline float rsqrt_u(float x) {
 __device__ inline double rsqrt_u(double x) { return rsqrt_nr<double>(x); }
 
 // 1/gamma = 1/sqrt(1 + u.u) that moves the particle, recomputed from the
-// momentum in FP64 whatever the momentum type (rsqrt_nr).
-template <typename T, typename U>
-__device__ inline T inv_gamma(const U u[3]) {
-  return (T)rsqrt_nr<T>(1.0 + (double)u[0] * u[0] + (double)u[1] * u[1] +
-                        (double)u[2] * u[2]);
+// momentum in FP64 whatever the momentum type.  FP64 momenta: 1 + u.u in
+// FP64, rsqrt_nr.  FP32 momenta: 1 + u.u is first formed exactly enough in
+// FP32 pairs -- each square split into its rounded value and the exact
+// remainder by an FMA, the seven terms summed with TwoSum (error ~2^-48) --
+// and the pair taken to FP64 by one addition; then the FP32 seed and the
+// FP64 Newton-Raphson step of rsqrt_nr.  This spends 9 instead of 13
+// instructions on GB300's narrow FP64 pipe.
+template <typename T>
+__device__ inline T inv_gamma(const double u[3]) {
+  return (T)rsqrt_nr<T>(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+}
+template <typename T>
+__device__ inline T inv_gamma(const float u[3]) {
+  float hi = 1.0f, lo = 0.0f;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    // (the _rn intrinsics keep the compiler from fusing these into FMAs)
+    const float p = __fmul_rn(u[a], u[a]);
+    const float e = fmaf(u[a], u[a], -p);  // u^2 = p + e exactly
+    const float s = __fadd_rn(hi, p);      // TwoSum(hi, p)
+    const float bp = __fsub_rn(s, hi);
+    lo += __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(p, bp)) + e;
+    hi = s;
+  }
+  const double x = (double)hi + (double)lo;
+  double y = (double)rsqrtf(hi);
+  y = y * (1.5 - 0.5 * x * y * y);
+  if (sizeof(T) == 8) y = y * (1.5 - 0.5 * x * y * y);
+  return (T)y;
 }
 
 // Boris rotation and kicks (Eq. BorisScheme) for charge-to-mass qm folded

@@ -1,0 +1,82 @@
+"""Runs of three or more steps replay a captured pair of steps (CUDA graph);
+single steps launch the kernels one by one.  Both give the same state
+(within the order of floating-point atomic additions), from either parity of
+the level ping-pong, and a change of the diagnostics or launch choices
+between runs reaches the replayed steps."""
+import numpy as np
+import pytest
+
+from paper_1612_03310_gb300 import build_lib, inputs
+
+pytestmark = pytest.mark.gpu
+
+UND = inputs.WORKLOADS["c1"]["undulator"]
+FIELDS = ["Ex", "Ey", "Ez", "Bx", "By", "Bz", "Ax", "phi", "Jx", "rho"]
+
+
+@pytest.fixture(scope="module")
+def M():
+    build_lib.build()
+    from paper_1612_03310_gb300 import mithra
+    try:
+        mithra.Simulation(dict(inputs.random_grid(0, 4, 4, 4), boundary=1), None, None).close()
+    except mithra.MithraError as e:
+        if e.status == mithra.ENODEV:
+            pytest.skip("no GB300 device")
+        raise
+    return mithra
+
+
+def rel_l2(a, b):
+    nb = np.linalg.norm(b)
+    return float(np.linalg.norm(a - b) / nb) if nb else float(np.linalg.norm(a))
+
+
+def pair(M, prec, seed=3):
+    g = dict(inputs.random_grid(seed, 30, 26, 40), boundary=1)
+    P = inputs.random_particles(seed + 1, g, 3000, u_scale=0.3)
+    und = dict(UND, z_ent_lab=0.0)
+    return (M.Simulation(g, und, P, precision=prec), M.Simulation(g, und, P, precision=prec))
+
+
+@pytest.mark.parametrize("prec_name", ["P32", "P64"])
+def test_replayed_steps_equal_single_steps(M, prec_name):
+    prec = getattr(M, prec_name)
+    tol = 1e-12 if prec == M.P64 else 1e-5
+    a, b = pair(M, prec)
+    with a, b:
+        a.set_power_sampling(20, 64)
+        b.set_power_sampling(20, 64)
+        # 1 eager step, then graph runs from the other parity, odd and even
+        for n in (1, 7, 4, 5):
+            a.step(n)
+            for _ in range(n):
+                b.step(1)
+        assert a.time()[0] == b.time()[0] == 17
+        for nm in FIELDS:
+            assert rel_l2(a.copy_field(nm), b.copy_field(nm)) <= tol, nm
+        pa, pb = a.read_power(), b.read_power()
+        assert pa.shape == pb.shape == (17, 3)
+        assert np.allclose(pa, pb, rtol=tol, atol=1e-30)
+        qa, qb = a.copy_particles(), b.copy_particles()
+        assert np.array_equal(qa["lost"], qb["lost"])
+
+
+def test_settings_changed_between_runs_reach_the_replay(M):
+    a, b = pair(M, M.P32, seed=7)
+    with a, b:
+        a.step(6)                       # captures and replays
+        b.step(6)
+        a.set_power_sampling(20, 100)   # must drop the captured steps
+        a.set_bunch_sampling(1.0e3, 2, 10)
+        a.step(6)
+        assert a.read_power().shape == (6, 3)
+        assert list(a.read_bunch()[:, 0]) == [8, 10, 12]
+        a.set_tuning(push_variant=0)    # another particle-step form
+        b.set_tuning(push_variant=0)
+        a.step(5)
+        for _ in range(11):
+            b.step(1)
+        assert a.time()[0] == b.time()[0] == 17
+        for nm in ("Ex", "Bz", "rho"):
+            assert rel_l2(a.copy_field(nm), b.copy_field(nm)) <= 1e-5, nm
