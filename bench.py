@@ -226,7 +226,7 @@ def run_gpu(args, rank, world):
     tuning = autotune.tune(g, und, bunch, prec, stream=stream.cuda_stream)  # untimed
     sim = mithra.Simulation(g, und, bunch, precision=prec, stream=stream.cuda_stream)
     sim.set_tuning(**tuning)
-    sim.set_power_sampling(kp, W + K)
+    sim.set_power_sampling(kp, W + 2 * K)
     sim.step(W)
     sim.sync()
     uuid = None
@@ -237,7 +237,8 @@ def run_gpu(args, rank, world):
     sampler = ClockSampler(uuid)
     sampler.start()
     time.sleep(0.3)
-    sim.profile(True)
+    # the timed region: K steps as the library runs them (pairs of steps
+    # replayed from a captured CUDA graph, no per-kernel events)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     barrier()
@@ -247,8 +248,19 @@ def run_gpu(args, rank, world):
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
-    sampler.stop()
     ms = e0.elapsed_time(e1)
+    # a second timed region of K steps launched one by one with a CUDA event
+    # pair around every kernel scope on the simulation's stream: the
+    # per-kernel durations of the roofline
+    sim.profile(True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    sim.step(K)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    sampler.stop()
+    ms_events = e0.elapsed_time(e1)
     kt = sim.kernel_times()
     sim.profile(False)
     power = sim.read_power()
@@ -256,7 +268,8 @@ def run_gpu(args, rank, world):
     sim.close()
     ms = max_over_ranks(ms, world)
     rec = autotune.record(g, n_part, prec) or {}
-    res = dict(ms=ms, kernel_times=kt, clocks=sampler.summary(), n_part=n_part, ncell=ncell,
+    res = dict(ms=ms, ms_events=max_over_ranks(ms_events, world), kernel_times=kt,
+               clocks=sampler.summary(), n_part=n_part, ncell=ncell,
                tuning=tuning, trials=[{k: (round(v, 4) if k == "ms" else v) for k, v in t.items()}
                                       for t in rec.get("trials", [])],
                grid=g, n_lost=parts["n_lost"], power_last=float(power[-1, 0]),
@@ -268,9 +281,8 @@ def run_gpu(args, rank, world):
     def side_run(precision, steps):
         sim = mithra.Simulation(g, und, bunch, precision=precision, stream=stream.cuda_stream)
         sim.set_tuning(**autotune.tune(g, und, bunch, precision, stream=stream.cuda_stream))
-        sim.set_power_sampling(kp, W + steps)
+        sim.set_power_sampling(kp, W + 2 * steps)
         sim.step(W)
-        sim.profile(True)
         torch.cuda.synchronize()
         barrier()
         e0.record(stream)
@@ -278,6 +290,9 @@ def run_gpu(args, rank, world):
         e1.record(stream)
         torch.cuda.synchronize()
         ms_side = e0.elapsed_time(e1)
+        sim.profile(True)           # per-kernel durations: a second region
+        sim.step(steps)
+        torch.cuda.synchronize()
         kts = sim.kernel_times()
         sim.close()
         ms_side = max_over_ranks(ms_side, world)
@@ -613,6 +628,10 @@ def main():
                     "achieved_gbs": stencil_gbs, "frac": stencil_gbs / peak,
                     "cell_updates_per_s": ncell / (stencil_ms / 1e3)},
         "kernel_share": {k: round(v[0] / total_kernel_ms, 4) for k, v in kt.items()},
+        "kernel_timing": {"region": "a second timed region of the same K steps launched one "
+                                    "by one, a CUDA event pair around every kernel scope on the "
+                                    "simulation's stream",
+                          "ms_per_step": res["ms_events"] / K},
         "clocks": res["clocks"],
         "gpu_launches": res["launches"],
         "tuning": res["tuning"],

@@ -175,15 +175,18 @@ __device__ inline bool boundary_vertex(int nx, int ny, int nz, int* i, int* j, i
 // evaluated here from the same inputs as the interior update (whose D_q^- is
 // still in place).  Face vertices of a second-order grid add mur2_terms.  The
 // boundary sources are zeroed (no deposit reads them).
-// The boundary vertices that k_potential_zloop_mur1 leaves (every vertex but
-// the x and y face vertices whose interior neighbour q lies on a plane
-// 2 .. nz-3 next to no other face), enumerated one per thread of a 1-D grid
-// of rest_count threads: the z faces; on each x face the rows k = 1, nz-2
-// and the columns j = 1, ny-2; on each y face the rows k = 1, nz-2 and the
-// columns i = 0, 1, nx-2, nx-1.  nx, ny, nz >= 4, so no vertex is listed
-// twice.
+// Whether the x+ face's lanes share a warp with their interior neighbours
+// (blocks are 32 wide along x, so i = nx-1 is a warp's lane 0 when
+// (nx-1) % 32 == 0).
+__host__ __device__ inline bool xhi_fused(int nx) { return ((nx - 1) & 31) != 0; }
+
+// The boundary vertices that k_potential_zloop_mur1 leaves, one per thread
+// of a 1-D grid of rest_count threads: the z faces, the y faces (edges
+// included), and the x+ face when its lanes cannot share a warp with their
+// neighbours (xhi_fused false).
 __host__ __device__ inline long long rest_count(int nx, int ny, int nz) {
-  return 2LL * nx * ny + 4LL * (ny - 2) + 4LL * (nz - 4) + 4LL * nx + 8LL * (nz - 4);
+  return 2LL * nx * ny + 2LL * nx * (nz - 2) +
+         (xhi_fused(nx) ? 0LL : (long long)(ny - 2) * (nz - 2));
 }
 __device__ inline bool rest_vertex(int nx, int ny, int nz, int* i, int* j, int* k) {
   long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -194,29 +197,15 @@ __device__ inline bool rest_vertex(int nx, int ny, int nz, int* i, int* j, int* 
     return true;
   }
   t -= 2 * nxy;
-  const int ry = ny - 2, cz = nz - 4;
-  if (t < 4LL * ry) {  // x faces, rows k = 1, nz-2
-    const int face = (int)(t / (2 * ry)), rr = (int)(t % (2 * ry));
-    *i = face ? nx - 1 : 0; *j = 1 + rr % ry; *k = rr / ry ? nz - 2 : 1;
+  const long long ny_face = (long long)nx * (nz - 2);
+  if (t < 2 * ny_face) {  // y faces, planes 1 .. nz-2
+    const long long r = t % ny_face;
+    *i = (int)(r % nx); *k = 1 + (int)(r / nx); *j = t < ny_face ? 0 : ny - 1;
     return true;
   }
-  t -= 4LL * ry;
-  if (t < 4LL * cz) {  // x faces, columns j = 1, ny-2, planes 2 .. nz-3
-    const int face = (int)(t / (2 * cz)), rr = (int)(t % (2 * cz));
-    *i = face ? nx - 1 : 0; *j = rr / cz ? ny - 2 : 1; *k = 2 + rr % cz;
-    return true;
-  }
-  t -= 4LL * cz;
-  if (t < 4LL * nx) {  // y faces, rows k = 1, nz-2
-    const int face = (int)(t / (2 * nx)), rr = (int)(t % (2 * nx));
-    *j = face ? ny - 1 : 0; *i = rr % nx; *k = rr / nx ? nz - 2 : 1;
-    return true;
-  }
-  t -= 4LL * nx;
-  if (t < 8LL * cz) {  // y faces, columns i = 0, 1, nx-2, nx-1, planes 2 .. nz-3
-    const int face = (int)(t / (4 * cz)), rr = (int)(t % (4 * cz));
-    const int c = rr / cz;
-    *j = face ? ny - 1 : 0; *i = c < 2 ? c : nx - 4 + c; *k = 2 + rr % cz;
+  t -= 2 * ny_face;
+  if (!xhi_fused(nx) && t < (long long)(ny - 2) * (nz - 2)) {  // x+ face
+    *i = nx - 1; *j = 1 + (int)(t % (ny - 2)); *k = 1 + (int)(t / (ny - 2));
     return true;
   }
   return false;
@@ -310,10 +299,13 @@ __device__ inline V4<T> plane_laplacian(const StencilP<T>& p, const PlaneSums<T>
   return L + p.rz2 * ((pl.c - z.c) + (m.c - z.c));
 }
 
-// kMur: a column next to exactly one x or y face also applies first-order
-// Mur (the condition of k_mur_boundary, from this thread's own D_q^- and
-// D_q^+) to its boundary vertex on the planes 2 .. nz-3; every other
-// boundary vertex is left to k_mur_boundary<.., kRest = true>.
+// kMur: the lanes of the x faces (i = 0, and i = nx-1 when xhi_fused) run
+// the column loop on their own boundary vertex b and, instead of the
+// interior update, take first-order Mur (the condition of k_mur_boundary)
+// from the increments D_q^-, D_q^+ of the neighbouring lane's vertex q, read
+// by warp shuffle: D_b^+ = b0 (D_q^+ - D_b^-) + D_q^-.  Their loads fall in
+// the rows the warp reads anyway; every other boundary vertex is left to
+// k_mur_boundary<.., kRest = true>.
 template <bool kLo, typename T, bool kMur>
 __device__ __forceinline__ void zloop_body(const StencilP<T>& p, const V4<T>* __restrict__ cur,
                                            const LoV4* __restrict__ curlo,
@@ -324,7 +316,18 @@ __device__ __forceinline__ void zloop_body(const StencilP<T>& p, const V4<T>* __
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   const int kb = max((int)blockIdx.z * lz, 1);
   const int ke = min((int)blockIdx.z * lz + lz, p.nz - 1);
-  if (kb >= ke || i < 1 || i > p.nx - 2 || j < 1 || j > p.ny - 2) return;
+  const bool xb = kMur && (i == 0 || (i == p.nx - 1 && xhi_fused(p.nx)));
+  const bool active = kb < ke && j >= 1 && j <= p.ny - 2 && ((i >= 1 && i <= p.nx - 2) || xb);
+  unsigned live = 0;
+  if (kMur) live = __ballot_sync(0xffffffffu, active);
+  if (!active) return;
+  bool xwarp = false;
+  int from = 0;
+  if (kMur) {
+    xwarp = __any_sync(live, xb);
+    const int lane = threadIdx.x & 31;
+    from = i == 0 ? lane + 1 : (xb ? lane - 1 : lane);
+  }
   const long long col = (long long)j * p.nx + i;
   const int nx = p.nx;
   auto hi = [&](long long q) { return ldg4(cur + q); };
@@ -336,26 +339,8 @@ __device__ __forceinline__ void zloop_body(const StencilP<T>& p, const V4<T>* __
     lm = plane_sums<T>(lo, (long long)(kb - 1) * p.nxy + col, nx);
     l0 = plane_sums<T>(lo, (long long)kb * p.nxy + col, nx);
   }
-  // kMur: a column next to exactly one x or y face has one boundary vertex
-  // at the fixed offset bo (|bo| = 1: an x face; nx >= 3, so |bo| = nx is a
-  // y face)
-  int bo = 0;
-  if (kMur) {
-    const int fx = (i == 1) | ((i == nx - 2) << 1), fy = (j == 1) | ((j == p.ny - 2) << 1);
-    if ((fx != 0) + (fy != 0) == 1 && fx != 3 && fy != 3)
-      bo = fx == 1 ? -1 : fx == 2 ? 1 : fy == 1 ? -nx : nx;
-  }
   for (int k = kb; k < ke; ++k) {
     const long long q = (long long)k * p.nxy + col;
-    const bool zface = kMur && (k == 1 || k == p.nz - 2);
-    const bool fast = kMur && bo != 0 && !zface;
-    // the compensated form has the registers to issue the boundary loads early
-    V4<T> dbm, cb, cbl;
-    if (kLo && fast) {
-      dbm = D[q + bo];
-      cb = ldg4(cur + q + bo);
-      cbl = ld_lo<T>(curlo, q + bo);
-    }
     const PlaneSums<T> hp = plane_sums<T>(hi, q + p.nxy, nx);
     V4<T> L = plane_laplacian(p, hm, h0, hp);
     PlaneSums<T> lp;
@@ -366,6 +351,13 @@ __device__ __forceinline__ void zloop_body(const StencilP<T>& p, const V4<T>* __
     const V4<T> dm = D[q];
     const V4<T> sv = src[q];
     V4<T> dp = dm + (L + source_term(p, sv));
+    if (kMur && xwarp) {  // warp-uniform
+      const V4<T> dq = v4(__shfl_sync(live, dp.x, from), __shfl_sync(live, dp.y, from),
+                          __shfl_sync(live, dp.z, from), __shfl_sync(live, dp.w, from));
+      const V4<T> mq = v4(__shfl_sync(live, dm.x, from), __shfl_sync(live, dm.y, from),
+                          __shfl_sync(live, dm.z, from), __shfl_sync(live, dm.w, from));
+      if (xb) dp = mur_beta0(p, 1) * (dq - dm) + mq;
+    }
     if (!p.space_charge) dp.w = (T)0;
     if (nonzero(sv)) src[q] = v4((T)0, (T)0, (T)0, (T)0);
     D[q] = dp;
@@ -378,24 +370,6 @@ __device__ __forceinline__ void zloop_body(const StencilP<T>& p, const V4<T>* __
       l0 = lp;
     } else {
       nxt[q] = h0.c + dp;
-    }
-    if (fast) {
-      if (!kLo) {
-        dbm = D[q + bo];
-        cb = ldg4(cur + q + bo);
-      }
-      V4<T> db = mur_beta0(p, (bo == 1 || bo == -1) ? 1 : 2) * (dp - dbm) + dm;
-      if (!p.space_charge) db.w = (T)0;
-      D[q + bo] = db;
-      if (kLo) {
-        V4<T> h, l;
-        comp_add(cb, cbl, db, &h, &l);
-        nxt[q + bo] = h;
-        st_lo(nxtlo, q + bo, l);
-      } else {
-        nxt[q + bo] = cb + db;
-      }
-      src[q + bo] = v4((T)0, (T)0, (T)0, (T)0);
     }
     hm = h0;
     h0 = hp;
