@@ -242,6 +242,32 @@ __device__ inline void boris(const PicP<T>& p, U u[3], const T Ef[3], const T Bf
   u[2] = t3z + h * E[2];
 }
 
+// FP64 momenta next to FP32 fields (P32_U64): everything in FP64 as in the
+// general form, except that gamma_1 takes the FP32-seeded Newton-Raphson of
+// rsqrt_nr and the factor 2 / (1 + t.t) an FP32-seeded Newton-Raphson
+// reciprocal (relative error ~1e-14) instead of an FP64 division, the
+// costliest sequence on GB300's narrow FP64 pipe.
+template <>
+__device__ inline void boris<float, double>(const PicP<float>& p, double u[3], const float Ef[3],
+                                            const float Bf[3]) {
+  const double h = p.h;
+  const double E[3] = {Ef[0], Ef[1], Ef[2]};
+  const double t1x = u[0] + h * E[0], t1y = u[1] + h * E[1], t1z = u[2] + h * E[2];
+  const double al = p.an * rsqrt_nr<float>(1.0 + t1x * t1x + t1y * t1y + t1z * t1z);
+  const double Tx = al * (double)Bf[0], Ty = al * (double)Bf[1], Tz = al * (double)Bf[2];
+  const double den = 1.0 + Tx * Tx + Ty * Ty + Tz * Tz;
+  double r = (double)(1.0f / (float)den);
+  r = r * (2.0 - den * r);
+  const double f = 2.0 * r;
+  const double Sx = f * Tx, Sy = f * Ty, Sz = f * Tz;
+  const double t2x = t1x + (t1y * Tz - t1z * Ty);
+  const double t2y = t1y + (t1z * Tx - t1x * Tz);
+  const double t2z = t1z + (t1x * Ty - t1y * Tx);
+  u[0] = t1x + (t2y * Sz - t2z * Sy) + h * E[0];
+  u[1] = t1y + (t2z * Sx - t2x * Sz) + h * E[1];
+  u[2] = t1z + (t2x * Sy - t2y * Sx) + h * E[2];
+}
+
 __device__ inline bool valid_cell(int i, int j, int k, int nx, int ny, int nz) {
   return i >= 1 && i <= nx - 3 && j >= 1 && j <= ny - 3 && k >= 1 && k <= nz - 3;
 }
