@@ -573,11 +573,17 @@ __global__ void k_scatter(Parts<T, U> a, Parts<T, U> b, long long np, const int*
                           const int* __restrict__ rank, const int* __restrict__ offset) {
   const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (q >= np) return;
-  const long long d = (long long)offset[key[q]] + rank[q];
-  b.cell[d] = a.cell[q];
-  b.fx[d] = a.fx[q]; b.fy[d] = a.fy[q]; b.fz[d] = a.fz[q];
-  b.ux[d] = a.ux[q]; b.uy[d] = a.uy[q]; b.uz[d] = a.uz[q];
-  b.id[d] = a.id[q];
+  // streaming loads and stores (the potential update in between evicts the
+  // particles from L2 anyway): 39 instead of 45 us on c2
+  const long long d = (long long)__ldcs(offset + __ldcs(key + q)) + __ldcs(rank + q);
+  __stcs(b.cell + d, __ldcs(a.cell + q));
+  __stcs(b.fx + d, __ldcs(a.fx + q));
+  __stcs(b.fy + d, __ldcs(a.fy + q));
+  __stcs(b.fz + d, __ldcs(a.fz + q));
+  __stcs(b.ux + d, __ldcs(a.ux + q));
+  __stcs(b.uy + d, __ldcs(a.uy + q));
+  __stcs(b.uz + d, __ldcs(a.uz + q));
+  __stcs(b.id + d, __ldcs(a.id + q));
 }
 
 // Copy-out in the original particle order: FP64 positions from (cell, f).
