@@ -151,6 +151,23 @@ NCU_TRAFFIC = {
 }
 
 
+def push_rates(kt: dict, n_particles: int, grid: dict, prec: str) -> dict | None:
+    """The particle step's achieved bandwidth and deposit (atomic) rates per
+    second of its CUDA-event duration: each particle deposits rho at 8
+    vertices (two int32 shared-memory atomics each, hi and lo of the
+    fixed-point block, in the FP32 forms) and J at 8 vertices (one FP32x4
+    vector reduction in L2 each)."""
+    if "push" not in kt or not kt["push"][1]:
+        return None
+    s = kt["push"][0] / kt["push"][1] / 1e3
+    ab = algorithmic_bytes("push", grid, n_particles, prec)
+    return {"avg_launch_ms": s * 1e3, "achieved_gbs": ab / s / 1e9,
+            "charge_vertex_deposits_per_s": 8 * n_particles / s,
+            "current_vertex_deposits_per_s": 8 * n_particles / s,
+            "shared_int32_atomics_per_s": (16 * n_particles / s) if prec != "p64" else None,
+            "l2_vector_reductions_per_s": (8 * n_particles / s) if prec != "p64" else None}
+
+
 def algorithmic_bytes(kernel: str, grid: dict, n_particles: int, prec: str) -> float:
     """Algorithmic bytes per launch (the minimum a kernel must move)."""
     r = 8 if prec == "p64" else 4                      # field and fraction values
@@ -627,6 +644,7 @@ def main():
         "stencil": {"kernel": "potential_step", "avg_launch_ms": stencil_ms,
                     "achieved_gbs": stencil_gbs, "frac": stencil_gbs / peak,
                     "cell_updates_per_s": ncell / (stencil_ms / 1e3)},
+        "push": push_rates(kt, npart, res["grid"], args.precision),
         "kernel_share": {k: round(v[0] / total_kernel_ms, 4) for k, v in kt.items()},
         "kernel_timing": {"region": "a second timed region of the same K steps launched one "
                                     "by one, a CUDA event pair around every kernel scope on the "

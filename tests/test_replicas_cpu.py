@@ -59,3 +59,19 @@ def test_replica_totals():
     assert v == 4 * 1000 * 10 / 0.5
     assert p == 4 * 50 * 2 * 10 / 0.5
     assert b.max_over_ranks(3.0, 1) == 3.0
+
+
+def test_push_rates():
+    """Deposit rates of the bench line: 8 charge and 8 current vertices per
+    particle, two int32 shared atomics per charge vertex in the FP32 forms,
+    over the particle step's average launch time."""
+    b = _bench()
+    g = dict(nx=16, ny=16, nz=16)
+    r = b.push_rates({"push": (2.0, 4)}, 1000, g, "p32")      # 0.5 ms per launch
+    assert r["avg_launch_ms"] == 0.5
+    assert r["charge_vertex_deposits_per_s"] == 8 * 1000 / 0.5e-3
+    assert r["shared_int32_atomics_per_s"] == 16 * 1000 / 0.5e-3
+    assert r["l2_vector_reductions_per_s"] == 8 * 1000 / 0.5e-3
+    assert r["achieved_gbs"] == b.algorithmic_bytes("push", g, 1000, "p32") / 0.5e-3 / 1e9
+    assert b.push_rates({"push": (2.0, 4)}, 1000, g, "p64")["shared_int32_atomics_per_s"] is None
+    assert b.push_rates({}, 1000, g, "p32") is None
