@@ -8,11 +8,12 @@
 //      (Sec. "Field Evaluation") into shared memory;
 //   3. pushes the tile's particles: trilinear gather from shared memory
 //      (Eq. fieldInterpolation), rest-frame undulator field, Boris
-//      (Eq. BorisScheme), FP64 cell carry;
-//   4. deposits J^{n+1} (mid point) and rho^{n+3/2} (end point) into a
-//      shared-memory copy of the 11^3 vertices with shared atomics, and adds
-//      it to the global sources with one 128-bit vector atomic per touched
-//      vertex.
+//      (Eq. BorisScheme), FP64 gamma, cell carry;
+//   4. deposits rho^{n+3/2} (end point) into a shared-memory block over the
+//      11^3 vertices -- in the FP32 forms as exact int32 fixed-point sums,
+//      added to the global sources once per touched vertex -- and
+//      J^{n+1} (mid point) with FP32 vector atomics straight into L2 (FP64:
+//      both components through a shared FP64 block).
 // A particle whose sub-step leaves the tile (n_sub > 1) gathers from global
 // memory, and one whose deposit leaves the 11^3 block deposits with global
 // atomics: the same arithmetic on another path.  Sparse tiles (fewer
