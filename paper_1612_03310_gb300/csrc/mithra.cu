@@ -389,7 +389,7 @@ constexpr bool push_form_lo() { return sizeof(T) == 4; }
 // device at once.
 template <typename T, typename U>
 mithra_status setup_push_grid(mithra_sim* s) {
-  const int smem = tile_smem_bytes<T>();
+  const int smem = tile_smem_bytes<T, U>();
   if constexpr (push_form_plain<T, U>()) {
     MCHECK(s, cudaFuncSetAttribute(k_push_tiled<false, T, U>,
                                    cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
@@ -538,7 +538,7 @@ mithra_status launch_step(mithra_sim* s) {
         if constexpr (push_form_lo<T, U>())
           if (lo) kern = opt ? k_push_tiled<true, T, U, true> : k_push_tiled<false, T, U, true>;
         if (!kern) return fail(s, MITHRA_EINVAL, "no particle-step form for this precision");
-        kern<<<s->push_grid, 256, tile_smem_bytes<T>(), s->stream>>>(
+        kern<<<s->push_grid, 256, tile_smem_bytes<T, U>(), s->stream>>>(
             s->tm_box[1 - s->cur], s->tm_box_d, pp, s->dstate, P1, Dn, S, A, s->offset, s->tiles,
             s->count, s->key, s->rank, &s->dstate->n_lost, s->np);
       } else {

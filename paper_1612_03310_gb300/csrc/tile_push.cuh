@@ -45,9 +45,21 @@ template <typename T>
 __host__ __device__ constexpr int tile_eb_offset() {
   return 2 * tile_box_stride<T>();
 }
+// The next-particle slots of the dense loop (one particle per thread: cell,
+// fractions, momenta), kept where T and U have one size: with FP64 momenta
+// next to FP32 fields the 10 KB would cost the third CTA per SM.
+template <typename T, typename U>
+__host__ __device__ constexpr bool tile_prefetch() {
+  return sizeof(T) == sizeof(U);
+}
 template <typename T>
-__host__ __device__ constexpr int tile_smem_bytes() {
+__host__ __device__ constexpr int tile_slot_offset() {
   return tile_eb_offset<T>() + kTEC * 2 * (int)sizeof(V4<T>) + 16;
+}
+template <typename T, typename U>
+__host__ __device__ constexpr int tile_smem_bytes() {
+  return tile_slot_offset<T>() +
+         (tile_prefetch<T, U>() ? 256 * (4 + 3 * (int)sizeof(T) + 3 * (int)sizeof(U)) : 0);
 }
 
 // E, B at local vertex l of the potential box (strides 1, 11, 121), global
@@ -144,22 +156,31 @@ __device__ inline void deposit_rho_fixed(const PicP<T>& p, int* __restrict__ hi,
 // One particle's field step (shared by the staged and the per-warp path):
 // push, then the deposits of rho at the end point and J at the mid point
 // through dep(kRho, i, j, k, f, jx, jy, jz, rho), and the re-sort bucket.
-template <bool kOpt, typename T, typename U, typename Gather, typename Frame, typename Dep>
+// The particle's state comes from ld_cell(q) and ld_fu(q, f, u); next() is
+// called once the state has been consumed (after the push, or for a lost
+// particle after its cell), where the dense loop starts the copy of the
+// thread's next particle into the slot it read.
+template <bool kOpt, typename T, typename U, typename Gather, typename Frame, typename Dep,
+          typename LdCell, typename LdFU, typename Next>
 __device__ inline void tile_particle(const PicP<T>& p, Parts<T, U>& P, long long q,
                                      int* __restrict__ count, int* __restrict__ key,
                                      int* __restrict__ rank, long long* __restrict__ lost_ctr,
-                                     Gather&& gather, Frame&& frame, Dep&& dep) {
-  const int cell = P.cell[q];
+                                     Gather&& gather, Frame&& frame, Dep&& dep, LdCell&& ld_cell,
+                                     LdFU&& ld_fu, Next&& next) {
+  const int cell = ld_cell(q);
   int kk = p.nkeys;
+  if (cell < 0) next();
   if (cell >= 0) {
     int i, j, k;
     decode_cell(p, cell, &i, &j, &k);
-    T f[3] = {P.fx[q], P.fy[q], P.fz[q]};
-    U u[3] = {P.ux[q], P.uy[q], P.uz[q]};
+    T f[3];
+    U u[3];
+    ld_fu(q, f, u);
     const int ia = i, ja = j, ka = k;
     const T f0[3] = {f[0], f[1], f[2]};
     T disp[3];
     const bool ok = push_particle<kOpt>(p, i, j, k, f, u, disp, gather, frame);
+    next();
     P.ux[q] = u[0]; P.uy[q] = u[1]; P.uz[q] = u[2];
     if (!ok) {
       P.cell[q] = -1;
@@ -208,6 +229,22 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 3 : 1)) k_push_tiled(
   // sums (hi, lo), the current going to global memory directly (vector
   // atomics in L2, measured faster than FP32 shared-memory atomics).
   constexpr bool kF32 = sizeof(T) == 4;
+  // this thread's next-particle slot (stride 256 between the components)
+  constexpr bool kPre = tile_prefetch<T, U>();
+  int* sl_cell = reinterpret_cast<int*>(smem + tile_slot_offset<T>()) + threadIdx.x;
+  T* sl_f = reinterpret_cast<T*>(smem + tile_slot_offset<T>() + 256 * 4) + threadIdx.x;
+  U* sl_u = reinterpret_cast<U*>(smem + tile_slot_offset<T>() + 256 * (4 + 3 * (int)sizeof(T))) +
+            threadIdx.x;
+  auto prefetch = [&](long long qq) {
+    cp_async<4>(sl_cell, P.cell + qq);
+    cp_async<sizeof(T)>(sl_f, P.fx + qq);
+    cp_async<sizeof(T)>(sl_f + 256, P.fy + qq);
+    cp_async<sizeof(T)>(sl_f + 512, P.fz + qq);
+    cp_async<sizeof(U)>(sl_u, P.ux + qq);
+    cp_async<sizeof(U)>(sl_u + 256, P.uy + qq);
+    cp_async<sizeof(U)>(sl_u + 512, P.uz + qq);
+    cp_async_commit();
+  };
   T* sJ = reinterpret_cast<T*>(sP);
   int* sRh = reinterpret_cast<int*>(sP);
   int* sRl = sRh + kTPC;
@@ -254,6 +291,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 3 : 1)) k_push_tiled(
     }
     __syncthreads();
     const int beg = offset[tile], end = offset[tile + 1];
+    if (kPre && beg + tid < end) prefetch(beg + tid);
     // fixed-point scale 2^b of the FP32 charge block (0: tiles of more
     // than 2^16 particles deposit rho in global memory)
     float sb = 0.0f;
@@ -269,6 +307,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 3 : 1)) k_push_tiled(
     __syncthreads();
 
     for (int q = beg + tid; q < end; q += blockDim.x) {
+      if (kPre) cp_async_wait_all();
       tile_particle<kOpt>(
           p, P, q, count, key, rank, lost_ctr,
           [&](int ci, int cj, int ck, const T* ff, T* E, T* B) {
@@ -310,6 +349,19 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 3 : 1)) k_push_tiled(
               deposit_tile<false>(p, sJ, src, i0, j0, k0, i, j, k, f[0], f[1], f[2], jx, jy, jz,
                                   q);
             }
+          },
+          [&](long long qq) { return kPre ? *sl_cell : P.cell[qq]; },
+          [&](long long qq, T* f, U* u) {
+            if (kPre) {
+              f[0] = sl_f[0]; f[1] = sl_f[256]; f[2] = sl_f[512];
+              u[0] = sl_u[0]; u[1] = sl_u[256]; u[2] = sl_u[512];
+            } else {
+              f[0] = P.fx[qq]; f[1] = P.fy[qq]; f[2] = P.fz[qq];
+              u[0] = P.ux[qq]; u[1] = P.uy[qq]; u[2] = P.uz[qq];
+            }
+          },
+          [&]() {
+            if (kPre && q + (int)blockDim.x < end) prefetch(q + blockDim.x);
           });
     }
     __syncthreads();
@@ -370,7 +422,13 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 3 : 1)) k_push_tiled(
             },
             [&](bool rho, int i, int j, int k, const T* f, T jx, T jy, T jz, T q) {
               deposit_cic(p, src, i, j, k, f[0], f[1], f[2], jx, jy, jz, q);
-            });
+            },
+            [&](long long qq) { return P.cell[qq]; },
+            [&](long long qq, T* f, U* u) {
+              f[0] = P.fx[qq]; f[1] = P.fy[qq]; f[2] = P.fz[qq];
+              u[0] = P.ux[qq]; u[1] = P.uy[qq]; u[2] = P.uz[qq];
+            },
+            [&]() {});
       }
     }
   }

@@ -55,6 +55,19 @@ __device__ inline bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int* er
 
 // orders earlier generic-proxy accesses of shared memory before later
 // async-proxy (TMA) writes to it
+// Per-thread asynchronous copy of 4 or 8 bytes from global to shared memory
+// (cp.async, cached in L1); cp_async_commit closes a group of them,
+// cp_async_wait_all waits for all of this thread's groups.
+template <int kBytes>
+__device__ inline void cp_async(void* dst, const void* src) {
+  static_assert(kBytes == 4 || kBytes == 8, "cp.async.ca copies 4, 8 or 16 bytes");
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(smem_addr(dst)), "l"(src),
+               "n"(kBytes)
+               : "memory");
+}
+__device__ inline void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ inline void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 __device__ inline void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
