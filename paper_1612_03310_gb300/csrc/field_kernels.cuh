@@ -90,14 +90,90 @@ __device__ inline V4<T> laplacian(const StencilP<T>& p, Load&& ld, long long c) 
   return L + p.rz2 * ((ld(c + nxy) - ac) + (ld(c - nxy) - ac));
 }
 
+// Register z-marching form of the interior update (no shared memory): a
+// thread owns column (i, j) for a run of lz planes and keeps, for the planes
+// k-1 and k, what they bring to the Laplacian (PlaneTerms) in registers, so a
+// plane of psi^n is read once per run (its x and y neighbours are the
+// adjacent threads' loads and hit L1) instead of three times as in the
+// direct form.  The same sums as the direct form, grouped per plane.
+template <typename T>
+struct PlaneSums {
+  V4<T> c, X, Y;
+};
+
+template <typename T, typename Load>
+__device__ inline PlaneSums<T> plane_sums(Load&& ld, long long q, int nx) {
+  PlaneSums<T> r;
+  r.c = ld(q);
+  r.X = (ld(q + 1) - r.c) + (ld(q - 1) - r.c);
+  r.Y = (ld(q + nx) - r.c) + (ld(q - nx) - r.c);
+  return r;
+}
+
+template <typename T>
+__device__ inline V4<T> plane_laplacian(const StencilP<T>& p, const PlaneSums<T>& m,
+                                        const PlaneSums<T>& z, const PlaneSums<T>& pl) {
+  V4<T> L = p.rxA * (m.X + pl.X) + p.rxB * z.X;
+  L = L + p.ryA * (m.Y + pl.Y) + p.ryB * z.Y;
+  return L + p.rz2 * ((pl.c - z.c) + (m.c - z.c));
+}
+
+// What one plane brings to the NSFD Laplacian (Eq. NSFDCoefficient) at its
+// own column and its z neighbours': a = rxA X + ryA Y (as plane k-1 or k+1),
+// b = rxB X + ryB Y (as plane k), X and Y the x and y neighbour-difference
+// sums of the level (hi + lo parts: the sums are small, so merging the parts
+// there costs nothing), and the level at the column, hi c and lo cl, for the
+// z second difference, formed part by part.  The z-marching loop carries
+// two planes of these instead of two planes of hi and lo sums each.
+template <typename T>
+struct PlaneTerms {
+  V4<T> a, b, c, cl;
+};
+
+template <bool kLo, typename T, typename LdHi, typename LdLo>
+__device__ inline PlaneTerms<T> plane_terms(const StencilP<T>& p, LdHi&& hi, LdLo&& lo,
+                                            long long q, int nx) {
+  const PlaneSums<T> h = plane_sums<T>(hi, q, nx);
+  V4<T> X = h.X, Y = h.Y, cl = v4((T)0, (T)0, (T)0, (T)0);
+  if (kLo) {
+    const PlaneSums<T> l = plane_sums<T>(lo, q, nx);
+    X = X + l.X;
+    Y = Y + l.Y;
+    cl = l.c;
+  }
+  return {p.rxA * X + p.ryA * Y, p.rxB * X + p.ryB * Y, h.c, cl};
+}
+
 template <bool kLo, typename T>
+__device__ inline V4<T> terms_laplacian(const StencilP<T>& p, const PlaneTerms<T>& m,
+                                        const PlaneTerms<T>& z, const PlaneTerms<T>& pl) {
+  V4<T> L = (m.a + pl.a) + z.b + p.rz2 * ((pl.c - z.c) + (m.c - z.c));
+  if (kLo) L = L + p.rz2 * ((pl.cl - z.cl) + (m.cl - z.cl));
+  return L;
+}
+
+// D^{n+1/2} at interior vertex c (and D^{n-1/2}, the source there): the
+// Laplacian in the direct form's order, or with kTerms in the z-marching
+// form's (so that a boundary kernel beside that form sees its increments bit
+// for bit).
+template <bool kLo, typename T, bool kTerms = false>
 __device__ inline V4<T> interior_increment(const StencilP<T>& p, const V4<T>* __restrict__ cur,
                                            const LoV4* __restrict__ curlo,
                                            const V4<T>* __restrict__ D,
                                            const V4<T>* __restrict__ src, long long c,
                                            V4<T>* dm_out, V4<T>* sv_out) {
-  V4<T> L = laplacian(p, [&](long long q) { return ldg4(cur + q); }, c);
-  if (kLo) L = L + laplacian(p, [&](long long q) { return ld_lo<T>(curlo, q); }, c);
+  auto hi = [&](long long q) { return ldg4(cur + q); };
+  auto lo = [&](long long q) { return ld_lo<T>(curlo, q); };
+  V4<T> L;
+  if (kTerms) {  // the arithmetic of the z-marching form, term for term
+    const int nx = p.nx;
+    L = terms_laplacian<kLo>(p, plane_terms<kLo>(p, hi, lo, c - p.nxy, nx),
+                             plane_terms<kLo>(p, hi, lo, c, nx),
+                             plane_terms<kLo>(p, hi, lo, c + p.nxy, nx));
+  } else {
+    L = laplacian(p, hi, c);
+    if (kLo) L = L + laplacian(p, lo, c);
+  }
   const V4<T> dm = D[c];
   const V4<T> sv = src[c];
   V4<T> dp = dm + (L + source_term(p, sv));
@@ -212,8 +288,9 @@ __device__ inline bool rest_vertex(int nx, int ny, int nz, int* i, int* j, int* 
 }
 
 // With kRest, only the vertices of rest_vertex (1-D launch of rest_count
-// threads).
-template <bool kLo, typename T, bool kRest = false>
+// threads).  kTerms: the interior update is the z-marching form, whose
+// arithmetic D_q^+ is recomputed with.
+template <bool kLo, typename T, bool kRest = false, bool kTerms = false>
 __global__ void __launch_bounds__(256) k_mur_boundary(StencilP<T> p,
                                                       const V4<T>* __restrict__ cur,
                                                       const LoV4* __restrict__ curlo,
@@ -230,7 +307,7 @@ __global__ void __launch_bounds__(256) k_mur_boundary(StencilP<T> p,
   const int mask = (qi != i) | ((qj != j) << 1) | ((qk != k) << 2);
   const long long b = cidx(i, j, k, p.nx, p.nxy), q = cidx(qi, qj, qk, p.nx, p.nxy);
   V4<T> dq_old, sq;
-  const V4<T> dq_new = interior_increment<kLo>(p, cur, curlo, D, src, q, &dq_old, &sq);
+  const V4<T> dq_new = interior_increment<kLo, T, kTerms>(p, cur, curlo, D, src, q, &dq_old, &sq);
   const V4<T> db_old = D[b];
   V4<T> db = mur_beta0(p, mask) * (dq_new - db_old) + dq_old;
   if (p.mur2 && (mask & (mask - 1)) == 0) db = db + mur2_terms(p, cur, mask, b, q);
@@ -271,33 +348,6 @@ __global__ void __launch_bounds__(256) k_potential_step(StencilP<T> p,
   store_level<kLo>(cur, curlo, nxt, nxtlo, c, dp);
 }
 
-// Register z-marching form of the interior update (no shared memory): a
-// thread owns column (i, j) for a run of lz planes and keeps, for the planes
-// k-1, k, k+1, the centre value and the x and y neighbour-difference sums in
-// registers, so a plane of psi^n is read once per run (its x and y
-// neighbours are the adjacent threads' loads and hit L1) instead of three
-// times as in the direct form.  Same arithmetic and order as the direct form.
-template <typename T>
-struct PlaneSums {
-  V4<T> c, X, Y;
-};
-
-template <typename T, typename Load>
-__device__ inline PlaneSums<T> plane_sums(Load&& ld, long long q, int nx) {
-  PlaneSums<T> r;
-  r.c = ld(q);
-  r.X = (ld(q + 1) - r.c) + (ld(q - 1) - r.c);
-  r.Y = (ld(q + nx) - r.c) + (ld(q - nx) - r.c);
-  return r;
-}
-
-template <typename T>
-__device__ inline V4<T> plane_laplacian(const StencilP<T>& p, const PlaneSums<T>& m,
-                                        const PlaneSums<T>& z, const PlaneSums<T>& pl) {
-  V4<T> L = p.rxA * (m.X + pl.X) + p.rxB * z.X;
-  L = L + p.ryA * (m.Y + pl.Y) + p.ryB * z.Y;
-  return L + p.rz2 * ((pl.c - z.c) + (m.c - z.c));
-}
 
 // kMur: the lanes of the x faces (i = 0, and i = nx-1 when xhi_fused) run
 // the column loop on their own boundary vertex b and, instead of the
@@ -332,22 +382,12 @@ __device__ __forceinline__ void zloop_body(const StencilP<T>& p, const V4<T>* __
   const int nx = p.nx;
   auto hi = [&](long long q) { return ldg4(cur + q); };
   auto lo = [&](long long q) { return ld_lo<T>(curlo, q); };
-  PlaneSums<T> hm = plane_sums<T>(hi, (long long)(kb - 1) * p.nxy + col, nx);
-  PlaneSums<T> h0 = plane_sums<T>(hi, (long long)kb * p.nxy + col, nx);
-  PlaneSums<T> lm, l0;
-  if (kLo) {
-    lm = plane_sums<T>(lo, (long long)(kb - 1) * p.nxy + col, nx);
-    l0 = plane_sums<T>(lo, (long long)kb * p.nxy + col, nx);
-  }
+  PlaneTerms<T> tm = plane_terms<kLo>(p, hi, lo, (long long)(kb - 1) * p.nxy + col, nx);
+  PlaneTerms<T> t0 = plane_terms<kLo>(p, hi, lo, (long long)kb * p.nxy + col, nx);
   for (int k = kb; k < ke; ++k) {
     const long long q = (long long)k * p.nxy + col;
-    const PlaneSums<T> hp = plane_sums<T>(hi, q + p.nxy, nx);
-    V4<T> L = plane_laplacian(p, hm, h0, hp);
-    PlaneSums<T> lp;
-    if (kLo) {
-      lp = plane_sums<T>(lo, q + p.nxy, nx);
-      L = L + plane_laplacian(p, lm, l0, lp);
-    }
+    const PlaneTerms<T> tp = plane_terms<kLo>(p, hi, lo, q + p.nxy, nx);
+    const V4<T> L = terms_laplacian<kLo>(p, tm, t0, tp);
     const V4<T> dm = D[q];
     const V4<T> sv = src[q];
     V4<T> dp = dm + (L + source_term(p, sv));
@@ -363,16 +403,14 @@ __device__ __forceinline__ void zloop_body(const StencilP<T>& p, const V4<T>* __
     D[q] = dp;
     if (kLo) {
       V4<T> h, l;
-      comp_add(h0.c, l0.c, dp, &h, &l);
+      comp_add(t0.c, t0.cl, dp, &h, &l);
       nxt[q] = h;
       st_lo(nxtlo, q, l);
-      lm = l0;
-      l0 = lp;
     } else {
-      nxt[q] = h0.c + dp;
+      nxt[q] = t0.c + dp;
     }
-    hm = h0;
-    h0 = hp;
+    tm = t0;
+    t0 = tp;
   }
 }
 
@@ -390,7 +428,7 @@ __global__ void __launch_bounds__(256) k_potential_zloop(StencilP<T> p,
 // The same with first-order Mur fused; the register caps keep the
 // occupancy of the plain form.
 template <bool kLo, typename T>
-__global__ void __launch_bounds__(256, sizeof(T) == 4 ? (kLo ? 2 : 3) : (kLo ? 1 : 2))
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? (kLo ? 3 : 4) : (kLo ? 1 : 2))
     k_potential_zloop_mur1(StencilP<T> p, const V4<T>* __restrict__ cur,
                            const LoV4* __restrict__ curlo, V4<T>* __restrict__ nxt,
                            LoV4* __restrict__ nxtlo, V4<T>* __restrict__ D,

@@ -465,12 +465,21 @@ mithra_status launch_step(mithra_sim* s) {
     // form (the rest first, by the boundary kernel); the other forms and
     // second-order Mur take the boundary kernel for every boundary vertex
     const bool fused = s->stencil_variant == 2 && s->g.boundary == 1;
+    // beside the z-marching form the boundary recomputes D_q^+ in its
+    // arithmetic
+    const bool zm = s->stencil_variant == 2;
     const dim3 mg = mur_grid(s->g.nx, s->g.ny, s->g.nz);
     const unsigned rg = blocks_for(rest_count(s->g.nx, s->g.ny, s->g.nz), 256);
     if (fused && L0)
-      k_mur_boundary<true, T, true><<<rg, 256, 0, s->stream>>>(sp, P0, L0, P1, L1, Dn, S);
+      k_mur_boundary<true, T, true, true><<<rg, 256, 0, s->stream>>>(sp, P0, L0, P1, L1, Dn, S);
     else if (fused)
-      k_mur_boundary<false, T, true><<<rg, 256, 0, s->stream>>>(sp, P0, L0, P1, L1, Dn, S);
+      k_mur_boundary<false, T, true, true><<<rg, 256, 0, s->stream>>>(sp, P0, L0, P1, L1, Dn, S);
+    else if (zm && L0)
+      k_mur_boundary<true, T, false, true><<<mg, dim3(32, 8), 0, s->stream>>>(sp, P0, L0, P1, L1,
+                                                                             Dn, S);
+    else if (zm)
+      k_mur_boundary<false, T, false, true><<<mg, dim3(32, 8), 0, s->stream>>>(sp, P0, L0, P1, L1,
+                                                                              Dn, S);
     else if (L0)
       k_mur_boundary<true, T><<<mg, dim3(32, 8), 0, s->stream>>>(sp, P0, L0, P1, L1, Dn, S);
     else
