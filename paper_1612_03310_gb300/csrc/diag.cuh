@@ -123,6 +123,7 @@ __global__ void __launch_bounds__(256) k_spectrum_accumulate(
   const double t = p.t0 + ((double)st->n + 0.5) * p.dt;
   const double tl = g0 * (t + b0 * zp / kC);
   const double dtl = g0 * p.dt;
+  const double b0c = b0 / kC;
   for (int m = threadIdx.x; m < nf; m += blockDim.x) {
     double sn, cs;
     sincos(omega[m] * tl, &sn, &cs);
@@ -139,7 +140,7 @@ __global__ void __launch_bounds__(256) k_spectrum_accumulate(
     eb_vertex(p, pn, D, cidx(i, j, kp, p.nx, p.nxy), E, B);
     const double Ex = E[0], Ey = E[1], Bx = B[0], By = B[1];
     const double F[4] = {g0 * (Ex + b0 * kC * By), g0 * (Ey - b0 * kC * Bx),
-                         g0 * (Bx - b0 * Ey / kC), g0 * (By + b0 * Ex / kC)};
+                         g0 * (Bx - b0c * Ey), g0 * (By + b0c * Ex)};
     for (int m = 0; m < nf; ++m) {
       double* a = acc + ((long long)m * nv + v) * 8;
       const double2 e = ph[m];

@@ -779,6 +779,7 @@ __global__ void __launch_bounds__(256) k_power(PicP<T> p, const V4<T>* __restric
     if (slot >= cap) return;
   }
   const int nin = (p.nx - 2) * (p.ny - 2);
+  const double b0c = b0 / kC;  // one FP64 division per thread, not two per vertex
   double part = 0.0;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nin; t += gridDim.x * blockDim.x) {
     const int i = 1 + t % (p.nx - 2);
@@ -788,8 +789,8 @@ __global__ void __launch_bounds__(256) k_power(PicP<T> p, const V4<T>* __restric
     const double Ex = E[0], Ey = E[1], Bx = B[0], By = B[1];
     const double exl = g0 * (Ex + b0 * kC * By);
     const double eyl = g0 * (Ey - b0 * kC * Bx);
-    const double bxl = g0 * (Bx - b0 * Ey / kC);
-    const double byl = g0 * (By + b0 * Ex / kC);
+    const double bxl = g0 * (Bx - b0c * Ey);
+    const double byl = g0 * (By + b0c * Ex);
     part += (exl * byl - eyl * bxl);
   }
   for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);

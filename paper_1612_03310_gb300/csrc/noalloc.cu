@@ -73,6 +73,7 @@ __global__ void __launch_bounds__(256) k_plane_rows(PicP<T> p, const V4<T>* __re
                                                     double g0, double b0,
                                                     double* __restrict__ rows) {
   const int j = 1 + blockIdx.x;
+  const double b0c = b0 / kC;
   double part = 0.0;
   for (int i = 1 + threadIdx.x; i <= p.nx - 2; i += blockDim.x) {
     T E[3], B[3];
@@ -80,8 +81,8 @@ __global__ void __launch_bounds__(256) k_plane_rows(PicP<T> p, const V4<T>* __re
     const double Ex = E[0], Ey = E[1], Bx = B[0], By = B[1];
     const double exl = g0 * (Ex + b0 * kC * By);
     const double eyl = g0 * (Ey - b0 * kC * Bx);
-    const double bxl = g0 * (Bx - b0 * Ey / kC);
-    const double byl = g0 * (By + b0 * Ex / kC);
+    const double bxl = g0 * (Bx - b0c * Ey);
+    const double byl = g0 * (By + b0c * Ex);
     part += exl * byl - eyl * bxl;
   }
   for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
