@@ -166,7 +166,8 @@ mithra_status mithra_create(const mithra_grid* grid, const mithra_undulator* und
 /* Enqueues n >= 0 field steps (potential update, E/B, gather, push, deposit,
  * re-sort, optional power sample) on the stream and returns without waiting.
  * With n >= 3 (and no profiling, and a stream other than the legacy or
- * per-thread default stream) the steps run as replays of two steps captured
+ * per-thread default stream that the caller is not capturing itself) the
+ * steps run as replays of two steps captured
  * once as a CUDA graph per parity of the level ping-pong; any later change of
  * sampling, spectrum, seed, fields or tuning re-captures them.  Returns the
  * status of work that has already finished. */

@@ -1013,9 +1013,15 @@ mithra_status mithra_step(mithra_sim* s, int64_t n) {
   int64_t t = 0;
   // runs of steps replay a captured pair (no profiling events inside; the
   // legacy and per-thread default streams cannot be captured)
-  const bool graph = n >= 3 && !s->profiling && s->stream != nullptr &&
-                     s->stream != reinterpret_cast<cudaStream_t>(1) &&
-                     s->stream != reinterpret_cast<cudaStream_t>(2);
+  bool graph = n >= 3 && !s->profiling && s->stream != nullptr &&
+               s->stream != reinterpret_cast<cudaStream_t>(1) &&
+               s->stream != reinterpret_cast<cudaStream_t>(2);
+  if (graph) {  // a stream the caller is capturing takes the launches themselves
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s->stream, &cs) != cudaSuccess ||
+        cs != cudaStreamCaptureStatusNone)
+      graph = false;
+  }
   if (graph) {
     if (!s->step_exec[s->cur]) {
       mithra_status st = capture_step_pair(s);
