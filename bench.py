@@ -145,8 +145,9 @@ PRECISIONS = {"p32": "P32", "p32_u64": "P32_U64", "p32_c": "P32_C", "p64": "P64"
 # now, by (timed scope, precision, workload); a kernel changed since its
 # capture must leave this table
 NCU_TRAFFIC = {
-    # k_mur_boundary<0, float, 1> + k_potential_zloop_mur1<0, float>
-    ("potential_step", "p32", "c2"): 28196096 + 57856 + 819375104 + 509474304,
+    # k_mur_boundary<0, float, 1, 1> + k_potential_zloop_mur1<0, float>
+    ("potential_step", "p32", "c2"): 28196096 + 61696 + 824917760 + 509206016,
+    ("push", "p32", "c2"): 179321088 + 62403328,
 }
 
 
