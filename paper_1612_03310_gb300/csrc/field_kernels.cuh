@@ -1,5 +1,6 @@
 // field_kernels.cuh -- potential update (Eq. updateEquation) with the Mur
-// boundary (Sec. "First Order ABCs", "Second Order ABCs") fused in, E/B at the
+// boundary (Sec. "First Order ABCs", "Second Order ABCs": its own kernel, and
+// first-order Mur at the x faces inside the z-marching update), E/B at the
 // vertices (Sec. "Field Evaluation"), radiated power and field copy-out.
 //
 // Storage of the leapfrog: the newest level psi^{n+1} in one of two
@@ -70,12 +71,11 @@ __device__ inline V4<T> source_term(const StencilP<T>& p, V4<T> s) {
   return v4(p.sA * s.x, p.sA * s.y, p.sA * s.z, p.sphi * s.w);
 }
 
-// Increment D^{n+1/2} of interior vertex c = (i, j, k) (the update equation
-// in increment form), neighbours of psi^n read through L1; *dm receives
-// D^{n-1/2} and *sv the source read.  With compensated levels (kLo) the
-// level is hi + lo and the Laplacian is taken of both parts: the neighbour
-// differences of hi are exact or nearly so, so the sum carries the level to
-// about twice FP32's precision.
+// (c dt)^2 lap_h of the level read by ld at interior vertex c, the direct
+// form: neighbours of psi^n read through L1.  With compensated levels (kLo)
+// the Laplacian is taken of both parts, hi and lo: the neighbour differences
+// of hi are exact or nearly so, so the sum carries the level to about twice
+// FP32's precision.
 template <typename T, typename Load>
 __device__ inline V4<T> laplacian(const StencilP<T>& p, Load&& ld, long long c) {
   const long long nxy = p.nxy;
