@@ -242,30 +242,79 @@ __device__ inline void boris(const PicP<T>& p, U u[3], const T Ef[3], const T Bf
   u[2] = t3z + h * E[2];
 }
 
-// FP64 momenta next to FP32 fields (P32_U64): everything in FP64 as in the
-// general form, except that gamma_1 takes the FP32-seeded Newton-Raphson of
-// rsqrt_nr and the factor 2 / (1 + t.t) an FP32-seeded Newton-Raphson
-// reciprocal (relative error ~1e-14) instead of an FP64 division, the
-// costliest sequence on GB300's narrow FP64 pipe.
+// Float-float numbers (hi + lo, |lo| <= ulp(hi)/2, ~2^-46 relative) by the
+// error-free transformations: Knuth's TwoSum, Dekker's FastTwoSum and the
+// FMA product split.  The _rn intrinsics keep the compiler from fusing the
+// steps whose rounding the transformations rely on.
+struct FF {
+  float hi, lo;
+};
+__device__ inline FF ff_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b), bb = __fsub_rn(s, a);
+  return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ inline FF ff_fast(float a, float b) {  // |a| >= |b| or a == 0
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ inline FF ff_prod(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  return {p, fmaf(a, b, -p)};
+}
+__device__ inline FF ff_add(FF a, FF b) {
+  const FF s = ff_two_sum(a.hi, b.hi);
+  return ff_fast(s.hi, s.lo + (a.lo + b.lo));
+}
+__device__ inline FF ff_sub(FF a, FF b) { return ff_add(a, {-b.hi, -b.lo}); }
+__device__ inline FF ff_mul(FF a, FF b) {
+  const FF p = ff_prod(a.hi, b.hi);
+  return ff_fast(p.hi, p.lo + (a.hi * b.lo + a.lo * b.hi));
+}
+__device__ inline FF ff_mul(FF a, float b) {
+  const FF p = ff_prod(a.hi, b);
+  return ff_fast(p.hi, p.lo + a.lo * b);
+}
+__device__ inline FF ff_of(double x) {
+  const float h = (float)x;
+  return {h, (float)(x - (double)h)};
+}
+__device__ inline double ff_to_double(FF a) { return (double)a.hi + (double)a.lo; }
+
+// FP64 momenta next to FP32 fields (P32_U64): the momenta are stored in FP64
+// and the Boris step runs in float-float arithmetic on FP32 instructions
+// (GB300's FP64 pipe is narrow): kicks, gamma_1 by an FP32 seed and one
+// float-float Newton-Raphson step, the rotation vectors t and s (2 / (1 + t.t)
+// by a Newton reciprocal) and both cross products carry ~2^-46, far below the
+// FP32 fields they act with.
 template <>
 __device__ inline void boris<float, double>(const PicP<float>& p, double u[3], const float Ef[3],
                                             const float Bf[3]) {
-  const double h = p.h;
-  const double E[3] = {Ef[0], Ef[1], Ef[2]};
-  const double t1x = u[0] + h * E[0], t1y = u[1] + h * E[1], t1z = u[2] + h * E[2];
-  const double al = p.an * rsqrt_nr<float>(1.0 + t1x * t1x + t1y * t1y + t1z * t1z);
-  const double Tx = al * (double)Bf[0], Ty = al * (double)Bf[1], Tz = al * (double)Bf[2];
-  const double den = 1.0 + Tx * Tx + Ty * Ty + Tz * Tz;
-  double r = (double)(1.0f / (float)den);
-  r = r * (2.0 - den * r);
-  const double f = 2.0 * r;
-  const double Sx = f * Tx, Sy = f * Ty, Sz = f * Tz;
-  const double t2x = t1x + (t1y * Tz - t1z * Ty);
-  const double t2y = t1y + (t1z * Tx - t1x * Tz);
-  const double t2z = t1z + (t1x * Ty - t1y * Tx);
-  u[0] = t1x + (t2y * Sz - t2z * Sy) + h * E[0];
-  u[1] = t1y + (t2z * Sx - t2x * Sz) + h * E[1];
-  u[2] = t1z + (t2x * Sy - t2y * Sx) + h * E[2];
+  const FF h = ff_of(p.h), an = ff_of(p.an);
+  const FF hE[3] = {ff_mul(h, Ef[0]), ff_mul(h, Ef[1]), ff_mul(h, Ef[2])};
+  const FF t1[3] = {ff_add(ff_of(u[0]), hE[0]), ff_add(ff_of(u[1]), hE[1]),
+                    ff_add(ff_of(u[2]), hE[2])};
+  // 1 / gamma_1 = 1 / sqrt(1 + t1.t1)
+  const FF g2 = ff_add(ff_add(ff_add(FF{1.0f, 0.0f}, ff_mul(t1[0], t1[0])), ff_mul(t1[1], t1[1])),
+                       ff_mul(t1[2], t1[2]));
+  const float y0 = rsqrtf(g2.hi);
+  const FF e1 = ff_sub(FF{1.0f, 0.0f}, ff_mul(g2, ff_prod(y0, y0)));  // 1 - g2 y0^2, small
+  const FF ig1 = ff_two_sum(y0, 0.5f * y0 * e1.hi);
+  const FF al = ff_mul(an, ig1);
+  const FF t[3] = {ff_mul(al, Bf[0]), ff_mul(al, Bf[1]), ff_mul(al, Bf[2])};
+  // f = 2 / (1 + t.t)
+  const FF den = ff_add(ff_add(ff_add(FF{1.0f, 0.0f}, ff_mul(t[0], t[0])), ff_mul(t[1], t[1])),
+                        ff_mul(t[2], t[2]));
+  const float r0 = 1.0f / den.hi;
+  const FF e2 = ff_sub(FF{1.0f, 0.0f}, ff_mul(den, r0));  // 1 - den r0, small
+  const FF f = ff_two_sum(2.0f * r0, 2.0f * r0 * e2.hi);
+  const FF sv[3] = {ff_mul(f, t[0]), ff_mul(f, t[1]), ff_mul(f, t[2])};
+  const FF t2[3] = {ff_add(t1[0], ff_sub(ff_mul(t1[1], t[2]), ff_mul(t1[2], t[1]))),
+                    ff_add(t1[1], ff_sub(ff_mul(t1[2], t[0]), ff_mul(t1[0], t[2]))),
+                    ff_add(t1[2], ff_sub(ff_mul(t1[0], t[1]), ff_mul(t1[1], t[0])))};
+  const FF c[3] = {ff_sub(ff_mul(t2[1], sv[2]), ff_mul(t2[2], sv[1])),
+                   ff_sub(ff_mul(t2[2], sv[0]), ff_mul(t2[0], sv[2])),
+                   ff_sub(ff_mul(t2[0], sv[1]), ff_mul(t2[1], sv[0]))};
+  for (int a = 0; a < 3; ++a) u[a] = ff_to_double(ff_add(ff_add(t1[a], c[a]), hE[a]));
 }
 
 __device__ inline bool valid_cell(int i, int j, int k, int nx, int ny, int nz) {
