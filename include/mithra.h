@@ -222,6 +222,22 @@ mithra_status mithra_copy_particles(mithra_sim* sim, double* x, double* y, doubl
                                     double* ux, double* uy, double* uz, int32_t* lost,
                                     int64_t* n_lost);
 
+/* Checkpoint and resume.  mithra_snapshot_bytes gives the size of a
+ * snapshot; mithra_snapshot waits for the stream and copies the simulation's
+ * device state (both potential levels and their lo parts, the increment, the
+ * sources, the particles, the last re-sort's tile offsets and list, the step
+ * counter, lost count and error word) into out (host, caller-allocated, that
+ * size).  mithra_restore copies such a snapshot back into a simulation
+ * created with the same grid, precision and particle count (MITHRA_EINVAL
+ * otherwise, nothing changed; MITHRA_EBUSY in a batch); its undulator, seed
+ * and launch choices are its own.  Recording diagnostics (power, bunch,
+ * spectrum) are not part of the state and stop at a restore.  Stepping a
+ * restored simulation continues the saved one (up to the order of the
+ * floating-point current atomics). */
+mithra_status mithra_snapshot_bytes(const mithra_sim* sim, int64_t* bytes);
+mithra_status mithra_snapshot(mithra_sim* sim, void* out);
+mithra_status mithra_restore(mithra_sim* sim, const void* in);
+
 /* Frees everything the simulation owns (waits for its work first). */
 mithra_status mithra_destroy(mithra_sim* sim);
 

@@ -1390,6 +1390,99 @@ mithra_status mithra_get_tuning(const mithra_sim* s, mithra_tuning* t) {
   return MITHRA_OK;
 }
 
+// ---- snapshot and restore -------------------------------------------------
+// The device state a later step reads: both potential levels (and their lo
+// parts), the increment, the sources, the particle buffer in use, the tile
+// counts, offsets and list of the last re-sort, and the step state (device
+// clock, lost count, error word); after a header that identifies the
+// simulation's shape.
+namespace {
+
+constexpr uint64_t kSnapMagic = 0x31504e5348544d4dULL;
+
+struct SnapHeader {
+  uint64_t magic;
+  int32_t prec, nx, ny, nz, nkeys, has_lo, cur, pb;
+  int64_t np, n_issued;
+  double t0;
+};
+
+struct SnapPart {
+  void* dev;
+  size_t bytes;
+};
+
+std::vector<SnapPart> snap_parts(const mithra_sim* s) {
+  const size_t cells = (size_t)ncell_of(&s->g);
+  const size_t fb = cells * 4 * real_size(s->prec);
+  std::vector<SnapPart> v = {{s->P[0], fb}, {s->P[1], fb}, {s->D, fb}, {s->S, fb}};
+  if (s->PL[0]) {
+    v.push_back({s->PL[0], cells * sizeof(LoV4)});
+    v.push_back({s->PL[1], cells * sizeof(LoV4)});
+  }
+  v.push_back({s->pbuf[s->pb], particle_buffer_bytes(s->np, s->prec)});
+  v.push_back({s->count, sizeof(int) * (size_t)(s->nkeys + 2)});
+  v.push_back({s->offset, sizeof(int) * (size_t)(s->nkeys + 2)});
+  v.push_back({s->tiles, sizeof(int) * (size_t)(s->nkeys + 1)});
+  v.push_back({s->dstate, sizeof(StepState)});
+  return v;
+}
+
+}  // namespace
+
+mithra_status mithra_snapshot_bytes(const mithra_sim* s, int64_t* bytes) {
+  if (!s || !bytes) return fail(nullptr, MITHRA_EINVAL, "sim or bytes is NULL");
+  int64_t b = sizeof(SnapHeader);
+  for (const SnapPart& part : snap_parts(s)) b += (int64_t)part.bytes;
+  *bytes = b;
+  return MITHRA_OK;
+}
+
+mithra_status mithra_snapshot(mithra_sim* s, void* out) {
+  if (!s || !out) return fail(s, MITHRA_EINVAL, "sim or out is NULL");
+  mithra_status st = sync_status(s);
+  if (st != MITHRA_OK) return st;
+  SnapHeader h{kSnapMagic, s->prec, s->g.nx, s->g.ny, s->g.nz, s->nkeys, s->PL[0] ? 1 : 0,
+               s->cur, s->pb, s->np, s->n_issued, s->t0};
+  unsigned char* o = static_cast<unsigned char*>(out);
+  std::memcpy(o, &h, sizeof(h));
+  size_t at = sizeof(h);
+  for (const SnapPart& part : snap_parts(s)) {
+    MCHECK(s, cudaMemcpyAsync(o + at, part.dev, part.bytes, cudaMemcpyDeviceToHost, s->stream));
+    at += part.bytes;
+  }
+  return sync_status(s);
+}
+
+mithra_status mithra_restore(mithra_sim* s, const void* in) {
+  if (!s || !in) return fail(s, MITHRA_EINVAL, "sim or in is NULL");
+  if (s->in_batch) return fail(s, MITHRA_EBUSY, "sim is stepped by a batch");
+  SnapHeader h;
+  std::memcpy(&h, in, sizeof(h));
+  if (h.magic != kSnapMagic || h.prec != s->prec || h.nx != s->g.nx || h.ny != s->g.ny ||
+      h.nz != s->g.nz || h.nkeys != s->nkeys || h.has_lo != (s->PL[0] ? 1 : 0) ||
+      h.np != s->np || (h.cur & ~1) != 0 || (h.pb & ~1) != 0)
+    return fail(s, MITHRA_EINVAL, "snapshot of another grid, precision or particle count");
+  MCHECK(s, cudaStreamSynchronize(s->stream));
+  drop_step_graphs(s);
+  s->cur = h.cur;
+  s->pb = h.pb;
+  s->n_issued = h.n_issued;
+  s->t0 = h.t0;
+  // the diagnostics' records are not part of the state: restoring stops them
+  s->power_cap = 0;
+  s->bunch_every = 0;
+  s->spec_nf = 0;
+  const unsigned char* p = static_cast<const unsigned char*>(in) + sizeof(h);
+  for (const SnapPart& part : snap_parts(s)) {
+    MCHECK(s, cudaMemcpyAsync(part.dev, p, part.bytes, cudaMemcpyHostToDevice, s->stream));
+    p += part.bytes;
+  }
+  MCHECK(s, cudaMemcpyAsync(s->h_err, &s->dstate->err, sizeof(int), cudaMemcpyDeviceToHost,
+                            s->stream));
+  return sync_status(s);
+}
+
 mithra_status mithra_destroy(mithra_sim* s) {
   if (!s) return MITHRA_OK;
   if (s->in_batch) mithra_batch_remove(s->in_batch, s);

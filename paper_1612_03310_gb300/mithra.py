@@ -31,7 +31,7 @@ EXPORTS = ["mithra_create", "mithra_step", "mithra_sync", "mithra_time", "mithra
            "mithra_batch_sync", "mithra_batch_size", "mithra_batch_last_error",
            "mithra_batch_destroy", "mithra_bunch_stats", "mithra_set_spectrum",
            "mithra_read_spectrum", "mithra_set_seed", "mithra_set_bunch_sampling",
-           "mithra_read_bunch"]
+           "mithra_read_bunch", "mithra_snapshot_bytes", "mithra_snapshot", "mithra_restore"]
 
 
 class MithraError(RuntimeError):
@@ -327,6 +327,19 @@ class Simulation:
             _check(lib().mithra_read_bunch(self.h, _dp(out), int(cnt.value), C.byref(cnt)),
                    self.h)
         return out
+
+    def snapshot(self) -> np.ndarray:
+        """The simulation's device state as bytes (mithra_snapshot)."""
+        n = C.c_int64()
+        _check(lib().mithra_snapshot_bytes(self.h, C.byref(n)), self.h)
+        buf = np.empty(int(n.value), dtype=np.uint8)
+        _check(lib().mithra_snapshot(self.h, buf.ctypes.data_as(C.c_void_p)), self.h)
+        return buf
+
+    def restore(self, snap: np.ndarray) -> None:
+        """Restores a snapshot of a simulation of the same shape."""
+        snap = np.ascontiguousarray(snap, dtype=np.uint8)
+        _check(lib().mithra_restore(self.h, snap.ctypes.data_as(C.c_void_p)), self.h)
 
     def set_spectrum(self, k_plane: int, lambda_lab) -> None:
         lam = np.ascontiguousarray(lambda_lab, dtype=np.float64)
