@@ -414,6 +414,35 @@ mithra_status mithra_footprint(const mithra_grid* grid, int64_t n_particles,
 /* Library version: major*10000 + minor*100 + patch. */
 int32_t mithra_version(void);
 
+/* Lab-frame description of an FEL case and the rest-frame numbers the
+ * library takes (Sec. "Lorentz Boost"; host only, FP64, no GPU needed). */
+typedef struct {
+    double gamma;             /* beam Lorentz factor in the lab */
+    double sigma_gamma_rel;   /* rms energy spread over gamma */
+    double lambda_u;          /* undulator period [m] */
+    double K;                 /* undulator parameter */
+    int32_t steps_per_period; /* time steps per rest-frame undulator period */
+    double courant;           /* c dt / dz, in (0, 1] */
+} mithra_lab_case;
+
+typedef struct {
+    double gamma0, beta0;     /* the frame: gamma / sqrt(1 + K^2/2) */
+    double dt, dz;            /* rest-frame time step [s] and longitudinal cell [m] */
+    double uz_mean, uz_sigma; /* the beam's mean longitudinal u = gamma beta in the
+                                 frame, and the spread the lab energy spread maps to */
+    double k_b;               /* rest-frame ponderomotive (bunching) wavenumber [1/m] */
+    double lambda_r_lab;      /* resonant wavelength lambda_u (1 + K^2/2) / (2 gamma^2) */
+} mithra_rest_frame;
+
+/* Fills *out from *lab: gamma0 = gamma / sqrt(1 + K^2/2), c dt = (lambda_u /
+ * gamma0) / steps_per_period, dz = c dt / courant; the beam's rest-frame
+ * Lorentz factor gamma gamma0 (1 - beta beta0) gives uz_mean, and the lab
+ * spread sigma_gamma_rel gamma scales by gamma0 (1 - beta beta0) to uz_sigma;
+ * k_b = gamma0 (2 pi / lambda_u)(1 + beta0).  MITHRA_EINVAL for gamma <= 1,
+ * lambda_u <= 0, K < 0, steps_per_period < 1, courant outside (0, 1], or a
+ * beam slower than the frame (gamma0 < 1 is impossible by construction). */
+mithra_status mithra_boost_from_lab(const mithra_lab_case* lab, mithra_rest_frame* out);
+
 #ifdef __cplusplus
 }
 #endif

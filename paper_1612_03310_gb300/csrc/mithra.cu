@@ -4,6 +4,7 @@
 // particle_kernels.cuh.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -1481,6 +1482,30 @@ mithra_status mithra_restore(mithra_sim* s, const void* in) {
   MCHECK(s, cudaMemcpyAsync(s->h_err, &s->dstate->err, sizeof(int), cudaMemcpyDeviceToHost,
                             s->stream));
   return sync_status(s);
+}
+
+mithra_status mithra_boost_from_lab(const mithra_lab_case* lab, mithra_rest_frame* out) {
+  if (!lab || !out) return fail(nullptr, MITHRA_EINVAL, "lab or out is NULL");
+  if (!(lab->gamma > 1.0) || !(lab->lambda_u > 0.0) || !(lab->K >= 0.0) ||
+      lab->steps_per_period < 1 || !(lab->courant > 0.0 && lab->courant <= 1.0) ||
+      !(lab->sigma_gamma_rel >= 0.0))
+    return fail(nullptr, MITHRA_EINVAL, "bad lab case");
+  const double g = lab->gamma;
+  const double g0 = g / std::sqrt(1.0 + 0.5 * lab->K * lab->K);
+  const double b0 = std::sqrt(1.0 - 1.0 / (g0 * g0));
+  const double b = std::sqrt(1.0 - 1.0 / (g * g));
+  const double shift = g0 * (1.0 - b * b0);  // gamma_rest / gamma of the beam
+  const double gr = g * shift;
+  const double cdt = lab->lambda_u / g0 / lab->steps_per_period;
+  out->gamma0 = g0;
+  out->beta0 = b0;
+  out->dt = cdt / kC;
+  out->dz = cdt / lab->courant;
+  out->uz_mean = std::sqrt(std::max(gr * gr - 1.0, 0.0));
+  out->uz_sigma = g * lab->sigma_gamma_rel * shift;
+  out->k_b = g0 * 2.0 * kPi / lab->lambda_u * (1.0 + b0);
+  out->lambda_r_lab = lab->lambda_u * (1.0 + 0.5 * lab->K * lab->K) / (2.0 * g * g);
+  return MITHRA_OK;
 }
 
 mithra_status mithra_destroy(mithra_sim* s) {

@@ -31,7 +31,8 @@ EXPORTS = ["mithra_create", "mithra_step", "mithra_sync", "mithra_time", "mithra
            "mithra_batch_sync", "mithra_batch_size", "mithra_batch_last_error",
            "mithra_batch_destroy", "mithra_bunch_stats", "mithra_set_spectrum",
            "mithra_read_spectrum", "mithra_set_seed", "mithra_set_bunch_sampling",
-           "mithra_read_bunch", "mithra_snapshot_bytes", "mithra_snapshot", "mithra_restore"]
+           "mithra_read_bunch", "mithra_snapshot_bytes", "mithra_snapshot", "mithra_restore",
+           "mithra_boost_from_lab"]
 
 
 class MithraError(RuntimeError):
@@ -142,6 +143,27 @@ def make_grid(g: dict) -> Grid:
                 g.get("x0", 0.0), g.get("y0", 0.0), g.get("z0", 0.0), g["dt"],
                 int(g.get("n_sub", 1)), int(g.get("stencil", 0)), int(g.get("boundary", 1)),
                 int(g.get("space_charge", 1)))
+
+
+class LabCase(C.Structure):
+    _fields_ = [("gamma", C.c_double), ("sigma_gamma_rel", C.c_double),
+                ("lambda_u", C.c_double), ("K", C.c_double),
+                ("steps_per_period", C.c_int32), ("courant", C.c_double)]
+
+
+class RestFrame(C.Structure):
+    _fields_ = [("gamma0", C.c_double), ("beta0", C.c_double), ("dt", C.c_double),
+                ("dz", C.c_double), ("uz_mean", C.c_double), ("uz_sigma", C.c_double),
+                ("k_b", C.c_double), ("lambda_r_lab", C.c_double)]
+
+
+def boost_from_lab(gamma: float, lambda_u: float, K: float, steps_per_period: int,
+                   courant: float, sigma_gamma_rel: float = 0.0) -> dict:
+    """Rest-frame numbers of a lab-frame FEL case (mithra_boost_from_lab)."""
+    lab = LabCase(gamma, sigma_gamma_rel, lambda_u, K, int(steps_per_period), courant)
+    out = RestFrame()
+    _check(lib().mithra_boost_from_lab(C.byref(lab), C.byref(out)), None)
+    return {name: getattr(out, name) for name, _ in RestFrame._fields_}
 
 
 def normalized_wavelengths(lambda_r: float, f_min: float, f_max: float, df: float) -> np.ndarray:

@@ -134,3 +134,30 @@ def test_normalized_wavelengths():
     lam = mithra.normalized_wavelengths(2.0e-6, 0.9, 1.1, 0.05)
     assert lam.size == 5
     assert np.allclose(2.0e-6 / lam, [0.9, 0.95, 1.0, 1.05, 1.1])
+
+
+def test_boost_from_lab_reproduces_the_workloads(M):
+    """The host helper mithra_boost_from_lab against the workload table's
+    rest-frame numbers (themselves pinned to the Lorentz-boost closed forms
+    above): the frame, the time step and cell, the beam's momentum moments and
+    the bunching wavenumber; bad cases refused."""
+    c = 299792458.0
+    for name, gamma, spp in (("c1", 10.0, 32), ("c2", 100.0, 50), ("c3", 100.0, 100)):
+        w = inputs.WORKLOADS[name]
+        u, g, b = w["undulator"], w["grid"], w["bunch"]
+        r = M.boost_from_lab(gamma, u["lambda_u"], u["K"], spp, 0.95, sigma_gamma_rel=1e-4)
+        assert r["gamma0"] == pytest.approx(u["gamma0"], rel=1e-13)
+        assert r["dt"] == pytest.approx(g["dt"], rel=1e-13)
+        assert r["dz"] == pytest.approx(g["dz"], rel=1e-13)
+        assert r["uz_mean"] == pytest.approx(b["uz_mean"], rel=1e-12)
+        assert r["uz_sigma"] == pytest.approx(b["uz_sigma"], rel=1e-12)
+        assert r["k_b"] == pytest.approx(b["kb"], rel=1e-12)
+        assert r["lambda_r_lab"] == pytest.approx(
+            u["lambda_u"] * (1 + u["K"] ** 2 / 2) / (2 * gamma ** 2), rel=1e-14)
+        assert r["dt"] * c * spp * r["gamma0"] == pytest.approx(u["lambda_u"], rel=1e-13)
+    for bad in (dict(gamma=1.0), dict(courant=1.5), dict(steps_per_period=0),
+                dict(lambda_u=-0.01)):
+        args = dict(gamma=10.0, lambda_u=0.015, K=1.0, steps_per_period=32, courant=0.95)
+        args.update(bad)
+        with pytest.raises(M.MithraError):
+            M.boost_from_lab(**args)
