@@ -464,6 +464,7 @@ def run_serve(args, duration: float | None = None) -> dict:
         srv = serve.Server(budget, max_slots=64, tick_steps=64)
         st = srv.run(jobs, time_limit=dur)
         st.pop("done")
+        st.pop("not_done", None)
         out[name] = dict(st, offered_rate=rate)
     cap = out["rate"]["completed"] / out["rate"]["wall_s"]
     half = max(0.05, 0.5 * cap)
@@ -471,6 +472,7 @@ def run_serve(args, duration: float | None = None) -> dict:
     srv = serve.Server(budget, max_slots=64, tick_steps=64)
     st = srv.run(jobs, time_limit=dur + 120.0)
     st.pop("done")
+    st.pop("not_done", None)
     out["half_capacity"] = dict(st, offered_rate=half)
     r = out["rate"]
     return {"metric": "jobs/h and p50/p99 latency, continuous batching (c5)", "impl": "mithra",

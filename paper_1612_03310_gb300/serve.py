@@ -14,6 +14,14 @@ freed, and its latency (arrival to completion) recorded.
 Time is the wall clock (clock="wall", arrivals in seconds) or the server's
 own step counter (clock="steps", arrivals in steps), the latter for
 reproducible schedules in tests.
+
+Failures stay with the jobs they hit: a job whose footprint exceeds the
+whole budget is rejected on arrival; a job whose simulation cannot be
+created (an allocation failure, an invalid grid) fails at admission; a job
+with "cancel_at" (server time) is cancelled then, its partial power record
+kept; a step that returns an error fails the jobs in the batch and the
+server goes on with a fresh batch.  None of this touches the GPU beyond the
+library's own error returns.
 """
 from __future__ import annotations
 
@@ -37,6 +45,8 @@ class JobState:
     t_done: float | None = None
     power: np.ndarray | None = None
     fields: dict = field(default_factory=dict)
+    status: str = "pending"  # pending, active, done, rejected, failed, cancelled
+    error: str | None = None
 
 
 class Server:
@@ -70,16 +80,20 @@ class Server:
         g = dict(spec["grid"], boundary=1)
         bunch = inputs.make_bunch(spec["bunch_spec"], spec["seed"])
         sim = self._sim(g, spec["undulator"], bunch, precision=self.precision)
-        if self.tuning:
-            sim.set_tuning(**self.tuning)
-        sim.set_power_sampling(g["nz"] - self.kp_top, spec["steps"])
-        batch.add(sim)
+        try:
+            if self.tuning:
+                sim.set_tuning(**self.tuning)
+            sim.set_power_sampling(g["nz"] - self.kp_top, spec["steps"])
+            batch.add(sim)
+        except Exception:
+            sim.close()
+            raise
         js.sim = sim
         js.remaining = spec["steps"]
         js.t_admit = now
         self.used += js.footprint
 
-    def _retire(self, js: JobState, batch, now: float):
+    def _retire(self, js: JobState, batch, now: float, status: str = "done"):
         js.power = js.sim.read_power()
         for nm in self.keep_fields:
             js.fields[nm] = js.sim.copy_field(nm)
@@ -87,17 +101,38 @@ class Server:
         js.sim.close()
         js.sim = None
         js.t_done = now
+        js.status = status
+        self.used -= js.footprint
+
+    def _drop(self, js: JobState, batch, now: float, error: str):
+        """A job whose step failed: its simulation is closed, its memory freed."""
+        try:
+            batch.remove(js.sim)
+        except Exception:
+            pass
+        try:
+            js.sim.close()
+        except Exception:
+            pass
+        js.sim = None
+        js.t_done = now
+        js.status = "failed"
+        js.error = error
         self.used -= js.footprint
 
     # -- main loop ---------------------------------------------------------
     def run(self, jobs: list[dict], time_limit: float | None = None) -> dict:
         pending = deque(sorted((JobState(j, float(j.get("arrival", 0.0))) for j in jobs),
                                key=lambda s: s.arrival))
-        for js in pending:
+        failed: list[JobState] = []
+        for js in list(pending):
             js.footprint = int(self._fp(dict(js.spec["grid"], boundary=1),
                                         js.spec["bunch_spec"]["n"], self.precision))
             if js.footprint > self.budget:
-                raise ValueError(f"job {js.spec.get('jid')} needs {js.footprint} B > budget")
+                js.status = "rejected"
+                js.error = f"needs {js.footprint} B of a {self.budget} B budget"
+                pending.remove(js)
+                failed.append(js)
         queue: list[JobState] = []
         active: list[JobState] = []
         done: list[JobState] = []
@@ -115,8 +150,22 @@ class Server:
                         break
                     if self.used + js.footprint <= self.budget:
                         queue.remove(js)
-                        self._admit(js, batch, now)
+                        try:
+                            self._admit(js, batch, now)
+                        except mithra.MithraError as e:  # e.g. out of device memory
+                            if js.sim is not None:
+                                js.sim.close()
+                            js.sim = None
+                            js.status, js.error, js.t_done = "failed", str(e), now
+                            failed.append(js)
+                            continue
+                        js.status = "active"
                         active.append(js)
+                for js in [a for a in active
+                           if a.spec.get("cancel_at") is not None and a.spec["cancel_at"] <= now]:
+                    self._retire(js, batch, now, status="cancelled")
+                    active.remove(js)
+                    failed.append(js)
                 self.queue_depth.append((now, len(queue)))
                 if not active:
                     if self.clock == "steps":
@@ -129,8 +178,25 @@ class Server:
                 if self.clock == "steps" and pending:
                     # stop at the next arrival so that it is admitted on time
                     tick = max(1, min(tick, int(np.ceil(pending[0].arrival)) - self.steps_done))
-                batch.step(tick)
-                batch.sync()
+                if self.clock == "steps":
+                    # stop at the next cancellation as well
+                    cut = [int(np.ceil(a.spec["cancel_at"])) - self.steps_done for a in active
+                           if a.spec.get("cancel_at") is not None]
+                    if cut:
+                        tick = max(1, min([tick] + cut))
+                try:
+                    batch.step(tick)
+                    batch.sync()
+                except mithra.MithraError as e:
+                    # the batch's state is unknown: fail its jobs, start afresh
+                    now = self._now(t0)
+                    for js in active:
+                        self._drop(js, batch, now, str(e))
+                        failed.append(js)
+                    active.clear()
+                    batch.close()
+                    batch = self._batch()
+                    continue
                 self.steps_done += tick
                 now = self._now(t0)
                 for js in active:
@@ -148,9 +214,11 @@ class Server:
                     pass
             batch.close()
         wall = time.perf_counter() - t0
-        return self.stats(done, queue + active + list(pending), wall)
+        return self.stats(done, queue + active + list(pending), wall, failed)
 
-    def stats(self, done: list[JobState], left: list[JobState], wall: float) -> dict:
+    def stats(self, done: list[JobState], left: list[JobState], wall: float,
+              failed: list[JobState] | None = None) -> dict:
+        failed = failed or []
         lat = np.array([js.t_done - js.arrival for js in done]) if done else np.array([])
         cells = sum(js.spec["grid"]["nx"] * js.spec["grid"]["ny"] * js.spec["grid"]["nz"] *
                     js.spec["steps"] for js in done)
@@ -161,4 +229,7 @@ class Server:
             p99_s=float(np.percentile(lat, 99)) if lat.size else None,
             cell_updates_per_s=cells / wall if wall > 0 else 0.0,
             max_queue=max((q for _, q in self.queue_depth), default=0),
-            done=done)
+            rejected=sum(js.status == "rejected" for js in failed),
+            failed=sum(js.status == "failed" for js in failed),
+            cancelled=sum(js.status == "cancelled" for js in failed),
+            done=done, not_done=failed)

@@ -101,6 +101,70 @@ def test_slot_limit():
 
 
 def test_oversized_job_rejected():
-    jobs = make_jobs([0], [10], [128])
-    with pytest.raises(ValueError):
-        run(jobs, budget=1000)
+    # a job larger than the whole budget is rejected alone; the others run
+    jobs = make_jobs([0, 0], [10, 10], [128, 32])
+    st, b = run(jobs, budget=64 * 1000)
+    assert st["rejected"] == 1 and st["completed"] == 1
+    assert [js.spec["jid"] for js in st["done"]] == [1]
+    assert st["not_done"][0].status == "rejected" and "budget" in st["not_done"][0].error
+
+
+class OOMSim(FakeSim):
+    """Creation fails like a device allocation failure for grids of nx 48."""
+
+    def __init__(self, grid, und, bunch, precision=1):
+        if grid["nx"] == 48:
+            from paper_1612_03310_gb300 import mithra
+            raise mithra.MithraError(3, "device allocation failed")
+        super().__init__(grid, und, bunch, precision)
+
+
+def test_allocation_failure_fails_that_job_only():
+    jobs = make_jobs([0, 0, 5], [20, 20, 20], [32, 48, 32])
+    b = FakeBatch()
+    srv = serve.Server(10 ** 9, max_slots=8, tick_steps=16, clock="steps",
+                       sim_factory=OOMSim, batch_factory=lambda: b,
+                       footprint_fn=lambda g, n, p: g["nx"] * 1000)
+    st = srv.run(jobs)
+    assert st["completed"] == 2 and st["failed"] == 1
+    bad = st["not_done"][0]
+    assert bad.spec["jid"] == 1 and "allocation" in bad.error
+    assert srv.used == 0                          # nothing leaked
+
+
+def test_cancelled_job_keeps_its_partial_record():
+    jobs = make_jobs([0, 0], [100, 40], [32, 32])
+    jobs[0]["cancel_at"] = 25
+    st, b = run(jobs, budget=10 ** 9)
+    assert st["completed"] == 1 and st["cancelled"] == 1
+    c = st["not_done"][0]
+    assert c.status == "cancelled" and c.power.shape[0] == 25 and c.t_done == 25
+    assert st["done"][0].power.shape[0] == 40
+
+
+class FailingBatch(FakeBatch):
+    """Its third step returns an error, like a device error the library reports."""
+
+    def step(self, n):
+        super().step(n)
+        if len(self.ticks) == 3:
+            from paper_1612_03310_gb300 import mithra
+            raise mithra.MithraError(4, "CUDA error in a step")
+
+
+def test_step_error_fails_the_batch_and_the_server_goes_on():
+    jobs = make_jobs([0, 0, 200], [100, 100, 30], [32, 32, 32])
+    made = []
+
+    def factory():
+        made.append(FailingBatch() if not made else FakeBatch())
+        return made[-1]
+
+    srv = serve.Server(10 ** 9, max_slots=8, tick_steps=16, clock="steps",
+                       sim_factory=FakeSim, batch_factory=factory,
+                       footprint_fn=lambda g, n, p: g["nx"] * 1000)
+    st = srv.run(jobs)
+    assert st["failed"] == 2 and st["completed"] == 1
+    assert all("CUDA error" in js.error for js in st["not_done"])
+    assert len(made) == 2 and st["done"][0].spec["jid"] == 2
+    assert srv.used == 0
