@@ -68,6 +68,7 @@ class Server:
         self._batch = batch_factory or mithra.Batch
         self._fp = footprint_fn or mithra.footprint
         self.used = 0
+        self.used_peak = 0
         self.steps_done = 0
         self.queue_depth: list[tuple[float, int]] = []
 
@@ -92,6 +93,7 @@ class Server:
         js.remaining = spec["steps"]
         js.t_admit = now
         self.used += js.footprint
+        self.used_peak = max(self.used_peak, self.used)
 
     def _retire(self, js: JobState, batch, now: float, status: str = "done"):
         js.power = js.sim.read_power()
@@ -229,6 +231,7 @@ class Server:
             p99_s=float(np.percentile(lat, 99)) if lat.size else None,
             cell_updates_per_s=cells / wall if wall > 0 else 0.0,
             max_queue=max((q for _, q in self.queue_depth), default=0),
+            hbm_in_use_peak=self.used_peak, hbm_budget=self.budget,
             rejected=sum(js.status == "rejected" for js in failed),
             failed=sum(js.status == "failed" for js in failed),
             cancelled=sum(js.status == "cancelled" for js in failed),

@@ -88,6 +88,7 @@ def test_admission_by_footprint_first_fit():
     # budget fits one 64-job or two 32-jobs at a time
     jobs = make_jobs([0, 0, 0], [20, 20, 20], [64, 32, 32])
     st, b = run(jobs, budget=64 * 1000)
+    assert st["hbm_in_use_peak"] == 64 * 1000 == st["hbm_budget"]
     done = {js.spec["jid"]: js for js in st["done"]}
     assert done[0].t_admit == 0
     assert done[1].t_admit >= done[0].t_done and done[2].t_admit >= done[0].t_done
