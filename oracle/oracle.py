@@ -60,10 +60,12 @@ class _Und(C.Structure):
                 ("a0", C.c_double), ("lambda_l", C.c_double), ("pol_x", C.c_double),
                 ("pol_y", C.c_double), ("z0_lab", C.c_double), ("offset", C.c_double),
                 ("variance", C.c_double), ("cep", C.c_double), ("direction", C.c_int32),
-                ("signal", C.c_int32)]
+                ("signal", C.c_int32), ("beam", C.c_int32), ("x0_lab", C.c_double),
+                ("y0_lab", C.c_double), ("w_par", C.c_double), ("w_perp", C.c_double)]
 
 
 SIGNALS = {"neumann": 0, "gaussian": 1, "secant-hyperbolic": 2, "flat-top": 3}
+BEAMS = {"plane-wave": 0, "gaussian-beam": 1}
 
 
 _lib = None
@@ -99,7 +101,10 @@ def lib():
                                                  dp, dp]
         _lib.orc_spectrum_density.argtypes = [C.POINTER(_Grid), C.c_int32, dp, dp]
         _lib.orc_seed_correction.argtypes = [C.POINTER(_Grid), C.POINTER(_Und), C.c_double, dp]
-        _lib.orc_incident_potential.argtypes = [C.POINTER(_Und), C.c_double, C.c_double, dp]
+        _lib.orc_incident_potential.argtypes = [C.POINTER(_Und), C.c_double, C.c_double,
+                                                C.c_double, C.c_double, dp]
+        _lib.orc_incident_potential_many.argtypes = [C.POINTER(_Und), C.c_int64, dp, dp, dp,
+                                                     dp, dp]
     return _lib
 
 
@@ -128,14 +133,19 @@ def make_grid(g: dict) -> _Grid:
 def make_und(u: dict | None) -> _Und:
     """Static undulator keys: gamma0, lambda_u, K, z_ent_lab, length_lab,
     fringe.  Optical (type "optical"): gamma0, a0, lambda_l, polarization
-    (px, py), z0_lab, offset, variance, cep, direction (-1 or +1), signal."""
+    (px, py), z0_lab, offset, variance, cep, direction (-1 or +1), signal;
+    a seed also beam ("plane-wave" or "gaussian-beam") and, for the Gaussian
+    beam, x0_lab, y0_lab and rayleigh_radius (w_par, w_perp)."""
     if u is None:
         return _Und(1.0e3, 1.0, 0.0, 0.0, 0.0, 0)
     if u.get("type", "static") == "optical":
         px, py = u.get("polarization", (0.0, 1.0))
+        wp, wq = u.get("rayleigh_radius", (0.0, 0.0))
         return _Und(u["gamma0"], 1.0, 0.0, 0.0, 0.0, 0, 1, u["a0"], u["lambda_l"], px, py,
                     u.get("z0_lab", 0.0), u["offset"], u["variance"], u.get("cep", 0.0),
-                    int(u.get("direction", -1)), SIGNALS[u.get("signal", "flat-top")])
+                    int(u.get("direction", -1)), SIGNALS[u.get("signal", "flat-top")],
+                    BEAMS[u.get("beam", "plane-wave")], u.get("x0_lab", 0.0),
+                    u.get("y0_lab", 0.0), wp, wq)
     return _Und(u["gamma0"], u["lambda_u"], u["K"], u.get("z_ent_lab", 0.0),
                 u.get("length_lab", 0.0), int(u.get("fringe", 1)))
 
@@ -218,9 +228,14 @@ def spectrum_density(g: dict, n_freq: int, acc: np.ndarray) -> np.ndarray:
     return out
 
 
-def incident_potential(u: dict, z: float, t: float) -> np.ndarray:
-    out = np.zeros(2)
-    lib().orc_incident_potential(C.byref(make_und(dict(u, type="optical"))), z, t, _p(out))
+def incident_potential(u: dict, z, t, x=0.0, y=0.0) -> np.ndarray:
+    """(A_x, A_y) of a seed at rest-frame points; z, t, x, y broadcast
+    together, the result has their shape plus a last axis of 2."""
+    z, t, x, y = (np.array(a, dtype=np.float64, order="C")
+                  for a in np.broadcast_arrays(z, t, x, y))
+    out = np.zeros(z.shape + (2,))
+    lib().orc_incident_potential_many(C.byref(make_und(dict(u, type="optical"))), z.size,
+                                      _p(x), _p(y), _p(z), _p(t), _p(out))
     return out
 
 
@@ -305,8 +320,9 @@ class OracleSim:
         return out
 
     def set_seed(self, seed: dict | None):
-        """Plane-wave seed injected through the TF/SF planes (orc_seed_correction);
-        the same keys as an optical undulator; None switches it off."""
+        """Seed injected through the TF/SF planes (orc_seed_correction): the
+        keys of an optical undulator plus beam, x0_lab, y0_lab and
+        rayleigh_radius; None switches it off."""
         self.seed = None if seed is None else make_und(dict(seed, type="optical"))
 
     def bunch_stats(self, k_b: float) -> np.ndarray:

@@ -303,10 +303,11 @@ static double signal_derivative(const orc_undulator* u, double x) {
     }
 }
 
-static double signal_value(const orc_undulator* u, double x) {
+/* the signal with an extra carrier phase ph (the Gaussian beam's Gouy phase) */
+static double signal_value(const orc_undulator* u, double x, double ph) {
     const double w = 2.0 * ORC_PI * ORC_C / u->lambda_l;
     const double tv = u->variance / ORC_C;
-    const double C = cos(w * x + u->cep);
+    const double C = cos(w * x + u->cep + ph);
     const double a = 2.0 * log(2.0) / (tv * tv);
     switch (u->signal) {
         case 0: return -4.0 * log(2.0) * (x / tv) * C * exp(-a * x * x);
@@ -324,11 +325,42 @@ static double wave_tau(const orc_undulator* u, double z, double t) {
     return tl - (double)u->direction * (zl - u->z0_lab) / ORC_C;
 }
 
-void orc_incident_potential(const orc_undulator* u, double z, double t, double out[2]) {
+void orc_incident_potential(const orc_undulator* u, double x, double y, double z, double t,
+                            double out[2]) {
     const double A0 = u->a0 * ORC_ME * ORC_C / ORC_E;
-    const double s = signal_value(u, wave_tau(u, z, t) - u->offset / ORC_C);
+    const double tau = wave_tau(u, z, t);
+    double s;
+    if (u->beam == 1) {
+        const double g0 = u->gamma0;
+        const double b0 = sqrt(1.0 - 1.0 / (g0 * g0));
+        const double zl = g0 * (z + b0 * ORC_C * t);
+        const double zeta = (double)u->direction * (zl - u->z0_lab);
+        const double pn = sqrt(u->pol_x * u->pol_x + u->pol_y * u->pol_y);
+        const double px = u->pol_x / pn, py = u->pol_y / pn;
+        const double X = x - u->x0_lab, Y = y - u->y0_lab;
+        const double off[2] = {px * X + py * Y, -py * X + px * Y};  /* xi, eta */
+        const double w0[2] = {u->w_par, u->w_perp};
+        double amp = 1.0, delay = 0.0, gouy = 0.0;
+        for (int a = 0; a < 2; ++a) {
+            const double zr = ORC_PI * w0[a] * w0[a] / u->lambda_l;
+            const double w = w0[a] * sqrt(1.0 + (zeta / zr) * (zeta / zr));
+            const double invR = zeta / (zeta * zeta + zr * zr);
+            amp *= sqrt(w0[a] / w) * exp(-off[a] * off[a] / (w * w));
+            delay += off[a] * off[a] * invR / (2.0 * ORC_C);
+            gouy += 0.5 * atan(zeta / zr);
+        }
+        s = amp * signal_value(u, tau - delay - u->offset / ORC_C, gouy);
+    } else {
+        s = signal_value(u, tau - u->offset / ORC_C, 0.0);
+    }
     out[0] = u->pol_x * A0 * s;
     out[1] = u->pol_y * A0 * s;
+}
+
+void orc_incident_potential_many(const orc_undulator* u, int64_t n, const double* x,
+                                 const double* y, const double* z, const double* t,
+                                 double* out) {
+    for (int64_t q = 0; q < n; ++q) orc_incident_potential(u, x[q], y[q], z[q], t[q], out + 2 * q);
 }
 
 void orc_seed_correction(const orc_grid* g, const orc_undulator* seed, double t_n,
@@ -338,23 +370,37 @@ void orc_seed_correction(const orc_grid* g, const orc_undulator* seed, double t_
     const double A = co[0], a2 = co[2], a4 = co[3], a6 = co[4];
     const int64_t n = ncell(g);
     const int ks = 2, kt = 3;
-    double fs[2], ft[2];
-    /* the incident potential on the two planes (uniform in x and y) */
-    orc_incident_potential(seed, g->z0 + ks * g->dz, t_n, fs);
-    orc_incident_potential(seed, g->z0 + kt * g->dz, t_n, ft);
+    const int64_t nxy = (int64_t)g->nx * g->ny;
+    /* the incident potential at every vertex of the two planes */
+    double* fs = (double*)malloc(sizeof(double) * 2 * nxy);
+    double* ft = (double*)malloc(sizeof(double) * 2 * nxy);
+    for (int j = 0; j < g->ny; ++j) {
+        for (int i = 0; i < g->nx; ++i) {
+            const double x = g->x0 + i * g->dx, y = g->y0 + j * g->dy;
+            const int64_t v = (int64_t)j * g->nx + i;
+            orc_incident_potential(seed, x, y, g->z0 + ks * g->dz, t_n, fs + 2 * v);
+            orc_incident_potential(seed, x, y, g->z0 + kt * g->dz, t_n, ft + 2 * v);
+        }
+    }
+#define F(f, i, j, c) (f)[2 * ((int64_t)(j) * g->nx + (i)) + (c)]
     for (int c = 0; c < 2; ++c) {
         double* pn = next + c * n;
         for (int j = 1; j < g->ny - 1; ++j) {
             for (int i = 1; i < g->nx - 1; ++i) {
                 /* scattered-field plane: its k+1 neighbours hold the total field */
-                pn[ix(g, i, j, ks)] -= A * (a2 * ft[c] + a2 * ft[c] + a4 * ft[c] + a4 * ft[c])
-                                     + a6 * ft[c];
+                pn[ix(g, i, j, ks)] -= A * (a2 * F(ft, i + 1, j, c) + a2 * F(ft, i - 1, j, c)
+                                            + a4 * F(ft, i, j + 1, c) + a4 * F(ft, i, j - 1, c))
+                                     + a6 * F(ft, i, j, c);
                 /* total-field plane: its k-1 neighbours hold the scattered field */
-                pn[ix(g, i, j, kt)] += A * (a2 * fs[c] + a2 * fs[c] + a4 * fs[c] + a4 * fs[c])
-                                     + a6 * fs[c];
+                pn[ix(g, i, j, kt)] += A * (a2 * F(fs, i + 1, j, c) + a2 * F(fs, i - 1, j, c)
+                                            + a4 * F(fs, i, j + 1, c) + a4 * F(fs, i, j - 1, c))
+                                     + a6 * F(fs, i, j, c);
             }
         }
     }
+#undef F
+    free(fs);
+    free(ft);
 }
 
 static void optical_field(const orc_undulator* u, double z, double t, double E[3], double B[3]) {

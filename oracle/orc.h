@@ -61,6 +61,14 @@ typedef struct {
     int32_t signal;         /* 0 modulated Neumann, 1 modulated Gaussian,
                                2 modulated hyperbolic secant, 3 sinusoidal pulse
                                (flat-top) */
+    /* seed only (input group field-initialization, type): 0 plane wave,
+     * 1 Gaussian beam focused at (x0_lab, y0_lab, z0_lab) with waist radii
+     * w_par along the polarization and w_perp across it (the
+     * rayleigh-radius-parallel / -perpendicular parameters, read as the 1/e
+     * radius of the field at the focus) */
+    int32_t beam;
+    double x0_lab, y0_lab;
+    double w_par, w_perp;
 } orc_undulator;
 
 /* Coefficients of the update equation (Eq. updateEquation):
@@ -75,9 +83,9 @@ int orc_coefficients(const orc_grid* g, double out[6]);
 void orc_potential_step(const orc_grid* g, const double* prev, const double* cur,
                         const double* src, double* next);
 
-/* Seed field (Sec. "Seed Field"): a plane wave along z given in the lab
- * frame like the optical undulator (the same parameters, orc_undulator with
- * type 1), injected by the total-field/scattered-field technique: the
+/* Seed field (Sec. "Seed Field"): a plane wave or Gaussian beam along z
+ * given in the lab frame like the optical undulator (the same parameters,
+ * orc_undulator with type 1), injected by the total-field/scattered-field technique: the
  * vertex plane k = 2 is the last of the scattered-field region (next to the
  * z = z_min boundary), k = 3 the first of the total-field region.  After the
  * update of level n+1 the stencil's coupling across the two planes is
@@ -86,13 +94,36 @@ void orc_potential_step(const orc_grid* g, const double* prev, const double* cur
  *   k = 2:  psi' = psi - [A (a2 f_{i+1,k+1} + a2 f_{i-1,k+1} + a4 f_{j+1,k+1}
  *                           + a4 f_{j-1,k+1}) + a6 f_{k+1}]
  *   k = 3:  psi' = psi + [A (a2 f_{i+1,k-1} + ...) + a6 f_{k-1}],
- * over interior (i, j), with f^n = p A0 s(tau) at the vertex and t_n. */
+ * over interior (i, j), with f^n = orc_incident_potential at the neighbour
+ * vertex and t_n (a plane wave is uniform in x and y; a Gaussian beam is
+ * not, so each neighbour takes its own value). */
 void orc_seed_correction(const orc_grid* g, const orc_undulator* seed, double t_n,
                          double* next);
 
-/* The incident vector potential of a plane-wave seed or optical undulator at
- * rest-frame (z, t): out = A0 s(tau) times the polarization (x, y). */
-void orc_incident_potential(const orc_undulator* u, double z, double t, double out[2]);
+/* The incident vector potential of a seed or optical undulator at the
+ * rest-frame point (x, y, z, t), out = (A_x, A_y).  Plane wave: A0 s(tau)
+ * times the polarization.  Gaussian beam (beam = 1; the paper names the
+ * type and its parameters but prints no formula, so this is the textbook
+ * paraxial beam, one factor per transverse axis): with the lab point
+ * (x, y, z', t') of the boost, zeta = d (z' - z0_lab) the distance past the
+ * focus, xi and eta the offsets from (x0_lab, y0_lab) along p and along
+ * z x p, and for each axis a with waist w_a: Rayleigh length
+ * z_a = pi w_a^2 / lambda_l, width w_a(zeta) = w_a sqrt(1 + (zeta/z_a)^2),
+ * wavefront curvature 1/R_a = zeta / (zeta^2 + z_a^2), Gouy phase
+ * psi_a = atan(zeta / z_a):
+ *   A = p A0 sqrt(w_xi/w_xi(zeta)) sqrt(w_eta/w_eta(zeta))
+ *         exp(-xi^2/w_xi(zeta)^2 - eta^2/w_eta(zeta)^2) s~(x),
+ *   x = tau - (xi^2/R_xi + eta^2/R_eta) / (2c) - offset/c,
+ * s~ the signal with the carrier phase cep + (psi_xi + psi_eta)/2.  The lab
+ * beam has no phi and no A_z (paraxial), so the boost leaves A_x, A_y as
+ * they are. */
+void orc_incident_potential(const orc_undulator* u, double x, double y, double z, double t,
+                            double out[2]);
+
+/* The same at n points (arrays of n doubles each; out holds n pairs). */
+void orc_incident_potential_many(const orc_undulator* u, int64_t n, const double* x,
+                                 const double* y, const double* z, const double* t,
+                                 double* out);
 
 /* E and B at t = (n+1/2) dt at the vertices [1, n-2]^3 from A^n, A^{n+1},
  * phi^n (Sec. "Field Evaluation"); all other vertices are set to zero. */

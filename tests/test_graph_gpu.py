@@ -32,10 +32,15 @@ def rel_l2(a, b):
     return float(np.linalg.norm(a - b) / nb) if nb else float(np.linalg.norm(a))
 
 
-def pair(M, prec, seed=3):
-    g = dict(inputs.random_grid(seed, 30, 26, 40), boundary=1)
+OPTICAL = dict(type="optical", gamma0=UND["gamma0"], a0=UND["K"], lambda_l=2 * UND["lambda_u"],
+               polarization=(0.6, 0.8), z0_lab=0.0, offset=0.0, variance=2 * UND["lambda_u"],
+               cep=0.3, direction=-1, signal="gaussian")
+
+
+def pair(M, prec, seed=3, n_sub=1, und=None, boundary=1):
+    g = dict(inputs.random_grid(seed, 30, 26, 40, n_sub=n_sub), boundary=boundary)
     P = inputs.random_particles(seed + 1, g, 3000, u_scale=0.3)
-    und = dict(UND, z_ent_lab=0.0)
+    und = und or dict(UND, z_ent_lab=0.0)
     return (M.Simulation(g, und, P, precision=prec), M.Simulation(g, und, P, precision=prec))
 
 
@@ -80,3 +85,26 @@ def test_settings_changed_between_runs_reach_the_replay(M):
         assert a.time()[0] == b.time()[0] == 17
         for nm in ("Ex", "Bz", "rho"):
             assert rel_l2(a.copy_field(nm), b.copy_field(nm)) <= 1e-5, nm
+
+
+@pytest.mark.parametrize("prec_name,n_sub,optical,boundary", [
+    ("P32_C", 3, False, 1), ("P32_U64", 2, True, 2), ("P64", 3, True, 2)])
+def test_replay_with_sub_steps_and_both_undulators(M, prec_name, n_sub, optical, boundary):
+    # sub-cycled particle steps, the compensated levels, the optical
+    # undulator's time-dependent field and both Mur orders in the replay
+    prec = getattr(M, prec_name)
+    tol = 1e-12 if prec == M.P64 else 1e-5
+    a, b = pair(M, prec, seed=11, n_sub=n_sub, und=OPTICAL if optical else None,
+                boundary=boundary)
+    with a, b:
+        for n in (2, 5, 6):
+            a.step(n)
+            for _ in range(n):
+                b.step(1)
+        assert a.time()[0] == b.time()[0] == 13
+        for nm in FIELDS:
+            assert rel_l2(a.copy_field(nm), b.copy_field(nm)) <= tol, nm
+        qa, qb = a.copy_particles(), b.copy_particles()
+        assert np.array_equal(qa["lost"], qb["lost"])
+        for k in ("ux", "uy", "uz"):
+            assert rel_l2(qa[k], qb[k]) <= tol, k
