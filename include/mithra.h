@@ -120,7 +120,9 @@ typedef struct {
  *   signal 3 sinusoidal pulse     the Gaussian for x <= 0, C for x > 0
  *                                 (flat-top)
  * E' = -dA'/dt', B' = curl A'; direction -1 travels towards -z (the
- * counter-propagating laser of the paper's examples), +1 towards +z. */
+ * counter-propagating laser of the paper's examples), +1 towards +z.  The
+ * beam-type gaussian-beam optical undulator is not built (beam must be 0);
+ * a seed may be a Gaussian beam (mithra_set_seed). */
 typedef struct {
     double gamma0;
     double lambda_u;
@@ -138,6 +140,10 @@ typedef struct {
     double cep;           /* optical: carrier envelope phase [rad] */
     int32_t direction;    /* optical: -1 or +1 */
     int32_t signal;       /* optical: 0..3 */
+    int32_t beam;         /* seed only: 0 plane wave, 1 Gaussian beam (an
+                             optical undulator must be 0) */
+    double x0_lab, y0_lab;/* Gaussian beam: transverse position of the focus [m] */
+    double w_par, w_perp; /* Gaussian beam: waist radii along and across p [m] */
 } mithra_undulator;
 
 /* Macroparticles, host arrays of n doubles in the rest frame at t = t0:
@@ -257,15 +263,32 @@ mithra_status mithra_kernel_times(mithra_sim* sim, double* ms, int64_t* launches
                                   int32_t max_kernels, int32_t* n_kernels);
 const char* mithra_kernel_name(int32_t kernel);
 
-/* Seed field (Sec. "Seed Field"), injected by the total-field/scattered-
- * field technique: wave describes a plane wave along z in the lab frame with
- * the parameters of an optical undulator (type must be 1; its gamma0 is not
- * used, the simulation's frame is).  Vertex plane k = 2 is the last of the
- * scattered-field region next to the z = z_min boundary, k = 3 the first of
- * the total-field region; after each update of the potentials the coupling
- * across the two planes is corrected with the incident vector potential of
- * level n, so that the seed enters the total-field region.  NULL switches
- * the seed off.  Needs nz >= 8; MITHRA_EBUSY while the sim is in a batch. */
+/* Seed field (Sec. "Seed Field"; input group field-initialization),
+ * injected by the total-field/scattered-field technique: wave describes a
+ * wave along z in the lab frame with the parameters of an optical undulator
+ * (type must be 1; its gamma0 is not used, the simulation's frame is).
+ * beam 0: the plane wave A' = p A0 s(tau).  beam 1: a Gaussian beam
+ * focused at (x0_lab, y0_lab, z0_lab) with waist radii w_par along p and
+ * w_perp across it (the rayleigh-radius-parallel / -perpendicular
+ * parameters, read as the 1/e radius of the field at the focus; the paper
+ * prints no formula, this is the paraxial beam): with zeta = direction
+ * (z' - z0_lab), xi and eta the lab offsets from the focus along p and
+ * along z x p, and per axis z_a = pi w_a^2 / lambda_l,
+ * w_a(zeta) = w_a sqrt(1 + zeta^2/z_a^2), 1/R_a = zeta / (zeta^2 + z_a^2),
+ * psi_a = atan(zeta / z_a),
+ *   A' = p A0 sqrt(w_xi w_eta / (w_xi(zeta) w_eta(zeta)))
+ *          exp(-xi^2/w_xi(zeta)^2 - eta^2/w_eta(zeta)^2) s~(x),
+ *   x = tau - (xi^2/R_xi + eta^2/R_eta)/(2c) - offset/c,
+ * s~ the signal with carrier phase cep + (psi_xi + psi_eta)/2; no phi and
+ * no A_z, so the boost leaves A_x and A_y as they are.  Vertex plane k = 2
+ * is the last of the scattered-field region next to the z = z_min boundary,
+ * k = 3 the first of the total-field region; after each update of the
+ * potentials the coupling of each vertex of one plane to its neighbours on
+ * the other (the z neighbour and, through the NSFD terms, its x and y
+ * neighbours) is corrected with the incident vector potential of level n at
+ * those neighbours, so that the seed enters the total-field region.  NULL
+ * switches the seed off.  Needs nz >= 8; MITHRA_EINVAL for a bad wave;
+ * MITHRA_EBUSY while the sim is in a batch. */
 mithra_status mithra_set_seed(mithra_sim* sim, const mithra_undulator* wave);
 
 /* Bunch sampling (the input group "bunch-sampling": mean position, mean

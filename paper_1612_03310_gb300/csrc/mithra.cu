@@ -509,7 +509,16 @@ mithra_status launch_step(mithra_sim* s) {
       else
         k_potential_step<false, T><<<grd, blk, 0, s->stream>>>(sp, P0, L0, P1, L1, Dn, S);
     }
-    if (s->seed.on) {
+    if (s->seed.on && s->seed.beam) {
+      dim3 blk(kSeedTile, kSeedTile, 1);
+      dim3 grd((s->g.nx - 2 + kSeedTile - 1) / kSeedTile,
+               (s->g.ny - 2 + kSeedTile - 1) / kSeedTile, 1);
+      if (L0)
+        k_seed_tfsf_beam<true, T><<<grd, blk, 0, s->stream>>>(sp, s->seed, s->dstate, P1, L1, Dn);
+      else
+        k_seed_tfsf_beam<false, T><<<grd, blk, 0, s->stream>>>(sp, s->seed, s->dstate, P1, L1,
+                                                                Dn);
+    } else if (s->seed.on) {
       dim3 blk(32, 8, 1);
       dim3 grd((s->g.nx - 2 + 31) / 32, (s->g.ny - 2 + 7) / 8, 2);
       if (L0)
@@ -848,6 +857,8 @@ mithra_status mithra_create(const mithra_grid* grid, const mithra_undulator* und
       return fail(nullptr, MITHRA_EINVAL,
                   "optical undulator needs lambda_l > 0, variance > 0, a polarization, "
                   "direction +-1 and signal 0..3");
+    if (und->beam != 0)
+      return fail(nullptr, MITHRA_EINVAL, "the optical undulator is a plane wave (beam 0)");
   } else if (und->type != 0 || !(und->lambda_u > 0.0)) {
     return fail(nullptr, MITHRA_EINVAL, "undulator type must be 0 (static, lambda_u > 0) or 1");
   }
@@ -1159,6 +1170,12 @@ mithra_status mithra_set_seed(mithra_sim* s, const mithra_undulator* w) {
     return fail(s, MITHRA_EINVAL,
                 "seed needs type 1, lambda_l > 0, variance > 0, a polarization, direction +-1 "
                 "and signal 0..3");
+  if (w->beam != 0 &&
+      (w->beam != 1 || !(w->w_par > 0.0) || !(w->w_perp > 0.0) || !std::isfinite(w->w_par) ||
+       !std::isfinite(w->w_perp) || !std::isfinite(w->x0_lab) || !std::isfinite(w->y0_lab)))
+    return fail(s, MITHRA_EINVAL,
+                "seed beam must be 0 (plane wave) or 1 (Gaussian beam with finite waists > 0 "
+                "and a finite focus)");
   if (s->g.nz < 8 || s->g.nx < 4 || s->g.ny < 4)
     return fail(s, MITHRA_EINVAL, "seeding needs nz >= 8 (planes 2 and 3 inside)");
   const double g0 = s->u.gamma0;  // the simulation's frame
@@ -1184,6 +1201,37 @@ mithra_status mithra_set_seed(mithra_sim* s, const mithra_undulator* w) {
   q.z3 = s->g.z0 + 3.0 * s->g.dz;
   q.t0 = s->t0;
   q.dt = s->g.dt;
+  if (w->beam == 1) {
+    q.beam = 1;
+    q.px = w->pol_x / pn;
+    q.py = w->pol_y / pn;
+    q.xf = w->x0_lab;
+    q.yf = w->y0_lab;
+    q.zeta_t = d * g0 * b0 * kC;  // zeta = d (z' - z_focus), z' = g0 (z + b0 c t)
+    q.zeta_z = d * g0;
+    q.zeta_c = -d * w->z0_lab;
+    const double zp = kPi * w->w_par * w->w_par / w->lambda_l;
+    const double zq = kPi * w->w_perp * w->w_perp / w->lambda_l;
+    q.zr_p = zp;
+    q.zr_q = zq;
+    q.inv_w2p = 1.0 / (w->w_par * w->w_par);
+    q.inv_w2q = 1.0 / (w->w_perp * w->w_perp);
+    q.gx0 = s->g.x0;
+    q.gy0 = s->g.y0;
+    q.gdx = s->g.dx;
+    q.gdy = s->g.dy;
+    // the coupling of a vertex to the other plane (NSFD terms of the update)
+    const double cdt = kC * s->g.dt;
+    const double rx2 = (cdt / s->g.dx) * (cdt / s->g.dx), ry2 = (cdt / s->g.dy) * (cdt / s->g.dy);
+    double A = 0.0;
+    if (s->g.stencil == 0) {
+      const double qx = s->g.dz / s->g.dx, qy = s->g.dz / s->g.dy;
+      A = 0.25 * (1.0 + 0.02 / (qx * qx + qy * qy));  // Eq. NSFDCoefficient
+    }
+    q.kxA = rx2 * A;
+    q.kyA = ry2 * A;
+    q.kz2 = (cdt / s->g.dz) * (cdt / s->g.dz);
+  }
   MCHECK(s, cudaStreamSynchronize(s->stream));
   s->seed = q;
   return MITHRA_OK;

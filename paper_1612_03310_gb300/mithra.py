@@ -55,10 +55,13 @@ class Undulator(C.Structure):
                 ("type", C.c_int32), ("a0", C.c_double), ("lambda_l", C.c_double),
                 ("pol_x", C.c_double), ("pol_y", C.c_double), ("z0_lab", C.c_double),
                 ("offset", C.c_double), ("variance", C.c_double), ("cep", C.c_double),
-                ("direction", C.c_int32), ("signal", C.c_int32)]
+                ("direction", C.c_int32), ("signal", C.c_int32), ("beam", C.c_int32),
+                ("x0_lab", C.c_double), ("y0_lab", C.c_double), ("w_par", C.c_double),
+                ("w_perp", C.c_double)]
 
 
 SIGNALS = {"neumann": 0, "gaussian": 1, "secant-hyperbolic": 2, "flat-top": 3}
+BEAMS = {"plane-wave": 0, "gaussian-beam": 1}
 
 
 class Tuning(C.Structure):
@@ -177,14 +180,19 @@ def normalized_wavelengths(lambda_r: float, f_min: float, f_max: float, df: floa
 def make_undulator(u: dict | None) -> Undulator:
     """Static: gamma0, lambda_u, K, z_ent_lab, length_lab, fringe.  Optical
     (type "optical"): gamma0, a0, lambda_l, polarization (px, py), z0_lab,
-    offset, variance, cep, direction (-1 or +1), signal (a SIGNALS name)."""
+    offset, variance, cep, direction (-1 or +1), signal (a SIGNALS name);
+    a seed also beam (a BEAMS name) and, for the Gaussian beam, x0_lab,
+    y0_lab and rayleigh_radius (waist along, across the polarization)."""
     if u is None:
         return Undulator(1.0e3, 1.0, 0.0, 0.0, 0.0, 0)
     if u.get("type", "static") == "optical":
         px, py = u.get("polarization", (0.0, 1.0))
+        wp, wq = u.get("rayleigh_radius", (0.0, 0.0))
         return Undulator(u["gamma0"], 1.0, 0.0, 0.0, 0.0, 0, 1, u["a0"], u["lambda_l"], px, py,
                          u.get("z0_lab", 0.0), u["offset"], u["variance"], u.get("cep", 0.0),
-                         int(u.get("direction", -1)), SIGNALS[u.get("signal", "flat-top")])
+                         int(u.get("direction", -1)), SIGNALS[u.get("signal", "flat-top")],
+                         BEAMS[u.get("beam", "plane-wave")], u.get("x0_lab", 0.0),
+                         u.get("y0_lab", 0.0), wp, wq)
     return Undulator(u["gamma0"], u["lambda_u"], u["K"], u.get("z_ent_lab", 0.0),
                      u.get("length_lab", 0.0), int(u.get("fringe", 1)))
 
@@ -318,8 +326,9 @@ class Simulation:
         return out
 
     def set_seed(self, seed: dict | None) -> None:
-        """mithra_set_seed: a plane-wave seed with an optical undulator's keys
-        (type is implied), or None to switch it off."""
+        """mithra_set_seed: a seed with an optical undulator's keys (type is
+        implied) plus beam ("plane-wave" or "gaussian-beam"), x0_lab, y0_lab
+        and rayleigh_radius (w_par, w_perp); None switches it off."""
         if seed is None:
             _check(lib().mithra_set_seed(self.h, None), self.h)
             return
