@@ -436,8 +436,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? (kLo ? 3 : 4) : (kLo ? 1
   zloop_body<kLo, T, true>(p, cur, curlo, nxt, nxtlo, D, src, lz);
 }
 
-// Seed field (Sec. "Seed Field"): a plane wave along z given in the lab like
-// the optical undulator, injected by the total-field/scattered-field planes
+// Seed field (Sec. "Seed Field"): a plane wave (this kernel) or a Gaussian
+// beam (k_seed_tfsf_beam below) along z, given in the lab like the optical
+// undulator, injected by the total-field/scattered-field planes
 // k = 2 (last scattered-field plane, next to the z = z_min boundary) and
 // k = 3 (first total-field plane).  The update of level n+1 took, across the
 // two planes, neighbours of the other region; with the incident vector
