@@ -513,28 +513,44 @@ __global__ void __launch_bounds__(256) k_seed_tfsf(StencilP<T> p, SeedP q,
 //   g(i,j) kz2 + kxA (g(i+1,j) + g(i-1,j) - 2 g(i,j))
 //              + kyA (g(i,j+1) + g(i,j-1) - 2 g(i,j)),
 // g the incident value on the other plane (x and y neighbour differences on
-// planes k +- 1 carry the weights rx^2 A and ry^2 A).  A 16 x 16 tile of
-// columns evaluates g once per vertex of its 18 x 18 halo on both planes in
-// shared memory, then corrects its vertices on planes 2 and 3.
+// planes k +- 1 carry the weights rx^2 A and ry^2 A).  A CTA takes a 16 x 16
+// tile of columns and one plane of the pair (blockIdx.z): it evaluates g once
+// per vertex of the tile's 18 x 18 halo on the other plane in shared memory,
+// then corrects its tile on its own plane.
 constexpr int kSeedTile = 16;
 
 // Scalar of the paraxial beam at a rest-frame point: A = (ax, ay) times it.
 // Per transverse axis a (xi along p, eta across it), with
 // s_a = zeta^2 + z_a^2: amplitude (z_a^2 / s_a)^(1/4), exponent
 // -a^2 z_a^2 / (w_a^2 s_a), delay a^2 zeta / (2 c s_a), phase atan(zeta/z_a)/2.
-__device__ inline double beam_value(const SeedP& q, double x, double y, double z, double t) {
-  const double zeta = q.zeta_t * t + q.zeta_z * z + q.zeta_c;
-  const double X = x - q.xf, Y = y - q.yf;
-  const double xi = q.px * X + q.py * Y, eta = q.px * Y - q.py * X;
-  const double z2 = zeta * zeta;
+// zeta and tau depend only on the plane's z and the time, so everything but
+// the transverse terms is taken once per plane (BeamPlane).
+struct BeamPlane {
+  double zeta, tau, amp, gouy, ep, eq, isp, isq;
+};
+
+__device__ inline BeamPlane beam_plane(const SeedP& q, double z, double t) {
+  BeamPlane b;
+  b.zeta = q.zeta_t * t + q.zeta_z * z + q.zeta_c;
+  b.tau = q.tau_t * t + q.tau_z * z + q.tau_c - q.t0o;
+  const double z2 = b.zeta * b.zeta;
   const double sp = z2 + q.zr_p * q.zr_p, sq = z2 + q.zr_q * q.zr_q;
   const double fp = q.zr_p * q.zr_p / sp, fq = q.zr_q * q.zr_q / sq;
-  const double amp = sqrt(sqrt(fp * fq));
-  const double ex = xi * xi * q.inv_w2p * fp + eta * eta * q.inv_w2q * fq;
-  const double delay = (xi * xi / sp + eta * eta / sq) * zeta * (0.5 / kC);
-  const double gouy = 0.5 * (atan2(zeta, q.zr_p) + atan2(zeta, q.zr_q));
-  const double tau = q.tau_t * t + q.tau_z * z + q.tau_c;
-  return amp * exp(-ex) * seed_signal(q, tau - delay - q.t0o, gouy);
+  b.amp = sqrt(sqrt(fp * fq));
+  b.gouy = 0.5 * (atan2(b.zeta, q.zr_p) + atan2(b.zeta, q.zr_q));
+  b.ep = q.inv_w2p * fp;
+  b.eq = q.inv_w2q * fq;
+  b.isp = 1.0 / sp;
+  b.isq = 1.0 / sq;
+  return b;
+}
+
+__device__ inline double beam_value(const SeedP& q, const BeamPlane& b, double x, double y) {
+  const double X = x - q.xf, Y = y - q.yf;
+  const double xi = q.px * X + q.py * Y, eta = q.px * Y - q.py * X;
+  const double x2 = xi * xi, e2 = eta * eta;
+  const double delay = (x2 * b.isp + e2 * b.isq) * b.zeta * (0.5 / kC);
+  return b.amp * exp(-(x2 * b.ep + e2 * b.eq)) * seed_signal(q, b.tau - delay, b.gouy);
 }
 
 template <bool kLo, typename T>
@@ -543,40 +559,41 @@ __global__ void __launch_bounds__(kSeedTile * kSeedTile)
                      V4<T>* __restrict__ nxt, LoV4* __restrict__ nxtlo,
                      V4<T>* __restrict__ D) {
   constexpr int H = kSeedTile + 2;
-  __shared__ double g[2][H][H];  // [0]: plane 2, [1]: plane 3
+  __shared__ double g[H][H];  // the incident scalar on the other plane
+  __shared__ BeamPlane bp;
+  const int k = 2 + blockIdx.z;  // the corrected plane: 2 scattered, 3 total field
   const int i0 = 1 + blockIdx.x * kSeedTile, j0 = 1 + blockIdx.y * kSeedTile;
-  const double tn = q.t0 + (double)st->n * q.dt;  // time of level n
-  for (int h = threadIdx.y * kSeedTile + threadIdx.x; h < 2 * H * H; h += kSeedTile * kSeedTile) {
-    const int pl = h / (H * H), r = h % (H * H);
-    const int a = r % H, b = r / H;
+  const int tid = threadIdx.y * kSeedTile + threadIdx.x;
+  if (tid == 0) {
+    const double tn = q.t0 + (double)st->n * q.dt;  // time of level n
+    bp = beam_plane(q, k == 2 ? q.z3 : q.z2, tn);
+  }
+  __syncthreads();
+  for (int h = tid; h < H * H; h += kSeedTile * kSeedTile) {
+    const int a = h % H, b = h / H;
     const int ii = i0 - 1 + a, jj = j0 - 1 + b;  // >= 0; used only up to nx-1, ny-1
     double v = 0.0;
-    if (ii < p.nx && jj < p.ny)
-      v = beam_value(q, q.gx0 + ii * q.gdx, q.gy0 + jj * q.gdy, pl ? q.z3 : q.z2, tn);
-    g[pl][b][a] = v;
+    if (ii < p.nx && jj < p.ny) v = beam_value(q, bp, q.gx0 + ii * q.gdx, q.gy0 + jj * q.gdy);
+    g[b][a] = v;
   }
   __syncthreads();
   const int i = i0 + threadIdx.x, j = j0 + threadIdx.y;
   if (i > p.nx - 2 || j > p.ny - 2) return;
   const int a = threadIdx.x + 1, b = threadIdx.y + 1;
-#pragma unroll
-  for (int k = 2; k <= 3; ++k) {
-    const int o = (k == 2) ? 1 : 0;  // the other plane of the pair
-    const double c0 = g[o][b][a];
-    const double cpl = c0 * q.kz2 + q.kxA * ((g[o][b][a + 1] - c0) + (g[o][b][a - 1] - c0)) +
-                       q.kyA * ((g[o][b + 1][a] - c0) + (g[o][b - 1][a] - c0));
-    const double sgn = (k == 2) ? -1.0 : 1.0;
-    const V4<T> corr = v4((T)(sgn * q.ax * cpl), (T)(sgn * q.ay * cpl), (T)0, (T)0);
-    const long long c = cidx(i, j, k, p.nx, p.nxy);
-    D[c] = D[c] + corr;
-    if (kLo) {
-      V4<T> hh, ll;
-      comp_add(nxt[c], ld_lo<T>(nxtlo, c), corr, &hh, &ll);
-      nxt[c] = hh;
-      st_lo(nxtlo, c, ll);
-    } else {
-      nxt[c] = nxt[c] + corr;
-    }
+  const double c0 = g[b][a];
+  const double cpl = c0 * q.kz2 + q.kxA * ((g[b][a + 1] - c0) + (g[b][a - 1] - c0)) +
+                     q.kyA * ((g[b + 1][a] - c0) + (g[b - 1][a] - c0));
+  const double sgn = (k == 2) ? -1.0 : 1.0;
+  const V4<T> corr = v4((T)(sgn * q.ax * cpl), (T)(sgn * q.ay * cpl), (T)0, (T)0);
+  const long long c = cidx(i, j, k, p.nx, p.nxy);
+  D[c] = D[c] + corr;
+  if (kLo) {
+    V4<T> hh, ll;
+    comp_add(nxt[c], ld_lo<T>(nxtlo, c), corr, &hh, &ll);
+    nxt[c] = hh;
+    st_lo(nxtlo, c, ll);
+  } else {
+    nxt[c] = nxt[c] + corr;
   }
 }
 

@@ -512,7 +512,7 @@ mithra_status launch_step(mithra_sim* s) {
     if (s->seed.on && s->seed.beam) {
       dim3 blk(kSeedTile, kSeedTile, 1);
       dim3 grd((s->g.nx - 2 + kSeedTile - 1) / kSeedTile,
-               (s->g.ny - 2 + kSeedTile - 1) / kSeedTile, 1);
+               (s->g.ny - 2 + kSeedTile - 1) / kSeedTile, 2);
       if (L0)
         k_seed_tfsf_beam<true, T><<<grd, blk, 0, s->stream>>>(sp, s->seed, s->dstate, P1, L1, Dn);
       else
