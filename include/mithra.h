@@ -354,7 +354,9 @@ mithra_status mithra_read_spectrum(mithra_sim* sim, double* dW_domega, int64_t* 
  *     particles with E and B from global memory and deposits with global
  *     atomics, after the CTAs have taken every denser tile (0: every tile is
  *     staged).  Takes effect from the tile list of the next re-sort.
- * Variant 1 of both is the default when the driver provides TMA tensor maps. */
+ * Defaults: stencil_variant 2 with lz 16 (the fastest form of the potential
+ * update on every grid timed), push_variant 1 when the driver provides TMA
+ * tensor maps (else 0), push_ctas_per_sm 0, push_sparse_below 0. */
 typedef struct {
     int32_t stencil_variant;
     int32_t lz;

@@ -945,14 +945,17 @@ mithra_status mithra_create(const mithra_grid* grid, const mithra_undulator* und
                                   kTP) &&
                  encode_field_map(&s->tm_col_d, s->D, es, grid->nx, grid->ny, grid->nz, kMX, kMY) &&
                  encode_field_map(&s->tm_col_s, s->S, es, grid->nx, grid->ny, grid->nz, kMX, kMY);
-    s->stencil_variant = (s->have_tm && !s->PL[0]) ? 1 : 0;
+    // defaults: the register z-marching update (fastest on every grid the
+    // autotuner has timed, any precision) and the tiled push when TMA maps
+    // exist
+    s->stencil_variant = 2;
     s->push_variant = s->have_tm ? 1 : 0;
     st = with_types(precision, [&](auto t, auto u) {
       TYPES_OF(t, u);
       mithra_status r = setup_push_grid<T, U>(s);
       return r == MITHRA_OK ? setup_march<T>(s) : r;
     });
-    s->lz = default_lz(grid, s->march_resident);
+    s->lz = 16;
     if (st != MITHRA_OK) {
       std::string msg = s->err;
       return bail(st, msg);
