@@ -74,3 +74,29 @@ def test_batch_equals_alone(M, prec_name):
     for inb, alone in pairs:
         inb.close()
         alone.close()
+
+
+def test_seeded_members_equal_alone(M):
+    # a Gaussian-beam seed and a plane-wave seed set before joining the batch
+    from test_seed_gpu import beam_for, seed_for
+    shapes = [(36, 30, 44), (24, 20, 40)]
+    pairs = [make(M, 200 + 7 * k, sh, 1500, M.P32) for k, sh in enumerate(shapes)]
+    g0 = [dict(inputs.random_grid(200 + 7 * k, *sh), boundary=1) for k, sh in enumerate(shapes)]
+    seeds = [beam_for(g0[0], UND["gamma0"]), seed_for(g0[1], UND["gamma0"])]
+    for (inb, alone), s in zip(pairs, seeds):
+        inb.set_seed(s)
+        alone.set_seed(s)
+    with M.Batch() as b:
+        for inb, _ in pairs:
+            b.add(inb)
+        b.step(25)           # the pulses reach the total-field planes at step 20
+        for _, alone in pairs:
+            alone.step(25)
+        b.sync()
+        for inb, alone in pairs:
+            for nm in ("Ax", "Ay", "Ey", "Bx", "rho"):
+                assert rel_l2(inb.copy_field(nm), alone.copy_field(nm)) <= 1e-5, nm
+            assert np.abs(alone.copy_field("Ay")).max() > 1e-3 * 1.7e-3 * 0.1  # 0.1 A0
+    for inb, alone in pairs:
+        inb.close()
+        alone.close()
