@@ -371,31 +371,42 @@ mithra_status mithra_get_tuning(const mithra_sim* sim, mithra_tuning* tuning);
 /* Radiated power through vertex plane k_plane (1 <= k_plane <= nz-2), as
  * mithra_radiated_power computes it, from caller-owned device arrays, and
  * without allocating any memory.  The paper has no counterpart: this entry
- * point exists for callers that cannot call cudaMalloc, such as code running
- * while a stream is captured into a CUDA graph, an operator inside another
- * framework whose allocator owns the device memory, or a real-time loop that
- * must not wait on the allocator.
+ * point exists for callers that cannot call cudaMalloc, such as an operator
+ * inside another framework whose caching allocator owns the device memory
+ * (a second allocator beside it fragments the device and fails once that
+ * allocator has reserved the rest), or a real-time loop that must not wait
+ * on the driver's allocator.
  *   psi_newest: device array of nx*ny*nz cells of 4 values {A_x, A_y, A_z,
  *     phi} of the newest potential level (float for the MITHRA_P32 forms,
  *     their hi part when compensated; double for MITHRA_P64), cell (i,j,k) at
- *     (k*ny + j)*nx + i; increment: the same layout, newest minus previous
- *     level.  E and B are taken at the time between the two levels.
+ *     (k*ny + j)*nx + i;
+ *   lo_newest: compensated forms (MITHRA_P32_C, MITHRA_P32_U64) only: device
+ *     array of the level's lo parts, 4 bfloat16 per cell in the same order
+ *     and layout (the level is hi + lo); NULL takes the hi parts alone, which
+ *     drops the lo parts' share of E and B (a relative change of the power of
+ *     order 1e-5 on the built-in workloads).  Must be NULL for MITHRA_P32 and
+ *     MITHRA_P64 (MITHRA_EINVAL);
+ *   increment: the same layout as psi_newest, newest minus previous level.
+ *     E and B are taken at the time between the two levels.
  *   gamma0: Lorentz factor of the rest frame; *p_lab (host) receives the
  *     lab-frame power [W]; cuda_stream: stream to run on (NULL: the legacy
- *     default stream); the call waits for its own work.
+ *     default stream).  The call synchronises that stream and copies the
+ *     result to *p_lab before it returns.
  * Scratch memory is one fixed file-scope device array of 8192 + 1 doubles
  * (64 KiB per device that loads the library, held until exit): grids with
- * ny > 8192 are rejected with MITHRA_EINVAL.  The first call on a device
- * looks up that array's device address (cudaGetSymbolAddress) with the
- * device current; make that first call before any stream capture.  All calls
- * on a device share the array and it keeps the last call's partial sums;
- * every call writes the entries it reads, so none needs clearing, but calls
- * whose GPU work overlaps (unordered streams) race on it: order them.
- * Errors are reported by mithra_last_error(NULL). */
+ * ny > 8192 are rejected with MITHRA_EINVAL.  Every call looks up that
+ * array's device address (cudaGetSymbolAddress, which allocates nothing) in
+ * the caller's current context, so the address stays right after a
+ * cudaDeviceReset or in a non-primary context; the first call in a context
+ * may load the library's device code there, so make it before any stream
+ * capture.  All calls on a device share the array and it keeps the last
+ * call's partial sums; every call writes the entries it reads, so none needs
+ * clearing, but calls whose GPU work overlaps (unordered streams) race on it:
+ * order them.  Errors are reported by mithra_last_error(NULL). */
 mithra_status mithra_plane_power_noalloc(const mithra_grid* grid, double gamma0,
                                          mithra_precision precision, const void* psi_newest,
-                                         const void* increment, int32_t k_plane, double* p_lab,
-                                         void* cuda_stream);
+                                         const void* lo_newest, const void* increment,
+                                         int32_t k_plane, double* p_lab, void* cuda_stream);
 
 /* Batched stepping (the served and batched forms): a batch advances all its
  * member simulations together.  Each member keeps its own stream, buffers and

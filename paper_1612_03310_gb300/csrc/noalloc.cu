@@ -1,12 +1,12 @@
 // noalloc.cu -- radiated power through one vertex plane from caller-owned
 // device arrays, without allocating any device or pinned memory.
 //
-// Some callers cannot call cudaMalloc: code that runs while a stream is being
-// captured into a CUDA graph (allocation is not a capturable operation), a
-// custom operator inside another framework whose allocator owns all device
-// memory, or a real-time loop that must not stall on the driver's allocator.
-// For them this file keeps its scratch memory in one file-scope device array
-// of fixed size instead of allocating it.
+// Some callers cannot call cudaMalloc: a custom operator inside another
+// framework whose caching allocator owns all device memory (a second
+// allocator beside it fragments the device and can fail once that allocator
+// has reserved the rest), or a real-time loop that must not stall on the
+// driver's allocator.  For them this file keeps its scratch memory in one
+// file-scope device array of fixed size instead of allocating it.
 //
 // Scratch: kRows + 1 doubles (64 KiB).  Slots 0 .. ny-1 take one partial sum
 // per grid row j (rows 1 .. ny-2 are used), slot kRows the total.  Every call
@@ -14,10 +14,12 @@
 // array keeps the last call's values.  The array is shared by all calls on a
 // device: two calls whose work overlaps on the GPU (different streams, no
 // ordering between them) race on it and must be serialised by the caller.
+//
+// The call waits for its own work (it synchronises the stream it is given)
+// and copies the result to the caller's host variable before it returns.
 #include <cuda_runtime.h>
 
 #include <cmath>
-#include <mutex>
 #include <string>
 
 #include "mithra.h"
@@ -41,27 +43,19 @@ mithra_status na_fail(mithra_status st, const std::string& msg) {
   return st;
 }
 
-// Device address of g_scratch for each device, looked up once per device
-// with that device current (the host-side name g_scratch is only a stand-in
-// for the symbol, not a device address).
-constexpr int kMaxDevices = 64;
-double* g_scratch_ptr[kMaxDevices] = {nullptr};
-std::mutex g_scratch_mu;
-
-mithra_status scratch_of_current_device(double** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return na_fail(MITHRA_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
-  if (dev < 0 || dev >= kMaxDevices) return na_fail(MITHRA_EINVAL, "device ordinal out of range");
-  std::lock_guard<std::mutex> lock(g_scratch_mu);
-  if (!g_scratch_ptr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_scratch);
-    if (e != cudaSuccess)
-      return na_fail(MITHRA_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-    g_scratch_ptr[dev] = static_cast<double*>(p);
-  }
-  *out = g_scratch_ptr[dev];
+// Device address of g_scratch in the current context, looked up on every
+// call with the caller's device current (the host-side name g_scratch is only
+// a stand-in for the symbol, not a device address).  cudaGetSymbolAddress
+// allocates nothing; looking it up each time keeps the address right after a
+// cudaDeviceReset or in a context other than the device's primary one, where
+// the module is loaded again at another address.  The first call in a
+// context may load the module.
+mithra_status scratch_of_current_context(double** out) {
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+  if (e != cudaSuccess)
+    return na_fail(MITHRA_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+  *out = static_cast<double*>(p);
   return MITHRA_OK;
 }
 
@@ -113,8 +107,9 @@ __global__ void __launch_bounds__(256) k_plane_total(const double* __restrict__ 
 }
 
 template <typename T>
-PicP<T> plane_params(const mithra_grid* g) {
+PicP<T> plane_params(const mithra_grid* g, const LoV4* lo) {
   PicP<T> p{};
+  p.plo = lo;
   p.nx = g->nx; p.ny = g->ny; p.nz = g->nz;
   p.nxy = (long long)g->nx * g->ny;
   p.inv2dx = (T)(0.5 / g->dx); p.inv2dy = (T)(0.5 / g->dy); p.inv2dz = (T)(0.5 / g->dz);
@@ -124,10 +119,11 @@ PicP<T> plane_params(const mithra_grid* g) {
 }
 
 template <typename T>
-mithra_status run(const mithra_grid* g, double gamma0, const void* psi, const void* incr,
-                  int kp, double* p_lab, cudaStream_t stream, double* scratch) {
+mithra_status run(const mithra_grid* g, double gamma0, const void* psi, const void* lo,
+                  const void* incr, int kp, double* p_lab, cudaStream_t stream,
+                  double* scratch) {
   const double b0 = std::sqrt(1.0 - 1.0 / (gamma0 * gamma0));
-  const PicP<T> p = plane_params<T>(g);
+  const PicP<T> p = plane_params<T>(g, static_cast<const LoV4*>(lo));
   k_plane_rows<T><<<g->ny - 2, 256, 0, stream>>>(p, static_cast<const V4<T>*>(psi),
                                                 static_cast<const V4<T>*>(incr), kp, gamma0, b0,
                                                 scratch);
@@ -147,8 +143,8 @@ extern "C" {
 
 mithra_status mithra_plane_power_noalloc(const mithra_grid* grid, double gamma0,
                                          mithra_precision precision, const void* psi_newest,
-                                         const void* increment, int32_t k_plane,
-                                         double* p_lab, void* cuda_stream) {
+                                         const void* lo_newest, const void* increment,
+                                         int32_t k_plane, double* p_lab, void* cuda_stream) {
   if (!grid || !psi_newest || !increment || !p_lab)
     return na_fail(MITHRA_EINVAL, "grid, arrays and p_lab must not be NULL");
   if (grid->nx < 4 || grid->ny < 4 || grid->nz < 4 || !(grid->dx > 0) || !(grid->dy > 0) ||
@@ -163,13 +159,17 @@ mithra_status mithra_plane_power_noalloc(const mithra_grid* grid, double gamma0,
   if (precision != MITHRA_P64 && precision != MITHRA_P32 && precision != MITHRA_P32_U64 &&
       precision != MITHRA_P32_C)
     return na_fail(MITHRA_EINVAL, "bad precision");
+  if (lo_newest && (precision == MITHRA_P64 || precision == MITHRA_P32))
+    return na_fail(MITHRA_EINVAL, "lo_newest is only for the compensated forms P32_C, P32_U64");
   double* scratch = nullptr;
-  mithra_status st = scratch_of_current_device(&scratch);
+  mithra_status st = scratch_of_current_context(&scratch);
   if (st != MITHRA_OK) return st;
   cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
   if (precision == MITHRA_P64)
-    return run<double>(grid, gamma0, psi_newest, increment, k_plane, p_lab, stream, scratch);
-  return run<float>(grid, gamma0, psi_newest, increment, k_plane, p_lab, stream, scratch);
+    return run<double>(grid, gamma0, psi_newest, nullptr, increment, k_plane, p_lab, stream,
+                       scratch);
+  return run<float>(grid, gamma0, psi_newest, lo_newest, increment, k_plane, p_lab, stream,
+                    scratch);
 }
 
 }  // extern "C"

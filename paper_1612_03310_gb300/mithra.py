@@ -115,7 +115,7 @@ def lib():
                                       C.POINTER(C.c_int32)]
     L.mithra_kernel_name.argtypes = [C.c_int32]
     L.mithra_kernel_name.restype = C.c_char_p
-    L.mithra_plane_power_noalloc.argtypes = [C.POINTER(Grid), C.c_double, C.c_int, vp, vp,
+    L.mithra_plane_power_noalloc.argtypes = [C.POINTER(Grid), C.c_double, C.c_int, vp, vp, vp,
                                              C.c_int32, dp, vp]
     L.mithra_batch_create.argtypes = [vp, C.POINTER(vp)]
     L.mithra_batch_add.argtypes = [vp, vp]
@@ -216,13 +216,17 @@ def footprint(g: dict, n_particles: int, precision: int = P32) -> int:
 
 
 def plane_power_noalloc(grid: dict, gamma0: float, precision: int, psi_newest_ptr: int,
-                        increment_ptr: int, k_plane: int, stream: int | None = None) -> float:
+                        increment_ptr: int, k_plane: int, stream: int | None = None,
+                        lo_newest_ptr: int | None = None) -> float:
     """Lab-frame power through vertex plane k_plane from device arrays the
-    caller owns (device pointers as integers), with no allocation inside the
+    caller owns (device pointers as integers; lo_newest_ptr the bfloat16 lo
+    parts of a compensated level, or None), with no allocation inside the
     library; see mithra_plane_power_noalloc in include/mithra.h."""
     out = C.c_double()
     _check(lib().mithra_plane_power_noalloc(C.byref(make_grid(grid)), float(gamma0), int(precision),
-                                            C.c_void_p(psi_newest_ptr), C.c_void_p(increment_ptr),
+                                            C.c_void_p(psi_newest_ptr),
+                                            C.c_void_p(lo_newest_ptr or None),
+                                            C.c_void_p(increment_ptr),
                                             int(k_plane), C.byref(out), stream_arg(stream)))
     return float(out.value)
 
