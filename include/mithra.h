@@ -439,7 +439,12 @@ mithra_status mithra_batch_destroy(mithra_batch* batch);
  * condition of the scheme.  Standard scheme: Eq. CFLcondition.  NSFD: with
  * r_l = c dt / d_l, the left side of Eq. NSFDDispersionCD times (c dt)^2 is
  * linear in sin^2(kz dz / 2), so a real omega for every wave vector needs
- * r_x^2 + r_y^2 < 1 and r_z <= 1. */
+ * r_x^2 + r_y^2 < 1 and r_z <= 1.  This is the bound of the interior
+ * scheme; the Mur boundaries are not stable over all of it: random
+ * potentials grow within a few hundred steps for first-order faces at
+ * r_z >= 0.97 with r_x^2 + r_y^2 >= 0.7 (>= 0.5 at r_z = 1), and for either
+ * order at r_z = 0.8 with r_x^2 + r_y^2 >= 0.8; at r_z = 0.95 both orders
+ * stayed bounded up to r_x^2 + r_y^2 = 0.97. */
 mithra_status mithra_check_grid(const mithra_grid* grid);
 
 /* Device bytes mithra_create will allocate for this grid, particle count and
