@@ -63,7 +63,9 @@ typedef enum {
                             compensated pairs (float hi + bfloat16 lo, so that
                             the rounding of a quasi-static potential no longer
                             accumulates) and the particle momenta are stored
-                            and Boris-rotated in FP64 */
+                            in 64 bits as float-float pairs (about 2^-46
+                            relative) and Boris-rotated in float-float
+                            arithmetic; gamma as in MITHRA_P32 */
     MITHRA_P32_C = 3     /* as MITHRA_P32 with compensated potential levels */
 } mithra_precision;
 

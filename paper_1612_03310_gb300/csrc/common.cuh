@@ -178,6 +178,39 @@ struct PicP {
   FastDiv fd_nx, fd_nxy;  // cell index -> (i, j, k)
 };
 
+// Momentum stored as a float-float pair (hi + lo, |lo| <= ulp(hi)/2: about
+// 2^-46 relative, the storage of an FP64 value in 8 bytes) for the FP32 form
+// with compensated momenta: the Boris step runs on it in FP32 arithmetic
+// without converting to and from FP64, whose pipe is narrow on GB300.
+struct alignas(8) FF2 {
+  float hi, lo;
+};
+
+// Conversions of a stored momentum U (float, double or FF2) to and from FP64,
+// and its leading value in the fraction type T.
+__host__ __device__ inline double u_dbl(float u) { return (double)u; }
+__host__ __device__ inline double u_dbl(double u) { return u; }
+__host__ __device__ inline double u_dbl(FF2 u) { return (double)u.hi + (double)u.lo; }
+template <typename U>
+__host__ __device__ inline U u_from(double x);
+template <>
+__host__ __device__ inline float u_from<float>(double x) { return (float)x; }
+template <>
+__host__ __device__ inline double u_from<double>(double x) { return x; }
+template <>
+__host__ __device__ inline FF2 u_from<FF2>(double x) {
+  FF2 r;
+  r.hi = (float)x;
+  r.lo = (float)(x - (double)r.hi);
+  return r;
+}
+template <typename T>
+__host__ __device__ inline T u_lead(float u) { return (T)u; }
+template <typename T>
+__host__ __device__ inline T u_lead(double u) { return (T)u; }
+template <typename T>
+__host__ __device__ inline T u_lead(FF2 u) { return (T)u.hi; }
+
 // T: type of the in-cell fractions; U: type of the momenta.
 template <typename T, typename U>
 struct Parts {

@@ -50,7 +50,7 @@ __global__ void __launch_bounds__(256) k_bunch_partial(PicP<T> p, Parts<T, U> P,
     const double v[6] = {p.x0 + ((double)i + (double)P.fx[q]) * p.dxd,
                          p.y0 + ((double)j + (double)P.fy[q]) * p.dyd,
                          p.z0 + ((double)k + (double)P.fz[q]) * p.dzd,
-                         (double)P.ux[q], (double)P.uy[q], (double)P.uz[q]};
+                         u_dbl(P.ux[q]), u_dbl(P.uy[q]), u_dbl(P.uz[q])};
 #pragma unroll
     for (int a = 0; a < 6; ++a) {
       acc[a] += v[a];

@@ -183,7 +183,7 @@ bool has_lo(int prec) { return prec == MITHRA_P32_C || prec == MITHRA_P32_U64; }
 template <typename F>
 mithra_status with_types(int prec, F&& f) {
   if (prec == MITHRA_P64) return f((double*)nullptr, (double*)nullptr);
-  if (prec == MITHRA_P32_U64) return f((float*)nullptr, (double*)nullptr);
+  if (prec == MITHRA_P32_U64) return f((float*)nullptr, (FF2*)nullptr);
   return f((float*)nullptr, (float*)nullptr);
 }
 #define TYPES_OF(t, u)                                   \

@@ -216,6 +216,29 @@ __device__ inline T inv_gamma(const float u[3]) {
   return (T)y;
 }
 
+// 1/gamma from float-float momenta: 1 + u.u summed in FP32 pairs (each hi^2
+// split exactly by an FMA, the cross terms 2 hi lo and the remainders added
+// to the low word), then to FP64 by one addition and the FP64 Newton-Raphson
+// step of rsqrt_nr from the FP32 seed, as for FP32 momenta.
+template <typename T>
+__device__ inline T inv_gamma(const FF2 u[3]) {
+  float hi = 1.0f, lo = 0.0f;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float p = __fmul_rn(u[a].hi, u[a].hi);
+    const float e = fmaf(u[a].hi, u[a].hi, -p) + 2.0f * u[a].hi * u[a].lo;
+    const float s = __fadd_rn(hi, p);
+    const float bp = __fsub_rn(s, hi);
+    lo += __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(p, bp)) + e;
+    hi = s;
+  }
+  const double x = (double)hi + (double)lo;
+  double y = (double)rsqrtf(hi);
+  y = y * (1.5 - 0.5 * x * y * y);
+  if (sizeof(T) == 8) y = y * (1.5 - 0.5 * x * y * y);
+  return (T)y;
+}
+
 // Boris rotation and kicks (Eq. BorisScheme) for charge-to-mass qm folded
 // into h = qm dtb / (2c) and an = qm dtb / 2, in the momentum type U.  The
 // gamma of the half-kicked momentum t1, which only sets the rotation angle,
@@ -280,19 +303,17 @@ __device__ inline FF ff_of(double x) {
 }
 __device__ inline double ff_to_double(FF a) { return (double)a.hi + (double)a.lo; }
 
-// FP64 momenta next to FP32 fields (P32_U64): the momenta are stored in FP64
-// and the Boris step runs in float-float arithmetic on FP32 instructions
-// (GB300's FP64 pipe is narrow): kicks, gamma_1 by an FP32 seed and one
-// float-float Newton-Raphson step, the rotation vectors t and s (2 / (1 + t.t)
-// by a Newton reciprocal) and both cross products carry ~2^-46, far below the
-// FP32 fields they act with.
-template <>
-__device__ inline void boris<float, double>(const PicP<float>& p, double u[3], const float Ef[3],
-                                            const float Bf[3]) {
+// Compensated momenta next to FP32 fields (P32_U64): the momenta are stored
+// as float-float pairs (FF2) and the Boris step runs in float-float
+// arithmetic on FP32 instructions (GB300's FP64 pipe is narrow): kicks,
+// gamma_1 by an FP32 seed and one float-float Newton-Raphson step, the
+// rotation vectors t and s (2 / (1 + t.t) by a Newton reciprocal) and both
+// cross products carry ~2^-46, far below the FP32 fields they act with.
+__device__ inline void boris_ff(const PicP<float>& p, FF u[3], const float Ef[3],
+                                const float Bf[3]) {
   const FF h = ff_of(p.h), an = ff_of(p.an);
   const FF hE[3] = {ff_mul(h, Ef[0]), ff_mul(h, Ef[1]), ff_mul(h, Ef[2])};
-  const FF t1[3] = {ff_add(ff_of(u[0]), hE[0]), ff_add(ff_of(u[1]), hE[1]),
-                    ff_add(ff_of(u[2]), hE[2])};
+  const FF t1[3] = {ff_add(u[0], hE[0]), ff_add(u[1], hE[1]), ff_add(u[2], hE[2])};
   // 1 / gamma_1 = 1 / sqrt(1 + t1.t1)
   const FF g2 = ff_add(ff_add(ff_add(FF{1.0f, 0.0f}, ff_mul(t1[0], t1[0])), ff_mul(t1[1], t1[1])),
                        ff_mul(t1[2], t1[2]));
@@ -314,7 +335,18 @@ __device__ inline void boris<float, double>(const PicP<float>& p, double u[3], c
   const FF c[3] = {ff_sub(ff_mul(t2[1], sv[2]), ff_mul(t2[2], sv[1])),
                    ff_sub(ff_mul(t2[2], sv[0]), ff_mul(t2[0], sv[2])),
                    ff_sub(ff_mul(t2[0], sv[1]), ff_mul(t2[1], sv[0]))};
-  for (int a = 0; a < 3; ++a) u[a] = ff_to_double(ff_add(ff_add(t1[a], c[a]), hE[a]));
+  for (int a = 0; a < 3; ++a) u[a] = ff_add(ff_add(t1[a], c[a]), hE[a]);
+}
+
+template <>
+__device__ inline void boris<float, FF2>(const PicP<float>& p, FF2 u[3], const float Ef[3],
+                                         const float Bf[3]) {
+  FF v[3] = {{u[0].hi, u[0].lo}, {u[1].hi, u[1].lo}, {u[2].hi, u[2].lo}};
+  boris_ff(p, v, Ef, Bf);
+  for (int a = 0; a < 3; ++a) {
+    u[a].hi = v[a].hi;
+    u[a].lo = v[a].lo;
+  }
 }
 
 __device__ inline bool valid_cell(int i, int j, int k, int nx, int ny, int nz) {
@@ -407,7 +439,8 @@ __device__ inline bool push_particle(const PicP<T>& p, int& i, int& j, int& k, T
     for (int e = 0; e < 3; ++e) { E[e] += Eu[e]; B[e] += Bu[e]; }
     boris(p, u, E, B);
     const T ig = inv_gamma<T>(u);
-    const T d[3] = {p.cx * ig * (T)u[0], p.cy * ig * (T)u[1], p.cz * ig * (T)u[2]};
+    const T d[3] = {p.cx * ig * u_lead<T>(u[0]), p.cy * ig * u_lead<T>(u[1]),
+                    p.cz * ig * u_lead<T>(u[2])};
     i = split_cell_t(i, f[0] + d[0], &f[0]);
     j = split_cell_t(j, f[1] + d[1], &f[1]);
     k = split_cell_t(k, f[2] + d[2], &f[2]);
@@ -498,7 +531,7 @@ __global__ void k_init_particles(PicP<T> p, long long np, const double* __restri
     atomicAdd(reinterpret_cast<unsigned long long*>(lost_ctr), 1ULL);
   }
   P.fx[q] = to_frac<T>(fr[0]); P.fy[q] = to_frac<T>(fr[1]); P.fz[q] = to_frac<T>(fr[2]);
-  P.ux[q] = (U)ux[q]; P.uy[q] = (U)uy[q]; P.uz[q] = (U)uz[q];
+  P.ux[q] = u_from<U>(ux[q]); P.uy[q] = u_from<U>(uy[q]); P.uz[q] = u_from<U>(uz[q]);
   P.id[q] = (int)q;
   key[q] = kk;
   rank[q] = bin_rank(count, kk);
@@ -616,6 +649,24 @@ __global__ void __launch_bounds__(kScanBlock) k_scan_final(int* __restrict__ cou
   }
 }
 
+// Streaming load and store of a stored momentum (FF2 as one 8-byte word).
+template <typename U>
+__device__ inline U ldcs_u(const U* a) { return __ldcs(a); }
+template <>
+__device__ inline FF2 ldcs_u<FF2>(const FF2* a) {
+  const float2 v = __ldcs(reinterpret_cast<const float2*>(a));
+  FF2 r;
+  r.hi = v.x;
+  r.lo = v.y;
+  return r;
+}
+template <typename U>
+__device__ inline void stcs_u(U* a, U v) { __stcs(a, v); }
+template <>
+__device__ inline void stcs_u<FF2>(FF2* a, FF2 v) {
+  __stcs(reinterpret_cast<float2*>(a), make_float2(v.hi, v.lo));
+}
+
 // Moves every particle to offset[key] + rank in the other buffer.
 template <typename T, typename U>
 __global__ void k_scatter(Parts<T, U> a, Parts<T, U> b, long long np, const int* __restrict__ key,
@@ -629,9 +680,9 @@ __global__ void k_scatter(Parts<T, U> a, Parts<T, U> b, long long np, const int*
   __stcs(b.fx + d, __ldcs(a.fx + q));
   __stcs(b.fy + d, __ldcs(a.fy + q));
   __stcs(b.fz + d, __ldcs(a.fz + q));
-  __stcs(b.ux + d, __ldcs(a.ux + q));
-  __stcs(b.uy + d, __ldcs(a.uy + q));
-  __stcs(b.uz + d, __ldcs(a.uz + q));
+  stcs_u(b.ux + d, ldcs_u(a.ux + q));
+  stcs_u(b.uy + d, ldcs_u(a.uy + q));
+  stcs_u(b.uz + d, ldcs_u(a.uz + q));
   __stcs(b.id + d, __ldcs(a.id + q));
 }
 
@@ -654,9 +705,9 @@ __global__ void k_copy_out(PicP<T> p, Parts<T, U> P, long long np, double* __res
   out[0 * np + d] = x;
   out[1 * np + d] = y;
   out[2 * np + d] = z;
-  out[3 * np + d] = (double)P.ux[q];
-  out[4 * np + d] = (double)P.uy[q];
-  out[5 * np + d] = (double)P.uz[q];
+  out[3 * np + d] = u_dbl(P.ux[q]);
+  out[4 * np + d] = u_dbl(P.uy[q]);
+  out[5 * np + d] = u_dbl(P.uz[q]);
   out[6 * np + d] = lost;
 }
 
