@@ -48,7 +48,8 @@ typedef enum {
     MITHRA_ENOMEM = 3,    /* device or pinned host allocation failed */
     MITHRA_ECUDA = 4,     /* a CUDA runtime call or kernel failed */
     MITHRA_ENUMERIC = 5,  /* NaN or Inf seen in a reduction */
-    MITHRA_ELOST = 6,     /* reserved: strict mode for lost particles */
+    MITHRA_ELOST = 6,     /* a particle left the valid region (strict mode,
+                             mithra_set_lost_policy) */
     MITHRA_EBUSY = 7,     /* reserved: batch slot in use */
     MITHRA_ENODEV = 8     /* no CUDA device of compute capability 10.3 */
 } mithra_status;
@@ -159,7 +160,10 @@ typedef struct {
     const double *ux, *uy, *uz;
 } mithra_bunch;
 
-/* Creates a simulation: validates the grid (MITHRA_EUNSTABLE if dt breaks
+/* Creates a simulation (the initial state of Sec. "Quantity Initialization":
+ * Sec. "Field Initialization" with no seed, zero potentials; the bunch as
+ * given, see mithra_make_bunch for Sec. "Electron Bunch Generation"):
+ * validates the grid (MITHRA_EUNSTABLE if dt breaks
  * the stability condition, see mithra_check_grid), allocates device memory
  * (mithra_footprint bytes), copies the bunch, sorts it into cell tiles and
  * deposits rho^{1/2}.  Potentials start at zero at levels -1 and 0, J^0 = 0,
@@ -171,8 +175,15 @@ mithra_status mithra_create(const mithra_grid* grid, const mithra_undulator* und
                             const mithra_bunch* bunch, mithra_precision precision,
                             void* cuda_stream, mithra_sim** out);
 
-/* Enqueues n >= 0 field steps (potential update, E/B, gather, push, deposit,
- * re-sort, optional power sample) on the stream and returns without waiting.
+/* Enqueues n >= 0 field steps on the stream and returns without waiting.
+ * One step is the loop of Sec. "Finite Difference Time Domain (FDTD)" and
+ * Sec. "Particle In Cell (PIC)": the potential update (Eq. updateEquation,
+ * Sec. "FDTD for Scalar Potential") with the boundary (Sec. "Boundary
+ * Truncation"), E and B at the vertices (Sec. "Field Evaluation"), the
+ * gather (Eq. fieldInterpolation) and Boris push (Eq. BorisScheme) in the
+ * grid and undulator fields (Sec. "Undulator Field"), the deposit of J and
+ * rho (Sec. "Current Deposition", Eq. currentIntegral), then the re-sort of
+ * the particles into cell tiles and the optional power sample.
  * With n >= 3 (and no profiling, and a stream other than the legacy or
  * per-thread default stream that the caller is not capturing itself) the
  * steps run as replays of two steps captured
@@ -183,6 +194,18 @@ mithra_status mithra_step(mithra_sim* sim, int64_t n);
 
 /* Waits for all enqueued work; returns its status. */
 mithra_status mithra_sync(mithra_sim* sim);
+
+/* Lost particles (a particle whose cell leaves [1, n-3] along any axis is
+ * lost: flagged, counted and never pushed or deposited again; the paper does
+ * not say what happens there).  strict == 0 (the default): that is all.
+ * strict != 0: once a particle has been lost in a step taken after this
+ * call, mithra_sync (and mithra_batch_sync for a member) returns
+ * MITHRA_ELOST, and so does every later mithra_step (which then enqueues
+ * nothing), with the count in mithra_last_error; the state is kept as it is
+ * and the copy-out calls work as usual, so mithra_copy_particles shows which
+ * particles left.  The call waits for the stream and takes the count so far
+ * as its baseline; mithra_restore takes the restored count. */
+mithra_status mithra_set_lost_policy(mithra_sim* sim, int32_t strict);
 
 /* Number of field steps taken and the rest-frame time t0 + n dt. */
 mithra_status mithra_time(const mithra_sim* sim, int64_t* n_steps, double* t);
@@ -485,6 +508,52 @@ typedef struct {
  * lambda_u <= 0, K < 0, steps_per_period < 1, courant outside (0, 1], or a
  * beam slower than the frame (gamma0 < 1 is impossible by construction). */
 mithra_status mithra_boost_from_lab(const mithra_lab_case* lab, mithra_rest_frame* out);
+
+/* Synthetic bunch in the rest frame (Sec. "Electron Bunch Generation";
+ * input group bunch-initialization, type ellipsoid; host only, FP64, no GPU
+ * needed).  Uniform numbers come from the Halton sequence (sequence 1, the
+ * paper's loader: point i + 1 of the radical inverses in the primes 2 .. 23,
+ * one prime per coordinate) or from a counter-based SplitMix64 generator
+ * keyed by seed (sequence 0).  Per particle:
+ *   - (x, y) = (x0, y0) + (sigma_x, sigma_y) sqrt(-2 ln a) (cos, sin)(2 pi b)
+ *     (Eq. gaussian2D), drawn again while the distance from (x0, y0) exceeds
+ *     trunc_r (trunc_r <= 0: no truncation; transverse-truncation);
+ *   - z uniform in [z_lo, z_hi] (Eq. uniform1D); with taper_sigma > 0 a share
+ *     sqrt(2 pi) taper_sigma / (z_hi - z_lo + sqrt(2 pi) taper_sigma) of the
+ *     particles instead forms a Gaussian of rms taper_sigma of the same peak
+ *     density, its lower half placed behind z_lo and its upper half ahead of
+ *     z_hi (the smooth head and tail that avoid coherent emission at the
+ *     edges of a uniform profile);
+ *   - with bf > 0, z -> z - (2 bf / kb) sin(kb z), which gives
+ *     |<exp(i kb z)>| = J_1(2 bf) = bf (1 - bf^2/2 + ...) for a uniform
+ *     profile over whole periods (Eq. bunchingFactor; its
+ *     printed form is not dimensionally consistent, and kb is the caller's
+ *     rest-frame ponderomotive wavenumber, gamma0 ku (1 + beta0) for the
+ *     static undulator, mithra_rest_frame.k_b);
+ *   - (u_x, u_y) Gaussian of rms (ux_sigma, uy_sigma) (Eq. gaussian2D) and
+ *     u_z Gaussian of mean uz_mean and rms uz_sigma (Eq. gaussian1D).
+ * x .. uz: host arrays of n doubles, written; *q_macro (may be NULL)
+ * receives -charge / n, the electron macroparticle charge for
+ * mithra_bunch.  MITHRA_EINVAL for n < 1, z_hi < z_lo, a negative spread,
+ * bf outside [0, 1) or bf > 0 without kb > 0, or a truncation that rejects
+ * nearly every draw (message in mithra_last_error(NULL)). */
+typedef struct {
+    int64_t n;
+    double charge;               /* total charge [C], > 0 (electrons) */
+    double x0, y0;               /* transverse centre [m] */
+    double sigma_x, sigma_y;     /* rms transverse size [m] */
+    double trunc_r;              /* transverse truncation radius [m], <= 0: none */
+    double z_lo, z_hi;           /* uniform longitudinal extent [m] */
+    double taper_sigma;          /* rms of the head/tail Gaussian [m], 0: none */
+    double ux_sigma, uy_sigma;   /* rms transverse momenta (u = gamma beta) */
+    double uz_mean, uz_sigma;    /* longitudinal momentum mean and rms */
+    double bf, kb;               /* bunching factor and its wavenumber [1/m] */
+    int32_t sequence;            /* 0 SplitMix64 (counter-based), 1 Halton */
+    uint64_t seed;               /* sequence 0 only */
+} mithra_bunch_spec;
+
+mithra_status mithra_make_bunch(const mithra_bunch_spec* spec, double* x, double* y, double* z,
+                                double* ux, double* uy, double* uz, double* q_macro);
 
 #ifdef __cplusplus
 }

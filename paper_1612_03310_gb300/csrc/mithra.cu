@@ -78,7 +78,14 @@ struct mithra_sim {
   // changes
   cudaGraphExec_t step_exec[2] = {nullptr, nullptr};
   double t0 = 0.0;
-  int* h_err = nullptr;  // pinned mirror of dstate->err
+  // pinned mirror of the device's lost counter and error word, refreshed
+  // at the end of every mithra_step and read by the next one
+  struct Mirror {
+    long long n_lost;
+    int err;
+  }* h_mirror = nullptr;
+  bool strict_lost = false;  // mithra_set_lost_policy
+  long long lost_base = 0;   // lost count when strict mode was switched on
   std::string err;
   // potential-update variant: 0 direct, 1 z-marching TMA tiles (needs tm)
   int stencil_variant = 0;
@@ -625,13 +632,29 @@ mithra_status init_particles(mithra_sim* s, const mithra_bunch* b) {
   return MITHRA_OK;
 }
 
-mithra_status sync_status(mithra_sim* s) {
+// Copies the device's lost counter and error word into the pinned mirror
+// (ordered on the stream; read by the next mithra_step).
+cudaError_t refresh_mirror(mithra_sim* s) {
+  static_assert(offsetof(StepState, err) - offsetof(StepState, n_lost) ==
+                    offsetof(mithra_sim::Mirror, err) - offsetof(mithra_sim::Mirror, n_lost),
+                "mirror layout");
+  return cudaMemcpyAsync(s->h_mirror, &s->dstate->n_lost,
+                         offsetof(StepState, err) + sizeof(int) - offsetof(StepState, n_lost),
+                         cudaMemcpyDeviceToHost, s->stream);
+}
+
+// Waits for the stream; the status of its work.  report_lost: strict mode's
+// lost particles count as a failure (mithra_sync, mithra_batch_sync).
+mithra_status sync_status(mithra_sim* s, bool report_lost = false) {
   cudaError_t e = cudaStreamSynchronize(s->stream);
   if (e != cudaSuccess) return cuda_fail(s, e, "stream synchronize");
   StepState st;
   e = cudaMemcpy(&st, s->dstate, sizeof(st), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(s, e, "state copy");
   if (st.err & 1) return fail(s, MITHRA_ENUMERIC, "NaN or Inf in a power reduction");
+  if (report_lost && s->strict_lost && st.n_lost > s->lost_base)
+    return fail(s, MITHRA_ELOST, std::to_string(st.n_lost - s->lost_base) +
+                                     " particle(s) left the valid region (strict mode)");
   return MITHRA_OK;
 }
 
@@ -790,7 +813,7 @@ void free_all(mithra_sim* s) {
                   s->d_bunch_rec, s->d_bunch_part};
   for (void* p : ptrs)
     if (p) cudaFree(p);
-  if (s->h_err) cudaFreeHost(s->h_err);
+  if (s->h_mirror) cudaFreeHost(s->h_mirror);
   for (auto& r : s->recs) {
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);
@@ -919,9 +942,10 @@ mithra_status mithra_create(const mithra_grid* grid, const mithra_undulator* und
   if (ok && has_lo(precision))
     ok = dalloc(&s->PL[0], lo_bytes) && dalloc(&s->PL[1], lo_bytes);
   if (!ok) return bail(MITHRA_ENOMEM, "device allocation failed");
-  if (cudaMallocHost((void**)&s->h_err, sizeof(int)) != cudaSuccess)
+  if (cudaMallocHost((void**)&s->h_mirror, sizeof(*s->h_mirror)) != cudaSuccess)
     return bail(MITHRA_ENOMEM, "pinned allocation failed");
-  *s->h_err = 0;
+  s->h_mirror->n_lost = 0;
+  s->h_mirror->err = 0;
   cudaMemsetAsync(s->P[0], 0, field_bytes, s->stream);
   cudaMemsetAsync(s->P[1], 0, field_bytes, s->stream);
   for (void* l : s->PL)
@@ -1023,7 +1047,10 @@ mithra_status launch_one_step(mithra_sim* s) {
 mithra_status mithra_step(mithra_sim* s, int64_t n) {
   if (!s) return fail(nullptr, MITHRA_EINVAL, "sim is NULL");
   if (n < 0) return fail(s, MITHRA_EINVAL, "n must be >= 0");
-  if (*s->h_err & 1) return fail(s, MITHRA_ENUMERIC, "NaN or Inf in a power reduction");
+  if (s->h_mirror->err & 1) return fail(s, MITHRA_ENUMERIC, "NaN or Inf in a power reduction");
+  if (s->strict_lost && s->h_mirror->n_lost > s->lost_base)
+    return fail(s, MITHRA_ELOST, std::to_string(s->h_mirror->n_lost - s->lost_base) +
+                                     " particle(s) left the valid region (strict mode)");
   if (s->in_batch) return fail(s, MITHRA_EBUSY, "sim belongs to a batch: step it with mithra_batch_step");
   int64_t t = 0;
   // runs of steps replay a captured pair (no profiling events inside; the
@@ -1052,13 +1079,30 @@ mithra_status mithra_step(mithra_sim* s, int64_t n) {
     mithra_status st = launch_one_step(s);
     if (st != MITHRA_OK) return st;
   }
-  cudaMemcpyAsync(s->h_err, &s->dstate->err, sizeof(int), cudaMemcpyDeviceToHost, s->stream);
+  refresh_mirror(s);
   return MITHRA_OK;
 }
 
 mithra_status mithra_sync(mithra_sim* s) {
   if (!s) return fail(nullptr, MITHRA_EINVAL, "sim is NULL");
-  return sync_status(s);
+  return sync_status(s, true);
+}
+
+mithra_status mithra_set_lost_policy(mithra_sim* s, int32_t strict) {
+  if (!s) return fail(nullptr, MITHRA_EINVAL, "sim is NULL");
+  const bool was = s->strict_lost;
+  s->strict_lost = false;
+  mithra_status st = sync_status(s);
+  if (st != MITHRA_OK) {
+    s->strict_lost = was;
+    return st;
+  }
+  StepState d;
+  MCHECK(s, cudaMemcpy(&d, s->dstate, sizeof(d), cudaMemcpyDeviceToHost));
+  s->h_mirror->n_lost = d.n_lost;
+  s->lost_base = d.n_lost;
+  s->strict_lost = strict != 0;
+  return MITHRA_OK;
 }
 
 mithra_status mithra_time(const mithra_sim* s, int64_t* n_steps, double* t) {
@@ -1530,9 +1574,11 @@ mithra_status mithra_restore(mithra_sim* s, const void* in) {
     MCHECK(s, cudaMemcpyAsync(part.dev, p, part.bytes, cudaMemcpyHostToDevice, s->stream));
     p += part.bytes;
   }
-  MCHECK(s, cudaMemcpyAsync(s->h_err, &s->dstate->err, sizeof(int), cudaMemcpyDeviceToHost,
-                            s->stream));
-  return sync_status(s);
+  MCHECK(s, refresh_mirror(s));
+  mithra_status st = sync_status(s);
+  // a strict count starts again from the restored state
+  if (s->strict_lost) s->lost_base = s->h_mirror->n_lost;
+  return st;
 }
 
 mithra_status mithra_boost_from_lab(const mithra_lab_case* lab, mithra_rest_frame* out) {
@@ -1765,7 +1811,7 @@ mithra_status mithra_batch_sync(mithra_batch* b) {
   cudaError_t e = cudaStreamSynchronize(b->stream);
   if (e != cudaSuccess) return bfail(b, MITHRA_ECUDA, std::string("synchronize: ") + cudaGetErrorString(e));
   for (mithra_sim* s : b->sims) {
-    mithra_status st = sync_status(s);
+    mithra_status st = sync_status(s, true);
     if (st != MITHRA_OK) return bfail(b, st, s->err);
   }
   return MITHRA_OK;

@@ -32,7 +32,7 @@ EXPORTS = ["mithra_create", "mithra_step", "mithra_sync", "mithra_time", "mithra
            "mithra_batch_destroy", "mithra_bunch_stats", "mithra_set_spectrum",
            "mithra_read_spectrum", "mithra_set_seed", "mithra_set_bunch_sampling",
            "mithra_read_bunch", "mithra_snapshot_bytes", "mithra_snapshot", "mithra_restore",
-           "mithra_boost_from_lab"]
+           "mithra_boost_from_lab", "mithra_make_bunch", "mithra_set_lost_policy"]
 
 
 class MithraError(RuntimeError):
@@ -74,6 +74,15 @@ class Bunch(C.Structure):
                 ("x", C.POINTER(C.c_double)), ("y", C.POINTER(C.c_double)),
                 ("z", C.POINTER(C.c_double)), ("ux", C.POINTER(C.c_double)),
                 ("uy", C.POINTER(C.c_double)), ("uz", C.POINTER(C.c_double))]
+
+
+class BunchSpec(C.Structure):
+    _fields_ = [("n", C.c_int64), ("charge", C.c_double), ("x0", C.c_double),
+                ("y0", C.c_double), ("sigma_x", C.c_double), ("sigma_y", C.c_double),
+                ("trunc_r", C.c_double), ("z_lo", C.c_double), ("z_hi", C.c_double),
+                ("taper_sigma", C.c_double), ("ux_sigma", C.c_double), ("uy_sigma", C.c_double),
+                ("uz_mean", C.c_double), ("uz_sigma", C.c_double), ("bf", C.c_double),
+                ("kb", C.c_double), ("sequence", C.c_int32), ("seed", C.c_uint64)]
 
 
 _lib = None
@@ -127,6 +136,8 @@ def lib():
     L.mithra_batch_last_error.argtypes = [vp]
     L.mithra_batch_last_error.restype = C.c_char_p
     L.mithra_batch_destroy.argtypes = [vp]
+    L.mithra_make_bunch.argtypes = [C.POINTER(BunchSpec), dp, dp, dp, dp, dp, dp, dp]
+    L.mithra_set_lost_policy.argtypes = [vp, C.c_int32]
     L.mithra_set_tuning.argtypes = [vp, C.POINTER(Tuning)]
     L.mithra_get_tuning.argtypes = [vp, C.POINTER(Tuning)]
     for name in EXPORTS:
@@ -167,6 +178,27 @@ def boost_from_lab(gamma: float, lambda_u: float, K: float, steps_per_period: in
     out = RestFrame()
     _check(lib().mithra_boost_from_lab(C.byref(lab), C.byref(out)), None)
     return {name: getattr(out, name) for name, _ in RestFrame._fields_}
+
+
+def make_bunch(n: int, charge: float, *, sigma_x: float, sigma_y: float, z_lo: float,
+               z_hi: float, uz_mean: float, x0: float = 0.0, y0: float = 0.0,
+               trunc_r: float = 0.0, taper_sigma: float = 0.0, ux_sigma: float = 0.0,
+               uy_sigma: float = 0.0, uz_sigma: float = 0.0, bf: float = 0.0, kb: float = 0.0,
+               sequence: str = "halton", seed: int = 0) -> dict:
+    """Rest-frame bunch from the library's generator (mithra_make_bunch):
+    arrays x, y, z, ux, uy, uz and the macroparticle charge q_macro, the
+    dictionary Simulation takes."""
+    spec = BunchSpec(int(n), charge, x0, y0, sigma_x, sigma_y, trunc_r, z_lo, z_hi, taper_sigma,
+                     ux_sigma, uy_sigma, uz_mean, uz_sigma, bf, kb,
+                     {"splitmix64": 0, "halton": 1}[sequence], int(seed))
+    out = {k: np.empty(max(int(n), 1)) for k in ("x", "y", "z", "ux", "uy", "uz")}
+    q = C.c_double(0.0)
+    dp = C.POINTER(C.c_double)
+    _check(lib().mithra_make_bunch(C.byref(spec), *[out[k].ctypes.data_as(dp) for k in
+                                                     ("x", "y", "z", "ux", "uy", "uz")],
+                                   C.byref(q)), None)
+    out["q_macro"] = q.value
+    return out
 
 
 def normalized_wavelengths(lambda_r: float, f_min: float, f_max: float, df: float) -> np.ndarray:
@@ -279,6 +311,11 @@ class Simulation:
 
     def sync(self):
         _check(lib().mithra_sync(self.h), self.h)
+
+    def set_lost_policy(self, strict: bool):
+        """strict: a particle lost from now on makes sync / step raise
+        MithraError with status ELOST (mithra_set_lost_policy)."""
+        _check(lib().mithra_set_lost_policy(self.h, 1 if strict else 0), self.h)
 
     def time(self):
         n = C.c_int64()

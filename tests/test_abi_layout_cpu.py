@@ -14,7 +14,8 @@ from paper_1612_03310_gb300 import mithra
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 PAIRS = [("mithra_grid", mithra.Grid), ("mithra_undulator", mithra.Undulator),
          ("mithra_bunch", mithra.Bunch), ("mithra_tuning", mithra.Tuning),
-         ("mithra_lab_case", mithra.LabCase), ("mithra_rest_frame", mithra.RestFrame)]
+         ("mithra_lab_case", mithra.LabCase), ("mithra_rest_frame", mithra.RestFrame),
+         ("mithra_bunch_spec", mithra.BunchSpec)]
 
 
 def _layout(tmp_path_factory, header, incdir, pairs):

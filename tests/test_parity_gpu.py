@@ -89,6 +89,33 @@ def compare_fields(sim, o, tol, names=FIELDS, report=None):
     assert not bad, bad
 
 
+def shell_mask(g, width=2):
+    """Vertices within `width` of any face (the boundary vertices and the
+    interior vertices their Mur updates read)."""
+    k, j, i = np.meshgrid(np.arange(g["nz"]), np.arange(g["ny"]), np.arange(g["nx"]),
+                          indexing="ij")
+    return ((i < width) | (i >= g["nx"] - width) | (j < width) | (j >= g["ny"] - width) |
+            (k < width) | (k >= g["nz"] - width))
+
+
+def compare_vertices(sim, o, tol, mask, names):
+    """Per-vertex check on a region: max |GPU - oracle| over the masked
+    vertices, scaled by the field's largest value anywhere, so that an error
+    confined to a few vertices (one boundary face, one injection plane) shows
+    even where the whole-field L2 norm would hide it."""
+    ref = oracle_fields(o)
+    bad = {}
+    for nm in names:
+        r = ref[nm]
+        scale = np.abs(r).max()
+        if scale == 0.0:
+            continue
+        e = float(np.abs(sim.copy_field(nm) - r)[mask].max() / scale)
+        if e > tol:
+            bad[nm] = e
+    assert not bad, bad
+
+
 def compare_particles(sim, o, tol_cells, face_eps):
     got = sim.copy_particles()
     lost_o = o.lost.astype(bool)
@@ -142,6 +169,9 @@ def test_vacuum_update_parity(M, orc, prec, shape, variant, lz, boundary):
             sim.sync()
             compare_fields(sim, o, tol, names=["Ax", "Ay", "Az", "phi", "Ex", "Ey", "Ez",
                                                "Bx", "By", "Bz"])
+            # the boundary shell vertex by vertex (Mur faces, edges, corners)
+            compare_vertices(sim, o, 20 * tol, shell_mask(g),
+                             ["Ax", "Ay", "Az", "phi", "Ax_prev", "phi_prev", "Ex", "Bz"])
             ref = oracle_fields(o)
             for nm in ("Ax_prev", "phi_prev"):
                 assert rel_l2(sim.copy_field(nm), ref[nm]) <= tol
@@ -207,6 +237,42 @@ def test_lost_particles_flagged(M, orc, prec):
         assert list(got["lost"]) == list(o.lost) == [1, 1, 1, 0]
         assert got["n_lost"] == 3
         compare_fields(sim, o, 1e-10 if prec == "P64" else 1e-5, names=["rho", "Jx", "Jz"])
+
+
+@pytest.mark.parametrize("prec", ["P64", "P32_U64"])
+def test_strict_lost_policy(M, prec):
+    # the three escaping particles of test_lost_particles_flagged: by default
+    # they are flagged and counted; in strict mode the first synchronising
+    # call after the step that loses them reports MITHRA_ELOST, the next step
+    # enqueues nothing, and the state shows which particles left
+    g = inputs.random_grid(31, 16, 16, 16)
+    P = dict(x=np.array([g["x0"] + 12.9 * g["dx"], g["x0"] + 7.5 * g["dx"]]),
+             y=np.array([g["y0"] + 7.5 * g["dy"], g["y0"] + 7.5 * g["dy"]]),
+             z=np.array([g["z0"] + 7.5 * g["dz"], g["z0"] + 7.5 * g["dz"]]),
+             ux=np.array([5.0, 0.0]), uy=np.array([0.0, 0.0]), uz=np.array([0.0, 0.1]),
+             q_macro=-1e-15)
+    with M.Simulation(dict(g, boundary=1), None, P, precision=getattr(M, prec)) as sim:
+        sim.set_lost_policy(True)
+        sim.step(1)
+        sim.sync()  # nothing lost yet
+        sim.step(2)
+        with pytest.raises(M.MithraError) as e:
+            sim.sync()
+        assert e.value.status == M.ELOST
+        assert "1 particle(s) left" in str(e.value)
+        with pytest.raises(M.MithraError) as e:
+            sim.step(1)
+        assert e.value.status == M.ELOST
+        assert sim.time()[0] == 3
+        got = sim.copy_particles()  # the state is kept
+        assert list(got["lost"]) == [1, 0]
+        sim.set_lost_policy(False)  # back to counting only
+        sim.step(1)
+        sim.sync()
+    with M.Simulation(dict(g, boundary=1), None, P, precision=getattr(M, prec)) as sim:
+        sim.step(3)
+        sim.sync()
+        assert sim.copy_particles()["n_lost"] == 1
 
 
 @pytest.mark.parametrize("prec", ["P64", "P32"])

@@ -4,7 +4,7 @@ import numpy as np
 import pytest
 
 from paper_1612_03310_gb300 import build_lib, inputs
-from test_parity_gpu import compare_fields, compare_particles
+from test_parity_gpu import compare_fields, compare_particles, compare_vertices
 
 pytestmark = pytest.mark.gpu
 
@@ -22,6 +22,13 @@ def M():
             pytest.skip("no GB300 device")
         raise
     return mithra
+
+
+def tfsf_mask(g):
+    """The vertex planes k = 1 .. 4 around the injection planes k = 2, 3."""
+    m = np.zeros((g["nz"], g["ny"], g["nx"]), dtype=bool)
+    m[1:5] = True
+    return m
 
 
 def seed_for(g, gamma0, signal="gaussian", pol=(0.0, 1.0), centre=20):
@@ -49,6 +56,8 @@ def test_seeded_vacuum_matches_oracle(M, orc, prec, signal):
             sim.sync()
             compare_fields(sim, o, 1e-10 if p == M.P64 else 1e-5,
                            names=["Ax", "Ay", "Az", "phi", "Ex", "Ey", "Bx", "By"])
+            compare_vertices(sim, o, 2e-9 if p == M.P64 else 2e-4, tfsf_mask(g),
+                             ["Ax", "Ay", "Ex", "Ey", "Bx", "By"])
         assert np.abs(sim.copy_field("Ay")).max() > 0  # the seed is inside
 
 
@@ -84,6 +93,8 @@ def test_gaussian_beam_seed_vacuum_matches_oracle(M, orc, prec, signal, stencil)
             sim.sync()
             compare_fields(sim, o, 1e-10 if p == M.P64 else 1e-5,
                            names=["Ax", "Ay", "Az", "phi", "Ex", "Ey", "Bx", "By"])
+            compare_vertices(sim, o, 2e-9 if p == M.P64 else 2e-4, tfsf_mask(g),
+                             ["Ax", "Ay", "Ex", "Ey", "Bx", "By"])
         Ay = sim.copy_field("Ay")
         assert np.abs(Ay).max() > 0.1 * seed["a0"] * 9.109e-31 * C0 / 1.602e-19
         # not uniform across the planes: the beam's waist is inside the grid
