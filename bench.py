@@ -1,6 +1,11 @@
 #!/usr/bin/env python3
 """Throughput of the FDTD/PIC time step on one GB300 (or N replicas).
 
+The default precision form is P32_U64 (FP32 fields with compensated
+potential levels and float-float momenta, FP64 frame clock, gamma and power):
+the form whose error after c2's 5000 steps stays within the stated field
+(1e-4) and power (1e-3) tolerances.  P32 and P64 are timed beside it.
+
 A step is one pass of the whole hot path over the c2 workload
 (128x128x1024 cells, 2^21 macroparticles, rest-frame IR FEL shaped like the
 paper's Example 1): potential update with Mur faces, E/B from the potentials,
@@ -41,7 +46,14 @@ def parse():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="mithra", choices=["mithra", "reference"])
     ap.add_argument("--workload", default="c2")
-    ap.add_argument("--precision", default="p32", choices=["p32", "p32_u64", "p32_c", "p64"])
+    ap.add_argument("--precision", default="p32_u64", choices=["p32", "p32_u64", "p32_c", "p64"],
+                    help="p32_u64 (default): FP32 fields with compensated levels and "
+                         "float-float momenta, the form that meets the 1e-4 field and 1e-3 "
+                         "power tolerance after the configured 5000 steps; p32: plain FP32 "
+                         "state; p64: all FP64")
+    ap.add_argument("--no-c3", action="store_true",
+                    help="step mode: skip the c3 summary (256x256x2048 cells, 2^24 particles)")
+    ap.add_argument("--c3-steps", type=int, default=60)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-p64", action="store_true")
@@ -148,6 +160,10 @@ NCU_TRAFFIC = {
     # k_mur_boundary<0, float, 1, 1> + k_potential_zloop_mur1<0, float>
     ("potential_step", "p32", "c2"): 28196096 + 61696 + 824917760 + 509206016,
     ("push", "p32", "c2"): 179321088 + 62403328,
+    # k_mur_boundary<1, float, 1, 1> + k_potential_zloop_mur1<1, float>
+    ("potential_step", "p32_u64", "c2"): 35244992 + 18752 + 973243712 + 638126848,
+    # k_push_tiled<0, float, FF2, 1>
+    ("push", "p32_u64", "c2"): 231833856 + 90103168,
 }
 
 
@@ -194,6 +210,20 @@ def algorithmic_bytes(kernel: str, grid: dict, n_particles: int, prec: str) -> f
     return 0.0
 
 
+def minimum_bytes(kernel: str, grid: dict, n_particles: int, prec: str) -> float:
+    """The algorithmic minimum of the survey's table for the potential update
+    (read psi^n, psi^{n-1} and the source, write psi^{n+1}: 16 words per
+    cell, plus the bfloat16 lo parts of compensated levels read and
+    written); the increment form's extra read and write of the increment
+    are not in it."""
+    if kernel != "potential_step":
+        return algorithmic_bytes(kernel, grid, n_particles, prec)
+    r = 8 if prec == "p64" else 4
+    lo = prec in ("p32_c", "p32_u64")
+    interior = (grid["nx"] - 2) * (grid["ny"] - 2) * (grid["nz"] - 2)
+    return interior * (4 * 4 * r + (16 if lo else 0))
+
+
 def max_over_ranks(x: float, world: int) -> float:
     """The largest value over the ranks (the slowest replica's time); the
     reduction runs on the process group's own device (CUDA for NCCL)."""
@@ -204,6 +234,10 @@ def max_over_ranks(x: float, world: int) -> float:
     t = torch.tensor([x], device=dev, dtype=torch.float64)
     torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
     return float(t.item())
+
+
+def interior_cells(g: dict) -> int:
+    return (g["nx"] - 2) * (g["ny"] - 2) * (g["nz"] - 2)
 
 
 def replica_bunch(workload: dict, rank: int) -> dict:
@@ -319,6 +353,8 @@ def run_gpu(args, rank, world):
         res["p64"] = side_run(mithra.P64, max(20, K // 10))
     if not args.no_p64 and prec == mithra.P32:
         res["p32_u64"] = side_run(mithra.P32_U64, max(50, K // 4))
+    if not args.no_p64 and prec == mithra.P32_U64:
+        res["p32"] = side_run(mithra.P32, max(50, K // 4))
 
     # end to end through the C ABI from host buffers
     if not args.no_e2e:
@@ -339,6 +375,68 @@ def run_gpu(args, rank, world):
         res["e2e"] = dict(seconds=e2e_s, h2d=6 * 8 * n_part, d2h=rec.nbytes + 7 * 8 * n_part,
                           check=float(np.isfinite(out["x"]).all()))
     return res
+
+
+def run_c3(args, peak: float) -> dict:
+    """c3, the largest single-GPU workload (256x256x2048 cells, 2^24
+    particles), in the bench's precision form: K3 steps as the library runs
+    them (graph replays), then K3 more with per-kernel CUDA events for the
+    roofline of its dominant kernel and of the potential update."""
+    import torch
+    from paper_1612_03310_gb300 import autotune, inputs, mithra
+    w = inputs.workload("c3")
+    g, und = dict(w["grid"], boundary=1), w["undulator"]
+    bunch = inputs.make_bunch(w["bunch_spec"], w["seed"])
+    n_part = bunch["x"].size
+    ncell = g["nx"] * g["ny"] * g["nz"]
+    prec = getattr(mithra, PRECISIONS[args.precision])
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    K3 = args.c3_steps
+    tuning = autotune.tune(g, und, bunch, prec, stream=stream.cuda_stream)
+    sim = mithra.Simulation(g, und, bunch, precision=prec, stream=stream.cuda_stream)
+    sim.set_tuning(**tuning)
+    sim.set_power_sampling(g["nz"] - 16, 5 + 2 * K3)
+    sim.step(5)
+    sim.sync()
+    sampler = ClockSampler(None)
+    sampler.start()
+    time.sleep(0.3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    sim.step(K3)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    sim.profile(True)
+    sim.step(K3)
+    sim.sync()
+    sampler.stop()
+    kt = sim.kernel_times()
+    sim.profile(False)
+    n_lost = sim.copy_particles()["n_lost"]
+    sim.close()
+    s = ms / 1e3
+    dom = max(kt, key=lambda k: kt[k][0])
+    dom_ms = kt[dom][0] / max(kt[dom][1], 1)
+    ab = algorithmic_bytes(dom, g, n_part, args.precision)
+    st_ms = kt["potential_step"][0] / max(kt["potential_step"][1], 1)
+    st_b = algorithmic_bytes("potential_step", g, n_part, args.precision)
+    total = sum(v[0] for v in kt.values())
+    return {"workload": inputs.describe("c3"), "precision": args.precision, "steps": K3,
+            "ms_per_step": ms / K3, "cell_updates_per_s": ncell * K3 / s,
+            "particle_pushes_per_s": n_part * K3 / s,
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": ab / (dom_ms / 1e3) / 1e9,
+                         "peak": peak, "unit": "GB/s",
+                         "frac": ab / (dom_ms / 1e3) / 1e9 / peak,
+                         "algorithmic_bytes_per_launch": ab, "avg_launch_ms": dom_ms,
+                         "traffic": None},
+            "stencil": {"avg_launch_ms": st_ms, "achieved_gbs": st_b / (st_ms / 1e3) / 1e9,
+                        "frac": st_b / (st_ms / 1e3) / 1e9 / peak,
+                        "cell_updates_per_s": ncell / (st_ms / 1e3)},
+            "kernel_share": {k: round(v[0] / total, 4) for k, v in kt.items()},
+            "tuning": tuning, "clocks": sampler.summary(), "n_lost": n_lost}
 
 
 def cpu_oracle_rate(workload: str, budget_s: float, max_steps: int | None = None):
@@ -631,6 +729,8 @@ def main():
     stencil_ms = kt["potential_step"][0] / max(kt["potential_step"][1], 1)
     stencil_gbs = algorithmic_bytes("potential_step", res["grid"], npart, args.precision) / (
         stencil_ms / 1e3) / 1e9
+    stencil_min_gbs = minimum_bytes("potential_step", res["grid"], npart, args.precision) / (
+        stencil_ms / 1e3) / 1e9
     total_kernel_ms = sum(v[0] for v in kt.values())
     line = {
         "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world,
@@ -645,6 +745,11 @@ def main():
                      "traffic": NCU_TRAFFIC.get((dom, args.precision, args.workload))},
         "stencil": {"kernel": "potential_step", "avg_launch_ms": stencil_ms,
                     "achieved_gbs": stencil_gbs, "frac": stencil_gbs / peak,
+                    "bytes_per_cell": algorithmic_bytes("potential_step", res["grid"], npart,
+                                                        args.precision) / interior_cells(g),
+                    "frac_at_minimum_bytes": stencil_min_gbs / peak,
+                    "minimum_bytes_per_cell": minimum_bytes("potential_step", res["grid"], npart,
+                                                            args.precision) / interior_cells(g),
                     "cell_updates_per_s": ncell / (stencil_ms / 1e3)},
         "push": push_rates(kt, npart, res["grid"], args.precision),
         "kernel_share": {k: round(v[0] / total_kernel_ms, 4) for k, v in kt.items()},
@@ -658,7 +763,7 @@ def main():
         "tuning_trials": res.get("trials"),
         "n_lost": res["n_lost"],
     }
-    for side in ("p64", "p32_u64"):
+    for side in ("p64", "p32_u64", "p32"):
         if side not in res:
             continue
         p = res[side]
@@ -676,6 +781,8 @@ def main():
         line["e2e"] = {"value": world * ncell * K / e["seconds"], "unit": "cell-updates/s",
                        "h2d_bytes_per_step": e["h2d"] / K, "d2h_bytes_per_step": e["d2h"] / K,
                        "seconds": e["seconds"]}
+    if world == 1 and not args.no_c3:
+        line["c3"] = run_c3(args, peak)
     if world == 1 and not args.no_batch:
         bt = run_batch(args, K=40, plain_jobs=4)
         line["batch"] = {k: bt[k] for k in ("value", "unit", "ms_per_step", "plain_p64_jobs_per_h",
