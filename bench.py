@@ -470,113 +470,184 @@ def cpu_oracle_rate(workload: str, budget_s: float, max_steps: int | None = None
                        f"the particle loop is serial, the grid loops use OpenMP")
 
 
-def run_batch(args, K: int | None = None, plain_jobs: int | None = None) -> dict:
-    """c4: 64 simulations of uneven size advanced together (P32, one captured
-    graph per two steps) against the plain form (P64, one simulation after
-    another, one launch sequence per step).  Jobs are 1000 steps; the timed
-    runs take --job-steps steps and jobs/h is scaled to 1000-step jobs."""
+def _time_steps(stream, stepper, K: int) -> float:
+    """ms per step of K steps of stepper (CUDA events on stream)."""
     import torch
-    from paper_1612_03310_gb300 import autotune, inputs, mithra
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    stepper(K)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / K
+
+
+def _batch_arm(jobs, prec, mode, K, stream, kp_frac=None):
+    """A batch of jobs in precision prec and batch mode ("auto", True fused,
+    False per member): ms per batched step over K steps (after 4 untimed
+    ones), the form the graph took, and with kp_frac each job's power record
+    at plane kp_frac * nz and its final E_x."""
+    from paper_1612_03310_gb300 import inputs, mithra
+    sims = []
+    for j in jobs:
+        g = dict(j["grid"], boundary=1)
+        sim = mithra.Simulation(g, j["undulator"], inputs.make_bunch(j["bunch_spec"], j["seed"]),
+                                precision=prec)
+        kp = int(kp_frac * g["nz"]) if kp_frac else g["nz"] - 8
+        sim.set_power_sampling(kp, K + 8)
+        sims.append(sim)
+    b = mithra.Batch(stream=stream.cuda_stream)
+    for sim in sims:
+        b.add(sim)
+    b.set_mode(mode)
+    b.step(4)
+    b.sync()
+    ms = _time_steps(stream, b.step, K)
+    out = dict(ms=ms, fused=b.fused())
+    if kp_frac:
+        out["power"] = [sim.read_power()[:, 0] for sim in sims]
+        out["Ex"] = [sim.copy_field("Ex") for sim in sims]
+    b.close()
+    for sim in sims:
+        sim.close()
+    return out
+
+
+def _plain_arm(jobs, prec, K, stream, kp_frac=None):
+    """The same jobs one after another, each a plain simulation stepped alone:
+    ms per job of K steps, and the power records and final E_x."""
+    from paper_1612_03310_gb300 import inputs, mithra
+    total = 0.0
+    power, ex = [], []
+    for j in jobs:
+        g = dict(j["grid"], boundary=1)
+        sim = mithra.Simulation(g, j["undulator"], inputs.make_bunch(j["bunch_spec"], j["seed"]),
+                                precision=prec, stream=stream.cuda_stream)
+        kp = int(kp_frac * g["nz"]) if kp_frac else g["nz"] - 8
+        sim.set_power_sampling(kp, K + 8)
+        sim.step(4)
+        sim.sync()
+        total += _time_steps(stream, sim.step, K) * K
+        if kp_frac:
+            power.append(sim.read_power()[:, 0])
+            ex.append(sim.copy_field("Ex"))
+        sim.close()
+    return dict(ms_per_job=total / len(jobs), power=power, Ex=ex)
+
+
+def run_batch(args, K: int | None = None, plain_jobs: int | None = None) -> dict:
+    """c4: 64 design-sweep simulations of uneven size advanced together, in
+    jobs/h of 1000-step jobs (K timed steps, scaled), against the same jobs
+    run one after another as plain simulations (P32, to isolate what batching
+    buys, and P64, the plain FP64 form).  The tolerance-meeting form P32_U64
+    is timed batched as well, and its per-job power (on a plane the radiation
+    reaches within the run) and E_x are compared with P64 job by job.  A
+    second case, 256 tiny jobs, is where the fused batched form (one launch
+    per phase for all members) pays over one launch sequence per member."""
+    import torch
+    from paper_1612_03310_gb300 import inputs, mithra
     jobs = inputs.batch_jobs(64, steps=1000)
     K = args.job_steps if K is None else K
     n_plain = args.plain_jobs if plain_jobs is None else plain_jobs
     scale = 1000.0 / K
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    sims = []
-    for j in jobs:
-        g = dict(j["grid"], boundary=1)
-        sim = mithra.Simulation(g, j["undulator"], inputs.make_bunch(j["bunch_spec"], j["seed"]),
-                                precision=mithra.P32)
-        sim.set_tuning(stencil_variant=0, push_variant=1, push_ctas_per_sm=0)
-        sim.set_power_sampling(g["nz"] - 8, K + 4)
-        sims.append(sim)
-    b = mithra.Batch(stream=stream.cuda_stream)
-    for sim in sims:
-        b.add(sim)
-    b.step(4)  # warm-up (and graph capture)
-    b.sync()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    b.step(K)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms_batch = e0.elapsed_time(e1)
-    p32 = [sim.read_power()[:, 0] for sim in sims[:n_plain]]
-    b.close()
-    for sim in sims:
-        sim.close()
-    # plain FP64, one job at a time
-    t_plain = 0.0
-    errs = []
-    for k, j in enumerate(jobs[:n_plain]):
-        g = dict(j["grid"], boundary=1)
-        sim = mithra.Simulation(g, j["undulator"], inputs.make_bunch(j["bunch_spec"], j["seed"]),
-                                precision=mithra.P64, stream=stream.cuda_stream)
-        sim.set_power_sampling(g["nz"] - 8, K + 4)
-        sim.step(4)
-        sim.sync()
-        e0.record(stream)
-        sim.step(K)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        t_plain += e0.elapsed_time(e1)
-        p64 = sim.read_power()[:, 0]
-        sim.close()
-        if np.abs(p64).max() > 0:  # radiation has reached the plane
-            errs.append(float(np.abs(p32[k] - p64).max() / np.abs(p64).max()))
-    per_job_plain = t_plain / n_plain * scale / 1e3
-    jobs_h_batch = 3600.0 * len(jobs) / (ms_batch * scale / 1e3)
-    jobs_h_plain = 3600.0 / per_job_plain
+    jh = lambda ms_per_step, n: 3600.0 * n / (ms_per_step * 1000.0 / 1e3)  # noqa: E731
+    auto = _batch_arm(jobs, mithra.P32, "auto", K, stream)
+    fused = _batch_arm(jobs, mithra.P32, True, max(10, K // 5), stream)
+    member = _batch_arm(jobs, mithra.P32, False, max(10, K // 5), stream)
+    kpf = 0.8  # 0.05 nz ahead of the bunch head: radiation arrives within the run
+    u64 = _batch_arm(jobs[:n_plain], mithra.P32_U64, "auto", K, stream, kp_frac=kpf)
+    u64_all = _batch_arm(jobs, mithra.P32_U64, "auto", max(10, K // 5), stream)
+    plain32 = _plain_arm(jobs[:n_plain], mithra.P32, K, stream)
+    plain64 = _plain_arm(jobs[:n_plain], mithra.P64, K, stream, kp_frac=kpf)
+    perr, ferr = [], []
+    for k in range(n_plain):
+        p64, p32 = plain64["power"][k], u64["power"][k]
+        m = np.abs(p64).max()
+        if m > 0:
+            perr.append(float(np.abs(p32 - p64).max() / m))
+        e64 = plain64["Ex"][k]
+        ferr.append(float(np.linalg.norm(u64["Ex"][k] - e64) / np.linalg.norm(e64)))
     cells = sum(j["grid"]["nx"] * j["grid"]["ny"] * j["grid"]["nz"] for j in jobs)
     parts = sum(j["bunch_spec"]["n"] for j in jobs)
+    per_job_plain64 = plain64["ms_per_job"] * scale / 1e3
+    per_job_plain32 = plain32["ms_per_job"] * scale / 1e3
+    # tiny jobs: 256 of 32 x 32 x 128 cells and 2000 particles
+    tiny = inputs.uniform_jobs(256, 32, 128, 2000)
+    t_auto = _batch_arm(tiny, mithra.P32, "auto", K, stream)
+    t_member = _batch_arm(tiny, mithra.P32, False, K, stream)
+    t_plain = _plain_arm(tiny[:16], mithra.P32, K, stream)
     return {"metric": "jobs/h, 64 uneven simulations of 1000 steps (c4)", "impl": "mithra",
-            "mode": "batch", "value": jobs_h_batch, "unit": "jobs/h", "higher_is_better": True,
-            "n_gpus": 1, "steps": K, "ms_per_step": ms_batch / K,
-            "plain_p64_jobs_per_h": jobs_h_plain, "speedup_vs_plain": jobs_h_batch / jobs_h_plain,
-            "cell_updates_per_s": cells * K / (ms_batch / 1e3),
-            "particle_pushes_per_s": parts * K / (ms_batch / 1e3),
-            "power_rel_err_p32_vs_p64": {"max": max(errs) if errs else None, "jobs": len(errs),
-                                         "note": "jobs whose plane saw radiation in the timed "
-                                                 "steps"},
+            "mode": "batch", "value": jh(auto["ms"], len(jobs)), "unit": "jobs/h",
+            "higher_is_better": True, "n_gpus": 1, "steps": K, "ms_per_step": auto["ms"],
+            "form": "fused" if auto["fused"] else "per member",
+            "fused_jobs_per_h": jh(fused["ms"], len(jobs)),
+            "per_member_jobs_per_h": jh(member["ms"], len(jobs)),
+            "plain_p32_jobs_per_h": 3600.0 / per_job_plain32,
+            "plain_p64_jobs_per_h": 3600.0 / per_job_plain64,
+            "speedup_vs_plain_p32": jh(auto["ms"], len(jobs)) * per_job_plain32 / 3600.0,
+            "speedup_vs_plain": jh(auto["ms"], len(jobs)) * per_job_plain64 / 3600.0,
+            "p32_u64_jobs_per_h": jh(u64_all["ms"], len(jobs)),
+            "p32_u64_speedup_vs_plain_p64": jh(u64_all["ms"], len(jobs)) * per_job_plain64 / 3600,
+            "cell_updates_per_s": cells / (auto["ms"] / 1e3),
+            "particle_pushes_per_s": parts / (auto["ms"] / 1e3),
+            "accuracy_p32_u64_vs_p64": {
+                "power_max_rel": max(perr) if perr else None, "jobs_with_power": len(perr),
+                "Ex_rel_l2_max": max(ferr), "jobs": n_plain,
+                "note": f"{K} steps, power through the plane at 0.8 nz (0.05 nz ahead of the "
+                        f"bunch head), the first {n_plain} jobs, batched P32_U64 against each "
+                        f"job run alone in P64"},
+            "tiny": {"jobs": len(tiny), "grid": "32x32x128", "particles": 2000,
+                     "form": "fused" if t_auto["fused"] else "per member",
+                     "jobs_per_h": jh(t_auto["ms"], len(tiny)),
+                     "per_member_jobs_per_h": jh(t_member["ms"], len(tiny)),
+                     "plain_p32_jobs_per_h": 3600.0 / (t_plain["ms_per_job"] * scale / 1e3)},
             "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"c4: 64 grids 48^2x192..128^2x768, {cells} cells, "
                                    f"{parts} particles, 64-512 particles per cell column",
-                       "timed": f"{K} steps per job, jobs/h scaled to 1000 steps",
-                       "plain": f"P64, {n_plain} jobs one after another"}}
+                       "timed": f"{K} steps per arm (fused/per-member/all-P32_U64 arms "
+                                f"{max(10, K // 5)}), jobs/h scaled to 1000 steps",
+                       "plain": f"{n_plain} jobs one after another, P32 and P64"}}
 
 
 def run_serve(args, duration: float | None = None) -> dict:
     """c5: Poisson arrivals of design-sweep jobs served by continuous
     batching, at the configured rate and at half of the measured capacity."""
     import torch
-    from paper_1612_03310_gb300 import serve, inputs
+    from paper_1612_03310_gb300 import mithra, serve, inputs
     free, _ = torch.cuda.mem_get_info()
     budget = int(0.85 * free)
     dur = args.duration if duration is None else duration
+    prec = getattr(mithra, PRECISIONS[args.precision])
     out = {}
     runs = [("rate", args.rate)]
     for name, rate in runs:
         jobs = inputs.serve_jobs(int(rate * dur) + 1, rate)
-        srv = serve.Server(budget, max_slots=64, tick_steps=64)
+        srv = serve.Server(budget, tick_steps=64, precision=prec)
         st = srv.run(jobs, time_limit=dur)
         st.pop("done")
         st.pop("not_done", None)
         out[name] = dict(st, offered_rate=rate)
-    cap = out["rate"]["completed"] / out["rate"]["wall_s"]
+    # capacity in jobs/s: the cell updates the GPU served per second over the
+    # cell updates of a mean job of the stream
+    all_jobs = inputs.serve_jobs(int(args.rate * dur) + 1, args.rate)
+    mean_cells = float(np.mean([j["grid"]["nx"] * j["grid"]["ny"] * j["grid"]["nz"] * j["steps"]
+                                for j in all_jobs]))
+    cap = out["rate"]["served_cell_updates_per_s"] / mean_cells
     half = max(0.05, 0.5 * cap)
     jobs = inputs.serve_jobs(int(half * dur) + 1, half, seed=6)
-    srv = serve.Server(budget, max_slots=64, tick_steps=64)
+    srv = serve.Server(budget, tick_steps=64, precision=prec)
     st = srv.run(jobs, time_limit=dur + 120.0)
     st.pop("done")
     st.pop("not_done", None)
     out["half_capacity"] = dict(st, offered_rate=half)
     r = out["rate"]
+    out["capacity_jobs_per_s"] = cap
     return {"metric": "jobs/h and p50/p99 latency, continuous batching (c5)", "impl": "mithra",
             "mode": "serve", "value": r["jobs_per_hour"], "unit": "jobs/h",
             "higher_is_better": True, "n_gpus": 1, "p50_s": r["p50_s"], "p99_s": r["p99_s"],
-            "dtype": "f32", "data": "synthetic", "runs": out,
+            "dtype": "f32", "data": "synthetic", "runs": out, "precision": args.precision,
             "config": {"workload": "c5: Poisson arrivals, grids 32^2x128..160^2x1024, "
                                    "1e3-4e6 particles, 500-5000 steps",
                        "duration_s": dur, "hbm_budget": budget}}
@@ -784,15 +855,15 @@ def main():
     if world == 1 and not args.no_c3:
         line["c3"] = run_c3(args, peak)
     if world == 1 and not args.no_batch:
-        bt = run_batch(args, K=40, plain_jobs=4)
-        line["batch"] = {k: bt[k] for k in ("value", "unit", "ms_per_step", "plain_p64_jobs_per_h",
-                                            "speedup_vs_plain", "cell_updates_per_s",
-                                            "particle_pushes_per_s", "power_rel_err_p32_vs_p64")}
-        line["batch"]["config"] = bt["config"]
+        bt = run_batch(args, K=100, plain_jobs=4)
+        line["batch"] = {k: v for k, v in bt.items()
+                         if k not in ("metric", "impl", "mode", "higher_is_better", "n_gpus",
+                                      "dtype", "data")}
     if world == 1 and not args.no_serve:
         sv = run_serve(args, duration=20.0)
         line["serve"] = {"jobs_per_h": sv["value"], "p50_s": sv["p50_s"], "p99_s": sv["p99_s"],
-                         "runs": sv["runs"], "config": sv["config"]}
+                         "precision": sv["precision"], "runs": sv["runs"],
+                         "config": sv["config"]}
     if world == 1 and not args.no_cpu_baseline:
         r = cpu_oracle_rate(args.workload, 20.0)
         line["cpu_baseline"] = {"value": r["cell_updates_per_s"], "unit": "cell-updates/s",

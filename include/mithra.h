@@ -434,12 +434,27 @@ mithra_status mithra_plane_power_noalloc(const mithra_grid* grid, double gamma0,
                                          int32_t k_plane, double* p_lab, void* cuda_stream);
 
 /* Batched stepping (the served and batched forms): a batch advances all its
- * member simulations together.  Each member keeps its own stream, buffers and
- * launch choices; the batch captures one CUDA graph that forks from the
- * batch's stream to every member stream, runs two steps of every member and
- * joins back, and replays it for every pair of steps (two steps return each
- * member's ping-pong buffers to their state at capture).  The graph is
- * captured again after the membership changes or after an odd step count.
+ * member simulations together, two steps per replay of one captured CUDA
+ * graph (two steps return each member's ping-pong buffers to their state at
+ * capture).  Two forms of the graph:
+ *   - fused: a step is eight launches whatever the number of members (for
+ *     every 40 members of the particle step and 96 of the grid phases one
+ *     more): the boundary rest, the potential update, the power sample, the
+ *     numbering of the members' tiles, the particle step, the two scan
+ *     passes of the re-sort and the scatter, each one kernel over a work list
+ *     that spans all members (flat block lists for the grid phases,
+ *     persistent CTAs taking every member's tiles from one counter for the
+ *     particle step), with each member's arguments in the launch's
+ *     parameter space or a device table.  The members must share the
+ *     precision form, undulator type and boundary order, use the register
+ *     z-marching update and the tiled particle step, and record no seed,
+ *     spectrum or bunch samples;
+ *   - per member: the graph forks from the batch's stream to every member
+ *     stream and runs each member's own launches, so that one member's
+ *     memory-bound potential update overlaps another's particle step.
+ * The graph is captured again after the membership changes, after an odd
+ * step count, or after a member's launch parameters change (power sampling,
+ * tuning, fields set from the host).
  * A member must have been created with its own stream (cuda_stream NULL, or
  * a non-default stream other than the batch's); while in a batch it is
  * stepped only by mithra_batch_step (mithra_step returns MITHRA_EBUSY), and
@@ -454,6 +469,21 @@ mithra_status mithra_batch_remove(mithra_batch* batch, mithra_sim* sim);
 mithra_status mithra_batch_step(mithra_batch* batch, int64_t n);
 /* Waits for the batch and returns the first failing member's status. */
 mithra_status mithra_batch_sync(mithra_batch* batch);
+/* mode 0: always per member; 1: fused whenever the members allow it; 2
+ * (the default): fused when they allow it and their average size is below
+ * 5e5 cell updates per step (a particle counted as 4), where the launches
+ * dominate (measured: 256 members of 32 x 32 x 128 cells and 2000 particles
+ * 3.8x faster fused; members of several million cells 2-5 % faster per
+ * member).  mithra_batch_get_mode reports the form of the graph captured
+ * last (1 fused, 0 per member). */
+mithra_status mithra_batch_set_mode(mithra_batch* batch, int32_t fused);
+/* Graph captures of the batch so far (each membership change, odd step
+ * count or member parameter change costs one at the next step), how many
+ * took the fused form, and their summed host time [s]; any pointer may be
+ * NULL. */
+mithra_status mithra_batch_stats(const mithra_batch* batch, int64_t* captures,
+                                 int64_t* fused_captures, double* capture_seconds);
+mithra_status mithra_batch_get_mode(const mithra_batch* batch, int32_t* fused);
 int32_t mithra_batch_size(const mithra_batch* batch);
 const char* mithra_batch_last_error(const mithra_batch* batch);
 mithra_status mithra_batch_destroy(mithra_batch* batch);

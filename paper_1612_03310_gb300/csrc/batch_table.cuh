@@ -1,0 +1,67 @@
+// batch_table.cuh -- argument sets of one simulation's step, as the kernels
+// read them: PushArgs for the tiled particle step (a kernel parameter for one
+// simulation or a group of batch members, in param space), and the table
+// entry of a batch member (BatchMember, BatchMaps), written by the host once
+// per membership and step parity.
+#pragma once
+#include <cuda.h>
+
+#include "common.cuh"
+
+namespace mithra {
+
+template <typename T, typename U>
+struct PushArgs {
+  PicP<T> p;
+  StepState* st;
+  const V4<T>* pn;  // psi^{n+1}
+  const V4<T>* D;   // increment
+  V4<T>* src;
+  Parts<T, U> P;
+  const int* offset;
+  const int* tiles;
+  int* count;
+  int* key;
+  int* rank;
+  long long* lost_ctr;
+  long long np;
+};
+
+template <typename T, typename U>
+struct BatchMember {
+  StencilP<T> sp;
+  PicP<T> pp;  // pp.plo: lo parts of the level E and B come from
+  V4<T>* P0;   // psi^n
+  V4<T>* P1;   // receives psi^{n+1}
+  LoV4* L0;
+  LoV4* L1;
+  V4<T>* D;
+  V4<T>* S;
+  Parts<T, U> A, B;  // particles in use, and the buffer of the re-sort
+  int* offset;
+  int* tiles;
+  int* count;
+  int* key;
+  int* rank;
+  int4* scan_part;
+  StepState* st;
+  double* power_acc;    // record base minus the first recorded step
+  long long power_end;  // first + capacity (0: no recording)
+  double g0, b0;        // frame of the power transformation
+  long long np;
+  int lz;
+  int power_plane;
+  int nkeys;
+  int scan_nb;
+  int sparse_below;
+  int fused_mur;  // first-order Mur at the x faces inside the z-marching loop
+};
+
+// Tensor maps of a member's particle step, collected on the host (the
+// kernels take them in their parameter space).
+struct BatchMaps {
+  CUtensorMap box;    // psi^{n+1}, 11^3 boxes
+  CUtensorMap box_d;  // increment, 11^3 boxes
+};
+
+}  // namespace mithra

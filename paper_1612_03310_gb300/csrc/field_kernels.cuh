@@ -264,8 +264,8 @@ __host__ __device__ inline long long rest_count(int nx, int ny, int nz) {
   return 2LL * nx * ny + 2LL * nx * (nz - 2) +
          (xhi_fused(nx) ? 0LL : (long long)(ny - 2) * (nz - 2));
 }
-__device__ inline bool rest_vertex(int nx, int ny, int nz, int* i, int* j, int* k) {
-  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+__device__ inline bool rest_vertex_at(long long t, int nx, int ny, int nz, int* i, int* j,
+                                      int* k) {
   const long long nxy = (long long)nx * ny;
   if (t < 2 * nxy) {  // z faces
     const long long r = t % nxy;
@@ -287,6 +287,32 @@ __device__ inline bool rest_vertex(int nx, int ny, int nz, int* i, int* j, int* 
   return false;
 }
 
+__device__ inline bool rest_vertex(int nx, int ny, int nz, int* i, int* j, int* k) {
+  return rest_vertex_at(blockIdx.x * (long long)blockDim.x + threadIdx.x, nx, ny, nz, i, j, k);
+}
+
+// Mur update of boundary vertex (i, j, k) (see k_mur_boundary).
+template <bool kLo, typename T, bool kTerms>
+__device__ __forceinline__ void mur_vertex(const StencilP<T>& p, const V4<T>* __restrict__ cur,
+                                           const LoV4* __restrict__ curlo,
+                                           V4<T>* __restrict__ nxt, LoV4* __restrict__ nxtlo,
+                                           V4<T>* __restrict__ D, V4<T>* __restrict__ src, int i,
+                                           int j, int k) {
+  const int qi = min(max(i, 1), p.nx - 2), qj = min(max(j, 1), p.ny - 2),
+            qk = min(max(k, 1), p.nz - 2);
+  const int mask = (qi != i) | ((qj != j) << 1) | ((qk != k) << 2);
+  const long long b = cidx(i, j, k, p.nx, p.nxy), q = cidx(qi, qj, qk, p.nx, p.nxy);
+  V4<T> dq_old, sq;
+  const V4<T> dq_new = interior_increment<kLo, T, kTerms>(p, cur, curlo, D, src, q, &dq_old, &sq);
+  const V4<T> db_old = D[b];
+  V4<T> db = mur_beta0(p, mask) * (dq_new - db_old) + dq_old;
+  if (p.mur2 && (mask & (mask - 1)) == 0) db = db + mur2_terms(p, cur, mask, b, q);
+  if (!p.space_charge) db.w = (T)0;
+  D[b] = db;
+  store_level<kLo>(cur, curlo, nxt, nxtlo, b, db);
+  src[b] = v4((T)0, (T)0, (T)0, (T)0);
+}
+
 // With kRest, only the vertices of rest_vertex (1-D launch of rest_count
 // threads).  kTerms: the interior update is the z-marching form, whose
 // arithmetic D_q^+ is recomputed with.
@@ -302,19 +328,7 @@ __global__ void __launch_bounds__(256) k_mur_boundary(StencilP<T> p,
   if (kRest ? !rest_vertex(p.nx, p.ny, p.nz, &i, &j, &k)
             : !boundary_vertex(p.nx, p.ny, p.nz, &i, &j, &k))
     return;
-  const int qi = min(max(i, 1), p.nx - 2), qj = min(max(j, 1), p.ny - 2),
-            qk = min(max(k, 1), p.nz - 2);
-  const int mask = (qi != i) | ((qj != j) << 1) | ((qk != k) << 2);
-  const long long b = cidx(i, j, k, p.nx, p.nxy), q = cidx(qi, qj, qk, p.nx, p.nxy);
-  V4<T> dq_old, sq;
-  const V4<T> dq_new = interior_increment<kLo, T, kTerms>(p, cur, curlo, D, src, q, &dq_old, &sq);
-  const V4<T> db_old = D[b];
-  V4<T> db = mur_beta0(p, mask) * (dq_new - db_old) + dq_old;
-  if (p.mur2 && (mask & (mask - 1)) == 0) db = db + mur2_terms(p, cur, mask, b, q);
-  if (!p.space_charge) db.w = (T)0;
-  D[b] = db;
-  store_level<kLo>(cur, curlo, nxt, nxtlo, b, db);
-  src[b] = v4((T)0, (T)0, (T)0, (T)0);
+  mur_vertex<kLo, T, kTerms>(p, cur, curlo, nxt, nxtlo, D, src, i, j, k);
 }
 
 // Launch shape of k_mur_boundary.
@@ -361,11 +375,11 @@ __device__ __forceinline__ void zloop_body(const StencilP<T>& p, const V4<T>* __
                                            const LoV4* __restrict__ curlo,
                                            V4<T>* __restrict__ nxt, LoV4* __restrict__ nxtlo,
                                            V4<T>* __restrict__ D, V4<T>* __restrict__ src,
-                                           int lz) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int j = blockIdx.y * blockDim.y + threadIdx.y;
-  const int kb = max((int)blockIdx.z * lz, 1);
-  const int ke = min((int)blockIdx.z * lz + lz, p.nz - 1);
+                                           int lz, int bx, int by, int bz) {
+  const int i = bx * 32 + threadIdx.x;
+  const int j = by * 8 + threadIdx.y;
+  const int kb = max(bz * lz, 1);
+  const int ke = min(bz * lz + lz, p.nz - 1);
   const bool xb = kMur && (i == 0 || (i == p.nx - 1 && xhi_fused(p.nx)));
   const bool active = kb < ke && j >= 1 && j <= p.ny - 2 && ((i >= 1 && i <= p.nx - 2) || xb);
   unsigned live = 0;
@@ -422,7 +436,8 @@ __global__ void __launch_bounds__(256) k_potential_zloop(StencilP<T> p,
                                                          LoV4* __restrict__ nxtlo,
                                                          V4<T>* __restrict__ D,
                                                          V4<T>* __restrict__ src, int lz) {
-  zloop_body<kLo, T, false>(p, cur, curlo, nxt, nxtlo, D, src, lz);
+  zloop_body<kLo, T, false>(p, cur, curlo, nxt, nxtlo, D, src, lz, blockIdx.x, blockIdx.y,
+                            blockIdx.z);
 }
 
 // The same with first-order Mur fused; the register caps keep the
@@ -433,7 +448,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? (kLo ? 3 : 4) : (kLo ? 1
                            const LoV4* __restrict__ curlo, V4<T>* __restrict__ nxt,
                            LoV4* __restrict__ nxtlo, V4<T>* __restrict__ D,
                            V4<T>* __restrict__ src, int lz) {
-  zloop_body<kLo, T, true>(p, cur, curlo, nxt, nxtlo, D, src, lz);
+  zloop_body<kLo, T, true>(p, cur, curlo, nxt, nxtlo, D, src, lz, blockIdx.x, blockIdx.y,
+                           blockIdx.z);
 }
 
 // Seed field (Sec. "Seed Field"): a plane wave (this kernel) or a Gaussian
@@ -865,15 +881,15 @@ __global__ void k_sample(PicP<T> p, const V4<T>* __restrict__ pn, const V4<T>* _
 // Radiated power through vertex plane kp in the lab frame, FP64 accumulation:
 // E'_x = g0 (E_x + b0 c B_y), E'_y = g0 (E_y - b0 c B_x),
 // B'_x = g0 (B_x - b0 E_y / c), B'_y = g0 (B_y + b0 E_x / c),
-// P = sum (E'_x B'_y - E'_y B'_x) / mu0 dx dy over interior (i, j).
-// The result is added to *acc (zeroed by the caller); slot_from_state makes
-// the kernel write into acc[state->n] (per-step recording) when below cap.
+// P = sum (E'_x B'_y - E'_y B'_x) / mu0 dx dy over interior (i, j), the
+// part of block bidx of nblocks.
 template <typename T>
-__global__ void __launch_bounds__(256) k_power(PicP<T> p, const V4<T>* __restrict__ pn,
-                                               const V4<T>* __restrict__ D, int kp, double g0,
-                                               double b0, double* __restrict__ acc,
-                                               const StepState* __restrict__ st, long long cap,
-                                               int slot_from_state, int* __restrict__ err) {
+__device__ __forceinline__ void power_body(const PicP<T>& p, const V4<T>* __restrict__ pn,
+                                           const V4<T>* __restrict__ D, int kp, double g0,
+                                           double b0, double* __restrict__ acc,
+                                           const StepState* __restrict__ st, long long cap,
+                                           int slot_from_state, int* __restrict__ err, int bidx,
+                                           int nblocks) {
   long long slot = 0;
   if (slot_from_state) {
     slot = st->n;
@@ -882,7 +898,7 @@ __global__ void __launch_bounds__(256) k_power(PicP<T> p, const V4<T>* __restric
   const int nin = (p.nx - 2) * (p.ny - 2);
   const double b0c = b0 / kC;  // one FP64 division per thread, not two per vertex
   double part = 0.0;
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nin; t += gridDim.x * blockDim.x) {
+  for (int t = bidx * blockDim.x + threadIdx.x; t < nin; t += nblocks * blockDim.x) {
     const int i = 1 + t % (p.nx - 2);
     const int j = 1 + t / (p.nx - 2);
     T E[3], B[3];
@@ -907,6 +923,17 @@ __global__ void __launch_bounds__(256) k_power(PicP<T> p, const V4<T>* __restric
       atomicAdd(acc + slot, v);
     }
   }
+}
+
+// The result is added to *acc (zeroed by the caller); slot_from_state makes
+// the kernel write into acc[state->n] (per-step recording) when below cap.
+template <typename T>
+__global__ void __launch_bounds__(256) k_power(PicP<T> p, const V4<T>* __restrict__ pn,
+                                               const V4<T>* __restrict__ D, int kp, double g0,
+                                               double b0, double* __restrict__ acc,
+                                               const StepState* __restrict__ st, long long cap,
+                                               int slot_from_state, int* __restrict__ err) {
+  power_body(p, pn, D, kp, g0, b0, acc, st, cap, slot_from_state, err, blockIdx.x, gridDim.x);
 }
 
 }  // namespace mithra

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -19,6 +20,7 @@
 #include "particle_kernels.cuh"
 #include "tile_push.cuh"
 #include "diag.cuh"
+#include "batch_kernels.cuh"
 
 using namespace mithra;
 
@@ -112,6 +114,8 @@ struct mithra_sim {
   double prof_ms[8] = {0};
   int64_t prof_n[8] = {0};
 };
+
+void batch_mark_dirty(mithra_batch* b);  // defined with the batch
 
 namespace {
 
@@ -564,9 +568,24 @@ mithra_status launch_step(mithra_sim* s) {
         if constexpr (push_form_lo<T, U>())
           if (lo) kern = opt ? k_push_tiled<true, T, U, true> : k_push_tiled<false, T, U, true>;
         if (!kern) return fail(s, MITHRA_EINVAL, "no particle-step form for this precision");
-        kern<<<s->push_grid, 256, tile_smem_bytes<T, U>(), s->stream>>>(
-            s->tm_box[1 - s->cur], s->tm_box_d, pp, s->dstate, P1, Dn, S, A, s->offset, s->tiles,
-            s->count, s->key, s->rank, &s->dstate->n_lost, s->np);
+        PushParams<T, U, false> prm;
+        prm.tm_pn = s->tm_box[1 - s->cur];
+        prm.tm_d = s->tm_box_d;
+        PushArgs<T, U>& pa = prm.args;
+        pa.p = pp;
+        pa.st = s->dstate;
+        pa.pn = P1;
+        pa.D = Dn;
+        pa.src = S;
+        pa.P = A;
+        pa.offset = s->offset;
+        pa.tiles = s->tiles;
+        pa.count = s->count;
+        pa.key = s->key;
+        pa.rank = s->rank;
+        pa.lost_ctr = &s->dstate->n_lost;
+        pa.np = s->np;
+        kern<<<s->push_grid, 256, tile_smem_bytes<T, U>(), s->stream>>>(prm);
       } else {
         decltype(&k_push<false, T, U, kAnyLo>) kern = nullptr;
         if constexpr (push_form_plain<T, U>())
@@ -1001,11 +1020,14 @@ mithra_status mithra_create(const mithra_grid* grid, const mithra_undulator* und
 }
 
 namespace {
+// Drops the captured steps of s (and of the batch s belongs to: a launch
+// parameter of s changed).
 void drop_step_graphs(mithra_sim* s) {
   for (auto& e : s->step_exec) {
     if (e) cudaGraphExecDestroy(e);
     e = nullptr;
   }
+  if (s->in_batch) batch_mark_dirty(s->in_batch);
 }
 
 // Captures two steps from the current state (they bring the level and
@@ -1633,7 +1655,26 @@ struct mithra_batch {
   cudaEvent_t done = nullptr;
   std::vector<cudaEvent_t> joins;
   std::string err;
+  // fused form (batch_kernels.cuh): one launch per phase over all members
+  int mode = 2;           // mithra_batch_set_mode: 0 per member, 1 fused, 2 automatic
+  bool fused_now = false;  // the captured graph is the fused form
+  void* d_table = nullptr;  // member tables of the two captured steps
+  size_t table_bytes = 0;
+  int* d_blk = nullptr;     // block prefixes, kBPCount x (M + 1)
+  size_t blk_bytes = 0;
+  int* d_pref = nullptr;    // the particle step's tile prefix (M + 1) and counter
+  size_t pref_bytes = 0;
+  int* d_zblk = nullptr;    // boundary and update block prefixes, per group from 0
+  size_t zblk_bytes = 0;
+  int push_grid = 0;
+  // captures so far, their host time, and how many were fused
+  int64_t captures = 0, fused_captures = 0;
+  double capture_s = 0.0;
 };
+
+void batch_mark_dirty(mithra_batch* b) {
+  if (b) b->dirty = true;
+}
 
 namespace {
 
@@ -1648,8 +1689,282 @@ void drop_graph(mithra_batch* b) {
   b->dirty = true;
 }
 
+// Whether every member can take the fused form: one precision form and
+// undulator type, the register z-marching update, the tiled particle step
+// with its tensor maps, and none of the per-step extras the batched kernels
+// leave out (seed, spectrum, bunch recording).
+// Average work of a member in cell-update equivalents (a particle step costs
+// about four cell updates on GB300), the automatic mode's measure of size.
+double member_work(const mithra_batch* b) {
+  double w = 0.0;
+  for (const mithra_sim* s : b->sims)
+    w += (double)ncell_of(&s->g) + 4.0 * (double)s->np * s->g.n_sub;
+  return w / (double)b->sims.size();
+}
+
+// Below this average member size the fused form is faster (measured on
+// GB300: 64 and 256 members of 32 x 32 x 128 cells and 2000 particles ran
+// 1.3x and 3.8x faster fused; members of 0.3 M cells and 0.2 M particles, and
+// the c4 design sweep of 4 M cells and 2.3 M particles per member, ran 5 %
+// and 2 % faster as one launch sequence per member, whose members' phases
+// overlap on the device).
+constexpr double kFuseBelowWork = 5.0e5;
+
+bool fusable(const mithra_batch* b) {
+  if (b->mode == 0 || b->sims.empty()) return false;
+  if (b->mode == 2 && member_work(b) >= kFuseBelowWork) return false;
+  const mithra_sim* f = b->sims[0];
+  for (const mithra_sim* s : b->sims) {
+    if (s->prec != f->prec || s->u.type != f->u.type || s->g.boundary != f->g.boundary)
+      return false;
+    if (s->stencil_variant != 2 || s->push_variant != 1 || !s->have_tm) return false;
+    if (s->seed.on || s->spec_nf > 0 || s->bunch_every > 0) return false;
+  }
+  return true;
+}
+
+mithra_status grow(mithra_batch* b, void** p, size_t* have, size_t need) {
+  if (*have >= need) return MITHRA_OK;
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  *have = 0;
+  if (cudaMalloc(p, need) != cudaSuccess) return bfail(b, MITHRA_ENOMEM, "batch table allocation");
+  *have = need;
+  return MITHRA_OK;
+}
+
+// Member table entry of s for the step that starts with level buffer c and
+// particle buffer pb.
+template <typename T, typename U>
+BatchMember<T, U> member_entry(mithra_sim* s, int c, int pb) {
+  BatchMember<T, U> m{};
+  m.sp = make_stencil<T>(s->g);
+  m.pp = make_pic<T>(s);
+  m.P0 = static_cast<V4<T>*>(s->P[c]);
+  m.P1 = static_cast<V4<T>*>(s->P[1 - c]);
+  m.L0 = static_cast<LoV4*>(s->PL[c]);
+  m.L1 = static_cast<LoV4*>(s->PL[1 - c]);
+  m.pp.plo = m.L1;
+  m.D = static_cast<V4<T>*>(s->D);
+  m.S = static_cast<V4<T>*>(s->S);
+  m.A = parts_of<T, U>(s, pb);
+  m.B = parts_of<T, U>(s, 1 - pb);
+  m.offset = s->offset;
+  m.tiles = s->tiles;
+  m.count = s->count;
+  m.key = s->key;
+  m.rank = s->rank;
+  m.scan_part = s->scan_part;
+  m.st = s->dstate;
+  m.power_acc = s->d_power_rec ? s->d_power_rec - s->power_first : nullptr;
+  m.power_end = s->power_cap > 0 ? s->power_first + s->power_cap : 0;
+  m.g0 = s->u.gamma0;
+  m.b0 = std::sqrt(1.0 - 1.0 / (s->u.gamma0 * s->u.gamma0));
+  m.np = s->np;
+  m.lz = s->lz;
+  m.power_plane = s->power_plane;
+  m.nkeys = s->nkeys;
+  m.scan_nb = (s->nkeys + 1 + kScanBlock - 1) / kScanBlock;
+  m.sparse_below = 0;  // the fused particle step stages every tile
+  m.fused_mur = s->g.boundary == 1;
+  return m;
+}
+
+// The particle step's arguments of a member table entry.
+template <typename T, typename U>
+PushArgs<T, U> push_args_of(const BatchMember<T, U>& m) {
+  PushArgs<T, U> a;
+  a.p = m.pp;
+  a.st = m.st;
+  a.pn = m.P1;
+  a.D = m.D;
+  a.src = m.S;
+  a.P = m.A;
+  a.offset = m.offset;
+  a.tiles = m.tiles;
+  a.count = m.count;
+  a.key = m.key;
+  a.rank = m.rank;
+  a.lost_ctr = &m.st->n_lost;
+  a.np = m.np;
+  return a;
+}
+
+template <typename T, typename U>
+mithra_status capture_fused_typed(mithra_batch* b) {
+  const int M = (int)b->sims.size();
+  std::vector<BatchMember<T, U>> tab(2 * (size_t)M);
+  std::vector<BatchMaps> maps(2 * (size_t)M);
+  std::vector<int> blk((size_t)kBPCount * (M + 1), 0);
+  for (int k = 0; k < M; ++k) {
+    mithra_sim* s = b->sims[k];
+    for (int t = 0; t < 2; ++t) {
+      const int c = t == 0 ? s->cur : 1 - s->cur;
+      const int pb = t == 0 ? s->pb : 1 - s->pb;
+      tab[(size_t)t * M + k] = member_entry<T, U>(s, c, pb);
+      maps[(size_t)t * M + k].box = s->tm_box[1 - c];
+      maps[(size_t)t * M + k].box_d = s->tm_box_d;
+    }
+    const mithra_grid& g = s->g;
+    const long long nb[kBPCount] = {
+        (long long)blocks_for(batch_mur_count(g.nx, g.ny, g.nz, g.boundary == 1), 256),
+        (long long)((g.nx + 31) / 32) * ((g.ny + 7) / 8) * ((g.nz + s->lz - 1) / s->lz),
+        s->power_cap > 0 ? kBatchPowerBlocks : 0,
+        (long long)((s->nkeys + 1 + kScanBlock - 1) / kScanBlock),
+        s->np > 0 ? (long long)blocks_for(s->np, 256) : 0};
+    for (int ph = 0; ph < kBPCount; ++ph) {
+      const long long v = blk[(size_t)ph * (M + 1) + k] + nb[ph];
+      if (v >= (1LL << 31)) return bfail(b, MITHRA_EINVAL, "batch work list exceeds 2^31 blocks");
+      blk[(size_t)ph * (M + 1) + k + 1] = (int)v;
+    }
+  }
+  mithra_status st = grow(b, &b->d_table, &b->table_bytes, sizeof(BatchMember<T, U>) * tab.size());
+  if (st == MITHRA_OK)
+    st = grow(b, reinterpret_cast<void**>(&b->d_blk), &b->blk_bytes, sizeof(int) * blk.size());
+  const int npg = (M + kPushGroup - 1) / kPushGroup;
+  if (st == MITHRA_OK)
+    st = grow(b, reinterpret_cast<void**>(&b->d_pref), &b->pref_bytes,
+              sizeof(int) * (size_t)(M + 2 * npg));
+  // block prefixes of the boundary and update phases, restarted at 0 for
+  // each group of kZGroup members (M + 1 per group's entries)
+  const int ngroups = (M + kZGroup - 1) / kZGroup;
+  std::vector<int> zblk(2 * (size_t)(M + ngroups), 0);
+  for (int pi = 0; pi < 2; ++pi) {
+    const int ph = pi == 0 ? kBPMur : kBPZ;
+    for (int g0 = 0; g0 < M; g0 += kZGroup) {
+      const int Mg = std::min(kZGroup, M - g0);
+      int* z = zblk.data() + (size_t)pi * (M + ngroups) + g0 + g0 / kZGroup;
+      for (int k = 0; k <= Mg; ++k) z[k] = blk[(size_t)ph * (M + 1) + g0 + k] - blk[(size_t)ph * (M + 1) + g0];
+    }
+  }
+  if (st == MITHRA_OK)
+    st = grow(b, reinterpret_cast<void**>(&b->d_zblk), &b->zblk_bytes, sizeof(int) * zblk.size());
+  if (st != MITHRA_OK) return st;
+  if (cudaMemcpy(b->d_zblk, zblk.data(), sizeof(int) * zblk.size(), cudaMemcpyHostToDevice) !=
+      cudaSuccess)
+    return bfail(b, MITHRA_ECUDA, "batch table upload");
+  // the tables replace the ones the previous graph read: after its work
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess ||
+      cudaMemcpy(b->d_table, tab.data(), sizeof(BatchMember<T, U>) * tab.size(),
+                 cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(b->d_blk, blk.data(), sizeof(int) * blk.size(), cudaMemcpyHostToDevice) !=
+          cudaSuccess)
+    return bfail(b, MITHRA_ECUDA, "batch table upload");
+  const bool opt = b->sims[0]->u.type == 1;
+  const bool lo = b->sims[0]->PL[0] != nullptr;
+  constexpr bool kAnyLo = sizeof(T) == 4;  // compensated levels exist for FP32 fields only
+  const int smem = tile_smem_bytes<T, U>();
+  auto kpush = opt ? (lo ? k_push_tiled<true, T, U, kAnyLo, true>
+                        : k_push_tiled<true, T, U, false, true>)
+                   : (lo ? k_push_tiled<false, T, U, kAnyLo, true>
+                         : k_push_tiled<false, T, U, false, true>);
+  if (cudaFuncSetAttribute(kpush, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) !=
+      cudaSuccess)
+    return bfail(b, MITHRA_ECUDA, "batched particle step: shared memory attribute");
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kpush, 256, smem) != cudaSuccess ||
+      per_sm < 1)
+    return bfail(b, MITHRA_ECUDA, "batched particle step does not fit an SM");
+  b->push_grid = b->sims[0]->n_sm * per_sm;
+  auto total = [&](int ph) { return blk[(size_t)ph * (M + 1) + M]; };
+  const int* dblk = b->d_blk;
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return bfail(b, MITHRA_ECUDA, std::string("begin capture: ") + cudaGetErrorString(e));
+  for (int t = 0; t < 2; ++t) {
+    const BatchMember<T, U>* mem = static_cast<const BatchMember<T, U>*>(b->d_table) + (size_t)t * M;
+    cudaStream_t q = b->stream;
+    // boundary and potential update, one launch each per group of up to
+    // kZGroup members (their arguments in the launch's parameter space);
+    // the groups' block numbers start at the group's first member
+    for (int g0 = 0; g0 < M; g0 += kZGroup) {
+      const int Mg = std::min(kZGroup, M - g0);
+      ZParams<T> zp;
+      for (int k = 0; k < Mg; ++k) {
+        const BatchMember<T, U>& e = tab[(size_t)t * M + g0 + k];
+        zp.m[k] = ZMember<T>{e.sp, e.P0, e.L0, e.P1, e.L1, e.D, e.S, e.lz, e.fused_mur};
+      }
+      zp.M = Mg;
+      for (int ph : {(int)kBPMur, (int)kBPZ}) {
+        const int* pb = blk.data() + (size_t)ph * (M + 1);
+        const int nblk = pb[g0 + Mg] - pb[g0];
+        if (nblk == 0) continue;
+        zp.blk = b->d_zblk + (size_t)(ph == kBPMur ? 0 : 1) * (M + ngroups) + g0 + g0 / kZGroup;
+        if (ph == kBPMur) {
+          if (lo) kb_mur<kAnyLo, T><<<nblk, 256, 0, q>>>(zp);
+          else kb_mur<false, T><<<nblk, 256, 0, q>>>(zp);
+        } else if (b->sims[0]->g.boundary == 1) {
+          if (lo) kb_potential<kAnyLo, T, true><<<nblk, dim3(32, 8), 0, q>>>(zp);
+          else kb_potential<false, T, true><<<nblk, dim3(32, 8), 0, q>>>(zp);
+        } else {
+          if (lo) kb_potential<kAnyLo, T, false><<<nblk, dim3(32, 8), 0, q>>>(zp);
+          else kb_potential<false, T, false><<<nblk, dim3(32, 8), 0, q>>>(zp);
+        }
+      }
+    }
+    if (total(kBPPow) > 0)
+      kb_power<T, U><<<total(kBPPow), 256, 0, q>>>(mem, dblk + kBPPow * (M + 1), M);
+    // the particle step, one launch per group of up to kPushGroup members
+    // (their arguments in the launch's parameter space)
+    for (int g0 = 0; g0 < M; g0 += kPushGroup) {
+      const int Mg = std::min(kPushGroup, M - g0);
+      int* pref = b->d_pref + g0 + 2 * (g0 / kPushGroup);  // Mg + 1 entries, then the counter
+      int* work = pref + Mg + 1;
+      kb_tile_prefix<T, U><<<1, 1024, 0, q>>>(mem + g0, Mg, pref, work);
+      PushParams<T, U, true> prm;
+      for (int k = 0; k < Mg; ++k) {
+        prm.m[k] = push_args_of(tab[(size_t)t * M + g0 + k]);
+        prm.box[k] = maps[(size_t)t * M + g0 + k].box;
+        prm.box_d[k] = maps[(size_t)t * M + g0 + k].box_d;
+      }
+      prm.pref = pref;
+      prm.work = work;
+      prm.M = Mg;
+      kpush<<<b->push_grid, 256, smem, q>>>(prm);
+    }
+    kb_scan_partials<T, U><<<total(kBPScan), kScanBlock, 0, q>>>(mem, dblk + kBPScan * (M + 1), M);
+    kb_scan_final<T, U><<<total(kBPScan), kScanBlock, 0, q>>>(mem, dblk + kBPScan * (M + 1), M);
+    if (total(kBPScat) > 0)
+      kb_scatter<T, U><<<total(kBPScat), 256, 0, q>>>(mem, dblk + kBPScat * (M + 1), M);
+  }
+  cudaError_t le = cudaGetLastError();
+  e = cudaStreamEndCapture(b->stream, &graph);
+  if (le != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return bfail(b, MITHRA_ECUDA, std::string("batched launch: ") + cudaGetErrorString(le));
+  }
+  if (e != cudaSuccess) return bfail(b, MITHRA_ECUDA, std::string("end capture: ") + cudaGetErrorString(e));
+  e = cudaGraphInstantiate(&b->exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return bfail(b, MITHRA_ECUDA, std::string("instantiate: ") + cudaGetErrorString(e));
+  b->fused_now = true;
+  b->dirty = false;
+  return MITHRA_OK;
+}
+
+mithra_status capture_graph(mithra_batch* b);
+
+// Captures the batch's two-step graph in the fused or the per-member form,
+// counting the captures and their host time.
 mithra_status capture(mithra_batch* b) {
+  const auto t0 = std::chrono::steady_clock::now();
   drop_graph(b);
+  b->fused_now = false;
+  mithra_status st;
+  if (fusable(b))
+    st = with_types(b->sims[0]->prec, [&](auto tt, auto uu) {
+      TYPES_OF(tt, uu);
+      return capture_fused_typed<T, U>(b);
+    });
+  else
+    st = capture_graph(b);
+  b->captures += 1;
+  b->fused_captures += b->fused_now ? 1 : 0;
+  b->capture_s += std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  return st;
+}
+
+mithra_status capture_graph(mithra_batch* b) {
   while (b->joins.size() < b->sims.size()) {
     cudaEvent_t e;
     if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
@@ -1817,6 +2132,31 @@ mithra_status mithra_batch_sync(mithra_batch* b) {
   return MITHRA_OK;
 }
 
+mithra_status mithra_batch_set_mode(mithra_batch* b, int32_t fused) {
+  if (!b) return bfail(nullptr, MITHRA_EINVAL, "batch is NULL");
+  if (fused < 0 || fused > 2) return bfail(b, MITHRA_EINVAL, "mode must be 0, 1 or 2");
+  if (b->mode != fused) {
+    b->mode = fused;
+    drop_graph(b);
+  }
+  return MITHRA_OK;
+}
+
+mithra_status mithra_batch_get_mode(const mithra_batch* b, int32_t* fused) {
+  if (!b || !fused) return bfail(nullptr, MITHRA_EINVAL, "batch or out is NULL");
+  *fused = b->fused_now ? 1 : 0;
+  return MITHRA_OK;
+}
+
+mithra_status mithra_batch_stats(const mithra_batch* b, int64_t* captures,
+                                 int64_t* fused_captures, double* capture_seconds) {
+  if (!b) return bfail(nullptr, MITHRA_EINVAL, "batch is NULL");
+  if (captures) *captures = b->captures;
+  if (fused_captures) *fused_captures = b->fused_captures;
+  if (capture_seconds) *capture_seconds = b->capture_s;
+  return MITHRA_OK;
+}
+
 int32_t mithra_batch_size(const mithra_batch* b) { return b ? (int32_t)b->sims.size() : 0; }
 
 const char* mithra_batch_last_error(const mithra_batch* b) {
@@ -1828,6 +2168,10 @@ mithra_status mithra_batch_destroy(mithra_batch* b) {
   cudaStreamSynchronize(b->stream);
   for (mithra_sim* s : b->sims) s->in_batch = nullptr;
   drop_graph(b);
+  if (b->d_table) cudaFree(b->d_table);
+  if (b->d_blk) cudaFree(b->d_blk);
+  if (b->d_pref) cudaFree(b->d_pref);
+  if (b->d_zblk) cudaFree(b->d_zblk);
   for (cudaEvent_t e : b->joins) cudaEventDestroy(e);
   if (b->fork) cudaEventDestroy(b->fork);
   if (b->done) cudaEventDestroy(b->done);

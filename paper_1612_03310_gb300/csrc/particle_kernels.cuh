@@ -592,11 +592,11 @@ __device__ inline void tile_class(int c, int t, int nkeys, int sparse_below, int
   *sparse = (nonempty && c < sparse_below) ? 1 : 0;
 }
 
-__global__ void __launch_bounds__(kScanBlock) k_scan_partials(const int* __restrict__ count,
-                                                              int nkeys, int sparse_below,
-                                                              int4* __restrict__ part) {
+__device__ __forceinline__ void scan_partials_body(const int* __restrict__ count, int nkeys,
+                                                   int sparse_below, int4* __restrict__ part,
+                                                   int bidx) {
   __shared__ int ws[32];
-  const int t = blockIdx.x * kScanBlock + threadIdx.x;
+  const int t = bidx * kScanBlock + threadIdx.x;
   const int c = (t <= nkeys) ? count[t] : 0;
   int dn, sp;
   tile_class(c, t, nkeys, sparse_below, &dn, &sp);
@@ -604,16 +604,20 @@ __global__ void __launch_bounds__(kScanBlock) k_scan_partials(const int* __restr
   block_exclusive_scan(c, ws, &tot);
   block_exclusive_scan(dn, ws, &nd);
   block_exclusive_scan(sp, ws, &ns);
-  if (threadIdx.x == 0) part[blockIdx.x] = make_int4(tot, nd, ns, 0);
+  if (threadIdx.x == 0) part[bidx] = make_int4(tot, nd, ns, 0);
 }
 
-__global__ void __launch_bounds__(kScanBlock) k_scan_final(int* __restrict__ count,
-                                                           int* __restrict__ offset,
-                                                           int* __restrict__ tiles, int nkeys,
-                                                           int sparse_below,
-                                                           const int4* __restrict__ part,
-                                                           int nblocks, StepState* __restrict__ st,
-                                                           int advance) {
+__global__ void __launch_bounds__(kScanBlock) k_scan_partials(const int* __restrict__ count,
+                                                              int nkeys, int sparse_below,
+                                                              int4* __restrict__ part) {
+  scan_partials_body(count, nkeys, sparse_below, part, blockIdx.x);
+}
+
+__device__ __forceinline__ void scan_final_body(int* __restrict__ count, int* __restrict__ offset,
+                                                int* __restrict__ tiles, int nkeys,
+                                                int sparse_below, const int4* __restrict__ part,
+                                                int nblocks, StepState* __restrict__ st,
+                                                int advance, int bidx) {
   __shared__ int ws[32];
   __shared__ int base[3], total[3];
   // bases of this block from the block sums (nblocks <= kScanBlock)
@@ -622,10 +626,10 @@ __global__ void __launch_bounds__(kScanBlock) k_scan_final(int* __restrict__ cou
   const int bc = block_exclusive_scan(pv.x, ws, &all_c);
   const int bd = block_exclusive_scan(pv.y, ws, &all_d);
   const int bs = block_exclusive_scan(pv.z, ws, &all_s);
-  if (threadIdx.x == blockIdx.x) { base[0] = bc; base[1] = bd; base[2] = bs; }
+  if (threadIdx.x == bidx) { base[0] = bc; base[1] = bd; base[2] = bs; }
   if (threadIdx.x == 0) { total[0] = all_c; total[1] = all_d; total[2] = all_s; }
   __syncthreads();
-  const int t = blockIdx.x * kScanBlock + threadIdx.x;
+  const int t = bidx * kScanBlock + threadIdx.x;
   const int c = (t <= nkeys) ? count[t] : 0;
   int dn, sp;
   tile_class(c, t, nkeys, sparse_below, &dn, &sp);
@@ -639,7 +643,7 @@ __global__ void __launch_bounds__(kScanBlock) k_scan_final(int* __restrict__ cou
     if (dn) tiles[sd] = t;
     if (sp) tiles[ss] = t;
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (bidx == 0 && threadIdx.x == 0) {
     offset[nkeys + 1] = total[0];
     st->n_tiles = total[1];
     st->n_sparse = total[2];
@@ -647,6 +651,17 @@ __global__ void __launch_bounds__(kScanBlock) k_scan_final(int* __restrict__ cou
     st->work_sparse = 0;
     if (advance) st->n += 1;
   }
+}
+
+__global__ void __launch_bounds__(kScanBlock) k_scan_final(int* __restrict__ count,
+                                                           int* __restrict__ offset,
+                                                           int* __restrict__ tiles, int nkeys,
+                                                           int sparse_below,
+                                                           const int4* __restrict__ part,
+                                                           int nblocks, StepState* __restrict__ st,
+                                                           int advance) {
+  scan_final_body(count, offset, tiles, nkeys, sparse_below, part, nblocks, st, advance,
+                  blockIdx.x);
 }
 
 // Streaming load and store of a stored momentum (FF2 as one 8-byte word).
@@ -669,10 +684,10 @@ __device__ inline void stcs_u<FF2>(FF2* a, FF2 v) {
 
 // Moves every particle to offset[key] + rank in the other buffer.
 template <typename T, typename U>
-__global__ void k_scatter(Parts<T, U> a, Parts<T, U> b, long long np, const int* __restrict__ key,
-                          const int* __restrict__ rank, const int* __restrict__ offset) {
-  const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (q >= np) return;
+__device__ __forceinline__ void scatter_one(const Parts<T, U>& a, const Parts<T, U>& b,
+                                            long long q, const int* __restrict__ key,
+                                            const int* __restrict__ rank,
+                                            const int* __restrict__ offset) {
   // streaming loads and stores (the potential update in between evicts the
   // particles from L2 anyway): 39 instead of 45 us on c2
   const long long d = (long long)__ldcs(offset + __ldcs(key + q)) + __ldcs(rank + q);
@@ -684,6 +699,14 @@ __global__ void k_scatter(Parts<T, U> a, Parts<T, U> b, long long np, const int*
   stcs_u(b.uy + d, ldcs_u(a.uy + q));
   stcs_u(b.uz + d, ldcs_u(a.uz + q));
   __stcs(b.id + d, __ldcs(a.id + q));
+}
+
+template <typename T, typename U>
+__global__ void k_scatter(Parts<T, U> a, Parts<T, U> b, long long np, const int* __restrict__ key,
+                          const int* __restrict__ rank, const int* __restrict__ offset) {
+  const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (q >= np) return;
+  scatter_one(a, b, q, key, rank, offset);
 }
 
 // Copy-out in the original particle order: FP64 positions from (cell, f).

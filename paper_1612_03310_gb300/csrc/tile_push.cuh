@@ -24,6 +24,7 @@
 #include "common.cuh"
 #include "field_kernels.cuh"
 #include "particle_kernels.cuh"
+#include "batch_table.cuh"
 #include "tma.cuh"
 
 namespace mithra {
@@ -162,7 +163,7 @@ __device__ inline void deposit_rho_fixed(const PicP<T>& p, int* __restrict__ hi,
 // thread's next particle into the slot it read.
 template <bool kOpt, typename T, typename U, typename Gather, typename Frame, typename Dep,
           typename LdCell, typename LdFU, typename Next>
-__device__ inline void tile_particle(const PicP<T>& p, Parts<T, U>& P, long long q,
+__device__ inline void tile_particle(const PicP<T>& p, const Parts<T, U>& P, long long q,
                                      int* __restrict__ count, int* __restrict__ key,
                                      int* __restrict__ rank, long long* __restrict__ lost_ctr,
                                      Gather&& gather, Frame&& frame, Dep&& dep, LdCell&& ld_cell,
@@ -208,14 +209,47 @@ __device__ inline void tile_origin(const PicP<T>& p, int tile, int* i0, int* j0,
   *k0 = (tile / (p.ntx * p.nty)) * kTile;
 }
 
-template <bool kOpt, typename T, typename U, bool kLo = false>
-__global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 3 : 1)) k_push_tiled(
-    const __grid_constant__ CUtensorMap tm_pn, const __grid_constant__ CUtensorMap tm_d,
-    PicP<T> p, StepState* __restrict__ st, const V4<T>* __restrict__ pn,
-    const V4<T>* __restrict__ D, V4<T>* __restrict__ src, Parts<T, U> P,
-    const int* __restrict__ offset, const int* __restrict__ tiles, int* __restrict__ count,
-    int* __restrict__ key, int* __restrict__ rank, long long* __restrict__ lost_ctr,
-    long long np) {
+// Kernel parameters of the tiled particle step, all in param space (read
+// where used, like constants, instead of held in registers; the tensor maps
+// there too, so that no TMA unit can hold a stale copy of a map rewritten in
+// global memory): one simulation's arguments and tensor maps, or those of up
+// to kPushGroup batch members, whose non-empty tiles, numbered member after
+// member by pref, one counter hands out.
+constexpr int kPushGroup = 32;  // 32 x (688 + 256) B (FP64) of the 32 KB parameter space
+
+// Member of tile number w of a batch group: pref[m] <= w < pref[m+1].
+__device__ inline int member_of_tile(const int* __restrict__ pref, int M, int w) {
+  int lo = 0, hi = M - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (pref[mid] <= w) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <typename T, typename U, bool kBatch>
+struct PushParams;
+
+template <typename T, typename U>
+struct PushParams<T, U, false> {
+  CUtensorMap tm_pn;  // psi^{n+1}, 11^3 boxes
+  CUtensorMap tm_d;   // increment, 11^3 boxes
+  PushArgs<T, U> args;
+};
+
+template <typename T, typename U>
+struct PushParams<T, U, true> {
+  CUtensorMap box[kPushGroup];    // the members' psi^{n+1}, 11^3 boxes
+  CUtensorMap box_d[kPushGroup];  // their increments
+  PushArgs<T, U> m[kPushGroup];
+  const int* pref;  // pref[0 .. M]: tiles before each member
+  int* work;        // tile counter
+  int M;
+};
+
+template <bool kOpt, typename T, typename U, bool kLo = false, bool kBatch = false>
+__global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 3 : 1))
+    k_push_tiled(const __grid_constant__ PushParams<T, U, kBatch> prm) {
   extern __shared__ __align__(128) unsigned char smem[];
   V4<T>* sP = reinterpret_cast<V4<T>*>(smem);
   V4<T>* sD = reinterpret_cast<V4<T>*>(smem + tile_box_stride<T>());
@@ -235,16 +269,6 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 3 : 1)) k_push_tiled(
   T* sl_f = reinterpret_cast<T*>(smem + tile_slot_offset<T>() + 256 * 4) + threadIdx.x;
   U* sl_u = reinterpret_cast<U*>(smem + tile_slot_offset<T>() + 256 * (4 + 3 * (int)sizeof(T))) +
             threadIdx.x;
-  auto prefetch = [&](long long qq) {
-    cp_async<4>(sl_cell, P.cell + qq);
-    cp_async<sizeof(T)>(sl_f, P.fx + qq);
-    cp_async<sizeof(T)>(sl_f + 256, P.fy + qq);
-    cp_async<sizeof(T)>(sl_f + 512, P.fz + qq);
-    cp_async<sizeof(U)>(sl_u, P.ux + qq);
-    cp_async<sizeof(U)>(sl_u + 256, P.uy + qq);
-    cp_async<sizeof(U)>(sl_u + 512, P.uz + qq);
-    cp_async_commit();
-  };
   T* sJ = reinterpret_cast<T*>(sP);
   int* sRh = reinterpret_cast<int*>(sP);
   int* sRl = sRh + kTPC;
@@ -257,187 +281,262 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 3 : 1)) k_push_tiled(
     mbar_fence_init();
   }
   __syncthreads();
-  const int ntiles = st->n_tiles;
-  const double th = p.t0 + ((double)st->n + 0.5) * p.dt;
   uint32_t phase = 0;
-  for (;;) {
-    if (tid == 0) s_tile = atomicAdd(&st->work, 1);
-    __syncthreads();
-    const int t = s_tile;
-    if (t >= ntiles) break;
-    const int tile = tiles[t];
-    int i0, j0, k0;
-    tile_origin(p, tile, &i0, &j0, &k0);
-    if (tid == 0) {
-      fence_proxy_async_smem();
-      mbar_arrive_expect_tx(bar, 2u * tile_box_bytes<T>());
-      tma_load_4d(sP, &tm_pn, 0, i0 - 1, j0 - 1, k0 - 1, bar);
-      tma_load_4d(sD, &tm_d, 0, i0 - 1, j0 - 1, k0 - 1, bar);
-    }
-    // FP64 moving-window bookkeeping once per tile and sub-step
-    for (int m = tid; m < p.n_sub && m < kMaxFrames; m += blockDim.x)
-      s_frame[m] = und_frame(p, k0, th + m * p.dtb);
-    mbar_wait_bounded(bar, phase, &st->err);
-    phase ^= 1u;
-    // E and B at the tile's vertices
-    for (int v = tid; v < kTEC; v += blockDim.x) {
-      const int a = v % kTE, b = (v / kTE) % kTE, c = v / (kTE * kTE);
-      V4<T> E = v4((T)0, (T)0, (T)0, (T)0), B = E;
-      if (interior(i0 + a, j0 + b, k0 + c, p.nx, p.ny, p.nz))
-        eb_local<kLo>(p, sP, sD, ((c + 1) * kTP + (b + 1)) * kTP + (a + 1),
-                 cidx(i0 + a, j0 + b, k0 + c, p.nx, p.nxy), E, B);
-      sE[v] = E;
-      sB[v] = B;
-    }
-    __syncthreads();
-    const int beg = offset[tile], end = offset[tile + 1];
-    if (kPre && beg + tid < end) prefetch(beg + tid);
-    // fixed-point scale 2^b of the FP32 charge block (0: tiles of more
-    // than 2^16 particles deposit rho in global memory)
-    float sb = 0.0f;
-    int bsh = 0;
-    if (kF32) {
-      const int nt = end - beg;
-      bsh = min(21, 30 - (nt > 1 ? 32 - __clz(nt - 1) : 0));
-      if (nt <= 65536) sb = __int_as_float((127 + bsh) << 23);
-      for (int c = tid; c < 2 * kTPC; c += blockDim.x) sRh[c] = 0;
-    } else {
-      for (int c = tid; c < 4 * kTPC; c += blockDim.x) sJ[c] = (T)0;
-    }
-    __syncthreads();
-
-    for (int q = beg + tid; q < end; q += blockDim.x) {
-      if (kPre) cp_async_wait_all();
-      tile_particle<kOpt>(
-          p, P, q, count, key, rank, lost_ctr,
-          [&](int ci, int cj, int ck, const T* ff, T* E, T* B) {
-            const int a = ci - i0, b = cj - j0, c = ck - k0;
-            if (a >= 0 && a < kTile && b >= 0 && b < kTile && c >= 0 && c < kTile) {
-              const T wx[2] = {(T)1 - ff[0], ff[0]}, wy[2] = {(T)1 - ff[1], ff[1]},
-                      wz[2] = {(T)1 - ff[2], ff[2]};
-              E[0] = E[1] = E[2] = B[0] = B[1] = B[2] = (T)0;
-#pragma unroll
-              for (int K = 0; K < 2; ++K)
-#pragma unroll
-                for (int J = 0; J < 2; ++J)
-#pragma unroll
-                  for (int I = 0; I < 2; ++I) {
-                    const int v = ((c + K) * kTE + (b + J)) * kTE + (a + I);
-                    const V4<T> e = sE[v], bb = sB[v];
-                    const T w = wx[I] * wy[J] * wz[K];
-                    E[0] += w * e.x; E[1] += w * e.y; E[2] += w * e.z;
-                    B[0] += w * bb.x; B[1] += w * bb.y; B[2] += w * bb.z;
-                  }
-            } else {
-              gather_eb<kLo>(p, pn, D, ci, cj, ck, ff[0], ff[1], ff[2], E, B);
-            }
-          },
-          [&](int m, int kc, int* kref) {
-            *kref = k0;
-            return m < kMaxFrames ? s_frame[m] : und_frame(p, k0, th + m * p.dtb);
-          },
-          [&](bool rho, int i, int j, int k, const T* f, T jx, T jy, T jz, T q) {
-            if (kF32) {
-              if (rho)
-                deposit_rho_fixed(p, sRh, sRl, src, i0, j0, k0, i, j, k, f[0], f[1], f[2], sb);
-              else
-                deposit_cic(p, src, i, j, k, f[0], f[1], f[2], jx, jy, jz, (T)0);
-            } else if (rho) {
-              deposit_tile<true>(p, sJ, src, i0, j0, k0, i, j, k, f[0], f[1], f[2], jx, jy, jz,
-                                 q);
-            } else {
-              deposit_tile<false>(p, sJ, src, i0, j0, k0, i, j, k, f[0], f[1], f[2], jx, jy, jz,
-                                  q);
-            }
-          },
-          [&](long long qq) { return kPre ? *sl_cell : P.cell[qq]; },
-          [&](long long qq, T* f, U* u) {
-            if (kPre) {
-              f[0] = sl_f[0]; f[1] = sl_f[256]; f[2] = sl_f[512];
-              u[0] = sl_u[0]; u[1] = sl_u[256]; u[2] = sl_u[512];
-            } else {
-              f[0] = P.fx[qq]; f[1] = P.fy[qq]; f[2] = P.fz[qq];
-              u[0] = P.ux[qq]; u[1] = P.uy[qq]; u[2] = P.uz[qq];
-            }
-          },
-          [&]() {
-            if (kPre && q + (int)blockDim.x < end) prefetch(q + blockDim.x);
-          });
-    }
-    __syncthreads();
-    // add the block to the global sources (touched vertices only)
-    if (kF32) {
-      const float s1 = (float)p.qV * __int_as_float((127 - bsh) << 23);
-      const float s2 = s1 * __int_as_float((127 - bsh) << 23);
-      for (int c = tid; c < kTPC; c += blockDim.x) {
-        const int h = sRh[c], l = sRl[c];
-        if (h != 0 || l != 0) {
-          const int a = c % kTP, b = (c / kTP) % kTP, cc = c / (kTP * kTP);
-          atomicAdd(&src[cidx(i0 - 1 + a, j0 - 1 + b, k0 - 1 + cc, p.nx, p.nxy)].w,
-                    (T)((float)h * s1 + (float)l * s2));
-        }
-      }
-    } else {
-      for (int c = tid; c < kTPC; c += blockDim.x) {
-        const V4<T> v = v4(sJ[c], sJ[kTPC + c], sJ[2 * kTPC + c], sJ[3 * kTPC + c]);
-        if (v.x != (T)0 || v.y != (T)0 || v.z != (T)0 || v.w != (T)0) {
-          const int a = c % kTP, b = (c / kTP) % kTP, cc = c / (kTP * kTP);
-          dep_add(src + cidx(i0 - 1 + a, j0 - 1 + b, k0 - 1 + cc, p.nx, p.nxy), v.x, v.y, v.z,
-                  v.w);
-        }
-      }
-    }
-    __syncthreads();
-  }
-  // Sparse tiles: one warp per tile, no staging -- E and B evaluated at the
-  // vertices from global memory and the deposits added with global atomics.
-  // The whole CTA has left the loop above, so the E/B area is free for the
-  // warps' undulator frames.
-  const int nsparse = st->n_sparse;
-  if (nsparse > 0) {
-    const int lane = tid & 31;
-    UndFrame<T>* wf = reinterpret_cast<UndFrame<T>*>(sE) + (tid >> 5) * kMaxFrames;
-    for (;;) {
-      int w = 0;
-      if (lane == 0) w = atomicAdd(&st->work_sparse, 1);
-      w = __shfl_sync(0xffffffffu, w, 0);
-      if (w >= nsparse) break;
-      const int tile = tiles[ntiles + w];
+  auto prefetch = [&](const Parts<T, U>& P, long long qq) {
+    cp_async<4>(sl_cell, P.cell + qq);
+    cp_async<sizeof(T)>(sl_f, P.fx + qq);
+    cp_async<sizeof(T)>(sl_f + 256, P.fy + qq);
+    cp_async<sizeof(T)>(sl_f + 512, P.fz + qq);
+    cp_async<sizeof(U)>(sl_u, P.ux + qq);
+    cp_async<sizeof(U)>(sl_u + 256, P.uy + qq);
+    cp_async<sizeof(U)>(sl_u + 512, P.uz + qq);
+    cp_async_commit();
+  };
+  // the dense tiles of one simulation's list, then its sparse tiles and lost
+  // tail (each written once; one simulation runs them straight through, a
+  // batch member by member)
+  // one staged tile: entry t of the simulation's tile list
+  auto dense = [&](const PushArgs<T, U>& a, const CUtensorMap* tmp, const CUtensorMap* tmd,
+                   int t, double th) {
+    const PicP<T>& p = a.p;
+    StepState* const& st = a.st;
+    const V4<T>* const& pn = a.pn;
+    const V4<T>* const& D = a.D;
+    V4<T>* const& src = a.src;
+    const Parts<T, U>& P = a.P;
+    const int* const& offset = a.offset;
+    const int* const& tiles = a.tiles;
+    int* const& count = a.count;
+    int* const& key = a.key;
+    int* const& rank = a.rank;
+    long long* const& lost_ctr = a.lost_ctr;
+    {
+      const int tile = tiles[t];
       int i0, j0, k0;
       tile_origin(p, tile, &i0, &j0, &k0);
-      __syncwarp();
-      for (int m = lane; m < p.n_sub && m < kMaxFrames; m += 32)
-        wf[m] = und_frame(p, k0, th + m * p.dtb);
-      __syncwarp();
+      if (tid == 0) {
+        fence_proxy_async_smem();
+        mbar_arrive_expect_tx(bar, 2u * tile_box_bytes<T>());
+        tma_load_4d(sP, tmp, 0, i0 - 1, j0 - 1, k0 - 1, bar);
+        tma_load_4d(sD, tmd, 0, i0 - 1, j0 - 1, k0 - 1, bar);
+      }
+      // FP64 moving-window bookkeeping once per tile and sub-step
+      for (int m = tid; m < p.n_sub && m < kMaxFrames; m += blockDim.x)
+        s_frame[m] = und_frame(p, k0, th + m * p.dtb);
+      mbar_wait_bounded(bar, phase, &st->err);
+      phase ^= 1u;
+      // E and B at the tile's vertices
+      for (int v = tid; v < kTEC; v += blockDim.x) {
+        const int a = v % kTE, b = (v / kTE) % kTE, c = v / (kTE * kTE);
+        V4<T> E = v4((T)0, (T)0, (T)0, (T)0), B = E;
+        if (interior(i0 + a, j0 + b, k0 + c, p.nx, p.ny, p.nz))
+          eb_local<kLo>(p, sP, sD, ((c + 1) * kTP + (b + 1)) * kTP + (a + 1),
+                   cidx(i0 + a, j0 + b, k0 + c, p.nx, p.nxy), E, B);
+        sE[v] = E;
+        sB[v] = B;
+      }
+      __syncthreads();
       const int beg = offset[tile], end = offset[tile + 1];
-      for (int q = beg + lane; q < end; q += 32) {
+      if (kPre && beg + tid < end) prefetch(P, beg + tid);
+      // fixed-point scale 2^b of the FP32 charge block (0: tiles of more
+      // than 2^16 particles deposit rho in global memory)
+      float sb = 0.0f;
+      int bsh = 0;
+      if (kF32) {
+        const int nt = end - beg;
+        bsh = min(21, 30 - (nt > 1 ? 32 - __clz(nt - 1) : 0));
+        if (nt <= 65536) sb = __int_as_float((127 + bsh) << 23);
+        for (int c = tid; c < 2 * kTPC; c += blockDim.x) sRh[c] = 0;
+      } else {
+        for (int c = tid; c < 4 * kTPC; c += blockDim.x) sJ[c] = (T)0;
+      }
+      __syncthreads();
+
+      for (int q = beg + tid; q < end; q += blockDim.x) {
+        if (kPre) cp_async_wait_all();
         tile_particle<kOpt>(
             p, P, q, count, key, rank, lost_ctr,
             [&](int ci, int cj, int ck, const T* ff, T* E, T* B) {
-              gather_eb<kLo>(p, pn, D, ci, cj, ck, ff[0], ff[1], ff[2], E, B);
+              const int a = ci - i0, b = cj - j0, c = ck - k0;
+              if (a >= 0 && a < kTile && b >= 0 && b < kTile && c >= 0 && c < kTile) {
+                const T wx[2] = {(T)1 - ff[0], ff[0]}, wy[2] = {(T)1 - ff[1], ff[1]},
+                        wz[2] = {(T)1 - ff[2], ff[2]};
+                E[0] = E[1] = E[2] = B[0] = B[1] = B[2] = (T)0;
+  #pragma unroll
+                for (int K = 0; K < 2; ++K)
+  #pragma unroll
+                  for (int J = 0; J < 2; ++J)
+  #pragma unroll
+                    for (int I = 0; I < 2; ++I) {
+                      const int v = ((c + K) * kTE + (b + J)) * kTE + (a + I);
+                      const V4<T> e = sE[v], bb = sB[v];
+                      const T w = wx[I] * wy[J] * wz[K];
+                      E[0] += w * e.x; E[1] += w * e.y; E[2] += w * e.z;
+                      B[0] += w * bb.x; B[1] += w * bb.y; B[2] += w * bb.z;
+                    }
+              } else {
+                gather_eb<kLo>(p, pn, D, ci, cj, ck, ff[0], ff[1], ff[2], E, B);
+              }
             },
             [&](int m, int kc, int* kref) {
               *kref = k0;
-              return m < kMaxFrames ? wf[m] : und_frame(p, k0, th + m * p.dtb);
+              return m < kMaxFrames ? s_frame[m] : und_frame(p, k0, th + m * p.dtb);
             },
             [&](bool rho, int i, int j, int k, const T* f, T jx, T jy, T jz, T q) {
-              deposit_cic(p, src, i, j, k, f[0], f[1], f[2], jx, jy, jz, q);
+              if (kF32) {
+                if (rho)
+                  deposit_rho_fixed(p, sRh, sRl, src, i0, j0, k0, i, j, k, f[0], f[1], f[2], sb);
+                else
+                  deposit_cic(p, src, i, j, k, f[0], f[1], f[2], jx, jy, jz, (T)0);
+              } else if (rho) {
+                deposit_tile<true>(p, sJ, src, i0, j0, k0, i, j, k, f[0], f[1], f[2], jx, jy, jz,
+                                   q);
+              } else {
+                deposit_tile<false>(p, sJ, src, i0, j0, k0, i, j, k, f[0], f[1], f[2], jx, jy, jz,
+                                    q);
+              }
             },
-            [&](long long qq) { return P.cell[qq]; },
+            [&](long long qq) { return kPre ? *sl_cell : P.cell[qq]; },
             [&](long long qq, T* f, U* u) {
-              f[0] = P.fx[qq]; f[1] = P.fy[qq]; f[2] = P.fz[qq];
-              u[0] = P.ux[qq]; u[1] = P.uy[qq]; u[2] = P.uz[qq];
+              if (kPre) {
+                f[0] = sl_f[0]; f[1] = sl_f[256]; f[2] = sl_f[512];
+                u[0] = sl_u[0]; u[1] = sl_u[256]; u[2] = sl_u[512];
+              } else {
+                f[0] = P.fx[qq]; f[1] = P.fy[qq]; f[2] = P.fz[qq];
+                u[0] = P.ux[qq]; u[1] = P.uy[qq]; u[2] = P.uz[qq];
+              }
             },
-            [&]() {});
+            [&]() {
+              if (kPre && q + (int)blockDim.x < end) prefetch(P, q + blockDim.x);
+            });
+      }
+      __syncthreads();
+      // add the block to the global sources (touched vertices only)
+      if (kF32) {
+        const float s1 = (float)p.qV * __int_as_float((127 - bsh) << 23);
+        const float s2 = s1 * __int_as_float((127 - bsh) << 23);
+        for (int c = tid; c < kTPC; c += blockDim.x) {
+          const int h = sRh[c], l = sRl[c];
+          if (h != 0 || l != 0) {
+            const int a = c % kTP, b = (c / kTP) % kTP, cc = c / (kTP * kTP);
+            atomicAdd(&src[cidx(i0 - 1 + a, j0 - 1 + b, k0 - 1 + cc, p.nx, p.nxy)].w,
+                      (T)((float)h * s1 + (float)l * s2));
+          }
+        }
+      } else {
+        for (int c = tid; c < kTPC; c += blockDim.x) {
+          const V4<T> v = v4(sJ[c], sJ[kTPC + c], sJ[2 * kTPC + c], sJ[3 * kTPC + c]);
+          if (v.x != (T)0 || v.y != (T)0 || v.z != (T)0 || v.w != (T)0) {
+            const int a = c % kTP, b = (c / kTP) % kTP, cc = c / (kTP * kTP);
+            dep_add(src + cidx(i0 - 1 + a, j0 - 1 + b, k0 - 1 + cc, p.nx, p.nxy), v.x, v.y, v.z,
+                    v.w);
+          }
+        }
+      }
+      __syncthreads();
+    }
+  };
+  auto sparse = [&](const PushArgs<T, U>& a, int ntiles, double th) {
+    const PicP<T>& p = a.p;
+    StepState* const& st = a.st;
+    const V4<T>* const& pn = a.pn;
+    const V4<T>* const& D = a.D;
+    V4<T>* const& src = a.src;
+    const Parts<T, U>& P = a.P;
+    const int* const& offset = a.offset;
+    const int* const& tiles = a.tiles;
+    int* const& count = a.count;
+    int* const& key = a.key;
+    int* const& rank = a.rank;
+    long long* const& lost_ctr = a.lost_ctr;
+    const long long& np = a.np;
+    // Sparse tiles: one warp per tile, no staging -- E and B evaluated at the
+    // vertices from global memory and the deposits added with global atomics.
+    // The whole CTA has left the loop above, so the E/B area is free for the
+    // warps' undulator frames.
+    const int nsparse = st->n_sparse;
+    if (nsparse > 0) {
+      const int lane = tid & 31;
+      UndFrame<T>* wf = reinterpret_cast<UndFrame<T>*>(sE) + (tid >> 5) * kMaxFrames;
+      for (;;) {
+        int w = 0;
+        if (lane == 0) w = atomicAdd(&st->work_sparse, 1);
+        w = __shfl_sync(0xffffffffu, w, 0);
+        if (w >= nsparse) break;
+        const int tile = tiles[ntiles + w];
+        int i0, j0, k0;
+        tile_origin(p, tile, &i0, &j0, &k0);
+        __syncwarp();
+        for (int m = lane; m < p.n_sub && m < kMaxFrames; m += 32)
+          wf[m] = und_frame(p, k0, th + m * p.dtb);
+        __syncwarp();
+        const int beg = offset[tile], end = offset[tile + 1];
+        for (int q = beg + lane; q < end; q += 32) {
+          tile_particle<kOpt>(
+              p, P, q, count, key, rank, lost_ctr,
+              [&](int ci, int cj, int ck, const T* ff, T* E, T* B) {
+                gather_eb<kLo>(p, pn, D, ci, cj, ck, ff[0], ff[1], ff[2], E, B);
+              },
+              [&](int m, int kc, int* kref) {
+                *kref = k0;
+                return m < kMaxFrames ? wf[m] : und_frame(p, k0, th + m * p.dtb);
+              },
+              [&](bool rho, int i, int j, int k, const T* f, T jx, T jy, T jz, T q) {
+                deposit_cic(p, src, i, j, k, f[0], f[1], f[2], jx, jy, jz, q);
+              },
+              [&](long long qq) { return P.cell[qq]; },
+              [&](long long qq, T* f, U* u) {
+                f[0] = P.fx[qq]; f[1] = P.fy[qq]; f[2] = P.fz[qq];
+                u[0] = P.ux[qq]; u[1] = P.uy[qq]; u[2] = P.uz[qq];
+              },
+              [&]() {});
+        }
       }
     }
-  }
-  // particles lost before this step sit at the tail of the sorted order (the
-  // bucket after the last tile); they keep that bucket in the re-sort
-  for (long long q = offset[p.nkeys] + (long long)blockIdx.x * blockDim.x + tid; q < np;
-       q += (long long)gridDim.x * blockDim.x) {
-    key[q] = p.nkeys;
-    rank[q] = bin_rank(count, p.nkeys);
+    // particles lost before this step sit at the tail of the sorted order (the
+    // bucket after the last tile); they keep that bucket in the re-sort
+    for (long long q = offset[p.nkeys] + (long long)blockIdx.x * blockDim.x + tid; q < np;
+         q += (long long)gridDim.x * blockDim.x) {
+      key[q] = p.nkeys;
+      rank[q] = bin_rank(count, p.nkeys);
+    }
+  };
+  if constexpr (!kBatch) {
+    const PushArgs<T, U>& a = prm.args;
+    const int ntiles = a.st->n_tiles;
+    const double th = a.p.t0 + ((double)a.st->n + 0.5) * a.p.dt;
+    for (;;) {  // the CTA takes tiles from the list until none is left
+      if (tid == 0) s_tile = atomicAdd(&a.st->work, 1);
+      __syncthreads();
+      const int t = s_tile;
+      if (t >= ntiles) break;
+      dense(a, &prm.tm_pn, &prm.tm_d, t, th);
+    }
+    sparse(a, ntiles, th);
+  } else {
+    // the group's non-empty tiles (the dense and the sparse entries of each
+    // member's list, all staged) from one counter
+    const int M = prm.M;
+    for (;;) {
+      if (tid == 0) s_tile = atomicAdd(prm.work, 1);
+      __syncthreads();
+      const int w = s_tile;
+      if (w >= prm.pref[M]) break;
+      const int mi = member_of_tile(prm.pref, M, w);
+      const PushArgs<T, U>& a = prm.m[mi];
+      const double th = a.p.t0 + ((double)a.st->n + 0.5) * a.p.dt;
+      dense(a, &prm.box[mi], &prm.box_d[mi], w - prm.pref[mi], th);
+    }
+    // the particles each member lost before this step keep their bucket
+    for (int r = 0; r < M; ++r) {
+      const PushArgs<T, U>& a = prm.m[r];
+      const int nk = a.p.nkeys;
+      for (long long q = a.offset[nk] + (long long)blockIdx.x * blockDim.x + tid; q < a.np;
+           q += (long long)gridDim.x * blockDim.x) {
+        a.key[q] = nk;
+        a.rank[q] = bin_rank(a.count, nk);
+      }
+    }
   }
 }
 

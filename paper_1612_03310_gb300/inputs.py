@@ -183,6 +183,14 @@ def batch_jobs(n_jobs: int = 64, steps: int = 1000, seed: int = 4) -> list[dict]
     return jobs
 
 
+def uniform_jobs(n_jobs: int, nx: int, nz: int, n_particles: int, steps: int = 1000,
+                 seed: int = 9) -> list[dict]:
+    """n_jobs design-sweep jobs of one size (nx = ny, nz, n_particles) with
+    the physics drawn as for c4 and c5: many small members of a batch."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return [_job(rng, nx, nz, n_particles, steps, k) for k in range(n_jobs)]
+
+
 def serve_jobs(n_jobs: int, rate: float, seed: int = 5) -> list[dict]:
     """c5: Poisson arrivals at `rate` jobs/s; nx = ny in [32, 160], nz in
     [128, 1024] (multiples of 64), 1e3-4e6 particles (log-uniform), 500-5000
@@ -209,5 +217,5 @@ def describe(name: str) -> str:
             f"{w['steps']} steps")
 
 
-__all__ = ["WORKLOADS", "workload", "make_bunch", "random_grid", "random_fields",
+__all__ = ["WORKLOADS", "workload", "make_bunch", "random_grid", "random_fields", "uniform_jobs",
            "random_particles", "centred_grid", "describe", "batch_jobs", "serve_jobs"]

@@ -32,7 +32,8 @@ EXPORTS = ["mithra_create", "mithra_step", "mithra_sync", "mithra_time", "mithra
            "mithra_batch_destroy", "mithra_bunch_stats", "mithra_set_spectrum",
            "mithra_read_spectrum", "mithra_set_seed", "mithra_set_bunch_sampling",
            "mithra_read_bunch", "mithra_snapshot_bytes", "mithra_snapshot", "mithra_restore",
-           "mithra_boost_from_lab", "mithra_make_bunch", "mithra_set_lost_policy"]
+           "mithra_boost_from_lab", "mithra_make_bunch", "mithra_set_lost_policy",
+           "mithra_batch_set_mode", "mithra_batch_get_mode", "mithra_batch_stats"]
 
 
 class MithraError(RuntimeError):
@@ -138,6 +139,9 @@ def lib():
     L.mithra_batch_destroy.argtypes = [vp]
     L.mithra_make_bunch.argtypes = [C.POINTER(BunchSpec), dp, dp, dp, dp, dp, dp, dp]
     L.mithra_set_lost_policy.argtypes = [vp, C.c_int32]
+    L.mithra_batch_set_mode.argtypes = [vp, C.c_int32]
+    L.mithra_batch_get_mode.argtypes = [vp, C.POINTER(C.c_int32)]
+    L.mithra_batch_stats.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), dp]
     L.mithra_set_tuning.argtypes = [vp, C.POINTER(Tuning)]
     L.mithra_get_tuning.argtypes = [vp, C.POINTER(Tuning)]
     for name in EXPORTS:
@@ -519,6 +523,26 @@ class Batch:
 
     def sync(self):
         self._check(lib().mithra_batch_sync(self.h))
+
+    def set_mode(self, fused):
+        """True: one launch per phase over all members when they allow it;
+        False: one launch sequence per member; "auto" (the default): fused
+        for small members (mithra_batch_set_mode)."""
+        mode = 2 if fused == "auto" else (1 if fused else 0)
+        self._check(lib().mithra_batch_set_mode(self.h, mode))
+
+    def stats(self) -> dict:
+        """Graph captures so far, fused ones, and their host time [s]."""
+        c, f, t = C.c_int64(0), C.c_int64(0), C.c_double(0.0)
+        self._check(lib().mithra_batch_stats(self.h, C.byref(c), C.byref(f), C.byref(t)))
+        return dict(captures=int(c.value), fused_captures=int(f.value),
+                    capture_seconds=float(t.value))
+
+    def fused(self) -> bool:
+        """Whether the graph captured last is the fused form."""
+        out = C.c_int32(0)
+        self._check(lib().mithra_batch_get_mode(self.h, C.byref(out)))
+        return bool(out.value)
 
     def __len__(self):
         return int(lib().mithra_batch_size(self.h))

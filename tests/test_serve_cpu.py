@@ -169,3 +169,29 @@ def test_step_error_fails_the_batch_and_the_server_goes_on():
     assert all("CUDA error" in js.error for js in st["not_done"])
     assert len(made) == 2 and st["done"][0].spec["jid"] == 2
     assert srv.used == 0
+
+
+def test_work_budget_limits_the_batch():
+    # three jobs of 32 x 32 x 64 cells and 1000 particles (69,536 work units
+    # per step each): a budget of two jobs' work admits two at a time, the
+    # third waits although memory would hold it; a job larger than the
+    # budget runs alone
+    jobs = make_jobs([0, 0, 0], [20, 20, 20], [32, 32, 32])
+    w = serve.Server.job_work(jobs[0])
+    assert w == 32 * 32 * 64 + 4 * 1000
+    b = FakeBatch()
+    srv = serve.Server(10 ** 9, max_slots=8, tick_steps=16, clock="steps", work_budget=2.5 * w,
+                       sim_factory=FakeSim, batch_factory=lambda: b,
+                       footprint_fn=lambda g, n, p: 1)
+    st = srv.run(jobs)
+    assert st["completed"] == 3
+    assert max(m for _, m in b.ticks) == 2
+    assert st["active_peak"] == 2
+    big = make_jobs([0], [10], [64])
+    b2 = FakeBatch()
+    srv = serve.Server(10 ** 9, max_slots=8, tick_steps=16, clock="steps", work_budget=w,
+                       sim_factory=FakeSim, batch_factory=lambda: b2,
+                       footprint_fn=lambda g, n, p: 1)
+    assert srv.run(big)["completed"] == 1
+    # the served rate counts the cells of every job stepped, finished or not
+    assert st["served_cell_updates_per_s"] > 0
