@@ -152,8 +152,11 @@ struct PicP {
   // lo parts of the level that E and B are evaluated from (compensated
   // forms), nullptr otherwise; set at each launch beside that level
   const LoV4* plo;
-  // Boris: h = qm dtb / (2c), an = qm dtb / 2
+  // Boris: h = qm dtb / (2c), an = qm dtb / 2, and each as a float pair
+  // (hi the nearest float, lo the nearest float to the remainder) for the
+  // FP32 forms, whose particle loop then runs no FP64 instruction
   double h, an;
+  float h_hi, h_lo, an_hi, an_lo;
   T cx, cy, cz;  // c dt_b / (dx, dy, dz): cells moved per unit beta in a sub-step
   int n_sub;
   double t0, dt, dtb;

@@ -680,10 +680,10 @@ __global__ void __launch_bounds__(kMX* kMY, (sizeof(T) == 4 ? 4 : 1)) k_potentia
     const int kd = kb - 2 + q;
     const bool cols = kd >= kb && kd < ke;
     mbar_arrive_expect_tx(&full[s], march_psi_bytes<T>() + (cols ? 2 * march_col_bytes<T>() : 0));
-    tma_load_4d(base, &tm_cur, 0, i0 - 1, j0 - 1, kb - 1 + q, &full[s]);
+    tma_load_field(base, &tm_cur, i0 - 1, j0 - 1, kb - 1 + q, &full[s]);
     if (cols) {
-      tma_load_4d(base + OFF_D, &tm_d, 0, i0, j0, kd, &full[s]);
-      tma_load_4d(base + OFF_S, &tm_s, 0, i0, j0, kd, &full[s]);
+      tma_load_field(base + OFF_D, &tm_d, i0, j0, kd, &full[s]);
+      tma_load_field(base + OFF_S, &tm_s, i0, j0, kd, &full[s]);
     }
   };
   if (threadIdx.x == 0)

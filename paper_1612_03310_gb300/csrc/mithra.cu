@@ -301,6 +301,8 @@ PicP<T> make_pic(const mithra_sim* s) {
   const double dtb = g.dt / g.n_sub;
   p.h = qm * dtb / (2.0 * kC);
   p.an = qm * dtb / 2.0;
+  p.h_hi = (float)p.h; p.h_lo = (float)(p.h - (double)p.h_hi);
+  p.an_hi = (float)p.an; p.an_lo = (float)(p.an - (double)p.an_hi);
   p.cx = (T)(kC * dtb / g.dx); p.cy = (T)(kC * dtb / g.dy); p.cz = (T)(kC * dtb / g.dz);
   p.n_sub = g.n_sub;
   p.t0 = s->t0; p.dt = g.dt; p.dtb = dtb;
@@ -419,10 +421,10 @@ mithra_status setup_push_grid(mithra_sim* s) {
   MCHECK(s, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
   if constexpr (push_form_plain<T, U>())
     MCHECK(s, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_push_tiled<false, T, U>,
-                                                            256, smem));
+                                                            kPushThreads, smem));
   else
     MCHECK(s, cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                  &per_sm, k_push_tiled<false, T, U, true>, 256, smem));
+                  &per_sm, k_push_tiled<false, T, U, true>, kPushThreads, smem));
   s->n_sm = nsm;
   s->push_max_per_sm = per_sm > 0 ? per_sm : 1;
   s->push_grid = nsm * s->push_max_per_sm;
@@ -585,7 +587,7 @@ mithra_status launch_step(mithra_sim* s) {
         pa.rank = s->rank;
         pa.lost_ctr = &s->dstate->n_lost;
         pa.np = s->np;
-        kern<<<s->push_grid, 256, tile_smem_bytes<T, U>(), s->stream>>>(prm);
+        kern<<<s->push_grid, kPushThreads, tile_smem_bytes<T, U>(), s->stream>>>(prm);
       } else {
         decltype(&k_push<false, T, U, kAnyLo>) kern = nullptr;
         if constexpr (push_form_plain<T, U>())
@@ -1862,7 +1864,8 @@ mithra_status capture_fused_typed(mithra_batch* b) {
       cudaSuccess)
     return bfail(b, MITHRA_ECUDA, "batched particle step: shared memory attribute");
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kpush, 256, smem) != cudaSuccess ||
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kpush, kPushThreads, smem) !=
+          cudaSuccess ||
       per_sm < 1)
     return bfail(b, MITHRA_ECUDA, "batched particle step does not fit an SM");
   b->push_grid = b->sims[0]->n_sm * per_sm;
@@ -1920,7 +1923,7 @@ mithra_status capture_fused_typed(mithra_batch* b) {
       prm.pref = pref;
       prm.work = work;
       prm.M = Mg;
-      kpush<<<b->push_grid, 256, smem, q>>>(prm);
+      kpush<<<b->push_grid, kPushThreads, smem, q>>>(prm);
     }
     kb_scan_partials<T, U><<<total(kBPScan), kScanBlock, 0, q>>>(mem, dblk + kBPScan * (M + 1), M);
     kb_scan_final<T, U><<<total(kBPScan), kScanBlock, 0, q>>>(mem, dblk + kBPScan * (M + 1), M);

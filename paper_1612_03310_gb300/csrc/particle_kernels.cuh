@@ -163,108 +163,6 @@ __device__ inline void gather_eb(const PicP<T>& p, const V4<T>* __restrict__ pn,
       }
 }
 
-// 1/sqrt(x) for x >= 1 in FP64 by the Newton-Raphson iteration for the
-// reciprocal square root, y <- y (3 - x y^2) / 2, from an FP32 seed (rsqrtf):
-// the error squares each step, one step reaches ~1e-13 (enough next to FP32
-// momenta), two reach FP64 rounding (used when T is double).  Gives
-// 1/gamma = 1/sqrt(1 + u.u) without an FP64 square root or division.
-template <typename T>
-__device__ inline double rsqrt_nr(double x) {
-  double y = (double)rsqrtf((float)x);
-  y = y * (1.5 - 0.5 * x * y * y);  // relative error ~1e-13 after one step
-  if (sizeof(T) == 8) y = y * (1.5 - 0.5 * x * y * y);  // FP64 rounding
-  return y;
-}
-
-// 1/sqrt(x) in the momentum type: FP64 as above; FP32 from the rsqrtf seed
-// with one FP32 Newton-Raphson step.
-__device__ inline float rsqrt_u(float x) {
-  const float y = rsqrtf(x);
-  return y * (1.5f - 0.5f * x * y * y);
-}
-__device__ inline double rsqrt_u(double x) { return rsqrt_nr<double>(x); }
-
-// 1/gamma = 1/sqrt(1 + u.u) that moves the particle, recomputed from the
-// momentum in FP64 whatever the momentum type.  FP64 momenta: 1 + u.u in
-// FP64, rsqrt_nr.  FP32 momenta: 1 + u.u is first formed exactly enough in
-// FP32 pairs -- each square split into its rounded value and the exact
-// remainder by an FMA, the seven terms summed with TwoSum (error ~2^-48) --
-// and the pair taken to FP64 by one addition; then the FP32 seed and the
-// FP64 Newton-Raphson step of rsqrt_nr.  This spends 9 instead of 13
-// instructions on GB300's narrow FP64 pipe.
-template <typename T>
-__device__ inline T inv_gamma(const double u[3]) {
-  return (T)rsqrt_nr<T>(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-}
-template <typename T>
-__device__ inline T inv_gamma(const float u[3]) {
-  float hi = 1.0f, lo = 0.0f;
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    // (the _rn intrinsics keep the compiler from fusing these into FMAs)
-    const float p = __fmul_rn(u[a], u[a]);
-    const float e = fmaf(u[a], u[a], -p);  // u^2 = p + e exactly
-    const float s = __fadd_rn(hi, p);      // TwoSum(hi, p)
-    const float bp = __fsub_rn(s, hi);
-    lo += __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(p, bp)) + e;
-    hi = s;
-  }
-  const double x = (double)hi + (double)lo;
-  double y = (double)rsqrtf(hi);
-  y = y * (1.5 - 0.5 * x * y * y);
-  if (sizeof(T) == 8) y = y * (1.5 - 0.5 * x * y * y);
-  return (T)y;
-}
-
-// 1/gamma from float-float momenta: 1 + u.u summed in FP32 pairs (each hi^2
-// split exactly by an FMA, the cross terms 2 hi lo and the remainders added
-// to the low word), then to FP64 by one addition and the FP64 Newton-Raphson
-// step of rsqrt_nr from the FP32 seed, as for FP32 momenta.
-template <typename T>
-__device__ inline T inv_gamma(const FF2 u[3]) {
-  float hi = 1.0f, lo = 0.0f;
-#pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    const float p = __fmul_rn(u[a].hi, u[a].hi);
-    const float e = fmaf(u[a].hi, u[a].hi, -p) + 2.0f * u[a].hi * u[a].lo;
-    const float s = __fadd_rn(hi, p);
-    const float bp = __fsub_rn(s, hi);
-    lo += __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(p, bp)) + e;
-    hi = s;
-  }
-  const double x = (double)hi + (double)lo;
-  double y = (double)rsqrtf(hi);
-  y = y * (1.5 - 0.5 * x * y * y);
-  if (sizeof(T) == 8) y = y * (1.5 - 0.5 * x * y * y);
-  return (T)y;
-}
-
-// Boris rotation and kicks (Eq. BorisScheme) for charge-to-mass qm folded
-// into h = qm dtb / (2c) and an = qm dtb / 2, in the momentum type U.  The
-// gamma of the half-kicked momentum t1, which only sets the rotation angle,
-// is taken in U as well; the gamma that moves the particle is recomputed in
-// FP64 by the caller.
-template <typename T, typename U>
-__device__ inline void boris(const PicP<T>& p, U u[3], const T Ef[3], const T Bf[3]) {
-  const U h = (U)p.h;
-  const U E[3] = {(U)Ef[0], (U)Ef[1], (U)Ef[2]};
-  const U B[3] = {(U)Bf[0], (U)Bf[1], (U)Bf[2]};
-  const U t1x = u[0] + h * E[0], t1y = u[1] + h * E[1], t1z = u[2] + h * E[2];
-  const U ig1 = rsqrt_u((U)1 + t1x * t1x + t1y * t1y + t1z * t1z);
-  const U al = (U)p.an * ig1;
-  const U t2x = t1x + al * (t1y * B[2] - t1z * B[1]);
-  const U t2y = t1y + al * (t1z * B[0] - t1x * B[2]);
-  const U t2z = t1z + al * (t1x * B[1] - t1y * B[0]);
-  const U f = (U)2 * al / ((U)1 + al * al * (B[0] * B[0] + B[1] * B[1] + B[2] * B[2]));
-  const U sx = f * B[0], sy = f * B[1], sz = f * B[2];
-  const U t3x = t1x + (t2y * sz - t2z * sy);
-  const U t3y = t1y + (t2z * sx - t2x * sz);
-  const U t3z = t1z + (t2x * sy - t2y * sx);
-  u[0] = t3x + h * E[0];
-  u[1] = t3y + h * E[1];
-  u[2] = t3z + h * E[2];
-}
-
 // Float-float numbers (hi + lo, |lo| <= ulp(hi)/2, ~2^-46 relative) by the
 // error-free transformations: Knuth's TwoSum, Dekker's FastTwoSum and the
 // FMA product split.  The _rn intrinsics keep the compiler from fusing the
@@ -297,11 +195,127 @@ __device__ inline FF ff_mul(FF a, float b) {
   const FF p = ff_prod(a.hi, b);
   return ff_fast(p.hi, p.lo + a.lo * b);
 }
-__device__ inline FF ff_of(double x) {
-  const float h = (float)x;
-  return {h, (float)(x - (double)h)};
+
+// 1/sqrt(x) for x >= 1 in FP64 by the Newton-Raphson iteration for the
+// reciprocal square root, y <- y (3 - x y^2) / 2, from an FP32 seed (rsqrtf):
+// the error squares each step, one step reaches ~1e-13, two reach FP64
+// rounding (used when T is double).  Gives
+// 1/gamma = 1/sqrt(1 + u.u) without an FP64 square root or division.
+template <typename T>
+__device__ inline double rsqrt_nr(double x) {
+  double y = (double)rsqrtf((float)x);
+  y = y * (1.5 - 0.5 * x * y * y);  // relative error ~1e-13 after one step
+  if (sizeof(T) == 8) y = y * (1.5 - 0.5 * x * y * y);  // FP64 rounding
+  return y;
 }
-__device__ inline double ff_to_double(FF a) { return (double)a.hi + (double)a.lo; }
+
+// 1/sqrt(x) in the momentum type: FP64 as above; FP32 from the rsqrtf seed
+// with one FP32 Newton-Raphson step.
+__device__ inline float rsqrt_u(float x) {
+  const float y = rsqrtf(x);
+  return y * (1.5f - 0.5f * x * y * y);
+}
+__device__ inline double rsqrt_u(double x) { return rsqrt_nr<double>(x); }
+
+// 1/sqrt(x) for x = hi + lo >= 1 (a float pair) to FP32 rounding on FP32
+// instructions only: the seed y0 = rsqrtf(hi) and one Newton-Raphson step
+// y = y0 + y0 r / 2, with the residual r = 1 - x y0^2 formed in float-float
+// (y0^2 split exactly by an FMA).  r carries ~2^-46, the step leaves ~2^-43
+// (the square of the seed's error), and the one rounding of the final FMA
+// gives the nearest float but for near-ties -- what the same Newton step in
+// FP64 followed by a conversion to float gives, without GB300's narrow FP64
+// pipe.
+__device__ inline float rsqrt_ff(float hi, float lo) {
+  const float y0 = rsqrtf(hi);
+  const FF r = ff_sub(FF{1.0f, 0.0f}, ff_mul(FF{hi, lo}, ff_prod(y0, y0)));
+  return fmaf(0.5f * y0, r.hi, y0);
+}
+
+// 1/gamma = 1/sqrt(1 + u.u) that moves the particle, recomputed from the
+// momentum whatever its type, to the rounding of the fraction type T.
+// FP64 momenta: 1 + u.u in FP64, rsqrt_nr.  FP32 momenta: 1 + u.u is first
+// formed exactly enough in FP32 pairs -- each square split into its rounded
+// value and the exact remainder by an FMA, the seven terms summed with
+// TwoSum (error ~2^-48) -- then rsqrt_ff (an FP64 T takes the pair to FP64
+// and rsqrt_nr instead).
+template <typename T>
+__device__ inline T inv_gamma(const double u[3]) {
+  return (T)rsqrt_nr<T>(1.0 + u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+}
+template <typename T>
+__device__ inline T inv_gamma_pair(float hi, float lo) {
+  if constexpr (sizeof(T) == 4) {
+    return rsqrt_ff(hi, lo);
+  } else {
+    return (T)rsqrt_nr<T>((double)hi + (double)lo);
+  }
+}
+template <typename T>
+__device__ inline T inv_gamma(const float u[3]) {
+  float hi = 1.0f, lo = 0.0f;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    // (the _rn intrinsics keep the compiler from fusing these into FMAs)
+    const float p = __fmul_rn(u[a], u[a]);
+    const float e = fmaf(u[a], u[a], -p);  // u^2 = p + e exactly
+    const float s = __fadd_rn(hi, p);      // TwoSum(hi, p)
+    const float bp = __fsub_rn(s, hi);
+    lo += __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(p, bp)) + e;
+    hi = s;
+  }
+  return inv_gamma_pair<T>(hi, lo);
+}
+
+// 1/gamma from float-float momenta: 1 + u.u summed in FP32 pairs (each hi^2
+// split exactly by an FMA, the cross terms 2 hi lo and the remainders added
+// to the low word), then rsqrt_ff as for FP32 momenta.
+template <typename T>
+__device__ inline T inv_gamma(const FF2 u[3]) {
+  float hi = 1.0f, lo = 0.0f;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float p = __fmul_rn(u[a].hi, u[a].hi);
+    const float e = fmaf(u[a].hi, u[a].hi, -p) + 2.0f * u[a].hi * u[a].lo;
+    const float s = __fadd_rn(hi, p);
+    const float bp = __fsub_rn(s, hi);
+    lo += __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(p, bp)) + e;
+    hi = s;
+  }
+  return inv_gamma_pair<T>(hi, lo);
+}
+
+// Boris rotation and kicks (Eq. BorisScheme) for charge-to-mass qm folded
+// into h = qm dtb / (2c) and an = qm dtb / 2, in the momentum type U.  The
+// gamma of the half-kicked momentum t1, which only sets the rotation angle,
+// is taken in U as well; the gamma that moves the particle is recomputed by
+// the caller (inv_gamma).
+template <typename T, typename U>
+__device__ inline void boris(const PicP<T>& p, U u[3], const T Ef[3], const T Bf[3]) {
+  U h, an;
+  if constexpr (sizeof(U) == 4) {
+    h = p.h_hi;
+    an = p.an_hi;
+  } else {
+    h = (U)p.h;
+    an = (U)p.an;
+  }
+  const U E[3] = {(U)Ef[0], (U)Ef[1], (U)Ef[2]};
+  const U B[3] = {(U)Bf[0], (U)Bf[1], (U)Bf[2]};
+  const U t1x = u[0] + h * E[0], t1y = u[1] + h * E[1], t1z = u[2] + h * E[2];
+  const U ig1 = rsqrt_u((U)1 + t1x * t1x + t1y * t1y + t1z * t1z);
+  const U al = an * ig1;
+  const U t2x = t1x + al * (t1y * B[2] - t1z * B[1]);
+  const U t2y = t1y + al * (t1z * B[0] - t1x * B[2]);
+  const U t2z = t1z + al * (t1x * B[1] - t1y * B[0]);
+  const U f = (U)2 * al / ((U)1 + al * al * (B[0] * B[0] + B[1] * B[1] + B[2] * B[2]));
+  const U sx = f * B[0], sy = f * B[1], sz = f * B[2];
+  const U t3x = t1x + (t2y * sz - t2z * sy);
+  const U t3y = t1y + (t2z * sx - t2x * sz);
+  const U t3z = t1z + (t2x * sy - t2y * sx);
+  u[0] = t3x + h * E[0];
+  u[1] = t3y + h * E[1];
+  u[2] = t3z + h * E[2];
+}
 
 // Compensated momenta next to FP32 fields (P32_U64): the momenta are stored
 // as float-float pairs (FF2) and the Boris step runs in float-float
@@ -311,7 +325,7 @@ __device__ inline double ff_to_double(FF a) { return (double)a.hi + (double)a.lo
 // cross products carry ~2^-46, far below the FP32 fields they act with.
 __device__ inline void boris_ff(const PicP<float>& p, FF u[3], const float Ef[3],
                                 const float Bf[3]) {
-  const FF h = ff_of(p.h), an = ff_of(p.an);
+  const FF h{p.h_hi, p.h_lo}, an{p.an_hi, p.an_lo};
   const FF hE[3] = {ff_mul(h, Ef[0]), ff_mul(h, Ef[1]), ff_mul(h, Ef[2])};
   const FF t1[3] = {ff_add(u[0], hE[0]), ff_add(u[1], hE[1]), ff_add(u[2], hE[2])};
   // 1 / gamma_1 = 1 / sqrt(1 + t1.t1)
@@ -421,7 +435,7 @@ __device__ inline int split_cell_t(int c0, T s, T* frac) {
 
 // n_sub Boris steps of one particle (Eq. BorisScheme) with the grid E, B from
 // gather(i, j, k, f, E, B) and the undulator at each sub-step time, through
-// the frame frame(m, k, &kref) of sub-step m; 1/gamma in FP64, the position
+// the frame frame(m, k, &kref) of sub-step m; 1/gamma by inv_gamma, the position
 // advanced in cells (fraction type T, carry into the cell index).  disp
 // receives the displacement in cells over the field step.  Returns false when
 // the particle leaves the valid cells.

@@ -33,6 +33,7 @@ constexpr int kTP = kTile + 3;             // potential / deposit vertices per a
 constexpr int kTE = kTile + 1;             // E/B vertices per axis
 constexpr int kTPC = kTP * kTP * kTP;      // 1331
 constexpr int kTEC = kTE * kTE * kTE;      // 729
+constexpr int kPushThreads = 256;          // threads of a particle-step CTA
 
 template <typename T>
 __host__ __device__ constexpr int tile_box_bytes() {
@@ -46,21 +47,36 @@ template <typename T>
 __host__ __device__ constexpr int tile_eb_offset() {
   return 2 * tile_box_stride<T>();
 }
-// The next-particle slots of the dense loop (one particle per thread: cell,
-// fractions, momenta), kept where T and U have one size: with FP64 momenta
-// next to FP32 fields the 10 KB would cost the third CTA per SM.
-template <typename T, typename U>
-__host__ __device__ constexpr bool tile_prefetch() {
-  return sizeof(T) == sizeof(U);
+// E and B per vertex as (E_x, E_y, E_z, B_x) and (B_y, B_z): 24 instead of
+// 32 bytes a vertex in FP32, which keeps three CTAs per SM within the
+// 196 KB shared-memory configuration and leaves 60 KB of the SM's L1 to
+// register spills and the particles' loads.
+template <typename T>
+struct alignas(2 * sizeof(T)) V2 {
+  T x, y;
+};
+template <typename T>
+__host__ __device__ constexpr int tile_b2_offset() {
+  return tile_eb_offset<T>() + kTEC * (int)sizeof(V4<T>);
 }
 template <typename T>
-__host__ __device__ constexpr int tile_slot_offset() {
-  return tile_eb_offset<T>() + kTEC * 2 * (int)sizeof(V4<T>) + 16;
+__host__ __device__ constexpr int tile_bar_offset() {
+  return tile_b2_offset<T>() + kTEC * (int)sizeof(V2<T>);
 }
 template <typename T, typename U>
 __host__ __device__ constexpr int tile_smem_bytes() {
-  return tile_slot_offset<T>() +
-         (tile_prefetch<T, U>() ? 256 * (4 + 3 * (int)sizeof(T) + 3 * (int)sizeof(U)) : 0);
+  return tile_bar_offset<T>() + 16;
+}
+// The next-particle slots of the dense loop (one particle per thread: cell,
+// fractions, momenta) in the increment box, which is free once E and B are
+// built.
+template <typename T>
+__host__ __device__ constexpr int tile_slot_offset() {
+  return tile_box_stride<T>();
+}
+template <typename T, typename U>
+__host__ __device__ constexpr int tile_slot_bytes() {
+  return kPushThreads * (4 + 3 * (int)sizeof(T) + 3 * (int)sizeof(U));
 }
 
 // E, B at local vertex l of the potential box (strides 1, 11, 121), global
@@ -248,26 +264,29 @@ struct PushParams<T, U, true> {
 };
 
 template <bool kOpt, typename T, typename U, bool kLo = false, bool kBatch = false>
-__global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 3 : 1))
+__global__ void __launch_bounds__(kPushThreads, (sizeof(T) == 4 ? 3 : 1))
     k_push_tiled(const __grid_constant__ PushParams<T, U, kBatch> prm) {
   extern __shared__ __align__(128) unsigned char smem[];
   V4<T>* sP = reinterpret_cast<V4<T>*>(smem);
   V4<T>* sD = reinterpret_cast<V4<T>*>(smem + tile_box_stride<T>());
-  V4<T>* sE = reinterpret_cast<V4<T>*>(smem + tile_eb_offset<T>());  // E per vertex
-  V4<T>* sB = sE + kTEC;                                                 // B per vertex
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + tile_eb_offset<T>() +
-                                              kTEC * 2 * (int)sizeof(V4<T>));
+  V4<T>* sE = reinterpret_cast<V4<T>*>(smem + tile_eb_offset<T>());   // E_x..E_z, B_x
+  V2<T>* sB = reinterpret_cast<V2<T>*>(smem + tile_b2_offset<T>());   // B_y, B_z
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + tile_bar_offset<T>());
+  static_assert(tile_slot_bytes<T, U>() <= tile_box_bytes<T>(), "slots fit the increment box");
   // deposit block, reuses the psi box once E, B are built.  FP64: one array
   // per component (J_x, J_y, J_z, rho), so that atomics of a component from
   // different vertices spread over all banks.  FP32: the fixed-point rho
   // sums (hi, lo), the current going to global memory directly (vector
   // atomics in L2, measured faster than FP32 shared-memory atomics).
   constexpr bool kF32 = sizeof(T) == 4;
-  // this thread's next-particle slot (stride 256 between the components)
-  constexpr bool kPre = tile_prefetch<T, U>();
+  // this thread's next-particle slot (stride kPushThreads between the
+  // components), in
+  // the increment box: written only after E and B are built, and drained
+  // before the CTA's next tile loads into the box
   int* sl_cell = reinterpret_cast<int*>(smem + tile_slot_offset<T>()) + threadIdx.x;
-  T* sl_f = reinterpret_cast<T*>(smem + tile_slot_offset<T>() + 256 * 4) + threadIdx.x;
-  U* sl_u = reinterpret_cast<U*>(smem + tile_slot_offset<T>() + 256 * (4 + 3 * (int)sizeof(T))) +
+  T* sl_f = reinterpret_cast<T*>(smem + tile_slot_offset<T>() + kPushThreads * 4) + threadIdx.x;
+  U* sl_u = reinterpret_cast<U*>(smem + tile_slot_offset<T>() +
+                                 kPushThreads * (4 + 3 * (int)sizeof(T))) +
             threadIdx.x;
   T* sJ = reinterpret_cast<T*>(sP);
   int* sRh = reinterpret_cast<int*>(sP);
@@ -285,11 +304,11 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 3 : 1))
   auto prefetch = [&](const Parts<T, U>& P, long long qq) {
     cp_async<4>(sl_cell, P.cell + qq);
     cp_async<sizeof(T)>(sl_f, P.fx + qq);
-    cp_async<sizeof(T)>(sl_f + 256, P.fy + qq);
-    cp_async<sizeof(T)>(sl_f + 512, P.fz + qq);
+    cp_async<sizeof(T)>(sl_f + kPushThreads, P.fy + qq);
+    cp_async<sizeof(T)>(sl_f + 2 * kPushThreads, P.fz + qq);
     cp_async<sizeof(U)>(sl_u, P.ux + qq);
-    cp_async<sizeof(U)>(sl_u + 256, P.uy + qq);
-    cp_async<sizeof(U)>(sl_u + 512, P.uz + qq);
+    cp_async<sizeof(U)>(sl_u + kPushThreads, P.uy + qq);
+    cp_async<sizeof(U)>(sl_u + 2 * kPushThreads, P.uz + qq);
     cp_async_commit();
   };
   // the dense tiles of one simulation's list, then its sparse tiles and lost
@@ -317,8 +336,8 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 3 : 1))
       if (tid == 0) {
         fence_proxy_async_smem();
         mbar_arrive_expect_tx(bar, 2u * tile_box_bytes<T>());
-        tma_load_4d(sP, tmp, 0, i0 - 1, j0 - 1, k0 - 1, bar);
-        tma_load_4d(sD, tmd, 0, i0 - 1, j0 - 1, k0 - 1, bar);
+        tma_load_field(sP, tmp, i0 - 1, j0 - 1, k0 - 1, bar);
+        tma_load_field(sD, tmd, i0 - 1, j0 - 1, k0 - 1, bar);
       }
       // FP64 moving-window bookkeeping once per tile and sub-step
       for (int m = tid; m < p.n_sub && m < kMaxFrames; m += blockDim.x)
@@ -332,12 +351,12 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 3 : 1))
         if (interior(i0 + a, j0 + b, k0 + c, p.nx, p.ny, p.nz))
           eb_local<kLo>(p, sP, sD, ((c + 1) * kTP + (b + 1)) * kTP + (a + 1),
                    cidx(i0 + a, j0 + b, k0 + c, p.nx, p.nxy), E, B);
-        sE[v] = E;
-        sB[v] = B;
+        sE[v] = v4(E.x, E.y, E.z, B.x);
+        sB[v] = V2<T>{B.y, B.z};
       }
       __syncthreads();
       const int beg = offset[tile], end = offset[tile + 1];
-      if (kPre && beg + tid < end) prefetch(P, beg + tid);
+      if (beg + tid < end) prefetch(P, beg + tid);
       // fixed-point scale 2^b of the FP32 charge block (0: tiles of more
       // than 2^16 particles deposit rho in global memory)
       float sb = 0.0f;
@@ -353,7 +372,7 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 3 : 1))
       __syncthreads();
 
       for (int q = beg + tid; q < end; q += blockDim.x) {
-        if (kPre) cp_async_wait_all();
+        cp_async_wait_all();
         tile_particle<kOpt>(
             p, P, q, count, key, rank, lost_ctr,
             [&](int ci, int cj, int ck, const T* ff, T* E, T* B) {
@@ -369,10 +388,11 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 3 : 1))
   #pragma unroll
                     for (int I = 0; I < 2; ++I) {
                       const int v = ((c + K) * kTE + (b + J)) * kTE + (a + I);
-                      const V4<T> e = sE[v], bb = sB[v];
+                      const V4<T> e = sE[v];
+                      const V2<T> bb = sB[v];
                       const T w = wx[I] * wy[J] * wz[K];
                       E[0] += w * e.x; E[1] += w * e.y; E[2] += w * e.z;
-                      B[0] += w * bb.x; B[1] += w * bb.y; B[2] += w * bb.z;
+                      B[0] += w * e.w; B[1] += w * bb.x; B[2] += w * bb.y;
                     }
               } else {
                 gather_eb<kLo>(p, pn, D, ci, cj, ck, ff[0], ff[1], ff[2], E, B);
@@ -396,18 +416,13 @@ __global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 3 : 1))
                                     q);
               }
             },
-            [&](long long qq) { return kPre ? *sl_cell : P.cell[qq]; },
-            [&](long long qq, T* f, U* u) {
-              if (kPre) {
-                f[0] = sl_f[0]; f[1] = sl_f[256]; f[2] = sl_f[512];
-                u[0] = sl_u[0]; u[1] = sl_u[256]; u[2] = sl_u[512];
-              } else {
-                f[0] = P.fx[qq]; f[1] = P.fy[qq]; f[2] = P.fz[qq];
-                u[0] = P.ux[qq]; u[1] = P.uy[qq]; u[2] = P.uz[qq];
-              }
+            [&](long long) { return *sl_cell; },
+            [&](long long, T* f, U* u) {
+              f[0] = sl_f[0]; f[1] = sl_f[kPushThreads]; f[2] = sl_f[2 * kPushThreads];
+              u[0] = sl_u[0]; u[1] = sl_u[kPushThreads]; u[2] = sl_u[2 * kPushThreads];
             },
             [&]() {
-              if (kPre && q + (int)blockDim.x < end) prefetch(P, q + blockDim.x);
+              if (q + (int)blockDim.x < end) prefetch(P, q + blockDim.x);
             });
       }
       __syncthreads();

@@ -72,16 +72,17 @@ __device__ inline void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
-// 4-D tiled TMA load of one box into shared memory, completion counted in
-// bytes on bar.  Coordinate c0 is the innermost (component) index and is
-// always 0 here, so it is 16-byte aligned.
-__device__ inline void tma_load_4d(void* dst, const CUtensorMap* tm, int c0, int c1, int c2, int c3,
-                                   uint64_t* bar) {
+// 3-D tiled TMA load of one box of a field map (encode_field_map) into shared
+// memory, completion counted in bytes on bar.  (i, j, k) is the box's first
+// vertex; the four components of a vertex are folded into the innermost
+// dimension (element 4 i), so the inner coordinate is 16 or 32 bytes times
+// i: a multiple of 16 bytes for every i, negative ones included.
+__device__ inline void tma_load_field(void* dst, const CUtensorMap* tm, int i, int j, int k,
+                                      uint64_t* bar) {
   asm volatile(
-      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_addr(dst)),
-      "l"(reinterpret_cast<uint64_t>(tm)), "r"(c0), "r"(c1), "r"(c2), "r"(c3),
-      "r"(smem_addr(bar))
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(tm)), "r"(4 * i), "r"(j), "r"(k), "r"(smem_addr(bar))
       : "memory");
 }
 
@@ -107,20 +108,23 @@ inline TensorMapEncodeTiled tensor_map_encoder() {
   return fn;
 }
 
-// Tensor map of a 4-component field array (nx*ny*nz cells of 4 values of
-// elem_bytes each, x fastest) with a box of 4 x bx x by x bz values.
+// Tensor map of a 4-component field array (nx*ny*nz vertices of 4 values of
+// elem_bytes each, x fastest) with a box of bx x by x bz vertices.  The map
+// is 3-D with the components folded into x (4 nx values per row, boxes of
+// 4 bx): the TMA unit then moves rows of 4 bx values instead of one vertex
+// (16 or 32 bytes) at a time.
 inline bool encode_field_map(CUtensorMap* tm, void* base, int elem_bytes, int nx, int ny, int nz,
                              int bx, int by, int bz = 1) {
   TensorMapEncodeTiled enc = tensor_map_encoder();
   if (!enc) return false;
-  const cuuint64_t cell = 4ull * elem_bytes;
-  const cuuint64_t dims[4] = {4, (cuuint64_t)nx, (cuuint64_t)ny, (cuuint64_t)nz};
-  const cuuint64_t strides[3] = {cell, cell * nx, cell * nx * ny};
-  const cuuint32_t box[4] = {4, (cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz};
-  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  const cuuint64_t row = 4ull * elem_bytes * nx;
+  const cuuint64_t dims[3] = {4ull * nx, (cuuint64_t)ny, (cuuint64_t)nz};
+  const cuuint64_t strides[2] = {row, row * ny};
+  const cuuint32_t box[3] = {4u * bx, (cuuint32_t)by, (cuuint32_t)bz};
+  const cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = enc(tm, elem_bytes == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                        : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
-                   4, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
