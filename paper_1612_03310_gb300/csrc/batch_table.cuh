@@ -25,6 +25,12 @@ struct PushArgs {
   int* rank;
   long long* lost_ctr;
   long long np;
+  // source-tile flags (StencilP::dirty): two arrays of dirty_words words,
+  // the one of parity cur read by this step's potential update (cleared
+  // here), the other marked for the next
+  unsigned char* dirty;
+  int dirty_words;
+  int cur;
 };
 
 template <typename T, typename U>
@@ -55,6 +61,9 @@ struct BatchMember {
   int scan_nb;
   int sparse_below;
   int fused_mur;  // first-order Mur at the x faces inside the z-marching loop
+  unsigned char* dirty;  // source-tile flags, as in PushArgs
+  int dirty_words;
+  int cur;
 };
 
 // Tensor maps of a member's particle step, collected on the host (the

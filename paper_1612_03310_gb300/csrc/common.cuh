@@ -120,7 +120,10 @@ struct StepState {
   int work;             // next dense entry of the tile list to hand out
   int n_sparse;         // sparse tiles, listed after the dense ones
   int work_sparse;      // next sparse entry to hand out
-  int pad[2];
+  // per level parity c: nonzero when sources may sit outside the tiles
+  // marked in the parity's flag array (see StencilP::dirty), so that the
+  // potential update of parity c reads every vertex's sources
+  int src_all[2];
 };
 
 // Coefficients of the potential update in increment form (r_l = c dt / d_l,
@@ -140,6 +143,14 @@ struct StencilP {
   T m2[3][2];
   int mur2;
   int space_charge;
+  // Sources to read: one flag per 8^3-cell particle tile (tile index
+  // ((k/8) nty + j/8) ntx + i/8 of vertex (i, j, k)), set by the particle
+  // step for the tiles its deposits reached; the sources of an unmarked
+  // tile are zero, and the z-marching update skips their loads unless
+  // *src_all is set.  nullptr: every vertex's sources are read.
+  const unsigned char* dirty;
+  const int* src_all;
+  int ntx, nty;
 };
 
 // Everything the particle and field-evaluation kernels need.

@@ -398,12 +398,16 @@ __device__ __forceinline__ void zloop_body(const StencilP<T>& p, const V4<T>* __
   auto lo = [&](long long q) { return ld_lo<T>(curlo, q); };
   PlaneTerms<T> tm = plane_terms<kLo>(p, hi, lo, (long long)(kb - 1) * p.nxy + col, nx);
   PlaneTerms<T> t0 = plane_terms<kLo>(p, hi, lo, (long long)kb * p.nxy + col, nx);
+  // sources: loaded (and cleared) in the tiles the particle step marked only
+  const bool src_every = p.dirty == nullptr || *p.src_all != 0;
+  const int trow = (j >> 3) * p.ntx + (i >> 3), ntxy = p.ntx * p.nty;
   for (int k = kb; k < ke; ++k) {
     const long long q = (long long)k * p.nxy + col;
     const PlaneTerms<T> tp = plane_terms<kLo>(p, hi, lo, q + p.nxy, nx);
     const V4<T> L = terms_laplacian<kLo>(p, tm, t0, tp);
     const V4<T> dm = D[q];
-    const V4<T> sv = src[q];
+    V4<T> sv = v4((T)0, (T)0, (T)0, (T)0);
+    if (src_every || p.dirty[(k >> 3) * ntxy + trow] != 0) sv = src[q];
     V4<T> dp = dm + (L + source_term(p, sv));
     if (kMur && xwarp) {  // warp-uniform
       const V4<T> dq = v4(__shfl_sync(live, dp.x, from), __shfl_sync(live, dp.y, from),

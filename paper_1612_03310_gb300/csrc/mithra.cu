@@ -51,6 +51,10 @@ struct mithra_sim {
   int* count = nullptr;
   int* offset = nullptr;
   int* tiles = nullptr;  // non-empty tile list written by the scan
+  // source-tile flags of the two level parities (StencilP::dirty), each
+  // dirty_words words
+  unsigned char* dirty = nullptr;
+  int dirty_words = 0;
   int4* scan_part = nullptr;  // block sums of the two-pass scan
   StepState* dstate = nullptr;
   double* d_scalar = nullptr;   // one-off reductions
@@ -462,9 +466,28 @@ unsigned blocks_for(long long n, int threads) {
   return (unsigned)(b < 1 ? 1 : b);
 }
 
+// Marks the sources of both level parities as possibly nonzero anywhere, so
+// that the next two potential updates read every vertex's (after writers
+// that mark no tiles: the initial deposit, the per-particle step, a set or
+// restored source field).
+void mark_sources_everywhere(mithra_sim* s) {
+  cudaMemsetAsync(reinterpret_cast<char*>(s->dstate) + offsetof(StepState, src_all), 1,
+                  sizeof(StepState::src_all), s->stream);
+}
+
+// The source-tile flags of level parity c in the stencil parameters.
+template <typename T>
+void set_source_flags(const mithra_sim* s, int c, StencilP<T>* sp) {
+  sp->dirty = s->dirty + (size_t)c * 4 * s->dirty_words;
+  sp->src_all = &s->dstate->src_all[c];
+  sp->ntx = s->ntx;
+  sp->nty = s->nty;
+}
+
 template <typename T, typename U>
 mithra_status launch_step(mithra_sim* s) {
-  const StencilP<T> sp = make_stencil<T>(s->g);
+  StencilP<T> sp = make_stencil<T>(s->g);
+  set_source_flags(s, s->cur, &sp);
   PicP<T> pp = make_pic<T>(s);
   V4<T>* P0 = static_cast<V4<T>*>(s->P[s->cur]);       // psi^n
   V4<T>* P1 = static_cast<V4<T>*>(s->P[1 - s->cur]);   // receives psi^{n+1}
@@ -587,6 +610,9 @@ mithra_status launch_step(mithra_sim* s) {
         pa.rank = s->rank;
         pa.lost_ctr = &s->dstate->n_lost;
         pa.np = s->np;
+        pa.dirty = s->dirty;
+        pa.dirty_words = s->dirty_words;
+        pa.cur = s->cur;
         kern<<<s->push_grid, kPushThreads, tile_smem_bytes<T, U>(), s->stream>>>(prm);
       } else {
         decltype(&k_push<false, T, U, kAnyLo>) kern = nullptr;
@@ -598,6 +624,7 @@ mithra_status launch_step(mithra_sim* s) {
         kern<<<blocks_for(s->np, 256), 256, 0, s->stream>>>(pp, s->dstate, P1, Dn, S, A, s->np,
                                                              s->count, s->key, s->rank,
                                                              &s->dstate->n_lost);
+        mark_sources_everywhere(s);  // this form marks no tiles
       }
     }
     if (s->bunch_every > 0) {
@@ -647,6 +674,7 @@ mithra_status init_particles(mithra_sim* s, const mithra_bunch* b) {
   s->pb = 1;
   k_deposit_rho<T, U><<<blocks_for(n, 256), 256, 0, s->stream>>>(pp, B, n,
                                                               static_cast<V4<T>*>(s->S));
+  mark_sources_everywhere(s);
   MCHECK(s, cudaGetLastError());
   MCHECK(s, cudaStreamSynchronize(s->stream));
   MCHECK(s, cudaFree(d));
@@ -729,6 +757,7 @@ mithra_status set_field_impl(mithra_sim* s, int what, const double* in) {
   MCHECK(s, cudaMalloc(&d, sizeof(double) * n));
   MCHECK(s, cudaMemcpyAsync(d, in, sizeof(double) * n, cudaMemcpyHostToDevice, s->stream));
   k_insert<T><<<1024, 256, 0, s->stream>>>(n, d, dst, dstlo, comp);
+  if (dst == static_cast<V4<T>*>(s->S)) mark_sources_everywhere(s);
   if (dst != static_cast<V4<T>*>(s->S))
     k_increment<T><<<1024, 256, 0, s->stream>>>(n, static_cast<const V4<T>*>(s->P[s->cur]),
                                                 static_cast<const V4<T>*>(s->P[1 - s->cur]),
@@ -829,7 +858,7 @@ void lab_of(const mithra_sim* s, int32_t kp, double t, double* t_lab, double* z_
 void free_all(mithra_sim* s) {
   if (s->stream) cudaStreamSynchronize(s->stream);
   void* ptrs[] = {s->P[0], s->P[1], s->PL[0], s->PL[1], s->D, s->S, s->pbuf[0], s->pbuf[1], s->key, s->rank, s->count,
-                  s->offset, s->tiles, s->scan_part, s->dstate, s->d_scalar, s->d_power_rec,
+                  s->offset, s->tiles, s->dirty, s->scan_part, s->dstate, s->d_scalar, s->d_power_rec,
                   s->d_spec_omega, s->d_spec_acc, s->d_spec_out, s->d_spec_samples,
                   s->d_bunch_rec, s->d_bunch_part};
   for (void* p : ptrs)
@@ -877,6 +906,7 @@ mithra_status mithra_footprint(const mithra_grid* grid, int64_t n_particles,
   b += 2 * (int64_t)particle_buffer_bytes(n_particles, precision);
   b += 2 * n_particles * (int64_t)sizeof(int);                   // key, rank
   b += 3 * (nkeys + 2) * (int64_t)sizeof(int);                   // count, offset, tiles
+  b += 8 * ((nkeys + 3) / 4);                                     // source-tile flags
   b += (nkeys / kScanBlock + 2) * (int64_t)sizeof(int4);         // scan block sums
   b += (int64_t)sizeof(StepState) + (int64_t)sizeof(double);
   *bytes = b;
@@ -932,6 +962,7 @@ mithra_status mithra_create(const mithra_grid* grid, const mithra_undulator* und
   s->np = np;
   tiles_of(grid, &s->ntx, &s->nty, &s->ntz);
   s->nkeys = s->ntx * s->nty * s->ntz;
+  s->dirty_words = (s->nkeys + 3) / 4;
   auto bail = [&](mithra_status code, const std::string& msg) {
     free_all(s);
     delete s;
@@ -956,6 +987,7 @@ mithra_status mithra_create(const mithra_grid* grid, const mithra_undulator* und
             dalloc((void**)&s->count, sizeof(int) * (size_t)(s->nkeys + 2)) &&
             dalloc((void**)&s->offset, sizeof(int) * (size_t)(s->nkeys + 2)) &&
             dalloc((void**)&s->tiles, sizeof(int) * (size_t)(s->nkeys + 1)) &&
+            dalloc((void**)&s->dirty, 8 * (size_t)s->dirty_words) &&
             dalloc((void**)&s->scan_part, sizeof(int4) * (size_t)(s->nkeys / kScanBlock + 2)) &&
             dalloc((void**)&s->dstate, sizeof(StepState)) &&
             dalloc((void**)&s->d_scalar, sizeof(double));
@@ -975,6 +1007,8 @@ mithra_status mithra_create(const mithra_grid* grid, const mithra_undulator* und
   cudaMemsetAsync(s->S, 0, field_bytes, s->stream);
   cudaMemsetAsync(s->count, 0, sizeof(int) * (size_t)(s->nkeys + 2), s->stream);
   cudaMemsetAsync(s->dstate, 0, sizeof(StepState), s->stream);
+  cudaMemsetAsync(s->dirty, 0, 8 * (size_t)s->dirty_words, s->stream);
+  mark_sources_everywhere(s);
   {
     const int es = (int)r;
     s->have_tm = encode_field_map(&s->tm[0], s->P[0], es, grid->nx, grid->ny, grid->nz,
@@ -1598,6 +1632,7 @@ mithra_status mithra_restore(mithra_sim* s, const void* in) {
     MCHECK(s, cudaMemcpyAsync(part.dev, p, part.bytes, cudaMemcpyHostToDevice, s->stream));
     p += part.bytes;
   }
+  mark_sources_everywhere(s);
   MCHECK(s, refresh_mirror(s));
   mithra_status st = sync_status(s);
   // a strict count starts again from the restored state
@@ -1769,6 +1804,10 @@ BatchMember<T, U> member_entry(mithra_sim* s, int c, int pb) {
   m.scan_nb = (s->nkeys + 1 + kScanBlock - 1) / kScanBlock;
   m.sparse_below = 0;  // the fused particle step stages every tile
   m.fused_mur = s->g.boundary == 1;
+  set_source_flags(s, c, &m.sp);
+  m.dirty = s->dirty;
+  m.dirty_words = s->dirty_words;
+  m.cur = c;
   return m;
 }
 
@@ -1789,6 +1828,9 @@ PushArgs<T, U> push_args_of(const BatchMember<T, U>& m) {
   a.rank = m.rank;
   a.lost_ctr = &m.st->n_lost;
   a.np = m.np;
+  a.dirty = m.dirty;
+  a.dirty_words = m.dirty_words;
+  a.cur = m.cur;
   return a;
 }
 

@@ -301,6 +301,31 @@ __global__ void __launch_bounds__(kPushThreads, (sizeof(T) == 4 ? 3 : 1))
   }
   __syncthreads();
   uint32_t phase = 0;
+  // Source-tile flags (StencilP::dirty): the array this step's potential
+  // update read is cleared, and the deposits mark the other -- a tile's 27
+  // neighbours, which hold every vertex a particle of the tile deposits to
+  // while its end and mid-point cells stay within [t0 - 8, t0 + 14] on each
+  // axis (t0 the tile's first cell); a deposit beyond that sets src_all of
+  // the next parity instead.
+  auto clear_flags = [&](const PushArgs<T, U>& a) {
+    unsigned* f = reinterpret_cast<unsigned*>(a.dirty) + (size_t)a.cur * a.dirty_words;
+    for (int w = blockIdx.x * blockDim.x + tid; w < a.dirty_words; w += gridDim.x * blockDim.x)
+      f[w] = 0u;
+    if (blockIdx.x == 0 && tid == 0) a.st->src_all[a.cur] = 0;
+  };
+  auto mark_tile = [&](const PushArgs<T, U>& a, int tile, int r) {  // neighbour r of 27
+    const PicP<T>& p = a.p;
+    const int tx = tile % p.ntx + r % 3 - 1, ty = (tile / p.ntx) % p.nty + (r / 3) % 3 - 1,
+              tz = tile / (p.ntx * p.nty) + r / 9 - 1;
+    if (tx >= 0 && tx < p.ntx && ty >= 0 && ty < p.nty && tz >= 0 && tz < p.ntz)
+      a.dirty[(size_t)(1 - a.cur) * 4 * a.dirty_words + ((size_t)tz * p.nty + ty) * p.ntx + tx] =
+          1;
+  };
+  auto far_deposit = [&](const PushArgs<T, U>& a, int i0, int j0, int k0, int i, int j, int k) {
+    if ((unsigned)(i - i0 + 8) > 22u || (unsigned)(j - j0 + 8) > 22u ||
+        (unsigned)(k - k0 + 8) > 22u)
+      a.st->src_all[1 - a.cur] = 1;
+  };
   auto prefetch = [&](const Parts<T, U>& P, long long qq) {
     cp_async<4>(sl_cell, P.cell + qq);
     cp_async<sizeof(T)>(sl_f, P.fx + qq);
@@ -339,6 +364,7 @@ __global__ void __launch_bounds__(kPushThreads, (sizeof(T) == 4 ? 3 : 1))
         tma_load_field(sP, tmp, i0 - 1, j0 - 1, k0 - 1, bar);
         tma_load_field(sD, tmd, i0 - 1, j0 - 1, k0 - 1, bar);
       }
+      if (tid < 27) mark_tile(a, tile, tid);
       // FP64 moving-window bookkeeping once per tile and sub-step
       for (int m = tid; m < p.n_sub && m < kMaxFrames; m += blockDim.x)
         s_frame[m] = und_frame(p, k0, th + m * p.dtb);
@@ -403,6 +429,7 @@ __global__ void __launch_bounds__(kPushThreads, (sizeof(T) == 4 ? 3 : 1))
               return m < kMaxFrames ? s_frame[m] : und_frame(p, k0, th + m * p.dtb);
             },
             [&](bool rho, int i, int j, int k, const T* f, T jx, T jy, T jz, T q) {
+              far_deposit(a, i0, j0, k0, i, j, k);
               if (kF32) {
                 if (rho)
                   deposit_rho_fixed(p, sRh, sRl, src, i0, j0, k0, i, j, k, f[0], f[1], f[2], sb);
@@ -481,6 +508,7 @@ __global__ void __launch_bounds__(kPushThreads, (sizeof(T) == 4 ? 3 : 1))
         const int tile = tiles[ntiles + w];
         int i0, j0, k0;
         tile_origin(p, tile, &i0, &j0, &k0);
+        if (lane < 27) mark_tile(a, tile, lane);
         __syncwarp();
         for (int m = lane; m < p.n_sub && m < kMaxFrames; m += 32)
           wf[m] = und_frame(p, k0, th + m * p.dtb);
@@ -497,6 +525,7 @@ __global__ void __launch_bounds__(kPushThreads, (sizeof(T) == 4 ? 3 : 1))
                 return m < kMaxFrames ? wf[m] : und_frame(p, k0, th + m * p.dtb);
               },
               [&](bool rho, int i, int j, int k, const T* f, T jx, T jy, T jz, T q) {
+                far_deposit(a, i0, j0, k0, i, j, k);
                 deposit_cic(p, src, i, j, k, f[0], f[1], f[2], jx, jy, jz, q);
               },
               [&](long long qq) { return P.cell[qq]; },
@@ -518,6 +547,7 @@ __global__ void __launch_bounds__(kPushThreads, (sizeof(T) == 4 ? 3 : 1))
   };
   if constexpr (!kBatch) {
     const PushArgs<T, U>& a = prm.args;
+    clear_flags(a);
     const int ntiles = a.st->n_tiles;
     const double th = a.p.t0 + ((double)a.st->n + 0.5) * a.p.dt;
     for (;;) {  // the CTA takes tiles from the list until none is left
@@ -532,6 +562,7 @@ __global__ void __launch_bounds__(kPushThreads, (sizeof(T) == 4 ? 3 : 1))
     // the group's non-empty tiles (the dense and the sparse entries of each
     // member's list, all staged) from one counter
     const int M = prm.M;
+    for (int r = 0; r < M; ++r) clear_flags(prm.m[r]);
     for (;;) {
       if (tid == 0) s_tile = atomicAdd(prm.work, 1);
       __syncthreads();
