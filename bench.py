@@ -157,13 +157,6 @@ PRECISIONS = {"p32": "P32", "p32_u64": "P32_U64", "p32_c": "P32_C", "p64": "P64"
 # now, by (timed scope, precision, workload); a kernel changed since its
 # capture must leave this table
 NCU_TRAFFIC = {
-    # k_mur_boundary<0, float, 1, 1> + k_potential_zloop_mur1<0, float>
-    ("potential_step", "p32", "c2"): 28196096 + 61696 + 824917760 + 509206016,
-    ("push", "p32", "c2"): 179321088 + 62403328,
-    # k_mur_boundary<1, float, 1, 1> + k_potential_zloop_mur1<1, float>
-    ("potential_step", "p32_u64", "c2"): 35244992 + 18752 + 973243712 + 638126848,
-    # k_push_tiled<0, float, FF2, 1>
-    ("push", "p32_u64", "c2"): 231833856 + 90103168,
 }
 
 
@@ -184,18 +177,24 @@ def push_rates(kt: dict, n_particles: int, grid: dict, prec: str) -> dict | None
             "l2_vector_reductions_per_s": (8 * n_particles / s) if prec != "p64" else None}
 
 
-def algorithmic_bytes(kernel: str, grid: dict, n_particles: int, prec: str) -> float:
-    """Algorithmic bytes per launch (the minimum a kernel must move)."""
+def algorithmic_bytes(kernel: str, grid: dict, n_particles: int, prec: str,
+                      source_vertices: int | None = None) -> float:
+    """Algorithmic bytes per launch (the minimum a kernel must move).
+    source_vertices: the vertices whose sources the potential update reads
+    (the vertices of the tiles the particle step marked; None: every
+    interior vertex)."""
     r = 8 if prec == "p64" else 4                      # field and fraction values
     um = 4 if prec in ("p32", "p32_c") else 8          # momenta
     lo = prec in ("p32_c", "p32_u64")                  # compensated potential levels
     interior = (grid["nx"] - 2) * (grid["ny"] - 2) * (grid["nz"] - 2)
     if kernel == "potential_step":
-        # read psi^n, the increment and the sources; write psi^{n+1} and the
-        # new increment: 5 x 4 values per interior cell, plus 2 x 8 bytes for
-        # the bfloat16 lo parts of compensated levels (the zeroing stores of
-        # the sources the last deposit touched are not counted)
-        return interior * (5 * 4 * r + (16 if lo else 0))
+        # read psi^n and the increment, write psi^{n+1} and the new
+        # increment: 4 x 4 values per interior cell, plus 2 x 8 bytes for the
+        # bfloat16 lo parts of compensated levels; and the 4 source values of
+        # every vertex of a marked tile (the zeroing stores of the sources
+        # the last deposit touched are not counted)
+        sv = interior if source_vertices is None else min(source_vertices, interior)
+        return interior * (4 * 4 * r + (16 if lo else 0)) + sv * 4 * r
     if kernel == "push":
         # read and write cell + 3 fractions + 3 momenta; write key and rank
         return n_particles * (2 * (4 + 3 * r + 3 * um) + 8)
@@ -238,6 +237,14 @@ def max_over_ranks(x: float, world: int) -> float:
 
 def interior_cells(g: dict) -> int:
     return (g["nx"] - 2) * (g["ny"] - 2) * (g["nz"] - 2)
+
+
+def source_reads(sim, g: dict) -> dict:
+    """The source tiles the simulation's next potential update reads, and
+    their vertices (512 a tile, at most the interior)."""
+    marked, everywhere = sim.source_tiles()
+    verts = interior_cells(g) if everywhere else min(512 * marked, interior_cells(g))
+    return {"marked_tiles": marked, "everywhere": everywhere, "vertices": verts}
 
 
 def replica_bunch(workload: dict, rank: int) -> dict:
@@ -316,6 +323,7 @@ def run_gpu(args, rank, world):
     sim.profile(False)
     power = sim.read_power()
     parts = sim.copy_particles()
+    src_reads = source_reads(sim, g)
     sim.close()
     ms = max_over_ranks(ms, world)
     rec = autotune.record(g, n_part, prec) or {}
@@ -324,6 +332,7 @@ def run_gpu(args, rank, world):
                tuning=tuning, trials=[{k: (round(v, 4) if k == "ms" else v) for k, v in t.items()}
                                       for t in rec.get("trials", [])],
                grid=g, n_lost=parts["n_lost"], power_last=float(power[-1, 0]),
+               source_reads=src_reads,
                launches=sum(n * KERNELS_PER_SCOPE.get(k, 1) for k, (_, n) in kt.items()))
 
     # the other precision forms on the same workload, shorter: P64 (plain
@@ -345,9 +354,10 @@ def run_gpu(args, rank, world):
         sim.step(steps)
         torch.cuda.synchronize()
         kts = sim.kernel_times()
+        src = source_reads(sim, g)
         sim.close()
         ms_side = max_over_ranks(ms_side, world)
-        return dict(ms=ms_side, steps=steps, kernel_times=kts)
+        return dict(ms=ms_side, steps=steps, kernel_times=kts, source_reads=src)
 
     if not args.no_p64 and prec != mithra.P64:
         res["p64"] = side_run(mithra.P64, max(20, K // 10))
@@ -416,13 +426,14 @@ def run_c3(args, peak: float) -> dict:
     kt = sim.kernel_times()
     sim.profile(False)
     n_lost = sim.copy_particles()["n_lost"]
+    src = source_reads(sim, g)
     sim.close()
     s = ms / 1e3
     dom = max(kt, key=lambda k: kt[k][0])
     dom_ms = kt[dom][0] / max(kt[dom][1], 1)
-    ab = algorithmic_bytes(dom, g, n_part, args.precision)
+    ab = algorithmic_bytes(dom, g, n_part, args.precision, src["vertices"])
     st_ms = kt["potential_step"][0] / max(kt["potential_step"][1], 1)
-    st_b = algorithmic_bytes("potential_step", g, n_part, args.precision)
+    st_b = algorithmic_bytes("potential_step", g, n_part, args.precision, src["vertices"])
     total = sum(v[0] for v in kt.values())
     return {"workload": inputs.describe("c3"), "precision": args.precision, "steps": K3,
             "ms_per_step": ms / K3, "cell_updates_per_s": ncell * K3 / s,
@@ -434,7 +445,8 @@ def run_c3(args, peak: float) -> dict:
                          "traffic": None},
             "stencil": {"avg_launch_ms": st_ms, "achieved_gbs": st_b / (st_ms / 1e3) / 1e9,
                         "frac": st_b / (st_ms / 1e3) / 1e9 / peak,
-                        "cell_updates_per_s": ncell / (st_ms / 1e3)},
+                        "cell_updates_per_s": ncell / (st_ms / 1e3),
+                        "bytes_per_cell": st_b / interior_cells(g), "source_reads": src},
             "kernel_share": {k: round(v[0] / total, 4) for k, v in kt.items()},
             "tuning": tuning, "clocks": sampler.summary(), "n_lost": n_lost}
 
@@ -795,11 +807,12 @@ def main():
     kt = res["kernel_times"]
     dom = max(kt, key=lambda k: kt[k][0])
     avg_ms = kt[dom][0] / max(kt[dom][1], 1)
-    ab = algorithmic_bytes(dom, res["grid"], npart, args.precision)
+    sv = res["source_reads"]["vertices"]
+    ab = algorithmic_bytes(dom, res["grid"], npart, args.precision, sv)
     achieved = ab / (avg_ms / 1e3) / 1e9
     stencil_ms = kt["potential_step"][0] / max(kt["potential_step"][1], 1)
-    stencil_gbs = algorithmic_bytes("potential_step", res["grid"], npart, args.precision) / (
-        stencil_ms / 1e3) / 1e9
+    stencil_b = algorithmic_bytes("potential_step", res["grid"], npart, args.precision, sv)
+    stencil_gbs = stencil_b / (stencil_ms / 1e3) / 1e9
     stencil_min_gbs = minimum_bytes("potential_step", res["grid"], npart, args.precision) / (
         stencil_ms / 1e3) / 1e9
     total_kernel_ms = sum(v[0] for v in kt.values())
@@ -816,8 +829,8 @@ def main():
                      "traffic": NCU_TRAFFIC.get((dom, args.precision, args.workload))},
         "stencil": {"kernel": "potential_step", "avg_launch_ms": stencil_ms,
                     "achieved_gbs": stencil_gbs, "frac": stencil_gbs / peak,
-                    "bytes_per_cell": algorithmic_bytes("potential_step", res["grid"], npart,
-                                                        args.precision) / interior_cells(g),
+                    "bytes_per_cell": stencil_b / interior_cells(g),
+                    "source_reads": res["source_reads"],
                     "frac_at_minimum_bytes": stencil_min_gbs / peak,
                     "minimum_bytes_per_cell": minimum_bytes("potential_step", res["grid"], npart,
                                                             args.precision) / interior_cells(g),
@@ -844,7 +857,8 @@ def main():
                       "cell_updates_per_s": world * ncell * p["steps"] / (p["ms"] / 1e3),
                       "particle_pushes_per_s": world * npart * p["steps"] / (p["ms"] / 1e3),
                       "stencil_gbs": algorithmic_bytes("potential_step", res["grid"], npart,
-                                                       side) / (sts / 1e3) / 1e9,
+                                                       side, p["source_reads"]["vertices"])
+                      / (sts / 1e3) / 1e9,
                       "kernel_ms_per_launch": {k: v[0] / max(v[1], 1) for k, v in kts.items()
                                                if v[1]}}
     if "e2e" in res:

@@ -288,6 +288,21 @@ mithra_status mithra_kernel_times(mithra_sim* sim, double* ms, int64_t* launches
                                   int32_t max_kernels, int32_t* n_kernels);
 const char* mithra_kernel_name(int32_t kernel);
 
+/* Source tiles the next potential update reads (Sec. "Current Deposition"
+ * deposits J and rho at the vertices around each particle; the update of
+ * the potentials (Eq. waveEquation) adds them).  The particle step marks
+ * the 8x8x8-cell tiles (tile index ((k/8) nty + j/8) ntx + i/8 of vertex
+ * (i, j, k), ntx = ceil(nx/8), nty = ceil(ny/8)) that its deposits reached,
+ * and the z-marching update loads the sources of marked tiles only; the
+ * sources of every other tile are zero.  *marked receives the number of
+ * tiles marked for the next step, *everywhere 1 when that update reads the
+ * sources of every vertex instead (after the initial deposit, a step of the
+ * per-particle form, a set or restored source field, or a deposit further
+ * than one tile from its particle's tile) and 0 otherwise.  Waits for the
+ * simulation's stream.  Errors: MITHRA_EINVAL for a NULL argument,
+ * MITHRA_ECUDA when a copy fails. */
+mithra_status mithra_source_tiles(mithra_sim* sim, int64_t* marked, int32_t* everywhere);
+
 /* Seed field (Sec. "Seed Field"; input group field-initialization),
  * injected by the total-field/scattered-field technique: wave describes a
  * wave along z in the lab frame with the parameters of an optical undulator

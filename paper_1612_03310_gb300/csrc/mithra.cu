@@ -1503,6 +1503,22 @@ mithra_status mithra_kernel_times(mithra_sim* s, double* ms, int64_t* launches,
   return MITHRA_OK;
 }
 
+mithra_status mithra_source_tiles(mithra_sim* s, int64_t* marked, int32_t* everywhere) {
+  if (!s || !marked || !everywhere) return fail(s, MITHRA_EINVAL, "sim and outputs must not be NULL");
+  std::vector<unsigned char> f((size_t)4 * s->dirty_words);
+  int all = 0;
+  MCHECK(s, cudaMemcpyAsync(f.data(), s->dirty + (size_t)s->cur * 4 * s->dirty_words, f.size(),
+                            cudaMemcpyDeviceToHost, s->stream));
+  MCHECK(s, cudaMemcpyAsync(&all, &s->dstate->src_all[s->cur], sizeof(int),
+                            cudaMemcpyDeviceToHost, s->stream));
+  MCHECK(s, cudaStreamSynchronize(s->stream));
+  int64_t n = 0;
+  for (int t = 0; t < s->nkeys; ++t) n += f[t] != 0;
+  *marked = n;
+  *everywhere = all != 0;
+  return MITHRA_OK;
+}
+
 const char* mithra_kernel_name(int32_t kernel) {
   return (kernel >= 0 && kernel < K_COUNT) ? kKernelNames[kernel] : nullptr;
 }

@@ -205,13 +205,19 @@ __device__ inline void tile_particle(const PicP<T>& p, const Parts<T, U>& P, lon
     } else {
       P.cell[q] = (int)cidx(i, j, k, p.nx, p.nxy);
       P.fx[q] = f[0]; P.fy[q] = f[1]; P.fz[q] = f[2];
+      // the bucket's rank first: its atomic's round trip overlaps the
+      // deposits
+      kk = tile_key(p, i, j, k);
+      const int r = bin_rank(count, kk);
       dep(true, i, j, k, f, (T)0, (T)0, (T)0, p.qV);
       T mf[3];
       const int mi = split_cell_t(ia, f0[0] + (T)0.5 * disp[0], &mf[0]);
       const int mj = split_cell_t(ja, f0[1] + (T)0.5 * disp[1], &mf[1]);
       const int mk = split_cell_t(ka, f0[2] + (T)0.5 * disp[2], &mf[2]);
       dep(false, mi, mj, mk, mf, p.jx * disp[0], p.jy * disp[1], p.jz * disp[2], (T)0);
-      kk = tile_key(p, i, j, k);
+      key[q] = kk;
+      rank[q] = r;
+      return;
     }
   }
   key[q] = kk;
@@ -356,6 +362,8 @@ __global__ void __launch_bounds__(kPushThreads, (sizeof(T) == 4 ? 3 : 1))
     long long* const& lost_ctr = a.lost_ctr;
     {
       const int tile = tiles[t];
+      // the tile's particle range, loaded while the boxes are in flight
+      const int beg = offset[tile], end = offset[tile + 1];
       int i0, j0, k0;
       tile_origin(p, tile, &i0, &j0, &k0);
       if (tid == 0) {
@@ -381,7 +389,6 @@ __global__ void __launch_bounds__(kPushThreads, (sizeof(T) == 4 ? 3 : 1))
         sB[v] = V2<T>{B.y, B.z};
       }
       __syncthreads();
-      const int beg = offset[tile], end = offset[tile + 1];
       if (beg + tid < end) prefetch(P, beg + tid);
       // fixed-point scale 2^b of the FP32 charge block (0: tiles of more
       // than 2^16 particles deposit rho in global memory)

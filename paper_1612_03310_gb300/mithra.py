@@ -26,6 +26,7 @@ EXPORTS = ["mithra_create", "mithra_step", "mithra_sync", "mithra_time", "mithra
            "mithra_set_power_sampling", "mithra_read_power", "mithra_copy_particles",
            "mithra_destroy", "mithra_last_error", "mithra_check_grid", "mithra_footprint",
            "mithra_version", "mithra_profile", "mithra_kernel_times", "mithra_kernel_name",
+           "mithra_source_tiles",
            "mithra_set_tuning", "mithra_get_tuning", "mithra_plane_power_noalloc",
            "mithra_batch_create", "mithra_batch_add", "mithra_batch_remove", "mithra_batch_step",
            "mithra_batch_sync", "mithra_batch_size", "mithra_batch_last_error",
@@ -123,6 +124,7 @@ def lib():
     L.mithra_profile.argtypes = [vp, C.c_int32]
     L.mithra_kernel_times.argtypes = [vp, dp, C.POINTER(C.c_int64), C.c_int32,
                                       C.POINTER(C.c_int32)]
+    L.mithra_source_tiles.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int32)]
     L.mithra_kernel_name.argtypes = [C.c_int32]
     L.mithra_kernel_name.restype = C.c_char_p
     L.mithra_plane_power_noalloc.argtypes = [C.POINTER(Grid), C.c_double, C.c_int, vp, vp, vp,
@@ -476,6 +478,14 @@ class Simulation:
         for k in range(nk.value):
             out[lib().mithra_kernel_name(k).decode()] = (float(ms[k]), int(n[k]))
         return out
+
+    def source_tiles(self) -> tuple[int, bool]:
+        """(tiles whose sources the next potential update reads, whether it
+        reads every vertex's instead)."""
+        n = C.c_int64()
+        e = C.c_int32()
+        _check(lib().mithra_source_tiles(self.h, C.byref(n), C.byref(e)), self.h)
+        return int(n.value), bool(e.value)
 
     def close(self):
         if getattr(self, "h", None):

@@ -515,3 +515,53 @@ def test_workload_c3_first_step_sampled(M, orc):
         for a, (key, d) in enumerate((("x", "dx"), ("y", "dy"), ("z", "dz"))):
             r1 = P[key][q] + v[a] * g["dt"]
             assert abs(parts[key][q] - r1) <= 2e-5 * g[d]
+
+
+# ---------------------------------------------------------------------------
+# source tiles: the particle step marks the 27 tiles around every tile that
+# holds particles, and the z-marching update then skips the others' sources
+
+def expected_marked_tiles(g, P):
+    """Tiles of the 27-neighbourhoods of the tiles holding particles at P."""
+    ntx, nty, ntz = -(-g["nx"] // 8), -(-g["ny"] // 8), -(-g["nz"] // 8)
+    keep = P["lost"] == 0
+    cell = [np.floor((P[c][keep] - g[c + "0"]) / g["d" + c] + 1e-9).astype(np.int64) // 8
+            for c in ("x", "y", "z")]
+    flags = np.zeros((ntz + 2, nty + 2, ntx + 2), dtype=bool)
+    for dz in (-1, 0, 1):
+        for dy in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                flags[cell[2] + 1 + dz, cell[1] + 1 + dy, cell[0] + 1 + dx] = True
+    return int(flags[1:-1, 1:-1, 1:-1].sum())
+
+
+@pytest.mark.parametrize("prec,push_variant,sparse_below", [
+    ("P32_U64", 1, 16), ("P64", 1, 0), ("P32", 1, 1 << 30), ("P32", 0, 0)])
+def test_source_tiles_marked(M, orc, prec, push_variant, sparse_below):
+    w = inputs.workload("c1")
+    P0 = inputs.make_bunch(w["bunch_spec"], w["seed"])
+    g, und = dict(w["grid"], boundary=1), w["undulator"]
+    o = orc.OracleSim(g, und, P0)
+    with M.Simulation(g, und, P0, precision=getattr(M, prec)) as sim:
+        sim.set_tuning(push_variant=push_variant, push_sparse_below=sparse_below)
+        # the initial deposit marks no tiles: both parities read every source
+        assert sim.source_tiles()[1]
+        sim.step(1)
+        assert sim.source_tiles()[1]
+        sim.step(2)
+        P = sim.copy_particles()
+        sim.step(1)
+        sim.sync()
+        marked, everywhere = sim.source_tiles()
+        if push_variant == 0:
+            assert everywhere  # the per-particle form marks no tiles
+        else:
+            assert not everywhere
+            assert marked == expected_marked_tiles(g, P)
+        # the skipped sources were zero: the fields still follow the oracle
+        o.step(4)
+        for _ in range(3):
+            sim.step(1)
+            o.step(1)
+        sim.sync()
+        compare_fields(sim, o, 1e-10 if prec == "P64" else 1e-4)
