@@ -2009,6 +2009,11 @@ mithra_status capture_graph(mithra_batch* b);
 // counting the captures and their host time.
 mithra_status capture(mithra_batch* b) {
   const auto t0 = std::chrono::steady_clock::now();
+  // the graph launched last may still be reading the device tables that the
+  // capture rewrites (with copies outside the batch's stream): let it finish
+  const cudaError_t se = cudaStreamSynchronize(b->stream);
+  if (se != cudaSuccess)
+    return bfail(b, MITHRA_ECUDA, std::string("batch stream: ") + cudaGetErrorString(se));
   drop_graph(b);
   b->fused_now = false;
   mithra_status st;
