@@ -39,6 +39,11 @@ struct mithra_sim {
   double q_macro = 0.0;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
+  // the plane diagnostics (power, spectrum) of a step run on a side stream
+  // beside the particle step, forked after the potential update and joined
+  // before the re-sort advances the step counter
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   int cur = 0;  // P[cur] holds the newest level
   int pb = 0;   // particle buffer in use
   void* P[2] = {nullptr, nullptr};  // psi ping-pong; P[cur] is the newest level
@@ -563,9 +568,17 @@ mithra_status launch_step(mithra_sim* s) {
         k_seed_tfsf<false, T><<<grd, blk, 0, s->stream>>>(sp, s->seed, s->dstate, P1, L1, Dn);
     }
   }
+  // with per-kernel timing every kernel stays on the simulation's stream
+  const bool branch = !s->profiling && (s->power_cap > 0 || s->spec_nf > 0);
+  cudaStream_t dq = s->stream;
+  if (branch) {
+    cudaEventRecord(s->ev_fork, s->stream);
+    cudaStreamWaitEvent(s->side, s->ev_fork, 0);
+    dq = s->side;
+  }
   if (s->power_cap > 0) {
     ProfScope ps(s, K_POWER);
-    k_power<T><<<64, 256, 0, s->stream>>>(pp, P1, Dn, s->power_plane, s->u.gamma0,
+    k_power<T><<<64, 256, 0, dq>>>(pp, P1, Dn, s->power_plane, s->u.gamma0,
                                           std::sqrt(1.0 - 1.0 / (s->u.gamma0 * s->u.gamma0)),
                                           s->d_power_rec - s->power_first, s->dstate,
                                           s->power_first + s->power_cap, 1, &s->dstate->err);
@@ -574,7 +587,7 @@ mithra_status launch_step(mithra_sim* s) {
     ProfScope ps(s, K_SPECTRUM);
     const double g0 = s->u.gamma0;
     const long long nv = (long long)(s->g.nx - 2) * (s->g.ny - 2);
-    k_spectrum_accumulate<T><<<blocks_for(nv, 256), 256, 0, s->stream>>>(
+    k_spectrum_accumulate<T><<<blocks_for(nv, 256), 256, 0, dq>>>(
         pp, P1, Dn, s->spec_plane, g0, std::sqrt(1.0 - 1.0 / (g0 * g0)),
         s->g.z0 + s->spec_plane * s->g.dz, s->dstate, s->spec_nf, s->d_spec_omega,
         s->d_spec_acc, s->d_spec_samples);
@@ -635,6 +648,10 @@ mithra_status launch_step(mithra_sim* s) {
       k_bunch_final<<<1, 32, 0, s->stream>>>(s->d_bunch_part, nb, s->d_bunch_rec, s->dstate,
                                              s->bunch_first, s->bunch_every, s->bunch_cap);
     }
+    if (branch) {
+      cudaEventRecord(s->ev_join, s->side);
+      cudaStreamWaitEvent(s->stream, s->ev_join, 0);
+    }
     {
       ProfScope ps(s, K_SCAN);
       launch_scan(s, 1);
@@ -646,6 +663,10 @@ mithra_status launch_step(mithra_sim* s) {
     }
     s->pb = 1 - s->pb;
   } else {
+    if (branch) {
+      cudaEventRecord(s->ev_join, s->side);
+      cudaStreamWaitEvent(s->stream, s->ev_join, 0);
+    }
     launch_scan(s, 1);
   }
   s->cur = 1 - s->cur;
@@ -871,6 +892,9 @@ void free_all(mithra_sim* s) {
   for (cudaEvent_t e : s->spare) cudaEventDestroy(e);
   for (cudaGraphExec_t e : s->step_exec)
     if (e) cudaGraphExecDestroy(e);
+  if (s->side) cudaStreamDestroy(s->side);
+  if (s->ev_fork) cudaEventDestroy(s->ev_fork);
+  if (s->ev_join) cudaEventDestroy(s->ev_join);
   if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
 }
 
@@ -975,6 +999,10 @@ mithra_status mithra_create(const mithra_grid* grid, const mithra_undulator* und
       return bail(MITHRA_ECUDA, "stream creation failed");
     s->own_stream = true;
   }
+  if (cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming) != cudaSuccess)
+    return bail(MITHRA_ECUDA, "side stream creation failed");
   const size_t r = real_size(precision);
   const size_t field_bytes = (size_t)ncell_of(grid) * 4 * r;
   auto dalloc = [&](void** p, size_t bytes) { return cudaMalloc(p, bytes < 256 ? 256 : bytes) == cudaSuccess; };
