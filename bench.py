@@ -158,13 +158,13 @@ PRECISIONS = {"p32": "P32", "p32_u64": "P32_U64", "p32_c": "P32_C", "p64": "P64"
 # capture must leave this table
 NCU_TRAFFIC = {
     # k_mur_boundary<1, float, 1, 1> + k_potential_zloop_mur1<1, float>
-    ("potential_step", "p32_u64", "c2"): 35242240 + 231936 + 771630336 + 634868480,
+    ("potential_step", "p32_u64", "c2"): 35241984 + 226560 + 725267200 + 634713088,
     # k_push_tiled<0, float, FF2, 1, 0>
-    ("push", "p32_u64", "c2"): 230904576 + 85007360,
+    ("push", "p32_u64", "c2"): 232227328 + 88694272,
     # k_mur_boundary<0, float, 1, 1> + k_potential_zloop_mur1<0, float>
-    ("potential_step", "p32", "c2"): 28195840 + 45056 + 627343872 + 498310656,
+    ("potential_step", "p32", "c2"): 28196864 + 56832 + 588861184 + 498598912,
     # k_push_tiled<0, float, float, 0, 0>
-    ("push", "p32", "c2"): 179510528 + 58136320,
+    ("push", "p32", "c2"): 179453696 + 59533312,
 }
 
 
