@@ -57,9 +57,10 @@ typedef enum {
 typedef enum {
     MITHRA_P64 = 0,      /* all state and arithmetic in FP64 */
     MITHRA_P32 = 1,      /* FP32 fields and particle phase space with FP32
-                            arithmetic; FP64 frame clock, lab-frame phase of
-                            the undulator, cell carry of positions and power
-                            accumulation; the particle 1/gamma to FP32
+                            arithmetic; positions as an integer cell and an
+                            FP32 fraction in it; FP64 frame clock, lab-frame
+                            phase of the undulator and power accumulation;
+                            the particle 1/gamma to FP32
                             rounding from an exactly summed 1 + u.u and one
                             float-float Newton step */
     MITHRA_P32_U64 = 2,  /* as MITHRA_P32, but the potential levels are kept as
