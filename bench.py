@@ -218,11 +218,10 @@ def algorithmic_bytes(kernel: str, grid: dict, n_particles: int, prec: str,
 
 
 def minimum_bytes(kernel: str, grid: dict, n_particles: int, prec: str) -> float:
-    """The algorithmic minimum of the survey's table for the potential update
-    (read psi^n, psi^{n-1} and the source, write psi^{n+1}: 16 words per
-    cell, plus the bfloat16 lo parts of compensated levels read and
-    written); the increment form's extra read and write of the increment
-    are not in it."""
+    """The algorithmic minimum of a three-level potential update (read
+    psi^n, psi^{n-1} and the source, write psi^{n+1}: 16 words per cell,
+    plus the bfloat16 lo parts of compensated levels read and written); the
+    increment form's extra read and write of the increment are not in it."""
     if kernel != "potential_step":
         return algorithmic_bytes(kernel, grid, n_particles, prec)
     r = 8 if prec == "p64" else 4
