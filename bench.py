@@ -160,11 +160,11 @@ NCU_TRAFFIC = {
     # k_mur_boundary<1, float, 1, 1> + k_potential_zloop_mur1<1, float>
     ("potential_step", "p32_u64", "c2"): 35241984 + 226560 + 725267200 + 634713088,
     # k_push_tiled<0, float, FF2, 1, 0>
-    ("push", "p32_u64", "c2"): 232227328 + 88694272,
+    ("push", "p32_u64", "c2"): None,
     # k_mur_boundary<0, float, 1, 1> + k_potential_zloop_mur1<0, float>
     ("potential_step", "p32", "c2"): 28196864 + 56832 + 588861184 + 498598912,
     # k_push_tiled<0, float, float, 0, 0>
-    ("push", "p32", "c2"): 179453696 + 59533312,
+    ("push", "p32", "c2"): None,
 }
 
 
@@ -204,11 +204,13 @@ def algorithmic_bytes(kernel: str, grid: dict, n_particles: int, prec: str,
         sv = interior if source_vertices is None else min(source_vertices, interior)
         return interior * (4 * 4 * r + (16 if lo else 0)) + sv * 4 * r
     if kernel == "push":
-        # read and write cell + 3 fractions + 3 momenta; write key and rank
-        return n_particles * (2 * (4 + 3 * r + 3 * um) + 8)
+        # read the slot's position, read and write cell + 3 fractions + 3
+        # momenta + original index; write key and rank
+        return n_particles * (4 + 2 * (8 + 3 * r + 3 * um) + 8)
     if kernel == "scatter":
-        # read key, rank, offset and the particle; write the particle
-        return n_particles * (12 + 2 * (8 + 3 * r + 3 * um))
+        # the re-sort's slot map: read key, rank and offset, write the slot's
+        # position
+        return n_particles * 16
     if kernel == "scan_counts":
         ntiles = -(-grid["nx"] // 8) * -(-grid["ny"] // 8) * -(-grid["nz"] // 8)
         return ntiles * 12

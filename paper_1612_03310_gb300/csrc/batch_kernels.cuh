@@ -1,7 +1,7 @@
 // batch_kernels.cuh -- one field step of many simulations of uneven size in
 // a fixed handful of launches: every phase of the step (boundary rest,
 // potential update, power sample, particle step, the two scan passes of the
-// re-sort, the scatter) is one kernel over a work list that spans all
+// re-sort, the slot map) is one kernel over a work list that spans all
 // members, instead of one launch per member and phase.  The members share
 // the precision form and the undulator type (the template arguments); each
 // member's sizes, coefficients, buffers and tensor maps sit in a device
@@ -195,7 +195,7 @@ __global__ void __launch_bounds__(kScanBlock) kb_scan_final(
                   m.st, 1, g - blk[mi]);
 }
 
-// Scatter into tile order, 256 particles per block.
+// The re-sort's slot map (slot_one), 256 particles per block.
 template <typename T, typename U>
 __global__ void __launch_bounds__(256) kb_scatter(const BatchMember<T, U>* __restrict__ mem,
                                                   const int* __restrict__ blk, int M) {
@@ -204,7 +204,7 @@ __global__ void __launch_bounds__(256) kb_scatter(const BatchMember<T, U>* __res
   const BatchMember<T, U>& m = mem[mi];
   const long long q = (long long)(g - blk[mi]) * blockDim.x + threadIdx.x;
   if (q >= m.np) return;
-  scatter_one(m.A, m.B, q, m.key, m.rank, m.offset);
+  slot_one(q, m.key, m.rank, m.offset, m.perm);
 }
 
 }  // namespace mithra

@@ -17,7 +17,9 @@ struct PushArgs {
   const V4<T>* pn;  // psi^{n+1}
   const V4<T>* D;   // increment
   V4<T>* src;
-  Parts<T, U> P;
+  Parts<T, U> P;      // the particles, at the positions perm gives
+  Parts<T, U> O;      // receives them in slot order (the other buffer)
+  const int* perm;    // slot of the tile order -> position in P
   const int* offset;
   const int* tiles;
   int* count;
@@ -43,7 +45,8 @@ struct BatchMember {
   LoV4* L1;
   V4<T>* D;
   V4<T>* S;
-  Parts<T, U> A, B;  // particles in use, and the buffer of the re-sort
+  Parts<T, U> A, B;  // particles in use, and the buffer the particle step writes
+  int* perm;         // slot of the tile order -> position in A (the re-sort's output)
   int* offset;
   int* tiles;
   int* count;

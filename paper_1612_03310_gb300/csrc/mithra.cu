@@ -50,7 +50,12 @@ struct mithra_sim {
   void* D = nullptr;                // increment newest - previous level
   void* S = nullptr;
   void* PL[2] = {nullptr, nullptr};  // lo parts of the compensated levels (P32_C, P32_U64)
+  // particles: pbuf[pb] holds them at the positions perm gives for the
+  // slots of the tile order (perm[slot] = position); the particle step
+  // writes them to pbuf[1 - pb] in slot order, and the re-sort writes the
+  // next perm
   void* pbuf[2] = {nullptr, nullptr};
+  int* perm = nullptr;
   int* key = nullptr;
   int* rank = nullptr;
   int* count = nullptr;
@@ -616,6 +621,8 @@ mithra_status launch_step(mithra_sim* s) {
         pa.D = Dn;
         pa.src = S;
         pa.P = A;
+        pa.O = B;
+        pa.perm = s->perm;
         pa.offset = s->offset;
         pa.tiles = s->tiles;
         pa.count = s->count;
@@ -634,16 +641,16 @@ mithra_status launch_step(mithra_sim* s) {
         if constexpr (push_form_lo<T, U>())
           if (lo) kern = opt ? k_push<true, T, U, true> : k_push<false, T, U, true>;
         if (!kern) return fail(s, MITHRA_EINVAL, "no particle-step form for this precision");
-        kern<<<blocks_for(s->np, 256), 256, 0, s->stream>>>(pp, s->dstate, P1, Dn, S, A, s->np,
-                                                             s->count, s->key, s->rank,
-                                                             &s->dstate->n_lost);
+        kern<<<blocks_for(s->np, 256), 256, 0, s->stream>>>(pp, s->dstate, P1, Dn, S, A, B,
+                                                             s->perm, s->np, s->count, s->key,
+                                                             s->rank, &s->dstate->n_lost);
         mark_sources_everywhere(s);  // this form marks no tiles
       }
     }
     if (s->bunch_every > 0) {
       ProfScope ps(s, K_SPECTRUM);
       const int nb = (int)std::min<long long>(blocks_for(s->np, 256), 1024);
-      k_bunch_partial<T, U><<<nb, 256, 0, s->stream>>>(pp, A, s->np, s->bunch_kb, s->d_bunch_part,
+      k_bunch_partial<T, U><<<nb, 256, 0, s->stream>>>(pp, B, s->np, s->bunch_kb, s->d_bunch_part,
                                                         s->dstate, s->bunch_first, s->bunch_every);
       k_bunch_final<<<1, 32, 0, s->stream>>>(s->d_bunch_part, nb, s->d_bunch_rec, s->dstate,
                                              s->bunch_first, s->bunch_every, s->bunch_cap);
@@ -658,8 +665,8 @@ mithra_status launch_step(mithra_sim* s) {
     }
     {
       ProfScope ps(s, K_SCATTER);
-      k_scatter<T, U><<<blocks_for(s->np, 256), 256, 0, s->stream>>>(A, B, s->np, s->key,
-                                                                     s->rank, s->offset);
+      k_slot_map<<<blocks_for(s->np, 256), 256, 0, s->stream>>>(s->np, s->key, s->rank,
+                                                                  s->offset, s->perm);
     }
     s->pb = 1 - s->pb;
   } else {
@@ -691,7 +698,8 @@ mithra_status init_particles(mithra_sim* s, const mithra_bunch* b) {
       pp, n, d, d + n, d + 2 * n, d + 3 * n, d + 4 * n, d + 5 * n, A, s->count, s->key, s->rank,
       lost);
   launch_scan(s, 0);
-  k_scatter<T, U><<<blocks_for(n, 256), 256, 0, s->stream>>>(A, B, n, s->key, s->rank, s->offset);
+  k_sort_particles<T, U><<<blocks_for(n, 256), 256, 0, s->stream>>>(A, B, n, s->key, s->rank,
+                                                                    s->offset, s->perm);
   s->pb = 1;
   k_deposit_rho<T, U><<<blocks_for(n, 256), 256, 0, s->stream>>>(pp, B, n,
                                                               static_cast<V4<T>*>(s->S));
@@ -878,7 +886,7 @@ void lab_of(const mithra_sim* s, int32_t kp, double t, double* t_lab, double* z_
 
 void free_all(mithra_sim* s) {
   if (s->stream) cudaStreamSynchronize(s->stream);
-  void* ptrs[] = {s->P[0], s->P[1], s->PL[0], s->PL[1], s->D, s->S, s->pbuf[0], s->pbuf[1], s->key, s->rank, s->count,
+  void* ptrs[] = {s->P[0], s->P[1], s->PL[0], s->PL[1], s->D, s->S, s->pbuf[0], s->pbuf[1], s->perm, s->key, s->rank, s->count,
                   s->offset, s->tiles, s->dirty, s->scan_part, s->dstate, s->d_scalar, s->d_power_rec,
                   s->d_spec_omega, s->d_spec_acc, s->d_spec_out, s->d_spec_samples,
                   s->d_bunch_rec, s->d_bunch_part};
@@ -928,7 +936,7 @@ mithra_status mithra_footprint(const mithra_grid* grid, int64_t n_particles,
   int64_t b = 4 * ncell_of(grid) * 4 * (int64_t)r;              // 2 levels, increment, sources
   if (has_lo(precision)) b += 2 * ncell_of(grid) * (int64_t)sizeof(LoV4);  // lo parts
   b += 2 * (int64_t)particle_buffer_bytes(n_particles, precision);
-  b += 2 * n_particles * (int64_t)sizeof(int);                   // key, rank
+  b += 3 * n_particles * (int64_t)sizeof(int);                   // slot map, key, rank
   b += 3 * (nkeys + 2) * (int64_t)sizeof(int);                   // count, offset, tiles
   b += 8 * ((nkeys + 3) / 4);                                     // source-tile flags
   b += (nkeys / kScanBlock + 2) * (int64_t)sizeof(int4);         // scan block sums
@@ -1010,6 +1018,7 @@ mithra_status mithra_create(const mithra_grid* grid, const mithra_undulator* und
             dalloc(&s->D, field_bytes) && dalloc(&s->S, field_bytes) &&
             dalloc(&s->pbuf[0], particle_buffer_bytes(np, precision)) &&
             dalloc(&s->pbuf[1], particle_buffer_bytes(np, precision)) &&
+            dalloc((void**)&s->perm, sizeof(int) * (size_t)(np + 1)) &&
             dalloc((void**)&s->key, sizeof(int) * (size_t)(np + 1)) &&
             dalloc((void**)&s->rank, sizeof(int) * (size_t)(np + 1)) &&
             dalloc((void**)&s->count, sizeof(int) * (size_t)(s->nkeys + 2)) &&
@@ -1619,6 +1628,7 @@ std::vector<SnapPart> snap_parts(const mithra_sim* s) {
     v.push_back({s->PL[1], cells * sizeof(LoV4)});
   }
   v.push_back({s->pbuf[s->pb], particle_buffer_bytes(s->np, s->prec)});
+  v.push_back({s->perm, sizeof(int) * (size_t)s->np});
   v.push_back({s->count, sizeof(int) * (size_t)(s->nkeys + 2)});
   v.push_back({s->offset, sizeof(int) * (size_t)(s->nkeys + 2)});
   v.push_back({s->tiles, sizeof(int) * (size_t)(s->nkeys + 1)});
@@ -1830,6 +1840,7 @@ BatchMember<T, U> member_entry(mithra_sim* s, int c, int pb) {
   m.S = static_cast<V4<T>*>(s->S);
   m.A = parts_of<T, U>(s, pb);
   m.B = parts_of<T, U>(s, 1 - pb);
+  m.perm = s->perm;
   m.offset = s->offset;
   m.tiles = s->tiles;
   m.count = s->count;
@@ -1865,6 +1876,8 @@ PushArgs<T, U> push_args_of(const BatchMember<T, U>& m) {
   a.D = m.D;
   a.src = m.S;
   a.P = m.A;
+  a.O = m.B;
+  a.perm = m.perm;
   a.offset = m.offset;
   a.tiles = m.tiles;
   a.count = m.count;

@@ -464,27 +464,47 @@ __device__ inline bool push_particle(const PicP<T>& p, int& i, int& j, int& k, T
   return true;
 }
 
+// Particle at position from of buffer a to position to of buffer b (lost
+// particles, which the particle step moves without pushing them).
+template <typename T, typename U>
+__device__ inline void copy_particle(const Parts<T, U>& a, const Parts<T, U>& b, long long from,
+                                     long long to) {
+  b.cell[to] = a.cell[from];
+  b.fx[to] = a.fx[from];
+  b.fy[to] = a.fy[from];
+  b.fz[to] = a.fz[from];
+  b.ux[to] = a.ux[from];
+  b.uy[to] = a.uy[from];
+  b.uz[to] = a.uz[from];
+  b.id[to] = a.id[from];
+}
+
 // One field step of every particle: n_sub Boris steps with the grid E, B at
 // t = (n+1/2) dt held fixed and the undulator at each sub-step time, then the
 // deposit of J^{n+1} at the mid point of the path and rho^{n+3/2} at the end,
-// and the key/rank of the particle's new tile for the re-sort.
+// and the key/rank of the particle's new tile for the re-sort.  Slot q's
+// particle is read at position perm[q] of P and written to slot q of O.
 template <bool kOpt, typename T, typename U, bool kLo = false>
 __global__ void __launch_bounds__(256) k_push(PicP<T> p, const StepState* __restrict__ st,
                                               const V4<T>* __restrict__ pn,
                                               const V4<T>* __restrict__ D,
-                                              V4<T>* __restrict__ src, Parts<T, U> P, long long np,
-                                              int* __restrict__ count, int* __restrict__ key,
-                                              int* __restrict__ rank,
+                                              V4<T>* __restrict__ src, Parts<T, U> P,
+                                              Parts<T, U> O, const int* __restrict__ perm,
+                                              long long np, int* __restrict__ count,
+                                              int* __restrict__ key, int* __restrict__ rank,
                                               long long* __restrict__ lost_ctr) {
   const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (q >= np) return;
-  const int cell = P.cell[q];
+  const long long pos = perm[q];
+  const int cell = P.cell[pos];
   int kk = p.nkeys;  // bucket of lost particles
+  if (cell < 0) copy_particle(P, O, pos, q);
   if (cell >= 0) {
+    O.id[q] = P.id[pos];
     int i, j, k;
     decode_cell(p, cell, &i, &j, &k);
-    T f[3] = {P.fx[q], P.fy[q], P.fz[q]};
-    U u[3] = {P.ux[q], P.uy[q], P.uz[q]};
+    T f[3] = {P.fx[pos], P.fy[pos], P.fz[pos]};
+    U u[3] = {P.ux[pos], P.uy[pos], P.uz[pos]};
     const int i0 = i, j0 = j, k0 = k;
     const T f0[3] = {f[0], f[1], f[2]};
     T disp[3];
@@ -498,13 +518,14 @@ __global__ void __launch_bounds__(256) k_push(PicP<T> p, const StepState* __rest
           *kref = kc;
           return und_frame(p, kc, th + m * p.dtb);
         });
-    P.ux[q] = u[0]; P.uy[q] = u[1]; P.uz[q] = u[2];
+    O.ux[q] = u[0]; O.uy[q] = u[1]; O.uz[q] = u[2];
     if (!ok) {
-      P.cell[q] = -1;
+      O.cell[q] = -1;
+      O.fx[q] = f0[0]; O.fy[q] = f0[1]; O.fz[q] = f0[2];
       atomicAdd(reinterpret_cast<unsigned long long*>(lost_ctr), 1ULL);
     } else {
-      P.cell[q] = (int)cidx(i, j, k, p.nx, p.nxy);
-      P.fx[q] = f[0]; P.fy[q] = f[1]; P.fz[q] = f[2];
+      O.cell[q] = (int)cidx(i, j, k, p.nx, p.nxy);
+      O.fx[q] = f[0]; O.fy[q] = f[1]; O.fz[q] = f[2];
       // rho^{n+3/2} at the end position
       deposit_cic(p, src, i, j, k, f[0], f[1], f[2], (T)0, (T)0, (T)0, p.qV);
       // J^{n+1} at the mid point of the path
@@ -678,49 +699,40 @@ __global__ void __launch_bounds__(kScanBlock) k_scan_final(int* __restrict__ cou
                   blockIdx.x);
 }
 
-// Streaming load and store of a stored momentum (FF2 as one 8-byte word).
-template <typename U>
-__device__ inline U ldcs_u(const U* a) { return __ldcs(a); }
-template <>
-__device__ inline FF2 ldcs_u<FF2>(const FF2* a) {
-  const float2 v = __ldcs(reinterpret_cast<const float2*>(a));
-  FF2 r;
-  r.hi = v.x;
-  r.lo = v.y;
-  return r;
-}
-template <typename U>
-__device__ inline void stcs_u(U* a, U v) { __stcs(a, v); }
-template <>
-__device__ inline void stcs_u<FF2>(FF2* a, FF2 v) {
-  __stcs(reinterpret_cast<float2*>(a), make_float2(v.hi, v.lo));
+// The re-sort: slot offset[key] + rank of the next step's tile order gets
+// the position q at which the particle step left the particle (the
+// particles stay where they are; the next particle step reads each slot's
+// particle through this map and writes it to that slot of the other
+// buffer).
+__device__ __forceinline__ void slot_one(long long q, const int* __restrict__ key,
+                                         const int* __restrict__ rank,
+                                         const int* __restrict__ offset, int* __restrict__ perm) {
+  perm[(long long)offset[key[q]] + rank[q]] = (int)q;
 }
 
-// Moves every particle to offset[key] + rank in the other buffer.
+// The initial sort: every particle moved to its slot offset[key] + rank of
+// the other buffer, and the slot map the identity (the first particle step
+// then reads each tile's particles contiguously).
 template <typename T, typename U>
-__device__ __forceinline__ void scatter_one(const Parts<T, U>& a, const Parts<T, U>& b,
-                                            long long q, const int* __restrict__ key,
-                                            const int* __restrict__ rank,
-                                            const int* __restrict__ offset) {
-  // streaming loads and stores (the potential update in between evicts the
-  // particles from L2 anyway): 39 instead of 45 us on c2
-  const long long d = (long long)__ldcs(offset + __ldcs(key + q)) + __ldcs(rank + q);
-  __stcs(b.cell + d, __ldcs(a.cell + q));
-  __stcs(b.fx + d, __ldcs(a.fx + q));
-  __stcs(b.fy + d, __ldcs(a.fy + q));
-  __stcs(b.fz + d, __ldcs(a.fz + q));
-  stcs_u(b.ux + d, ldcs_u(a.ux + q));
-  stcs_u(b.uy + d, ldcs_u(a.uy + q));
-  stcs_u(b.uz + d, ldcs_u(a.uz + q));
-  __stcs(b.id + d, __ldcs(a.id + q));
-}
-
-template <typename T, typename U>
-__global__ void k_scatter(Parts<T, U> a, Parts<T, U> b, long long np, const int* __restrict__ key,
-                          const int* __restrict__ rank, const int* __restrict__ offset) {
+__global__ void __launch_bounds__(256) k_sort_particles(Parts<T, U> a, Parts<T, U> b, long long np,
+                                                        const int* __restrict__ key,
+                                                        const int* __restrict__ rank,
+                                                        const int* __restrict__ offset,
+                                                        int* __restrict__ perm) {
   const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (q >= np) return;
-  scatter_one(a, b, q, key, rank, offset);
+  const long long d = (long long)offset[key[q]] + rank[q];
+  copy_particle(a, b, q, d);
+  perm[d] = (int)d;
+}
+
+__global__ void __launch_bounds__(256) k_slot_map(long long np, const int* __restrict__ key,
+                                                  const int* __restrict__ rank,
+                                                  const int* __restrict__ offset,
+                                                  int* __restrict__ perm) {
+  const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (q >= np) return;
+  slot_one(q, key, rank, offset, perm);
 }
 
 // Copy-out in the original particle order: FP64 positions from (cell, f).

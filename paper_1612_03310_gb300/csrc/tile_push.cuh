@@ -68,15 +68,15 @@ __host__ __device__ constexpr int tile_smem_bytes() {
   return tile_bar_offset<T>() + 16;
 }
 // The next-particle slots of the dense loop (one particle per thread: cell,
-// fractions, momenta) in the increment box, which is free once E and B are
-// built.
+// fractions, momenta, original index, and the position of the particle
+// after it) in the increment box, which is free once E and B are built.
 template <typename T>
 __host__ __device__ constexpr int tile_slot_offset() {
   return tile_box_stride<T>();
 }
 template <typename T, typename U>
 __host__ __device__ constexpr int tile_slot_bytes() {
-  return kPushThreads * (4 + 3 * (int)sizeof(T) + 3 * (int)sizeof(U));
+  return kPushThreads * (4 + 3 * (int)sizeof(T) + 3 * (int)sizeof(U) + 8);
 }
 
 // E, B at local vertex l of the potential box (strides 1, 11, 121), global
@@ -173,38 +173,48 @@ __device__ inline void deposit_rho_fixed(const PicP<T>& p, int* __restrict__ hi,
 // One particle's field step (shared by the staged and the per-warp path):
 // push, then the deposits of rho at the end point and J at the mid point
 // through dep(kRho, i, j, k, f, jx, jy, jz, rho), and the re-sort bucket.
-// The particle's state comes from ld_cell(q) and ld_fu(q, f, u); next() is
-// called once the state has been consumed (after the push, or for a lost
-// particle after its cell), where the dense loop starts the copy of the
-// thread's next particle into the slot it read.
+// The particle in slot q of the tile order comes from ld_cell(), ld_fu(f, u)
+// and ld_id() (the state buffer at the slot's position) and goes to slot q
+// of the output buffer O, complete (a lost particle too), so that O holds
+// every particle in slot order.  next() is called once the state has been
+// consumed (after the push, or for a lost particle after its loads), where
+// the dense loop starts the copy of the thread's next particle into the
+// slot it read.
 template <bool kOpt, typename T, typename U, typename Gather, typename Frame, typename Dep,
-          typename LdCell, typename LdFU, typename Next>
-__device__ inline void tile_particle(const PicP<T>& p, const Parts<T, U>& P, long long q,
+          typename LdCell, typename LdFU, typename LdId, typename Next>
+__device__ inline void tile_particle(const PicP<T>& p, const Parts<T, U>& O, long long q,
                                      int* __restrict__ count, int* __restrict__ key,
                                      int* __restrict__ rank, long long* __restrict__ lost_ctr,
                                      Gather&& gather, Frame&& frame, Dep&& dep, LdCell&& ld_cell,
-                                     LdFU&& ld_fu, Next&& next) {
-  const int cell = ld_cell(q);
+                                     LdFU&& ld_fu, LdId&& ld_id, Next&& next) {
+  const int cell = ld_cell();
+  const int id = ld_id();
+  T f[3];
+  U u[3];
+  ld_fu(f, u);
+  O.id[q] = id;
   int kk = p.nkeys;
-  if (cell < 0) next();
-  if (cell >= 0) {
+  if (cell < 0) {
+    next();
+    O.cell[q] = cell;
+    O.fx[q] = f[0]; O.fy[q] = f[1]; O.fz[q] = f[2];
+    O.ux[q] = u[0]; O.uy[q] = u[1]; O.uz[q] = u[2];
+  } else {
     int i, j, k;
     decode_cell(p, cell, &i, &j, &k);
-    T f[3];
-    U u[3];
-    ld_fu(q, f, u);
     const int ia = i, ja = j, ka = k;
     const T f0[3] = {f[0], f[1], f[2]};
     T disp[3];
     const bool ok = push_particle<kOpt>(p, i, j, k, f, u, disp, gather, frame);
     next();
-    P.ux[q] = u[0]; P.uy[q] = u[1]; P.uz[q] = u[2];
+    O.ux[q] = u[0]; O.uy[q] = u[1]; O.uz[q] = u[2];
     if (!ok) {
-      P.cell[q] = -1;
+      O.cell[q] = -1;
+      O.fx[q] = f0[0]; O.fy[q] = f0[1]; O.fz[q] = f0[2];
       atomicAdd(reinterpret_cast<unsigned long long*>(lost_ctr), 1ULL);
     } else {
-      P.cell[q] = (int)cidx(i, j, k, p.nx, p.nxy);
-      P.fx[q] = f[0]; P.fy[q] = f[1]; P.fz[q] = f[2];
+      O.cell[q] = (int)cidx(i, j, k, p.nx, p.nxy);
+      O.fx[q] = f[0]; O.fy[q] = f[1]; O.fz[q] = f[2];
       // the bucket's rank first: its atomic's round trip overlaps the
       // deposits
       kk = tile_key(p, i, j, k);
@@ -237,7 +247,7 @@ __device__ inline void tile_origin(const PicP<T>& p, int tile, int* i0, int* j0,
 // global memory): one simulation's arguments and tensor maps, or those of up
 // to kPushGroup batch members, whose non-empty tiles, numbered member after
 // member by pref, one counter hands out.
-constexpr int kPushGroup = 32;  // 32 x (688 + 256) B (FP64) of the 32 KB parameter space
+constexpr int kPushGroup = 30;  // 30 x (792 + 256) B (FP64) of the 32 KB parameter space
 
 // Member of tile number w of a batch group: pref[m] <= w < pref[m+1].
 __device__ inline int member_of_tile(const int* __restrict__ pref, int M, int w) {
@@ -294,6 +304,11 @@ __global__ void __launch_bounds__(kPushThreads, (sizeof(T) == 4 ? 3 : 1))
   U* sl_u = reinterpret_cast<U*>(smem + tile_slot_offset<T>() +
                                  kPushThreads * (4 + 3 * (int)sizeof(T))) +
             threadIdx.x;
+  int* sl_id = reinterpret_cast<int*>(smem + tile_slot_offset<T>() +
+                                      kPushThreads * (4 + 3 * (int)sizeof(T) +
+                                                      3 * (int)sizeof(U))) +
+               threadIdx.x;
+  int* sl_pos = sl_id + kPushThreads;
   T* sJ = reinterpret_cast<T*>(sP);
   int* sRh = reinterpret_cast<int*>(sP);
   int* sRl = sRh + kTPC;
@@ -332,15 +347,32 @@ __global__ void __launch_bounds__(kPushThreads, (sizeof(T) == 4 ? 3 : 1))
         (unsigned)(k - k0 + 8) > 22u)
       a.st->src_all[1 - a.cur] = 1;
   };
-  auto prefetch = [&](const Parts<T, U>& P, long long qq) {
-    cp_async<4>(sl_cell, P.cell + qq);
-    cp_async<sizeof(T)>(sl_f, P.fx + qq);
-    cp_async<sizeof(T)>(sl_f + kPushThreads, P.fy + qq);
-    cp_async<sizeof(T)>(sl_f + 2 * kPushThreads, P.fz + qq);
-    cp_async<sizeof(U)>(sl_u, P.ux + qq);
-    cp_async<sizeof(U)>(sl_u + kPushThreads, P.uy + qq);
-    cp_async<sizeof(U)>(sl_u + 2 * kPushThreads, P.uz + qq);
+  // the particle at position pos of the state buffer into this thread's
+  // slot, and the position of the slot after it (qn, when below end) into
+  // sl_pos: issued after the particle's copies, which read the old sl_pos
+  auto prefetch = [&](const Parts<T, U>& P, const int* perm, long long pos, long long qn,
+                      int end) {
+    cp_async<4>(sl_cell, P.cell + pos);
+    cp_async<sizeof(T)>(sl_f, P.fx + pos);
+    cp_async<sizeof(T)>(sl_f + kPushThreads, P.fy + pos);
+    cp_async<sizeof(T)>(sl_f + 2 * kPushThreads, P.fz + pos);
+    cp_async<sizeof(U)>(sl_u, P.ux + pos);
+    cp_async<sizeof(U)>(sl_u + kPushThreads, P.uy + pos);
+    cp_async<sizeof(U)>(sl_u + 2 * kPushThreads, P.uz + pos);
+    cp_async<4>(sl_id, P.id + pos);
+    if (qn < end) cp_async<4>(sl_pos, perm + qn);
     cp_async_commit();
+  };
+  // the slots after the last tile's (particles lost before this step): moved
+  // to the output buffer, their bucket kept
+  auto lost_tail = [&](const PushArgs<T, U>& a) {
+    const int nk = a.p.nkeys;
+    for (long long q = a.offset[nk] + (long long)blockIdx.x * blockDim.x + tid; q < a.np;
+         q += (long long)gridDim.x * blockDim.x) {
+      copy_particle(a.P, a.O, a.perm[q], q);
+      a.key[q] = nk;
+      a.rank[q] = bin_rank(a.count, nk);
+    }
   };
   // the dense tiles of one simulation's list, then its sparse tiles and lost
   // tail (each written once; one simulation runs them straight through, a
@@ -354,6 +386,8 @@ __global__ void __launch_bounds__(kPushThreads, (sizeof(T) == 4 ? 3 : 1))
     const V4<T>* const& D = a.D;
     V4<T>* const& src = a.src;
     const Parts<T, U>& P = a.P;
+    const Parts<T, U>& O = a.O;
+    const int* const& perm = a.perm;
     const int* const& offset = a.offset;
     const int* const& tiles = a.tiles;
     int* const& count = a.count;
@@ -389,7 +423,7 @@ __global__ void __launch_bounds__(kPushThreads, (sizeof(T) == 4 ? 3 : 1))
         sB[v] = V2<T>{B.y, B.z};
       }
       __syncthreads();
-      if (beg + tid < end) prefetch(P, beg + tid);
+      if (beg + tid < end) prefetch(P, perm, perm[beg + tid], beg + tid + kPushThreads, end);
       // fixed-point scale 2^b of the FP32 charge block (0: tiles of more
       // than 2^16 particles deposit rho in global memory)
       float sb = 0.0f;
@@ -407,7 +441,7 @@ __global__ void __launch_bounds__(kPushThreads, (sizeof(T) == 4 ? 3 : 1))
       for (int q = beg + tid; q < end; q += blockDim.x) {
         cp_async_wait_all();
         tile_particle<kOpt>(
-            p, P, q, count, key, rank, lost_ctr,
+            p, O, q, count, key, rank, lost_ctr,
             [&](int ci, int cj, int ck, const T* ff, T* E, T* B) {
               const int a = ci - i0, b = cj - j0, c = ck - k0;
               if (a >= 0 && a < kTile && b >= 0 && b < kTile && c >= 0 && c < kTile) {
@@ -450,13 +484,15 @@ __global__ void __launch_bounds__(kPushThreads, (sizeof(T) == 4 ? 3 : 1))
                                     q);
               }
             },
-            [&](long long) { return *sl_cell; },
-            [&](long long, T* f, U* u) {
+            [&]() { return *sl_cell; },
+            [&](T* f, U* u) {
               f[0] = sl_f[0]; f[1] = sl_f[kPushThreads]; f[2] = sl_f[2 * kPushThreads];
               u[0] = sl_u[0]; u[1] = sl_u[kPushThreads]; u[2] = sl_u[2 * kPushThreads];
             },
+            [&]() { return *sl_id; },
             [&]() {
-              if (q + (int)blockDim.x < end) prefetch(P, q + blockDim.x);
+              if (q + kPushThreads < end)
+                prefetch(P, perm, *sl_pos, q + 2 * kPushThreads, end);
             });
       }
       __syncthreads();
@@ -492,6 +528,8 @@ __global__ void __launch_bounds__(kPushThreads, (sizeof(T) == 4 ? 3 : 1))
     const V4<T>* const& D = a.D;
     V4<T>* const& src = a.src;
     const Parts<T, U>& P = a.P;
+    const Parts<T, U>& O = a.O;
+    const int* const& perm = a.perm;
     const int* const& offset = a.offset;
     const int* const& tiles = a.tiles;
     int* const& count = a.count;
@@ -522,8 +560,9 @@ __global__ void __launch_bounds__(kPushThreads, (sizeof(T) == 4 ? 3 : 1))
         __syncwarp();
         const int beg = offset[tile], end = offset[tile + 1];
         for (int q = beg + lane; q < end; q += 32) {
+          const long long pos = perm[q];
           tile_particle<kOpt>(
-              p, P, q, count, key, rank, lost_ctr,
+              p, O, q, count, key, rank, lost_ctr,
               [&](int ci, int cj, int ck, const T* ff, T* E, T* B) {
                 gather_eb<kLo>(p, pn, D, ci, cj, ck, ff[0], ff[1], ff[2], E, B);
               },
@@ -535,22 +574,19 @@ __global__ void __launch_bounds__(kPushThreads, (sizeof(T) == 4 ? 3 : 1))
                 far_deposit(a, i0, j0, k0, i, j, k);
                 deposit_cic(p, src, i, j, k, f[0], f[1], f[2], jx, jy, jz, q);
               },
-              [&](long long qq) { return P.cell[qq]; },
-              [&](long long qq, T* f, U* u) {
-                f[0] = P.fx[qq]; f[1] = P.fy[qq]; f[2] = P.fz[qq];
-                u[0] = P.ux[qq]; u[1] = P.uy[qq]; u[2] = P.uz[qq];
+              [&]() { return P.cell[pos]; },
+              [&](T* f, U* u) {
+                f[0] = P.fx[pos]; f[1] = P.fy[pos]; f[2] = P.fz[pos];
+                u[0] = P.ux[pos]; u[1] = P.uy[pos]; u[2] = P.uz[pos];
               },
+              [&]() { return P.id[pos]; },
               [&]() {});
         }
       }
     }
     // particles lost before this step sit at the tail of the sorted order (the
     // bucket after the last tile); they keep that bucket in the re-sort
-    for (long long q = offset[p.nkeys] + (long long)blockIdx.x * blockDim.x + tid; q < np;
-         q += (long long)gridDim.x * blockDim.x) {
-      key[q] = p.nkeys;
-      rank[q] = bin_rank(count, p.nkeys);
-    }
+    lost_tail(a);
   };
   if constexpr (!kBatch) {
     const PushArgs<T, U>& a = prm.args;
@@ -581,15 +617,7 @@ __global__ void __launch_bounds__(kPushThreads, (sizeof(T) == 4 ? 3 : 1))
       dense(a, &prm.box[mi], &prm.box_d[mi], w - prm.pref[mi], th);
     }
     // the particles each member lost before this step keep their bucket
-    for (int r = 0; r < M; ++r) {
-      const PushArgs<T, U>& a = prm.m[r];
-      const int nk = a.p.nkeys;
-      for (long long q = a.offset[nk] + (long long)blockIdx.x * blockDim.x + tid; q < a.np;
-           q += (long long)gridDim.x * blockDim.x) {
-        a.key[q] = nk;
-        a.rank[q] = bin_rank(a.count, nk);
-      }
-    }
+    for (int r = 0; r < M; ++r) lost_tail(prm.m[r]);
   }
 }
 
