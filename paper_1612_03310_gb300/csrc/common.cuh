@@ -52,6 +52,59 @@ __host__ __device__ inline V4<T> operator*(T s, V4<T> a) {
   return v4(s * a.x, s * a.y, s * a.z, s * a.w);
 }
 
+// Four-component arithmetic of the potential update.  kPack: FP32 as two
+// packed pairs (sm_100's paired FP32 add, multiply and fused multiply-add:
+// one instruction for two components, each rounded as the scalar operation;
+// a - b as fma(b, -1, a), which rounds a - b once); otherwise (and for FP64)
+// the component-wise operators.  vfma(s, a, b) is s a + b, vfma4 the same
+// with one factor per component.
+__device__ inline float2 v4_xy(V4<float> a) { return make_float2(a.x, a.y); }
+__device__ inline float2 v4_zw(V4<float> a) { return make_float2(a.z, a.w); }
+__device__ inline V4<float> v4_of(float2 xy, float2 zw) { return v4(xy.x, xy.y, zw.x, zw.y); }
+
+template <bool kPack, typename T>
+__device__ inline V4<T> vadd(V4<T> a, V4<T> b) {
+  if constexpr (kPack && sizeof(T) == 4)
+    return v4_of(__fadd2_rn(v4_xy(a), v4_xy(b)), __fadd2_rn(v4_zw(a), v4_zw(b)));
+  else
+    return a + b;
+}
+template <bool kPack, typename T>
+__device__ inline V4<T> vsub(V4<T> a, V4<T> b) {
+  if constexpr (kPack && sizeof(T) == 4) {
+    const float2 m = make_float2(-1.0f, -1.0f);
+    return v4_of(__ffma2_rn(v4_xy(b), m, v4_xy(a)), __ffma2_rn(v4_zw(b), m, v4_zw(a)));
+  } else {
+    return a - b;
+  }
+}
+template <bool kPack, typename T>
+__device__ inline V4<T> vmul(T s, V4<T> a) {
+  if constexpr (kPack && sizeof(T) == 4) {
+    const float2 ss = make_float2(s, s);
+    return v4_of(__fmul2_rn(ss, v4_xy(a)), __fmul2_rn(ss, v4_zw(a)));
+  } else {
+    return s * a;
+  }
+}
+template <bool kPack, typename T>
+__device__ inline V4<T> vfma(T s, V4<T> a, V4<T> b) {
+  if constexpr (kPack && sizeof(T) == 4) {
+    const float2 ss = make_float2(s, s);
+    return v4_of(__ffma2_rn(ss, v4_xy(a), v4_xy(b)), __ffma2_rn(ss, v4_zw(a), v4_zw(b)));
+  } else {
+    return s * a + b;
+  }
+}
+template <bool kPack, typename T>
+__device__ inline V4<T> vfma4(V4<T> s, V4<T> a, V4<T> b) {
+  if constexpr (kPack && sizeof(T) == 4)
+    return v4_of(__ffma2_rn(v4_xy(s), v4_xy(a), v4_xy(b)),
+                 __ffma2_rn(v4_zw(s), v4_zw(a), v4_zw(b)));
+  else
+    return v4(s.x * a.x, s.y * a.y, s.z * a.z, s.w * a.w) + b;
+}
+
 template <typename T>
 __device__ inline V4<T> ldg4(const V4<T>* p) {
   return __ldg(p);

@@ -44,6 +44,13 @@ struct mithra_sim {
   // before the re-sort advances the step counter
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // inside a captured run of steps, the re-sort of a step (scan and slot
+  // map) runs on the side stream beside the next step's potential update,
+  // which reads nothing it writes, and is joined before the next particle
+  // step; resort_pending marks a step whose re-sort is still to be launched
+  // (never true between API calls)
+  cudaEvent_t ev_rs_fork = nullptr, ev_rs_join = nullptr;
+  bool resort_pending = false;
   int cur = 0;  // P[cur] holds the newest level
   int pb = 0;   // particle buffer in use
   void* P[2] = {nullptr, nullptr};  // psi ping-pong; P[cur] is the newest level
@@ -395,13 +402,14 @@ Parts<T, U> parts_of(mithra_sim* s, int b) {
   return P;
 }
 
-// Two-pass scan of the per-tile counts (see k_scan_final).
-void launch_scan(mithra_sim* s, int advance) {
+// Two-pass scan of the per-tile counts (see k_scan_final), on stream q
+// (default: the simulation's).
+void launch_scan(mithra_sim* s, int advance, cudaStream_t q = nullptr) {
+  if (!q) q = s->stream;
   const int nb = (s->nkeys + 1 + kScanBlock - 1) / kScanBlock;
   const int sparse_below = s->push_variant == 1 ? s->push_sparse_below : 0;
-  k_scan_partials<<<nb, kScanBlock, 0, s->stream>>>(s->count, s->nkeys, sparse_below,
-                                                    s->scan_part);
-  k_scan_final<<<nb, kScanBlock, 0, s->stream>>>(s->count, s->offset, s->tiles, s->nkeys,
+  k_scan_partials<<<nb, kScanBlock, 0, q>>>(s->count, s->nkeys, sparse_below, s->scan_part);
+  k_scan_final<<<nb, kScanBlock, 0, q>>>(s->count, s->offset, s->tiles, s->nkeys,
                                                  sparse_below, s->scan_part, nb, s->dstate,
                                                  advance);
 }
@@ -494,8 +502,33 @@ void set_source_flags(const mithra_sim* s, int c, StencilP<T>* sp) {
   sp->nty = s->nty;
 }
 
+// The re-sort of the particle step just launched: scan of the tile counts
+// (it advances the device step counter) and the slot map, on stream q.
+void launch_resort(mithra_sim* s, cudaStream_t q) {
+  {
+    ProfScope ps(s, K_SCAN);
+    launch_scan(s, 1, q);
+  }
+  ProfScope ps(s, K_SCATTER);
+  k_slot_map<<<blocks_for(s->np, 256 * kSlotPer), 256, 0, q>>>(s->np, s->key, s->rank,
+                                                               s->offset, s->perm);
+}
+
+// One field step.  defer: leave this step's re-sort to the next launch_step
+// of the same captured run, which runs it beside its potential update.
 template <typename T, typename U>
-mithra_status launch_step(mithra_sim* s) {
+mithra_status launch_step(mithra_sim* s, bool defer = false) {
+  // the previous step's re-sort, beside this step's potential update (which
+  // reads neither the tile counts nor the slot map), joined before the seed
+  // and the particle step read the step counter it advances
+  const bool overlap = s->resort_pending;
+  if (overlap) {
+    cudaEventRecord(s->ev_rs_fork, s->stream);
+    cudaStreamWaitEvent(s->side, s->ev_rs_fork, 0);
+    launch_resort(s, s->side);
+    cudaEventRecord(s->ev_rs_join, s->side);
+    s->resort_pending = false;
+  }
   StencilP<T> sp = make_stencil<T>(s->g);
   set_source_flags(s, s->cur, &sp);
   PicP<T> pp = make_pic<T>(s);
@@ -555,6 +588,7 @@ mithra_status launch_step(mithra_sim* s) {
       else
         k_potential_step<false, T><<<grd, blk, 0, s->stream>>>(sp, P0, L0, P1, L1, Dn, S);
     }
+    if (overlap) cudaStreamWaitEvent(s->stream, s->ev_rs_join, 0);
     if (s->seed.on && s->seed.beam) {
       dim3 blk(kSeedTile, kSeedTile, 1);
       dim3 grd((s->g.nx - 2 + kSeedTile - 1) / kSeedTile,
@@ -659,15 +693,10 @@ mithra_status launch_step(mithra_sim* s) {
       cudaEventRecord(s->ev_join, s->side);
       cudaStreamWaitEvent(s->stream, s->ev_join, 0);
     }
-    {
-      ProfScope ps(s, K_SCAN);
-      launch_scan(s, 1);
-    }
-    {
-      ProfScope ps(s, K_SCATTER);
-      k_slot_map<<<blocks_for(s->np, 256), 256, 0, s->stream>>>(s->np, s->key, s->rank,
-                                                                  s->offset, s->perm);
-    }
+    if (defer && !s->profiling)
+      s->resort_pending = true;
+    else
+      launch_resort(s, s->stream);
     s->pb = 1 - s->pb;
   } else {
     if (branch) {
@@ -903,6 +932,8 @@ void free_all(mithra_sim* s) {
   if (s->side) cudaStreamDestroy(s->side);
   if (s->ev_fork) cudaEventDestroy(s->ev_fork);
   if (s->ev_join) cudaEventDestroy(s->ev_join);
+  if (s->ev_rs_fork) cudaEventDestroy(s->ev_rs_fork);
+  if (s->ev_rs_join) cudaEventDestroy(s->ev_rs_join);
   if (s->own_stream && s->stream) cudaStreamDestroy(s->stream);
 }
 
@@ -1009,7 +1040,9 @@ mithra_status mithra_create(const mithra_grid* grid, const mithra_undulator* und
   }
   if (cudaStreamCreateWithFlags(&s->side, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&s->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming) != cudaSuccess)
+      cudaEventCreateWithFlags(&s->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&s->ev_rs_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&s->ev_rs_join, cudaEventDisableTiming) != cudaSuccess)
     return bail(MITHRA_ECUDA, "side stream creation failed");
   const size_t r = real_size(precision);
   const size_t field_bytes = (size_t)ncell_of(grid) * 4 * r;
@@ -1093,6 +1126,9 @@ mithra_status mithra_create(const mithra_grid* grid, const mithra_undulator* und
 }
 
 namespace {
+// Steps per captured graph of mithra_step (even).
+constexpr int kGraphSteps = 4;
+
 // Drops the captured steps of s (and of the batch s belongs to: a launch
 // parameter of s changed).
 void drop_step_graphs(mithra_sim* s) {
@@ -1103,18 +1139,21 @@ void drop_step_graphs(mithra_sim* s) {
   if (s->in_batch) batch_mark_dirty(s->in_batch);
 }
 
-// Captures two steps from the current state (they bring the level and
-// particle buffers back to it) into s->step_exec[s->cur].
-mithra_status capture_step_pair(mithra_sim* s) {
+// Captures kGraphSteps steps from the current state (an even number: they
+// bring the level and particle buffers back to it) into
+// s->step_exec[s->cur]; each step's re-sort but the last runs beside the
+// next step's potential update.
+mithra_status capture_step_run(mithra_sim* s) {
   cudaGraph_t graph = nullptr;
   cudaError_t e = cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return cuda_fail(s, e, "begin capture of the step");
   mithra_status st = MITHRA_OK;
-  for (int k = 0; k < 2 && st == MITHRA_OK; ++k)
+  for (int k = 0; k < kGraphSteps && st == MITHRA_OK; ++k)
     st = with_types(s->prec, [&](auto t, auto u) {
       TYPES_OF(t, u);
-      return launch_step<T, U>(s);
+      return launch_step<T, U>(s, k + 1 < kGraphSteps);
     });
+  s->resort_pending = false;
   e = cudaStreamEndCapture(s->stream, &graph);
   if (st != MITHRA_OK) {
     if (graph) cudaGraphDestroy(graph);
@@ -1148,9 +1187,9 @@ mithra_status mithra_step(mithra_sim* s, int64_t n) {
                                      " particle(s) left the valid region (strict mode)");
   if (s->in_batch) return fail(s, MITHRA_EBUSY, "sim belongs to a batch: step it with mithra_batch_step");
   int64_t t = 0;
-  // runs of steps replay a captured pair (no profiling events inside; the
+  // runs of steps replay a captured run (no profiling events inside; the
   // legacy and per-thread default streams cannot be captured)
-  bool graph = n >= 3 && !s->profiling && s->stream != nullptr &&
+  bool graph = n >= kGraphSteps && !s->profiling && s->stream != nullptr &&
                s->stream != reinterpret_cast<cudaStream_t>(1) &&
                s->stream != reinterpret_cast<cudaStream_t>(2);
   if (graph) {  // a stream the caller is capturing takes the launches themselves
@@ -1161,13 +1200,13 @@ mithra_status mithra_step(mithra_sim* s, int64_t n) {
   }
   if (graph) {
     if (!s->step_exec[s->cur]) {
-      mithra_status st = capture_step_pair(s);
+      mithra_status st = capture_step_run(s);
       if (st != MITHRA_OK) return st;
     }
-    for (; t + 1 < n; t += 2) {
+    for (; t + kGraphSteps <= n; t += kGraphSteps) {
       cudaError_t e = cudaGraphLaunch(s->step_exec[s->cur], s->stream);
       if (e != cudaSuccess) return cuda_fail(s, e, "step graph launch");
-      s->n_issued += 2;
+      s->n_issued += kGraphSteps;
     }
   }
   for (; t < n; ++t) {

@@ -726,13 +726,29 @@ __global__ void __launch_bounds__(256) k_sort_particles(Parts<T, U> a, Parts<T, 
   perm[d] = (int)d;
 }
 
+// kSlotPer particles a thread (strided by the block, so that the loads of
+// key and rank stay coalesced), all their loads in flight before the stores.
+constexpr int kSlotPer = 4;
+
 __global__ void __launch_bounds__(256) k_slot_map(long long np, const int* __restrict__ key,
                                                   const int* __restrict__ rank,
                                                   const int* __restrict__ offset,
                                                   int* __restrict__ perm) {
-  const long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (q >= np) return;
-  slot_one(q, key, rank, offset, perm);
+  const long long q0 = blockIdx.x * (long long)(blockDim.x * kSlotPer) + threadIdx.x;
+  int kk[kSlotPer], rr[kSlotPer];
+#pragma unroll
+  for (int u = 0; u < kSlotPer; ++u) {
+    const long long q = q0 + (long long)u * blockDim.x;
+    if (q < np) {
+      kk[u] = key[q];
+      rr[u] = rank[q];
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < kSlotPer; ++u) {
+    const long long q = q0 + (long long)u * blockDim.x;
+    if (q < np) perm[(long long)offset[kk[u]] + rr[u]] = (int)q;
+  }
 }
 
 // Copy-out in the original particle order: FP64 positions from (cell, f).
