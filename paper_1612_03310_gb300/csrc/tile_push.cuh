@@ -396,7 +396,8 @@ __global__ void __launch_bounds__(kPushThreads, (sizeof(T) == 4 ? 3 : 1))
     long long* const& lost_ctr = a.lost_ctr;
     {
       const int tile = tiles[t];
-      // the tile's particle range, loaded while the boxes are in flight
+      // the tile's particle range and the position of this thread's first
+      // particle, loaded while the boxes are in flight
       const int beg = offset[tile], end = offset[tile + 1];
       int i0, j0, k0;
       tile_origin(p, tile, &i0, &j0, &k0);
@@ -407,6 +408,18 @@ __global__ void __launch_bounds__(kPushThreads, (sizeof(T) == 4 ? 3 : 1))
         tma_load_field(sD, tmd, i0 - 1, j0 - 1, k0 - 1, bar);
       }
       if (tid < 27) mark_tile(a, tile, tid);
+      // the lo parts of psi^{n+1}, which the E/B phase reads from global
+      // memory (the update that wrote them has since streamed the grid
+      // through L2), asked of L2 while the boxes are in flight: the first
+      // and last vertex of each of the box's 11 x 11 rows of 88 bytes
+      // (clamped to the grid)
+      if (kLo && p.plo && tid < 2 * kTP * kTP) {
+        const int r = tid >> 1;
+        const int ii = min(max(i0 - 1 + (tid & 1) * (kTP - 1), 0), p.nx - 1);
+        const int jj = min(max(j0 - 1 + r % kTP, 0), p.ny - 1);
+        const int kk = min(max(k0 - 1 + r / kTP, 0), p.nz - 1);
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(p.plo + cidx(ii, jj, kk, p.nx, p.nxy)));
+      }
       // FP64 moving-window bookkeeping once per tile and sub-step
       for (int m = tid; m < p.n_sub && m < kMaxFrames; m += blockDim.x)
         s_frame[m] = und_frame(p, k0, th + m * p.dtb);
