@@ -158,13 +158,13 @@ PRECISIONS = {"p32": "P32", "p32_u64": "P32_U64", "p32_c": "P32_C", "p64": "P64"
 # capture must leave this table
 NCU_TRAFFIC = {
     # k_mur_boundary<1, float, 1, 1> + k_potential_zloop_mur1<1, float>
-    ("potential_step", "p32_u64", "c2"): 35241984 + 226560 + 725267200 + 634713088,
+    ("potential_step", "p32_u64", "c2"): 35241728 + 193792 + 725030656 + 634913024,
     # k_push_tiled<0, float, FF2, 1, 0>
-    ("push", "p32_u64", "c2"): None,
+    ("push", "p32_u64", "c2"): 252840960 + 107983616,
     # k_mur_boundary<0, float, 1, 1> + k_potential_zloop_mur1<0, float>
-    ("potential_step", "p32", "c2"): 28196864 + 56832 + 588861184 + 498598912,
+    ("potential_step", "p32", "c2"): 28195072 + 52224 + 589120000 + 498829312,
     # k_push_tiled<0, float, float, 0, 0>
-    ("push", "p32", "c2"): None,
+    ("push", "p32", "c2"): 199732992 + 80613888,
 }
 
 

@@ -1,8 +1,10 @@
-"""Runs of three or more steps replay a captured pair of steps (CUDA graph);
-single steps launch the kernels one by one.  Both give the same state
-(within the order of floating-point atomic additions), from either parity of
-the level ping-pong, and a change of the diagnostics or launch choices
-between runs reaches the replayed steps."""
+"""Runs of four or more steps replay a captured run of four steps (CUDA
+graph), in which each step's re-sort but the last runs on a side stream
+beside the next step's potential update; single steps launch the kernels
+one by one, the re-sort at the end of its own step.  Both give the same
+state (within the order of floating-point atomic additions), from either
+parity of the level ping-pong, and a change of the diagnostics or launch
+choices between runs reaches the replayed steps."""
 import numpy as np
 import pytest
 
