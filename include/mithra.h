@@ -187,12 +187,14 @@ mithra_status mithra_create(const mithra_grid* grid, const mithra_undulator* und
  * grid and undulator fields (Sec. "Undulator Field"), the deposit of J and
  * rho (Sec. "Current Deposition", Eq. currentIntegral), then the re-sort of
  * the particles into cell tiles and the optional power sample.
- * With n >= 3 (and no profiling, and a stream other than the legacy or
+ * With n >= 4 (and no profiling, and a stream other than the legacy or
  * per-thread default stream that the caller is not capturing itself) the
- * steps run as replays of two steps captured
- * once as a CUDA graph per parity of the level ping-pong; any later change of
- * sampling, spectrum, seed, fields or tuning re-captures them.  Returns the
- * status of work that has already finished. */
+ * steps run as replays of four steps captured once as a CUDA graph per
+ * parity of the level ping-pong (the remainder of n one by one); inside a
+ * replay each step's re-sort but the last runs on an internal side stream
+ * beside the next step's potential update.  Any later change of sampling,
+ * spectrum, seed, fields or tuning re-captures them.  Returns the status of
+ * work that has already finished. */
 mithra_status mithra_step(mithra_sim* sim, int64_t n);
 
 /* Waits for all enqueued work; returns its status. */
@@ -456,10 +458,10 @@ mithra_status mithra_plane_power_noalloc(const mithra_grid* grid, double gamma0,
  * graph (two steps return each member's ping-pong buffers to their state at
  * capture).  Two forms of the graph:
  *   - fused: a step is eight launches whatever the number of members (for
- *     every 40 members of the particle step and 96 of the grid phases one
+ *     every 30 members of the particle step and 96 of the grid phases one
  *     more): the boundary rest, the potential update, the power sample, the
  *     numbering of the members' tiles, the particle step, the two scan
- *     passes of the re-sort and the scatter, each one kernel over a work list
+ *     passes of the re-sort and its slot map, each one kernel over a work list
  *     that spans all members (flat block lists for the grid phases,
  *     persistent CTAs taking every member's tiles from one counter for the
  *     particle step), with each member's arguments in the launch's
