@@ -157,12 +157,14 @@ __device__ inline PlaneTerms<T> plane_terms(const StencilP<T>& p, LdHi&& hi, LdL
           vfma<kPack>(p.rxB, X, vmul<kPack>(p.ryB, Y)), h.c, cl};
 }
 
+// (The sum (m.a + z.b) + pl.a in this order: the z-marching loop carries
+// its first part from one plane to the next.)
 template <bool kLo, typename T>
 __device__ inline V4<T> terms_laplacian(const StencilP<T>& p, const PlaneTerms<T>& m,
                                         const PlaneTerms<T>& z, const PlaneTerms<T>& pl) {
   constexpr bool kPack = !kLo;
   V4<T> L = vfma<kPack>(p.rz2, vadd<kPack>(vsub<kPack>(pl.c, z.c), vsub<kPack>(m.c, z.c)),
-                        vadd<kPack>(vadd<kPack>(m.a, pl.a), z.b));
+                        vadd<kPack>(vadd<kPack>(m.a, z.b), pl.a));
   if (kLo) L = L + p.rz2 * ((pl.cl - z.cl) + (m.cl - z.cl));
   return L;
 }
@@ -411,8 +413,17 @@ __device__ __forceinline__ void zloop_body(const StencilP<T>& p, const V4<T>* __
   const int nx = p.nx;
   auto hi = [&](long long q) { return ldg4(cur + q); };
   auto lo = [&](long long q) { return ld_lo<T>(curlo, q); };
-  PlaneTerms<T> tm = plane_terms<kLo>(p, hi, lo, (long long)(kb - 1) * p.nxy + col, nx);
-  PlaneTerms<T> t0 = plane_terms<kLo>(p, hi, lo, (long long)kb * p.nxy + col, nx);
+  // the loop carries m.a + z.b (ab), z.a and the column's hi and lo of the
+  // planes k-1 and k: a plane's b term is used only while it is plane k,
+  // so 24 instead of 32 values (measured 2 % off the compensated update)
+  V4<T> ab, a0, cm, clm, c0, cl0;
+  {
+    const PlaneTerms<T> tm = plane_terms<kLo>(p, hi, lo, (long long)(kb - 1) * p.nxy + col, nx);
+    const PlaneTerms<T> t0 = plane_terms<kLo>(p, hi, lo, (long long)kb * p.nxy + col, nx);
+    ab = vadd<!kLo>(tm.a, t0.b);
+    a0 = t0.a;
+    cm = tm.c; clm = tm.cl; c0 = t0.c; cl0 = t0.cl;
+  }
   // sources: loaded (and cleared) in the tiles the particle step marked only
   const bool src_every = p.dirty == nullptr || *p.src_all != 0;
   const int trow = (j >> 3) * p.ntx + (i >> 3), ntxy = p.ntx * p.nty;
@@ -431,7 +442,10 @@ __device__ __forceinline__ void zloop_body(const StencilP<T>& p, const V4<T>* __
       asm volatile("prefetch.global.L2 [%0];" ::"l"(D + q + p.nxy));
     }
     const PlaneTerms<T> tp = plane_terms<kLo>(p, hi, lo, q + p.nxy, nx);
-    const V4<T> L = terms_laplacian<kLo>(p, tm, t0, tp);
+    // terms_laplacian's arithmetic with m.a + z.b carried
+    V4<T> L = vfma<!kLo>(p.rz2, vadd<!kLo>(vsub<!kLo>(tp.c, c0), vsub<!kLo>(cm, c0)),
+                         vadd<!kLo>(ab, tp.a));
+    if (kLo) L = L + p.rz2 * ((tp.cl - cl0) + (clm - cl0));
     const V4<T> dm = D[q];
     V4<T> sv = v4((T)0, (T)0, (T)0, (T)0);
     if (src_every || p.dirty[(k >> 3) * ntxy + trow] != 0) sv = src[q];
@@ -448,14 +462,15 @@ __device__ __forceinline__ void zloop_body(const StencilP<T>& p, const V4<T>* __
     D[q] = dp;
     if (kLo) {
       V4<T> h, l;
-      comp_add(t0.c, t0.cl, dp, &h, &l);
+      comp_add(c0, cl0, dp, &h, &l);
       nxt[q] = h;
       st_lo(nxtlo, q, l);
     } else {
-      nxt[q] = vadd<true>(t0.c, dp);
+      nxt[q] = vadd<true>(c0, dp);
     }
-    tm = t0;
-    t0 = tp;
+    ab = vadd<!kLo>(a0, tp.b);
+    a0 = tp.a;
+    cm = c0; clm = cl0; c0 = tp.c; cl0 = tp.cl;
   }
 }
 
