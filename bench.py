@@ -207,7 +207,7 @@ def algorithmic_bytes(kernel: str, grid: dict, n_particles: int, prec: str,
         # read the slot's position, read and write cell + 3 fractions + 3
         # momenta + original index; write key and rank
         return n_particles * (4 + 2 * (8 + 3 * r + 3 * um) + 8)
-    if kernel == "scatter":
+    if kernel == "slot_map":
         # the re-sort's slot map: read key, rank and offset, write the slot's
         # position
         return n_particles * 16

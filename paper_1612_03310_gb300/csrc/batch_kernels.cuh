@@ -24,7 +24,7 @@
 
 namespace mithra {
 
-enum BatchPhase { kBPMur = 0, kBPZ, kBPPow, kBPScan, kBPScat, kBPCount };
+enum BatchPhase { kBPMur = 0, kBPZ, kBPPow, kBPScan, kBPSlot, kBPCount };
 
 // Member of flat block g: the m with blk[m] <= g < blk[m+1] (blk has M + 1
 // non-decreasing entries, blk[0] = 0).
@@ -197,7 +197,7 @@ __global__ void __launch_bounds__(kScanBlock) kb_scan_final(
 
 // The re-sort's slot map (slot_one), 256 particles per block.
 template <typename T, typename U>
-__global__ void __launch_bounds__(256) kb_scatter(const BatchMember<T, U>* __restrict__ mem,
+__global__ void __launch_bounds__(256) kb_slot_map(const BatchMember<T, U>* __restrict__ mem,
                                                   const int* __restrict__ blk, int M) {
   const int g = blockIdx.x;
   const int mi = member_of(blk, M, g);

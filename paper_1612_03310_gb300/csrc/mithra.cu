@@ -140,8 +140,8 @@ void batch_mark_dirty(mithra_batch* b);  // defined with the batch
 
 namespace {
 
-enum KernelId { K_POTENTIAL = 0, K_POWER, K_PUSH, K_SCAN, K_SCATTER, K_SPECTRUM, K_COUNT };
-const char* kKernelNames[K_COUNT] = {"potential_step", "power", "push", "scan_counts", "scatter",
+enum KernelId { K_POTENTIAL = 0, K_POWER, K_PUSH, K_SCAN, K_SLOT_MAP, K_SPECTRUM, K_COUNT };
+const char* kKernelNames[K_COUNT] = {"potential_step", "power", "push", "scan_counts", "slot_map",
                                      "spectrum"};
 
 cudaEvent_t take_event(mithra_sim* s) {
@@ -509,7 +509,7 @@ void launch_resort(mithra_sim* s, cudaStream_t q) {
     ProfScope ps(s, K_SCAN);
     launch_scan(s, 1, q);
   }
-  ProfScope ps(s, K_SCATTER);
+  ProfScope ps(s, K_SLOT_MAP);
   k_slot_map<<<blocks_for(s->np, 256 * kSlotPer), 256, 0, q>>>(s->np, s->key, s->rank,
                                                                s->offset, s->perm);
 }
@@ -2065,8 +2065,8 @@ mithra_status capture_fused_typed(mithra_batch* b) {
     }
     kb_scan_partials<T, U><<<total(kBPScan), kScanBlock, 0, q>>>(mem, dblk + kBPScan * (M + 1), M);
     kb_scan_final<T, U><<<total(kBPScan), kScanBlock, 0, q>>>(mem, dblk + kBPScan * (M + 1), M);
-    if (total(kBPScat) > 0)
-      kb_scatter<T, U><<<total(kBPScat), 256, 0, q>>>(mem, dblk + kBPScat * (M + 1), M);
+    if (total(kBPSlot) > 0)
+      kb_slot_map<T, U><<<total(kBPSlot), 256, 0, q>>>(mem, dblk + kBPSlot * (M + 1), M);
   }
   cudaError_t le = cudaGetLastError();
   e = cudaStreamEndCapture(b->stream, &graph);

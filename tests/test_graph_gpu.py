@@ -110,3 +110,30 @@ def test_replay_with_sub_steps_and_both_undulators(M, prec_name, n_sub, optical,
         assert np.array_equal(qa["lost"], qb["lost"])
         for k in ("ux", "uy", "uz"):
             assert rel_l2(qa[k], qb[k]) <= tol, k
+
+
+def test_profiled_steps_between_replays(M):
+    """Per-kernel timing keeps every kernel of a step on the simulation's
+    stream and each step's re-sort at its own end; runs replayed before and
+    after it (their re-sorts beside the next update) give the state of
+    single steps, and the timed scopes count one launch per step."""
+    a, b = pair(M, M.P32, seed=5)
+    with a, b:
+        a.step(4)            # one replay
+        a.profile(True)
+        a.step(6)            # one by one, timed
+        kt = a.kernel_times()
+        a.profile(False)
+        a.step(9)            # two replays and one single step
+        for _ in range(19):
+            b.step(1)
+        assert a.time()[0] == b.time()[0] == 19
+        for k in ("potential_step", "push", "scan_counts", "slot_map"):
+            assert kt[k][1] == 6, (k, kt[k])
+            assert kt[k][0] > 0.0, (k, kt[k])
+        for nm in FIELDS:
+            assert rel_l2(a.copy_field(nm), b.copy_field(nm)) <= 1e-5, nm
+        qa, qb = a.copy_particles(), b.copy_particles()
+        assert np.array_equal(qa["lost"], qb["lost"])
+        for k in ("x", "y", "z", "ux", "uy", "uz"):
+            assert rel_l2(qa[k], qb[k]) <= 1e-5, k
