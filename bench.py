@@ -158,13 +158,13 @@ PRECISIONS = {"p32": "P32", "p32_u64": "P32_U64", "p32_c": "P32_C", "p64": "P64"
 # capture must leave this table
 NCU_TRAFFIC = {
     # k_mur_boundary<1, float, 1, 1> + k_potential_zloop_mur1<1, float>
-    ("potential_step", "p32_u64", "c2"): 35241728 + 193792 + 725030656 + 634913024,
+    ("potential_step", "p32_u64", "c2"): 35241728 + 187392 + 725083904 + 634589184,
     # k_push_tiled<0, float, FF2, 1, 0>
-    ("push", "p32_u64", "c2"): 252840960 + 107983616,
+    ("push", "p32_u64", "c2"): 252839424 + 108283648,
     # k_mur_boundary<0, float, 1, 1> + k_potential_zloop_mur1<0, float>
-    ("potential_step", "p32", "c2"): 28195072 + 52224 + 589120000 + 498829312,
+    ("potential_step", "p32", "c2"): 28195072 + 39680 + 589268224 + 498427136,
     # k_push_tiled<0, float, float, 0, 0>
-    ("push", "p32", "c2"): 199732992 + 80613888,
+    ("push", "p32", "c2"): 201409792 + 84482048,
 }
 
 
@@ -196,13 +196,15 @@ def algorithmic_bytes(kernel: str, grid: dict, n_particles: int, prec: str,
     lo = prec in ("p32_c", "p32_u64")                  # compensated potential levels
     interior = (grid["nx"] - 2) * (grid["ny"] - 2) * (grid["nz"] - 2)
     if kernel == "potential_step":
-        # read psi^n and the increment, write psi^{n+1} and the new
-        # increment: 4 x 4 values per interior cell, plus 2 x 8 bytes for the
-        # bfloat16 lo parts of compensated levels; and the 4 source values of
-        # every vertex of a marked tile (the zeroing stores of the sources
-        # the last deposit touched are not counted)
+        # every vertex of the grid (the interior by the update, the boundary
+        # by Mur in increment form, which also reads and writes the
+        # vertex's level and increment): read psi^n and the increment, write
+        # psi^{n+1} and the new increment, 4 x 4 values, plus 2 x 8 bytes
+        # for the bfloat16 lo parts of compensated levels; and the 4 source
+        # values of every vertex of a marked tile (the zeroing stores of the
+        # sources the last deposit touched are not counted)
         sv = interior if source_vertices is None else min(source_vertices, interior)
-        return interior * (4 * 4 * r + (16 if lo else 0)) + sv * 4 * r
+        return all_cells(grid) * (4 * 4 * r + (16 if lo else 0)) + sv * 4 * r
     if kernel == "push":
         # read the slot's position, read and write cell + 3 fractions + 3
         # momenta + original index; write key and rank
@@ -228,8 +230,7 @@ def minimum_bytes(kernel: str, grid: dict, n_particles: int, prec: str) -> float
         return algorithmic_bytes(kernel, grid, n_particles, prec)
     r = 8 if prec == "p64" else 4
     lo = prec in ("p32_c", "p32_u64")
-    interior = (grid["nx"] - 2) * (grid["ny"] - 2) * (grid["nz"] - 2)
-    return interior * (4 * 4 * r + (16 if lo else 0))
+    return all_cells(grid) * (4 * 4 * r + (16 if lo else 0))
 
 
 def max_over_ranks(x: float, world: int) -> float:
@@ -242,6 +243,10 @@ def max_over_ranks(x: float, world: int) -> float:
     t = torch.tensor([x], device=dev, dtype=torch.float64)
     torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
     return float(t.item())
+
+
+def all_cells(g: dict) -> int:
+    return g["nx"] * g["ny"] * g["nz"]
 
 
 def interior_cells(g: dict) -> int:
@@ -455,7 +460,7 @@ def run_c3(args, peak: float) -> dict:
             "stencil": {"avg_launch_ms": st_ms, "achieved_gbs": st_b / (st_ms / 1e3) / 1e9,
                         "frac": st_b / (st_ms / 1e3) / 1e9 / peak,
                         "cell_updates_per_s": ncell / (st_ms / 1e3),
-                        "bytes_per_cell": st_b / interior_cells(g), "source_reads": src},
+                        "bytes_per_cell": st_b / all_cells(g), "source_reads": src},
             "kernel_share": {k: round(v[0] / total, 4) for k, v in kt.items()},
             "tuning": tuning, "clocks": sampler.summary(), "n_lost": n_lost}
 
@@ -838,11 +843,16 @@ def main():
                      "traffic": NCU_TRAFFIC.get((dom, args.precision, args.workload))},
         "stencil": {"kernel": "potential_step", "avg_launch_ms": stencil_ms,
                     "achieved_gbs": stencil_gbs, "frac": stencil_gbs / peak,
-                    "bytes_per_cell": stencil_b / interior_cells(g),
+                    "bytes_per_cell": stencil_b / all_cells(g),
+                    "bytes_model": "every vertex of the grid (interior by the update, boundary "
+                                   "by Mur in increment form): read psi^n and D, write "
+                                   "psi^{n+1} and D (16 B each in FP32, plus 8 B lo parts read "
+                                   "and written for compensated levels), plus the 4 source "
+                                   "values of every vertex of the marked source tiles",
                     "source_reads": res["source_reads"],
                     "frac_at_minimum_bytes": stencil_min_gbs / peak,
                     "minimum_bytes_per_cell": minimum_bytes("potential_step", res["grid"], npart,
-                                                            args.precision) / interior_cells(g),
+                                                            args.precision) / all_cells(g),
                     "cell_updates_per_s": ncell / (stencil_ms / 1e3)},
         "push": push_rates(kt, npart, res["grid"], args.precision),
         "kernel_share": {k: round(v[0] / total_kernel_ms, 4) for k, v in kt.items()},
