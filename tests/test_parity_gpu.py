@@ -145,13 +145,16 @@ def compare_particles(sim, o, tol_cells, face_eps):
     ("P64", 0, 0), ("P64", 1, 0), ("P64", 1, 5), ("P64", 1, 1),
     ("P32", 0, 0), ("P32", 1, 0), ("P32", 1, 5), ("P32", 1, 1), ("P32", 2, 3),
     ("P32_C", 0, 0), ("P32_C", 2, 0), ("P32_C", 2, 5), ("P32_C", 2, 1), ("P64", 2, 7)])
-@pytest.mark.parametrize("shape", [(37, 29, 45), (4, 4, 4), (33, 9, 70), (5, 41, 6), (70, 17, 9)])
+@pytest.mark.parametrize("shape", [(37, 29, 45), (4, 4, 4), (33, 9, 70), (5, 41, 6), (70, 17, 9),
+                                   (64, 10, 30), (32, 4, 12)])
 @pytest.mark.parametrize("boundary", [1, 2])
 def test_vacuum_update_parity(M, orc, prec, shape, variant, lz, boundary):
     # every form of the potential update (direct; z-marching TMA tiles with
     # several plane-chunk lengths, ragged tiles in x and y -- single-float
     # levels only; register z-marching), first- and second-order Mur with
-    # random values on every boundary vertex
+    # random values on every boundary vertex; widths of whole 32-column
+    # blocks (64, 32) beside the ragged ones, and y+ faces in the second row
+    # of a block row (ny = 10) and in the first block row (ny = 4)
     nx, ny, nz = shape
     g = dict(inputs.random_grid(11, nx, ny, nz), boundary=boundary)
     f = inputs.random_fields(12, g)
