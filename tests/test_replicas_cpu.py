@@ -75,3 +75,22 @@ def test_push_rates():
     assert r["achieved_gbs"] == b.algorithmic_bytes("push", g, 1000, "p32") / 0.5e-3 / 1e9
     assert b.push_rates({"push": (2.0, 4)}, 1000, g, "p64")["shared_int32_atomics_per_s"] is None
     assert b.push_rates({}, 1000, g, "p32") is None
+
+
+def test_algorithmic_bytes_models():
+    """The bench's byte models: the potential update moves every grid
+    vertex's level and increment (16 B each in FP32, read and written, plus
+    the 8 B lo parts of compensated levels read and written) and the 16 B
+    of sources of each vertex whose sources it reads; the particle step
+    100 B per particle in P32_U64 (the slot's position, state and index in
+    and out, key and rank); the re-sort's slot map 16 B."""
+    b = _bench()
+    g = dict(nx=10, ny=12, nz=14)
+    n, interior = 10 * 12 * 14, 8 * 10 * 12
+    assert b.algorithmic_bytes("potential_step", g, 0, "p32") == n * 64 + interior * 16
+    assert b.algorithmic_bytes("potential_step", g, 0, "p32_u64", 512) == n * 80 + 512 * 16
+    assert b.algorithmic_bytes("potential_step", g, 0, "p64", 10 ** 9) == n * 128 + interior * 32
+    assert b.minimum_bytes("potential_step", g, 0, "p32_c") == n * 80
+    assert b.algorithmic_bytes("push", g, 7, "p32_u64") == 7 * 100
+    assert b.algorithmic_bytes("push", g, 7, "p32") == 7 * 76
+    assert b.algorithmic_bytes("slot_map", g, 7, "p32") == 7 * 16
