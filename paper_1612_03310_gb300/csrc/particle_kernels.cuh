@@ -1,7 +1,9 @@
 // particle_kernels.cuh -- macroparticles: set-up, gather + undulator + Boris
 // push (Eq. BorisScheme, Eq. fieldInterpolation, Sec. "Undulator Field"),
 // current and charge deposition (Sec. "Current Deposition",
-// Eq. currentIntegral), and the binning of particles into cell tiles.
+// Eq. currentIntegral), and the binning of particles into cell tiles (tile
+// counts, their scan, and the slot map through which the next particle step
+// reads the particles in tile order).
 #pragma once
 #include "common.cuh"
 #include "field_kernels.cuh"

@@ -6,9 +6,12 @@
 //      [t0 - 1, t0 + 9]^3 (11^3, two TMA box loads, one mbarrier);
 //   2. evaluates E and B at t = (n+1/2) dt at the tile's 9^3 vertices
 //      (Sec. "Field Evaluation") into shared memory;
-//   3. pushes the tile's particles: trilinear gather from shared memory
+//   3. pushes the tile's particles, each slot's particle read at the
+//      position the re-sort's slot map gives and written to the same slot
+//      of the other buffer: trilinear gather from shared memory
 //      (Eq. fieldInterpolation), rest-frame undulator field, Boris
-//      (Eq. BorisScheme), FP64 gamma, cell carry;
+//      (Eq. BorisScheme; 1/gamma to the particle precision's rounding, by a
+//      float-float Newton step in the FP32 forms), cell carry;
 //   4. deposits rho^{n+3/2} (end point) into a shared-memory block over the
 //      11^3 vertices -- in the FP32 forms as exact int32 fixed-point sums,
 //      added to the global sources once per touched vertex -- and
@@ -18,8 +21,8 @@
 // memory, and one whose deposit leaves the 11^3 block deposits with global
 // atomics: the same arithmetic on another path.  Sparse tiles (fewer
 // particles than the staging pays for) are then taken one per warp on that
-// global path.  Particles lost in earlier steps only get their re-sort
-// bucket.
+// global path.  Particles lost in earlier steps are only moved to the
+// other buffer and keep their re-sort bucket.
 #pragma once
 #include "common.cuh"
 #include "field_kernels.cuh"
