@@ -250,8 +250,10 @@ mithra_status mithra_set_power_sampling(mithra_sim* sim, int32_t k_plane, int64_
 mithra_status mithra_read_power(mithra_sim* sim, double* out, int64_t max_records,
                                 int64_t* count);
 
-/* Copies the particles back in their original order (the library keeps them
- * sorted by cell tile on the device): positions [m], momenta, and lost[p] = 1
+/* Copies the particles back in their original order (on the device the
+ * library keeps them in the order of their cell tiles, each step's re-sort
+ * writing the slot map the next step reads them through): positions [m],
+ * momenta, and lost[p] = 1
  * for lost particles (any of the pointers may be NULL).  *n_lost receives the
  * number of lost particles. */
 mithra_status mithra_copy_particles(mithra_sim* sim, double* x, double* y, double* z,
@@ -261,9 +263,9 @@ mithra_status mithra_copy_particles(mithra_sim* sim, double* x, double* y, doubl
 /* Checkpoint and resume.  mithra_snapshot_bytes gives the size of a
  * snapshot; mithra_snapshot waits for the stream and copies the simulation's
  * device state (both potential levels and their lo parts, the increment, the
- * sources, the particles, the last re-sort's tile offsets and list, the step
- * counter, lost count and error word) into out (host, caller-allocated, that
- * size).  mithra_restore copies such a snapshot back into a simulation
+ * sources, the particles, the last re-sort's tile offsets, list and slot map,
+ * the step counter, lost count and error word) into out (host,
+ * caller-allocated, that size).  mithra_restore copies such a snapshot back into a simulation
  * created with the same grid, precision and particle count (MITHRA_EINVAL
  * otherwise, nothing changed; MITHRA_EBUSY in a batch); its undulator, seed
  * and launch choices are its own.  Recording diagnostics (power, bunch,
