@@ -399,8 +399,7 @@ __global__ void __launch_bounds__(kPushThreads, (sizeof(T) == 4 ? 3 : 1))
     long long* const& lost_ctr = a.lost_ctr;
     {
       const int tile = tiles[t];
-      // the tile's particle range and the position of this thread's first
-      // particle, loaded while the boxes are in flight
+      // the tile's particle range, loaded while the boxes are in flight
       const int beg = offset[tile], end = offset[tile + 1];
       int i0, j0, k0;
       tile_origin(p, tile, &i0, &j0, &k0);
