@@ -160,11 +160,11 @@ NCU_TRAFFIC = {
     # k_mur_boundary<1, float, 1, 1> + k_potential_zloop_mur1<1, float>
     ("potential_step", "p32_u64", "c2"): 35241728 + 187392 + 725083904 + 634589184,
     # k_push_tiled<0, float, FF2, 1, 0>
-    ("push", "p32_u64", "c2"): 252839424 + 108283648,
+    ("push", "p32_u64", "c2"): None,
     # k_mur_boundary<0, float, 1, 1> + k_potential_zloop_mur1<0, float>
     ("potential_step", "p32", "c2"): 28195072 + 39680 + 589268224 + 498427136,
     # k_push_tiled<0, float, float, 0, 0>
-    ("push", "p32", "c2"): 201409792 + 84482048,
+    ("push", "p32", "c2"): None,
 }
 
 

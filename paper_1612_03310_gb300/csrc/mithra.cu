@@ -667,7 +667,20 @@ mithra_status launch_step(mithra_sim* s, bool defer = false) {
         pa.dirty = s->dirty;
         pa.dirty_words = s->dirty_words;
         pa.cur = s->cur;
-        kern<<<s->push_grid, kPushThreads, tile_smem_bytes<T, U>(), s->stream>>>(prm);
+        // a programmatic dependent launch: the grid is scheduled as the
+        // work before it drains and waits at its start for that work
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(s->push_grid);
+        cfg.blockDim = dim3(kPushThreads);
+        cfg.dynamicSmemBytes = tile_smem_bytes<T, U>();
+        cfg.stream = s->stream;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        const cudaError_t le = cudaLaunchKernelEx(&cfg, kern, prm);
+        if (le != cudaSuccess) return cuda_fail(s, le, "particle step launch");
       } else {
         decltype(&k_push<false, T, U, kAnyLo>) kern = nullptr;
         if constexpr (push_form_plain<T, U>())

@@ -324,6 +324,10 @@ __global__ void __launch_bounds__(kPushThreads, (sizeof(T) == 4 ? 3 : 1))
     mbar_fence_init();
   }
   __syncthreads();
+  // launched as a programmatic dependent of the potential update (one
+  // simulation): the CTAs are placed while the update drains, and wait here,
+  // before any global access, for it to complete (a no-op otherwise)
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   uint32_t phase = 0;
   // Source-tile flags (StencilP::dirty): the array this step's potential
   // update read is cleared, and the deposits mark the other -- a tile's 27
